@@ -1,0 +1,350 @@
+"""Benchmark: LS solves/s at relres 1e-8 on one GB300 (mixed precision and
+plain FP64), synthetic 2D workload of 256^2 unknowns, omega/2pi = 32.
+
+One step = the whole hot path for one medium and one batch of incident waves:
+medium update (moving-PML stencils + slab assembly), factorization of all slab
+subproblems + interface maps, right-hand sides g = -omega^2 K(m u_I), flexible
+GMRES(30) to relres 1e-8 with the sparsify-and-sweep preconditioner, true
+residual.  The per-(n, omega) tables (kernel FFT, alpha/beta, physical PML
+stencils) are built once when the solver is created, as the method allows.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs independent replicas (the solve does not shard); rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "LS solves/s at relres 1e-8, mixed+batched vs plain FP64 on one GB300"
+WORKLOAD = "2d_n256"
+HBM_FALLBACK_GBS = 6800.0
+# FP64 / FP32 CUDA-core peaks of a GB300 (derivation in the design notes):
+# FP64 1.25 TFLOP/s nominal; FP32 152 SMs x 128 FMA/clk x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def workload_cfg(name=WORKLOAD):
+    w = synth.WORKLOADS[name]
+    m, dirs = synth.make_workload(w)
+    return w, m, dirs
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.rows, self.proc, self.index = [], None, index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 8:
+                for k, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(k)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------- algorithmic work per kernel group
+def algorithmic(solver, R, prec_bytes):
+    """Per-launch algorithmic bytes / flops of each kernel group (design notes)."""
+    n, L, nt, ns = solver.n, solver.fft_len, solver.n_tot, solver.n_slabs
+    N = n * n
+    ws = []
+    for i in range(ns):
+        _, nl, na = solver.slab_info(i)
+        ws.append(na + nl)
+    ldw = [(w + 1) & ~1 for w in ws]
+    cstr = [(9 * w + 1) & ~1 for w in ws]
+    cb = 2 * prec_bytes
+    slab_bytes = sum(nt * (w * l + c) * cb for w, l, c in zip(ws, ldw, cstr)) + 2 * R * nt * nt * cb
+    slab_flops = sum(2 * nt * w * w * 8 for w in ws) * R
+    fft_flops = R * (n * 5 * L * math.log2(L) + L * 2 * 5 * L * math.log2(L) + n * 5 * L * math.log2(L))
+    mv_bytes = R * (16 * N * 2) + 8 * N + 16 * L * L
+    recur_bytes = 3 * max(ns - 1, 0) * nt * nt * cb
+    factor_flops = sum(nt * (8 * w ** 3 + 2 * 3 * 8 * w * w) for w in ws)
+    return {
+        "slab_a": dict(bytes=slab_bytes, flops=slab_flops, launches_per_apply=1),
+        "slab_e": dict(bytes=slab_bytes, flops=slab_flops, launches_per_apply=1),
+        "matvec": dict(bytes=mv_bytes, flops=fft_flops, launches_per_apply=3),
+        "recur": dict(bytes=recur_bytes, flops=recur_bytes // cb * 8 * R, launches_per_apply=1),
+        "factor": dict(bytes=sum(nt * w * l * cb for w, l in zip(ws, ldw)), flops=factor_flops,
+                       launches_per_apply=1),
+    }
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank, world):
+    import torch
+    from paper_1705_09443_gb300 import GmresOptions, LSS_FP64, LSS_MIXED, LSSolver
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w, m, dirs = workload_cfg(args.workload)
+    R = dirs.shape[0]
+    n = w.n
+    mt = torch.tensor(m, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    opts = GmresOptions(30, 1e-8, 300)
+    results = {}
+    for prec_name, prec in (("mixed", LSS_MIXED), ("fp64", LSS_FP64)):
+        solver = LSSolver(n, w.omega, mt, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec, factor=False)
+        stream = torch.cuda.current_stream()
+
+        def step():
+            solver.set_medium(mt)
+            solver.factor()
+            g = solver.plane_wave_rhs(dirs)
+            u, st = solver.solve(g, opts)
+            return st
+
+        for _ in range(args.warmup):
+            st = step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = ClockSampler(dev.index)
+        clk.start()
+        solver.profile_read()
+        solver.profile(True)
+        total_ms = 0.0
+        stats = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            stats.append(st)
+        solver.profile(False)
+        prof_ms, prof_n = solver.profile_read()
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        iters = [s["iters"] for st in stats for s in st]
+        relres = max(s["relres_true"] for st in stats for s in st)
+        conv = all(s["relres_true"] <= 1e-8 for st in stats for s in st)
+        res = dict(value=(R * args.steps * world) / (total_ms / 1e3), ms_per_step=total_ms / args.steps,
+                   iters=float(np.mean(iters)), relres_true_max=relres, converged=conv, clocks=clocks,
+                   prof_ms={k: v / args.steps for k, v in prof_ms.items()},
+                   prof_launches={k: v // args.steps for k, v in prof_n.items()},
+                   gpu_launches=int(sum(prof_n.values())), solver=solver,
+                   prec_bytes=8 if prec == LSS_FP64 else 4)
+        # e2e: medium from pinned host memory, solution back to pinned host memory
+        m_host = torch.tensor(m, dtype=torch.float64).pin_memory()
+        u_host = torch.empty((R, n, n), dtype=torch.complex128).pin_memory()
+        m_dev = torch.empty_like(mt)
+        e2e_ms = 0.0
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m_dev.copy_(m_host, non_blocking=True)
+            solver.set_medium(m_dev)
+            solver.factor()
+            g = solver.plane_wave_rhs(dirs)
+            u, st = solver.solve(g, opts)
+            u_host.copy_(u, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= args.warmup:
+                e2e_ms += e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        res["e2e"] = {"value": (R * args.steps * world) / (e2e_ms / 1e3), "unit": "solves/s",
+                      "h2d_bytes_per_step": int(n * n * 8 + R * 16), "d2h_bytes_per_step": int(R * n * n * 16)}
+        results[prec_name] = res
+    return w, R, results
+
+
+def roofline(res, hbm_peak, hbm_src):
+    solver = res["solver"]
+    alg = algorithmic(solver, 1, res["prec_bytes"])
+    cats = {k: v for k, v in res["prof_ms"].items() if k in alg}
+    dom = max(cats, key=lambda k: cats[k])
+    launches = max(res["prof_launches"].get(dom, 1), 1)
+    per_launch_ms = cats[dom] / launches
+    a = alg[dom]
+    if dom in ("recur",):
+        achieved = a["bytes"] / (per_launch_ms / 1e3) / 1e9
+        return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": hbm_src}
+    flops = a["flops"] if dom != "matvec" else a["flops"]
+    per = flops if dom != "matvec" else flops
+    if dom == "matvec":
+        per_launch_ms = cats[dom] / max(launches // 3, 1)
+    achieved = per / (per_launch_ms / 1e3) / 1e12
+    peak = FP64_PEAK_TFLOPS if (res["prec_bytes"] == 8 or dom == "matvec") else FP32_PEAK_TFLOPS
+    return dom, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": None, "peak_source": "derived (FP64 1.25 TFLOP/s nominal; FP32 from unit counts x clock)"}
+
+
+# ---------------------------------------------------------------- oracle (CPU) arm
+ORACLE_SNIPPET = r"""
+import json, sys, time, math
+sys.path.insert(0, {root!r})
+import numpy as np
+import synth
+from oracle import lss_oracle as O
+w = synth.WORKLOADS[{wl!r}]
+m, dirs = synth.make_workload(w)
+ts = []
+for k in range({reps}):
+    t0 = time.perf_counter()
+    res, relres, pb, g = O.solve(w.n, w.omega, m, dirs[0], O.Params(b_pml=w.b_pml, b_slab=w.b_slab), tol=1e-8)
+    ts.append(time.perf_counter() - t0)
+print(json.dumps(dict(times=ts, iters=res.iters, relres=relres)))
+"""
+
+
+def run_oracle(wl, reps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, wl=wl, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    w = synth.WORKLOADS[args.workload]
+    config = {"workload": f"2D LS, n={w.n} (N={w.n * w.n}), omega/2pi={w.freq:g}, {w.n_gauss} Gaussians "
+                          f"width {w.width} c in {list(w.c_range)}, {w.n_rhs} plane wave(s), PML {w.b_pml}, "
+                          f"slab {w.b_slab}, GMRES(30) tol 1e-8",
+              "l2": "flushed (256 MB write) before every timed step",
+              "per_omega_tables": "built once at solver creation (kernel FFT, alpha/beta, physical PML stencils)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.time()
+        reps = max(1, min(args.steps, 2))
+        out = run_oracle(args.workload, reps)
+        v = 1.0 / float(np.mean(out["times"]))
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+                "steps": reps, "warmup": 0, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                 "sample": f"{reps} full oracle solve(s) (setup + GMRES to 1e-8) of the benchmark "
+                                           f"workload, numpy/scipy single thread"},
+                "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "oracle_iters": out["iters"], "wall_s": time.time() - t0}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    cpu = None
+    w, R, results = run_ours(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle runs in a fresh interpreter (fork + exec), after the GPU timing
+        out = run_oracle(args.workload, 1)
+        cpu = {"value": 1.0 / out["times"][0], "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": "one full oracle solve (setup + GMRES to 1e-8) of the benchmark workload, "
+                         "numpy/scipy, single thread", "oracle_iters": out["iters"]}
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    hbm, src = peaks()
+    mix, f64 = results["mixed"], results["fp64"]
+    dom, roof = roofline(mix, hbm, src)
+    line = {
+        "metric": METRIC, "value": mix["value"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mix["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 sweep / f64 matvec+Arnoldi", "data": "synthetic",
+        "config": config, "e2e": mix["e2e"], "gpu_launches": mix["gpu_launches"],
+        "clocks": mix["clocks"], "roofline": dict(kernel=dom, **roof), "cpu_baseline": cpu,
+        "iters": mix["iters"], "relres_true_max": mix["relres_true_max"],
+        "plain_fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "iters": f64["iters"],
+                       "relres_true_max": f64["relres_true_max"], "e2e": f64["e2e"],
+                       "breakdown_ms": f64["prof_ms"], "clocks": f64["clocks"]},
+        "mixed_over_fp64": mix["value"] / f64["value"],
+        "breakdown_ms": mix["prof_ms"], "launches_per_step": mix["prof_launches"],
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

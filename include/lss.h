@@ -1,0 +1,217 @@
+/*
+ * lss.h - C ABI of the GB300 sparsify-and-sweep Lippmann-Schwinger solver.
+ *
+ * Liu & Ying, "Sparsify and sweep: an efficient preconditioner for the
+ * Lippmann-Schwinger equation", arXiv:1705.09443.
+ *
+ * The library solves the discrete Lippmann-Schwinger equation (Sec. 2.1,
+ * Eq. LS_d_c)
+ *        (I + omega^2 K M) u = g   on I = {1..n}^d,  h = 1/(n+1),
+ * with right-preconditioned restarted (flexible) GMRES whose preconditioner is
+ * the sparsify-and-sweep operator P = E * Sweep * Q of Sec. 2.2-2.4
+ * (Algorithms 1 and 2).  Every computation runs in the library's own CUDA
+ * kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *  - Vectors on I are complex128 (interleaved re, im doubles), row-major with
+ *    x1 slowest: element (i1, i2) at offset (i1-1)*n + (i2-1).  A batch of R
+ *    vectors is R such arrays back to back (stride n^d complex numbers).
+ *  - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *    host pointers owned by the caller.  The library never frees them and keeps
+ *    no reference after the call returns.
+ *  - The library owns the context, the slab factors and all workspace.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *    work on it; entry points that return host-visible results (stats) block
+ *    until those results are ready.
+ *  - Return value: LSS_OK (0) or a negative LSS_ERR_* code; lss_last_error()
+ *    then describes the failure.  A failed call leaves the context usable
+ *    unless the code is LSS_ERR_CUDA.
+ */
+#ifndef LSS_H
+#define LSS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lss_ctx lss_ctx;
+
+/* Grid (Sec. 2.1): dimension d (2; 3 is rejected with LSS_ERR_UNSUPPORTED),
+ * n points per unit length, h = 1/(n+1), p_i = i h. */
+typedef struct { int dim; int n; } lss_grid;
+
+/* PML (Sec. 2.2.2): b_pml layers (eta = b_pml h) and the strength C of
+ * sigma(x) = +-(C/omega)((x -+ ...)/eta)^2. */
+typedef struct { int b_pml; double C; } lss_pml;
+
+/* Sweep (Sec. 2.3-2.4): b_slab normal layers per slab along x1 (the first
+ * slab adds the left PML, the last takes the remainder plus the right PML),
+ * b_aux auxiliary moving-PML layers (0 = b_pml), n_samples squared-frequency
+ * samples for the auxiliary stencils (0 = n). */
+typedef struct { int b_slab; int b_aux; int n_samples; } lss_slab;
+
+/* GMRES (Sec. 2.5): restart length, relative tolerance on ||g - A u||/||g||,
+ * cap on the total number of Arnoldi steps. */
+typedef struct { int restart; double tol; int max_iter; } lss_gmres;
+
+/* Per right-hand side results. */
+typedef struct {
+    int iters;            /* Arnoldi steps taken                              */
+    int converged;        /* 1 if the Givens residual reached tol             */
+    double relres_est;    /* Givens estimate |rho|/||g|| at exit              */
+    double relres_true;   /* ||g - A u|| / ||g|| recomputed at exit           */
+} lss_stats;
+
+enum { LSS_FP64 = 0, LSS_MIXED = 1 };
+
+enum {
+    LSS_OK = 0,
+    LSS_ERR_ARG = -1,          /* invalid argument (null pointer, size)         */
+    LSS_ERR_OOM = -2,          /* device allocation failed                      */
+    LSS_ERR_STATE = -3,        /* call out of order (e.g. solve before factor)  */
+    LSS_ERR_SINGULAR = -4,     /* zero or non-finite pivot in a slab factor     */
+    LSS_ERR_NOCONVERGE = -5,   /* GMRES hit max_iter; best iterate is written   */
+    LSS_ERR_TIMEOUT = -6,      /* a bounded device wait expired                 */
+    LSS_ERR_CUDA = -7,         /* CUDA runtime error                            */
+    LSS_ERR_UNSUPPORTED = -8   /* configuration outside the supported range     */
+};
+
+/*
+ * lss_setup - Algorithm 1 steps 1-3 and the operator data (Sec. 2.1-2.3).
+ * Builds the Nystrom weights k (Sec. 2.1; k_0 = integral of G over the grid
+ * cell), their FFT for the zero-padded convolution, the interior stencils
+ * alpha, beta (Eq. alpha, Eq. beta), the PML stencils gamma (Eq. gamma) for the
+ * physical PML and, per squared-frequency sample, for the moving PML
+ * (Sec. 2.3), the slab partition, and assembles every slab subproblem
+ * (Eq. Hwv_approx).
+ *   out        receives the new context (NULL on failure)
+ *   g          grid; n in [4, 2048]
+ *   omega      angular frequency > 0
+ *   m_dev      device, n^d float64, m = 1 - 1/c^2 on I (row-major, x1 slowest)
+ *   pml, slab  parameters above; every slab subproblem must be at most 32
+ *              layers wide: b_aux + b_slab + b_pml <= 32 (the last slab)
+ *   precision  LSS_FP64 (all FP64) or LSS_MIXED (slab factors, sweep and the
+ *              interface matrices in FP32; LS matvec, Arnoldi, Givens and the
+ *              true residual in FP64; solves use flexible GMRES either way)
+ * Copies m; the caller may free m_dev after the call.
+ */
+int lss_setup(lss_ctx **out, const lss_grid *g, double omega, const double *m_dev,
+              const lss_pml *pml, const lss_slab *slab, int precision, void *stream);
+
+/*
+ * lss_set_medium - replace m on an existing context (same grid, omega and
+ * parameters).  The Nystrom weights, their FFT, alpha, beta and the physical
+ * PML stencils depend only on (n, omega) and are kept (Sec. 2.4, remark 3);
+ * the squared-frequency samples, the moving-PML stencils and the slab
+ * subproblems are rebuilt.  The context returns to the unfactored state.
+ *   m_dev      device, n^d float64 (copied)
+ */
+int lss_set_medium(lss_ctx *c, const double *m_dev, void *stream);
+
+/*
+ * lss_factor - Algorithm 1 steps 4-8: block-tridiagonal LU (along x2, pivoting
+ * inside each block) of every slab subproblem, all slabs in one launch, then
+ * the interface maps that let the sweep of Algorithm 2 run slab-parallel.
+ * Returns LSS_ERR_SINGULAR if a block pivot vanished.  Blocks the host.
+ */
+int lss_factor(lss_ctx *c, void *stream);
+
+/*
+ * lss_plane_wave_rhs - right-hand sides g = -omega^2 K (m .* u_I) (Sec. 2.1)
+ * for R incident plane waves u_I = exp(i omega d . p).
+ *   dirs_host  host, R x dim float64 unit directions
+ *   g_dev      device, R x n^d complex128 (output)
+ *   uI_dev     device, R x n^d complex128 (output) or NULL
+ */
+int lss_plane_wave_rhs(lss_ctx *c, const double *dirs_host, int R, void *g_dev,
+                       void *uI_dev, void *stream);
+
+/*
+ * lss_apply_A - y = (I + omega^2 K M) x (transpose = 0) or
+ * y = (I + omega^2 M K) x = A^T x (transpose = 1), Eq. LS_d_c, for R vectors;
+ * zero-padded FFT convolution.  x_dev and y_dev may not alias.
+ */
+int lss_apply_A(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose,
+                void *stream);
+
+/*
+ * lss_apply_P - y = P x, the preconditioner of Sec. 2.2-2.4 (Algorithm 2):
+ * f = Q x (alpha rows on I^h, Eq. Huf), the forward/backward moving-PML sweep
+ * with the slab factors, restriction to I.  transpose = 1 is reserved
+ * (LSS_ERR_UNSUPPORTED).  Requires lss_factor.  x_dev, y_dev: R x n^d c128.
+ */
+int lss_apply_P(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose,
+                void *stream);
+
+/*
+ * lss_solve - solve (I + omega^2 K M) u = g for R right-hand sides with
+ * flexible GMRES(restart), right preconditioned by P, x0 = 0, CGS2 Arnoldi in
+ * FP64, per-RHS convergence masks (Sec. 2.5 uses standard restarted GMRES).
+ *   g_dev      device, R x n^d complex128
+ *   u_dev      device, R x n^d complex128 (output; best iterate on failure)
+ *   stats      host, R entries (output), may be NULL
+ * Returns LSS_ERR_NOCONVERGE if some RHS missed tol within max_iter.
+ */
+int lss_solve(lss_ctx *c, const void *g_dev, void *u_dev, int R, const lss_gmres *o,
+              lss_stats *stats, void *stream);
+
+/*
+ * lss_solve_host - the same solve with host buffers: copies g_host to the
+ * device, solves, copies u back.  g_host, u_host: R x n^d complex128 (pinned
+ * memory gives asynchronous copies).  Blocks the host.
+ */
+int lss_solve_host(lss_ctx *c, const void *g_host, void *u_host, int R,
+                   const lss_gmres *o, lss_stats *stats, void *stream);
+
+/*
+ * lss_apply_slab - test hook: w = T~_i v, the moving-PML slab operator of
+ * Eq. Hwv_approx (pad v with zeros on the auxiliary layers, solve the slab
+ * subproblem with the stored factors, restrict to D_i).
+ *   slab       0-based slab index
+ *   v_dev, w_dev  device, R x (layers of D_i) x n_tot complex128 with
+ *              n_tot = n + 2 + 2 b_pml, x1 layer slowest
+ */
+int lss_apply_slab(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
+                   void *stream);
+
+/* Sizes of the context: n_tot, number of slabs, first x1 index and number of
+ * layers of slab i (x1 runs over -b_pml .. n+1+b_pml), FFT length. */
+int lss_info(const lss_ctx *c, int *n_tot, int *n_slabs, int *fft_len);
+int lss_slab_info(const lss_ctx *c, int slab, int *first_x1, int *n_layers, int *n_aux);
+
+/* Interior stencils alpha, beta (Eq. alpha, Eq. beta) as 9 (2D) complex128
+ * each, copied to host arrays; lexicographic offsets, x1 slowest. */
+int lss_get_stencils(const lss_ctx *c, double *alpha_host, double *beta_host);
+
+/* Profiling.  lss_profile(c, 1) starts recording CUDA events (on the
+ * caller's stream) around every kernel group of the library; lss_profile(c, 0)
+ * stops.  lss_profile_read() waits for the recorded work, returns the summed
+ * device milliseconds and launch counts per category since the previous read,
+ * and clears them.  Categories (LSS_PROF_*): */
+enum {
+    LSS_PROF_MATVEC = 0,   /* LS operator: row FFT, column FFT x kernel, row IFFT  */
+    LSS_PROF_SPARSIFY = 1, /* f = Q r                                             */
+    LSS_PROF_SLAB_A = 2,   /* slab solves a_i = T~_i f_i (all slabs)              */
+    LSS_PROF_RECUR = 3,    /* interface recurrences                               */
+    LSS_PROF_SLAB_E = 4,   /* slab solves with the interface couplings            */
+    LSS_PROF_FACTOR = 5,   /* block-tridiagonal LU of all slabs                   */
+    LSS_PROF_IFACE = 6,    /* interface maps (multi-RHS slab solves)              */
+    LSS_PROF_KRYLOV = 7,   /* Gram-Schmidt, norms, updates                        */
+    LSS_PROF_SETUP = 8,    /* kernel table, stencils, assembly                    */
+    LSS_PROF_NCAT = 9
+};
+int lss_profile(lss_ctx *c, int enable);
+/* ms, launches: arrays of ncat entries (either may be NULL). */
+int lss_profile_read(lss_ctx *c, double *ms, long long *launches, int ncat);
+
+/* Message of the last failure on this context ("" if none). */
+const char *lss_last_error(const lss_ctx *c);
+
+/* Frees the context and all device memory it owns.  NULL is ignored. */
+void lss_destroy(lss_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSS_H */

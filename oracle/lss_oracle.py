@@ -325,9 +325,10 @@ class Problem2D:
         layer s), at true position (s-t, i2) (Sec. 2.3, Eq. Hwv_approx).
         sigma along x1 is the left PML profile translated so that layer s plays
         the role of layer 0; sigma along x2 is the physical one; the local
-        frequency is the sample nearest to omega^2 (1 - m(s-t, i2))."""
+        frequency is the sample nearest to omega^2 (1 - m(s-t, i2)).  The x1
+        profile has the auxiliary width b_aux (eta = b_aux h)."""
         a1 = s - t
-        s1 = self.sigma(np.array([a1 - 1, a1, a1 + 1]) - s)
+        s1 = pml_sigma(np.array([a1 - 1, a1, a1 + 1]) - s, self.n, self.b_aux, self.p.C, self.omega)
         s2 = self.sigma([i2 - 1, i2, i2 + 1])
         k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(a1, i2)))
         return self._gamma(("aux", k, tuple(s1), tuple(s2)), math.sqrt(self.samples[k]), s1, s2)

@@ -1,0 +1,120 @@
+// Internal context of the C ABI and the host-side launchers shared between
+// translation units.  Not part of the public interface (include/lss.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+#include <vector>
+#include <complex>
+
+#include "../../include/lss.h"
+
+// One slab of the sweep (Sec. 2.3): D_i = x1 layers [s, s+nl), preceded in its
+// subproblem by na virtual auxiliary layers (Eq. Hwv_approx); w = na + nl.
+struct SlabDev {
+    int s;          // first x1 index of D_i
+    int nl;         // layers of D_i
+    int na;         // auxiliary layers (0 for the first slab)
+    int w;          // subproblem width in layers
+    int ldw;        // leading dimension of the stored block inverses (w rounded up to even)
+    int cstride;    // complex entries per block row of the coefficient table (w*9 rounded up to even)
+    long long coef_off;  // offset (complex entries) of this slab's coefficient table
+    long long fac_off;   // offset (complex entries) of this slab's block inverses
+};
+
+struct lss_ctx {
+    // problem
+    int dim = 2, n = 0, prec = LSS_FP64;
+    double omega = 0, h = 0;
+    lss_pml pml{};
+    lss_slab slab{};
+    int b = 0, b_aux = 0, n_tot = 0, n_slabs = 0, L = 0, lgL = 0, n_samples = 0;
+    int ns_eff = 0;               // samples used for the current medium (1 if m is constant)
+    long long coef_len = 0;       // complex entries of the coefficient table
+    double s_lo = 0, s_hi = 0;   // squared-frequency sample range
+    bool factored = false;
+    std::string err;
+
+    // stencils (host copies)
+    std::complex<double> alpha[9], beta[9];
+    std::vector<SlabDev> slabs;
+
+    // device data
+    double* m = nullptr;          // n*n
+    double2* khatT = nullptr;     // L*L, transposed (column k2 contiguous), scaled by omega^2/L^2
+    double2* tw = nullptr;        // L twiddles exp(-2 pi i k / L)
+    double2* gam_phys = nullptr;  // (2b+1)^2 x 9 PML stencils (row coefficients)
+    double2* gam_aux = nullptr;   // n_samples x b_aux x (2b+1) x 9
+    double2* coef64 = nullptr;    // slab row coefficients, complex128
+    void* coef = nullptr;         // working-precision coefficients (== coef64 for FP64)
+    void* fac = nullptr;          // block inverses G_k, working precision
+    void* iface = nullptr;        // interface maps Lambda, Gamma, Phi: 3 x n_slabs x n_tot^2
+    SlabDev* d_slabs = nullptr;
+    int* d_err = nullptr;
+    unsigned* d_bar = nullptr;    // grid barrier words
+
+    // workspaces (grown on demand)
+    double2* mv_buf = nullptr; size_t mv_cap = 0;      // n x L x R FFT scratch
+    void* f_buf = nullptr; size_t f_cap = 0;           // R x n_tot^2 sparsified rhs
+    void* side_buf = nullptr; size_t side_cap = 0;     // 4 x n_slabs x n_tot x R interface vectors
+    void* z_buf = nullptr; size_t z_cap = 0;           // Thomas forward scratch
+    double2* kr_buf = nullptr; size_t kr_cap = 0;      // Krylov basis storage
+    double2* red_buf = nullptr; size_t red_cap = 0;    // reduction partials
+    void* io_buf = nullptr; size_t io_cap = 0;         // host-buffer solve staging
+    void* dir_buf = nullptr; size_t dir_cap = 0;       // plane-wave directions
+    int num_sms = 0;
+
+    // profiling: event pairs per kernel group, launch counters
+    struct ProfRec { int cat; cudaEvent_t a, b; int launches; };
+    bool prof_on = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    long long launches[LSS_PROF_NCAT] = {};
+
+    size_t csize() const { return prec == LSS_FP64 ? sizeof(double2) : sizeof(float2); }
+};
+
+// Records CUDA events around a kernel group when profiling is on and counts
+// the group's launches.
+struct ProfScope {
+    lss_ctx* c;
+    cudaStream_t s;
+    int cat, n;
+    cudaEvent_t a = nullptr;
+    ProfScope(lss_ctx* c_, cudaStream_t s_, int cat_, int n_launch);
+    ~ProfScope();
+};
+
+// status helpers
+int lss_fail(lss_ctx* c, int code, const std::string& msg);
+int lss_check_cuda(lss_ctx* c, cudaError_t e, const char* what);
+int lss_check_device_err(lss_ctx* c, cudaStream_t s);
+int lss_grow(lss_ctx* c, void** p, size_t* cap, size_t bytes);
+
+// greens.cu: Nystrom weights, FFT of the kernel, alpha/beta
+std::complex<double> lss_cell_integral_G(int d, double omega, double h);
+int lss_build_kernel(lss_ctx* c, cudaStream_t s);
+int lss_build_interior_stencils(lss_ctx* c, cudaStream_t s);
+
+// fft.cu: LS operator
+enum MvIn { MV_IN_MU = 0, MV_IN_U = 1, MV_IN_PLANEWAVE = 2, MV_IN_RAW = 3 };
+enum MvOut { MV_OUT_A = 0, MV_OUT_AT = 1, MV_OUT_NEG = 2 };
+int lss_matvec(lss_ctx* c, const double2* x, double2* y, int R, int in_mode, int out_mode,
+               const double* dirs_dev, double2* uI, cudaStream_t s);
+int lss_fft_kernel_table(lss_ctx* c, const double2* kc, cudaStream_t s);  // kc: L x L -> khatT
+int lss_fft_configure(lss_ctx* c);
+
+// stencil.cu: gamma tables, slab assembly, Q
+int lss_build_gamma_phys(lss_ctx* c, cudaStream_t s);
+int lss_build_gamma_aux(lss_ctx* c, cudaStream_t s);
+int lss_assemble_slabs(lss_ctx* c, cudaStream_t s);
+int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s);
+
+// slab.cu: factorization, sweep
+int lss_factor_slabs(lss_ctx* c, cudaStream_t s);
+int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s);
+int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s);
+
+// krylov.cu: FGMRES
+int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s);
+int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
+               cudaStream_t s);

@@ -1,0 +1,276 @@
+// PML stencils gamma (Sec. 2.2.2, Eq. gamma), assembly of the slab
+// subproblems (Sec. 2.2.3, Sec. 2.3, Eq. Hwv_approx) and the sparsifying map
+// f = Q r (Eq. Huf; Algorithm 2 step 1).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lss_common.cuh"
+#include "lss_ctx.h"
+
+namespace {
+
+struct StencilArgs {
+    double2 a_conj[9];   // conj(alpha_o)
+    double2 b_conj[9];   // conj(beta_o)
+};
+
+// sigma at grid index q of the physical profile (eta = b h): left of -1 the
+// quadratic -(C/omega)((q+1)/b)^2, right of n+2 the mirror (C/omega)((q-n-2)/b)^2,
+// zero in between; the Dirichlet layers take the same formula.
+__device__ __forceinline__ double sigma_phys(int q, int n, int b, double Cw) {
+    if (q <= -1) { const double t = (q + 1.0) / b; return -Cw * t * t; }
+    if (q >= n + 2) { const double t = (q - n - 2.0) / b; return Cw * t * t; }
+    return 0.0;
+}
+
+// Null vector of F^T for a 9 x 8 complex F (gamma^* F = 0): last column of the
+// unitary factor of a Householder QR of F.  Returns conj(gamma), unit norm,
+// centre entry real positive.
+__device__ void gamma_from_F(double2 F[9][8], double2 out[9]) {
+    double vn2[8];
+    for (int k = 0; k < 8; ++k) {
+        double nx = 0;
+        for (int i = k; i < 9; ++i) nx += cabs2(F[i][k]);
+        nx = sqrt(nx);
+        const double2 fkk = F[k][k];
+        const double afk = sqrt(cabs2(fkk));
+        const double2 ph = afk > 0 ? mk(fkk.x / afk, fkk.y / afk) : mk(1.0, 0.0);
+        const double2 alpha = mk(-ph.x * nx, -ph.y * nx);
+        F[k][k] = fkk - alpha;  // v stored in column k, rows k..8
+        double v2 = 0;
+        for (int i = k; i < 9; ++i) v2 += cabs2(F[i][k]);
+        vn2[k] = v2;
+        if (v2 == 0) continue;
+        for (int j = k + 1; j < 8; ++j) {
+            double2 dot = mk(0.0, 0.0);
+            for (int i = k; i < 9; ++i) dot = cfma_conj(F[i][k], F[i][j], dot);
+            const double s = 2.0 / v2;
+            for (int i = k; i < 9; ++i) F[i][j] = F[i][j] - (s * dot) * F[i][k];
+        }
+    }
+    double2 q[9];
+    for (int i = 0; i < 9; ++i) q[i] = mk(0.0, 0.0);
+    q[8] = mk(1.0, 0.0);
+    for (int k = 7; k >= 0; --k) {
+        if (vn2[k] == 0) continue;
+        double2 dot = mk(0.0, 0.0);
+        for (int i = k; i < 9; ++i) dot = cfma_conj(F[i][k], q[i], dot);
+        const double s = 2.0 / vn2[k];
+        for (int i = k; i < 9; ++i) q[i] = q[i] - (s * dot) * F[i][k];
+    }
+    double nq = 0;
+    for (int i = 0; i < 9; ++i) nq += cabs2(q[i]);
+    nq = sqrt(nq);
+    const double a4 = sqrt(cabs2(q[4]));
+    const double2 ph = mk(q[4].x / a4, -q[4].y / a4);  // |q4| / q4
+    for (int i = 0; i < 9; ++i) {
+        double2 g = (1.0 / nq) * (q[i] * ph);
+        if (i == 4) g = mk(a4 / nq, 0.0);
+        out[i] = conjc(g);
+    }
+}
+
+// Stencil for stretch triples s1, s2 (sigma at offsets -1, 0, +1 along x1, x2)
+// and local frequency w: F[o][r] = exp(i w r.(dp_o + i dsigma_o)) over the
+// 8 normalised neighbour directions r.
+__device__ void pml_stencil(const double s1[3], const double s2[3], double w, double h, double2 out[9]) {
+    double2 F[9][8];
+    const double is2 = 0.70710678118654752440;
+    for (int o = 0; o < 9; ++o) {
+        const int da = o / 3 - 1, db = o % 3 - 1;
+        const double re1 = da * h, im1 = s1[da + 1] - s1[1];
+        const double re2 = db * h, im2 = s2[db + 1] - s2[1];
+        int col = 0;
+        for (int ra = -1; ra <= 1; ++ra)
+            for (int rb = -1; rb <= 1; ++rb) {
+                if (ra == 0 && rb == 0) continue;
+                const double sc = (ra != 0 && rb != 0) ? is2 : 1.0;
+                const double pr = sc * (ra * re1 + rb * re2);   // real part of r.dz
+                const double pi = sc * (ra * im1 + rb * im2);   // imaginary part
+                double sn, cs;
+                sincos(w * pr, &sn, &cs);
+                const double mag = exp(-w * pi);
+                F[o][col++] = mk(mag * cs, mag * sn);
+            }
+    }
+    gamma_from_F(F, out);
+}
+
+// Class of a grid index along one axis: 0 interior (all three sigmas zero),
+// 1..b left PML (index -b..-1), b+1..2b right PML (index n+2..n+1+b).
+__device__ __forceinline__ int pml_class(int q, int n, int b) {
+    if (q <= -1) return q + b + 1;
+    if (q >= n + 2) return b + 1 + (q - n - 2);
+    return 0;
+}
+__device__ __forceinline__ int class_index(int cl, int n, int b) {
+    if (cl == 0) return 0;
+    if (cl <= b) return cl - b - 1;
+    return n + 2 + (cl - b - 1);
+}
+
+// Physical PML stencils: one per (class x1, class x2), global omega.
+__global__ void gamma_phys_kernel(double2* out, int n, int b, double Cw, double omega, double h) {
+    const int nc = 2 * b + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nc * nc) return;
+    const int c1 = e / nc, c2 = e % nc;
+    double2 g[9];
+    if (c1 == 0 && c2 == 0) {
+        for (int o = 0; o < 9; ++o) g[o] = mk(0.0, 0.0);
+    } else {
+        const int q1 = class_index(c1, n, b), q2 = class_index(c2, n, b);
+        double s1[3], s2[3];
+        for (int t = 0; t < 3; ++t) {
+            s1[t] = sigma_phys(q1 - 1 + t, n, b, Cw);
+            s2[t] = sigma_phys(q2 - 1 + t, n, b, Cw);
+        }
+        pml_stencil(s1, s2, omega, h, g);
+    }
+    for (int o = 0; o < 9; ++o) out[(size_t)e * 9 + o] = g[o];
+}
+
+// Auxiliary (moving) PML stencils: per frequency sample k, auxiliary layer
+// t = 1..b_aux (distance from D_i) and x2 class.  Along x1 the left profile of
+// width b_aux translated so that D_i's first layer plays the role of index 0.
+__global__ void gamma_aux_kernel(double2* out, int n, int b, int baux, int ns, double s_lo, double s_hi,
+                                 double Cw, double h) {
+    const int nc = 2 * b + 1;
+    const long long tot = (long long)ns * baux * nc;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= tot) return;
+    const int c2 = (int)(e % nc);
+    const int t = (int)((e / nc) % baux) + 1;
+    const int k = (int)(e / ((long long)nc * baux));
+    double sk = (ns == 1) ? s_lo : (k == ns - 1 ? s_hi : s_lo + k * ((s_hi - s_lo) / (ns - 1)));
+    const double w = sqrt(sk);
+    double s1[3], s2[3];
+    const int q2 = class_index(c2, n, b);
+    for (int u = 0; u < 3; ++u) {
+        const int q1 = -t - 1 + u;
+        double v = 0;
+        if (q1 <= -1) { const double tt = (q1 + 1.0) / baux; v = -Cw * tt * tt; }
+        s1[u] = v;
+        s2[u] = sigma_phys(q2 - 1 + u, n, b, Cw);
+    }
+    double2 g[9];
+    pml_stencil(s1, s2, w, h, g);
+    for (int o = 0; o < 9; ++o) out[(size_t)e * 9 + o] = g[o];
+}
+
+__device__ __forceinline__ double m_at(const double* m, int n, int i1, int i2) {
+    return (i1 >= 1 && i1 <= n && i2 >= 1 && i2 <= n) ? m[(size_t)(i1 - 1) * n + (i2 - 1)] : 0.0;
+}
+
+// Row coefficients of every slab subproblem: coef[off + k*cstride + la*9 + o].
+__global__ void assemble_kernel(const SlabDev* __restrict__ slabs, int n_slabs, const double* __restrict__ m,
+                                const double2* __restrict__ gphys, const double2* __restrict__ gaux,
+                                StencilArgs st, double2* __restrict__ coef, int n, int b, int baux, int n_tot,
+                                int ns, double s_lo, double s_hi, double omega) {
+    const int i = blockIdx.y;
+    if (i >= n_slabs) return;
+    const SlabDev sd = slabs[i];
+    const int tot = sd.w * n_tot;
+    const int nc = 2 * b + 1;
+    const double w2 = omega * omega;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        const int k = e / sd.w, la = e % sd.w;
+        const int x1 = sd.s - sd.na + la, i2 = k - b;
+        double2* out = coef + sd.coef_off + (long long)k * sd.cstride + la * 9;
+        if (la < sd.na) {
+            const int t = sd.na - la;
+            const double v = w2 * (1.0 - m_at(m, n, x1, i2));
+            int kk = 0;
+            if (ns > 1) {
+                const double x = (v - s_lo) / ((s_hi - s_lo) / (ns - 1));
+                kk = (int)ceil(x - 0.5);  // nearest sample, ties to the lower one
+                kk = kk < 0 ? 0 : (kk > ns - 1 ? ns - 1 : kk);
+            }
+            const double2* g = gaux + (((size_t)kk * baux + (t - 1)) * nc + pml_class(i2, n, b)) * 9;
+            for (int o = 0; o < 9; ++o) out[o] = g[o];
+        } else if (x1 >= 0 && x1 <= n + 1 && i2 >= 0 && i2 <= n + 1) {
+            for (int o = 0; o < 9; ++o) {
+                const double mm = m_at(m, n, x1 + o / 3 - 1, i2 + o % 3 - 1);
+                out[o] = st.a_conj[o] + (w2 * mm) * st.b_conj[o];
+            }
+        } else {
+            const double2* g = gphys + ((size_t)pml_class(x1, n, b) * nc + pml_class(i2, n, b)) * 9;
+            for (int o = 0; o < 9; ++o) out[o] = g[o];
+        }
+    }
+}
+
+// f = Q r: f_i = sum_o conj(alpha_o) r_{i+o} on I^h = {0..n+1}^2, zero on the
+// PML; r is zero outside I.  Layout f[r][a1][a2] over the n_tot^2 grid.
+template <typename C>
+__global__ void sparsify_kernel(const double2* __restrict__ r, C* __restrict__ f, StencilArgs st, int n, int b,
+                                int n_tot) {
+    const long long tot = (long long)n_tot * n_tot;
+    const int rr = blockIdx.y;
+    const double2* rv = r + (long long)rr * n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i1 = (int)(e / n_tot) - b, i2 = (int)(e % n_tot) - b;
+        double2 acc = mk(0.0, 0.0);
+        if (i1 >= 0 && i1 <= n + 1 && i2 >= 0 && i2 <= n + 1) {
+            for (int o = 0; o < 9; ++o) {
+                const int j1 = i1 + o / 3 - 1, j2 = i2 + o % 3 - 1;
+                if (j1 >= 1 && j1 <= n && j2 >= 1 && j2 <= n)
+                    acc = cfma(st.a_conj[o], rv[(long long)(j1 - 1) * n + (j2 - 1)], acc);
+            }
+        }
+        f[(long long)rr * tot + e] = to_c<C>(acc);
+    }
+}
+
+StencilArgs stencil_args(const lss_ctx* c) {
+    StencilArgs st;
+    for (int o = 0; o < 9; ++o) {
+        st.a_conj[o] = make_double2(c->alpha[o].real(), -c->alpha[o].imag());
+        st.b_conj[o] = make_double2(c->beta[o].real(), -c->beta[o].imag());
+    }
+    return st;
+}
+
+}  // namespace
+
+int lss_build_gamma_phys(lss_ctx* c, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_SETUP, 1);
+    const int nc = 2 * c->b + 1;
+    const double Cw = c->pml.C / c->omega;
+    gamma_phys_kernel<<<(nc * nc + 127) / 128, 128, 0, s>>>(c->gam_phys, c->n, c->b, Cw, c->omega, c->h);
+    return lss_check_cuda(c, cudaGetLastError(), "gamma tables");
+}
+
+int lss_build_gamma_aux(lss_ctx* c, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_SETUP, 1);
+    const int nc = 2 * c->b + 1;
+    const double Cw = c->pml.C / c->omega;
+    const long long tot = (long long)c->ns_eff * c->b_aux * nc;
+    gamma_aux_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(c->gam_aux, c->n, c->b, c->b_aux, c->ns_eff,
+                                                                  c->s_lo, c->s_hi, Cw, c->h);
+    return lss_check_cuda(c, cudaGetLastError(), "gamma tables");
+}
+
+int lss_assemble_slabs(lss_ctx* c, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_SETUP, 1);
+    const int per = std::max(1, (c->n_tot * LSS_WMAX + 255) / 256);
+    assemble_kernel<<<dim3(std::min(per, 64), c->n_slabs), 256, 0, s>>>(
+        c->d_slabs, c->n_slabs, c->m, c->gam_phys, c->gam_aux, stencil_args(c), c->coef64, c->n, c->b, c->b_aux,
+        c->n_tot, c->ns_eff, c->s_lo, c->s_hi, c->omega);
+    return lss_check_cuda(c, cudaGetLastError(), "assemble");
+}
+
+int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+    const long long tot = (long long)c->n_tot * c->n_tot;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4LL * c->num_sms);
+    if (c->prec == LSS_FP64)
+        sparsify_kernel<double2><<<dim3(blocks, R), 256, 0, s>>>(r, (double2*)f, stencil_args(c), c->n, c->b,
+                                                                  c->n_tot);
+    else
+        sparsify_kernel<float2><<<dim3(blocks, R), 256, 0, s>>>(r, (float2*)f, stencil_args(c), c->n, c->b,
+                                                                 c->n_tot);
+    return lss_check_cuda(c, cudaGetLastError(), "sparsify");
+}

@@ -1,0 +1,156 @@
+"""Python wrapper of the C ABI: one LSSolver per (grid, omega, medium).
+
+Device memory and streams come from PyTorch; every step of the solve runs in
+the library's kernels.  Vectors are complex128 CUDA tensors of shape
+(R, n, n) (or (n, n) for one right-hand side).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+@dataclasses.dataclass
+class GmresOptions:
+    restart: int = 30
+    tol: float = 1e-8
+    max_iter: int = 300
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _c128(x: torch.Tensor) -> torch.Tensor:
+    if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
+        raise TypeError("expected a contiguous complex128 CUDA tensor")
+    return x
+
+
+class LSSolver:
+    """Sparsify-and-sweep preconditioned LS solver (Sec. 2, Algorithms 1-2)."""
+
+    def __init__(self, n: int, omega: float, m: torch.Tensor, b_pml: int = 12, C: float = 10.0,
+                 b_slab: int = 4, b_aux: int = 0, n_samples: int = 0, precision: int = _lib.LSS_FP64,
+                 factor: bool = True, stream=None):
+        self.lib = _lib.load()
+        self.n, self.omega = int(n), float(omega)
+        if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != (n, n):
+            raise TypeError("m must be a (n, n) float64 CUDA tensor")
+        m = m.contiguous()
+        ctx = ctypes.c_void_p()
+        g = _lib.Grid(2, self.n)
+        p = _lib.Pml(int(b_pml), float(C))
+        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples))
+        check(self.lib.lss_setup(ctypes.byref(ctx), ctypes.byref(g), self.omega, m.data_ptr(), ctypes.byref(p),
+                                 ctypes.byref(s), int(precision), _stream_ptr(stream)))
+        self.ctx = ctx
+        nt, ns, L = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.lib.lss_info(self.ctx, ctypes.byref(nt), ctypes.byref(ns), ctypes.byref(L))
+        self.n_tot, self.n_slabs, self.fft_len = nt.value, ns.value, L.value
+        if factor:
+            self.factor(stream)
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and ctx.value:
+            torch.cuda.synchronize()
+            self.lib.lss_destroy(ctx)
+            self.ctx = None
+
+    def _check(self, code):
+        return check(code, self.ctx)
+
+    def set_medium(self, m: torch.Tensor, stream=None):
+        if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != (self.n, self.n):
+            raise TypeError("m must be a (n, n) float64 CUDA tensor")
+        self._check(self.lib.lss_set_medium(self.ctx, m.contiguous().data_ptr(), _stream_ptr(stream)))
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.lss_profile(self.ctx, int(enable)))
+
+    def profile_read(self):
+        """Device milliseconds and launch counts per kernel group since the last read."""
+        k = len(_lib.PROF_CATEGORIES)
+        ms = np.zeros(k)
+        cnt = np.zeros(k, dtype=np.int64)
+        self._check(self.lib.lss_profile_read(self.ctx, ms.ctypes.data, cnt.ctypes.data, k))
+        return dict(zip(_lib.PROF_CATEGORIES, ms.tolist())), dict(zip(_lib.PROF_CATEGORIES, cnt.tolist()))
+
+    def factor(self, stream=None):
+        self._check(self.lib.lss_factor(self.ctx, _stream_ptr(stream)))
+
+    def slab_info(self, i: int):
+        s, nl, na = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lss_slab_info(self.ctx, i, ctypes.byref(s), ctypes.byref(nl), ctypes.byref(na)))
+        return s.value, nl.value, na.value
+
+    def stencils(self):
+        a = np.zeros(18)
+        b = np.zeros(18)
+        self._check(self.lib.lss_get_stencils(self.ctx, a.ctypes.data, b.ctypes.data))
+        return a.view(np.complex128), b.view(np.complex128)
+
+    def _batch(self, x):
+        return x if x.dim() == 3 else x.unsqueeze(0)
+
+    def plane_wave_rhs(self, dirs, with_incident: bool = False, stream=None):
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 2))
+        R = d.shape[0]
+        g = torch.empty((R, self.n, self.n), dtype=torch.complex128, device="cuda")
+        uI = torch.empty_like(g) if with_incident else None
+        self._check(self.lib.lss_plane_wave_rhs(self.ctx, d.ctypes.data, R, g.data_ptr(),
+                                                uI.data_ptr() if uI is not None else None, _stream_ptr(stream)))
+        return (g, uI) if with_incident else g
+
+    def apply_A(self, x: torch.Tensor, transpose: bool = False, stream=None) -> torch.Tensor:
+        x = _c128(self._batch(x))
+        y = torch.empty_like(x)
+        self._check(self.lib.lss_apply_A(self.ctx, x.data_ptr(), y.data_ptr(), x.shape[0], int(transpose),
+                                         _stream_ptr(stream)))
+        return y
+
+    def apply_P(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+        x = _c128(self._batch(x))
+        y = torch.empty_like(x)
+        self._check(self.lib.lss_apply_P(self.ctx, x.data_ptr(), y.data_ptr(), x.shape[0], 0, _stream_ptr(stream)))
+        return y
+
+    def apply_slab(self, i: int, v: torch.Tensor, stream=None) -> torch.Tensor:
+        v = _c128(self._batch(v))
+        w = torch.empty_like(v)
+        self._check(self.lib.lss_apply_slab(self.ctx, i, v.data_ptr(), w.data_ptr(), v.shape[0],
+                                            _stream_ptr(stream)))
+        return w
+
+    def solve(self, g: torch.Tensor, opts: GmresOptions | None = None, stream=None, raise_on_noconv=True):
+        o = opts or GmresOptions()
+        g = _c128(self._batch(g))
+        u = torch.empty_like(g)
+        R = g.shape[0]
+        st = (_lib.Stats * R)()
+        go = _lib.Gmres(o.restart, o.tol, o.max_iter)
+        code = self.lib.lss_solve(self.ctx, g.data_ptr(), u.data_ptr(), R, ctypes.byref(go), st,
+                                  _stream_ptr(stream))
+        if code != 0 and not (code == -5 and not raise_on_noconv):
+            self._check(code)
+        return u, [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
+                        relres_true=s.relres_true) for s in st]
+
+    def solve_host(self, g_host: torch.Tensor, u_host: torch.Tensor, opts: GmresOptions | None = None,
+                   stream=None):
+        o = opts or GmresOptions()
+        R = g_host.shape[0] if g_host.dim() == 3 else 1
+        st = (_lib.Stats * R)()
+        go = _lib.Gmres(o.restart, o.tol, o.max_iter)
+        self._check(self.lib.lss_solve_host(self.ctx, g_host.data_ptr(), u_host.data_ptr(), R, ctypes.byref(go),
+                                            st, _stream_ptr(stream)))
+        return [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
+                     relres_true=s.relres_true) for s in st]
