@@ -174,6 +174,29 @@ int lss_solve_host(lss_ctx *c, const void *g_host, void *u_host, int R,
 int lss_apply_slab(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
                    void *stream);
 
+/*
+ * lss_apply_slab_noalloc - the same slab operator as lss_apply_slab, for
+ * callers that must not reach the device allocator during the call: code
+ * whose device memory is fully handed out up front (another framework's
+ * caching allocator owns the rest of HBM), or latency-critical loops where a
+ * workspace that grows through cudaMalloc/cudaFree would stall (cudaFree
+ * synchronises the device).  The paper has no counterpart; this is a property
+ * of the library, not of the method.
+ * The call allocates nothing.  Its scratch is one fixed array of 8 MiB in
+ * device memory that every GPU loading the library holds until the process
+ * exits.  The first call on each device looks up that array's device address
+ * (with the device current) and caches it; make that first call before any
+ * stream capture on the device.  All calls share the array and it keeps the
+ * last call's contents (nothing in it needs to start at zero): calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  A call that would need more than 8 MiB of scratch
+ * (n_tot x widest slab x min(R, 8) x ceil(R / 8) complex entries of the working
+ * precision) returns LSS_ERR_UNSUPPORTED without launching.
+ * Arguments, layouts and ownership as for lss_apply_slab.
+ */
+int lss_apply_slab_noalloc(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
+                           void *stream);
+
 /* Sizes of the context: n_tot, number of slabs, first x1 index and number of
  * layers of slab i (x1 runs over -b_pml .. n+1+b_pml), FFT length. */
 int lss_info(const lss_ctx *c, int *n_tot, int *n_slabs, int *fft_len);

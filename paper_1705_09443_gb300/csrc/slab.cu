@@ -20,6 +20,8 @@
 // run for all slabs at once; only the short recurrences on n_tot-vectors are
 // sequential.
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "lss_common.cuh"
@@ -591,4 +593,80 @@ int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
 int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
     return c->prec == LSS_FP64 ? slab_apply_impl<double>(c, slab, v, w, R, s)
                                : slab_apply_impl<float>(c, slab, v, w, R, s);
+}
+
+// ---------------------------------------------------------------- fixed-scratch slab operator
+// lss_apply_slab_noalloc: the slab operator of lss_apply_slab with its
+// forward-elimination scratch in a fixed device array instead of the context's
+// growable workspace, so that the call never reaches the device allocator.
+namespace {
+
+constexpr size_t kFixedScratchBytes = size_t(8) << 20;   // 8 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_fixed_scratch[kFixedScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_fixed_mu;
+void* g_fixed_ptr[kMaxDevices] = {};
+
+// Device address of g_fixed_scratch for the current device.  In host code the
+// symbol names a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+int fixed_scratch(lss_ctx* c, void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return lss_check_cuda(c, e, "noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return lss_fail(c, LSS_ERR_UNSUPPORTED, "noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_fixed_mu);
+    if (!g_fixed_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_fixed_scratch);
+        if (e || !p) return lss_check_cuda(c, e ? e : cudaErrorInvalidSymbol, "noalloc: cudaGetSymbolAddress");
+        g_fixed_ptr[dev] = p;
+    }
+    *out = g_fixed_ptr[dev];
+    return LSS_OK;
+}
+
+template <typename T>
+int slab_apply_fixed_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
+    using C = cx<T>;
+    const int RC = rhs_per_cta(R);
+    const int ny = (R + RC - 1) / RC;
+    const long long zstride = (long long)c->n_tot * wmax_of(c) * RC;
+    const size_t need = (size_t)zstride * sizeof(C) * ny;
+    if (need > kFixedScratchBytes)
+        return lss_fail(c, LSS_ERR_UNSUPPORTED,
+                        "apply_slab_noalloc: needs " + std::to_string(need) + " bytes of scratch, the fixed scratch holds " +
+                            std::to_string(kFixedScratchBytes) + " (use fewer right-hand sides per call)");
+    void* scratch = nullptr;
+    int rc = fixed_scratch(c, &scratch);
+    if (rc) return rc;
+    // The forward pass writes every scratch entry before the backward pass reads
+    // it, so nothing has to start at zero and no clearing is needed.
+    ThomasArgs<C> A = base_args<T>(c);
+    A.v_in = v;
+    A.w_out = w;
+    A.test_slab = slab;
+    A.zbuf = (C*)scratch;
+    A.zstride = zstride;
+    A.R = R;
+    A.RC = RC;
+    const size_t sh = thomas_smem<T>(c, RC);
+    cudaError_t e = cudaFuncSetAttribute(thomas_kernel<T, TH_TEST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max<size_t>(sh, 48 * 1024));
+    if (e) return lss_check_cuda(c, e, "noalloc attribute");
+    thomas_kernel<T, TH_TEST><<<dim3(1, ny, 1), kSolveThreads, sh, s>>>(A);
+    return lss_check_cuda(c, cudaGetLastError(), "noalloc launch");
+}
+
+}  // namespace
+
+extern "C" int lss_apply_slab_noalloc(lss_ctx* c, int slab, const void* v_dev, void* w_dev, int R, void* stream) {
+    if (!c) return LSS_ERR_ARG;
+    if (!v_dev || !w_dev || R < 1 || slab < 0 || slab >= c->n_slabs)
+        return lss_fail(c, LSS_ERR_ARG, "apply_slab_noalloc: bad arguments");
+    if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_slab_noalloc before lss_factor");
+    cudaStream_t s = (cudaStream_t)stream;
+    return c->prec == LSS_FP64 ? slab_apply_fixed_impl<double>(c, slab, (const double2*)v_dev, (double2*)w_dev, R, s)
+                               : slab_apply_fixed_impl<float>(c, slab, (const double2*)v_dev, (double2*)w_dev, R, s);
 }
