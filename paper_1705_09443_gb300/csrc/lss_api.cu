@@ -198,10 +198,11 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
         }
         sd.ldw = (sd.w + 1) & ~1;
         sd.cstride = (sd.w * 9 + 1) & ~1;
+        sd.rsz = sd.w * sd.ldw + sd.cstride;
         sd.coef_off = coff;
         sd.fac_off = foff;
         coff += (long long)sd.cstride * c->n_tot;
-        foff += (long long)sd.w * sd.ldw * c->n_tot;
+        foff += (long long)sd.rsz * c->n_tot;
         c->slabs.push_back(sd);
     }
 

@@ -5,7 +5,9 @@
 #include <cstdint>
 
 #define LSS_WMAX 32            // widest slab subproblem (layers)
-#define LSS_WAIT_NS 2000000000ull   // every device-side wait gives up after 2 s
+// Every device-side wait gives up after ~2 s, counted in SM clock cycles
+// (clock64 is cheap to read; the global timer costs hundreds of cycles).
+#define LSS_WAIT_CYCLES 4000000000ll
 
 // Device error word bits (ctx->d_err).
 #define LSS_DERR_SINGULAR 1
@@ -103,11 +105,10 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
             __threadfence();
             st_release_u32(bar + 1, gen + 1);
         } else {
-            const unsigned long long t0 = global_ns();
+            const long long t0 = clock64();
             while (ld_acquire_u32(bar + 1) == gen) {
                 if (*(volatile int*)err & LSS_DERR_TIMEOUT) break;
-                if (global_ns() - t0 > LSS_WAIT_NS) { atomicOr(err, LSS_DERR_TIMEOUT); break; }
-                __nanosleep(32);
+                if (clock64() - t0 > LSS_WAIT_CYCLES) { atomicOr(err, LSS_DERR_TIMEOUT); break; }
             }
         }
     }
@@ -137,19 +138,28 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 // Bounded wait on phase `parity`; returns false (and flags the error) on expiry.
+__device__ __forceinline__ bool mbar_test(uint32_t a, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait on phase `parity`: polls first, starts the clock only when the
+// phase is not complete yet; returns false (and flags the error) on expiry.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* err) {
-    uint32_t a = smem_u32(bar);
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 0;; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 15) == 15 && global_ns() - t0 > LSS_WAIT_NS) break;
+    const uint32_t a = smem_u32(bar);
+    if (mbar_test(a, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_test(a, parity)) return true;
+        if (clock64() - t0 > LSS_WAIT_CYCLES) break;
     }
     atomicOr(err, LSS_DERR_TIMEOUT);
     return false;

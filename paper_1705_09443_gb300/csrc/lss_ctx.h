@@ -17,8 +17,9 @@ struct SlabDev {
     int w;          // subproblem width in layers
     int ldw;        // leading dimension of the stored block inverses (w rounded up to even)
     int cstride;    // complex entries per block row of the coefficient table (w*9 rounded up to even)
+    int rsz;        // complex entries per block-row record: G_k^T (w x ldw), then the coefficient row (cstride)
     long long coef_off;  // offset (complex entries) of this slab's coefficient table
-    long long fac_off;   // offset (complex entries) of this slab's block inverses
+    long long fac_off;   // offset (complex entries) of this slab's block-row records
 };
 
 struct lss_ctx {
@@ -46,7 +47,7 @@ struct lss_ctx {
     double2* gam_aux = nullptr;   // n_samples x b_aux x (2b+1) x 9
     double2* coef64 = nullptr;    // slab row coefficients, complex128
     void* coef = nullptr;         // working-precision coefficients (== coef64 for FP64)
-    void* fac = nullptr;          // block inverses G_k, working precision
+    void* fac = nullptr;          // per block row: G_k^T then the row's coefficients (working precision)
     void* iface = nullptr;        // interface maps Lambda, Gamma, Phi: 3 x n_slabs x n_tot^2
     SlabDev* d_slabs = nullptr;
     int* d_err = nullptr;

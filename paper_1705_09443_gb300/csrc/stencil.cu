@@ -202,7 +202,8 @@ __global__ void assemble_kernel(const SlabDev* __restrict__ slabs, int n_slabs, 
 }
 
 // f = Q r: f_i = sum_o conj(alpha_o) r_{i+o} on I^h = {0..n+1}^2, zero on the
-// PML; r is zero outside I.  Layout f[r][a1][a2] over the n_tot^2 grid.
+// PML; r is zero outside I.  Layout f[r][a2][a1] over the n_tot^2 grid (x2
+// slowest, so a slab solve reads one block row's layers contiguously).
 template <typename C>
 __global__ void sparsify_kernel(const double2* __restrict__ r, C* __restrict__ f, StencilArgs st, int n, int b,
                                 int n_tot) {
@@ -211,7 +212,7 @@ __global__ void sparsify_kernel(const double2* __restrict__ r, C* __restrict__ f
     const double2* rv = r + (long long)rr * n * n;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
          e += (long long)gridDim.x * blockDim.x) {
-        const int i1 = (int)(e / n_tot) - b, i2 = (int)(e % n_tot) - b;
+        const int i2 = (int)(e / n_tot) - b, i1 = (int)(e % n_tot) - b;   // x2 slowest
         double2 acc = mk(0.0, 0.0);
         if (i1 >= 0 && i1 <= n + 1 && i2 >= 0 && i2 <= n + 1) {
             for (int o = 0; o < 9; ++o) {
