@@ -190,8 +190,8 @@ int lss_apply_slab(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
  * last call's contents (nothing in it needs to start at zero): calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  A call that would need more than 8 MiB of scratch
- * (n_tot x widest slab x min(R, 8) x ceil(R / 8) complex entries of the working
- * precision) returns LSS_ERR_UNSUPPORTED without launching.
+ * (R x n_tot x the widest slab's width rounded up to even, in complex entries
+ * of the working precision) returns LSS_ERR_UNSUPPORTED without launching.
  * Arguments, layouts and ownership as for lss_apply_slab.
  */
 int lss_apply_slab_noalloc(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,

@@ -23,7 +23,7 @@ void free_ctx(lss_ctx* c) {
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
-                    c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->iface, c->d_slabs, c->d_err, c->d_bar,
+                    c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->d_slabs, c->d_err, c->d_bar,
                     c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf, c->io_buf, c->dir_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -179,7 +179,7 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     const int n = c->n, b = c->b, bs = slab->b_slab;
     const int nl = (n + 2 + bs - 1) / bs;
     c->n_slabs = nl;
-    long long coff = 0, foff = 0;
+    long long coff = 0, foff = 0, woff = 0;
     for (int i = 0; i < nl; ++i) {
         SlabDev sd{};
         if (i == 0) {
@@ -196,13 +196,15 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
             free_ctx(c);
             return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "a slab subproblem is wider than 32 layers");
         }
-        sd.ldw = (sd.w + 1) & ~1;
+        sd.ldw = sd.w <= 16 ? 16 : 32;
         sd.cstride = (sd.w * 9 + 1) & ~1;
-        sd.rsz = sd.w * sd.ldw + sd.cstride;
+        sd.bs = sd.ldw * sd.ldw;
         sd.coef_off = coff;
         sd.fac_off = foff;
+        sd.work_off = woff;
         coff += (long long)sd.cstride * c->n_tot;
-        foff += (long long)sd.rsz * c->n_tot;
+        foff += cr_fac_entries(c->n_tot, sd.bs, sd.ldw);
+        woff += (long long)sd.bs * cr_work_blocks(c->n_tot);
         c->slabs.push_back(sd);
     }
 
@@ -220,6 +222,8 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
         else rc = dalloc(c, &c->coef, (size_t)coff * cs, "coefficients fp32");
     }
     rc = rc ? rc : dalloc(c, &c->fac, (size_t)foff * cs, "slab factors");
+    c->work_len = woff;
+    rc = rc ? rc : dalloc(c, &c->cr_work, (size_t)2 * woff * cs, "reduction work");
     rc = rc ? rc : dalloc(c, &c->iface, (size_t)3 * nl * c->n_tot * c->n_tot * cs, "interface maps");
     rc = rc ? rc : dalloc(c, (void**)&c->d_slabs, nl * sizeof(SlabDev), "slabs");
     rc = rc ? rc : dalloc(c, (void**)&c->d_err, sizeof(int), "status");

@@ -15,12 +15,89 @@ struct SlabDev {
     int nl;         // layers of D_i
     int na;         // auxiliary layers (0 for the first slab)
     int w;          // subproblem width in layers
-    int ldw;        // leading dimension of the stored block inverses (w rounded up to even)
+    int ldw;        // padded block size: 16 when w <= 16, else 32 (blocks are ldw x ldw, zero outside w x w)
     int cstride;    // complex entries per block row of the coefficient table (w*9 rounded up to even)
-    int rsz;        // complex entries per block-row record: G_k^T (w x ldw), then the coefficient row (cstride)
+    int bs;         // complex entries per stored block (ldw x ldw, column-major)
     long long coef_off;  // offset (complex entries) of this slab's coefficient table
-    long long fac_off;   // offset (complex entries) of this slab's block-row records
+    long long fac_off;   // offset (complex entries) of this slab's cyclic-reduction factors
+    long long work_off;  // offset (complex entries) of this slab's factorization work blocks (per parity)
 };
+
+// Cyclic reduction along x2 (block rows k = 0..n_tot-1): level l has K_l rows,
+// K_0 = n_tot, K_{l+1} = ceil(K_l / 2); the odd rows of level l are eliminated
+// and its even rows form level l+1, until one row is left (L levels with more
+// than one row).  Per slab the factors are stored in the order a solve reads
+// them, in blocks of bs entries:
+//   forward part, level l = 0..L-1: D^{-1} of the odd rows (K_l / 2 blocks),
+//     then for l >= 1 the blocks C, B of the even rows (2 ceil(K_l / 2));
+//   the top row's D^{-1};
+//   backward part, level l = L-1..1: D^{-1}C, D^{-1}B of the odd rows
+//     (2 (K_l / 2) blocks);
+// then, in entries: level 0's off-diagonal bands, 6 ldw per block row (C then
+// B, layer offsets -1, 0, +1; even rows first, then odd rows), and rows na and
+// w-1 of level 0's D^{-1} (2 ldw per odd row).
+#ifdef __CUDACC__
+#define LSS_HD __host__ __device__
+#else
+#define LSS_HD
+#endif
+struct CrLevelOffs {
+    int K;              // rows of the level
+    long long dinv;     // block offset of the odd rows' D^{-1}
+    long long cbe;      // block offset of the even rows' C, B (l >= 1)
+    long long dcdb;     // block offset of the odd rows' D^{-1}C, D^{-1}B (l >= 1)
+};
+LSS_HD inline int cr_levels(int K0) {
+    int L = 0;
+    for (int K = K0; K > 1; K = (K + 1) / 2) ++L;
+    return L;
+}
+// Level l's offsets; for l = L, K = 1 and dinv is the top inverse's block.
+LSS_HD inline CrLevelOffs cr_level(int K0, int l) {
+    const int L = cr_levels(K0);
+    CrLevelOffs o{K0, 0, 0, 0};
+    long long off = 0;   // forward part
+    int k = K0;
+    for (int t = 0; t <= L; ++t) {
+        if (t == l) {
+            o.K = k;
+            o.dinv = off;
+            o.cbe = t >= 1 ? off + k / 2 : 0;
+        }
+        if (t == L) break;
+        off += k / 2;
+        if (t >= 1) off += 2LL * ((k + 1) / 2);
+        k = (k + 1) / 2;
+    }
+    if (l >= 1 && l < L) {   // backward part starts after the top block
+        long long d = off + 1;
+        k = K0;
+        for (int t = 0; t < L; ++t) {
+            if (t > l) d += 2LL * (k / 2);
+            k = (k + 1) / 2;
+        }
+        o.dcdb = d;
+    }
+    return o;
+}
+LSS_HD inline long long cr_top_block(int K0) { return cr_level(K0, cr_levels(K0)).dinv; }
+LSS_HD inline long long cr_nblocks(int K0) {
+    const int L = cr_levels(K0);
+    long long nb = cr_top_block(K0) + 1;
+    int k = K0;
+    for (int t = 0; t < L; ++t) {
+        if (t >= 1) nb += 2LL * (k / 2);
+        k = (k + 1) / 2;
+    }
+    return nb;
+}
+// Entries of one slab's factor area (blocks, level-0 bands, level-0 D^{-1} rows).
+LSS_HD inline long long cr_fac_entries(int K0, int bs, int ldw) {
+    return cr_nblocks(K0) * bs + 6LL * ldw * K0 + 2LL * ldw * (K0 / 2);
+}
+// Factorization work blocks per slab and parity: A (K_0), C and B (2 K_0) of
+// every row, D^{-1}C and D^{-1}B of the odd rows (2 (K_0 / 2)).
+LSS_HD inline long long cr_work_blocks(int K0) { return 4LL * K0; }
 
 struct lss_ctx {
     // problem
@@ -47,7 +124,8 @@ struct lss_ctx {
     double2* gam_aux = nullptr;   // n_samples x b_aux x (2b+1) x 9
     double2* coef64 = nullptr;    // slab row coefficients, complex128
     void* coef = nullptr;         // working-precision coefficients (== coef64 for FP64)
-    void* fac = nullptr;          // per block row: G_k^T then the row's coefficients (working precision)
+    void* fac = nullptr;          // cyclic-reduction factors of every slab (working precision)
+    void* cr_work = nullptr;      // factorization work blocks, two parities (levels alternate)
     void* iface = nullptr;        // interface maps Lambda, Gamma, Phi: 3 x n_slabs x n_tot^2
     SlabDev* d_slabs = nullptr;
     int* d_err = nullptr;
@@ -57,9 +135,10 @@ struct lss_ctx {
     double2* mv_buf = nullptr; size_t mv_cap = 0;      // n x L x R FFT scratch
     void* f_buf = nullptr; size_t f_cap = 0;           // R x n_tot^2 sparsified rhs
     void* side_buf = nullptr; size_t side_cap = 0;     // 4 x n_slabs x n_tot x R interface vectors
-    void* z_buf = nullptr; size_t z_cap = 0;           // Thomas forward scratch
+    void* z_buf = nullptr; size_t z_cap = 0;           // slab-solve right-hand sides in global memory
     double2* kr_buf = nullptr; size_t kr_cap = 0;      // Krylov basis storage
     double2* red_buf = nullptr; size_t red_cap = 0;    // reduction partials
+    long long work_len = 0;       // complex entries of one level work buffer
     void* io_buf = nullptr; size_t io_cap = 0;         // host-buffer solve staging
     void* dir_buf = nullptr; size_t dir_cap = 0;       // plane-wave directions
     int num_sms = 0;

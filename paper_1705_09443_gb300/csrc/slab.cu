@@ -3,11 +3,22 @@
 // Each slab subproblem S_i (Eq. Hwv_approx) is block tridiagonal along x2 with
 // w x w blocks (w layers of the slab): A_k (coupling dk = 0), C_k (dk = -1),
 // B_k (dk = +1), each tridiagonal in the layer index.  It is factored by block
-// Gaussian elimination, D_0 = A_0, D_k = A_k - C_k D_{k-1}^{-1} B_{k-1}, with
-// partial pivoting inside each D_k (Gauss-Jordan), storing G_k = D_k^{-1}.
-// Per block row k the slab keeps one contiguous record: G_k transposed
-// (element (p, a) at a*ldw + p) followed by the row's stencil coefficients, so
-// a solve streams one record per step with a single bulk copy.
+// cyclic reduction along x2: at level l the odd rows are eliminated, which
+// leaves the even rows coupled by
+//   A'_e = A_e - C_e D_{e-1}^{-1} B_{e-1} - B_e D_{e+1}^{-1} C_{e+1},
+//   C'_e = -C_e D_{e-1}^{-1} C_{e-1},  B'_e = -B_e D_{e+1}^{-1} B_{e+1},
+// with D_o = A_o inverted by Gauss-Jordan with partial pivoting.  A solve is
+//   forward:  y_o = D_o^{-1} b_o,  b_e <- b_e - C_e y_{e-1} - B_e y_{e+1},
+//   top:      x_0 = D_top^{-1} b_0,
+//   backward: x_o = y_o - D_o^{-1}C_o x_{o-1} - D_o^{-1}B_o x_{o+1}
+//             (level 0: x_o = y_o - D_o^{-1} (C_o x_{o-1} + B_o x_{o+1}) with the
+//             tridiagonal stencil bands),
+// log2(n_tot) levels deep instead of n_tot sequential block steps; every row
+// of a level is independent.  This is block Gaussian elimination in the
+// odd-even order, so it gives the same T~_i as the sequential sweep of the
+// block rows up to rounding.  The factors are stored in the order a solve
+// reads them, and a solve streams them through shared memory with TMA bulk
+// copies.
 //
 // Algorithm 2's sweep is evaluated slab-parallel.  With a_i = T~_i f_i and the
 // interface maps (rows of T~_i applied to unit couplings)
@@ -34,660 +45,748 @@
 
 namespace {
 
-constexpr int kStages = 3;      // TMA ring depth of the generic multi-RHS solve
-constexpr int kSolveThreads = 128;
+constexpr int kSolveThreads = 384;
+constexpr int kGjWarps = 2;
+constexpr int kEvWarps = 2;
+constexpr size_t kSmemBudget = size_t(220) * 1024;
+constexpr int kMaxIfSlabs = 2048;   // slab widths cached in shared memory by the interface-map kernel
+
+// acc - a*b
+__device__ __forceinline__ double2 cfnma(double2 a, double2 b, double2 acc) {
+    acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ float2 cfnma(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(-a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(-a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
+    return acc;
+}
+
+// Entry offsets of a slab's level-0 bands and level-0 D^{-1} rows.
+__host__ __device__ inline long long cr_t0_off(int K0, int bs) { return cr_nblocks(K0) * bs; }
+__host__ __device__ inline long long cr_p0_off(int K0, int bs, int ldw) { return cr_t0_off(K0, bs) + 6LL * ldw * K0; }
 
 // ---------------------------------------------------------------- factorization
-// One thread per column of the augmented block [D_k | I] (2w <= 64 columns) and
-// NR threads splitting the rows of each column (NR = 1 for FP32, NR = 4 for
-// FP64 to use all four sub-partitions).  The Schur update
-// D_k = A_k - C_k (G_{k-1} B_{k-1}) is computed column by column by the thread
-// owning the column; Gauss-Jordan with partial pivoting needs two barriers per
-// pivot.  Writes the block-row records (G_k^T, then the coefficient row).
-template <typename T, int NR>
-__global__ void __launch_bounds__(64 * NR) factor_kernel(const SlabDev* __restrict__ slabs,
-                                                         const cx<T>* __restrict__ coef, cx<T>* __restrict__ rec,
-                                                         int n_tot, int* err) {
-    using C = cx<T>;
-    const SlabDev sd = slabs[blockIdx.x];
-    const int w = sd.w, ldw = sd.ldw;
-    constexpr int LD = 65;                        // column stride of M (column-major, padded)
-    extern __shared__ __align__(128) unsigned char smraw_f[];
-    C* M = reinterpret_cast<C*>(smraw_f);         // column q at M + q*LD, rows 0..w-1
-    C* Gp = M + 64 * LD;                          // G_{k-1}, column-major, stride LD
-    C* X = Gp + 32 * LD;                          // G_{k-1} B_{k-1}, column-major
-    __shared__ int piv_row;
-    __shared__ C piv_inv;
-    const int q = threadIdx.x % 64, h = threadIdx.x / 64;
-    const bool colq = q < 2 * w;
-    const C* cf = coef + sd.coef_off;
-    C* Rr = rec + sd.fac_off;
-    const C zero = czero<C>();
-    C* Mq = M + q * LD;
-    for (int k = 0; k < n_tot; ++k) {
-        const C* ck = cf + (long long)k * sd.cstride;
-        C* Rk = Rr + (long long)k * sd.rsz;
-        for (int e = threadIdx.x; e < sd.cstride; e += blockDim.x) Rk[w * ldw + e] = ck[e];
-        if (colq && q < w) {
-            // column q of X = G_{k-1} B_{k-1}
-            C b0 = zero, b1 = zero, b2 = zero;   // B_{k-1}[a][q], a = q-1, q, q+1
-            if (k > 0) {
-                const C* cp = cf + (long long)(k - 1) * sd.cstride;
-                if (q > 0) b0 = cp[(q - 1) * 9 + 2 * 3 + 2];
-                b1 = cp[q * 9 + 1 * 3 + 2];
-                if (q + 1 < w) b2 = cp[(q + 1) * 9 + 0 * 3 + 2];
-            }
-            C* Xq = X + q * LD;
-            const C* G0 = Gp + (q > 0 ? q - 1 : 0) * LD;
-            const C* G1 = Gp + q * LD;
-            const C* G2 = Gp + (q + 1 < w ? q + 1 : q) * LD;
-#pragma unroll 4
-            for (int p = h; p < w; p += NR) {
-                C x = zero;
-                if (k > 0) {
-                    x = cfma(G1[p], b1, x);
-                    if (q > 0) x = cfma(G0[p], b0, x);
-                    if (q + 1 < w) x = cfma(G2[p], b2, x);
-                }
-                Xq[p] = x;
-            }
-        }
-        if (NR > 1) __syncthreads();
-        if (colq) {
-            const C* Xq = X + q * LD;
-#pragma unroll 4
-            for (int p = h; p < w; p += NR) {
-                C v = zero;
-                if (q < w) {
-                    const int d = q - p;
-                    if (d >= -1 && d <= 1) v = ck[p * 9 + (d + 1) * 3 + 1];
-                    if (k > 0) {
-                        const C* cr = ck + p * 9;
-                        if (p > 0) v = v - cr[0] * Xq[p - 1];
-                        v = v - cr[3] * Xq[p];
-                        if (p + 1 < w) v = v - cr[6] * Xq[p + 1];
-                    }
-                } else if (q - w == p) {
-                    v.x = T(1);
-                }
-                Mq[p] = v;
-            }
-        }
-        __syncthreads();
-        for (int j = 0; j < w; ++j) {
-            if (threadIdx.x < 32) {
-                const int i = j + threadIdx.x;
-                T val = (i < w) ? cabs2(M[j * LD + i]) : T(-1);
-                int best = i;
-                for (int off = 16; off > 0; off >>= 1) {
-                    const T ov = __shfl_down_sync(0xffffffffu, val, off);
-                    const int ob = __shfl_down_sync(0xffffffffu, best, off);
-                    if (ov > val || (ov == val && ob < best)) { val = ov; best = ob; }
-                }
-                if (threadIdx.x == 0) {
-                    piv_row = best;
-                    C pv = M[j * LD + best];
-                    const T a2 = cabs2(pv);
-                    if (!(a2 > T(0)) || !isfinite(a2)) {
-                        atomicOr(err, LSS_DERR_SINGULAR);
-                        pv = zero;
-                        pv.x = T(1);
-                    }
-                    piv_inv = crecip(pv);
-                }
-            }
-            __syncthreads();
-            // rows j and pr are swapped and row j scaled in every column q > j;
-            // columns <= j are never read again, so they are left as they are
-            const int pr = piv_row;
-            C a = zero, mj = zero;
-            if (colq && q > j) {
-                a = Mq[j];
-                mj = Mq[pr] * piv_inv;
-            }
-            if (NR > 1) __syncthreads();
-            if (colq && q > j) {
-                const C* Mj = M + j * LD;
-                const C mpj = Mj[j];                  // entry (pr, j) after the swap
-#pragma unroll 4
-                for (int i = h; i < w; i += NR) {
-                    const C mij = Mj[i];
-                    const C cur = Mq[i];
-                    C nv;
-                    if (i == j) nv = mj;
-                    else if (i == pr) nv = a - mpj * mj;
-                    else nv = cur - mij * mj;
-                    Mq[i] = nv;
-                }
-            }
-            __syncthreads();
-        }
-        // G_k = right half; column a of G is column w + a of M
-        if (colq && q >= w) {
-            const int a = q - w;
-            for (int p = h; p < ldw; p += NR) {
-                const C v = (p < w) ? Mq[p] : zero;
-                Rk[a * ldw + p] = v;
-                if (p < w) Gp[a * LD + p] = v;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------- generic multi-RHS slab solve
-template <typename C>
-struct SolveArgs {
-    const SlabDev* slabs;
-    int n_slabs, n_tot, n, b;
-    const C* rec;
-    const double2* v_in;   // R x (layers of D_i) x n_tot
-    double2* w_out;
-    int slab;
-    C* zbuf;               // forward-elimination scratch
-    long long zstride;     // per CTA
-    int R, RC;             // total RHS, RHS per CTA
-    int* err;
-};
-
-// One CTA solves S_i x = [0_aux; v] for RC right-hand sides and writes the
-// D_i part (T~_i v): forward elimination z_k = G_k (b_k - C_k z_{k-1}), back
-// substitution x_k = z_k - G_k B_k x_{k+1}.  Block-row records stream through
-// a TMA ring; the 2 n_tot - 1 block rows are visited as one sequence.
+// Level 0's blocks from the stencil rows of the coefficient table (row p of
+// block row k: entry (da + 1) * 3 + (dk + 1) couples layer p + da of row k + dk),
+// dense in the work area (C_0 = B_{K-1} = 0), and the banded copy the solves read.
 template <typename T>
-__global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs<cx<T>> A) {
+__global__ void cr_build0_kernel(const SlabDev* __restrict__ slabs, const cx<T>* __restrict__ coef,
+                                 cx<T>* __restrict__ work, cx<T>* __restrict__ fac, int K0) {
     using C = cx<T>;
-    const int i = A.slab;
-    const SlabDev sd = A.slabs[i];
-    const int w = sd.w, ldw = sd.ldw, K = A.n_tot, rsz = sd.rsz, gsz = w * ldw;
-    const int r0 = blockIdx.y * A.RC;
-    const int rc = min(A.RC, A.R - r0);
-    if (rc <= 0) return;
-    const int RC = A.RC;
-    extern __shared__ __align__(128) unsigned char smraw_s[];
-    C* Rs = reinterpret_cast<C*>(smraw_s);   // kStages x rsz
-    C* v = Rs + kStages * rsz;               // w x RC
-    C* zp = v + w * RC;                      // w x RC
-    __shared__ __align__(8) uint64_t bar[kStages];
-    const C* Rg = A.rec + sd.fac_off;
-    C* Z = A.zbuf + (long long)blockIdx.y * A.zstride;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int outs = w * rc;
-    int TP = 1;
-    while (TP < 32 && outs * TP * 2 <= nth) TP <<= 1;
-    const int ostep = nth / TP;
-    const int nseq = 2 * K - 1;
-    const unsigned rbytes = (unsigned)(rsz * sizeof(C));
-    auto kk_of = [K](int pos) { return pos < K ? pos : 2 * K - 2 - pos; };
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
-        fence_mbar_init();
+    const SlabDev sd = slabs[blockIdx.y];
+    const int k = blockIdx.x;
+    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
+    const C* ck = coef + sd.coef_off + (long long)k * sd.cstride;
+    C* W = work + sd.work_off;
+    C* Ab = W + (long long)k * bs;
+    C* Cb = W + ((long long)K0 + 2LL * k) * bs;
+    C* Bb = Cb + bs;
+    for (int e = threadIdx.x; e < bs; e += blockDim.x) {
+        const int q = e / ldw, p = e % ldw;   // element (p, q) at q * ldw + p
+        C a = czero<C>(), cm = czero<C>(), cp = czero<C>();
+        const int d = q - p;
+        if (p < w && q < w && d >= -1 && d <= 1) {
+            const C* r = ck + p * 9 + (d + 1) * 3;
+            a = r[1];
+            if (k > 0) cm = r[0];
+            if (k + 1 < K0) cp = r[2];
+        }
+        Ab[e] = a;
+        Cb[e] = cm;
+        Bb[e] = cp;
     }
-    __syncthreads();
-    if (tid == 0)
-        for (int pos = 0; pos < kStages && pos < nseq; ++pos) {
-            mbar_expect_tx(&bar[pos], rbytes);
-            tma_load_1d(Rs + pos * rsz, Rg + (long long)kk_of(pos) * rsz, rbytes, &bar[pos]);
-        }
-    bool ok = true;
-    for (int pos = 0; pos < nseq; ++pos) {
-        const int st = pos % kStages;
-        const int k = kk_of(pos);
-        if (!mbar_wait(&bar[st], (pos / kStages) & 1, A.err)) ok = false;
-        if (!__syncthreads_and(ok)) break;
-        const C* Gk = Rs + st * rsz;
-        const C* ck = Gk + gsz;
-        const bool fwd = pos < K;
-        for (int idx = tid; idx < w * rc; idx += nth) {
-            const int p = idx % w, rr = idx / w;
-            C bv = czero<C>();
-            if (fwd) {
-                if (p >= sd.na)
-                    bv = to_c<C>(A.v_in[((long long)(r0 + rr) * sd.nl + (p - sd.na)) * K + k]);
-                if (k > 0)
-                    for (int da = -1; da <= 1; ++da) {
-                        const int a = p + da;
-                        if (a >= 0 && a < w) bv = bv - ck[p * 9 + (da + 1) * 3 + 0] * zp[a * RC + rr];
-                    }
-            } else {
-                for (int da = -1; da <= 1; ++da) {
-                    const int a = p + da;
-                    if (a >= 0 && a < w) bv = cfma(ck[p * 9 + (da + 1) * 3 + 2], zp[a * RC + rr], bv);
-                }
-            }
-            v[p * RC + rr] = bv;
-        }
-        __syncthreads();
-        for (int ob = 0; ob < outs; ob += ostep) {
-            const int o = ob + tid / TP, kq = tid % TP;
-            const bool active = o < outs;
-            const int op = active ? o % w : 0, orr = active ? o / w : 0;
-            C acc = czero<C>();
-            if (active)
-                for (int a = kq; a < w; a += TP) acc = cfma(Gk[a * ldw + op], v[a * RC + orr], acc);
-            for (int off = TP >> 1; off > 0; off >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-            }
-            if (active && kq == 0) {
-                C x;
-                if (fwd) {
-                    x = acc;
-                    Z[((long long)k * w + op) * RC + orr] = x;
-                } else {
-                    x = Z[((long long)k * w + op) * RC + orr] - acc;
-                }
-                zp[op * RC + orr] = x;
-                if ((!fwd || k == K - 1) && op >= sd.na)
-                    A.w_out[((long long)(r0 + orr) * sd.nl + (op - sd.na)) * K + k] = to_d(x);
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && pos + kStages < nseq) {
-            mbar_expect_tx(&bar[st], rbytes);
-            tma_load_1d(Rs + st * rsz, Rg + (long long)kk_of(pos + kStages) * rsz, rbytes, &bar[st]);
-        }
-    }
-    if (!ok && tid == 0) {
-        // a wait expired: give the copies already issued a bounded chance to land
-        const long long t0 = clock64();
-        while (clock64() - t0 < 2000000ll) __nanosleep(1000);
+    const long long row = (k & 1) ? (K0 + 1) / 2 + k / 2 : k / 2;
+    C* band = fac + sd.fac_off + cr_t0_off(K0, bs) + row * 6 * ldw;
+    for (int e = threadIdx.x; e < 6 * ldw; e += blockDim.x) {
+        const int bnd = e / ldw, p = e % ldw;
+        const int da = bnd % 3 - 1, slot = bnd < 3 ? 0 : 2;
+        C v = czero<C>();
+        const bool has = bnd < 3 ? k > 0 : k + 1 < K0;
+        if (p < w && p + da >= 0 && p + da < w && has) v = ck[p * 9 + (da + 1) * 3 + slot];
+        band[e] = v;
     }
 }
 
-// ---------------------------------------------------------------- interface maps
-// Work item = (slab i, side, chunk of kIfNC columns j): solve S_i X = H e_j for
-// the chunk (side 0: the coupling H_{[i,i-1]} into D_i's first layer; side 1:
-// H_{[i,i+1]} into its last layer) and keep only the rows needed: side 0 ->
-// Lambda_i (last layer) and Gamma_i (first layer), side 1 -> Phi_i (first
-// layer).  Column j's right-hand side is zero above block row j-1, so the
-// forward pass of a chunk starts there.  Per block row the update is a
-// (w x w) x (w x kIfNC) product: threads own (column, rows p = rg, rg + 4, ...)
-// and G_k is read as a warp broadcast.  Persistent grid over the items.
-constexpr int kIfNC = 64;
-constexpr int kIfThreads = 256;
-constexpr int kIfRows = 8;      // rows per thread: w <= 32 over 4 row groups
-constexpr int kIfStages = 4;
-
+// Gauss-Jordan with partial pivoting on [A | I | C | B] for the odd rows of
+// level l (giving D^{-1}, D^{-1}C, D^{-1}B), or on [A | I] for the top row.
+// One warp per block row; the augmented matrix sits row-major in shared memory
+// (row stride rs) and the lanes own its columns.
 template <typename T>
-__global__ void __launch_bounds__(kIfThreads) iface_kernel(const SlabDev* __restrict__ slabs, int n_slabs,
-                                                           int n_tot, const cx<T>* __restrict__ rec,
-                                                           cx<T>* __restrict__ iface, cx<T>* __restrict__ zbuf,
-                                                           long long zstride, int nitems, int rmax, int* err) {
+__global__ void __launch_bounds__(32 * kGjWarps) cr_gj_kernel(const SlabDev* __restrict__ slabs,
+                                                              cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
+                                                              long long work_len, int K0, int l, int per_slab,
+                                                              int n_slabs, int top, int rs, int* err) {
     using C = cx<T>;
-    const int nch = (n_tot + kIfNC - 1) / kIfNC;
-    const int K = n_tot;
-    const long long nt2 = (long long)n_tot * n_tot;
-    extern __shared__ __align__(128) unsigned char smi[];
-    C* Rs = reinterpret_cast<C*>(smi);           // kIfStages x rmax
-    C* V = Rs + kIfStages * rmax;                // 32 x kIfNC
-    C* zp = V + 32 * kIfNC;                      // 32 x kIfNC
-    __shared__ __align__(8) uint64_t bar[kIfStages];
-    const int tid = threadIdx.x;
-    const int c = tid % kIfNC, rg = tid / kIfNC;
-    C* Z = zbuf + (long long)blockIdx.x * zstride;
-    if (tid == 0) {
-        for (int st = 0; st < kIfStages; ++st) mbar_init(&bar[st], 1);
-        fence_mbar_init();
+    extern __shared__ __align__(16) unsigned char smg[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int task = blockIdx.x * kGjWarps + warp;
+    if (task >= per_slab * n_slabs) return;   // the whole warp leaves
+    const int si = task / per_slab, o = task % per_slab;
+    const SlabDev sd = slabs[si];
+    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
+    C* M = reinterpret_cast<C*>(smg) + (size_t)warp * 32 * rs;
+    const CrLevelOffs lo = cr_level(K0, l);
+    const int K = lo.K;
+    C* W = work + sd.work_off + (l & 1) * work_len;
+    C* F = fac + sd.fac_off;
+    const int j = top ? 0 : 2 * o + 1;
+    const int ncol = top ? 2 * w : 4 * w;
+    const C* Ab = W + (long long)j * bs;
+    const C* Cb = W + ((long long)K0 + 2LL * j) * bs;
+    const C* Bb = Cb + bs;
+    const bool hasB = !top && j + 1 < K;
+    for (int e = lane; e < w * ncol; e += 32) {
+        const int i = e / ncol, q = e % ncol;
+        C v = czero<C>();
+        if (q < w) v = Ab[(long long)q * ldw + i];
+        else if (q < 2 * w) { if (q - w == i) v.x = T(1); }
+        else if (q < 3 * w) v = Cb[(long long)(q - 2 * w) * ldw + i];
+        else if (hasB) v = Bb[(long long)(q - 3 * w) * ldw + i];
+        M[i * rs + q] = v;
     }
-    __syncthreads();
-    unsigned gpos = 0;   // running TMA sequence position (continues across items)
-    bool ok = true;
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-        int t = item, i, side;
-        const int n0 = (n_slabs - 1) * nch;
-        if (t < n0) { i = 1 + t / nch; side = 0; t %= nch; }
-        else { t -= n0; i = 1 + t / nch; side = 1; t %= nch; }
-        const SlabDev sd = slabs[i];
-        const int w = sd.w, ldw = sd.ldw, gsz = w * ldw, rsz = sd.rsz, na = sd.na;
-        const int j0 = t * kIfNC;
-        const int ncol = min(kIfNC, n_tot - j0);
-        const int k0 = max(0, j0 - 1);
-        const int nf = K - k0, nseq = nf + K - 1;
-        const int pin = side == 0 ? na : w - 1;
-        const C* Rg = rec + sd.fac_off;
-        const unsigned rbytes = (unsigned)(rsz * sizeof(C));
-        // forward: k = k0 + pos (pos < nf); backward: k = K - 2 - (pos - nf)
-        auto kseq = [&](int pos) { return pos < nf ? k0 + pos : K - 2 - (pos - nf); };
-        if (tid == 0)
-            for (int pp = 0; pp < kIfStages && pp < nseq; ++pp) {
-                const unsigned gp = gpos + pp;
-                const int st = gp % kIfStages;
-                mbar_expect_tx(&bar[st], rbytes);
-                tma_load_1d(Rs + st * rmax, Rg + (long long)kseq(pp) * rsz, rbytes, &bar[st]);
-            }
-        for (int pos = 0; pos < nseq; ++pos) {
-            const unsigned gp = gpos + pos;
-            const int st = gp % kIfStages;
-            const int k = kseq(pos);
-            const bool fwd = pos < nf;
-            // scratch values of this block row, loaded before the wait and the product
-            C zold[kIfRows];
-#pragma unroll
-            for (int r = 0; r < kIfRows; ++r) {
-                const int p = rg + 4 * r;
-                zold[r] = (!fwd && p < w && k >= k0) ? Z[((long long)(k - k0) * w + p) * kIfNC + c] : czero<C>();
-            }
-            if (!mbar_wait(&bar[st], (gp / kIfStages) & 1, err)) ok = false;
-            if (!__syncthreads_and(ok)) break;
-            const C* Gk = Rs + st * rmax;
-            const C* ck = Gk + gsz;
-            // V = b_k - C_k z_{k-1} (forward) or B_k x_{k+1} (backward)
-            for (int idx = tid; idx < w * kIfNC; idx += kIfThreads) {
-                const int p = idx / kIfNC, cc = idx % kIfNC;
-                C v = czero<C>();
-                if (cc < ncol) {
-                    const C* cp = ck + p * 9;
-                    if (fwd) {
-                        const int dk = j0 + cc - k;
-                        if (p == pin && dk >= -1 && dk <= 1) v = cp[(side == 0 ? 0 : 6) + dk + 1];
-                        if (k > k0) {
-                            if (p > 0) v = v - cp[0] * zp[(p - 1) * kIfNC + cc];
-                            v = v - cp[3] * zp[p * kIfNC + cc];
-                            if (p + 1 < w) v = v - cp[6] * zp[(p + 1) * kIfNC + cc];
-                        }
-                    } else {
-                        if (p > 0) v = cfma(cp[2], zp[(p - 1) * kIfNC + cc], v);
-                        v = cfma(cp[5], zp[p * kIfNC + cc], v);
-                        if (p + 1 < w) v = cfma(cp[8], zp[(p + 1) * kIfNC + cc], v);
-                    }
-                }
-                V[p * kIfNC + cc] = v;
-            }
-            __syncthreads();
-            C acc[kIfRows];
-#pragma unroll
-            for (int r = 0; r < kIfRows; ++r) acc[r] = czero<C>();
-            for (int a = 0; a < w; ++a) {
-                const C v = V[a * kIfNC + c];
-#pragma unroll
-                for (int r = 0; r < kIfRows; ++r) {
-                    const int p = rg + 4 * r;
-                    if (p < w) acc[r] = cfma(Gk[a * ldw + p], v, acc[r]);
-                }
-            }
-            __syncthreads();   // every thread has read zp (through V), V and the stage
-            if (tid == 0 && pos + kIfStages < nseq) {
-                const unsigned gn = gpos + pos + kIfStages;
-                const int sn = gn % kIfStages;
-                mbar_expect_tx(&bar[sn], rbytes);
-                tma_load_1d(Rs + sn * rmax, Rg + (long long)kseq(pos + kIfStages) * rsz, rbytes, &bar[sn]);
-            }
-#pragma unroll
-            for (int r = 0; r < kIfRows; ++r) {
-                const int p = rg + 4 * r;
-                if (p >= w) continue;
-                C x;
-                if (fwd) {
-                    x = acc[r];
-                    Z[((long long)(k - k0) * w + p) * kIfNC + c] = x;
-                } else {
-                    x = zold[r] - acc[r];
-                }
-                zp[p * kIfNC + c] = x;
-                if ((!fwd || k == K - 1) && c < ncol) {
-                    const long long e = (long long)k * n_tot + j0 + c;
-                    if (side == 0) {
-                        if (p == w - 1) iface[(0LL * n_slabs + i) * nt2 + e] = x;
-                        if (p == na) iface[(1LL * n_slabs + i) * nt2 + e] = x;
-                    } else if (p == na) {
-                        iface[(2LL * n_slabs + i) * nt2 + e] = x;
-                    }
-                }
-            }
-            __syncthreads();
+    __syncwarp();
+    for (int jj = 0; jj < w; ++jj) {
+        T val = (lane >= jj && lane < w) ? cabs2(M[lane * rs + jj]) : T(-1);
+        if (!(val >= T(0)) || !isfinite(val)) val = (lane >= jj && lane < w) ? T(0) : T(-1);
+        int best = lane;
+        for (int off = 16; off > 0; off >>= 1) {
+            const T ov = __shfl_xor_sync(0xffffffffu, val, off);
+            const int ob = __shfl_xor_sync(0xffffffffu, best, off);
+            if (ov > val || (ov == val && ob < best)) { val = ov; best = ob; }
         }
-        gpos += nseq;
-    }
-    if (!ok && tid == 0) {
-        const long long t0 = clock64();
-        while (clock64() - t0 < 2000000ll) __nanosleep(1000);
-    }
-}
-
-// ---------------------------------------------------------------- sweep slab solves
-enum SweepMode { SW_A = 0, SW_E = 1 };
-
-template <typename C>
-struct SweepArgs {
-    const SlabDev* slabs;
-    int n_slabs, n_tot, n, b, R;
-    const C* rec;
-    const C* f;            // R x n_tot^2, x2 index slowest
-    C* a_first;            // [slab][k][R]
-    C* a_last;
-    const C* lam;          // [slab][k][R]
-    const C* phi;
-    double2* y;            // R x n^2
-    C* zbuf;               // forward-elimination scratch when it does not fit in shared memory
-    long long zstride;
-    int* err;
-};
-
-template <typename C>
-__device__ __forceinline__ C shfl_c(C v, int src) {
-    v.x = __shfl_sync(0xffffffffu, v.x, src);
-    v.y = __shfl_sync(0xffffffffu, v.y, src);
-    return v;
-}
-template <typename C>
-__device__ __forceinline__ C shfl_up_c(C v) {
-    v.x = __shfl_up_sync(0xffffffffu, v.x, 1);
-    v.y = __shfl_up_sync(0xffffffffu, v.y, 1);
-    return v;
-}
-template <typename C>
-__device__ __forceinline__ C shfl_down_c(C v) {
-    v.x = __shfl_down_sync(0xffffffffu, v.x, 1);
-    v.y = __shfl_down_sync(0xffffffffu, v.y, 1);
-    return v;
-}
-
-// Warp-specialised slab solve, one right-hand side per CTA.  Warp NQ is the
-// producer: it streams the block-row records into a ring of S stages, RB
-// consecutive records per stage in one TMA bulk copy (the forward pass walks
-// k upwards, the backward pass downwards; both read contiguous record runs).
-// Warps 0..NQ-1 consume.  Lane l owns row p = l mod 16 of the block row when
-// 2w <= 32 (the two half-warps then split the columns of G_k), else row p = l;
-// the NQ warps split the columns further and sum their slices through shared
-// memory (NQ > 1, FP64).  Neighbours along the layer index come from shuffles
-// and v is broadcast through a per-warp shared-memory vector.  The slab's
-// right-hand-side block and the coupling vectors lambda_{i-1}, phi_{i+1} are
-// preloaded into shared memory, so the consumers issue no global loads; a
-// consumer warp releases a stage by arriving on its "empty" mbarrier.  The
-// forward-elimination values stay in shared memory when they fit (zsmem),
-// else they go to global scratch and are fetched one step ahead.
-template <typename T, int MODE, int NQ, int S, int RB>
-__global__ void __launch_bounds__(32 * (NQ + 1)) sweep_kernel(SweepArgs<cx<T>> A, int zsmem, int rmax, int nlmax) {
-    using C = cx<T>;
-    const int i = blockIdx.x, r = blockIdx.y;
-    const SlabDev sd = A.slabs[i];
-    const int w = sd.w, ldw = sd.ldw, K = A.n_tot, na = sd.na, nl = sd.nl, gsz = w * ldw, rsz = sd.rsz;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    extern __shared__ __align__(128) unsigned char sm2[];
-    C* stage0 = reinterpret_cast<C*>(sm2);         // S x RB x rmax
-    C* part = stage0 + S * RB * rmax;              // 2 x NQ x 32 partial dots
-    C* vsb = part + 2 * NQ * 32;                   // NQ x 32 broadcast vectors
-    C* fs = vsb + NQ * 32;                         // K x nlmax: right-hand side of D_i
-    C* ls = fs + (long long)K * nlmax;             // K: lambda_{i-1}
-    C* ps = ls + K;                                // K: phi_{i+1}
-    C* Zs = ps + K;                                // K x w (zsmem)
-    __shared__ __align__(8) uint64_t full[S], empty[S], pbar[2];
-    const int nfc = (K + RB - 1) / RB, nbc = (K - 1 + RB - 1) / RB, nch = nfc + nbc;
-    // chunk ci -> first record lo and record count; forward chunks ascend, backward descend
-    auto chunk = [&](int ci, int& lo, int& cnt) {
-        if (ci < nfc) {
-            lo = ci * RB;
-            cnt = min(RB, K - lo);
-        } else {
-            const int hi = K - 2 - (ci - nfc) * RB;
-            lo = max(0, hi - RB + 1);
-            cnt = hi - lo + 1;
-        }
-    };
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < S; ++st) {
-            mbar_init(&full[st], 1);
-            mbar_init(&empty[st], NQ);
-        }
-        mbar_init(&pbar[0], NQ);
-        mbar_init(&pbar[1], NQ);
-        fence_mbar_init();
-    }
-    // preload f on D_i (and the coupling vectors) once
-    {
-        const long long nt2 = (long long)K * K;
-        const C* fr = A.f + (long long)r * nt2 + (sd.s + A.b);
-        for (int e = threadIdx.x; e < K * nl; e += blockDim.x) {
-            const int k = e / nl, j = e % nl;
-            fs[k * nlmax + j] = fr[(long long)k * K + j];
-        }
-        if (MODE == SW_E) {
-            const long long vec = (long long)K * A.R;
-            for (int k = threadIdx.x; k < K; k += blockDim.x) {
-                ls[k] = i > 0 ? A.lam[(long long)(i - 1) * vec + (long long)k * A.R + r] : czero<C>();
-                ps[k] = i < A.n_slabs - 1 ? A.phi[(long long)(i + 1) * vec + (long long)k * A.R + r] : czero<C>();
-            }
-        }
-    }
-    __syncthreads();
-    if (warp == NQ) {
-        // ---------------- producer: one bulk copy of RB records per stage
-        if (lane == 0) {
-            const C* Rg = A.rec + sd.fac_off;
-            for (int ci = 0; ci < nch; ++ci) {
-                const int st = ci % S;
-                if (ci >= S && !mbar_wait(&empty[st], ((ci / S) - 1) & 1, A.err)) break;
-                int lo, cnt;
-                chunk(ci, lo, cnt);
-                const unsigned bytes = (unsigned)(cnt * rsz * sizeof(C));
-                mbar_expect_tx(&full[st], bytes);
-                tma_load_1d(stage0 + st * RB * rmax, Rg + (long long)lo * rsz, bytes, &full[st]);
-            }
-        }
-        return;
-    }
-    // ---------------- consumers
-    const int q = warp;
-    const int H = (2 * w <= 32) ? 2 : 1;            // half-warps splitting the columns
-    const int half = H == 2 ? lane >> 4 : 0;
-    const int p = H == 2 ? lane & 15 : lane;
-    const int gw = H == 2 ? 16 : 32;                // shuffle group width
-    const bool act = p < w;
-    const bool lead = act && q == 0 && half == 0;   // writes scratch and outputs
-    C* Z = zsmem ? Zs : A.zbuf + ((long long)i * gridDim.y + r) * A.zstride;
-    const int nsl = NQ * H;                         // column slices
-    const int per = (w + nsl - 1) / nsl;
-    const int sl = q * H + half;
-    const int a0 = min(w, sl * per), a1 = min(w, a0 + per);
-    C* vs = vsb + q * 32;
-    C z = czero<C>();
-    C znext = czero<C>();   // Z[k] for the next backward step (global scratch only)
-    int pos = 0;            // global step index
-    bool ok = true;
-    for (int ci = 0; ci < nch && ok; ++ci) {
-        const int st = ci % S;
-        int lo, cnt;
-        chunk(ci, lo, cnt);
-        const bool fwd = ci < nfc;
-        if (!mbar_wait(&full[st], (ci / S) & 1, A.err)) break;
-        const C* stg = stage0 + st * RB * rmax;
-        for (int jj = 0; jj < cnt; ++jj, ++pos) {
-            const int k = fwd ? lo + jj : lo + cnt - 1 - jj;
-            const C zold = znext;
-            if (!zsmem && !fwd && act && half == 0) {
-                const int kn = k - 1;   // next backward block row
-                if (kn >= 0) znext = Z[(long long)kn * w + p];
-            } else if (!zsmem && fwd && k == K - 1 && act && half == 0 && K >= 2) {
-                znext = Z[(long long)(K - 2) * w + p];
-            }
-            const C* Gk = stg + (k - lo) * rsz;
-            const C* ck = Gk + gsz;
-            C zm, zpl;
-            zm.x = __shfl_up_sync(0xffffffffu, z.x, 1, gw);
-            zm.y = __shfl_up_sync(0xffffffffu, z.y, 1, gw);
-            zpl.x = __shfl_down_sync(0xffffffffu, z.x, 1, gw);
-            zpl.y = __shfl_down_sync(0xffffffffu, z.y, 1, gw);
-            C v = czero<C>();
-            if (act) {
-                const C* cp = ck + p * 9;
-                if (fwd) {
-                    if (p >= na) v = fs[k * nlmax + (p - na)];
-                    if (MODE == SW_E) {
-                        if (p == na && i > 0)
-                            for (int dk = -1; dk <= 1; ++dk) {
-                                const int kk = k + dk;
-                                if (kk >= 0 && kk < K) v = v - cp[0 * 3 + dk + 1] * ls[kk];
-                            }
-                        if (p == w - 1 && i < A.n_slabs - 1)
-                            for (int dk = -1; dk <= 1; ++dk) {
-                                const int kk = k + dk;
-                                if (kk >= 0 && kk < K) v = v - cp[2 * 3 + dk + 1] * ps[kk];
-                            }
-                    }
-                    if (k > 0) {
-                        if (p > 0) v = v - cp[0] * zm;
-                        v = v - cp[3] * z;
-                        if (p + 1 < w) v = v - cp[6] * zpl;
-                    }
-                } else {
-                    if (p > 0) v = cfma(cp[2], zm, v);
-                    v = cfma(cp[5], z, v);
-                    if (p + 1 < w) v = cfma(cp[8], zpl, v);
-                }
-            }
-            __syncwarp();
-            if (half == 0) vs[lane] = v;
-            __syncwarp();
-            C acc0 = czero<C>(), acc1 = czero<C>();
-            if (act) {
-                int a = a0;
-                for (; a + 1 < a1; a += 2) {
-                    acc0 = cfma(Gk[a * ldw + p], vs[a], acc0);
-                    acc1 = cfma(Gk[(a + 1) * ldw + p], vs[a + 1], acc1);
-                }
-                if (a < a1) acc0 = cfma(Gk[a * ldw + p], vs[a], acc0);
-            }
-            C acc = acc0 + acc1;
-            if (H == 2) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
-            }
-            if (NQ > 1) {
-                // sum the column slices of the warps: a bounded mbarrier exchange, two buffers
-                C* pb = part + (pos & 1) * NQ * 32;
-                pb[q * 32 + lane] = acc;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&pbar[pos & 1]);
-                if (!mbar_wait(&pbar[pos & 1], (pos >> 1) & 1, A.err)) { ok = false; break; }
-                acc = pb[lane];
-                for (int qq = 1; qq < NQ; ++qq) acc = acc + pb[qq * 32 + lane];
-            }
-            if (fwd) {
-                z = acc;
-                if (lead) Z[(long long)k * w + p] = z;
-            } else {
-                const C zk = zsmem ? Z[(long long)k * w + p] : zold;
-                z = act ? zk - acc : czero<C>();
-                if (!zsmem) {   // the half-warp / other warps take the value from the lead lane
-                    z.x = __shfl_sync(0xffffffffu, z.x, p, 32);
-                    z.y = __shfl_sync(0xffffffffu, z.y, p, 32);
-                }
-            }
-            if (lead && (!fwd || k == K - 1)) {
-                if (MODE == SW_A) {
-                    const long long e = ((long long)i * K + k) * A.R + r;
-                    if (p == na) A.a_first[e] = z;
-                    if (p == w - 1) A.a_last[e] = z;
-                } else if (p >= na) {
-                    const int x1 = sd.s + (p - na), i2 = k - A.b;
-                    if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
-                        A.y[(long long)r * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(z);
-                }
+        const int r = __shfl_sync(0xffffffffu, best, 0);
+        if (r != jj) {
+            for (int q = jj + lane; q < ncol; q += 32) {
+                const C t = M[jj * rs + q];
+                M[jj * rs + q] = M[r * rs + q];
+                M[r * rs + q] = t;
             }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[st]);   // stage no longer read by this warp
+        C pv = M[jj * rs + jj];
+        const T a2 = cabs2(pv);
+        if (!(a2 > T(0)) || !isfinite(a2)) {
+            if (lane == 0) atomicOr(err, LSS_DERR_SINGULAR);
+            pv = czero<C>();
+            pv.x = T(1);
+        }
+        const C pinv = crecip(pv);
+        __syncwarp();
+        for (int q = jj + 1 + lane; q < ncol; q += 32) M[jj * rs + q] = M[jj * rs + q] * pinv;
+        __syncwarp();
+        // column jj is not written below and not read after this pivot
+        for (int q = jj + 1 + lane; q < ncol; q += 32) {
+            const C mj = M[jj * rs + q];
+            for (int i = 0; i < w; ++i)
+                if (i != jj) M[i * rs + q] = cfnma(M[i * rs + jj], mj, M[i * rs + q]);
+        }
+        __syncwarp();
+    }
+    // [I | D^{-1} | D^{-1}C | D^{-1}B]: column-major blocks
+    C* Dout = F + (lo.dinv + (top ? 0 : o)) * bs;
+    C* DCw = W + (3LL * K0 + 2LL * o) * bs;
+    C* DCf = (!top && l >= 1) ? F + (lo.dcdb + 2LL * o) * bs : nullptr;
+    for (int e = lane; e < bs; e += 32) {
+        const int q = e / ldw, p = e % ldw;
+        const bool in = p < w && q < w;
+        Dout[e] = in ? M[p * rs + w + q] : czero<C>();
+        if (!top) {
+            const C dc = in ? M[p * rs + 2 * w + q] : czero<C>();
+            const C db = in ? M[p * rs + 3 * w + q] : czero<C>();
+            DCw[e] = dc;
+            DCw[bs + e] = db;
+            if (DCf) {
+                DCf[e] = dc;
+                DCf[bs + e] = db;
+            }
+        }
+    }
+    if (!top && l == 0) {   // rows na and w-1 of D^{-1} for the solves that keep only those layers
+        C* P0 = F + cr_p0_off(K0, bs, ldw) + 2LL * o * ldw;
+        for (int e = lane; e < 2 * ldw; e += 32) {
+            const int a = e % ldw, pr = e < ldw ? sd.na : w - 1;
+            P0[e] = a < w ? M[pr * rs + w + a] : czero<C>();
+        }
+    }
+}
+
+// Even rows of level l: A'_e, C'_e, B'_e of level l+1 from D^{-1}C and D^{-1}B
+// of the neighbouring odd rows, into the other work parity (and, for the even
+// rows of level l+1, C' and B' into the factors).  One warp per block row; C_e
+// and B_e are staged row-major in shared memory, lane q computes column q of
+// each product with the right factor's column in registers.
+template <typename T>
+__global__ void __launch_bounds__(32 * kEvWarps) cr_even_kernel(const SlabDev* __restrict__ slabs,
+                                                                cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
+                                                                long long work_len, int K0, int l, int per_slab,
+                                                                int n_slabs, int nlev) {
+    using C = cx<T>;
+    constexpr int LS = 33;
+    extern __shared__ __align__(16) unsigned char sme[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int task = blockIdx.x * kEvWarps + warp;
+    if (task >= per_slab * n_slabs) return;
+    const int si = task / per_slab, t = task % per_slab;
+    const SlabDev sd = slabs[si];
+    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
+    const int K = cr_level(K0, l).K;
+    const C* W = work + sd.work_off + (l & 1) * work_len;
+    C* Wn = work + sd.work_off + ((l + 1) & 1) * work_len;
+    C* F = fac + sd.fac_off;
+    const int e = 2 * t;
+    const bool hasL = e >= 1, hasR = e + 1 < K;
+    const C* Ae = W + (long long)e * bs;
+    const C* Ce = W + ((long long)K0 + 2LL * e) * bs;
+    const C* Be = Ce + bs;
+    const C* DCm = W + (3LL * K0 + 2LL * (t - 1)) * bs;   // odd row e-1
+    const C* DCp = W + (3LL * K0 + 2LL * t) * bs;         // odd row e+1
+    C* An = Wn + (long long)t * bs;
+    const bool next_cb = l + 1 < nlev;                     // level l+1 has more than one row
+    C* Cn = Wn + ((long long)K0 + 2LL * t) * bs;
+    C* Bn = Cn + bs;
+    C* Cf = nullptr;
+    if (next_cb && (t & 1) == 0) Cf = F + (cr_level(K0, l + 1).cbe + 2LL * (t >> 1)) * bs;
+    C* L0 = reinterpret_cast<C*>(sme) + (size_t)warp * 2 * 32 * LS;
+    C* L1 = L0 + 32 * LS;
+    for (int x = lane; x < w * w; x += 32) {
+        const int p = x % w, a = x / w;
+        L0[p * LS + a] = Ce[(long long)a * ldw + p];
+        L1[p * LS + a] = Be[(long long)a * ldw + p];
+    }
+    __syncwarp();
+    const int q = lane;
+    if (q >= w && q < ldw) {   // padding columns of the produced blocks
+        for (int p = 0; p < ldw; ++p) {
+            An[(long long)q * ldw + p] = czero<C>();
+            if (next_cb) {
+                Cn[(long long)q * ldw + p] = czero<C>();
+                Bn[(long long)q * ldw + p] = czero<C>();
+                if (Cf) {
+                    Cf[(long long)q * ldw + p] = czero<C>();
+                    Cf[bs + (long long)q * ldw + p] = czero<C>();
+                }
+            }
+        }
+    }
+    if (q < w) {
+        C R[32];
+        auto load_col = [&](const C* blk) {
+#pragma unroll
+            for (int a = 0; a < 32; ++a) R[a] = a < w ? blk[(long long)q * ldw + a] : czero<C>();
+        };
+        auto dot = [&](const C* Lrow) {   // row p of (L R) for the staged left factor L
+            C acc = czero<C>();
+#pragma unroll
+            for (int a = 0; a < 32; ++a)
+                if (a < w) acc = cfma(Lrow[a], R[a], acc);
+            return acc;
+        };
+        C* Acol = An + (long long)q * ldw;
+        for (int p = 0; p < ldw; ++p) Acol[p] = p < w ? Ae[(long long)q * ldw + p] : czero<C>();
+        if (hasL) {
+            load_col(DCm + bs);   // D^{-1}B of row e-1
+            for (int p = 0; p < w; ++p) Acol[p] = Acol[p] - dot(L0 + p * LS);
+        }
+        if (hasR) {
+            load_col(DCp);        // D^{-1}C of row e+1
+            for (int p = 0; p < w; ++p) Acol[p] = Acol[p] - dot(L1 + p * LS);
+        }
+        if (next_cb) {
+            C* Ccol = Cn + (long long)q * ldw;
+            C* Bcol = Bn + (long long)q * ldw;
+            if (hasL) {
+                load_col(DCm);    // D^{-1}C of row e-1
+                for (int p = 0; p < w; ++p) { const C v = dot(L0 + p * LS); Ccol[p] = mk(-v.x, -v.y); }
+            } else {
+                for (int p = 0; p < w; ++p) Ccol[p] = czero<C>();
+            }
+            if (hasR) {
+                load_col(DCp + bs);   // D^{-1}B of row e+1
+                for (int p = 0; p < w; ++p) { const C v = dot(L1 + p * LS); Bcol[p] = mk(-v.x, -v.y); }
+            } else {
+                for (int p = 0; p < w; ++p) Bcol[p] = czero<C>();
+            }
+            for (int p = w; p < ldw; ++p) { Ccol[p] = czero<C>(); Bcol[p] = czero<C>(); }
+            if (Cf) {
+                for (int p = 0; p < ldw; ++p) {
+                    Cf[(long long)q * ldw + p] = Ccol[p];
+                    Cf[bs + (long long)q * ldw + p] = Bcol[p];
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- slab solves
+// One kernel for the four uses of T~_i:
+//   CR_A    sweep, first pass: a_i = T~_i f_i, first and last layers kept;
+//   CR_E    sweep, second pass: T~_i (f_i - H lambda_{i-1} - H phi_{i+1}) on D_i;
+//   CR_TEST T~_i applied to given vectors (lss_apply_slab);
+//   CR_IF   interface maps: T~_i H e_j for a chunk of columns j.
+// A CTA solves nc right-hand sides of one slab.  The right-hand sides live in
+// shared memory (or per-CTA global scratch when they do not fit), row k of
+// column c at b + (k * nc + c) * ldw.  The factors stream through a ring of
+// shared-memory stages in the order the solve reads them, one TMA bulk copy
+// (two for the finest backward level) per chunk of block rows; thread 0 issues
+// the copies, every thread waits on the stage's mbarrier (bounded) and the
+// block-wide barrier after each chunk frees its stage.  Lanes are grouped by G
+// (16 when the slab is at most 16 layers wide, else 32): lane p of a group owns
+// layer p of one block row.
+enum CrMode { CR_A = 0, CR_E = 1, CR_TEST = 2, CR_IF = 3 };
+enum CrPhase { PH_FODD = 0, PH_FEVEN = 1, PH_TOP = 2, PH_BODD = 3, PH_B0 = 4 };
+
+template <typename C>
+struct CrArgs {
+    const SlabDev* slabs;
+    int n_slabs, n_tot, n, b, R;
+    const C* fac;
+    const C* coef;
+    const C* f;              // sweep: R x n_tot^2 sparsified right-hand side, x2 index slowest
+    C* a_first;              // CR_A outputs, [slab][k][R]
+    C* a_last;
+    const C* lam;            // CR_E inputs, [slab][k][R]
+    const C* phi;
+    double2* y;              // CR_E output, R x n^2
+    int slab;                // CR_TEST
+    const double2* v_in;     // R x (layers of D_i) x n_tot
+    double2* w_out;
+    C* iface;                // CR_IF output: Lambda, Gamma, Phi, each n_slabs x n_tot^2
+    int nitems;              // CR_IF work items
+    int row_cap;             // CR_IF: complex entries available per block row of b (all columns)
+    C* bg;                   // right-hand sides in global memory when bsm == 0
+    long long bstride;       // entries of b per CTA
+    int bsm;
+    int nst, stage_ent;      // ring stages and complex entries per stage
+    int* err;
+};
+
+// Per-level data of the solve: offsets, and for the forward pass the ranges of
+// odd rows [olo, ohi) and even rows [elo, ehi) (as r with j = 2r+1, e = 2r)
+// that can be non-zero.
+struct CrLv {
+    int K, olo, ohi, elo, ehi;
+    long long dinv, cbe, dcdb;
+};
+
+// acc (+/-)= sum_{a < G} M(p, a) x[a]: M a zero-padded G x G column-major block
+// in shared memory, x one block row of one right-hand side.  Fully unrolled
+// with two partial sums, so the loads issue ahead of the FMA chains.
+template <typename C, int G, bool SUB>
+__device__ __forceinline__ C mv_row(const C* M, int p, const C* x, C acc) {
+    C acc2 = czero<C>();
+#pragma unroll
+    for (int a = 0; a < G; a += 2) {
+        const C m0 = M[a * G + p], m1 = M[(a + 1) * G + p];
+        const C x0 = x[a], x1 = x[a + 1];
+        if (SUB) {
+            acc = cfnma(m0, x0, acc);
+            acc2 = cfnma(m1, x1, acc2);
+        } else {
+            acc = cfma(m0, x0, acc);
+            acc2 = cfma(m1, x1, acc2);
+        }
+    }
+    return acc + acc2;
+}
+
+// Level-0 off-diagonal block from its bands (band[(da + 1) * G + p] couples
+// layer p to layer p + da, zero outside the slab): acc (+/-)= sum_da band x[p + da].
+template <typename C, int G, bool SUB>
+__device__ __forceinline__ C band_row(const C* band, int p, const C* x, C acc) {
+#pragma unroll
+    for (int da = -1; da <= 1; ++da) {
+        const int a = p + da;
+        if (a < 0 || a >= G) continue;
+        const C cv = band[(da + 1) * G + p];
+        acc = SUB ? cfnma(cv, x[a], acc) : cfma(cv, x[a], acc);
+    }
+    return acc;
+}
+
+// Walks the chunks of one solve: phases FODD(l), FEVEN(l) for l = 0..L-1, TOP,
+// BODD(l) for l = L-1..1, B0; each phase's rows in chunks of at most rpc rows.
+struct ChunkIter {
+    int ph, r;   // phase index, next row
+};
+
+template <typename C, int MODE, int NC, int G>
+__device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, int i, int r, int side, int col0,
+                                        int nc, C* b, C* tb, C* ring, uint64_t* full, unsigned& gch,
+                                        const CrLv* lv, int L, bool& ok) {
+    const int K = A.n_tot, w = sd.w, ldw = sd.ldw, bs = sd.bs, na = sd.na, lw = sd.ldw;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    constexpr int GPW = 32 / G;
+    const int grp = lane / G, p = lane % G;
+    const int ngroups = nw * GPW;
+    const C* F = A.fac + sd.fac_off;
+    const C* cf = A.coef + sd.coef_off;
+    const long long t0off = cr_t0_off(K, bs), p0off = cr_p0_off(K, bs, ldw);
+    const int rowl = nc * lw;   // entries per block row of b
+    C* tg = tb + (size_t)(warp * GPW + grp) * G;
+    auto row = [&](int k) { return b + (long long)k * rowl; };
+    const long long nt2 = (long long)K * K;
+    constexpr bool kPart = MODE == CR_A || MODE == CR_IF;
+    const int nph = 3 * L + 1;
+    const int maxrows = 2 * ngroups;
+
+    // ---- phase geometry
+    auto phase = [&](int ph, int& kind, int& l, int& ra, int& rb) {
+        if (ph < 2 * L) {
+            l = ph >> 1;
+            kind = (ph & 1) ? PH_FEVEN : PH_FODD;
+            ra = kind == PH_FODD ? lv[l].olo : lv[l].elo;
+            rb = kind == PH_FODD ? lv[l].ohi : lv[l].ehi;
+        } else if (ph == 2 * L) {
+            kind = PH_TOP; l = L; ra = 0; rb = 1;
+        } else if (ph < 3 * L) {
+            kind = PH_BODD; l = 3 * L - ph; ra = 0; rb = lv[l].K >> 1;
+        } else {
+            kind = PH_B0; l = 0; ra = 0; rb = K >> 1;
+        }
+    };
+    auto row_ent = [&](int kind, int l) -> int {
+        switch (kind) {
+            case PH_FODD: return bs;
+            case PH_FEVEN: return l == 0 ? 6 * ldw : 2 * bs;
+            case PH_TOP: return bs;
+            case PH_BODD: return 2 * bs;
+            default: return 6 * ldw + (kPart ? 2 * ldw : bs);
+        }
+    };
+    // next chunk of the walk: false when done
+    auto next = [&](ChunkIter& it, int& kind, int& l, int& r0, int& r1) -> bool {
+        while (it.ph < nph) {
+            int ra, rb;
+            phase(it.ph, kind, l, ra, rb);
+            if (it.r < ra) it.r = ra;
+            if (it.r < rb) {
+                const int rpc = max(1, min(maxrows, A.stage_ent / row_ent(kind, l)));
+                r0 = it.r;
+                r1 = min(rb, r0 + rpc);
+                it.r = r1;
+                return true;
+            }
+            ++it.ph;
+            it.r = 0;
+        }
+        return false;
+    };
+    auto issue = [&](int kind, int l, int r0, int r1, C* dst, uint64_t* bar) {
+        const int nr = r1 - r0;
+        const C* src;
+        long long ent;
+        const C* src2 = nullptr;
+        long long ent2 = 0;
+        switch (kind) {
+            case PH_FODD: src = F + (lv[l].dinv + r0) * bs; ent = (long long)nr * bs; break;
+            case PH_FEVEN:
+                if (l == 0) { src = F + t0off + (long long)r0 * 6 * ldw; ent = (long long)nr * 6 * ldw; }
+                else { src = F + (lv[l].cbe + 2LL * r0) * bs; ent = 2LL * nr * bs; }
+                break;
+            case PH_TOP: src = F + lv[L].dinv * bs; ent = bs; break;
+            case PH_BODD: src = F + (lv[l].dcdb + 2LL * r0) * bs; ent = 2LL * nr * bs; break;
+            default:
+                src = F + t0off + ((long long)(K + 1) / 2 + r0) * 6 * ldw;
+                ent = (long long)nr * 6 * ldw;
+                if (kPart) { src2 = F + p0off + 2LL * r0 * ldw; ent2 = 2LL * nr * ldw; }
+                else { src2 = F + (lv[0].dinv + r0) * bs; ent2 = (long long)nr * bs; }
+        }
+        mbar_expect_tx(bar, (unsigned)((ent + ent2) * sizeof(C)));
+        tma_load_1d(dst, src, (unsigned)(ent * sizeof(C)), bar);
+        if (ent2) tma_load_1d(dst + ent, src2, (unsigned)(ent2 * sizeof(C)), bar);
+    };
+
+    // ---- first chunks in flight while the right-hand sides are written
+    ChunkIter pit{0, 0}, cit{0, 0};
+    const unsigned g0 = gch;
+    if (tid == 0)
+        for (int s = 0; s < A.nst; ++s) {
+            int kind, l, r0, r1;
+            if (!next(pit, kind, l, r0, r1)) break;
+            issue(kind, l, r0, r1, ring + (size_t)((g0 + s) % A.nst) * A.stage_ent, &full[(g0 + s) % A.nst]);
+        }
+
+    // ---- right-hand sides
+    const int total = K * rowl;
+    for (int e = tid; e < total; e += nth) {
+        const int pp = e % lw;
+        const int kc = e / lw;
+        const int c = kc % nc, k = kc / nc;
+        C v = czero<C>();
+        if (pp < w) {
+            if (MODE == CR_A || MODE == CR_E) {
+                if (pp >= na) v = A.f[(long long)r * nt2 + (long long)k * K + sd.s + A.b + (pp - na)];
+                if (MODE == CR_E) {
+                    const C* ck = cf + (long long)k * sd.cstride + pp * 9;
+                    const long long vec = (long long)K * A.R;
+                    if (pp == na && i > 0)
+                        for (int dk = -1; dk <= 1; ++dk) {
+                            const int kk = k + dk;
+                            if (kk >= 0 && kk < K)
+                                v = cfnma(ck[dk + 1], A.lam[(long long)(i - 1) * vec + (long long)kk * A.R + r], v);
+                        }
+                    if (pp == w - 1 && i < A.n_slabs - 1)
+                        for (int dk = -1; dk <= 1; ++dk) {
+                            const int kk = k + dk;
+                            if (kk >= 0 && kk < K)
+                                v = cfnma(ck[6 + dk + 1], A.phi[(long long)(i + 1) * vec + (long long)kk * A.R + r], v);
+                        }
+                }
+            } else if (MODE == CR_TEST) {
+                if (pp >= na) v = to_c<C>(A.v_in[((long long)r * sd.nl + (pp - na)) * K + k]);
+            } else {
+                const int pin = side == 0 ? na : w - 1;
+                const int dk = col0 + c - k;
+                if (pp == pin && dk >= -1 && dk <= 1)
+                    v = cf[(long long)k * sd.cstride + pin * 9 + (side == 0 ? 0 : 6) + dk + 1];
+            }
+        }
+        b[e] = v;
+    }
+
+    // ---- the chunk walk
+    int kind, l, r0, r1;
+    while (next(cit, kind, l, r0, r1)) {
+        const unsigned g = gch++;
+        const int st = g % A.nst;
+        if (!mbar_wait(&full[st], (g / A.nst) & 1, A.err)) ok = false;
+        if (!__syncthreads_and(ok)) { ok = false; return; }
+        const C* S = ring + (size_t)st * A.stage_ent;
+        const int cnt = r1 - r0;
+        const int ntask = cnt * nc;   // (row, column) pairs, one per group
+        const int Kl = lv[l].K;
+        for (int t0 = warp * GPW; t0 < ntask; t0 += nw * GPW) {
+            const int tk = t0 + grp;
+            const bool on = tk < ntask;
+            const int t = on ? tk / nc : 0, c = on ? tk % nc : 0;
+            const int rr = r0 + t;
+            if (kind == PH_FODD || kind == PH_TOP) {
+                // y_o = D_o^{-1} b_o (top: x_0 = D^{-1} b_0); the group reads its whole row first
+                const int k = kind == PH_TOP ? 0 : (2 * rr + 1) << l;
+                C* x = row(k) + c * lw;
+                C acc = czero<C>();
+                if (on) acc = mv_row<C, G, false>(S + (size_t)t * bs, p, x, acc);
+                __syncwarp();
+                if (on) x[p] = acc;
+                __syncwarp();
+            } else if (kind == PH_FEVEN) {
+                // b_e -= C_e y_{e-1} + B_e y_{e+1}
+                if (!on) continue;
+                const int e = 2 * rr, k = e << l;
+                C* x = row(k) + c * lw;
+                C acc = x[p];
+                if (l == 0) {
+                    const C* band = S + (size_t)t * 6 * G;
+                    if (e >= 1) acc = band_row<C, G, true>(band, p, row(k - 1) + c * lw, acc);
+                    if (e + 1 < Kl) acc = band_row<C, G, true>(band + 3 * G, p, row(k + 1) + c * lw, acc);
+                } else {
+                    const C* Cm = S + (size_t)2 * t * bs;
+                    if (e >= 1) acc = mv_row<C, G, true>(Cm, p, row((e - 1) << l) + c * lw, acc);
+                    if (e + 1 < Kl) acc = mv_row<C, G, true>(Cm + bs, p, row((e + 1) << l) + c * lw, acc);
+                }
+                x[p] = acc;
+            } else if (kind == PH_BODD) {
+                // x_o = y_o - D^{-1}C x_{o-1} - D^{-1}B x_{o+1}
+                if (!on) continue;
+                const int j = 2 * rr + 1, k = j << l;
+                C* x = row(k) + c * lw;
+                const C* DC = S + (size_t)2 * t * bs;
+                C acc = mv_row<C, G, true>(DC, p, row((j - 1) << l) + c * lw, x[p]);
+                if (j + 1 < Kl) acc = mv_row<C, G, true>(DC + bs, p, row((j + 1) << l) + c * lw, acc);
+                x[p] = acc;
+            } else {
+                // level 0: x_o = y_o - D_o^{-1} (C_o x_{o-1} + B_o x_{o+1})
+                const int k = 2 * rr + 1;
+                const C* band = S + (size_t)t * 6 * G;
+                C tv = czero<C>();
+                if (on) {
+                    tv = band_row<C, G, false>(band, p, row(k - 1) + c * lw, tv);
+                    if (k + 1 < Kl) tv = band_row<C, G, false>(band + 3 * G, p, row(k + 1) + c * lw, tv);
+                }
+                const C* Dp = S + (size_t)cnt * 6 * G;
+                C* x = row(k) + c * lw;
+                if (!kPart) {
+                    if (on) tg[p] = tv;
+                    __syncwarp();
+                    if (on) x[p] = mv_row<C, G, true>(Dp + (size_t)t * bs, p, tg, x[p]);
+                    __syncwarp();
+                } else {
+                    // only layers na and w-1: the two rows of D^{-1} against t, reduced over the group
+                    const C* pr = Dp + (size_t)t * 2 * G;
+                    C d0 = czero<C>(), d1 = czero<C>();
+                    if (on) {
+                        d0 = pr[p] * tv;
+                        d1 = pr[G + p] * tv;
+                    }
+#pragma unroll
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
+                        d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
+                        d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
+                        d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
+                    }
+                    if (on && p == na) x[na] = x[na] - d0;
+                    if (on && p == w - 1 && w - 1 != na) x[w - 1] = x[w - 1] - d1;
+                }
+            }
+        }
+        __syncthreads();   // the stage is free, the phase's rows are written
+        if (tid == 0) {
+            int k2, l2, q0, q1;
+            if (next(pit, k2, l2, q0, q1)) {
+                const unsigned gn = g + A.nst;
+                issue(k2, l2, q0, q1, ring + (size_t)(gn % A.nst) * A.stage_ent, &full[gn % A.nst]);
+            }
+        }
+    }
+
+    // ---- outputs
+    if (MODE == CR_A) {
+        const long long base = (long long)i * K * A.R + r;
+        for (int k = tid; k < K; k += nth) {
+            A.a_first[base + (long long)k * A.R] = row(k)[na];
+            A.a_last[base + (long long)k * A.R] = row(k)[w - 1];
+        }
+    } else if (MODE == CR_E) {
+        const int nl = sd.nl;
+        for (int e = tid; e < nl * K; e += nth) {
+            const int k = e % K, pp = na + e / K;
+            const int x1 = sd.s + (pp - na), i2 = k - A.b;
+            if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
+                A.y[(long long)r * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(row(k)[pp]);
+        }
+    } else if (MODE == CR_TEST) {
+        const int nl = sd.nl;
+        for (int e = tid; e < nl * K; e += nth) {
+            const int k = e % K, pp = na + e / K;
+            A.w_out[((long long)r * nl + (pp - na)) * K + k] = to_d(row(k)[pp]);
+        }
+    } else {
+        const int ns = A.n_slabs;
+        for (int e = tid; e < K * nc; e += nth) {
+            const int c = e % nc, k = e / nc;
+            const long long o = (long long)k * K + col0 + c;
+            const C* rk = row(k) + c * lw;
+            if (side == 0) {
+                A.iface[(0LL * ns + i) * nt2 + o] = rk[w - 1];
+                A.iface[(1LL * ns + i) * nt2 + o] = rk[na];
+            } else {
+                A.iface[(2LL * ns + i) * nt2 + o] = rk[na];
+            }
+        }
+    }
+}
+
+// Columns of one interface-map work item for a slab whose block rows have ldw
+// entries, given row_cap entries per block row of b.
+__host__ __device__ inline int cr_if_cols(int NC, int row_cap, int ldw) {
+    return std::min(NC, std::max(1, row_cap / ldw));
+}
+
+template <typename T, int MODE, int NC>
+__global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A) {
+    using C = cx<T>;
+    __shared__ CrLv lv[33];
+    __shared__ int s_L, s_item[4];
+    __shared__ short s_ldw[MODE == CR_IF ? kMaxIfSlabs : 1];
+    __shared__ __align__(8) uint64_t full[4];
+    extern __shared__ __align__(128) unsigned char sms[];
+    const int K = A.n_tot;
+    C* b = A.bsm ? reinterpret_cast<C*>(sms) : nullptr;
+    C* tb = reinterpret_cast<C*>(sms) + (A.bsm ? A.bstride : 0);
+    C* ring = tb + (size_t)kSolveThreads;
+    if (threadIdx.x == 0) {
+        const int L = cr_levels(K);
+        int lo = 0, hi = K - 1;
+        for (int l = 0; l <= L; ++l) {
+            const CrLevelOffs o = cr_level(K, l);
+            CrLv v;
+            v.K = o.K; v.dinv = o.dinv; v.cbe = o.cbe; v.dcdb = o.dcdb;
+            v.olo = v.ohi = v.elo = v.ehi = 0;
+            if (l < L) {
+                const int j0 = lo | 1, j1 = min(hi, o.K - 1);
+                if (j0 <= j1) { v.olo = j0 >> 1; v.ohi = (j1 >> 1) + ((j1 & 1) ? 1 : 0); }
+                int e0 = max(0, lo - 1);
+                e0 += e0 & 1;
+                const int e1 = min(o.K - 1, hi + 1);
+                if (e0 <= e1) { v.elo = e0 >> 1; v.ehi = (e1 >> 1) + 1; lo = e0 >> 1; hi = e1 >> 1; }
+                else { lo = 1; hi = 0; }
+            }
+            lv[l] = v;
+        }
+        s_L = L;
+        for (int s = 0; s < A.nst; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    bool ok = true;
+    unsigned gch = 0;
+    if (MODE != CR_IF) {
+        __syncthreads();
+        int i, r;
+        long long cta;
+        if (MODE == CR_TEST) { i = A.slab; r = blockIdx.x; cta = blockIdx.x; }
+        else { i = blockIdx.x; r = blockIdx.y; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
+        const SlabDev sd = A.slabs[i];
+        if (!A.bsm) b = A.bg + cta * A.bstride;
+        if (sd.w <= 16) cr_body<C, MODE, 1, 16>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, gch, lv, s_L, ok);
+        else cr_body<C, MODE, 1, 32>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, gch, lv, s_L, ok);
+    } else {
+        if (!A.bsm) b = A.bg + (long long)blockIdx.x * A.bstride;
+        const bool ldw_sm = A.n_slabs <= kMaxIfSlabs;
+        if (ldw_sm)
+            for (int ii = threadIdx.x; ii < A.n_slabs; ii += blockDim.x) s_ldw[ii] = (short)A.slabs[ii].ldw;
+        for (int item = blockIdx.x; item < A.nitems && ok; item += gridDim.x) {
+            __syncthreads();   // the previous item is finished with b and s_item
+            if (threadIdx.x == 0) {
+                // items: side 0 for slabs 1..l-1, then side 1 for slabs 1..l-2; each
+                // slab's n_tot columns in chunks of cr_if_cols columns
+                int t = item, side = -1, i = 0, col0 = 0, nc = 0;
+                for (int s2 = 0; s2 < 2 && side < 0; ++s2) {
+                    const int iend = s2 == 0 ? A.n_slabs - 1 : A.n_slabs - 2;
+                    for (int ii = 1; ii <= iend; ++ii) {
+                        const int ncs = cr_if_cols(NC, A.row_cap, ldw_sm ? (int)s_ldw[ii] : A.slabs[ii].ldw);
+                        const int nch = (K + ncs - 1) / ncs;
+                        if (t < nch) {
+                            side = s2; i = ii; col0 = t * ncs; nc = min(ncs, K - col0);
+                            break;
+                        }
+                        t -= nch;
+                    }
+                }
+                s_item[0] = side; s_item[1] = i; s_item[2] = col0; s_item[3] = nc;
+            }
+            __syncthreads();
+            const int side = s_item[0], i = s_item[1], col0 = s_item[2], nc = s_item[3];
+            if (side < 0) break;
+            const SlabDev sd = A.slabs[i];
+            // the sparse forward ranges depend on the item's columns
+            if (threadIdx.x == 0) {
+                int lo = max(0, col0 - 1), hi = min(K - 1, col0 + nc);
+                for (int l = 0; l < s_L; ++l) {
+                    const int Kl = lv[l].K;
+                    const int j0 = lo | 1, j1 = min(hi, Kl - 1);
+                    lv[l].olo = lv[l].ohi = 0;
+                    if (j0 <= j1) { lv[l].olo = j0 >> 1; lv[l].ohi = (j1 >> 1) + ((j1 & 1) ? 1 : 0); }
+                    int e0 = max(0, lo - 1);
+                    e0 += e0 & 1;
+                    const int e1 = min(Kl - 1, hi + 1);
+                    lv[l].elo = lv[l].ehi = 0;
+                    if (e0 <= e1) { lv[l].elo = e0 >> 1; lv[l].ehi = (e1 >> 1) + 1; lo = e0 >> 1; hi = e1 >> 1; }
+                    else { lo = 1; hi = 0; }
+                }
+            }
+            __syncthreads();
+            if (sd.w <= 16) cr_body<C, CR_IF, NC, 16>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, gch, lv, s_L, ok);
+            else cr_body<C, CR_IF, NC, 32>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, gch, lv, s_L, ok);
+        }
+    }
+    if (!ok && threadIdx.x == 0) {
+        // a wait expired: give the copies already issued a bounded chance to land
+        const long long t0 = clock64();
+        while (clock64() - t0 < 2000000ll) __nanosleep(1000);
     }
 }
 
@@ -752,21 +851,19 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
     }
 }
 
-// Interface recurrences inside one thread-block cluster.  Each CTA owns a
-// block of rows of the n_tot x n_tot maps and keeps the current vector
-// (lambda_{i-1} or phi_{i+1}) replicated in its shared memory; new entries are
-// stored into every CTA's copy through distributed shared memory, and the
-// cluster barrier closes each step.  Each warp owns at most RW (row, rhs)
-// tasks and holds their matrix rows for the next step in registers (CW
-// entries per lane), loaded before the barrier so the load latency overlaps
-// it.  mu_i (not on the chain) is computed for all slabs in one parallel phase
-// between the two chains.
+// One interface recurrence inside one thread-block cluster:
+//   forward  (lambda): out_i = base_i - M_i out_{i-1},  i = 1..l-2, out_0 = init;
+//   backward (phi):    out_i = base_i - M_i out_{i+1},  i = l-2..1, out_{l-1} = init.
+// Each CTA owns a block of rows of the n_tot x n_tot maps and keeps the current
+// vector replicated in its shared memory; new entries are stored into every
+// CTA's copy through distributed shared memory, and the cluster barrier closes
+// each step.  Each warp owns at most RW (row, rhs) tasks and holds their next
+// matrix rows (CW entries per lane) and base values in registers, loaded before
+// the barrier so their latency overlaps it.
 template <typename T, int RW, int CW, int NT>
-__global__ void __launch_bounds__(NT) recur_cluster_kernel(int n_slabs, int n_tot, int R,
-                                                           const cx<T>* __restrict__ iface,
-                                                           const cx<T>* __restrict__ a_first,
-                                                           const cx<T>* __restrict__ a_last, cx<T>* lam,
-                                                           cx<T>* phi) {
+__global__ void __launch_bounds__(NT) recur_chain_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ maps,
+                                                         const cx<T>* base, const cx<T>* __restrict__ init,
+                                                         cx<T>* out, int backward) {
     using C = cx<T>;
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -779,89 +876,105 @@ __global__ void __launch_bounds__(NT) recur_cluster_kernel(int n_slabs, int n_to
     const int r0 = min(n_tot, cr * rows_per), r1 = min(n_tot, r0 + rows_per);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int ntask = (r1 - r0) * R;
+    const int nsteps = n_slabs - 2;
+    const int i0 = backward ? n_slabs - 2 : 1, di = backward ? -1 : 1;
     C Mr[RW][CW];
+    C bv[RW];
 
-    auto load_rows = [&](const C* M) {
+    auto prefetch = [&](int i) {
+        const C* M = maps + (long long)i * nt2;
 #pragma unroll
         for (int t = 0; t < RW; ++t) {
             const int task = warp + t * nw;
-            const int row = r0 + (task < ntask ? task / R : 0);
+            const bool on = task < ntask;
+            const int row = r0 + (on ? task / R : 0), rr = on ? task % R : 0;
 #pragma unroll
             for (int cc = 0; cc < CW; ++cc) {
                 const int j = lane + 32 * cc;
-                Mr[t][cc] = (task < ntask && j < n_tot) ? M[(long long)row * n_tot + j] : czero<C>();
+                Mr[t][cc] = (on && j < n_tot) ? M[(long long)row * n_tot + j] : czero<C>();
             }
+            bv[t] = on ? base[(long long)i * vec + (long long)row * R + rr] : czero<C>();
         }
     };
-    auto step = [&](const C* base_vec, long long out_off, C* gout, int cur) {
+
+    // out_{i0 - di} = init, replicated into every CTA's vector
+    const long long o0 = (long long)(i0 - di) * vec;
+    for (long long e = threadIdx.x; e < vec; e += blockDim.x) vb[e] = init[e];
+    if (out + o0 != init)
+        for (long long e = (long long)r0 * R + threadIdx.x; e < (long long)r1 * R; e += blockDim.x) out[o0 + e] = init[e];
+    if (nsteps >= 1) prefetch(i0);
+    cl.sync();   // every CTA of the cluster is running before remote stores
+    int cur = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        const int i = i0 + s * di;
+        C acc[RW];
 #pragma unroll
         for (int t = 0; t < RW; ++t) {
             const int task = warp + t * nw;
-            if (task >= ntask) break;
-            const int row = r0 + task / R, rr = task % R;
+            const int rr = task < ntask ? task % R : 0;
             const C* x = vb + cur * vec + rr;
-            C acc = czero<C>();
+            C a = czero<C>();
 #pragma unroll
             for (int cc = 0; cc < CW; ++cc) {
                 const int j = lane + 32 * cc;
-                if (j < n_tot) acc = cfma(Mr[t][cc], x[(long long)j * R], acc);
+                if (j < n_tot) a = cfma(Mr[t][cc], x[(long long)j * R], a);
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            acc[t] = a;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int t = 0; t < RW; ++t) {
+                acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, off);
+                acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, off);
             }
-            if (lane < CL) {
-                const long long e = (long long)row * R + rr;
-                const C val = base_vec[out_off + e] - acc;
-                if (lane == 0) gout[out_off + e] = val;
+#pragma unroll
+        for (int t = 0; t < RW; ++t) {
+            const int task = warp + t * nw;
+            if (task < ntask && lane < CL) {
+                const long long e = (long long)(r0 + task / R) * R + task % R;
+                const C val = bv[t] - acc[t];
+                if (lane == 0) out[(long long)i * vec + e] = val;
                 C* dst = cl.map_shared_rank(vb, lane);
                 dst[(cur ^ 1) * vec + e] = val;
             }
         }
-    };
+        if (s + 1 < nsteps) prefetch(i + di);
+        cl.sync();
+        cur ^= 1;
+    }
+}
 
-    for (long long e = threadIdx.x; e < vec; e += blockDim.x) vb[e] = a_last[e];
-    for (long long e = (long long)r0 * R + threadIdx.x; e < (long long)r1 * R; e += blockDim.x) lam[e] = a_last[e];
-    if (n_slabs - 2 >= 1) load_rows(iface + (0LL * n_slabs + 1) * nt2);
-    __syncthreads();
-    int cur = 0;
-    // lambda chain: lambda_i = last(a_i) - Lambda_i lambda_{i-1}
-    for (int i = 1; i <= n_slabs - 2; ++i) {
-        step(a_last, (long long)i * vec, lam, cur);
-        if (i + 1 <= n_slabs - 2) load_rows(iface + (0LL * n_slabs + i + 1) * nt2);
-        cl.sync();
-        cur ^= 1;
+// mu_i = first(a_i) - Gamma_i lambda_{i-1} for i = 1..l-1, all independent:
+// one warp per (slab, row, rhs) dot product over the whole GPU.
+template <typename T>
+__global__ void __launch_bounds__(256) recur_mu_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ gam,
+                                                       const cx<T>* __restrict__ a_first,
+                                                       const cx<T>* __restrict__ lam, cx<T>* __restrict__ phi) {
+    using C = cx<T>;
+    const long long nt2 = (long long)n_tot * n_tot;
+    const long long vec = (long long)n_tot * R;
+    const long long task = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (task >= (long long)(n_slabs - 1) * vec) return;
+    const int i = 1 + (int)(task / vec);
+    const long long rem = task % vec;
+    const int row = (int)(rem / R), rr = (int)(rem % R);
+    const C* lp = lam + (long long)(i - 1) * vec + rr;
+    const C* Mrow = gam + (long long)i * nt2 + (long long)row * n_tot;
+    C acc = czero<C>(), acc2 = czero<C>();
+    int j = lane;
+    for (; j + 32 < n_tot; j += 64) {
+        acc = cfma(Mrow[j], lp[(long long)j * R], acc);
+        acc2 = cfma(Mrow[j + 32], lp[(long long)(j + 32) * R], acc2);
     }
-    // mu_i = first(a_i) - Gamma_i lambda_{i-1} for every slab, in parallel
-    {
-        const long long total = (long long)(n_slabs - 1) * vec;
-        for (long long t = (long long)cr * nw + warp; t < total; t += (long long)CL * nw) {
-            const int i = 1 + (int)(t / vec);
-            const long long rem = t % vec;
-            const int row = (int)(rem / R), rr = (int)(rem % R);
-            const C* lp = (i == 1 ? a_last : lam + (long long)(i - 1) * vec) + rr;
-            const C* Mrow = iface + (1LL * n_slabs + i) * nt2 + (long long)row * n_tot;
-            C acc = czero<C>();
-#pragma unroll 4
-            for (int j = lane; j < n_tot; j += 32) acc = cfma(Mrow[j], lp[(long long)j * R], acc);
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-            }
-            if (lane == 0) phi[(long long)i * vec + rem] = a_first[(long long)i * vec + rem] - acc;
-        }
+    if (j < n_tot) acc = cfma(Mrow[j], lp[(long long)j * R], acc);
+    acc = acc + acc2;
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
     }
-    if (n_slabs - 2 >= 1) load_rows(iface + (2LL * n_slabs + n_slabs - 2) * nt2);
-    cl.sync();
-    // phi chain: phi_{l-1} = mu_{l-1}, phi_i = mu_i - Phi_i phi_{i+1}
-    for (long long e = threadIdx.x; e < vec; e += blockDim.x) vb[cur * vec + e] = phi[(long long)(n_slabs - 1) * vec + e];
-    __syncthreads();
-    for (int i = n_slabs - 2; i >= 1; --i) {
-        step(phi, (long long)i * vec, phi, cur);
-        if (i - 1 >= 1) load_rows(iface + (2LL * n_slabs + i - 1) * nt2);
-        cl.sync();
-        cur ^= 1;
-    }
+    if (lane == 0) phi[(long long)i * vec + rem] = a_first[(long long)i * vec + rem] - acc;
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -870,15 +983,16 @@ int wmax_of(const lss_ctx* c) {
     for (const auto& s : c->slabs) w = std::max(w, s.w);
     return w;
 }
-int rmax_of(const lss_ctx* c) {
-    int r = 0;
-    for (const auto& s : c->slabs) r = std::max(r, s.rsz);
-    return r;
+int ldwmax_of(const lss_ctx* c) {
+    int w = 0;
+    for (const auto& s : c->slabs) w = std::max(w, s.ldw);
+    return w;
 }
-int nlmax_of(const lss_ctx* c) {
-    int r = 0;
-    for (const auto& s : c->slabs) r = std::max(r, s.nl);
-    return r;
+// Largest chunk row of any slab's factor stream, in complex entries.
+long long max_row_ent(const lss_ctx* c) {
+    long long m = 0;
+    for (const auto& s : c->slabs) m = std::max<long long>(m, std::max<long long>(2LL * s.bs, 6LL * s.ldw + s.bs));
+    return m;
 }
 
 template <typename F>
@@ -891,81 +1005,179 @@ int set_smem(lss_ctx* c, F kern, size_t sh, size_t* configured) {
     return LSS_OK;
 }
 
-int rhs_per_cta(int R) { return R >= 8 ? 8 : R; }
+template <typename C>
+CrArgs<C> base_args(lss_ctx* c) {
+    CrArgs<C> A{};
+    A.slabs = c->d_slabs;
+    A.n_slabs = c->n_slabs;
+    A.n_tot = c->n_tot;
+    A.n = c->n;
+    A.b = c->b;
+    A.R = 1;
+    A.fac = (const C*)c->fac;
+    A.coef = (const C*)c->coef;
+    A.err = c->d_err;
+    return A;
+}
+
+// Shared-memory plan of a solve launch: right-hand sides (bb bytes, in shared
+// memory when they fit), per-group scratch (tb bytes) and the factor ring.
+struct SolvePlan {
+    int bsm, nst, stage_ent;
+    size_t sh;
+};
+template <typename C>
+bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, SolvePlan* P) {
+    const size_t min_stage = sizeof(C) * (size_t)max_row_ent(c);
+    const size_t want = std::max<size_t>(48 * 1024, min_stage);
+    for (int bsm = allow_smem_b ? 1 : 0; bsm >= 0; --bsm) {
+        const size_t fixed = tb + (bsm ? bb : 0);
+        if (fixed + 2 * min_stage > kSmemBudget) continue;
+        const size_t avail = kSmemBudget - fixed;
+        int nst = (int)std::min<size_t>(4, avail / want);
+        size_t stage = want;
+        if (nst < 2) {
+            nst = 2;
+            stage = (avail / 2) / 16 * 16;
+        }
+        P->bsm = bsm;
+        P->nst = nst;
+        P->stage_ent = (int)(stage / sizeof(C)) & ~1;
+        P->sh = fixed + (size_t)nst * P->stage_ent * sizeof(C);
+        return true;
+    }
+    return false;
+}
+
+// Launches the slab-solve kernel with per_cta complex entries of right-hand
+// sides per CTA: in shared memory when they fit (and no fixed scratch is
+// given), else in global scratch (the fixed array `scratch`, or the context's
+// growable buffer).  items > 0 makes the grid persistent: as many CTAs as fit
+// on the GPU at once, at most items.
+template <typename T, int MODE, int NC>
+int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, int items, void* scratch,
+                 size_t scratch_bytes, cudaStream_t s) {
+    using C = cx<T>;
+    auto kern = cr_solve_kernel<T, MODE, NC>;
+    const size_t tb = sizeof(C) * (size_t)kSolveThreads;
+    const size_t bb = sizeof(C) * (size_t)per_cta;
+    SolvePlan P;
+    if (!plan_solve<C>(c, bb, tb, scratch == nullptr, &P))
+        return lss_fail(c, LSS_ERR_UNSUPPORTED, "slab solve: the factor stream does not fit in shared memory");
+    A.bstride = per_cta;
+    A.bsm = P.bsm;
+    A.nst = P.nst;
+    A.stage_ent = P.stage_ent;
+    static size_t cfg = 0;
+    int rc = set_smem(c, kern, P.sh, &cfg);
+    if (rc) return rc;
+    if (items > 0) {
+        static size_t occ_sh = 0;
+        static int occ = 0;
+        if (occ_sh != P.sh || !occ) {
+            int per = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSolveThreads, P.sh);
+            if (e) return lss_check_cuda(c, e, "slab solve occupancy");
+            occ = std::max(1, per);
+            occ_sh = P.sh;
+        }
+        grid = dim3((unsigned)std::min<long long>(items, (long long)occ * c->num_sms));
+    }
+    if (!A.bsm) {
+        const size_t need = bb * (size_t)grid.x * grid.y;
+        if (scratch) {
+            if (need > scratch_bytes)
+                return lss_fail(c, LSS_ERR_UNSUPPORTED,
+                                "apply_slab_noalloc: needs " + std::to_string(need) +
+                                    " bytes of scratch, the fixed scratch holds " + std::to_string(scratch_bytes) +
+                                    " (use fewer right-hand sides per call)");
+            A.bg = (C*)scratch;
+        } else {
+            rc = lss_grow(c, &c->z_buf, &c->z_cap, need);
+            if (rc) return rc;
+            A.bg = (C*)c->z_buf;
+        }
+    }
+    kern<<<grid, kSolveThreads, P.sh, s>>>(A);
+    return lss_check_cuda(c, cudaGetLastError(), "slab solve launch");
+}
+
+// Interface maps with NC columns per item; *used = false when b does not fit
+// in shared memory at this NC (the caller tries a smaller one).
+template <typename T, int NC>
+int launch_iface(lss_ctx* c, cudaStream_t s, bool* used) {
+    using C = cx<T>;
+    const int K = c->n_tot;
+    const int row_cap = std::max(NC * 16, ldwmax_of(c));
+    SolvePlan P;
+    *used = NC == 1 || (plan_solve<C>(c, sizeof(C) * (size_t)K * row_cap, sizeof(C) * (size_t)kSolveThreads, true,
+                                      &P) && P.bsm);
+    if (!*used) return LSS_OK;
+    int nitems = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int iend = side == 0 ? c->n_slabs - 1 : c->n_slabs - 2;
+        for (int i = 1; i <= iend; ++i) {
+            const int ncs = cr_if_cols(NC, row_cap, c->slabs[i].ldw);
+            nitems += (K + ncs - 1) / ncs;
+        }
+    }
+    CrArgs<C> A = base_args<C>(c);
+    A.iface = (C*)c->iface;
+    A.nitems = nitems;
+    A.row_cap = row_cap;
+    ProfScope ps(c, s, LSS_PROF_IFACE, 1);
+    return launch_solve<T, CR_IF, NC>(c, A, dim3(1), (long long)K * row_cap, nitems, nullptr, 0, s);
+}
 
 template <typename T>
 int factor_impl(lss_ctx* c, cudaStream_t s) {
     using C = cx<T>;
-    constexpr int NR = sizeof(T) == 8 ? 4 : 8;
-    const int w = wmax_of(c);
-    const size_t sh = sizeof(C) * (size_t)(64 + 32 + 32) * 65;
-    static size_t cfg_f = 0;
-    int rc = set_smem(c, factor_kernel<T, NR>, sh, &cfg_f);
+    const int K0 = c->n_tot, ns = c->n_slabs, nlev = cr_levels(K0);
+    const int wmax = wmax_of(c);
+    C* fac = (C*)c->fac;
+    C* work = (C*)c->cr_work;
+    const int rs = 4 * wmax + 1;
+    const size_t shg = sizeof(C) * (size_t)kGjWarps * 32 * rs;
+    const size_t she = sizeof(C) * (size_t)kEvWarps * 2 * 32 * 33;
+    static size_t cfg_g = 0, cfg_e = 0;
+    int rc = set_smem(c, cr_gj_kernel<T>, shg, &cfg_g);
+    if (!rc) rc = set_smem(c, cr_even_kernel<T>, she, &cfg_e);
     if (rc) return rc;
     {
-        ProfScope ps(c, s, LSS_PROF_FACTOR, 1);
-        factor_kernel<T, NR><<<c->n_slabs, 64 * NR, sh, s>>>(c->d_slabs, (const C*)c->coef, (C*)c->fac, c->n_tot,
-                                                            c->d_err);
+        ProfScope ps(c, s, LSS_PROF_FACTOR, 2 * nlev + 2);
+        cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
+        for (int l = 0; l < nlev; ++l) {
+            const int K = cr_level(K0, l).K;
+            const int nodd = K / 2, nev = (K + 1) / 2;
+            cr_gj_kernel<T><<<(nodd * ns + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg, s>>>(
+                c->d_slabs, fac, work, c->work_len, K0, l, nodd, ns, 0, rs, c->d_err);
+            cr_even_kernel<T><<<(nev * ns + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she, s>>>(
+                c->d_slabs, fac, work, c->work_len, K0, l, nev, ns, nlev);
+        }
+        cr_gj_kernel<T><<<(ns + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg, s>>>(c->d_slabs, fac, work, c->work_len,
+                                                                                  K0, nlev, 1, ns, 1, rs, c->d_err);
     }
     rc = lss_check_cuda(c, cudaGetLastError(), "factor launch");
-    if (rc) return rc;
-    if (c->n_slabs == 1) return LSS_OK;
-    // interface maps: persistent grid over (slab, side, column chunk) items
-    const int nch = (c->n_tot + kIfNC - 1) / kIfNC;
-    const int nitems = (c->n_slabs - 1) * nch + std::max(0, c->n_slabs - 2) * nch;
-    const int grid = std::min(nitems, 2 * c->num_sms);
-    const long long zstride = (long long)c->n_tot * w * kIfNC;
-    rc = lss_grow(c, &c->z_buf, &c->z_cap, (size_t)zstride * sizeof(C) * grid);
-    if (rc) return rc;
-    const int rmax = (rmax_of(c) + 1) & ~1;
-    const size_t shi = sizeof(C) * ((size_t)kIfStages * rmax + 2 * 32 * (size_t)kIfNC);
-    static size_t cfg_i = 0;
-    rc = set_smem(c, iface_kernel<T>, shi, &cfg_i);
-    if (rc) return rc;
-    ProfScope ps(c, s, LSS_PROF_IFACE, 1);
-    iface_kernel<T><<<grid, kIfThreads, shi, s>>>(c->d_slabs, c->n_slabs, c->n_tot, (const C*)c->fac, (C*)c->iface,
-                                                  (C*)c->z_buf, zstride, nitems, rmax, c->d_err);
-    return lss_check_cuda(c, cudaGetLastError(), "iface launch");
+    if (rc || ns == 1) return rc;
+    bool used = false;
+    constexpr int NCI = sizeof(T) == 8 ? 2 : 4;
+    rc = launch_iface<T, NCI>(c, s, &used);
+    if (!rc && !used) rc = launch_iface<T, NCI / 2>(c, s, &used);
+    if (!rc && !used) rc = launch_iface<T, 1>(c, s, &used);
+    return rc;
 }
 
-template <typename T, int MODE>
-int launch_sweep(lss_ctx* c, SweepArgs<cx<T>> A, cudaStream_t s) {
-    using C = cx<T>;
-    constexpr int NQ = sizeof(T) == 8 ? 4 : 1;
-    constexpr int S = sizeof(T) == 8 ? 2 : 3;
-    constexpr int RB = 4;
-    const int rmax = (rmax_of(c) + 1) & ~1, nlmax = nlmax_of(c), wmax = wmax_of(c);
-    const size_t base = sizeof(C) * ((size_t)S * RB * rmax + 3 * NQ * 32 + (size_t)c->n_tot * nlmax +
-                                     2 * (size_t)c->n_tot);
-    const size_t zb = sizeof(C) * (size_t)c->n_tot * wmax;
-    const int zsmem = (base + zb <= (size_t)220 * 1024) ? 1 : 0;
-    const size_t sh = base + (zsmem ? zb : 0);
-    if (sh > (size_t)225 * 1024) return lss_fail(c, LSS_ERR_UNSUPPORTED, "slab solve does not fit in shared memory");
-    static size_t cfg = 0;
-    int rc = set_smem(c, sweep_kernel<T, MODE, NQ, S, RB>, sh, &cfg);
-    if (rc) return rc;
-    if (!zsmem) {
-        A.zstride = (long long)c->n_tot * wmax;
-        rc = lss_grow(c, &c->z_buf, &c->z_cap, (size_t)A.zstride * sizeof(C) * c->n_slabs * A.R);
-        if (rc) return rc;
-        A.zbuf = (C*)c->z_buf;
-    }
-    ProfScope ps(c, s, MODE == SW_A ? LSS_PROF_SLAB_A : LSS_PROF_SLAB_E, 1);
-    sweep_kernel<T, MODE, NQ, S, RB><<<dim3(c->n_slabs, A.R), 32 * (NQ + 1), sh, s>>>(A, zsmem, rmax, nlmax);
-    return lss_check_cuda(c, cudaGetLastError(), "sweep launch");
-}
-
-// Cluster size for the recurrence kernel: 16 CTAs when the GPU can co-schedule
-// them (non-portable size), else 8.  Returns LSS_ERR_UNSUPPORTED when a warp
-// would own more rows than its prefetch registers hold, so the caller uses the
-// grid kernel.
+// Cluster size for the recurrence kernels: 16 CTAs when the GPU can
+// co-schedule them (non-portable size), else 8.  Returns LSS_ERR_UNSUPPORTED
+// when a warp would own more rows than its prefetch registers hold, so the
+// caller uses the grid kernel.
 template <typename T, int RW, int CW, int NT>
-int launch_recur_cluster_cfg(lss_ctx* c, cx<T>* lam, cx<T>* phi, const cx<T>* a_first, const cx<T>* a_last, int R,
-                             cudaStream_t s) {
+int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward,
+                     int R, cudaStream_t s) {
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(cx<T>);
     static int cl_size = 0;
     static size_t configured = 0;
-    auto kern = recur_cluster_kernel<T, RW, CW, NT>;
+    auto kern = recur_chain_kernel<T, RW, CW, NT>;
     if (sh > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
@@ -1000,40 +1212,56 @@ int launch_recur_cluster_cfg(lss_ctx* c, cx<T>* lam, cx<T>* phi, const cx<T>* a_
     attr[0].val.clusterDim.x = cl_size;
     cfg.gridDim = dim3(cl_size);
     int ns = c->n_slabs, nt = c->n_tot;
-    const cx<T>* ifc = (const cx<T>*)c->iface;
-    ProfScope ps(c, s, LSS_PROF_RECUR, 1);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, ifc, a_first, a_last, lam, phi);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, maps, base, init, out, backward);
     return lss_check_cuda(c, e, "recurrence cluster launch");
 }
 
 template <typename T>
+int launch_chain(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward, int R,
+                 cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (c->n_tot <= 384) return launch_chain_cfg<T, 3, 12, 256>(c, maps, base, init, out, backward, R, s);
+        return launch_chain_cfg<T, 3, 20, 384>(c, maps, base, init, out, backward, R, s);
+    } else {
+        return launch_chain_cfg<T, 3, 9, 256>(c, maps, base, init, out, backward, R, s);
+    }
+}
+
+// lambda chain, mu for every slab, phi chain (three launches), or the
+// cooperative grid kernel when the vectors do not fit the cluster kernels.
+template <typename T>
 int launch_recur(lss_ctx* c, cx<T>* lam, cx<T>* phi, const cx<T>* a_first, const cx<T>* a_last, int R,
                  cudaStream_t s) {
     using C = cx<T>;
+    const long long nt2 = (long long)c->n_tot * c->n_tot;
+    const long long vec = (long long)c->n_tot * R;
+    const int ns = c->n_slabs;
+    const C* ifc = (const C*)c->iface;
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(C);
-    int rc = LSS_ERR_UNSUPPORTED;
     if (sh <= (size_t)160 * 1024) {
-        if constexpr (sizeof(T) == 4) {
-            if (c->n_tot <= 384) rc = launch_recur_cluster_cfg<T, 3, 12, 256>(c, lam, phi, a_first, a_last, R, s);
-            else rc = launch_recur_cluster_cfg<T, 3, 20, 384>(c, lam, phi, a_first, a_last, R, s);
-        } else {
-            rc = launch_recur_cluster_cfg<T, 3, 9, 256>(c, lam, phi, a_first, a_last, R, s);
+        ProfScope ps(c, s, LSS_PROF_RECUR, 3);
+        int rc = launch_chain<T>(c, ifc, a_last, a_last, lam, 0, R, s);
+        if (rc == LSS_OK) {
+            const long long warps = (long long)(ns - 1) * vec;
+            recur_mu_kernel<T><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(ns, c->n_tot, R, ifc + ns * nt2, a_first,
+                                                                          lam, phi);
+            rc = lss_check_cuda(c, cudaGetLastError(), "mu launch");
+            if (rc) return rc;
+            return launch_chain<T>(c, ifc + 2LL * ns * nt2, phi, phi + (long long)(ns - 1) * vec, phi, 1, R, s);
         }
+        if (rc != LSS_ERR_UNSUPPORTED) return rc;
     }
-    if (rc != LSS_ERR_UNSUPPORTED) return rc;
     static int grid = 0;
     if (!grid) {
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, recur_grid_kernel<T>, 256, 0);
         grid = std::max(1, per) * c->num_sms;
     }
-    const long long vec = (long long)c->n_tot * R;
     int nb = (int)std::min<long long>(grid, std::max<long long>(1, (2 * vec + 7) / 8));
-    int ns = c->n_slabs, nt = c->n_tot;
-    const C* ifc = (const C*)c->iface;
+    int nsl = c->n_slabs, nt = c->n_tot;
     unsigned* bar = c->d_bar;
     int* err = c->d_err;
-    void* args[] = {&ns, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
+    void* args[] = {&nsl, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
     ProfScope ps(c, s, LSS_PROF_RECUR, 1);
     cudaError_t e = cudaLaunchCooperativeKernel((void*)recur_grid_kernel<T>, dim3(nb), dim3(256), args, 0, s);
     return lss_check_cuda(c, e, "recurrence launch");
@@ -1051,14 +1279,8 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     rc = lss_sparsify(c, r, c->f_buf, R, s);
     if (rc) return rc;
     C* side = (C*)c->side_buf;
-    SweepArgs<C> A{};
-    A.slabs = c->d_slabs;
-    A.n_slabs = c->n_slabs;
-    A.n_tot = c->n_tot;
-    A.n = c->n;
-    A.b = c->b;
+    CrArgs<C> A = base_args<C>(c);
     A.R = R;
-    A.rec = (const C*)c->fac;
     A.f = (const C*)c->f_buf;
     A.a_first = side;
     A.a_last = side + c->n_slabs * vec;
@@ -1067,46 +1289,34 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     A.lam = lam;
     A.phi = phi;
     A.y = y;
-    A.err = c->d_err;
+    const long long per_cta = (long long)c->n_tot * ldwmax_of(c);
+    const dim3 grid(c->n_slabs, R);
     if (c->n_slabs > 1) {
-        rc = launch_sweep<T, SW_A>(c, A, s);
+        {
+            ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
+            rc = launch_solve<T, CR_A, 1>(c, A, grid, per_cta, 0, nullptr, 0, s);
+        }
         if (rc) return rc;
         rc = launch_recur<T>(c, lam, phi, A.a_first, A.a_last, R, s);
         if (rc) return rc;
     }
-    return launch_sweep<T, SW_E>(c, A, s);
+    ProfScope ps(c, s, LSS_PROF_SLAB_E, 1);
+    return launch_solve<T, CR_E, 1>(c, A, grid, per_cta, 0, nullptr, 0, s);
 }
 
 template <typename T>
-int slab_apply_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
+int slab_apply_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, void* scratch, size_t scratch_bytes,
+                    cudaStream_t s) {
     using C = cx<T>;
-    const int RC = rhs_per_cta(R);
-    const int ny = (R + RC - 1) / RC;
-    const long long zstride = (long long)c->n_tot * wmax_of(c) * RC;
-    int rc = lss_grow(c, &c->z_buf, &c->z_cap, (size_t)zstride * sizeof(C) * ny);
-    if (rc) return rc;
-    SolveArgs<C> A{};
-    A.slabs = c->d_slabs;
-    A.n_slabs = c->n_slabs;
-    A.n_tot = c->n_tot;
-    A.n = c->n;
-    A.b = c->b;
-    A.rec = (const C*)c->fac;
+    CrArgs<C> A = base_args<C>(c);
+    A.R = R;
+    A.slab = slab;
     A.v_in = v;
     A.w_out = w;
-    A.slab = slab;
-    A.zbuf = (C*)c->z_buf;
-    A.zstride = zstride;
-    A.R = R;
-    A.RC = RC;
-    A.err = c->d_err;
-    const size_t sh = sizeof(C) * ((size_t)kStages * ((rmax_of(c) + 1) & ~1) + 2 * (size_t)wmax_of(c) * RC);
-    static size_t cfg = 0;
-    rc = set_smem(c, solve_kernel<T>, sh, &cfg);
-    if (rc) return rc;
+    const long long per_cta = (long long)c->n_tot * ldwmax_of(c);
+    if (scratch) return launch_solve<T, CR_TEST, 1>(c, A, dim3(R), per_cta, 0, scratch, scratch_bytes, s);
     ProfScope ps(c, s, LSS_PROF_SLAB_E, 1);
-    solve_kernel<T><<<dim3(1, ny), kSolveThreads, sh, s>>>(A);
-    return lss_check_cuda(c, cudaGetLastError(), "slab solve launch");
+    return launch_solve<T, CR_TEST, 1>(c, A, dim3(R), per_cta, 0, nullptr, 0, s);
 }
 
 }  // namespace
@@ -1120,13 +1330,13 @@ int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
 }
 
 int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
-    return c->prec == LSS_FP64 ? slab_apply_impl<double>(c, slab, v, w, R, s)
-                               : slab_apply_impl<float>(c, slab, v, w, R, s);
+    return c->prec == LSS_FP64 ? slab_apply_impl<double>(c, slab, v, w, R, nullptr, 0, s)
+                               : slab_apply_impl<float>(c, slab, v, w, R, nullptr, 0, s);
 }
 
 // ---------------------------------------------------------------- fixed-scratch slab operator
 // lss_apply_slab_noalloc: the slab operator of lss_apply_slab with its
-// forward-elimination scratch in a fixed device array instead of the context's
+// right-hand-side scratch in a fixed device array instead of the context's
 // growable workspace, so that the call never reaches the device allocator.
 namespace {
 
@@ -1156,45 +1366,6 @@ int fixed_scratch(lss_ctx* c, void** out) {
     return LSS_OK;
 }
 
-template <typename T>
-int slab_apply_fixed_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
-    using C = cx<T>;
-    const int RC = rhs_per_cta(R);
-    const int ny = (R + RC - 1) / RC;
-    const long long zstride = (long long)c->n_tot * wmax_of(c) * RC;
-    const size_t need = (size_t)zstride * sizeof(C) * ny;
-    if (need > kFixedScratchBytes)
-        return lss_fail(c, LSS_ERR_UNSUPPORTED,
-                        "apply_slab_noalloc: needs " + std::to_string(need) + " bytes of scratch, the fixed scratch holds " +
-                            std::to_string(kFixedScratchBytes) + " (use fewer right-hand sides per call)");
-    void* scratch = nullptr;
-    int rc = fixed_scratch(c, &scratch);
-    if (rc) return rc;
-    // The forward pass writes every scratch entry before the backward pass reads
-    // it, so nothing has to start at zero and no clearing is needed.
-    SolveArgs<C> A{};
-    A.slabs = c->d_slabs;
-    A.n_slabs = c->n_slabs;
-    A.n_tot = c->n_tot;
-    A.n = c->n;
-    A.b = c->b;
-    A.rec = (const C*)c->fac;
-    A.v_in = v;
-    A.w_out = w;
-    A.slab = slab;
-    A.zbuf = (C*)scratch;
-    A.zstride = zstride;
-    A.R = R;
-    A.RC = RC;
-    A.err = c->d_err;
-    const size_t sh = sizeof(C) * ((size_t)kStages * ((rmax_of(c) + 1) & ~1) + 2 * (size_t)wmax_of(c) * RC);
-    cudaError_t e = cudaFuncSetAttribute(solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(sh, 48 * 1024));
-    if (e) return lss_check_cuda(c, e, "noalloc attribute");
-    solve_kernel<T><<<dim3(1, ny), kSolveThreads, sh, s>>>(A);
-    return lss_check_cuda(c, cudaGetLastError(), "noalloc launch");
-}
-
 }  // namespace
 
 extern "C" int lss_apply_slab_noalloc(lss_ctx* c, int slab, const void* v_dev, void* w_dev, int R, void* stream) {
@@ -1202,7 +1373,15 @@ extern "C" int lss_apply_slab_noalloc(lss_ctx* c, int slab, const void* v_dev, v
     if (!v_dev || !w_dev || R < 1 || slab < 0 || slab >= c->n_slabs)
         return lss_fail(c, LSS_ERR_ARG, "apply_slab_noalloc: bad arguments");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_slab_noalloc before lss_factor");
+    void* scratch = nullptr;
+    int rc = fixed_scratch(c, &scratch);
+    if (rc) return rc;
+    // Every scratch entry a CTA reads is written by that CTA first, so
+    // nothing has to start at zero and no clearing is needed.
     cudaStream_t s = (cudaStream_t)stream;
-    return c->prec == LSS_FP64 ? slab_apply_fixed_impl<double>(c, slab, (const double2*)v_dev, (double2*)w_dev, R, s)
-                               : slab_apply_fixed_impl<float>(c, slab, (const double2*)v_dev, (double2*)w_dev, R, s);
+    return c->prec == LSS_FP64
+               ? slab_apply_impl<double>(c, slab, (const double2*)v_dev, (double2*)w_dev, R, scratch,
+                                         kFixedScratchBytes, s)
+               : slab_apply_impl<float>(c, slab, (const double2*)v_dev, (double2*)w_dev, R, scratch,
+                                        kFixedScratchBytes, s);
 }
