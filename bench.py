@@ -105,30 +105,84 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- algorithmic work per kernel group
+def _levels(K0):
+    Ks, K = [], K0
+    while K > 1:
+        Ks.append(K)
+        K = (K + 1) // 2
+    return Ks
+
+
+def cr_solve_work(K0, w, part, rows=None):
+    """Complex MACs and factor entries (unpadded w x w blocks) of one cyclic-
+    reduction solve of a slab of width w: forward over the rows that can be
+    non-zero (all, or a column's neighbourhood for the interface maps), the top
+    row, back substitution with only the first and last layers kept at level 0
+    when `part`."""
+    Ks = _levels(K0)
+    w2 = w * w
+    mac = ent = 0
+    lo, hi = (0, K0 - 1) if rows is None else rows
+    for l, K in enumerate(Ks):
+        j0, j1 = lo | 1, min(hi, K - 1)
+        nodd = (j1 - j0) // 2 + 1 if j0 <= j1 else 0
+        e0 = max(0, lo - 1)
+        e0 += e0 & 1
+        e1 = min(K - 1, hi + 1)
+        nev = (e1 - e0) // 2 + 1 if e0 <= e1 else 0
+        mac += nodd * w2
+        ent += nodd * w2
+        per_even = 6 * w if l == 0 else 2 * w2
+        mac += nev * per_even
+        ent += nev * per_even
+        lo, hi = (e0 // 2, e1 // 2) if nev else (1, 0)
+    mac += w2
+    ent += w2
+    for l, K in enumerate(Ks):
+        per_odd = (6 * w + (2 * w if part else w2)) if l == 0 else 2 * w2
+        mac += (K // 2) * per_odd
+        ent += (K // 2) * per_odd
+    return mac, ent
+
+
 def algorithmic(solver, R, prec_bytes):
-    """Per-launch algorithmic bytes / flops of each kernel group (design notes)."""
+    """Per-launch algorithmic bytes / flops of each kernel group (design notes,
+    section on kernels and rooflines)."""
     n, L, nt, ns = solver.n, solver.fft_len, solver.n_tot, solver.n_slabs
     N = n * n
     ws = []
     for i in range(ns):
         _, nl, na = solver.slab_info(i)
         ws.append(na + nl)
-    ldw = [(w + 1) & ~1 for w in ws]
-    cstr = [(9 * w + 1) & ~1 for w in ws]
     cb = 2 * prec_bytes
-    slab_bytes = sum(nt * (w * l + c) * cb for w, l, c in zip(ws, ldw, cstr)) + 2 * R * nt * nt * cb
-    slab_flops = sum(2 * nt * w * w * 8 for w in ws) * R
+    a_mac = a_ent = e_mac = e_ent = 0
+    for w in ws:
+        m1, e1 = cr_solve_work(nt, w, True)
+        m2, e2 = cr_solve_work(nt, w, False)
+        a_mac, a_ent, e_mac, e_ent = a_mac + m1, a_ent + e1, e_mac + m2, e_ent + e2
+    if_mac = 0
+    cache = {}
+    for side in (0, 1):
+        for i in range(1, ns - 1 if side == 0 else ns - 2 + 1):
+            if side == 1 and i > ns - 2:
+                continue
+            w = ws[i]
+            if w not in cache:
+                cache[w] = sum(cr_solve_work(nt, w, True, (max(0, j - 1), min(nt - 1, j + 1)))[0]
+                               for j in range(nt))
+            if_mac += cache[w]
     fft_flops = R * (n * 5 * L * math.log2(L) + L * 2 * 5 * L * math.log2(L) + n * 5 * L * math.log2(L))
     mv_bytes = R * (16 * N * 2) + 8 * N + 16 * L * L
-    recur_bytes = 3 * max(ns - 1, 0) * nt * nt * cb
-    factor_flops = sum(nt * (8 * w ** 3 + 2 * 3 * 8 * w * w) for w in ws)
+    recur_bytes = (2 * max(ns - 2, 0) + max(ns - 1, 0)) * nt * nt * cb   # Lambda, Phi chains + Gamma (mu)
+    factor_flops = sum(8 * 2 * nt * (3.5 + 4.0) * w ** 3 for w in ws)
+    rhs_bytes = R * (nt * nt * cb + 16 * N)
     return {
-        "slab_a": dict(bytes=slab_bytes, flops=slab_flops, launches_per_apply=1),
-        "slab_e": dict(bytes=slab_bytes, flops=slab_flops, launches_per_apply=1),
+        "slab_a": dict(bytes=a_ent * cb + rhs_bytes, flops=8 * a_mac * R, launches_per_apply=1),
+        "slab_e": dict(bytes=e_ent * cb + rhs_bytes, flops=8 * e_mac * R, launches_per_apply=1),
+        "iface": dict(bytes=3 * ns * nt * nt * cb, flops=8 * if_mac, launches_per_apply=1),
         "matvec": dict(bytes=mv_bytes, flops=fft_flops, launches_per_apply=3),
-        "recur": dict(bytes=recur_bytes, flops=recur_bytes // cb * 8 * R, launches_per_apply=1),
-        "factor": dict(bytes=sum(nt * w * l * cb for w, l in zip(ws, ldw)), flops=factor_flops,
-                       launches_per_apply=1),
+        "recur": dict(bytes=recur_bytes * R, flops=recur_bytes // cb * 8 * R, launches_per_apply=3),
+        "factor": dict(bytes=sum(nt * 3 * w * w * cb for w in ws), flops=factor_flops, launches_per_apply=None),
     }
 
 
@@ -146,7 +200,8 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     opts = GmresOptions(30, 1e-8, 300)
     results = {}
-    for prec_name, prec in (("mixed", LSS_MIXED), ("fp64", LSS_FP64)):
+    arms = [a for a in (("mixed", LSS_MIXED), ("fp64", LSS_FP64)) if a[0] in args.arms.split(",")]
+    for prec_name, prec in arms:
         solver = LSSolver(n, w.omega, mt, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec, factor=False)
         stream = torch.cuda.current_stream()
 
@@ -195,6 +250,40 @@ def run_ours(args, rank, world):
                    prof_launches={k: v // args.steps for k, v in prof_n.items()},
                    gpu_launches=int(sum(prof_n.values())), solver=solver,
                    prec_bytes=8 if prec == LSS_FP64 else 4)
+        # solve only (the metric's lss_solve time): factors in place, right-hand side resident
+        solver.set_medium(mt)
+        solver.factor()
+        g = solver.plane_wave_rhs(dirs)
+        for _ in range(args.warmup):
+            solver.solve(g, opts)
+        solve_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.solve(g, opts)
+            e1.record(stream)
+            e1.synchronize()
+            solve_ms += e0.elapsed_time(e1)
+        setup_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.set_medium(mt)
+            solver.factor()
+            e1.record(stream)
+            e1.synchronize()
+            setup_ms += e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([solve_ms, setup_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            solve_ms, setup_ms = (float(x) for x in t.tolist())
+        res["solve_only"] = {"value": (R * args.steps * world) / (solve_ms / 1e3), "unit": "solves/s",
+                             "ms_per_solve_call": solve_ms / args.steps}
+        res["setup_factor_ms"] = setup_ms / args.steps
         # e2e: medium from pinned host memory, solution back to pinned host memory
         m_host = torch.tensor(m, dtype=torch.float64).pin_memory()
         u_host = torch.empty((R, n, n), dtype=torch.complex128).pin_memory()
@@ -226,25 +315,26 @@ def run_ours(args, rank, world):
 
 
 def roofline(res, hbm_peak, hbm_src):
+    """Roofline of the kernel group that takes the most time in the timed
+    steps: algorithmic work per launch over its CUDA-event time per launch."""
     solver = res["solver"]
     alg = algorithmic(solver, 1, res["prec_bytes"])
     cats = {k: v for k, v in res["prof_ms"].items() if k in alg}
     dom = max(cats, key=lambda k: cats[k])
     launches = max(res["prof_launches"].get(dom, 1), 1)
-    per_launch_ms = cats[dom] / launches
     a = alg[dom]
-    if dom in ("recur",):
-        achieved = a["bytes"] / (per_launch_ms / 1e3) / 1e9
+    per = a["launches_per_apply"] or launches
+    per_apply_ms = cats[dom] / max(launches // per, 1)
+    if dom in ("recur", "slab_a", "slab_e"):
+        achieved = a["bytes"] / (per_apply_ms / 1e3) / 1e9
         return dom, {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": hbm_src}
-    flops = a["flops"] if dom != "matvec" else a["flops"]
-    per = flops if dom != "matvec" else flops
-    if dom == "matvec":
-        per_launch_ms = cats[dom] / max(launches // 3, 1)
-    achieved = per / (per_launch_ms / 1e3) / 1e12
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": hbm_src,
+                     "per_launch_ms": per_apply_ms}
+    achieved = a["flops"] / (per_apply_ms / 1e3) / 1e12
     peak = FP64_PEAK_TFLOPS if (res["prec_bytes"] == 8 or dom == "matvec") else FP32_PEAK_TFLOPS
     return dom, {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": None, "peak_source": "derived (FP64 1.25 TFLOP/s nominal; FP32 from unit counts x clock)"}
+                 "traffic": None, "per_launch_ms": per_apply_ms,
+                 "peak_source": "derived: FP64 1.25 TFLOP/s nominal; FP32 = 152 SMs x 128 FMA/clk x 2 x 2.07 GHz"}
 
 
 # ---------------------------------------------------------------- oracle (CPU) arm
@@ -282,6 +372,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arms", default="mixed,fp64",
+                    help="precisions to run (mixed first; the JSON line needs both, profiling may take one)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -326,6 +418,11 @@ def main():
             torch.distributed.destroy_process_group()
         return
     hbm, src = peaks()
+    if "mixed" not in results or "fp64" not in results:
+        for name, r in results.items():
+            print(json.dumps({"arm": name, "value": r["value"], "ms_per_step": r["ms_per_step"],
+                              "breakdown_ms": r["prof_ms"], "launches_per_step": r["prof_launches"]}))
+        return
     mix, f64 = results["mixed"], results["fp64"]
     dom, roof = roofline(mix, hbm, src)
     line = {
@@ -335,8 +432,11 @@ def main():
         "config": config, "e2e": mix["e2e"], "gpu_launches": mix["gpu_launches"],
         "clocks": mix["clocks"], "roofline": dict(kernel=dom, **roof), "cpu_baseline": cpu,
         "iters": mix["iters"], "relres_true_max": mix["relres_true_max"],
+        "step": "set_medium + factor (setup) + plane-wave RHS + FGMRES solve, per medium and batch",
+        "solve_only": mix["solve_only"], "setup_factor_ms": mix["setup_factor_ms"],
         "plain_fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "iters": f64["iters"],
                        "relres_true_max": f64["relres_true_max"], "e2e": f64["e2e"],
+                       "solve_only": f64["solve_only"], "setup_factor_ms": f64["setup_factor_ms"],
                        "breakdown_ms": f64["prof_ms"], "clocks": f64["clocks"]},
         "mixed_over_fp64": mix["value"] / f64["value"],
         "breakdown_ms": mix["prof_ms"], "launches_per_step": mix["prof_launches"],

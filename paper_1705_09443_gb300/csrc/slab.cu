@@ -405,6 +405,33 @@ __device__ __forceinline__ C band_row(const C* band, int p, const C* x, C acc) {
     return acc;
 }
 
+// acc[c] (+/-)= sum_a M(p, a) x_c[a] for ncol <= CPT columns (x_c at x + c * xs):
+// the block's row is read into registers once (16 entries at a time, 8 in
+// double precision) and applied to every column.
+template <typename C, int G, int CPT, bool SUB>
+__device__ __forceinline__ void mv_cols(const C* M, int p, const C* x, int xs, int ncol, C (&acc)[CPT]) {
+    constexpr int HB = sizeof(C) == 16 ? 8 : 16;   // entries of the row held at once
+#pragma unroll
+    for (int h = 0; h < G; h += HB) {
+        C m[HB];
+#pragma unroll
+        for (int u = 0; u < HB; ++u) m[u] = M[(h + u) * G + p];
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+            if (c < ncol) {
+                const C* xc = x + c * xs + h;
+                C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+                for (int u = 0; u < HB; u += 2) {
+                    s0 = cfma(m[u], xc[u], s0);
+                    s1 = cfma(m[u + 1], xc[u + 1], s1);
+                }
+                acc[c] = SUB ? acc[c] - (s0 + s1) : acc[c] + (s0 + s1);
+            }
+        }
+    }
+}
+
 // Walks the chunks of one solve: phases FODD(l), FEVEN(l) for l = 0..L-1, TOP,
 // BODD(l) for l = L-1..1, B0; each phase's rows in chunks of at most rpc rows.
 struct ChunkIter {
@@ -413,19 +440,22 @@ struct ChunkIter {
 
 template <typename C, int MODE, int NC, int G>
 __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, int i, int r, int side, int col0,
-                                        int nc, C* b, C* tb, C* ring, uint64_t* full, unsigned& gch,
-                                        const CrLv* lv, int L, bool& ok) {
-    const int K = A.n_tot, w = sd.w, ldw = sd.ldw, bs = sd.bs, na = sd.na, lw = sd.ldw;
+                                        int nc_in, C* b, C* tb, C* ring, uint64_t* full, int4* desc,
+                                        unsigned& gch, const CrLv* lv, int L, bool& ok) {
+    const int K = A.n_tot, w = sd.w, ldw = sd.ldw, bs = sd.bs, na = sd.na;
+    constexpr int lw = G;   // ldw == G for every slab this body serves
+    const int nc = NC == 1 ? 1 : nc_in;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
     constexpr int GPW = 32 / G;
+    constexpr int CPT = NC >= 2 ? 2 : 1;   // columns per task
     const int grp = lane / G, p = lane % G;
     const int ngroups = nw * GPW;
     const C* F = A.fac + sd.fac_off;
     const C* cf = A.coef + sd.coef_off;
     const long long t0off = cr_t0_off(K, bs), p0off = cr_p0_off(K, bs, ldw);
     const int rowl = nc * lw;   // entries per block row of b
-    C* tg = tb + (size_t)(warp * GPW + grp) * G;
+    C* tg = tb + (size_t)(warp * GPW + grp) * CPT * G;
     auto row = [&](int k) { return b + (long long)k * rowl; };
     const long long nt2 = (long long)K * K;
     constexpr bool kPart = MODE == CR_A || MODE == CR_IF;
@@ -499,22 +529,43 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         if (ent2) tma_load_1d(dst + ent, src2, (unsigned)(ent2 * sizeof(C)), bar);
     };
 
-    // ---- first chunks in flight while the right-hand sides are written
-    ChunkIter pit{0, 0}, cit{0, 0};
+    // ---- first chunks in flight while the right-hand sides are written.  Only
+    // thread 0 walks the chunk sequence; it publishes each chunk's descriptor
+    // beside its stage (kind -1: no more chunks).
+    ChunkIter pit{0, 0};
     const unsigned g0 = gch;
-    if (tid == 0)
-        for (int s = 0; s < A.nst; ++s) {
-            int kind, l, r0, r1;
-            if (!next(pit, kind, l, r0, r1)) break;
-            issue(kind, l, r0, r1, ring + (size_t)((g0 + s) % A.nst) * A.stage_ent, &full[(g0 + s) % A.nst]);
+    auto issue_next = [&](unsigned g) {
+        const int st = g % A.nst;
+        int kind, l, r0, r1;
+        if (next(pit, kind, l, r0, r1)) {
+            desc[st] = make_int4(kind, l, r0, r1);
+            issue(kind, l, r0, r1, ring + (size_t)st * A.stage_ent, &full[st]);
+        } else {
+            desc[st] = make_int4(-1, 0, 0, 0);
         }
+    };
+    if (tid == 0)
+        for (int s = 0; s < A.nst; ++s) issue_next(g0 + s);
 
     // ---- right-hand sides
     const int total = K * rowl;
-    for (int e = tid; e < total; e += nth) {
+    if (MODE == CR_IF) {
+        // zeros, then the coupling coefficients H e_j: layer pin, rows j-1..j+1
+        float4* b4 = reinterpret_cast<float4*>(b);
+        const int n4 = total * (int)sizeof(C) / 16;
+        for (int e = tid; e < n4; e += nth) b4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        const int pin = side == 0 ? na : w - 1;
+        for (int e = tid; e < 3 * nc; e += nth) {
+            const int c = e / 3, k = col0 + c + e % 3 - 1;
+            if (k >= 0 && k < K)
+                b[((long long)k * nc + c) * lw + pin] =
+                    cf[(long long)k * sd.cstride + pin * 9 + (side == 0 ? 0 : 6) + (col0 + c - k) + 1];
+        }
+    } else {
+    for (int e = tid; e < total; e += nth) {   // one column: row k = e / lw
         const int pp = e % lw;
-        const int kc = e / lw;
-        const int c = kc % nc, k = kc / nc;
+        const int k = e / lw;
         C v = czero<C>();
         if (pp < w) {
             if (MODE == CR_A || MODE == CR_E) {
@@ -537,111 +588,133 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                 }
             } else if (MODE == CR_TEST) {
                 if (pp >= na) v = to_c<C>(A.v_in[((long long)r * sd.nl + (pp - na)) * K + k]);
-            } else {
-                const int pin = side == 0 ? na : w - 1;
-                const int dk = col0 + c - k;
-                if (pp == pin && dk >= -1 && dk <= 1)
-                    v = cf[(long long)k * sd.cstride + pin * 9 + (side == 0 ? 0 : 6) + dk + 1];
             }
         }
         b[e] = v;
     }
+    }
+    __syncthreads();   // b written, first descriptors published
 
     // ---- the chunk walk
-    int kind, l, r0, r1;
-    while (next(cit, kind, l, r0, r1)) {
-        const unsigned g = gch++;
+    while (true) {
+        const unsigned g = gch;
         const int st = g % A.nst;
+        const int4 dsc = desc[st];
+        if (dsc.x < 0) break;
+        ++gch;
+        const int kind = dsc.x, l = dsc.y, r0 = dsc.z, r1 = dsc.w;
         if (!mbar_wait(&full[st], (g / A.nst) & 1, A.err)) ok = false;
         if (!__syncthreads_and(ok)) { ok = false; return; }
         const C* S = ring + (size_t)st * A.stage_ent;
         const int cnt = r1 - r0;
-        const int ntask = cnt * nc;   // (row, column) pairs, one per group
+        const int ncg = (nc + CPT - 1) / CPT;   // column groups per row
+        const int ntask = cnt * ncg;            // (row, column group) pairs, one per lane group
         const int Kl = lv[l].K;
         for (int t0 = warp * GPW; t0 < ntask; t0 += nw * GPW) {
             const int tk = t0 + grp;
             const bool on = tk < ntask;
-            const int t = on ? tk / nc : 0, c = on ? tk % nc : 0;
+            const int t = on ? tk / ncg : 0, cgi = on ? tk % ncg : 0;
+            const int c0 = cgi * CPT, ncol = on ? min(CPT, nc - c0) : 0;
             const int rr = r0 + t;
+            C acc[CPT];
             if (kind == PH_FODD || kind == PH_TOP) {
-                // y_o = D_o^{-1} b_o (top: x_0 = D^{-1} b_0); the group reads its whole row first
+                // y_o = D_o^{-1} b_o (top: x_0 = D^{-1} b_0); the group reads its columns first
                 const int k = kind == PH_TOP ? 0 : (2 * rr + 1) << l;
-                C* x = row(k) + c * lw;
-                C acc = czero<C>();
-                if (on) acc = mv_row<C, G, false>(S + (size_t)t * bs, p, x, acc);
+                C* x = row(k) + c0 * lw;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) acc[c] = czero<C>();
+                if (on) mv_cols<C, G, CPT, false>(S + (size_t)t * bs, p, x, lw, ncol, acc);
                 __syncwarp();
-                if (on) x[p] = acc;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (c < ncol) x[c * lw + p] = acc[c];
                 __syncwarp();
             } else if (kind == PH_FEVEN) {
                 // b_e -= C_e y_{e-1} + B_e y_{e+1}
                 if (!on) continue;
                 const int e = 2 * rr, k = e << l;
-                C* x = row(k) + c * lw;
-                C acc = x[p];
+                C* x = row(k) + c0 * lw;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) acc[c] = c < ncol ? x[c * lw + p] : czero<C>();
                 if (l == 0) {
                     const C* band = S + (size_t)t * 6 * G;
-                    if (e >= 1) acc = band_row<C, G, true>(band, p, row(k - 1) + c * lw, acc);
-                    if (e + 1 < Kl) acc = band_row<C, G, true>(band + 3 * G, p, row(k + 1) + c * lw, acc);
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) {
+                        if (c >= ncol) continue;
+                        if (e >= 1) acc[c] = band_row<C, G, true>(band, p, row(k - 1) + (c0 + c) * lw, acc[c]);
+                        if (e + 1 < Kl) acc[c] = band_row<C, G, true>(band + 3 * G, p, row(k + 1) + (c0 + c) * lw, acc[c]);
+                    }
                 } else {
                     const C* Cm = S + (size_t)2 * t * bs;
-                    if (e >= 1) acc = mv_row<C, G, true>(Cm, p, row((e - 1) << l) + c * lw, acc);
-                    if (e + 1 < Kl) acc = mv_row<C, G, true>(Cm + bs, p, row((e + 1) << l) + c * lw, acc);
+                    if (e >= 1) mv_cols<C, G, CPT, true>(Cm, p, row((e - 1) << l) + c0 * lw, lw, ncol, acc);
+                    if (e + 1 < Kl) mv_cols<C, G, CPT, true>(Cm + bs, p, row((e + 1) << l) + c0 * lw, lw, ncol, acc);
                 }
-                x[p] = acc;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (c < ncol) x[c * lw + p] = acc[c];
             } else if (kind == PH_BODD) {
                 // x_o = y_o - D^{-1}C x_{o-1} - D^{-1}B x_{o+1}
                 if (!on) continue;
                 const int j = 2 * rr + 1, k = j << l;
-                C* x = row(k) + c * lw;
+                C* x = row(k) + c0 * lw;
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) acc[c] = c < ncol ? x[c * lw + p] : czero<C>();
                 const C* DC = S + (size_t)2 * t * bs;
-                C acc = mv_row<C, G, true>(DC, p, row((j - 1) << l) + c * lw, x[p]);
-                if (j + 1 < Kl) acc = mv_row<C, G, true>(DC + bs, p, row((j + 1) << l) + c * lw, acc);
-                x[p] = acc;
+                mv_cols<C, G, CPT, true>(DC, p, row((j - 1) << l) + c0 * lw, lw, ncol, acc);
+                if (j + 1 < Kl) mv_cols<C, G, CPT, true>(DC + bs, p, row((j + 1) << l) + c0 * lw, lw, ncol, acc);
+#pragma unroll
+                for (int c = 0; c < CPT; ++c)
+                    if (c < ncol) x[c * lw + p] = acc[c];
             } else {
                 // level 0: x_o = y_o - D_o^{-1} (C_o x_{o-1} + B_o x_{o+1})
                 const int k = 2 * rr + 1;
                 const C* band = S + (size_t)t * 6 * G;
-                C tv = czero<C>();
-                if (on) {
-                    tv = band_row<C, G, false>(band, p, row(k - 1) + c * lw, tv);
-                    if (k + 1 < Kl) tv = band_row<C, G, false>(band + 3 * G, p, row(k + 1) + c * lw, tv);
+                C tv[CPT];
+#pragma unroll
+                for (int c = 0; c < CPT; ++c) {
+                    tv[c] = czero<C>();
+                    if (c < ncol) {
+                        tv[c] = band_row<C, G, false>(band, p, row(k - 1) + (c0 + c) * lw, tv[c]);
+                        if (k + 1 < Kl) tv[c] = band_row<C, G, false>(band + 3 * G, p, row(k + 1) + (c0 + c) * lw, tv[c]);
+                    }
                 }
                 const C* Dp = S + (size_t)cnt * 6 * G;
-                C* x = row(k) + c * lw;
+                C* x = row(k) + c0 * lw;
                 if (!kPart) {
-                    if (on) tg[p] = tv;
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) tg[c * G + p] = tv[c];
                     __syncwarp();
-                    if (on) x[p] = mv_row<C, G, true>(Dp + (size_t)t * bs, p, tg, x[p]);
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c) acc[c] = c < ncol ? x[c * lw + p] : czero<C>();
+                    if (on) mv_cols<C, G, CPT, true>(Dp + (size_t)t * bs, p, tg, G, ncol, acc);
+#pragma unroll
+                    for (int c = 0; c < CPT; ++c)
+                        if (c < ncol) x[c * lw + p] = acc[c];
                     __syncwarp();
                 } else {
                     // only layers na and w-1: the two rows of D^{-1} against t, reduced over the group
                     const C* pr = Dp + (size_t)t * 2 * G;
-                    C d0 = czero<C>(), d1 = czero<C>();
-                    if (on) {
-                        d0 = pr[p] * tv;
-                        d1 = pr[G + p] * tv;
-                    }
+                    const C q0 = on ? pr[p] : czero<C>(), q1 = on ? pr[G + p] : czero<C>();
 #pragma unroll
-                    for (int off = G / 2; off > 0; off >>= 1) {
-                        d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
-                        d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
-                        d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
-                        d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
+                    for (int c = 0; c < CPT; ++c) {
+                        C d0 = q0 * tv[c], d1 = q1 * tv[c];
+#pragma unroll
+                        for (int off = G / 2; off > 0; off >>= 1) {
+                            d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
+                            d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
+                            d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
+                            d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
+                        }
+                        if (c < ncol && p == na) x[c * lw + na] = x[c * lw + na] - d0;
+                        if (c < ncol && p == w - 1 && w - 1 != na) x[c * lw + w - 1] = x[c * lw + w - 1] - d1;
                     }
-                    if (on && p == na) x[na] = x[na] - d0;
-                    if (on && p == w - 1 && w - 1 != na) x[w - 1] = x[w - 1] - d1;
                 }
             }
         }
         __syncthreads();   // the stage is free, the phase's rows are written
-        if (tid == 0) {
-            int k2, l2, q0, q1;
-            if (next(pit, k2, l2, q0, q1)) {
-                const unsigned gn = g + A.nst;
-                issue(k2, l2, q0, q1, ring + (size_t)(gn % A.nst) * A.stage_ent, &full[gn % A.nst]);
-            }
-        }
+        if (tid == 0) issue_next(g + A.nst);
     }
+    __syncthreads();   // the last descriptors are read before the next item rewrites them
 
     // ---- outputs
     if (MODE == CR_A) {
@@ -693,11 +766,12 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
     __shared__ int s_L, s_item[4];
     __shared__ short s_ldw[MODE == CR_IF ? kMaxIfSlabs : 1];
     __shared__ __align__(8) uint64_t full[4];
+    __shared__ int4 desc[4];
     extern __shared__ __align__(128) unsigned char sms[];
     const int K = A.n_tot;
     C* b = A.bsm ? reinterpret_cast<C*>(sms) : nullptr;
     C* tb = reinterpret_cast<C*>(sms) + (A.bsm ? A.bstride : 0);
-    C* ring = tb + (size_t)kSolveThreads;
+    C* ring = tb + (size_t)kSolveThreads * (NC >= 2 ? 2 : 1);
     if (threadIdx.x == 0) {
         const int L = cr_levels(K);
         int lo = 0, hi = K - 1;
@@ -731,8 +805,8 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
         else { i = blockIdx.x; r = blockIdx.y; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
         const SlabDev sd = A.slabs[i];
         if (!A.bsm) b = A.bg + cta * A.bstride;
-        if (sd.w <= 16) cr_body<C, MODE, 1, 16>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, gch, lv, s_L, ok);
-        else cr_body<C, MODE, 1, 32>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, gch, lv, s_L, ok);
+        if (sd.w <= 16) cr_body<C, MODE, 1, 16>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, desc, gch, lv, s_L, ok);
+        else cr_body<C, MODE, 1, 32>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, desc, gch, lv, s_L, ok);
     } else {
         if (!A.bsm) b = A.bg + (long long)blockIdx.x * A.bstride;
         const bool ldw_sm = A.n_slabs <= kMaxIfSlabs;
@@ -779,8 +853,8 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
                 }
             }
             __syncthreads();
-            if (sd.w <= 16) cr_body<C, CR_IF, NC, 16>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, gch, lv, s_L, ok);
-            else cr_body<C, CR_IF, NC, 32>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, gch, lv, s_L, ok);
+            if (sd.w <= 16) cr_body<C, CR_IF, NC, 16>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, desc, gch, lv, s_L, ok);
+            else cr_body<C, CR_IF, NC, 32>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, desc, gch, lv, s_L, ok);
         }
     }
     if (!ok && threadIdx.x == 0) {
@@ -1059,7 +1133,7 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, int 
                  size_t scratch_bytes, cudaStream_t s) {
     using C = cx<T>;
     auto kern = cr_solve_kernel<T, MODE, NC>;
-    const size_t tb = sizeof(C) * (size_t)kSolveThreads;
+    const size_t tb = sizeof(C) * (size_t)kSolveThreads * (NC >= 2 ? 2 : 1);
     const size_t bb = sizeof(C) * (size_t)per_cta;
     SolvePlan P;
     if (!plan_solve<C>(c, bb, tb, scratch == nullptr, &P))
@@ -1110,8 +1184,8 @@ int launch_iface(lss_ctx* c, cudaStream_t s, bool* used) {
     const int K = c->n_tot;
     const int row_cap = std::max(NC * 16, ldwmax_of(c));
     SolvePlan P;
-    *used = NC == 1 || (plan_solve<C>(c, sizeof(C) * (size_t)K * row_cap, sizeof(C) * (size_t)kSolveThreads, true,
-                                      &P) && P.bsm);
+    *used = NC == 1 || (plan_solve<C>(c, sizeof(C) * (size_t)K * row_cap,
+                                      sizeof(C) * (size_t)kSolveThreads * (NC >= 2 ? 2 : 1), true, &P) && P.bsm);
     if (!*used) return LSS_OK;
     int nitems = 0;
     for (int side = 0; side < 2; ++side) {
