@@ -137,8 +137,14 @@ int lss_apply_A(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose
 /*
  * lss_apply_P - y = P x, the preconditioner of Sec. 2.2-2.4 (Algorithm 2):
  * f = Q x (alpha rows on I^h, Eq. Huf), the forward/backward moving-PML sweep
- * with the slab factors, restriction to I.  transpose = 1 is reserved
- * (LSS_ERR_UNSUPPORTED).  Requires lss_factor.  x_dev, y_dev: R x n^d c128.
+ * with the slab factors, restriction to I.  transpose = 1 applies the bilinear
+ * transpose P^T = Q^T Sweep^T E^T: embedding of x on the grid, the sweep with
+ * the transposed slab solves in reverse order (forward pass
+ * w_i = v_i - H_{[i-1,i]}^T last(T~_{i-1}^T w_{i-1}), backward pass
+ * x_i = T~_i^T (w_i - H_{[i+1,i]}^T first(x_{i+1}))), then Q^T (conj(alpha)
+ * rows transposed).  The first transposed call after lss_factor also builds
+ * the transposed sweep's interface maps.  Requires lss_factor.
+ * x_dev, y_dev: R x n^d c128.
  */
 int lss_apply_P(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose,
                 void *stream);
@@ -154,6 +160,30 @@ int lss_apply_P(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose
  */
 int lss_solve(lss_ctx *c, const void *g_dev, void *u_dev, int R, const lss_gmres *o,
               lss_stats *stats, void *stream);
+
+/*
+ * lss_adjoint_solve - solve A^T mu = rhs, A^T = I + omega^2 M K (the bilinear
+ * transpose of Eq. LS_d_c; K is symmetric), for R right-hand sides with
+ * flexible GMRES right-preconditioned by P^T (lss_apply_P, transpose = 1),
+ * same options, statistics and errors as lss_solve.  For a real misfit L(u) of
+ * a solution u of lss_solve, rhs = conj(dL/du) (dL/du = dL/dRe u + i dL/dIm u)
+ * gives mu with dL/dm = Re((-omega^2 K mu) . (u + u_I)) (lss_medium_gradient).
+ *   rhs_dev, mu_dev  device, R x n^d complex128
+ */
+int lss_adjoint_solve(lss_ctx *c, const void *rhs_dev, void *mu_dev, int R, const lss_gmres *o,
+                      lss_stats *stats, void *stream);
+
+/*
+ * lss_medium_gradient - grad = sum_r Re((-omega^2 K mu_r) . (u_r + u_I,r)) on
+ * I: the derivative of a real misfit with respect to m, from the adjoint
+ * states mu (lss_adjoint_solve) and the scattered fields u of the plane waves
+ * with directions dirs (u_I = exp(i omega d.p), Eq. LS_d).
+ *   mu_dev, u_dev  device, R x n^d complex128
+ *   dirs_host      host, R x 2 unit directions
+ *   grad_dev       device, n^d float64 (output)
+ */
+int lss_medium_gradient(lss_ctx *c, const void *mu_dev, const void *u_dev, const double *dirs_host,
+                        int R, double *grad_dev, void *stream);
 
 /*
  * lss_solve_host - the same solve with host buffers: copies g_host to the

@@ -5,3 +5,4 @@ Liu & Ying, arXiv:1705.09443.  The compute path is the CUDA library liblss.so
 """
 from ._lib import LSS_FP64, LSS_MIXED, LssError, load  # noqa: F401
 from .solver import LSSolver, GmresOptions  # noqa: F401
+from .autograd import LSSolve, ls_solve  # noqa: F401

@@ -100,7 +100,12 @@ void dots(Krylov& K, const double2* V, long long vstride, int J, const double2* 
 }  // namespace
 
 int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
-               cudaStream_t s) {
+               cudaStream_t s, int transpose) {
+    // transpose: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T
+    const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
+    auto precond = [&](const double2* x, double2* y) {
+        return transpose ? lss_sweep_t(c, x, y, R, s) : lss_sweep(c, x, y, R, s);
+    };
     const long long N = (long long)c->n * c->n;
     const int m = o->restart;
     const double tol = o->tol;
@@ -174,8 +179,8 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         for (; j < m && total < maxit; ++j) {
             double2* Vj = V + (size_t)j * RN;
             double2* Zj = Z + (size_t)j * RN;
-            if ((rc = lss_sweep(c, Vj, Zj, R, s))) return rc;
-            if ((rc = lss_matvec(c, Zj, w, R, MV_IN_MU, MV_OUT_A, nullptr, nullptr, s))) return rc;
+            if ((rc = precond(Vj, Zj))) return rc;
+            if ((rc = lss_matvec(c, Zj, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
             dots(K, V, RN, j + 1, w, K.hdev, 0);
             { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, s>>>(V, RN, K.hdev, j + 1, w, N, R, -1.0); }
             dots(K, V, RN, j + 1, w, K.h2dev, 0);
@@ -250,14 +255,14 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         for (int r = 0; r < R; ++r) all_done &= (bool)done[r];
         if (all_done || total >= maxit) break;
         // restart: r = g - A u
-        if ((rc = lss_matvec(c, u, w, R, MV_IN_MU, MV_OUT_A, nullptr, nullptr, s))) return rc;
+        if ((rc = lss_matvec(c, u, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
         { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs, 256, 0, s>>>(g, w, rv, RN); }
         dots(K, rv, 0, 1, rv, K.hdev, 0);
         if ((rc = fetch(K.hdev, R))) return rc;
         for (int r = 0; r < R; ++r) beta[r] = std::sqrt(std::max(0.0, hh[r].x));
     }
     // true residual
-    if ((rc = lss_matvec(c, u, w, R, MV_IN_MU, MV_OUT_A, nullptr, nullptr, s))) return rc;
+    if ((rc = lss_matvec(c, u, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
     { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs, 256, 0, s>>>(g, w, rv, RN); }
     dots(K, rv, 0, 1, rv, K.hdev, 0);
     if ((rc = fetch(K.hdev, R))) return rc;

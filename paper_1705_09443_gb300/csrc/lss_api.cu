@@ -23,8 +23,9 @@ void free_ctx(lss_ctx* c) {
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
-                    c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->d_slabs, c->d_err, c->d_bar,
-                    c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf, c->io_buf, c->dir_buf};
+                    c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->iface_t, c->d_slabs,
+                    c->d_err, c->d_bar, c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf,
+                    c->io_buf, c->dir_buf, c->gr_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -319,7 +320,7 @@ int lss_apply_P(lss_ctx* c, const void* x, void* y, int R, int transpose, void* 
     if (!c) return LSS_ERR_ARG;
     if (!x || !y || R < 1) return lss_fail(c, LSS_ERR_ARG, "apply_P: bad arguments");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_P before lss_factor");
-    if (transpose) return lss_fail(c, LSS_ERR_UNSUPPORTED, "transposed preconditioner not built");
+    if (transpose) return lss_sweep_t(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
     return lss_sweep(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
 }
 
@@ -330,6 +331,34 @@ int lss_solve(lss_ctx* c, const void* g, void* u, int R, const lss_gmres* o, lss
         return lss_fail(c, LSS_ERR_ARG, "solve: bad GMRES options");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "solve before lss_factor");
     return lss_fgmres(c, (const double2*)g, (double2*)u, R, o, stats, (cudaStream_t)stream);
+}
+
+int lss_adjoint_solve(lss_ctx* c, const void* rhs, void* mu, int R, const lss_gmres* o, lss_stats* stats,
+                      void* stream) {
+    if (!c) return LSS_ERR_ARG;
+    if (!rhs || !mu || !o || R < 1 || rhs == mu) return lss_fail(c, LSS_ERR_ARG, "adjoint_solve: bad arguments");
+    if (o->restart < 1 || o->restart > 200 || !(o->tol > 0) || o->max_iter < 1)
+        return lss_fail(c, LSS_ERR_ARG, "adjoint_solve: bad GMRES options");
+    if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "adjoint_solve before lss_factor");
+    return lss_fgmres(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
+}
+
+int lss_medium_gradient(lss_ctx* c, const void* mu, const void* u, const double* dirs_host, int R, double* grad,
+                        void* stream) {
+    if (!c) return LSS_ERR_ARG;
+    if (!mu || !u || !dirs_host || !grad || R < 1) return lss_fail(c, LSS_ERR_ARG, "medium_gradient: bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)R * c->n * c->n * sizeof(double2);
+    int rc = lss_grow(c, &c->gr_buf, &c->gr_cap, bytes);
+    if (!rc) rc = lss_grow(c, &c->dir_buf, &c->dir_cap, (size_t)R * 2 * sizeof(double));
+    if (rc) return rc;
+    rc = lss_check_cuda(c, cudaMemcpyAsync(c->dir_buf, dirs_host, (size_t)R * 2 * sizeof(double),
+                                           cudaMemcpyHostToDevice, s), "directions");
+    if (rc) return rc;
+    // -omega^2 K mu, then the pointwise product with the total field
+    rc = lss_matvec(c, (const double2*)mu, (double2*)c->gr_buf, R, MV_IN_U, MV_OUT_NEG, nullptr, nullptr, s);
+    if (rc) return rc;
+    return lss_gradient_m(c, (const double2*)c->gr_buf, (const double2*)u, (const double*)c->dir_buf, grad, R, s);
 }
 
 int lss_solve_host(lss_ctx* c, const void* g_host, void* u_host, int R, const lss_gmres* o, lss_stats* stats,

@@ -95,6 +95,10 @@ LSS_HD inline long long cr_nblocks(int K0) {
 LSS_HD inline long long cr_fac_entries(int K0, int bs, int ldw) {
     return cr_nblocks(K0) * bs + 6LL * ldw * K0 + 2LL * ldw * (K0 / 2);
 }
+// Entry offsets (from a slab's factor base) of level 0's bands and of level
+// 0's D^{-1} rows na and w-1.
+LSS_HD inline long long cr_t0_off(int K0, int bs) { return cr_nblocks(K0) * bs; }
+LSS_HD inline long long cr_p0_off(int K0, int bs, int ldw) { return cr_t0_off(K0, bs) + 6LL * ldw * K0; }
 // Factorization work blocks per slab and parity: A (K_0), C and B (2 K_0) of
 // every row, D^{-1}C and D^{-1}B of the odd rows (2 (K_0 / 2)).
 LSS_HD inline long long cr_work_blocks(int K0) { return 4LL * K0; }
@@ -127,6 +131,8 @@ struct lss_ctx {
     void* fac = nullptr;          // cyclic-reduction factors of every slab (working precision)
     void* cr_work = nullptr;      // factorization work blocks, two parities (levels alternate)
     void* iface = nullptr;        // interface maps Lambda, Gamma, Phi: 3 x n_slabs x n_tot^2
+    void* iface_t = nullptr;      // maps of the transposed sweep (built on the first adjoint use)
+    bool iface_t_valid = false;
     SlabDev* d_slabs = nullptr;
     int* d_err = nullptr;
     unsigned* d_bar = nullptr;    // grid barrier words
@@ -141,6 +147,7 @@ struct lss_ctx {
     long long work_len = 0;       // complex entries of one level work buffer
     void* io_buf = nullptr; size_t io_cap = 0;         // host-buffer solve staging
     void* dir_buf = nullptr; size_t dir_cap = 0;       // plane-wave directions
+    void* gr_buf = nullptr; size_t gr_cap = 0;         // -omega^2 K mu for the medium gradient
     int num_sms = 0;
 
     // profiling: event pairs per kernel group, launch counters
@@ -193,8 +200,18 @@ int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s);
 int lss_factor_slabs(lss_ctx* c, cudaStream_t s);
 int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s);
 int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s);
+// the three interface recurrences with the maps at `maps` (Lambda, Gamma, Phi blocks)
+int lss_recurrences(lss_ctx* c, const void* maps, void* lam, void* phi, const void* a_first, const void* a_last,
+                    int R, cudaStream_t s);
+
+// adjoint.cu: the transposed preconditioner P^T = Q^T Sweep^T E^T
+int lss_sweep_t(lss_ctx* c, const double2* y, double2* r, int R, cudaStream_t s);
+// gradient of a data misfit with respect to m from adjoint states mu (stencil.cu)
+int lss_gradient_m(lss_ctx* c, const double2* Kmu, const double2* u, const double* dirs_dev, double* grad, int R,
+                   cudaStream_t s);
+int lss_sparsify_t(lss_ctx* c, const void* X, double2* r, int R, cudaStream_t s);
 
 // krylov.cu: FGMRES
 int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s);
 int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
-               cudaStream_t s);
+               cudaStream_t s, int transpose = 0);

@@ -63,9 +63,6 @@ __device__ __forceinline__ float2 cfnma(float2 a, float2 b, float2 acc) {
     return acc;
 }
 
-// Entry offsets of a slab's level-0 bands and level-0 D^{-1} rows.
-__host__ __device__ inline long long cr_t0_off(int K0, int bs) { return cr_nblocks(K0) * bs; }
-__host__ __device__ inline long long cr_p0_off(int K0, int bs, int ldw) { return cr_t0_off(K0, bs) + 6LL * ldw * K0; }
 
 // ---------------------------------------------------------------- factorization
 // Level 0's blocks from the stencil rows of the coefficient table (row p of
@@ -1304,13 +1301,12 @@ int launch_chain(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* 
 // lambda chain, mu for every slab, phi chain (three launches), or the
 // cooperative grid kernel when the vectors do not fit the cluster kernels.
 template <typename T>
-int launch_recur(lss_ctx* c, cx<T>* lam, cx<T>* phi, const cx<T>* a_first, const cx<T>* a_last, int R,
-                 cudaStream_t s) {
+int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<T>* a_first, const cx<T>* a_last,
+                 int R, cudaStream_t s) {
     using C = cx<T>;
     const long long nt2 = (long long)c->n_tot * c->n_tot;
     const long long vec = (long long)c->n_tot * R;
     const int ns = c->n_slabs;
-    const C* ifc = (const C*)c->iface;
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(C);
     if (sh <= (size_t)160 * 1024) {
         ProfScope ps(c, s, LSS_PROF_RECUR, 3);
@@ -1371,7 +1367,7 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
             rc = launch_solve<T, CR_A, 1>(c, A, grid, per_cta, 0, nullptr, 0, s);
         }
         if (rc) return rc;
-        rc = launch_recur<T>(c, lam, phi, A.a_first, A.a_last, R, s);
+        rc = launch_recur<T>(c, (const C*)c->iface, lam, phi, A.a_first, A.a_last, R, s);
         if (rc) return rc;
     }
     ProfScope ps(c, s, LSS_PROF_SLAB_E, 1);
@@ -1396,7 +1392,17 @@ int slab_apply_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, v
 }  // namespace
 
 int lss_factor_slabs(lss_ctx* c, cudaStream_t s) {
+    c->iface_t_valid = false;
     return c->prec == LSS_FP64 ? factor_impl<double>(c, s) : factor_impl<float>(c, s);
+}
+
+int lss_recurrences(lss_ctx* c, const void* maps, void* lam, void* phi, const void* a_first, const void* a_last,
+                    int R, cudaStream_t s) {
+    if (c->prec == LSS_FP64)
+        return launch_recur<double>(c, (const double2*)maps, (double2*)lam, (double2*)phi, (const double2*)a_first,
+                                    (const double2*)a_last, R, s);
+    return launch_recur<float>(c, (const float2*)maps, (float2*)lam, (float2*)phi, (const float2*)a_first,
+                               (const float2*)a_last, R, s);
 }
 
 int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {

@@ -225,6 +225,46 @@ __global__ void sparsify_kernel(const double2* __restrict__ r, C* __restrict__ f
     }
 }
 
+// Q^T (Eq. Huf transposed): r_j = sum_o conj(alpha_o) X_{j-o} for j in I, X on the
+// grid rows of I^h (x2 slowest, like the sparsified right-hand side).
+template <typename C>
+__global__ void sparsify_t_kernel(const C* __restrict__ X, double2* __restrict__ r, StencilArgs st, int n, int b,
+                                  int n_tot) {
+    const long long N = (long long)n * n, tot = (long long)n_tot * n_tot;
+    const int rr = blockIdx.y;
+    const C* xv = X + (long long)rr * tot;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int j1 = (int)(e / n) + 1, j2 = (int)(e % n) + 1;
+        double2 acc = mk(0.0, 0.0);
+        for (int o = 0; o < 9; ++o) {
+            const int i1 = j1 - (o / 3 - 1), i2 = j2 - (o % 3 - 1);   // in 0..n+1
+            acc = cfma(st.a_conj[o], to_d(xv[(long long)(i2 + b) * n_tot + (i1 + b)]), acc);
+        }
+        r[rr * N + e] = acc;
+    }
+}
+
+// dL/dm = Re((-omega^2 K mu) . (u + u_I)) summed over the right-hand sides, with
+// u_I = exp(i omega d.p) recomputed from the directions.
+__global__ void gradient_kernel(const double2* __restrict__ Kmu, const double2* __restrict__ u,
+                                const double* __restrict__ dirs, double* __restrict__ grad, int n, int R, double omega,
+                                double h) {
+    const long long N = (long long)n * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(e / n), col = (int)(e % n);
+        double acc = 0.0;
+        for (int r = 0; r < R; ++r) {
+            const double ph = omega * (dirs[2 * r] * (row + 1) * h + dirs[2 * r + 1] * (col + 1) * h);
+            double sn, cs;
+            sincos(ph, &sn, &cs);
+            const double2 ut = u[r * N + e] + mk(cs, sn);
+            const double2 k = Kmu[r * N + e];
+            acc += k.x * ut.x - k.y * ut.y;
+        }
+        grad[e] = acc;
+    }
+}
+
 StencilArgs stencil_args(const lss_ctx* c) {
     StencilArgs st;
     for (int o = 0; o < 9; ++o) {
@@ -274,4 +314,25 @@ int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s) {
         sparsify_kernel<float2><<<dim3(blocks, R), 256, 0, s>>>(r, (float2*)f, stencil_args(c), c->n, c->b,
                                                                  c->n_tot);
     return lss_check_cuda(c, cudaGetLastError(), "sparsify");
+}
+
+int lss_sparsify_t(lss_ctx* c, const void* X, double2* r, int R, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+    const long long N = (long long)c->n * c->n;
+    const int blocks = (int)std::min<long long>((N + 255) / 256, 4096);
+    if (c->prec == LSS_FP64)
+        sparsify_t_kernel<double2><<<dim3(blocks, R), 256, 0, s>>>((const double2*)X, r, stencil_args(c), c->n, c->b,
+                                                                    c->n_tot);
+    else
+        sparsify_t_kernel<float2><<<dim3(blocks, R), 256, 0, s>>>((const float2*)X, r, stencil_args(c), c->n, c->b,
+                                                                   c->n_tot);
+    return lss_check_cuda(c, cudaGetLastError(), "sparsify transpose");
+}
+
+int lss_gradient_m(lss_ctx* c, const double2* Kmu, const double2* u, const double* dirs_dev, double* grad, int R,
+                   cudaStream_t s) {
+    const long long N = (long long)c->n * c->n;
+    const int blocks = (int)std::min<long long>((N + 255) / 256, 4096);
+    gradient_kernel<<<blocks, 256, 0, s>>>(Kmu, u, dirs_dev, grad, c->n, R, c->omega, c->h);
+    return lss_check_cuda(c, cudaGetLastError(), "gradient");
 }

@@ -29,7 +29,11 @@ def _stream_ptr(stream=None) -> int:
 
 
 def _c128(x: torch.Tensor) -> torch.Tensor:
-    if x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous():
+    if x.dtype != torch.complex128 or not x.is_cuda:
+        raise TypeError("expected a complex128 CUDA tensor")
+    if x.is_conj():          # a lazy conjugate view: the library needs the values in memory
+        x = x.resolve_conj()
+    if not x.is_contiguous():
         raise TypeError("expected a contiguous complex128 CUDA tensor")
     return x
 
@@ -117,10 +121,11 @@ class LSSolver:
                                          _stream_ptr(stream)))
         return y
 
-    def apply_P(self, x: torch.Tensor, stream=None) -> torch.Tensor:
+    def apply_P(self, x: torch.Tensor, transpose: bool = False, stream=None) -> torch.Tensor:
         x = _c128(self._batch(x))
         y = torch.empty_like(x)
-        self._check(self.lib.lss_apply_P(self.ctx, x.data_ptr(), y.data_ptr(), x.shape[0], 0, _stream_ptr(stream)))
+        self._check(self.lib.lss_apply_P(self.ctx, x.data_ptr(), y.data_ptr(), x.shape[0], int(transpose),
+                                         _stream_ptr(stream)))
         return y
 
     def apply_slab(self, i: int, v: torch.Tensor, stream=None) -> torch.Tensor:
@@ -143,6 +148,32 @@ class LSSolver:
             self._check(code)
         return u, [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
                         relres_true=s.relres_true) for s in st]
+
+    def adjoint_solve(self, rhs: torch.Tensor, opts: GmresOptions | None = None, stream=None,
+                      raise_on_noconv=True):
+        """mu with (I + omega^2 M K) mu = rhs (lss_adjoint_solve)."""
+        o = opts or GmresOptions()
+        rhs = _c128(self._batch(rhs))
+        mu = torch.empty_like(rhs)
+        R = rhs.shape[0]
+        st = (_lib.Stats * R)()
+        go = _lib.Gmres(o.restart, o.tol, o.max_iter)
+        code = self.lib.lss_adjoint_solve(self.ctx, rhs.data_ptr(), mu.data_ptr(), R, ctypes.byref(go), st,
+                                          _stream_ptr(stream))
+        if code != 0 and not (code == -5 and not raise_on_noconv):
+            self._check(code)
+        return mu, [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
+                         relres_true=s.relres_true) for s in st]
+
+    def medium_gradient(self, mu: torch.Tensor, u: torch.Tensor, dirs, stream=None) -> torch.Tensor:
+        """sum_r Re((-omega^2 K mu_r) . (u_r + u_I,r)) on I (lss_medium_gradient)."""
+        mu = _c128(self._batch(mu))
+        u = _c128(self._batch(u))
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 2))
+        grad = torch.empty((self.n, self.n), dtype=torch.float64, device="cuda")
+        self._check(self.lib.lss_medium_gradient(self.ctx, mu.data_ptr(), u.data_ptr(), d.ctypes.data, d.shape[0],
+                                                 grad.data_ptr(), _stream_ptr(stream)))
+        return grad
 
     def solve_host(self, g_host: torch.Tensor, u_host: torch.Tensor, opts: GmresOptions | None = None,
                    stream=None):
