@@ -160,17 +160,22 @@ def algorithmic(solver, R, prec_bytes):
         m1, e1 = cr_solve_work(nt, w, True)
         m2, e2 = cr_solve_work(nt, w, False)
         a_mac, a_ent, e_mac, e_ent = a_mac + m1, a_ent + e1, e_mac + m2, e_ent + e2
+    # interface maps: all n_tot unit columns of a slab side at once; forward
+    # over the column windows of width 2^(l+1) - 1, dense back substitution,
+    # then the tridiagonal coupling
+    Ks = _levels(nt)
     if_mac = 0
-    cache = {}
     for side in (0, 1):
-        for i in range(1, ns - 1 if side == 0 else ns - 2 + 1):
-            if side == 1 and i > ns - 2:
-                continue
+        for i in range(1, (ns - 1) if side == 0 else (ns - 2) + 1):
             w = ws[i]
-            if w not in cache:
-                cache[w] = sum(cr_solve_work(nt, w, True, (max(0, j - 1), min(nt - 1, j + 1)))[0]
-                               for j in range(nt))
-            if_mac += cache[w]
+            mac = 0
+            for l, K in enumerate(Ks):
+                wodd, wev = min(nt, 2 ** (l + 1) - 1), min(nt, 2 ** (l + 2) - 1)
+                mac += (K // 2) * wodd * (w * w if l else w)
+                mac += ((K + 1) // 2) * wev * (2 * w * w if l else 6 * w)
+                mac += (K // 2) * nt * (2 * w * w if l else 8 * w)
+            mac += nt * w * w + nt * nt * 3 * (2 if side == 0 else 1)
+            if_mac += mac
     fft_flops = R * (n * 5 * L * math.log2(L) + L * 2 * 5 * L * math.log2(L) + n * 5 * L * math.log2(L))
     mv_bytes = R * (16 * N * 2) + 8 * N + 16 * L * L
     recur_bytes = (2 * max(ns - 2, 0) + max(ns - 1, 0)) * nt * nt * cb   # Lambda, Phi chains + Gamma (mu)
@@ -179,7 +184,7 @@ def algorithmic(solver, R, prec_bytes):
     return {
         "slab_a": dict(bytes=a_ent * cb + rhs_bytes, flops=8 * a_mac * R, launches_per_apply=1),
         "slab_e": dict(bytes=e_ent * cb + rhs_bytes, flops=8 * e_mac * R, launches_per_apply=1),
-        "iface": dict(bytes=3 * ns * nt * nt * cb, flops=8 * if_mac, launches_per_apply=1),
+        "iface": dict(bytes=3 * ns * nt * nt * cb, flops=8 * if_mac, launches_per_apply=3 * len(Ks) + 2),
         "matvec": dict(bytes=mv_bytes, flops=fft_flops, launches_per_apply=3),
         "recur": dict(bytes=recur_bytes * R, flops=recur_bytes // cb * 8 * R, launches_per_apply=3),
         "factor": dict(bytes=sum(nt * 3 * w * w * cb for w in ws), flops=factor_flops, launches_per_apply=None),

@@ -1,0 +1,407 @@
+// Interface maps of the slab-parallel sweep (Sec. 2.3, Algorithm 2), all
+// columns of a slab at once.
+//
+// For slab i and pin layer q (q = first layer of D_i for Lambda_i and Gamma_i,
+// q = last layer for Phi_i) the maps need W = S_i^{-1} [e_{(q,j)}]_j restricted
+// to two layers, for every block row j.  The n_tot unit right-hand sides of a
+// slab go through the cyclic reduction together.  Forward: the right-hand side
+// of column j starts in block row j, and the reduction of level l mixes rows
+// 2^l apart, so at level l block row k is non-zero only in the columns
+// [k - (2^l - 1), k + (2^l - 1)]; the forward pass touches only those windows.
+// The top row and the back substitution are dense in the columns: at level l
+// every odd row gets x_k = y_k - (D^{-1}C)_k x_{k-2^l} - (D^{-1}B)_k x_{k+2^l}
+// for all n_tot columns, a (G x 2G)(2G x columns) product; level 0 keeps only
+// the first and last layers.  The maps then apply the coupling H_{[i,i-1]}
+// (resp. H_{[i,i+1]}), tridiagonal in the columns:
+//   Lambda_i[k][j] = sum_{j'} W_last[k][j'] H(j', j),  Gamma_i with W_first,
+//   Phi_i with W_first and H_{[i,i+1]}.
+// One launch per phase covers every slab and side: grid (column tiles, block
+// rows of the level, problems); lane p of a column group owns layer p.  The column blocks live in a scratch array
+// X[problem][k][j][layer] (n_tot x n_tot x G entries per problem).
+#include <algorithm>
+#include <vector>
+
+#include "lss_common.cuh"
+#include "lss_ctx.h"
+
+namespace {
+
+constexpr int kIfT = 256;   // threads per CTA: G lanes per column (one per layer) x column groups
+constexpr int kIfTN = 64;   // columns per CTA
+
+struct IfProb {
+    int slab, side, G, pad;
+    long long xoff;   // entries of X before this problem
+    long long woff;   // entries of W before this problem (2 n_tot^2 each)
+};
+
+template <typename C>
+struct IfArgs {
+    const SlabDev* slabs;
+    int n_slabs, K;
+    const C* fac;
+    const C* coef;
+    const IfProb* probs;
+    C* X;
+    C* W;             // layers na and w-1 of the solution columns: 2 x n_tot x n_tot per problem
+    C* maps;
+};
+
+__device__ __forceinline__ double2 cfnma_i(double2 a, double2 b, double2 acc) {
+    acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ float2 cfnma_i(float2 a, float2 b, float2 acc) {
+    acc.x = fmaf(-a.x, b.x, acc.x); acc.x = fmaf(a.y, b.y, acc.x);
+    acc.y = fmaf(-a.x, b.y, acc.y); acc.y = fmaf(-a.y, b.x, acc.y);
+    return acc;
+}
+
+// Window of block row k at level l: [k - (2^l - 1), k + (2^l - 1)] within [0, K).
+__device__ __forceinline__ int win_lo(int k, int l) { return max(0, k - ((1 << l) - 1)); }
+__device__ __forceinline__ int win_hi(int k, int l, int K) { return min(K - 1, k + ((1 << l) - 1)); }
+
+// Copies n entries (blocks or bands) into shared memory.
+template <typename C>
+__device__ __forceinline__ void stage(C* dst, const C* src, int n) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+}
+
+// Forward phase of level l over the windows: phase 0 = odd rows
+// (y = D^{-1} b in place), 1 = even rows (b -= C y_{k-s} + B y_{k+s}, into the
+// window of level l+1), 2 = the top row (all columns, in place).  Lane p of a
+// column group owns layer p of CPT columns.
+template <typename T, int G>
+__device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int phase) {
+    using C = cx<T>;
+    extern __shared__ __align__(16) unsigned char smi[];
+    C* Ms = reinterpret_cast<C*>(smi);   // up to 2 blocks, or the bands of one row
+    const int K = A.K;
+    const SlabDev sd = A.slabs[pr.slab];
+    const int bs = G * G;
+    const C* F = A.fac + sd.fac_off;
+    const int pin = pr.side == 0 ? sd.na : sd.w - 1;
+    const int s = 1 << l;
+    const CrLevelOffs lv = cr_level(K, l);
+    const int r = blockIdx.y;
+    int k, lo, hi;
+    if (phase == 0) {
+        if (r >= lv.K / 2) return;
+        k = (2 * r + 1) * s;
+        lo = win_lo(k, l);
+        hi = win_hi(k, l, K);
+    } else if (phase == 1) {
+        if (r >= (lv.K + 1) / 2) return;
+        k = 2 * r * s;
+        lo = win_lo(k, l + 1);
+        hi = win_hi(k, l + 1, K);
+    } else {
+        if (r > 0) return;
+        k = 0;
+        lo = 0;
+        hi = K - 1;
+    }
+    const int j0 = lo + blockIdx.x * kIfTN;
+    if (j0 > hi) return;
+    C* X = A.X + pr.xoff;
+    auto at = [&](int kk, int j) { return X + ((long long)kk * K + j) * G; };
+    const int p = threadIdx.x % G, cg = threadIdx.x / G;
+    constexpr int NCG = kIfT / G, CPT = kIfTN / NCG;
+    if (phase == 0 || phase == 2) {
+        const C* D = phase == 0 ? F + (lv.dinv + r) * bs : F + cr_level(K, cr_levels(K)).dinv * bs;
+        stage(Ms, D, bs);
+        __syncthreads();
+        if (phase == 0 && l == 0) {   // b_k = e_(pin, k): y_k = column pin of D^{-1}, in column k only
+            if (threadIdx.x < G) at(k, k)[threadIdx.x] = Ms[pin * G + threadIdx.x];
+            return;
+        }
+        C acc[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int j = j0 + cg * CPT + q;
+            acc[q] = czero<C>();
+            if (j <= hi && j < j0 + kIfTN) {
+                const C* x = at(k, j);
+#pragma unroll
+                for (int a = 0; a < G; ++a) acc[q] = cfma(Ms[a * G + p], x[a], acc[q]);
+            }
+        }
+        __syncthreads();   // every column of the tile read before it is overwritten
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int j = j0 + cg * CPT + q;
+            if (j <= hi && j < j0 + kIfTN) at(k, j)[p] = acc[q];
+        }
+        return;
+    }
+    // even rows: b_k -= C_k y_{k-s} + B_k y_{k+s}
+    const bool hasL = k - s >= 0, hasR = k + s < K;
+    if (l == 0) {
+        const C* t0 = F + cr_t0_off(K, bs) + (long long)r * 6 * G;   // even row r's bands
+        stage(Ms, t0, 6 * G);
+    } else {
+        stage(Ms, F + (lv.cbe + 2LL * r) * bs, 2 * bs);
+    }
+    __syncthreads();
+    const int llo = win_lo(k, l), lhi = win_hi(k, l, K);
+    const int mlo = win_lo(k - s, l), mhi = hasL ? win_hi(k - s, l, K) : -1;
+    const int plo = hasR ? win_lo(k + s, l) : K, phi = hasR ? win_hi(k + s, l, K) : -1;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int j = j0 + cg * CPT + q;
+        if (j > hi || j >= j0 + kIfTN) continue;
+        C acc = czero<C>();
+        if (l == 0) {
+            if (j == k && p == pin) acc.x = T(1);
+        } else if (j >= llo && j <= lhi) {
+            acc = at(k, j)[p];
+        }
+        if (hasL && j >= mlo && j <= mhi) {
+            const C* x = at(k - s, j);
+            if (l == 0) {
+#pragma unroll
+                for (int da = -1; da <= 1; ++da)
+                    if (p + da >= 0 && p + da < G) acc = cfnma_i(Ms[(da + 1) * G + p], x[p + da], acc);
+            } else {
+#pragma unroll
+                for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[a * G + p], x[a], acc);
+            }
+        }
+        if (hasR && j >= plo && j <= phi) {
+            const C* x = at(k + s, j);
+            if (l == 0) {
+#pragma unroll
+                for (int da = -1; da <= 1; ++da)
+                    if (p + da >= 0 && p + da < G) acc = cfnma_i(Ms[(3 + da + 1) * G + p], x[p + da], acc);
+            } else {
+#pragma unroll
+                for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[bs + a * G + p], x[a], acc);
+            }
+        }
+        at(k, j)[p] = acc;
+    }
+}
+
+// Back substitution of level l for the odd rows, all columns:
+// x_k = [y_k on its window] - (D^{-1}C)_k x_{k-s} - (D^{-1}B)_k x_{k+s};
+// level 0 (bands, rows na and w-1 of D^{-1}) writes layers na and w-1 only.
+template <typename T, int G>
+__device__ void bwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l) {
+    using C = cx<T>;
+    extern __shared__ __align__(16) unsigned char smi[];
+    C* Ms = reinterpret_cast<C*>(smi);
+    const int K = A.K;
+    const SlabDev sd = A.slabs[pr.slab];
+    const int bs = G * G;
+    const C* F = A.fac + sd.fac_off;
+    const int s = 1 << l;
+    const CrLevelOffs lv = cr_level(K, l);
+    const int r = blockIdx.y;
+    if (r >= lv.K / 2) return;
+    const int k = (2 * r + 1) * s;
+    const int j0 = blockIdx.x * kIfTN;
+    if (j0 >= K) return;
+    C* X = A.X + pr.xoff;
+    auto at = [&](int kk, int j) { return X + ((long long)kk * K + j) * G; };
+    const int p = threadIdx.x % G, cg = threadIdx.x / G;
+    constexpr int NCG = kIfT / G, CPT = kIfTN / NCG;
+    const bool hasR = k + s < K;
+    const int ylo = win_lo(k, l), yhi = win_hi(k, l, K);
+    if (l > 0) {
+        stage(Ms, F + (lv.dcdb + 2LL * r) * bs, 2 * bs);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int j = j0 + cg * CPT + q;
+            if (j >= K) continue;
+            C acc = (j >= ylo && j <= yhi) ? at(k, j)[p] : czero<C>();
+            const C* xm = at(k - s, j);
+#pragma unroll
+            for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[a * G + p], xm[a], acc);
+            if (hasR) {
+                const C* xp = at(k + s, j);
+#pragma unroll
+                for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[bs + a * G + p], xp[a], acc);
+            }
+            at(k, j)[p] = acc;
+        }
+        return;
+    }
+    // level 0: t = C_k x_{k-1} + B_k x_{k+1} (bands), then layers na and w-1 by
+    // shuffle reductions over the lanes of a column, into the compact arrays W0
+    // (layer na) and W1 (layer w-1); the CTA also copies those layers of the
+    // even row k-1 (and of row K-1 when it is an unpaired even row).
+    stage(Ms, F + cr_t0_off(K, bs) + ((long long)(K + 1) / 2 + r) * 6 * G, 6 * G);
+    stage(Ms + 6 * G, F + cr_p0_off(K, bs, G) + (long long)r * 2 * G, 2 * G);
+    __syncthreads();
+    C* W0 = A.W + pr.woff;
+    C* W1 = W0 + (long long)K * K;
+    const int na = sd.na, wl = sd.w - 1;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int j = j0 + cg * CPT + q;
+        const bool on = j < K;
+        const int jc = on ? j : K - 1;
+        C t = czero<C>();
+        const C* xm = at(k - 1, jc);
+#pragma unroll
+        for (int da = -1; da <= 1; ++da)
+            if (p + da >= 0 && p + da < G) t = cfma(Ms[(da + 1) * G + p], xm[p + da], t);
+        if (hasR) {
+            const C* xp = at(k + 1, jc);
+#pragma unroll
+            for (int da = -1; da <= 1; ++da)
+                if (p + da >= 0 && p + da < G) t = cfma(Ms[(3 + da + 1) * G + p], xp[p + da], t);
+        }
+        C d0 = Ms[6 * G + p] * t, d1 = Ms[7 * G + p] * t;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
+            d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
+            d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
+            d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
+        }
+        if (on && p == 0) {
+            const long long o = (long long)k * K + j;
+            C y0 = czero<C>(), y1 = czero<C>();
+            if (j == k) {   // y_k is non-zero in column k only
+                y0 = at(k, j)[na];
+                y1 = at(k, j)[wl];
+            }
+            W0[o] = y0 - d0;
+            W1[o] = (wl == na) ? y0 - d0 : y1 - d1;
+            const C* xe = at(k - 1, j);
+            W0[o - K] = xe[na];
+            W1[o - K] = xe[wl];
+            if (k + 1 == K - 1) {
+                const C* xl = at(K - 1, j);
+                W0[o + K] = xl[na];
+                W1[o + K] = xl[wl];
+            }
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kIfT) if_fwd_kernel(IfArgs<cx<T>> A, int l, int phase) {
+    const IfProb pr = A.probs[blockIdx.z];
+    if (pr.G == 16) fwd_body<T, 16>(A, pr, l, phase);
+    else fwd_body<T, 32>(A, pr, l, phase);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kIfT) if_bwd_kernel(IfArgs<cx<T>> A, int l) {
+    const IfProb pr = A.probs[blockIdx.z];
+    if (pr.G == 16) bwd_body<T, 16>(A, pr, l);
+    else bwd_body<T, 32>(A, pr, l);
+}
+
+// Maps from the two kept layers and the coupling, tridiagonal in the columns.
+template <typename T>
+__global__ void __launch_bounds__(256) if_maps_kernel(IfArgs<cx<T>> A) {
+    using C = cx<T>;
+    const IfProb pr = A.probs[blockIdx.y];
+    const int K = A.K, i = pr.slab;
+    const SlabDev sd = A.slabs[i];
+    const C* cf = A.coef + sd.coef_off;
+    const long long nt2 = (long long)K * K;
+    const C* W0 = A.W + pr.woff;
+    const C* W1 = W0 + nt2;
+    const int ns = A.n_slabs;
+    const int pin = pr.side == 0 ? sd.na : sd.w - 1;
+    const int base = pr.side == 0 ? 0 : 6;   // coupling slot of layer offset -1 / +1
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nt2; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / K), j = (int)(e % K);
+        C v0 = czero<C>(), v1 = czero<C>();
+        for (int jp = max(0, j - 1); jp <= min(K - 1, j + 1); ++jp) {
+            const C h = cf[(long long)jp * sd.cstride + pin * 9 + base + (j - jp) + 1];
+            const long long o = (long long)k * K + jp;
+            v0 = cfma(W1[o], h, v0);
+            v1 = cfma(W0[o], h, v1);
+        }
+        if (pr.side == 0) {
+            A.maps[(0LL * ns + i) * nt2 + e] = v0;
+            A.maps[(1LL * ns + i) * nt2 + e] = v1;
+        } else {
+            A.maps[(2LL * ns + i) * nt2 + e] = v1;
+        }
+    }
+}
+
+template <typename T>
+int iface_impl(lss_ctx* c, cudaStream_t s) {
+    using C = cx<T>;
+    const int K = c->n_tot, ns = c->n_slabs;
+    if (ns == 1) return LSS_OK;
+    // problems: side 0 for slabs 1..l-1, side 1 for slabs 1..l-2
+    std::vector<IfProb> probs;
+    long long xoff = 0, woff = 0;
+    int gmax = 16;
+    for (int side = 0; side < 2; ++side)
+        for (int i = 1; i <= (side == 0 ? ns - 1 : ns - 2); ++i) {
+            IfProb p{i, side, c->slabs[i].ldw, 0, xoff, woff};
+            xoff += (long long)K * K * p.G;
+            woff += 2LL * K * K;
+            gmax = std::max(gmax, p.G);
+            probs.push_back(p);
+        }
+    const int np = (int)probs.size();
+    int rc = lss_grow(c, &c->ifx_buf, &c->ifx_cap, (size_t)(xoff + woff) * sizeof(C));
+    if (rc) return rc;
+    if (c->ifp_n != np) {   // the table depends on the slab layout only: uploaded once
+        rc = lss_grow(c, &c->ifp_buf, &c->ifp_cap, probs.size() * sizeof(IfProb));
+        if (!rc) rc = lss_check_cuda(c, cudaMemcpy(c->ifp_buf, probs.data(), probs.size() * sizeof(IfProb),
+                                                   cudaMemcpyHostToDevice), "interface problems");
+        if (rc) return rc;
+        c->ifp_n = np;
+    }
+    IfArgs<C> A{};
+    A.slabs = c->d_slabs;
+    A.n_slabs = ns;
+    A.K = K;
+    A.fac = (const C*)c->fac;
+    A.coef = (const C*)c->coef;
+    A.probs = (const IfProb*)c->ifp_buf;
+    A.X = (C*)c->ifx_buf;
+    A.W = A.X + xoff;
+    A.maps = (C*)c->iface;
+    const size_t sh = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)8 * gmax);
+    static size_t cfg_f = 0, cfg_b = 0;
+    if (sh > cfg_f) {
+        cudaError_t e = cudaFuncSetAttribute(if_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::max<size_t>(sh, 48 * 1024));
+        if (e) return lss_check_cuda(c, e, "interface attribute");
+        cfg_f = sh;
+    }
+    if (sh > cfg_b) {
+        cudaError_t e = cudaFuncSetAttribute(if_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::max<size_t>(sh, 48 * 1024));
+        if (e) return lss_check_cuda(c, e, "interface attribute");
+        cfg_b = sh;
+    }
+    const int L = cr_levels(K);
+    const int kt = (K + kIfTN - 1) / kIfTN;
+    ProfScope ps(c, s, LSS_PROF_IFACE, 3 * L + 2);
+    for (int l = 0; l < L; ++l) {
+        const int Kl = cr_level(K, l).K;
+        const int wt0 = ((1 << (l + 1)) - 1 + kIfTN - 1) / kIfTN;   // tiles of a level-l window
+        const int wt1 = ((1 << (l + 2)) - 1 + kIfTN - 1) / kIfTN;   // tiles of a level-(l+1) window
+        if_fwd_kernel<T><<<dim3(std::min(wt0, kt), std::max(1, Kl / 2), np), kIfT, sh, s>>>(A, l, 0);
+        if_fwd_kernel<T><<<dim3(std::min(wt1, kt), (Kl + 1) / 2, np), kIfT, sh, s>>>(A, l, 1);
+    }
+    if_fwd_kernel<T><<<dim3(kt, 1, np), kIfT, sh, s>>>(A, L, 2);
+    for (int l = L - 1; l >= 0; --l) {
+        const int Kl = cr_level(K, l).K;
+        if_bwd_kernel<T><<<dim3(kt, std::max(1, Kl / 2), np), kIfT, sh, s>>>(A, l);
+    }
+    if_maps_kernel<T><<<dim3((unsigned)std::min<long long>(((long long)K * K + 255) / 256, 1024), np), 256, 0,
+                        s>>>(A);
+    return lss_check_cuda(c, cudaGetLastError(), "interface launch");
+}
+
+}  // namespace
+
+int lss_iface_maps(lss_ctx* c, cudaStream_t s) {
+    return c->prec == LSS_FP64 ? iface_impl<double>(c, s) : iface_impl<float>(c, s);
+}

@@ -148,6 +148,9 @@ struct lss_ctx {
     void* io_buf = nullptr; size_t io_cap = 0;         // host-buffer solve staging
     void* dir_buf = nullptr; size_t dir_cap = 0;       // plane-wave directions
     void* gr_buf = nullptr; size_t gr_cap = 0;         // -omega^2 K mu for the medium gradient
+    void* ifx_buf = nullptr; size_t ifx_cap = 0;       // interface-map column blocks (all slabs, both sides)
+    void* ifp_buf = nullptr; size_t ifp_cap = 0;       // interface-map problem table
+    int ifp_n = 0;                                     // problems uploaded to ifp_buf
     int num_sms = 0;
 
     // profiling: event pairs per kernel group, launch counters
@@ -200,6 +203,8 @@ int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s);
 int lss_factor_slabs(lss_ctx* c, cudaStream_t s);
 int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s);
 int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s);
+// iface.cu: interface maps Lambda, Gamma, Phi of every slab (all columns at once)
+int lss_iface_maps(lss_ctx* c, cudaStream_t s);
 // the three interface recurrences with the maps at `maps` (Lambda, Gamma, Phi blocks)
 int lss_recurrences(lss_ctx* c, const void* maps, void* lam, void* phi, const void* a_first, const void* a_last,
                     int R, cudaStream_t s);

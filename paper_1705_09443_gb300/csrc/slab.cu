@@ -1230,12 +1230,7 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
     }
     rc = lss_check_cuda(c, cudaGetLastError(), "factor launch");
     if (rc || ns == 1) return rc;
-    bool used = false;
-    constexpr int NCI = sizeof(T) == 8 ? 2 : 4;
-    rc = launch_iface<T, NCI>(c, s, &used);
-    if (!rc && !used) rc = launch_iface<T, NCI / 2>(c, s, &used);
-    if (!rc && !used) rc = launch_iface<T, 1>(c, s, &used);
-    return rc;
+    return lss_iface_maps(c, s);
 }
 
 // Cluster size for the recurrence kernels: 16 CTAs when the GPU can
