@@ -1016,6 +1016,121 @@ __global__ void __launch_bounds__(NT) recur_chain_kernel(int n_slabs, int n_tot,
     }
 }
 
+// The same recurrence with each CTA's rows of the next maps moved into a ring
+// of shared-memory stages by TMA bulk copies, NB steps ahead (one thread issues,
+// every thread waits on the stage's mbarrier, bounded); the dot products read
+// the rows from shared memory, so the number of (row, rhs) tasks per warp is
+// free.  The base values of a warp's first tasks are loaded one step ahead.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ maps,
+                                                       const cx<T>* base, const cx<T>* __restrict__ init, cx<T>* out,
+                                                       int backward, int nb, int* err) {
+    using C = cx<T>;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int CL = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    extern __shared__ __align__(128) unsigned char smr2[];
+    const long long nt2 = (long long)n_tot * n_tot;
+    const long long vec = (long long)n_tot * R;
+    const int rows_per = (n_tot + CL - 1) / CL;
+    const int r0 = min(n_tot, cr * rows_per), r1 = min(n_tot, r0 + rows_per);
+    const int nrow = r1 - r0;
+    const long long stage_ent = (long long)rows_per * n_tot;
+    C* ring = reinterpret_cast<C*>(smr2);                 // nb x rows_per x n_tot
+    C* vb = ring + nb * stage_ent;                        // 2 x n_tot x R
+    __shared__ __align__(8) uint64_t full[4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT >> 5;
+    const int ntask = nrow * R;
+    const int nsteps = n_slabs - 2;
+    const int i0 = backward ? n_slabs - 2 : 1, di = backward ? -1 : 1;
+    const unsigned bytes = (unsigned)((long long)nrow * n_tot * sizeof(C));
+    auto issue = [&](int step) {
+        const int st = step % nb;
+        const C* src = maps + (long long)(i0 + step * di) * nt2 + (long long)r0 * n_tot;
+        mbar_expect_tx(&full[st], bytes);
+        tma_load_1d(ring + st * stage_ent, src, bytes, &full[st]);
+    };
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < nb; ++st) mbar_init(&full[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && nrow > 0)
+        for (int step = 0; step < nb && step < nsteps; ++step) issue(step);
+    // out_{i0 - di} = init, replicated into every CTA's vector
+    const long long o0 = (long long)(i0 - di) * vec;
+    for (long long e = threadIdx.x; e < vec; e += NT) vb[e] = init[e];
+    if (out + o0 != init)
+        for (long long e = (long long)r0 * R + threadIdx.x; e < (long long)r1 * R; e += NT) out[o0 + e] = init[e];
+    cl.sync();   // every CTA of the cluster is running before remote stores
+    // base values of the warp's first BV tasks, one step ahead
+    constexpr int BV = 4;
+    C bvn[BV];
+    auto load_bv = [&](int step) {
+#pragma unroll
+        for (int q = 0; q < BV; ++q) {
+            const int t0 = warp + q * nw;
+            bvn[q] = (t0 < ntask && step < nsteps)
+                         ? base[(long long)(i0 + step * di) * vec + (long long)(r0 + t0 / R) * R + t0 % R]
+                         : czero<C>();
+        }
+    };
+    load_bv(0);
+    bool ok = true;
+    int cur = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        const int i = i0 + s * di;
+        const int st = s % nb;
+        C bvc[BV];
+#pragma unroll
+        for (int q = 0; q < BV; ++q) bvc[q] = bvn[q];
+        load_bv(s + 1);
+        if (nrow > 0 && !mbar_wait(&full[st], (s / nb) & 1, err)) ok = false;
+        const C* M = ring + st * stage_ent;
+        for (int t0 = warp, q = 0; t0 < ntask; t0 += nw, ++q) {
+            const int rl = t0 / R, rr = t0 % R;
+            const long long e = (long long)(r0 + rl) * R + rr;
+            C bv;
+            if (q < BV) {
+#pragma unroll
+                for (int u = 0; u < BV; ++u)
+                    if (u == q) bv = bvc[u];
+            } else {
+                bv = base[(long long)i * vec + e];
+            }
+            const C* mrow = M + (long long)rl * n_tot;
+            const C* x = vb + cur * vec + rr;
+            C a0 = czero<C>(), a1 = czero<C>();
+            int j = lane;
+            for (; j + 32 < n_tot; j += 64) {
+                a0 = cfma(mrow[j], x[(long long)j * R], a0);
+                a1 = cfma(mrow[j + 32], x[(long long)(j + 32) * R], a1);
+            }
+            if (j < n_tot) a0 = cfma(mrow[j], x[(long long)j * R], a0);
+            C acc = a0 + a1;
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            if (lane < CL) {
+                const C val = bv - acc;
+                if (lane == 0) out[(long long)i * vec + e] = val;
+                C* dst = cl.map_shared_rank(vb, lane);
+                dst[(cur ^ 1) * vec + e] = val;
+            }
+        }
+        __syncthreads();   // the stage is no longer read
+        if (threadIdx.x == 0 && nrow > 0 && s + nb < nsteps) issue(s + nb);
+        cl.sync();
+        cur ^= 1;
+    }
+    if (!ok && threadIdx.x == 0) {
+        // a wait expired: give the copies already issued a bounded chance to land
+        const long long t0 = clock64();
+        while (clock64() - t0 < 2000000ll) __nanosleep(1000);
+    }
+}
+
 // mu_i = first(a_i) - Gamma_i lambda_{i-1} for i = 1..l-1, all independent:
 // one warp per (slab, row, rhs) dot product over the whole GPU.
 template <typename T>
@@ -1282,9 +1397,64 @@ int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     return lss_check_cuda(c, e, "recurrence cluster launch");
 }
 
+// TMA-ring version: 16-CTA clusters (8 when 16 cannot be co-scheduled), as
+// many ring stages (2..3) as fit beside the vectors.  LSS_ERR_UNSUPPORTED when
+// even two stages do not fit.
+template <typename T>
+int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward,
+                     int R, cudaStream_t s) {
+    using C = cx<T>;
+    constexpr int NT = sizeof(T) == 8 ? 512 : 1024;   // a warp per (row, rhs) task where possible
+    auto kern = recur_tma_kernel<T, NT>;
+    static int cl_size = 0;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (!e) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e) return lss_check_cuda(c, e, "recurrence attribute");
+        attr_done = true;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(NT);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    auto smem_for = [&](int cls, int nb) {
+        const long long rows_per = (c->n_tot + cls - 1) / cls;
+        return sizeof(C) * (size_t)(nb * rows_per * c->n_tot + 2LL * c->n_tot * R);
+    };
+    if (!cl_size) {
+        for (int cand : {16, 8}) {
+            attr[0].val.clusterDim.x = cand;
+            cfg.gridDim = dim3(cand);
+            cfg.dynamicSmemBytes = smem_for(cand, 2);
+            int nclusters = 0;
+            cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, (void*)kern, &cfg);
+            if (!e && nclusters > 0) { cl_size = cand; break; }
+            cudaGetLastError();
+        }
+        if (!cl_size) return LSS_ERR_UNSUPPORTED;
+    }
+    int nb = 3;
+    while (nb >= 2 && smem_for(cl_size, nb) > (size_t)220 * 1024) --nb;
+    if (nb < 2) return LSS_ERR_UNSUPPORTED;
+    attr[0].val.clusterDim.x = cl_size;
+    cfg.gridDim = dim3(cl_size);
+    cfg.dynamicSmemBytes = smem_for(cl_size, nb);
+    int ns = c->n_slabs, nt = c->n_tot;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, maps, base, init, out, backward, nb, c->d_err);
+    return lss_check_cuda(c, e, "recurrence cluster launch");
+}
+
 template <typename T>
 int launch_chain(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward, int R,
                  cudaStream_t s) {
+    const int rc = launch_chain_tma<T>(c, maps, base, init, out, backward, R, s);
+    if (rc != LSS_ERR_UNSUPPORTED) return rc;
     if constexpr (sizeof(T) == 4) {
         if (c->n_tot <= 384) return launch_chain_cfg<T, 3, 12, 256>(c, maps, base, init, out, backward, R, s);
         return launch_chain_cfg<T, 3, 20, 384>(c, maps, base, init, out, backward, R, s);
@@ -1303,7 +1473,7 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     const long long vec = (long long)c->n_tot * R;
     const int ns = c->n_slabs;
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(C);
-    if (sh <= (size_t)160 * 1024) {
+    if (sh <= (size_t)200 * 1024) {
         ProfScope ps(c, s, LSS_PROF_RECUR, 3);
         int rc = launch_chain<T>(c, ifc, a_last, a_last, lam, 0, R, s);
         if (rc == LSS_OK) {
