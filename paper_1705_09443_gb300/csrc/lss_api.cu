@@ -28,6 +28,8 @@ void free_ctx(lss_ctx* c) {
                     c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (void* p : c->chunk_dev)
+        if (p) cudaFree(p);
     delete c;
 }
 

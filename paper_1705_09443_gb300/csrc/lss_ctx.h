@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <string>
 #include <vector>
+#include <array>
 #include <complex>
 
 #include "../../include/lss.h"
@@ -151,6 +152,10 @@ struct lss_ctx {
     void* ifx_buf = nullptr; size_t ifx_cap = 0;       // interface-map column blocks (all slabs, both sides)
     void* ifp_buf = nullptr; size_t ifp_cap = 0;       // interface-map problem table
     int ifp_n = 0;                                     // problems uploaded to ifp_buf
+    // slab-solve chunk tables: key (first/last layers only, stage entries, chunks
+    // of 16-wide blocks, chunks of 32-wide blocks) and two device arrays per key
+    std::vector<std::array<long long, 4>> chunk_keys;
+    std::vector<void*> chunk_dev;
     int num_sms = 0;
 
     // profiling: event pairs per kernel group, launch counters

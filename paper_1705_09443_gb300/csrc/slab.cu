@@ -49,7 +49,6 @@ constexpr int kSolveThreads = 384;
 constexpr int kGjWarps = 2;
 constexpr int kEvWarps = 2;
 constexpr size_t kSmemBudget = size_t(220) * 1024;
-constexpr int kMaxIfSlabs = 2048;   // slab widths cached in shared memory by the interface-map kernel
 
 // acc - a*b
 __device__ __forceinline__ double2 cfnma(double2 a, double2 b, double2 acc) {
@@ -317,22 +316,31 @@ __global__ void __launch_bounds__(32 * kEvWarps) cr_even_kernel(const SlabDev* _
 }
 
 // ---------------------------------------------------------------- slab solves
-// One kernel for the four uses of T~_i:
+// One kernel for the three uses of T~_i:
 //   CR_A    sweep, first pass: a_i = T~_i f_i, first and last layers kept;
 //   CR_E    sweep, second pass: T~_i (f_i - H lambda_{i-1} - H phi_{i+1}) on D_i;
-//   CR_TEST T~_i applied to given vectors (lss_apply_slab);
-//   CR_IF   interface maps: T~_i H e_j for a chunk of columns j.
-// A CTA solves nc right-hand sides of one slab.  The right-hand sides live in
-// shared memory (or per-CTA global scratch when they do not fit), row k of
-// column c at b + (k * nc + c) * ldw.  The factors stream through a ring of
-// shared-memory stages in the order the solve reads them, one TMA bulk copy
-// (two for the finest backward level) per chunk of block rows; thread 0 issues
-// the copies, every thread waits on the stage's mbarrier (bounded) and the
-// block-wide barrier after each chunk frees its stage.  Lanes are grouped by G
-// (16 when the slab is at most 16 layers wide, else 32): lane p of a group owns
-// layer p of one block row.
-enum CrMode { CR_A = 0, CR_E = 1, CR_TEST = 2, CR_IF = 3 };
+//   CR_TEST T~_i applied to given vectors (lss_apply_slab).
+// A CTA solves one right-hand side of one slab, held in shared memory (or
+// per-CTA global scratch when it does not fit), block row k at b + k * G.  The
+// factors stream through a ring of shared-memory stages in the order the solve
+// reads them, one TMA bulk copy (two for the finest backward level) per chunk
+// of block rows.  The chunk sequence depends only on n_tot, the block size, the
+// output (first/last layers or all) and the stage size, so the host builds it
+// once as a table of copies; thread 0 reads the next entry and issues it,
+// every thread waits on the stage's mbarrier (bounded) and the block-wide
+// barrier after each chunk frees its stage.  Lanes are grouped by G (16 when
+// the slab is at most 16 layers wide, else 32): lane p of a group owns layer p
+// of one block row.
+enum CrMode { CR_A = 0, CR_E = 1, CR_TEST = 2 };
 enum CrPhase { PH_FODD = 0, PH_FEVEN = 1, PH_TOP = 2, PH_BODD = 3, PH_B0 = 4 };
+
+// One chunk of a solve: phase, level, block rows [r0, r1) of the phase, and the
+// one or two copies (entry offsets from the slab's factor base, entries).
+struct CrChunk {
+    int kind, l, r0, r1;
+    int ent, ent2;
+    long long src, src2;
+};
 
 template <typename C>
 struct CrArgs {
@@ -349,9 +357,9 @@ struct CrArgs {
     int slab;                // CR_TEST
     const double2* v_in;     // R x (layers of D_i) x n_tot
     double2* w_out;
-    C* iface;                // CR_IF output: Lambda, Gamma, Phi, each n_slabs x n_tot^2
-    int nitems;              // CR_IF work items
-    int row_cap;             // CR_IF: complex entries available per block row of b (all columns)
+    const CrChunk* tab16;    // chunk tables for 16- and 32-wide blocks
+    const CrChunk* tab32;
+    int n16, n32;
     C* bg;                   // right-hand sides in global memory when bsm == 0
     long long bstride;       // entries of b per CTA
     int bsm;
@@ -359,55 +367,17 @@ struct CrArgs {
     int* err;
 };
 
-// Per-level data of the solve: offsets, and for the forward pass the ranges of
-// odd rows [olo, ohi) and even rows [elo, ehi) (as r with j = 2r+1, e = 2r)
-// that can be non-zero.
 struct CrLv {
-    int K, olo, ohi, elo, ehi;
+    int K;
     long long dinv, cbe, dcdb;
 };
-
-// acc (+/-)= sum_{a < G} M(p, a) x[a]: M a zero-padded G x G column-major block
-// in shared memory, x one block row of one right-hand side.  Fully unrolled
-// with two partial sums, so the loads issue ahead of the FMA chains.
-template <typename C, int G, bool SUB>
-__device__ __forceinline__ C mv_row(const C* M, int p, const C* x, C acc) {
-    C acc2 = czero<C>();
-#pragma unroll
-    for (int a = 0; a < G; a += 2) {
-        const C m0 = M[a * G + p], m1 = M[(a + 1) * G + p];
-        const C x0 = x[a], x1 = x[a + 1];
-        if (SUB) {
-            acc = cfnma(m0, x0, acc);
-            acc2 = cfnma(m1, x1, acc2);
-        } else {
-            acc = cfma(m0, x0, acc);
-            acc2 = cfma(m1, x1, acc2);
-        }
-    }
-    return acc + acc2;
-}
-
-// Level-0 off-diagonal block from its bands (band[(da + 1) * G + p] couples
-// layer p to layer p + da, zero outside the slab): acc (+/-)= sum_da band x[p + da].
-template <typename C, int G, bool SUB>
-__device__ __forceinline__ C band_row(const C* band, int p, const C* x, C acc) {
-#pragma unroll
-    for (int da = -1; da <= 1; ++da) {
-        const int a = p + da;
-        if (a < 0 || a >= G) continue;
-        const C cv = band[(da + 1) * G + p];
-        acc = SUB ? cfnma(cv, x[a], acc) : cfma(cv, x[a], acc);
-    }
-    return acc;
-}
 
 // acc[c] (+/-)= sum_a M(p, a) x_c[a] for ncol <= CPT columns (x_c at x + c * xs):
 // the block's row is read into registers once (16 entries at a time, 8 in
 // double precision) and applied to every column.
 template <typename C, int G, int CPT, bool SUB>
 __device__ __forceinline__ void mv_cols(const C* M, int p, const C* x, int xs, int ncol, C (&acc)[CPT]) {
-    constexpr int HB = sizeof(C) == 16 ? 8 : 16;   // entries of the row held at once
+    constexpr int HB = sizeof(C) == 16 ? 8 : 16;
 #pragma unroll
     for (int h = 0; h < G; h += HB) {
         C m[HB];
@@ -429,138 +399,114 @@ __device__ __forceinline__ void mv_cols(const C* M, int p, const C* x, int xs, i
     }
 }
 
-// Walks the chunks of one solve: phases FODD(l), FEVEN(l) for l = 0..L-1, TOP,
-// BODD(l) for l = L-1..1, B0; each phase's rows in chunks of at most rpc rows.
-struct ChunkIter {
-    int ph, r;   // phase index, next row
-};
+// Level-0 off-diagonal block from its bands (band[(da + 1) * G + p] couples
+// layer p to layer p + da, zero outside the slab): acc (+/-)= sum_da band x[p + da].
+template <typename C, int G, bool SUB>
+__device__ __forceinline__ C band_row(const C* band, int p, const C* x, C acc) {
+#pragma unroll
+    for (int da = -1; da <= 1; ++da) {
+        const int a = p + da;
+        if (a < 0 || a >= G) continue;
+        const C cv = band[(da + 1) * G + p];
+        acc = SUB ? cfnma(cv, x[a], acc) : cfma(cv, x[a], acc);
+    }
+    return acc;
+}
 
-template <typename C, int MODE, int NC, int G>
-__device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, int i, int r, int side, int col0,
-                                        int nc_in, C* b, C* tb, C* ring, uint64_t* full, int4* desc,
-                                        unsigned& gch, const CrLv* lv, int L, bool& ok) {
-    const int K = A.n_tot, w = sd.w, ldw = sd.ldw, bs = sd.bs, na = sd.na;
-    constexpr int lw = G;   // ldw == G for every slab this body serves
-    const int nc = NC == 1 ? 1 : nc_in;
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
-    constexpr int GPW = 32 / G;
-    constexpr int CPT = NC >= 2 ? 2 : 1;   // columns per task
-    const int grp = lane / G, p = lane % G;
-    const int ngroups = nw * GPW;
-    const C* F = A.fac + sd.fac_off;
-    const C* cf = A.coef + sd.coef_off;
-    const long long t0off = cr_t0_off(K, bs), p0off = cr_p0_off(K, bs, ldw);
-    const int rowl = nc * lw;   // entries per block row of b
-    C* tg = tb + (size_t)(warp * GPW + grp) * CPT * G;
-    auto row = [&](int k) { return b + (long long)k * rowl; };
-    const long long nt2 = (long long)K * K;
-    constexpr bool kPart = MODE == CR_A || MODE == CR_IF;
-    const int nph = 3 * L + 1;
-    const int maxrows = 2 * ngroups;
-
-    // ---- phase geometry
-    auto phase = [&](int ph, int& kind, int& l, int& ra, int& rb) {
+// The chunk sequence of one solve (host side): phases FODD(l), FEVEN(l) for
+// l = 0..L-1, TOP, BODD(l) for l = L-1..1, B0; each phase's block rows in chunks
+// of at most min(2 x lane groups, stage / row size) rows.
+std::vector<CrChunk> cr_chunk_table(int K, int G, bool part, int stage_ent, int groups) {
+    std::vector<CrChunk> out;
+    const int L = cr_levels(K), bs = G * G;
+    const long long t0 = cr_t0_off(K, bs), p0 = cr_p0_off(K, bs, G);
+    const CrLevelOffs top = cr_level(K, L);
+    for (int ph = 0; ph < 3 * L + 1; ++ph) {
+        int kind, l, rb;
         if (ph < 2 * L) {
             l = ph >> 1;
             kind = (ph & 1) ? PH_FEVEN : PH_FODD;
-            ra = kind == PH_FODD ? lv[l].olo : lv[l].elo;
-            rb = kind == PH_FODD ? lv[l].ohi : lv[l].ehi;
+            const int Kl = cr_level(K, l).K;
+            rb = kind == PH_FODD ? Kl / 2 : (Kl + 1) / 2;
         } else if (ph == 2 * L) {
-            kind = PH_TOP; l = L; ra = 0; rb = 1;
+            kind = PH_TOP; l = L; rb = 1;
         } else if (ph < 3 * L) {
-            kind = PH_BODD; l = 3 * L - ph; ra = 0; rb = lv[l].K >> 1;
+            kind = PH_BODD; l = 3 * L - ph; rb = cr_level(K, l).K / 2;
         } else {
-            kind = PH_B0; l = 0; ra = 0; rb = K >> 1;
+            kind = PH_B0; l = 0; rb = K / 2;
         }
-    };
-    auto row_ent = [&](int kind, int l) -> int {
+        int row;
         switch (kind) {
-            case PH_FODD: return bs;
-            case PH_FEVEN: return l == 0 ? 6 * ldw : 2 * bs;
-            case PH_TOP: return bs;
-            case PH_BODD: return 2 * bs;
-            default: return 6 * ldw + (kPart ? 2 * ldw : bs);
+            case PH_FODD: case PH_TOP: row = bs; break;
+            case PH_FEVEN: row = l == 0 ? 6 * G : 2 * bs; break;
+            case PH_BODD: row = 2 * bs; break;
+            default: row = 6 * G + (part ? 2 * G : bs);
         }
-    };
-    // next chunk of the walk: false when done
-    auto next = [&](ChunkIter& it, int& kind, int& l, int& r0, int& r1) -> bool {
-        while (it.ph < nph) {
-            int ra, rb;
-            phase(it.ph, kind, l, ra, rb);
-            if (it.r < ra) it.r = ra;
-            if (it.r < rb) {
-                const int rpc = max(1, min(maxrows, A.stage_ent / row_ent(kind, l)));
-                r0 = it.r;
-                r1 = min(rb, r0 + rpc);
-                it.r = r1;
-                return true;
+        const int rpc = std::max(1, std::min(2 * groups, stage_ent / row));
+        const CrLevelOffs lv = cr_level(K, l);
+        for (int r0 = 0; r0 < rb; r0 += rpc) {
+            const int r1 = std::min(rb, r0 + rpc), nr = r1 - r0;
+            CrChunk ch{kind, l, r0, r1, 0, 0, 0, 0};
+            switch (kind) {
+                case PH_FODD: ch.src = (lv.dinv + r0) * bs; ch.ent = nr * bs; break;
+                case PH_FEVEN:
+                    if (l == 0) { ch.src = t0 + (long long)r0 * 6 * G; ch.ent = nr * 6 * G; }
+                    else { ch.src = (lv.cbe + 2LL * r0) * bs; ch.ent = 2 * nr * bs; }
+                    break;
+                case PH_TOP: ch.src = top.dinv * bs; ch.ent = bs; break;
+                case PH_BODD: ch.src = (lv.dcdb + 2LL * r0) * bs; ch.ent = 2 * nr * bs; break;
+                default:
+                    ch.src = t0 + ((long long)(K + 1) / 2 + r0) * 6 * G;
+                    ch.ent = nr * 6 * G;
+                    if (part) { ch.src2 = p0 + 2LL * r0 * G; ch.ent2 = 2 * nr * G; }
+                    else { ch.src2 = (cr_level(K, 0).dinv + r0) * bs; ch.ent2 = nr * bs; }
             }
-            ++it.ph;
-            it.r = 0;
+            out.push_back(ch);
         }
-        return false;
-    };
-    auto issue = [&](int kind, int l, int r0, int r1, C* dst, uint64_t* bar) {
-        const int nr = r1 - r0;
-        const C* src;
-        long long ent;
-        const C* src2 = nullptr;
-        long long ent2 = 0;
-        switch (kind) {
-            case PH_FODD: src = F + (lv[l].dinv + r0) * bs; ent = (long long)nr * bs; break;
-            case PH_FEVEN:
-                if (l == 0) { src = F + t0off + (long long)r0 * 6 * ldw; ent = (long long)nr * 6 * ldw; }
-                else { src = F + (lv[l].cbe + 2LL * r0) * bs; ent = 2LL * nr * bs; }
-                break;
-            case PH_TOP: src = F + lv[L].dinv * bs; ent = bs; break;
-            case PH_BODD: src = F + (lv[l].dcdb + 2LL * r0) * bs; ent = 2LL * nr * bs; break;
-            default:
-                src = F + t0off + ((long long)(K + 1) / 2 + r0) * 6 * ldw;
-                ent = (long long)nr * 6 * ldw;
-                if (kPart) { src2 = F + p0off + 2LL * r0 * ldw; ent2 = 2LL * nr * ldw; }
-                else { src2 = F + (lv[0].dinv + r0) * bs; ent2 = (long long)nr * bs; }
-        }
-        mbar_expect_tx(bar, (unsigned)((ent + ent2) * sizeof(C)));
-        tma_load_1d(dst, src, (unsigned)(ent * sizeof(C)), bar);
-        if (ent2) tma_load_1d(dst + ent, src2, (unsigned)(ent2 * sizeof(C)), bar);
-    };
+    }
+    return out;
+}
 
-    // ---- first chunks in flight while the right-hand sides are written.  Only
-    // thread 0 walks the chunk sequence; it publishes each chunk's descriptor
-    // beside its stage (kind -1: no more chunks).
-    ChunkIter pit{0, 0};
-    const unsigned g0 = gch;
-    auto issue_next = [&](unsigned g) {
+template <typename C, int MODE, int G>
+__device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, int i, int r, C* b, C* tb, C* ring,
+                                        uint64_t* full, int4* desc, const CrLv* lv, bool& ok) {
+    const int K = A.n_tot, w = sd.w, bs = sd.bs, na = sd.na;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
+    constexpr int GPW = 32 / G;
+    constexpr int CPT = 1;
+    constexpr int lw = G;
+    const int nc = 1;
+    const int grp = lane / G, p = lane % G;
+    const C* F = A.fac + sd.fac_off;
+    const C* cf = A.coef + sd.coef_off;
+    C* tg = tb + (size_t)(warp * GPW + grp) * G;
+    auto row = [&](int k) { return b + (long long)k * lw; };
+    const long long nt2 = (long long)K * K;
+    constexpr bool kPart = MODE == CR_A;
+    const CrChunk* tab = G == 16 ? A.tab16 : A.tab32;
+    const int ntab = G == 16 ? A.n16 : A.n32;
+
+    // ---- first chunks in flight while the right-hand side is written; thread
+    // 0 publishes each chunk's descriptor beside its stage (kind -1: the end)
+    auto issue_next = [&](int g) {
         const int st = g % A.nst;
-        int kind, l, r0, r1;
-        if (next(pit, kind, l, r0, r1)) {
-            desc[st] = make_int4(kind, l, r0, r1);
-            issue(kind, l, r0, r1, ring + (size_t)st * A.stage_ent, &full[st]);
+        if (g < ntab) {
+            const CrChunk ch = tab[g];
+            desc[st] = make_int4(ch.kind, ch.l, ch.r0, ch.r1);
+            C* dst = ring + (size_t)st * A.stage_ent;
+            mbar_expect_tx(&full[st], (unsigned)((ch.ent + ch.ent2) * (int)sizeof(C)));
+            tma_load_1d(dst, F + ch.src, (unsigned)(ch.ent * sizeof(C)), &full[st]);
+            if (ch.ent2) tma_load_1d(dst + ch.ent, F + ch.src2, (unsigned)(ch.ent2 * sizeof(C)), &full[st]);
         } else {
             desc[st] = make_int4(-1, 0, 0, 0);
         }
     };
     if (tid == 0)
-        for (int s = 0; s < A.nst; ++s) issue_next(g0 + s);
+        for (int st = 0; st < A.nst; ++st) issue_next(st);
 
-    // ---- right-hand sides
-    const int total = K * rowl;
-    if (MODE == CR_IF) {
-        // zeros, then the coupling coefficients H e_j: layer pin, rows j-1..j+1
-        float4* b4 = reinterpret_cast<float4*>(b);
-        const int n4 = total * (int)sizeof(C) / 16;
-        for (int e = tid; e < n4; e += nth) b4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        const int pin = side == 0 ? na : w - 1;
-        for (int e = tid; e < 3 * nc; e += nth) {
-            const int c = e / 3, k = col0 + c + e % 3 - 1;
-            if (k >= 0 && k < K)
-                b[((long long)k * nc + c) * lw + pin] =
-                    cf[(long long)k * sd.cstride + pin * 9 + (side == 0 ? 0 : 6) + (col0 + c - k) + 1];
-        }
-    } else {
-    for (int e = tid; e < total; e += nth) {   // one column: row k = e / lw
+    // ---- right-hand side
+    for (int e = tid; e < K * lw; e += nth) {   // block row k = e / lw
         const int pp = e % lw;
         const int k = e / lw;
         C v = czero<C>();
@@ -583,135 +529,103 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                                 v = cfnma(ck[6 + dk + 1], A.phi[(long long)(i + 1) * vec + (long long)kk * A.R + r], v);
                         }
                 }
-            } else if (MODE == CR_TEST) {
+            } else {
                 if (pp >= na) v = to_c<C>(A.v_in[((long long)r * sd.nl + (pp - na)) * K + k]);
             }
         }
         b[e] = v;
     }
-    }
     __syncthreads();   // b written, first descriptors published
 
     // ---- the chunk walk
-    while (true) {
-        const unsigned g = gch;
+    for (int g = 0;; ++g) {
         const int st = g % A.nst;
         const int4 dsc = desc[st];
         if (dsc.x < 0) break;
-        ++gch;
         const int kind = dsc.x, l = dsc.y, r0 = dsc.z, r1 = dsc.w;
         if (!mbar_wait(&full[st], (g / A.nst) & 1, A.err)) ok = false;
         if (!__syncthreads_and(ok)) { ok = false; return; }
         const C* S = ring + (size_t)st * A.stage_ent;
         const int cnt = r1 - r0;
-        const int ncg = (nc + CPT - 1) / CPT;   // column groups per row
-        const int ntask = cnt * ncg;            // (row, column group) pairs, one per lane group
         const int Kl = lv[l].K;
-        for (int t0 = warp * GPW; t0 < ntask; t0 += nw * GPW) {
-            const int tk = t0 + grp;
-            const bool on = tk < ntask;
-            const int t = on ? tk / ncg : 0, cgi = on ? tk % ncg : 0;
-            const int c0 = cgi * CPT, ncol = on ? min(CPT, nc - c0) : 0;
-            const int rr = r0 + t;
+        for (int t0 = warp * GPW; t0 < cnt; t0 += nw * GPW) {
+            const int t = t0 + grp;
+            const bool on = t < cnt;
+            const int rr = r0 + (on ? t : 0);
             C acc[CPT];
             if (kind == PH_FODD || kind == PH_TOP) {
-                // y_o = D_o^{-1} b_o (top: x_0 = D^{-1} b_0); the group reads its columns first
+                // y_o = D_o^{-1} b_o (top: x_0 = D^{-1} b_0); the group reads its row first
                 const int k = kind == PH_TOP ? 0 : (2 * rr + 1) << l;
-                C* x = row(k) + c0 * lw;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) acc[c] = czero<C>();
-                if (on) mv_cols<C, G, CPT, false>(S + (size_t)t * bs, p, x, lw, ncol, acc);
+                C* x = row(k);
+                acc[0] = czero<C>();
+                if (on) mv_cols<C, G, CPT, false>(S + (size_t)t * bs, p, x, lw, nc, acc);
                 __syncwarp();
-#pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    if (c < ncol) x[c * lw + p] = acc[c];
+                if (on) x[p] = acc[0];
                 __syncwarp();
             } else if (kind == PH_FEVEN) {
                 // b_e -= C_e y_{e-1} + B_e y_{e+1}
                 if (!on) continue;
                 const int e = 2 * rr, k = e << l;
-                C* x = row(k) + c0 * lw;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) acc[c] = c < ncol ? x[c * lw + p] : czero<C>();
+                C* x = row(k);
+                acc[0] = x[p];
                 if (l == 0) {
                     const C* band = S + (size_t)t * 6 * G;
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) {
-                        if (c >= ncol) continue;
-                        if (e >= 1) acc[c] = band_row<C, G, true>(band, p, row(k - 1) + (c0 + c) * lw, acc[c]);
-                        if (e + 1 < Kl) acc[c] = band_row<C, G, true>(band + 3 * G, p, row(k + 1) + (c0 + c) * lw, acc[c]);
-                    }
+                    if (e >= 1) acc[0] = band_row<C, G, true>(band, p, row(k - 1), acc[0]);
+                    if (e + 1 < Kl) acc[0] = band_row<C, G, true>(band + 3 * G, p, row(k + 1), acc[0]);
                 } else {
                     const C* Cm = S + (size_t)2 * t * bs;
-                    if (e >= 1) mv_cols<C, G, CPT, true>(Cm, p, row((e - 1) << l) + c0 * lw, lw, ncol, acc);
-                    if (e + 1 < Kl) mv_cols<C, G, CPT, true>(Cm + bs, p, row((e + 1) << l) + c0 * lw, lw, ncol, acc);
+                    if (e >= 1) mv_cols<C, G, CPT, true>(Cm, p, row((e - 1) << l), lw, nc, acc);
+                    if (e + 1 < Kl) mv_cols<C, G, CPT, true>(Cm + bs, p, row((e + 1) << l), lw, nc, acc);
                 }
-#pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    if (c < ncol) x[c * lw + p] = acc[c];
+                x[p] = acc[0];
             } else if (kind == PH_BODD) {
                 // x_o = y_o - D^{-1}C x_{o-1} - D^{-1}B x_{o+1}
                 if (!on) continue;
                 const int j = 2 * rr + 1, k = j << l;
-                C* x = row(k) + c0 * lw;
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) acc[c] = c < ncol ? x[c * lw + p] : czero<C>();
+                C* x = row(k);
+                acc[0] = x[p];
                 const C* DC = S + (size_t)2 * t * bs;
-                mv_cols<C, G, CPT, true>(DC, p, row((j - 1) << l) + c0 * lw, lw, ncol, acc);
-                if (j + 1 < Kl) mv_cols<C, G, CPT, true>(DC + bs, p, row((j + 1) << l) + c0 * lw, lw, ncol, acc);
-#pragma unroll
-                for (int c = 0; c < CPT; ++c)
-                    if (c < ncol) x[c * lw + p] = acc[c];
+                mv_cols<C, G, CPT, true>(DC, p, row((j - 1) << l), lw, nc, acc);
+                if (j + 1 < Kl) mv_cols<C, G, CPT, true>(DC + bs, p, row((j + 1) << l), lw, nc, acc);
+                x[p] = acc[0];
             } else {
                 // level 0: x_o = y_o - D_o^{-1} (C_o x_{o-1} + B_o x_{o+1})
                 const int k = 2 * rr + 1;
                 const C* band = S + (size_t)t * 6 * G;
-                C tv[CPT];
-#pragma unroll
-                for (int c = 0; c < CPT; ++c) {
-                    tv[c] = czero<C>();
-                    if (c < ncol) {
-                        tv[c] = band_row<C, G, false>(band, p, row(k - 1) + (c0 + c) * lw, tv[c]);
-                        if (k + 1 < Kl) tv[c] = band_row<C, G, false>(band + 3 * G, p, row(k + 1) + (c0 + c) * lw, tv[c]);
-                    }
+                C tv = czero<C>();
+                if (on) {
+                    tv = band_row<C, G, false>(band, p, row(k - 1), tv);
+                    if (k + 1 < Kl) tv = band_row<C, G, false>(band + 3 * G, p, row(k + 1), tv);
                 }
                 const C* Dp = S + (size_t)cnt * 6 * G;
-                C* x = row(k) + c0 * lw;
+                C* x = row(k);
                 if (!kPart) {
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) tg[c * G + p] = tv[c];
+                    tg[p] = tv;
                     __syncwarp();
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c) acc[c] = c < ncol ? x[c * lw + p] : czero<C>();
-                    if (on) mv_cols<C, G, CPT, true>(Dp + (size_t)t * bs, p, tg, G, ncol, acc);
-#pragma unroll
-                    for (int c = 0; c < CPT; ++c)
-                        if (c < ncol) x[c * lw + p] = acc[c];
+                    acc[0] = on ? x[p] : czero<C>();
+                    if (on) mv_cols<C, G, CPT, true>(Dp + (size_t)t * bs, p, tg, G, nc, acc);
+                    if (on) x[p] = acc[0];
                     __syncwarp();
                 } else {
                     // only layers na and w-1: the two rows of D^{-1} against t, reduced over the group
                     const C* pr = Dp + (size_t)t * 2 * G;
                     const C q0 = on ? pr[p] : czero<C>(), q1 = on ? pr[G + p] : czero<C>();
+                    C d0 = q0 * tv, d1 = q1 * tv;
 #pragma unroll
-                    for (int c = 0; c < CPT; ++c) {
-                        C d0 = q0 * tv[c], d1 = q1 * tv[c];
-#pragma unroll
-                        for (int off = G / 2; off > 0; off >>= 1) {
-                            d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
-                            d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
-                            d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
-                            d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
-                        }
-                        if (c < ncol && p == na) x[c * lw + na] = x[c * lw + na] - d0;
-                        if (c < ncol && p == w - 1 && w - 1 != na) x[c * lw + w - 1] = x[c * lw + w - 1] - d1;
+                    for (int off = G / 2; off > 0; off >>= 1) {
+                        d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
+                        d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
+                        d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
+                        d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
                     }
+                    if (on && p == na) x[na] = x[na] - d0;
+                    if (on && p == w - 1 && w - 1 != na) x[w - 1] = x[w - 1] - d1;
                 }
             }
         }
         __syncthreads();   // the stage is free, the phase's rows are written
         if (tid == 0) issue_next(g + A.nst);
     }
-    __syncthreads();   // the last descriptors are read before the next item rewrites them
 
     // ---- outputs
     if (MODE == CR_A) {
@@ -728,132 +642,44 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
             if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
                 A.y[(long long)r * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(row(k)[pp]);
         }
-    } else if (MODE == CR_TEST) {
+    } else {
         const int nl = sd.nl;
         for (int e = tid; e < nl * K; e += nth) {
             const int k = e % K, pp = na + e / K;
             A.w_out[((long long)r * nl + (pp - na)) * K + k] = to_d(row(k)[pp]);
         }
-    } else {
-        const int ns = A.n_slabs;
-        for (int e = tid; e < K * nc; e += nth) {
-            const int c = e % nc, k = e / nc;
-            const long long o = (long long)k * K + col0 + c;
-            const C* rk = row(k) + c * lw;
-            if (side == 0) {
-                A.iface[(0LL * ns + i) * nt2 + o] = rk[w - 1];
-                A.iface[(1LL * ns + i) * nt2 + o] = rk[na];
-            } else {
-                A.iface[(2LL * ns + i) * nt2 + o] = rk[na];
-            }
-        }
     }
 }
 
-// Columns of one interface-map work item for a slab whose block rows have ldw
-// entries, given row_cap entries per block row of b.
-__host__ __device__ inline int cr_if_cols(int NC, int row_cap, int ldw) {
-    return std::min(NC, std::max(1, row_cap / ldw));
-}
-
-template <typename T, int MODE, int NC>
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A) {
     using C = cx<T>;
     __shared__ CrLv lv[33];
-    __shared__ int s_L, s_item[4];
-    __shared__ short s_ldw[MODE == CR_IF ? kMaxIfSlabs : 1];
     __shared__ __align__(8) uint64_t full[4];
     __shared__ int4 desc[4];
     extern __shared__ __align__(128) unsigned char sms[];
     const int K = A.n_tot;
-    C* b = A.bsm ? reinterpret_cast<C*>(sms) : nullptr;
     C* tb = reinterpret_cast<C*>(sms) + (A.bsm ? A.bstride : 0);
-    C* ring = tb + (size_t)kSolveThreads * (NC >= 2 ? 2 : 1);
+    C* ring = tb + (size_t)kSolveThreads;
     if (threadIdx.x == 0) {
         const int L = cr_levels(K);
-        int lo = 0, hi = K - 1;
         for (int l = 0; l <= L; ++l) {
             const CrLevelOffs o = cr_level(K, l);
-            CrLv v;
-            v.K = o.K; v.dinv = o.dinv; v.cbe = o.cbe; v.dcdb = o.dcdb;
-            v.olo = v.ohi = v.elo = v.ehi = 0;
-            if (l < L) {
-                const int j0 = lo | 1, j1 = min(hi, o.K - 1);
-                if (j0 <= j1) { v.olo = j0 >> 1; v.ohi = (j1 >> 1) + ((j1 & 1) ? 1 : 0); }
-                int e0 = max(0, lo - 1);
-                e0 += e0 & 1;
-                const int e1 = min(o.K - 1, hi + 1);
-                if (e0 <= e1) { v.elo = e0 >> 1; v.ehi = (e1 >> 1) + 1; lo = e0 >> 1; hi = e1 >> 1; }
-                else { lo = 1; hi = 0; }
-            }
-            lv[l] = v;
+            lv[l] = CrLv{o.K, o.dinv, o.cbe, o.dcdb};
         }
-        s_L = L;
-        for (int s = 0; s < A.nst; ++s) mbar_init(&full[s], 1);
+        for (int st = 0; st < A.nst; ++st) mbar_init(&full[st], 1);
         fence_mbar_init();
     }
     bool ok = true;
-    unsigned gch = 0;
-    if (MODE != CR_IF) {
-        __syncthreads();
-        int i, r;
-        long long cta;
-        if (MODE == CR_TEST) { i = A.slab; r = blockIdx.x; cta = blockIdx.x; }
-        else { i = blockIdx.x; r = blockIdx.y; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
-        const SlabDev sd = A.slabs[i];
-        if (!A.bsm) b = A.bg + cta * A.bstride;
-        if (sd.w <= 16) cr_body<C, MODE, 1, 16>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, desc, gch, lv, s_L, ok);
-        else cr_body<C, MODE, 1, 32>(A, sd, i, r, 0, 0, 1, b, tb, ring, full, desc, gch, lv, s_L, ok);
-    } else {
-        if (!A.bsm) b = A.bg + (long long)blockIdx.x * A.bstride;
-        const bool ldw_sm = A.n_slabs <= kMaxIfSlabs;
-        if (ldw_sm)
-            for (int ii = threadIdx.x; ii < A.n_slabs; ii += blockDim.x) s_ldw[ii] = (short)A.slabs[ii].ldw;
-        for (int item = blockIdx.x; item < A.nitems && ok; item += gridDim.x) {
-            __syncthreads();   // the previous item is finished with b and s_item
-            if (threadIdx.x == 0) {
-                // items: side 0 for slabs 1..l-1, then side 1 for slabs 1..l-2; each
-                // slab's n_tot columns in chunks of cr_if_cols columns
-                int t = item, side = -1, i = 0, col0 = 0, nc = 0;
-                for (int s2 = 0; s2 < 2 && side < 0; ++s2) {
-                    const int iend = s2 == 0 ? A.n_slabs - 1 : A.n_slabs - 2;
-                    for (int ii = 1; ii <= iend; ++ii) {
-                        const int ncs = cr_if_cols(NC, A.row_cap, ldw_sm ? (int)s_ldw[ii] : A.slabs[ii].ldw);
-                        const int nch = (K + ncs - 1) / ncs;
-                        if (t < nch) {
-                            side = s2; i = ii; col0 = t * ncs; nc = min(ncs, K - col0);
-                            break;
-                        }
-                        t -= nch;
-                    }
-                }
-                s_item[0] = side; s_item[1] = i; s_item[2] = col0; s_item[3] = nc;
-            }
-            __syncthreads();
-            const int side = s_item[0], i = s_item[1], col0 = s_item[2], nc = s_item[3];
-            if (side < 0) break;
-            const SlabDev sd = A.slabs[i];
-            // the sparse forward ranges depend on the item's columns
-            if (threadIdx.x == 0) {
-                int lo = max(0, col0 - 1), hi = min(K - 1, col0 + nc);
-                for (int l = 0; l < s_L; ++l) {
-                    const int Kl = lv[l].K;
-                    const int j0 = lo | 1, j1 = min(hi, Kl - 1);
-                    lv[l].olo = lv[l].ohi = 0;
-                    if (j0 <= j1) { lv[l].olo = j0 >> 1; lv[l].ohi = (j1 >> 1) + ((j1 & 1) ? 1 : 0); }
-                    int e0 = max(0, lo - 1);
-                    e0 += e0 & 1;
-                    const int e1 = min(Kl - 1, hi + 1);
-                    lv[l].elo = lv[l].ehi = 0;
-                    if (e0 <= e1) { lv[l].elo = e0 >> 1; lv[l].ehi = (e1 >> 1) + 1; lo = e0 >> 1; hi = e1 >> 1; }
-                    else { lo = 1; hi = 0; }
-                }
-            }
-            __syncthreads();
-            if (sd.w <= 16) cr_body<C, CR_IF, NC, 16>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, desc, gch, lv, s_L, ok);
-            else cr_body<C, CR_IF, NC, 32>(A, sd, i, 0, side, col0, nc, b, tb, ring, full, desc, gch, lv, s_L, ok);
-        }
-    }
+    __syncthreads();
+    int i, r;
+    long long cta;
+    if (MODE == CR_TEST) { i = A.slab; r = blockIdx.x; cta = blockIdx.x; }
+    else { i = blockIdx.x; r = blockIdx.y; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
+    const SlabDev sd = A.slabs[i];
+    C* b = A.bsm ? reinterpret_cast<C*>(sms) : A.bg + cta * A.bstride;
+    if (sd.w <= 16) cr_body<C, MODE, 16>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
+    else cr_body<C, MODE, 32>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
     if (!ok && threadIdx.x == 0) {
         // a wait expired: give the copies already issued a bounded chance to land
         const long long t0 = clock64();
@@ -1206,6 +1032,12 @@ CrArgs<C> base_args(lss_ctx* c) {
     return A;
 }
 
+struct CrArgsTables {
+    void* t16;
+    void* t32;
+    int n16, n32;
+};
+
 // Shared-memory plan of a solve launch: right-hand sides (bb bytes, in shared
 // memory when they fit), per-group scratch (tb bytes) and the factor ring.
 struct SolvePlan {
@@ -1235,17 +1067,50 @@ bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, Solve
     return false;
 }
 
+// Chunk tables (16- and 32-wide blocks) of one output kind and stage size,
+// built and uploaded on first use.
+int chunk_tables(lss_ctx* c, bool part, int stage_ent, CrArgsTables* out) {
+    for (size_t q = 0; q < c->chunk_keys.size(); ++q)
+        if (c->chunk_keys[q][0] == (part ? 1 : 0) && c->chunk_keys[q][1] == stage_ent) {
+            out->t16 = c->chunk_dev[2 * q];
+            out->t32 = c->chunk_dev[2 * q + 1];
+            out->n16 = (int)c->chunk_keys[q][2];
+            out->n32 = (int)c->chunk_keys[q][3];
+            return LSS_OK;
+        }
+    const std::vector<CrChunk> t16 = cr_chunk_table(c->n_tot, 16, part, stage_ent, kSolveThreads / 16);
+    const std::vector<CrChunk> t32 = cr_chunk_table(c->n_tot, 32, part, stage_ent, kSolveThreads / 32);
+    void* d16 = nullptr;
+    void* d32 = nullptr;
+    cudaError_t e = cudaMalloc(&d16, t16.size() * sizeof(CrChunk));
+    if (!e) e = cudaMalloc(&d32, t32.size() * sizeof(CrChunk));
+    if (!e) e = cudaMemcpy(d16, t16.data(), t16.size() * sizeof(CrChunk), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(d32, t32.data(), t32.size() * sizeof(CrChunk), cudaMemcpyHostToDevice);
+    if (e) {
+        if (d16) cudaFree(d16);
+        if (d32) cudaFree(d32);
+        return lss_check_cuda(c, e, "chunk tables");
+    }
+    c->chunk_keys.push_back({part ? 1LL : 0LL, (long long)stage_ent, (long long)t16.size(), (long long)t32.size()});
+    c->chunk_dev.push_back(d16);
+    c->chunk_dev.push_back(d32);
+    out->t16 = d16;
+    out->t32 = d32;
+    out->n16 = (int)t16.size();
+    out->n32 = (int)t32.size();
+    return LSS_OK;
+}
+
 // Launches the slab-solve kernel with per_cta complex entries of right-hand
 // sides per CTA: in shared memory when they fit (and no fixed scratch is
 // given), else in global scratch (the fixed array `scratch`, or the context's
-// growable buffer).  items > 0 makes the grid persistent: as many CTAs as fit
-// on the GPU at once, at most items.
-template <typename T, int MODE, int NC>
-int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, int items, void* scratch,
-                 size_t scratch_bytes, cudaStream_t s) {
+// growable buffer).
+template <typename T, int MODE>
+int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void* scratch, size_t scratch_bytes,
+                 cudaStream_t s) {
     using C = cx<T>;
-    auto kern = cr_solve_kernel<T, MODE, NC>;
-    const size_t tb = sizeof(C) * (size_t)kSolveThreads * (NC >= 2 ? 2 : 1);
+    auto kern = cr_solve_kernel<T, MODE>;
+    const size_t tb = sizeof(C) * (size_t)kSolveThreads;
     const size_t bb = sizeof(C) * (size_t)per_cta;
     SolvePlan P;
     if (!plan_solve<C>(c, bb, tb, scratch == nullptr, &P))
@@ -1254,21 +1119,16 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, int 
     A.bsm = P.bsm;
     A.nst = P.nst;
     A.stage_ent = P.stage_ent;
-    static size_t cfg = 0;
-    int rc = set_smem(c, kern, P.sh, &cfg);
+    CrArgsTables tabs;
+    int rc = chunk_tables(c, MODE == CR_A, P.stage_ent, &tabs);
     if (rc) return rc;
-    if (items > 0) {
-        static size_t occ_sh = 0;
-        static int occ = 0;
-        if (occ_sh != P.sh || !occ) {
-            int per = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSolveThreads, P.sh);
-            if (e) return lss_check_cuda(c, e, "slab solve occupancy");
-            occ = std::max(1, per);
-            occ_sh = P.sh;
-        }
-        grid = dim3((unsigned)std::min<long long>(items, (long long)occ * c->num_sms));
-    }
+    A.tab16 = (const CrChunk*)tabs.t16;
+    A.tab32 = (const CrChunk*)tabs.t32;
+    A.n16 = tabs.n16;
+    A.n32 = tabs.n32;
+    static size_t cfg = 0;
+    rc = set_smem(c, kern, P.sh, &cfg);
+    if (rc) return rc;
     if (!A.bsm) {
         const size_t need = bb * (size_t)grid.x * grid.y;
         if (scratch) {
@@ -1288,35 +1148,30 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, int 
     return lss_check_cuda(c, cudaGetLastError(), "slab solve launch");
 }
 
-// Interface maps with NC columns per item; *used = false when b does not fit
-// in shared memory at this NC (the caller tries a smaller one).
-template <typename T, int NC>
-int launch_iface(lss_ctx* c, cudaStream_t s, bool* used) {
+// Chunk tables of every solve plan the entry points can use (right-hand sides
+// in shared or in global memory, all layers or first/last only), built at
+// factorization so that no later call allocates.
+template <typename T>
+int prepare_chunk_tables(lss_ctx* c) {
     using C = cx<T>;
-    const int K = c->n_tot;
-    const int row_cap = std::max(NC * 16, ldwmax_of(c));
-    SolvePlan P;
-    *used = NC == 1 || (plan_solve<C>(c, sizeof(C) * (size_t)K * row_cap,
-                                      sizeof(C) * (size_t)kSolveThreads * (NC >= 2 ? 2 : 1), true, &P) && P.bsm);
-    if (!*used) return LSS_OK;
-    int nitems = 0;
-    for (int side = 0; side < 2; ++side) {
-        const int iend = side == 0 ? c->n_slabs - 1 : c->n_slabs - 2;
-        for (int i = 1; i <= iend; ++i) {
-            const int ncs = cr_if_cols(NC, row_cap, c->slabs[i].ldw);
-            nitems += (K + ncs - 1) / ncs;
+    const size_t tb = sizeof(C) * (size_t)kSolveThreads;
+    const size_t bb = sizeof(C) * (size_t)c->n_tot * ldwmax_of(c);
+    for (int smem_b = 0; smem_b < 2; ++smem_b) {
+        SolvePlan P;
+        if (!plan_solve<C>(c, bb, tb, smem_b == 1, &P)) continue;
+        for (int part = 0; part < 2; ++part) {
+            CrArgsTables t;
+            const int rc = chunk_tables(c, part == 1, P.stage_ent, &t);
+            if (rc) return rc;
         }
     }
-    CrArgs<C> A = base_args<C>(c);
-    A.iface = (C*)c->iface;
-    A.nitems = nitems;
-    A.row_cap = row_cap;
-    ProfScope ps(c, s, LSS_PROF_IFACE, 1);
-    return launch_solve<T, CR_IF, NC>(c, A, dim3(1), (long long)K * row_cap, nitems, nullptr, 0, s);
+    return LSS_OK;
 }
 
 template <typename T>
 int factor_impl(lss_ctx* c, cudaStream_t s) {
+    int rc0 = prepare_chunk_tables<T>(c);
+    if (rc0) return rc0;
     using C = cx<T>;
     const int K0 = c->n_tot, ns = c->n_slabs, nlev = cr_levels(K0);
     const int wmax = wmax_of(c);
@@ -1529,14 +1384,14 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     if (c->n_slabs > 1) {
         {
             ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
-            rc = launch_solve<T, CR_A, 1>(c, A, grid, per_cta, 0, nullptr, 0, s);
+            rc = launch_solve<T, CR_A>(c, A, grid, per_cta, nullptr, 0, s);
         }
         if (rc) return rc;
         rc = launch_recur<T>(c, (const C*)c->iface, lam, phi, A.a_first, A.a_last, R, s);
         if (rc) return rc;
     }
     ProfScope ps(c, s, LSS_PROF_SLAB_E, 1);
-    return launch_solve<T, CR_E, 1>(c, A, grid, per_cta, 0, nullptr, 0, s);
+    return launch_solve<T, CR_E>(c, A, grid, per_cta, nullptr, 0, s);
 }
 
 template <typename T>
@@ -1549,9 +1404,9 @@ int slab_apply_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, v
     A.v_in = v;
     A.w_out = w;
     const long long per_cta = (long long)c->n_tot * ldwmax_of(c);
-    if (scratch) return launch_solve<T, CR_TEST, 1>(c, A, dim3(R), per_cta, 0, scratch, scratch_bytes, s);
+    if (scratch) return launch_solve<T, CR_TEST>(c, A, dim3(R), per_cta, scratch, scratch_bytes, s);
     ProfScope ps(c, s, LSS_PROF_SLAB_E, 1);
-    return launch_solve<T, CR_TEST, 1>(c, A, dim3(R), per_cta, 0, nullptr, 0, s);
+    return launch_solve<T, CR_TEST>(c, A, dim3(R), per_cta, nullptr, 0, s);
 }
 
 }  // namespace
