@@ -316,7 +316,67 @@ def run_ours(args, rank, world):
         res["e2e"] = {"value": (R * args.steps * world) / (e2e_ms / 1e3), "unit": "solves/s",
                       "h2d_bytes_per_step": int(n * n * 8 + R * 16), "d2h_bytes_per_step": int(R * n * n * 16)}
         results[prec_name] = res
+    if args.batched and "mixed" in results:
+        results["batched"] = run_batched(args, dev, world)
     return w, R, results
+
+
+def run_batched(args, dev, world):
+    """Form (2), batching: the same medium with R plane waves per solve call, in
+    mixed precision (set-up + factor + R-RHS solve per step); against it the
+    plain FP64 arm above solves one right-hand side per call."""
+    import torch
+    from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED, LSSolver
+    wb, m, dirs = workload_cfg(args.batched)
+    R = dirs.shape[0]
+    mt = torch.tensor(m, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts = GmresOptions(30, 1e-8, 300)
+    solver = LSSolver(wb.n, wb.omega, mt, b_pml=wb.b_pml, b_slab=wb.b_slab, precision=LSS_MIXED, factor=False)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        solver.set_medium(mt)
+        solver.factor()
+        g = solver.plane_wave_rhs(dirs)
+        return solver.solve(g, opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    total = 0.0
+    stats = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = step()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+        stats.append(st)
+    g = solver.plane_wave_rhs(dirs)
+    solve_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.solve(g, opts)
+        e1.record(stream)
+        e1.synchronize()
+        solve_ms += e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([total, solve_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total, solve_ms = (float(x) for x in t.tolist())
+    relres = max(s["relres_true"] for st in stats for s in st)
+    return {"workload": args.batched, "R": R, "value": R * args.steps * world / (total / 1e3),
+            "unit": "solves/s", "ms_per_step": total / args.steps,
+            "solve_only": {"value": R * args.steps * world / (solve_ms / 1e3), "ms_per_solve_call": solve_ms / args.steps},
+            "iters_mean": float(np.mean([s["iters"] for st in stats for s in st])), "relres_true_max": relres,
+            "converged": all(s["relres_true"] <= 1e-8 for st in stats for s in st)}
 
 
 def roofline(res, hbm_peak, hbm_src):
@@ -377,6 +437,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", default="2d_n256_r16",
+                    help="workload of the batched mixed-precision line ('' to skip)")
     ap.add_argument("--arms", default="mixed,fp64",
                     help="precisions to run (mixed first; the JSON line needs both, profiling may take one)")
     args = ap.parse_args()
@@ -444,6 +506,10 @@ def main():
                        "solve_only": f64["solve_only"], "setup_factor_ms": f64["setup_factor_ms"],
                        "breakdown_ms": f64["prof_ms"], "clocks": f64["clocks"]},
         "mixed_over_fp64": mix["value"] / f64["value"],
+        "batched": (dict(results["batched"], vs_plain_fp64=results["batched"]["value"] / f64["value"],
+                         solve_only_vs_plain_fp64=results["batched"]["solve_only"]["value"]
+                         / f64["solve_only"]["value"])
+                    if "batched" in results else None),
         "breakdown_ms": mix["prof_ms"], "launches_per_step": mix["prof_launches"],
     }
     print(json.dumps(line))
