@@ -16,8 +16,9 @@
 //   Lambda_i[k][j] = sum_{j'} W_last[k][j'] H(j', j),  Gamma_i with W_first,
 //   Phi_i with W_first and H_{[i,i+1]}.
 // One launch per phase covers every slab and side: grid (column tiles, block
-// rows of the level, problems); lane p of a column group owns layer p.  The column blocks live in a scratch array
-// X[problem][k][j][layer] (n_tot x n_tot x G entries per problem).
+// rows of the level, problems); lane p of a column group owns layer p.  The
+// column blocks live in a scratch array X[problem][k][j][layer] (n_tot x n_tot
+// x G entries per problem).
 #include <algorithm>
 #include <vector>
 
