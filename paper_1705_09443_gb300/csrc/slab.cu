@@ -208,6 +208,138 @@ __global__ void __launch_bounds__(32 * kGjWarps) cr_gj_kernel(const SlabDev* __r
     }
 }
 
+// Level 0's odd rows: A, C and B are tridiagonal in the layer index (the
+// stencil couplings), so D^{-1} = A^{-1}, D^{-1}C and D^{-1}B come from one LU
+// factorization of the tridiagonal A with partial pivoting (a row is exchanged
+// with the next one when the subdiagonal entry is the larger; U then has a
+// second superdiagonal) and 3w column solves: O(w^2) work instead of the O(w^3)
+// of Gauss-Jordan.  One warp per odd row: lane 0 factors A into shared memory,
+// every lane solves right-hand-side columns of [I | C | B] in registers.
+constexpr int kGj0Warps = 4;
+
+template <typename T>
+struct Gt0Sm {
+    cx<T> d[32], dl[32], du[32], du2[32];
+    int piv[32];
+};
+
+template <typename T, int G>
+__device__ void gj0_body(const SlabDev& sd, const cx<T>* __restrict__ coef, cx<T>* __restrict__ fac,
+                         cx<T>* __restrict__ work, int K0, int o, Gt0Sm<T>& sm, int* err) {
+    using C = cx<T>;
+    const int lane = threadIdx.x & 31;
+    const int w = sd.w, bs = G * G, na = sd.na;
+    const int j = 2 * o + 1;
+    const C* ck = coef + sd.coef_off + (long long)j * sd.cstride;   // row p at ck + 9p, entry (da+1)*3 + (dk+1)
+    const bool hasB = j + 1 < K0;
+    if (lane == 0) {
+        for (int p = 0; p < w; ++p) {
+            sm.d[p] = ck[p * 9 + 4];
+            sm.du[p] = p + 1 < w ? ck[p * 9 + 7] : czero<C>();        // A(p, p+1)
+            sm.dl[p] = p + 1 < w ? ck[(p + 1) * 9 + 1] : czero<C>();  // A(p+1, p)
+            sm.du2[p] = czero<C>();
+            sm.piv[p] = 0;
+        }
+        bool sing = false;
+        for (int i = 0; i + 1 < w; ++i) {
+            if (cabs2(sm.d[i]) >= cabs2(sm.dl[i])) {
+                if (!(cabs2(sm.d[i]) > T(0))) { sing = true; sm.d[i] = czero<C>(); sm.d[i].x = T(1); }
+                const C f = sm.dl[i] * crecip(sm.d[i]);
+                sm.dl[i] = f;
+                sm.d[i + 1] = cfnma(f, sm.du[i], sm.d[i + 1]);
+            } else {
+                const C f = sm.d[i] * crecip(sm.dl[i]);
+                sm.d[i] = sm.dl[i];
+                sm.dl[i] = f;
+                const C t = sm.du[i];
+                sm.du[i] = sm.d[i + 1];
+                sm.d[i + 1] = cfnma(f, sm.d[i + 1], t);
+                sm.piv[i] = 1;
+                if (i + 2 < w) {
+                    sm.du2[i] = sm.du[i + 1];
+                    sm.du[i + 1] = mk(-f.x, -f.y) * sm.du[i + 1];
+                }
+            }
+        }
+        for (int i = 0; i < w; ++i) {
+            if (!(cabs2(sm.d[i]) > T(0)) || !isfinite(cabs2(sm.d[i]))) { sing = true; sm.d[i] = czero<C>(); sm.d[i].x = T(1); }
+            sm.d[i] = crecip(sm.d[i]);   // reciprocals of U's diagonal
+        }
+        if (sing) atomicOr(err, LSS_DERR_SINGULAR);
+    }
+    __syncwarp();
+    C* Dout = fac + sd.fac_off + (cr_level(K0, 0).dinv + o) * bs;
+    C* DCw = work + sd.work_off + (3LL * K0 + 2LL * o) * bs;
+    C* P0 = fac + sd.fac_off + cr_p0_off(K0, bs, G) + 2LL * o * G;
+    for (int q = lane; q < 3 * G; q += 32) {
+        const int blk = q / G, a = q % G;   // block 0: D^{-1}, 1: D^{-1}C, 2: D^{-1}B; column a
+        C* out = blk == 0 ? Dout + a * G : DCw + (blk - 1) * bs + a * G;
+        C b[G];
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+            C v = czero<C>();
+            if (a < w && p < w) {
+                if (blk == 0) {
+                    if (p == a) v.x = T(1);
+                } else if (p >= a - 1 && p <= a + 1 && (blk == 1 || hasB)) {
+                    v = ck[p * 9 + (a - p + 1) * 3 + (blk == 1 ? 0 : 2)];   // C(p, a) or B(p, a)
+                }
+            }
+            b[p] = v;
+        }
+        if (a < w) {
+#pragma unroll
+            for (int i = 0; i + 1 < G; ++i) {   // L, with the row exchanges
+                if (i + 1 < w) {
+                    if (sm.piv[i]) {
+                        const C t = b[i];
+                        b[i] = b[i + 1];
+                        b[i + 1] = cfnma(sm.dl[i], b[i], t);
+                    } else {
+                        b[i + 1] = cfnma(sm.dl[i], b[i], b[i + 1]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = G - 1; i >= 0; --i) {   // U: diagonal, superdiagonal, second superdiagonal
+                if (i < w) {
+                    C v = b[i];
+                    if (i + 1 < G && i + 1 < w) v = cfnma(sm.du[i], b[i + 1], v);
+                    if (i + 2 < G && i + 2 < w) v = cfnma(sm.du2[i], b[i + 2], v);
+                    b[i] = v * sm.d[i];
+                }
+            }
+        }
+        C v_first = czero<C>(), v_last = czero<C>();   // rows na and w-1 (selected, not indexed)
+#pragma unroll
+        for (int p = 0; p < G; ++p) {
+            const C v = (a < w && p < w) ? b[p] : czero<C>();
+            out[p] = v;
+            if (p == na) v_first = v;
+            if (p == w - 1) v_last = v;
+        }
+        if (blk == 0) {   // rows na and w-1 of D^{-1}, column a
+            P0[a] = v_first;
+            P0[G + a] = v_last;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kGj0Warps) cr_gj0_kernel(const SlabDev* __restrict__ slabs,
+                                                                const cx<T>* __restrict__ coef,
+                                                                cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
+                                                                int K0, int per_slab, int n_slabs, int* err) {
+    __shared__ Gt0Sm<T> sm[kGj0Warps];
+    const int warp = threadIdx.x >> 5;
+    const int task = blockIdx.x * kGj0Warps + warp;
+    if (task >= per_slab * n_slabs) return;   // the whole warp leaves
+    const SlabDev sd = slabs[task / per_slab];
+    const int o = task % per_slab;
+    if (sd.w <= 16) gj0_body<T, 16>(sd, coef, fac, work, K0, o, sm[warp], err);
+    else gj0_body<T, 32>(sd, coef, fac, work, K0, o, sm[warp], err);
+}
+
 // Even rows of level l: A'_e, C'_e, B'_e of level l+1 from D^{-1}C and D^{-1}B
 // of the neighbouring odd rows, into the other work parity (and, for the even
 // rows of level l+1, C' and B' into the factors).  One warp per block row; C_e
@@ -279,30 +411,47 @@ __global__ void __launch_bounds__(32 * kEvWarps) cr_even_kernel(const SlabDev* _
                 if (a < w) acc = cfma(Lrow[a], R[a], acc);
             return acc;
         };
+        // Out[p] -= (L R)[p] for every p, L staged row-major; at level 0 L is
+        // tridiagonal (the stencil couplings), so only the band is summed
+        auto sub_product = [&](const C* L, C* Out) {
+            if (l == 0) {
+#pragma unroll
+                for (int pp = 0; pp < 32; ++pp) {
+                    if (pp >= w) break;
+                    C v = czero<C>();
+#pragma unroll
+                    for (int da = -1; da <= 1; ++da)
+                        if (pp + da >= 0 && pp + da < 32 && pp + da < w) v = cfma(L[pp * LS + pp + da], R[pp + da], v);
+                    Out[pp] = Out[pp] - v;
+                }
+            } else {
+                for (int pp = 0; pp < w; ++pp) Out[pp] = Out[pp] - dot(L + pp * LS);
+            }
+        };
         C* Acol = An + (long long)q * ldw;
         for (int p = 0; p < ldw; ++p) Acol[p] = p < w ? Ae[(long long)q * ldw + p] : czero<C>();
         if (hasL) {
             load_col(DCm + bs);   // D^{-1}B of row e-1
-            for (int p = 0; p < w; ++p) Acol[p] = Acol[p] - dot(L0 + p * LS);
+            sub_product(L0, Acol);
         }
         if (hasR) {
             load_col(DCp);        // D^{-1}C of row e+1
-            for (int p = 0; p < w; ++p) Acol[p] = Acol[p] - dot(L1 + p * LS);
+            sub_product(L1, Acol);
         }
         if (next_cb) {
             C* Ccol = Cn + (long long)q * ldw;
             C* Bcol = Bn + (long long)q * ldw;
+            for (int p = 0; p < w; ++p) {
+                Ccol[p] = czero<C>();
+                Bcol[p] = czero<C>();
+            }
             if (hasL) {
                 load_col(DCm);    // D^{-1}C of row e-1
-                for (int p = 0; p < w; ++p) { const C v = dot(L0 + p * LS); Ccol[p] = mk(-v.x, -v.y); }
-            } else {
-                for (int p = 0; p < w; ++p) Ccol[p] = czero<C>();
+                sub_product(L0, Ccol);
             }
             if (hasR) {
                 load_col(DCp + bs);   // D^{-1}B of row e+1
-                for (int p = 0; p < w; ++p) { const C v = dot(L1 + p * LS); Bcol[p] = mk(-v.x, -v.y); }
-            } else {
-                for (int p = 0; p < w; ++p) Bcol[p] = czero<C>();
+                sub_product(L1, Bcol);
             }
             for (int p = w; p < ldw; ++p) { Ccol[p] = czero<C>(); Bcol[p] = czero<C>(); }
             if (Cf) {
@@ -1190,8 +1339,12 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
         for (int l = 0; l < nlev; ++l) {
             const int K = cr_level(K0, l).K;
             const int nodd = K / 2, nev = (K + 1) / 2;
-            cr_gj_kernel<T><<<(nodd * ns + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg, s>>>(
-                c->d_slabs, fac, work, c->work_len, K0, l, nodd, ns, 0, rs, c->d_err);
+            if (l == 0)
+                cr_gj0_kernel<T><<<(nodd * ns + kGj0Warps - 1) / kGj0Warps, 32 * kGj0Warps, 0, s>>>(
+                    c->d_slabs, (const C*)c->coef, fac, work, K0, nodd, ns, c->d_err);
+            else
+                cr_gj_kernel<T><<<(nodd * ns + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg, s>>>(
+                    c->d_slabs, fac, work, c->work_len, K0, l, nodd, ns, 0, rs, c->d_err);
             cr_even_kernel<T><<<(nev * ns + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she, s>>>(
                 c->d_slabs, fac, work, c->work_len, K0, l, nev, ns, nlev);
         }
