@@ -562,6 +562,26 @@ __device__ __forceinline__ C band_row(const C* band, int p, const C* x, C acc) {
     return acc;
 }
 
+// Partial product sum_{a0 <= a < a0 + N} M(p, a) x[a] of one block row (M
+// column-major G x G in shared memory).
+template <typename C, int G, int N>
+__device__ __forceinline__ C mv_part(const C* M, int p, const C* x, int a0) {
+    C s0 = czero<C>(), s1 = czero<C>();
+#pragma unroll
+    for (int u = 0; u < N; u += 2) {
+        s0 = cfma(M[(a0 + u) * G + p], x[a0 + u], s0);
+        s1 = cfma(M[(a0 + u + 1) * G + p], x[a0 + u + 1], s1);
+    }
+    return s0 + s1;
+}
+
+// Phases whose 32-wide block rows are split over four warps, and the most
+// block rows such a chunk holds (4 x 6 warp tasks: two per warp)
+constexpr int kSplitRows = 6;
+__host__ __device__ __forceinline__ bool cr_split_phase(int G, int kind, int l, bool part) {
+    return G == 32 && !(kind == PH_FEVEN && l == 0) && !(kind == PH_B0 && part);
+}
+
 // The chunk sequence of one solve (host side): phases FODD(l), FEVEN(l) for
 // l = 0..L-1, TOP, BODD(l) for l = L-1..1, B0; each phase's block rows in chunks
 // of at most min(2 x lane groups, stage / row size) rows.
@@ -591,7 +611,8 @@ std::vector<CrChunk> cr_chunk_table(int K, int G, bool part, int stage_ent, int 
             case PH_BODD: row = 2 * bs; break;
             default: row = 6 * G + (part ? 2 * G : bs);
         }
-        const int rpc = std::max(1, std::min(2 * groups, stage_ent / row));
+        int rpc = std::max(1, std::min(2 * groups, stage_ent / row));
+        if (cr_split_phase(G, kind, l, part)) rpc = std::min(rpc, kSplitRows);
         const CrLevelOffs lv = cr_level(K, l);
         for (int r0 = 0; r0 < rb; r0 += rpc) {
             const int r1 = std::min(rb, r0 + rpc), nr = r1 - r0;
@@ -697,6 +718,57 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         const C* S = ring + (size_t)st * A.stage_ent;
         const int cnt = r1 - r0;
         const int Kl = lv[l].K;
+        // 32-wide blocks: only a few block rows fit a stage, so each row's
+        // products are split over four warps (column quarters, or block x half
+        // of the columns in the two-block phases) and the partial sums meet in
+        // shared memory after one more barrier
+        const bool split = cr_split_phase(G, kind, l, kPart);
+        if (split) {
+            C* part = tb + kSolveThreads;   // kSplitRows x 4 x 32 partial sums
+            for (int t0 = warp; t0 < cnt * 4; t0 += nw) {   // one warp per (row, part); G == 32
+                const int t = t0 >> 2, qs = t0 & 3;
+                const int rr = r0 + t;
+                C acc = czero<C>();
+                if (kind == PH_FODD || kind == PH_TOP) {
+                    const int k = kind == PH_TOP ? 0 : (2 * rr + 1) << l;
+                    acc = mv_part<C, G, 8>(S + (size_t)t * bs, p, row(k), qs * 8);
+                } else if (kind == PH_FEVEN || kind == PH_BODD) {
+                    const int blk = qs >> 1, half = qs & 1;
+                    const int j = kind == PH_FEVEN ? 2 * rr : 2 * rr + 1;
+                    const int nb = blk == 0 ? j - 1 : j + 1;
+                    if (nb >= 0 && nb < Kl)
+                        acc = mv_part<C, G, 16>(S + (size_t)(2 * t + blk) * bs, p, row(nb << l), half * 16);
+                } else {   // level 0, all layers: t = C x_{k-1} + B x_{k+1}, then a quarter of D^{-1} t
+                    const int k = 2 * rr + 1;
+                    const C* band = S + (size_t)t * 6 * G;
+                    C tv = band_row<C, G, false>(band, p, row(k - 1), czero<C>());
+                    if (k + 1 < Kl) tv = band_row<C, G, false>(band + 3 * G, p, row(k + 1), tv);
+                    const C* D = S + (size_t)cnt * 6 * G + (size_t)t * bs;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int a = qs * 8 + u;
+                        C ta;
+                        ta.x = __shfl_sync(0xffffffffu, tv.x, a);
+                        ta.y = __shfl_sync(0xffffffffu, tv.y, a);
+                        acc = cfma(D[a * G + p], ta, acc);
+                    }
+                }
+                part[(t * 4 + qs) * 32 + p] = acc;
+            }
+            __syncthreads();
+            for (int t = warp; t < cnt; t += nw) {
+                const int rr = r0 + t;
+                int k;
+                if (kind == PH_TOP) k = 0;
+                else if (kind == PH_FEVEN) k = (2 * rr) << l;
+                else if (kind == PH_B0) k = 2 * rr + 1;
+                else k = (2 * rr + 1) << l;
+                const C* pt = part + t * 4 * 32 + p;
+                const C sum = (pt[0] + pt[32]) + (pt[64] + pt[96]);
+                C* x = row(k);
+                x[p] = (kind == PH_FODD || kind == PH_TOP) ? sum : x[p] - sum;
+            }
+        } else
         for (int t0 = warp * GPW; t0 < cnt; t0 += nw * GPW) {
             const int t = t0 + grp;
             const bool on = t < cnt;
@@ -809,7 +881,7 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
     extern __shared__ __align__(128) unsigned char sms[];
     const int K = A.n_tot;
     C* tb = reinterpret_cast<C*>(sms) + (A.bsm ? A.bstride : 0);
-    C* ring = tb + (size_t)kSolveThreads;
+    C* ring = tb + (size_t)kSolveThreads + kSplitRows * 4 * 32;
     if (threadIdx.x == 0) {
         const int L = cr_levels(K);
         for (int l = 0; l <= L; ++l) {
@@ -1259,7 +1331,7 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
                  cudaStream_t s) {
     using C = cx<T>;
     auto kern = cr_solve_kernel<T, MODE>;
-    const size_t tb = sizeof(C) * (size_t)kSolveThreads;
+    const size_t tb = sizeof(C) * ((size_t)kSolveThreads + kSplitRows * 4 * 32);
     const size_t bb = sizeof(C) * (size_t)per_cta;
     SolvePlan P;
     if (!plan_solve<C>(c, bb, tb, scratch == nullptr, &P))
@@ -1303,7 +1375,7 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
 template <typename T>
 int prepare_chunk_tables(lss_ctx* c) {
     using C = cx<T>;
-    const size_t tb = sizeof(C) * (size_t)kSolveThreads;
+    const size_t tb = sizeof(C) * ((size_t)kSolveThreads + kSplitRows * 4 * 32);
     const size_t bb = sizeof(C) * (size_t)c->n_tot * ldwmax_of(c);
     for (int smem_b = 0; smem_b < 2; ++smem_b) {
         SolvePlan P;
