@@ -83,10 +83,66 @@ cd lss_cell_integral_G(int d, double omega, double h) {
 
 namespace {
 
+// (J0(x), Y0(x)) for x > 0 to about 1e-16 absolute, over the whole range of
+// arguments a table reaches (omega r up to several hundred), from two
+// published methods:
+//  x < 25: Miller's backward recurrence J_{k-1} = (2k/x) J_k - J_{k+1} from an
+//   even order N >= x + 40 (where J_N is negligible), normalised by
+//   J0 + 2 sum_{k>=1} J_{2k} = 1; Y0 from Neumann's series
+//   Y0 = (2/pi)(ln(x/2) + gamma) J0 - (4/pi) sum_{k>=1} (-1)^k J_{2k} / k;
+//  x >= 25: Hankel's asymptotic expansion
+//   H0(x) = J0 + i Y0 = sqrt(2/(pi x)) e^{i(x - pi/4)} sum_k a_k (i/x)^k,
+//   a_0 = 1, a_k = -a_{k-1} (2k-1)^2 / (8k), summed until a term is below
+//   1e-17 (about 20 terms at x = 25; the least term, near k = 2x, is far
+//   below that).
+__device__ double2 bessel_j0_y0(double x) {
+    if (x < 25.0) {
+        const int N = 2 * (int)((x + 40.0) * 0.5) + 2;
+        double jp = 0.0, jc = 1e-30, norm = 0.0, ys = 0.0;
+        for (int k = N; k > 0; --k) {
+            const double jm = (2.0 * k / x) * jc - jp;   // J_{k-1}
+            jp = jc;
+            jc = jm;
+            const int km = k - 1;
+            if (km > 0 && (km & 1) == 0) {
+                const int h = km >> 1;
+                norm += 2.0 * jc;
+                ys += ((h & 1) ? -jc : jc) / h;
+            }
+            if (fabs(jc) > 1e200) {   // rescale against overflow at small x
+                jp *= 1e-200;
+                jc *= 1e-200;
+                norm *= 1e-200;
+                ys *= 1e-200;
+            }
+        }
+        norm += jc;
+        const double J0 = jc / norm;
+        const double euler_gamma = 0.57721566490153286061;
+        const double Y0 = (2.0 / M_PI) * (log(0.5 * x) + euler_gamma) * J0 - (4.0 / M_PI) * (ys / norm);
+        return mk(J0, Y0);
+    }
+    double tr = 1.0, ti = 0.0, sr = 1.0, si = 0.0;   // term and sum of the series
+    for (int k = 1; k < 64; ++k) {
+        const double f = -(double)((2 * k - 1) * (2 * k - 1)) / (8.0 * k * x);
+        const double nr = -ti * f, ni = tr * f;   // term *= f * i
+        tr = nr;
+        ti = ni;
+        sr += tr;
+        si += ti;
+        if (fabs(tr) + fabs(ti) < 1e-17) break;
+    }
+    double sn, cs;
+    sincos(x, &sn, &cs);
+    const double a = sqrt(2.0 / (M_PI * x)) * M_SQRT1_2;   // e^{-i pi/4} = (1 - i)/sqrt(2)
+    const double er = a * (cs + sn), ei = a * (sn - cs);
+    return mk(er * sr - ei * si, er * si + ei * sr);
+}
+
 // G(r) h^2 = h^2 (i/4) (J0 + i Y0)(omega r) for r > 0 (2D).
 __device__ __forceinline__ double2 k_weight_2d(double r, double omega, double h2) {
-    const double x = omega * r;
-    return mk(-0.25 * y0(x) * h2, 0.25 * j0(x) * h2);
+    const double2 jy = bessel_j0_y0(omega * r);
+    return mk(-0.25 * jy.y * h2, 0.25 * jy.x * h2);
 }
 
 // Circular L x L table for the zero-padded convolution: offsets |o_a| <= n-1
