@@ -318,6 +318,8 @@ def run_ours(args, rank, world):
         results[prec_name] = res
     if args.batched and "mixed" in results:
         results["batched"] = run_batched(args, dev, world)
+    if args.ragged and "mixed" in results:
+        results["ragged"] = run_ragged(args, dev, world)
     return w, R, results
 
 
@@ -377,6 +379,68 @@ def run_batched(args, dev, world):
             "solve_only": {"value": R * args.steps * world / (solve_ms / 1e3), "ms_per_solve_call": solve_ms / args.steps},
             "iters_mean": float(np.mean([s["iters"] for st in stats for s in st])), "relres_true_max": relres,
             "converged": all(s["relres_true"] <= 1e-8 for st in stats for s in st)}
+
+
+def run_ragged(args, dev, world):
+    """Form (2), ragged instances: independent problems with n uniform on
+    {128..384}, omega/2pi = n/8, band-limited media, one plane wave each, all
+    behind one batch context (instances run concurrently); against it the same
+    instances solved one after another, each by its own context.  Mixed
+    precision; a step is factor + plane-wave RHS + solve of every instance."""
+    import torch
+    from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED, LSSolver, LSSolverBatch
+    spec = dict(synth.RAGGED_32, count=args.ragged)
+    ns = synth.ragged_sizes(**spec)
+    inst = synth.ragged_instances(ns, spec["seed"])
+    ms = [torch.tensor(m, dtype=torch.float64, device=dev) for _, m, _ in inst]
+    oms = [2 * math.pi * f for f, _, _ in inst]
+    dirs = np.stack([d for _, _, d in inst])
+    opts = GmresOptions(30, 1e-8, 300)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    batch = LSSolverBatch(ns, oms, ms, precision=LSS_MIXED, factor=False)
+    single = [LSSolver(n, om, m, precision=LSS_MIXED, factor=False) for n, om, m in zip(ns, oms, ms)]
+
+    def step_batch():
+        batch.factor()
+        return batch.solve(batch.plane_wave_rhs(dirs), opts)[1]
+
+    def step_seq():
+        st = []
+        for s, d in zip(single, dirs):
+            s.factor()
+            st.append(s.solve(s.plane_wave_rhs(d), opts)[1])
+        return st
+
+    out = {}
+    for name, step in (("batch", step_batch), ("sequential", step_seq)):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        total, stats = 0.0, []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        flat = [x for st in stats for q in st for x in q]
+        out[name] = {"value": len(ns) * args.steps * world / (total / 1e3), "ms_per_step": total / args.steps,
+                     "iters_mean": float(np.mean([x["iters"] for x in flat])),
+                     "relres_true_max": max(x["relres_true"] for x in flat),
+                     "converged": all(x["relres_true"] <= 1e-8 for x in flat)}
+    del batch, single
+    return {"instances": len(ns), "n": ns, "unit": "instances solved/s",
+            "step": "factor + plane-wave RHS + FGMRES solve of every instance (mixed precision)",
+            **out["batch"], "sequential": out["sequential"],
+            "batch_over_sequential": out["batch"]["value"] / out["sequential"]["value"]}
 
 
 # DRAM traffic per launch group from ncu captures (profiles/iface_maps_2d_n256_mixed.md):
@@ -445,6 +509,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", default="2d_n256_r16",
                     help="workload of the batched mixed-precision line ('' to skip)")
+    ap.add_argument("--ragged", type=int, default=32,
+                    help="instances of the ragged batch line (0 to skip)")
     ap.add_argument("--arms", default="mixed,fp64",
                     help="precisions to run (mixed first; the JSON line needs both, profiling may take one)")
     args = ap.parse_args()
@@ -516,6 +582,7 @@ def main():
                          solve_only_vs_plain_fp64=results["batched"]["solve_only"]["value"]
                          / f64["solve_only"]["value"])
                     if "batched" in results else None),
+        "ragged": results.get("ragged"),
         "breakdown_ms": mix["prof_ms"], "launches_per_step": mix["prof_launches"],
     }
     print(json.dumps(line))

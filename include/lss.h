@@ -257,6 +257,41 @@ int lss_profile(lss_ctx *c, int enable);
 /* ms, launches: arrays of ncat entries (either may be NULL). */
 int lss_profile_read(lss_ctx *c, double *ms, long long *launches, int ncat);
 
+/*
+ * Ragged instances: several independent problems of different grid size,
+ * frequency and medium behind one context (the paper treats one problem at a
+ * time; batching independent problems is this library's own form).  Each
+ * instance is a full context with its own stream; a call on the batch forks
+ * the caller's stream, drives every instance concurrently (one host thread
+ * per instance, up to 32) and joins back, so small instances share the GPU.
+ *
+ * lss_setup_batch - lss_setup for n_inst instances.
+ *   g, omega, m_dev  arrays of n_inst entries (grid, angular frequency, device
+ *                    pointer to that instance's n_q^2 float64 medium)
+ *   pml, slab, precision  shared by all instances
+ * On a batch context lss_factor, lss_plane_wave_rhs, lss_apply_A,
+ * lss_apply_P, lss_solve, lss_adjoint_solve, lss_medium_gradient,
+ * lss_profile, lss_profile_read and lss_destroy act on every instance:
+ *   vectors    instance q's R x n_q^2 complex128 values start at element
+ *              R * (n_0^2 + ... + n_{q-1}^2) of the one device array passed
+ *   stats      R x n_inst entries, instance-major (stats[q * R + r])
+ *   gradient   instance q's n_q^2 values start at n_0^2 + ... + n_{q-1}^2
+ *   directions R per instance, instance-major: n_inst x R x 2 float64 on the
+ *              host (lss_plane_wave_rhs, lss_medium_gradient)
+ * Errors: the first failing instance's code (LSS_ERR_NOCONVERGE only if no
+ * instance failed otherwise), its message prefixed with "instance q: ".
+ * lss_set_medium, lss_solve_host, lss_apply_slab(_noalloc), lss_info,
+ * lss_slab_info and lss_get_stencils return LSS_ERR_ARG on a batch context:
+ * call them on an instance.
+ */
+int lss_setup_batch(lss_ctx **out, int n_inst, const lss_grid *g, const double *omega,
+                    const double *const *m_dev, const lss_pml *pml, const lss_slab *slab,
+                    int precision, void *stream);
+/* Number of instances and sum of n_q^2 over them; LSS_ERR_ARG if c is not a batch. */
+int lss_batch_info(const lss_ctx *c, int *n_inst, long long *elems_per_rhs);
+/* Instance q of a batch (owned by the batch: do not destroy it). */
+int lss_batch_instance(lss_ctx *c, int q, lss_ctx **inst);
+
 /* Message of the last failure on this context ("" if none). */
 const char *lss_last_error(const lss_ctx *c);
 

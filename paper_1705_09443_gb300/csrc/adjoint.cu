@@ -313,12 +313,14 @@ int launch_t(lss_ctx* c, TArgs<cx<T>> A, dim3 grid, cudaStream_t s) {
         A.bg = (C*)c->z_buf;
     }
     static size_t cfg = 0;
+    std::unique_lock<std::mutex> lock(lss_config_mutex());
     if (sh > cfg) {
         cudaError_t e = cudaFuncSetAttribute(cr_solve_t_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "transposed solve attribute");
         cfg = sh;
     }
+    lock.unlock();
     cr_solve_t_kernel<T, MODE><<<grid, kTThreads, sh, s>>>(A);
     return lss_check_cuda(c, cudaGetLastError(), "transposed solve launch");
 }
@@ -342,7 +344,8 @@ template <typename T>
 int build_maps_t(lss_ctx* c, cudaStream_t s) {
     using C = cx<T>;
     if (c->iface_t_valid || c->n_slabs == 1) return LSS_OK;
-    const size_t bytes = (size_t)3 * c->n_slabs * c->n_tot * c->n_tot * sizeof(C);
+    // 64 bytes of slack for the recurrence's 16-byte aligned copy windows
+    const size_t bytes = (size_t)3 * c->n_slabs * c->n_tot * c->n_tot * sizeof(C) + 64;
     if (!c->iface_t) {
         cudaError_t e = cudaMalloc(&c->iface_t, bytes);
         if (e) return lss_check_cuda(c, e, "transposed interface maps");

@@ -229,6 +229,7 @@ int lss_fft_kernel_table(lss_ctx* c, const double2* kc, cudaStream_t s) {
 
 // Opt the FFT kernels into large dynamic shared memory once per process.
 int lss_fft_configure(lss_ctx* c) {
+    std::lock_guard<std::mutex> lock(lss_config_mutex());
     static bool done = false;
     if (done) return LSS_OK;
     const int smax = 200 * 1024;

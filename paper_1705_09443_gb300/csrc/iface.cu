@@ -352,8 +352,11 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     if (rc) return rc;
     if (c->ifp_n != np) {   // the table depends on the slab layout only: uploaded once
         rc = lss_grow(c, &c->ifp_buf, &c->ifp_cap, probs.size() * sizeof(IfProb));
-        if (!rc) rc = lss_check_cuda(c, cudaMemcpy(c->ifp_buf, probs.data(), probs.size() * sizeof(IfProb),
-                                                   cudaMemcpyHostToDevice), "interface problems");
+        // on the context's stream (ordered before the map kernels), and finished
+        // before the host table goes out of scope
+        if (!rc) rc = lss_check_cuda(c, cudaMemcpyAsync(c->ifp_buf, probs.data(), probs.size() * sizeof(IfProb),
+                                                        cudaMemcpyHostToDevice, s), "interface problems");
+        if (!rc) rc = lss_check_cuda(c, cudaStreamSynchronize(s), "interface problems");
         if (rc) return rc;
         c->ifp_n = np;
     }
@@ -369,6 +372,7 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     A.maps = (C*)c->iface;
     const size_t sh = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)8 * gmax);
     static size_t cfg_f = 0, cfg_b = 0;
+    std::unique_lock<std::mutex> lock(lss_config_mutex());
     if (sh > cfg_f) {
         cudaError_t e = cudaFuncSetAttribute(if_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
@@ -381,6 +385,7 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
         if (e) return lss_check_cuda(c, e, "interface attribute");
         cfg_b = sh;
     }
+    lock.unlock();
     const int L = cr_levels(K);
     const int kt = (K + kIfTN - 1) / kIfTN;
     ProfScope ps(c, s, LSS_PROF_IFACE, 3 * L + 2);

@@ -20,6 +20,7 @@ __global__ void cast_c128_c64(const double2* __restrict__ a, float2* __restrict_
 
 void free_ctx(lss_ctx* c) {
     if (!c) return;
+    if (!c->inst.empty() || c->fork_ev) lss_batch_free(c);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
@@ -31,6 +32,13 @@ void free_ctx(lss_ctx* c) {
     for (void* p : c->chunk_dev)
         if (p) cudaFree(p);
     delete c;
+}
+
+bool is_batch(const lss_ctx* c) { return !c->inst.empty(); }
+
+int batch_only_per_instance(lss_ctx* c, const char* what) {
+    return lss_fail(c, LSS_ERR_ARG, std::string(what) + ": not defined on a batch context; call it on an instance "
+                                                        "(lss_batch_instance)");
 }
 
 int dalloc(lss_ctx* c, void** p, size_t bytes, const char* what) {
@@ -72,6 +80,11 @@ ProfScope::~ProfScope() {
         cudaEventRecord(b, s);
         c->prof.push_back({cat, a, b, n});
     }
+}
+
+std::mutex& lss_config_mutex() {
+    static std::mutex m;
+    return m;
 }
 
 // ---------------------------------------------------------------- status helpers
@@ -227,7 +240,9 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     rc = rc ? rc : dalloc(c, &c->fac, (size_t)foff * cs, "slab factors");
     c->work_len = woff;
     rc = rc ? rc : dalloc(c, &c->cr_work, (size_t)2 * woff * cs, "reduction work");
-    rc = rc ? rc : dalloc(c, &c->iface, (size_t)3 * nl * c->n_tot * c->n_tot * cs, "interface maps");
+    // 64 bytes of slack: the recurrence copies 16-byte aligned windows that may
+    // end up to 15 bytes past the last map row
+    rc = rc ? rc : dalloc(c, &c->iface, (size_t)3 * nl * c->n_tot * c->n_tot * cs + 64, "interface maps");
     rc = rc ? rc : dalloc(c, (void**)&c->d_slabs, nl * sizeof(SlabDev), "slabs");
     rc = rc ? rc : dalloc(c, (void**)&c->d_err, sizeof(int), "status");
     rc = rc ? rc : dalloc(c, (void**)&c->d_bar, 2 * sizeof(unsigned), "barrier");
@@ -252,6 +267,7 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
 
 int lss_set_medium(lss_ctx* c, const double* m_dev, void* stream) {
     if (!c) return LSS_ERR_ARG;
+    if (is_batch(c)) return batch_only_per_instance(c, "set_medium");
     if (!m_dev) return lss_fail(c, LSS_ERR_ARG, "set_medium: m is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = lss_set_medium_impl(c, m_dev, s);
@@ -261,12 +277,27 @@ int lss_set_medium(lss_ctx* c, const double* m_dev, void* stream) {
 
 int lss_profile(lss_ctx* c, int enable) {
     if (!c) return LSS_ERR_ARG;
+    for (lss_ctx* ci : c->inst) lss_profile(ci, enable);
     c->prof_on = enable != 0;
     return LSS_OK;
 }
 
 int lss_profile_read(lss_ctx* c, double* ms, long long* launches, int ncat) {
     if (!c || ncat < 0) return LSS_ERR_ARG;
+    if (is_batch(c)) {   // sums over the instances
+        std::vector<double> sm(LSS_PROF_NCAT, 0.0), m1(LSS_PROF_NCAT);
+        std::vector<long long> sl(LSS_PROF_NCAT, 0), l1(LSS_PROF_NCAT);
+        for (lss_ctx* ci : c->inst) {
+            const int rc = lss_profile_read(ci, m1.data(), l1.data(), LSS_PROF_NCAT);
+            if (rc) return lss_fail(c, rc, ci->err);
+            for (int k = 0; k < LSS_PROF_NCAT; ++k) { sm[k] += m1[k]; sl[k] += l1[k]; }
+        }
+        for (int k = 0; k < ncat && k < LSS_PROF_NCAT; ++k) {
+            if (ms) ms[k] = sm[k];
+            if (launches) launches[k] = sl[k];
+        }
+        return LSS_OK;
+    }
     std::vector<double> acc(LSS_PROF_NCAT, 0.0);
     for (auto& r : c->prof) {
         cudaError_t e = cudaEventSynchronize(r.b);
@@ -289,6 +320,7 @@ int lss_profile_read(lss_ctx* c, double* ms, long long* launches, int ncat) {
 int lss_factor(lss_ctx* c, void* stream) {
     if (!c) return LSS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    if (is_batch(c)) return lss_batch_factor(c, s);
     c->factored = false;
     int rc = lss_factor_slabs(c, s);
     if (!rc) rc = lss_check_cuda(c, cudaStreamSynchronize(s), "factor");
@@ -302,6 +334,7 @@ int lss_plane_wave_rhs(lss_ctx* c, const double* dirs_host, int R, void* g_dev, 
     if (!c) return LSS_ERR_ARG;
     if (!dirs_host || !g_dev || R < 1) return lss_fail(c, LSS_ERR_ARG, "plane_wave_rhs: bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    if (is_batch(c)) return lss_batch_plane_wave_rhs(c, dirs_host, R, (double2*)g_dev, (double2*)uI_dev, s);
     int rc = lss_grow(c, &c->dir_buf, &c->dir_cap, (size_t)R * 2 * sizeof(double));
     if (rc) return rc;
     rc = lss_check_cuda(c, cudaMemcpyAsync(c->dir_buf, dirs_host, (size_t)R * 2 * sizeof(double),
@@ -314,6 +347,7 @@ int lss_plane_wave_rhs(lss_ctx* c, const double* dirs_host, int R, void* g_dev, 
 int lss_apply_A(lss_ctx* c, const void* x, void* y, int R, int transpose, void* stream) {
     if (!c) return LSS_ERR_ARG;
     if (!x || !y || R < 1 || x == y) return lss_fail(c, LSS_ERR_ARG, "apply_A: bad arguments");
+    if (is_batch(c)) return lss_batch_apply(c, 0, (const double2*)x, (double2*)y, R, transpose, (cudaStream_t)stream);
     return lss_matvec(c, (const double2*)x, (double2*)y, R, transpose ? MV_IN_U : MV_IN_MU,
                       transpose ? MV_OUT_AT : MV_OUT_A, nullptr, nullptr, (cudaStream_t)stream);
 }
@@ -322,6 +356,7 @@ int lss_apply_P(lss_ctx* c, const void* x, void* y, int R, int transpose, void* 
     if (!c) return LSS_ERR_ARG;
     if (!x || !y || R < 1) return lss_fail(c, LSS_ERR_ARG, "apply_P: bad arguments");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_P before lss_factor");
+    if (is_batch(c)) return lss_batch_apply(c, 1, (const double2*)x, (double2*)y, R, transpose, (cudaStream_t)stream);
     if (transpose) return lss_sweep_t(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
     return lss_sweep(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
 }
@@ -332,6 +367,7 @@ int lss_solve(lss_ctx* c, const void* g, void* u, int R, const lss_gmres* o, lss
     if (o->restart < 1 || o->restart > 200 || !(o->tol > 0) || o->max_iter < 1)
         return lss_fail(c, LSS_ERR_ARG, "solve: bad GMRES options");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "solve before lss_factor");
+    if (is_batch(c)) return lss_batch_solve(c, (const double2*)g, (double2*)u, R, o, stats, (cudaStream_t)stream, 0);
     return lss_fgmres(c, (const double2*)g, (double2*)u, R, o, stats, (cudaStream_t)stream);
 }
 
@@ -342,6 +378,8 @@ int lss_adjoint_solve(lss_ctx* c, const void* rhs, void* mu, int R, const lss_gm
     if (o->restart < 1 || o->restart > 200 || !(o->tol > 0) || o->max_iter < 1)
         return lss_fail(c, LSS_ERR_ARG, "adjoint_solve: bad GMRES options");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "adjoint_solve before lss_factor");
+    if (is_batch(c))
+        return lss_batch_solve(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
     return lss_fgmres(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
 }
 
@@ -350,6 +388,7 @@ int lss_medium_gradient(lss_ctx* c, const void* mu, const void* u, const double*
     if (!c) return LSS_ERR_ARG;
     if (!mu || !u || !dirs_host || !grad || R < 1) return lss_fail(c, LSS_ERR_ARG, "medium_gradient: bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    if (is_batch(c)) return lss_batch_gradient(c, (const double2*)mu, (const double2*)u, dirs_host, R, grad, s);
     const size_t bytes = (size_t)R * c->n * c->n * sizeof(double2);
     int rc = lss_grow(c, &c->gr_buf, &c->gr_cap, bytes);
     if (!rc) rc = lss_grow(c, &c->dir_buf, &c->dir_cap, (size_t)R * 2 * sizeof(double));
@@ -367,6 +406,7 @@ int lss_solve_host(lss_ctx* c, const void* g_host, void* u_host, int R, const ls
                    void* stream) {
     if (!c) return LSS_ERR_ARG;
     if (!g_host || !u_host || R < 1) return lss_fail(c, LSS_ERR_ARG, "solve_host: bad arguments");
+    if (is_batch(c)) return batch_only_per_instance(c, "solve_host");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)R * c->n * c->n * sizeof(double2);
     int rc = lss_grow(c, &c->io_buf, &c->io_cap, 2 * bytes);
@@ -384,6 +424,7 @@ int lss_solve_host(lss_ctx* c, const void* g_host, void* u_host, int R, const ls
 
 int lss_apply_slab(lss_ctx* c, int slab, const void* v, void* w, int R, void* stream) {
     if (!c) return LSS_ERR_ARG;
+    if (is_batch(c)) return batch_only_per_instance(c, "apply_slab");
     if (!v || !w || R < 1 || slab < 0 || slab >= c->n_slabs)
         return lss_fail(c, LSS_ERR_ARG, "apply_slab: bad arguments");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_slab before lss_factor");
@@ -391,7 +432,7 @@ int lss_apply_slab(lss_ctx* c, int slab, const void* v, void* w, int R, void* st
 }
 
 int lss_info(const lss_ctx* c, int* n_tot, int* n_slabs, int* fft_len) {
-    if (!c) return LSS_ERR_ARG;
+    if (!c || is_batch(c)) return LSS_ERR_ARG;
     if (n_tot) *n_tot = c->n_tot;
     if (n_slabs) *n_slabs = c->n_slabs;
     if (fft_len) *fft_len = c->L;
@@ -399,7 +440,7 @@ int lss_info(const lss_ctx* c, int* n_tot, int* n_slabs, int* fft_len) {
 }
 
 int lss_slab_info(const lss_ctx* c, int slab, int* first_x1, int* n_layers, int* n_aux) {
-    if (!c || slab < 0 || slab >= c->n_slabs) return LSS_ERR_ARG;
+    if (!c || is_batch(c) || slab < 0 || slab >= c->n_slabs) return LSS_ERR_ARG;
     const SlabDev& sd = c->slabs[slab];
     if (first_x1) *first_x1 = sd.s;
     if (n_layers) *n_layers = sd.nl;
@@ -408,7 +449,7 @@ int lss_slab_info(const lss_ctx* c, int slab, int* first_x1, int* n_layers, int*
 }
 
 int lss_get_stencils(const lss_ctx* c, double* alpha, double* beta) {
-    if (!c || !alpha || !beta) return LSS_ERR_ARG;
+    if (!c || is_batch(c) || !alpha || !beta) return LSS_ERR_ARG;
     for (int o = 0; o < 9; ++o) {
         alpha[2 * o] = c->alpha[o].real();
         alpha[2 * o + 1] = c->alpha[o].imag();

@@ -6,6 +6,7 @@
 #include <vector>
 #include <array>
 #include <complex>
+#include <mutex>
 
 #include "../../include/lss.h"
 
@@ -158,6 +159,14 @@ struct lss_ctx {
     std::vector<void*> chunk_dev;
     int num_sms = 0;
 
+    // ragged batch (lss_setup_batch): one full context per instance, each with
+    // its own stream and completion event; empty for an ordinary context
+    std::vector<lss_ctx*> inst;
+    std::vector<cudaStream_t> inst_stream;
+    std::vector<cudaEvent_t> inst_done;
+    std::vector<long long> inst_off;   // prefix sums of n_q^2 (elements per right-hand side)
+    cudaEvent_t fork_ev = nullptr;
+
     // profiling: event pairs per kernel group, launch counters
     struct ProfRec { int cat; cudaEvent_t a, b; int launches; };
     bool prof_on = false;
@@ -178,6 +187,21 @@ struct ProfScope {
     ProfScope(lss_ctx* c_, cudaStream_t s_, int cat_, int n_launch);
     ~ProfScope();
 };
+
+// Guards the process-wide, once-per-kernel launch configuration (shared
+// memory and cluster attributes, cached occupancy) when instances of a batch
+// are driven from several host threads.
+std::mutex& lss_config_mutex();
+
+// batch.cu: ragged instances (contexts made by lss_setup_batch)
+void lss_batch_free(lss_ctx* c);
+int lss_batch_factor(lss_ctx* c, cudaStream_t s);
+int lss_batch_plane_wave_rhs(lss_ctx* c, const double* dirs, int R, double2* g, double2* uI, cudaStream_t s);
+int lss_batch_apply(lss_ctx* c, int which, const double2* x, double2* y, int R, int transpose, cudaStream_t s);
+int lss_batch_solve(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
+                    cudaStream_t s, int adjoint);
+int lss_batch_gradient(lss_ctx* c, const double2* mu, const double2* u, const double* dirs, int R, double* grad,
+                       cudaStream_t s);
 
 // status helpers
 int lss_fail(lss_ctx* c, int code, const std::string& msg);

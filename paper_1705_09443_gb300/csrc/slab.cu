@@ -1068,6 +1068,11 @@ __global__ void __launch_bounds__(NT) recur_chain_kernel(int n_slabs, int n_tot,
 // every thread waits on the stage's mbarrier, bounded); the dot products read
 // the rows from shared memory, so the number of (row, rhs) tasks per warp is
 // free.  The base values of a warp's first tasks are loaded one step ahead.
+// Ring stage of the TMA recurrence kernel, in entries: a CTA's rows of one
+// map plus one entry of alignment lead, rounded up to an even count so every
+// stage starts on a 16-byte boundary.
+LSS_HD inline long long recur_stage_ent(int rows_per, int n_tot) { return ((long long)rows_per * n_tot + 2) & ~1LL; }
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ maps,
                                                        const cx<T>* base, const cx<T>* __restrict__ init, cx<T>* out,
@@ -1082,18 +1087,26 @@ __global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, i
     const int rows_per = (n_tot + CL - 1) / CL;
     const int r0 = min(n_tot, cr * rows_per), r1 = min(n_tot, r0 + rows_per);
     const int nrow = r1 - r0;
-    const long long stage_ent = (long long)rows_per * n_tot;
-    C* ring = reinterpret_cast<C*>(smr2);                 // nb x rows_per x n_tot
+    // a stage holds the CTA's rows of one map, copied from the 16-byte aligned
+    // address at or before their first entry (rows of odd length in single
+    // precision start on 8-byte boundaries) and rounded up to 16 bytes
+    const long long stage_ent = recur_stage_ent(rows_per, n_tot);
+    C* ring = reinterpret_cast<C*>(smr2);                 // nb x stage_ent
     C* vb = ring + nb * stage_ent;                        // 2 x n_tot x R
     __shared__ __align__(8) uint64_t full[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT >> 5;
     const int ntask = nrow * R;
     const int nsteps = n_slabs - 2;
     const int i0 = backward ? n_slabs - 2 : 1, di = backward ? -1 : 1;
-    const unsigned bytes = (unsigned)((long long)nrow * n_tot * sizeof(C));
+    auto lead_of = [&](int step) {   // entries between the aligned copy start and the CTA's first row
+        const C* src = maps + (long long)(i0 + step * di) * nt2 + (long long)r0 * n_tot;
+        return (int)((reinterpret_cast<uintptr_t>(src) & 15) / sizeof(C));
+    };
     auto issue = [&](int step) {
         const int st = step % nb;
-        const C* src = maps + (long long)(i0 + step * di) * nt2 + (long long)r0 * n_tot;
+        const int lead = lead_of(step);
+        const C* src = maps + (long long)(i0 + step * di) * nt2 + (long long)r0 * n_tot - lead;
+        const unsigned bytes = (unsigned)((((long long)nrow * n_tot + lead) * sizeof(C) + 15) & ~15LL);
         mbar_expect_tx(&full[st], bytes);
         tma_load_1d(ring + st * stage_ent, src, bytes, &full[st]);
     };
@@ -1133,7 +1146,7 @@ __global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, i
         for (int q = 0; q < BV; ++q) bvc[q] = bvn[q];
         load_bv(s + 1);
         if (nrow > 0 && !mbar_wait(&full[st], (s / nb) & 1, err)) ok = false;
-        const C* M = ring + st * stage_ent;
+        const C* M = ring + st * stage_ent + lead_of(s);
         for (int t0 = warp, q = 0; t0 < ntask; t0 += nw, ++q) {
             const int rl = t0 / R, rr = t0 % R;
             const long long e = (long long)(r0 + rl) * R + rr;
@@ -1230,6 +1243,7 @@ long long max_row_ent(const lss_ctx* c) {
 
 template <typename F>
 int set_smem(lss_ctx* c, F kern, size_t sh, size_t* configured) {
+    std::lock_guard<std::mutex> lock(lss_config_mutex());
     if (sh <= *configured) return LSS_OK;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max<size_t>(sh, 48 * 1024));
@@ -1289,8 +1303,10 @@ bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, Solve
 }
 
 // Chunk tables (16- and 32-wide blocks) of one output kind and stage size,
-// built and uploaded on first use.
-int chunk_tables(lss_ctx* c, bool part, int stage_ent, CrArgsTables* out) {
+// built and uploaded on first use (on stream s, ahead of the solves that read
+// them: a copy on the legacy default stream would not be ordered before
+// kernels on a non-blocking stream).
+int chunk_tables(lss_ctx* c, bool part, int stage_ent, CrArgsTables* out, cudaStream_t s) {
     for (size_t q = 0; q < c->chunk_keys.size(); ++q)
         if (c->chunk_keys[q][0] == (part ? 1 : 0) && c->chunk_keys[q][1] == stage_ent) {
             out->t16 = c->chunk_dev[2 * q];
@@ -1305,8 +1321,9 @@ int chunk_tables(lss_ctx* c, bool part, int stage_ent, CrArgsTables* out) {
     void* d32 = nullptr;
     cudaError_t e = cudaMalloc(&d16, t16.size() * sizeof(CrChunk));
     if (!e) e = cudaMalloc(&d32, t32.size() * sizeof(CrChunk));
-    if (!e) e = cudaMemcpy(d16, t16.data(), t16.size() * sizeof(CrChunk), cudaMemcpyHostToDevice);
-    if (!e) e = cudaMemcpy(d32, t32.data(), t32.size() * sizeof(CrChunk), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpyAsync(d16, t16.data(), t16.size() * sizeof(CrChunk), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(d32, t32.data(), t32.size() * sizeof(CrChunk), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaStreamSynchronize(s);   // the host tables go out of scope
     if (e) {
         if (d16) cudaFree(d16);
         if (d32) cudaFree(d32);
@@ -1341,7 +1358,7 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
     A.nst = P.nst;
     A.stage_ent = P.stage_ent;
     CrArgsTables tabs;
-    int rc = chunk_tables(c, MODE == CR_A, P.stage_ent, &tabs);
+    int rc = chunk_tables(c, MODE == CR_A, P.stage_ent, &tabs, s);
     if (rc) return rc;
     A.tab16 = (const CrChunk*)tabs.t16;
     A.tab32 = (const CrChunk*)tabs.t32;
@@ -1373,7 +1390,7 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
 // in shared or in global memory, all layers or first/last only), built at
 // factorization so that no later call allocates.
 template <typename T>
-int prepare_chunk_tables(lss_ctx* c) {
+int prepare_chunk_tables(lss_ctx* c, cudaStream_t s) {
     using C = cx<T>;
     const size_t tb = sizeof(C) * ((size_t)kSolveThreads + kSplitRows * 4 * 32);
     const size_t bb = sizeof(C) * (size_t)c->n_tot * ldwmax_of(c);
@@ -1382,7 +1399,7 @@ int prepare_chunk_tables(lss_ctx* c) {
         if (!plan_solve<C>(c, bb, tb, smem_b == 1, &P)) continue;
         for (int part = 0; part < 2; ++part) {
             CrArgsTables t;
-            const int rc = chunk_tables(c, part == 1, P.stage_ent, &t);
+            const int rc = chunk_tables(c, part == 1, P.stage_ent, &t, s);
             if (rc) return rc;
         }
     }
@@ -1391,7 +1408,7 @@ int prepare_chunk_tables(lss_ctx* c) {
 
 template <typename T>
 int factor_impl(lss_ctx* c, cudaStream_t s) {
-    int rc0 = prepare_chunk_tables<T>(c);
+    int rc0 = prepare_chunk_tables<T>(c, s);
     if (rc0) return rc0;
     using C = cx<T>;
     const int K0 = c->n_tot, ns = c->n_slabs, nlev = cr_levels(K0);
@@ -1439,6 +1456,7 @@ int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     static int cl_size = 0;
     static size_t configured = 0;
     auto kern = recur_chain_kernel<T, RW, CW, NT>;
+    std::unique_lock<std::mutex> lock(lss_config_mutex());
     if (sh > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
@@ -1468,10 +1486,12 @@ int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
         }
         if (!cl_size) return LSS_ERR_UNSUPPORTED;
     }
-    const int rows_per = (c->n_tot + cl_size - 1) / cl_size;
+    const int cl = cl_size;
+    lock.unlock();
+    const int rows_per = (c->n_tot + cl - 1) / cl;
     if ((rows_per * R + NT / 32 - 1) / (NT / 32) > RW || c->n_tot > 32 * CW) return LSS_ERR_UNSUPPORTED;
-    attr[0].val.clusterDim.x = cl_size;
-    cfg.gridDim = dim3(cl_size);
+    attr[0].val.clusterDim.x = cl;
+    cfg.gridDim = dim3(cl);
     int ns = c->n_slabs, nt = c->n_tot;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, maps, base, init, out, backward);
     return lss_check_cuda(c, e, "recurrence cluster launch");
@@ -1488,6 +1508,7 @@ int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     auto kern = recur_tma_kernel<T, NT>;
     static int cl_size = 0;
     static bool attr_done = false;
+    std::unique_lock<std::mutex> lock(lss_config_mutex());
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (!e) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1504,8 +1525,8 @@ int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     auto smem_for = [&](int cls, int nb) {
-        const long long rows_per = (c->n_tot + cls - 1) / cls;
-        return sizeof(C) * (size_t)(nb * rows_per * c->n_tot + 2LL * c->n_tot * R);
+        const int rows_per = (c->n_tot + cls - 1) / cls;
+        return sizeof(C) * (size_t)(nb * recur_stage_ent(rows_per, c->n_tot) + 2LL * c->n_tot * R);
     };
     if (!cl_size) {
         for (int cand : {16, 8}) {
@@ -1519,12 +1540,14 @@ int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
         }
         if (!cl_size) return LSS_ERR_UNSUPPORTED;
     }
+    const int cl = cl_size;
+    lock.unlock();
     int nb = 3;
-    while (nb >= 2 && smem_for(cl_size, nb) > (size_t)220 * 1024) --nb;
+    while (nb >= 2 && smem_for(cl, nb) > (size_t)220 * 1024) --nb;
     if (nb < 2) return LSS_ERR_UNSUPPORTED;
-    attr[0].val.clusterDim.x = cl_size;
-    cfg.gridDim = dim3(cl_size);
-    cfg.dynamicSmemBytes = smem_for(cl_size, nb);
+    attr[0].val.clusterDim.x = cl;
+    cfg.gridDim = dim3(cl);
+    cfg.dynamicSmemBytes = smem_for(cl, nb);
     int ns = c->n_slabs, nt = c->n_tot;
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, maps, base, init, out, backward, nb, c->d_err);
     return lss_check_cuda(c, e, "recurrence cluster launch");
@@ -1567,12 +1590,17 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
         if (rc != LSS_ERR_UNSUPPORTED) return rc;
     }
     static int grid = 0;
-    if (!grid) {
-        int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, recur_grid_kernel<T>, 256, 0);
-        grid = std::max(1, per) * c->num_sms;
+    int grid_now;
+    {
+        std::lock_guard<std::mutex> lock(lss_config_mutex());
+        if (!grid) {
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, recur_grid_kernel<T>, 256, 0);
+            grid = std::max(1, per) * c->num_sms;
+        }
+        grid_now = grid;
     }
-    int nb = (int)std::min<long long>(grid, std::max<long long>(1, (2 * vec + 7) / 8));
+    int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, (2 * vec + 7) / 8));
     int nsl = c->n_slabs, nt = c->n_tot;
     unsigned* bar = c->d_bar;
     int* err = c->d_err;

@@ -185,3 +185,127 @@ class LSSolver:
                                             st, _stream_ptr(stream)))
         return [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
                      relres_true=s.relres_true) for s in st]
+
+
+class LSSolverBatch:
+    """Independent problems of different size, frequency and medium behind one
+    context (lss_setup_batch); calls run the instances concurrently.
+
+    Vectors are flat complex128 CUDA tensors holding instance q's (R, n_q, n_q)
+    block after the blocks of instances 0..q-1; `views` splits one."""
+
+    def __init__(self, ns, omegas, ms, b_pml: int = 12, C: float = 10.0, b_slab: int = 4, b_aux: int = 0,
+                 n_samples: int = 0, precision: int = _lib.LSS_FP64, factor: bool = True, stream=None):
+        self.lib = _lib.load()
+        self.ns = [int(n) for n in ns]
+        self.omegas = [float(w) for w in omegas]
+        if not (len(self.ns) == len(self.omegas) == len(ms)) or not self.ns:
+            raise ValueError("ns, omegas and ms must have the same non-zero length")
+        self._ms = []
+        for n, m in zip(self.ns, ms):
+            if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != (n, n):
+                raise TypeError("each m must be a (n, n) float64 CUDA tensor")
+            self._ms.append(m.contiguous())
+        q = len(self.ns)
+        grids = (_lib.Grid * q)(*[_lib.Grid(2, n) for n in self.ns])
+        om = (ctypes.c_double * q)(*self.omegas)
+        mp = (ctypes.c_void_p * q)(*[m.data_ptr() for m in self._ms])
+        p = _lib.Pml(int(b_pml), float(C))
+        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples))
+        ctx = ctypes.c_void_p()
+        check(self.lib.lss_setup_batch(ctypes.byref(ctx), q, grids, om, mp, ctypes.byref(p), ctypes.byref(s),
+                                       int(precision), _stream_ptr(stream)))
+        self.ctx = ctx
+        nq, tot = ctypes.c_int(), ctypes.c_longlong()
+        self._check(self.lib.lss_batch_info(self.ctx, ctypes.byref(nq), ctypes.byref(tot)))
+        self.n_inst, self.elems_per_rhs = nq.value, tot.value
+        if factor:
+            self.factor(stream)
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and ctx.value:
+            torch.cuda.synchronize()
+            self.lib.lss_destroy(ctx)
+            self.ctx = None
+
+    def _check(self, code):
+        return check(code, self.ctx)
+
+    def views(self, flat: torch.Tensor, R: int):
+        """Instance q's (R, n_q, n_q) view of a flat batch vector."""
+        out, o = [], 0
+        for n in self.ns:
+            out.append(flat[o:o + R * n * n].view(R, n, n))
+            o += R * n * n
+        return out
+
+    def pack(self, xs):
+        """One flat batch vector from a list of (R, n_q, n_q) tensors."""
+        return torch.cat([_c128(x).reshape(-1) for x in xs])
+
+    def factor(self, stream=None):
+        self._check(self.lib.lss_factor(self.ctx, _stream_ptr(stream)))
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.lss_profile(self.ctx, int(enable)))
+
+    def profile_read(self):
+        k = len(_lib.PROF_CATEGORIES)
+        ms = np.zeros(k)
+        cnt = np.zeros(k, dtype=np.int64)
+        self._check(self.lib.lss_profile_read(self.ctx, ms.ctypes.data, cnt.ctypes.data, k))
+        return dict(zip(_lib.PROF_CATEGORIES, ms.tolist())), dict(zip(_lib.PROF_CATEGORIES, cnt.tolist()))
+
+    def plane_wave_rhs(self, dirs, stream=None) -> torch.Tensor:
+        """dirs: (n_inst, R, 2) directions, R per instance (or (R, 2): the same for all)."""
+        d = np.asarray(dirs, dtype=np.float64)
+        if d.ndim == 2:
+            d = np.broadcast_to(d, (self.n_inst,) + d.shape)
+        d = np.ascontiguousarray(d.reshape(self.n_inst, -1, 2))
+        R = d.shape[1]
+        g = torch.empty(R * self.elems_per_rhs, dtype=torch.complex128, device="cuda")
+        self._check(self.lib.lss_plane_wave_rhs(self.ctx, d.ctypes.data, R, g.data_ptr(), None, _stream_ptr(stream)))
+        return g
+
+    def _R(self, flat):
+        R, rem = divmod(flat.numel(), self.elems_per_rhs)
+        if rem or R < 1:
+            raise ValueError("batch vector length must be R * sum(n_q^2)")
+        return R
+
+    def apply_A(self, x: torch.Tensor, transpose: bool = False, stream=None) -> torch.Tensor:
+        x = _c128(x)
+        y = torch.empty_like(x)
+        self._check(self.lib.lss_apply_A(self.ctx, x.data_ptr(), y.data_ptr(), self._R(x), int(transpose),
+                                         _stream_ptr(stream)))
+        return y
+
+    def apply_P(self, x: torch.Tensor, transpose: bool = False, stream=None) -> torch.Tensor:
+        x = _c128(x)
+        y = torch.empty_like(x)
+        self._check(self.lib.lss_apply_P(self.ctx, x.data_ptr(), y.data_ptr(), self._R(x), int(transpose),
+                                         _stream_ptr(stream)))
+        return y
+
+    def _solve(self, fn, g, opts, stream, raise_on_noconv):
+        o = opts or GmresOptions()
+        g = _c128(g)
+        u = torch.empty_like(g)
+        R = self._R(g)
+        st = (_lib.Stats * (R * self.n_inst))()
+        go = _lib.Gmres(o.restart, o.tol, o.max_iter)
+        code = fn(self.ctx, g.data_ptr(), u.data_ptr(), R, ctypes.byref(go), st, _stream_ptr(stream))
+        if code != 0 and not (code == -5 and not raise_on_noconv):
+            self._check(code)
+        stats = [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
+                      relres_true=s.relres_true) for s in st]
+        return u, [stats[q * R:(q + 1) * R] for q in range(self.n_inst)]
+
+    def solve(self, g: torch.Tensor, opts: GmresOptions | None = None, stream=None, raise_on_noconv=True):
+        """u for every instance and RHS; stats[q][r]."""
+        return self._solve(self.lib.lss_solve, g, opts, stream, raise_on_noconv)
+
+    def adjoint_solve(self, rhs: torch.Tensor, opts: GmresOptions | None = None, stream=None,
+                      raise_on_noconv=True):
+        return self._solve(self.lib.lss_adjoint_solve, rhs, opts, stream, raise_on_noconv)

@@ -26,6 +26,9 @@ __all__ = [
     "bandlimited_medium",
     "plane_wave_directions",
     "make_workload",
+    "ragged_sizes",
+    "ragged_instances",
+    "RAGGED_32",
 ]
 
 
@@ -155,3 +158,26 @@ def make_workload(w: Workload | str, n: int | None = None):
     else:
         dirs = plane_wave_directions(w.dim, w.n_rhs)
     return m, dirs
+
+
+# The ragged-instance batch: 32 independent problems, n uniform on
+# {128, ..., 384}, omega/2pi = n/8 (8 points per wavelength), band-limited
+# media with c in [0.8, 1.2], one plane wave each at a seeded angle.
+RAGGED_32 = dict(count=32, n_lo=128, n_hi=384, seed=1710)
+
+
+def ragged_sizes(count: int, n_lo: int, n_hi: int, seed: int) -> list[int]:
+    """Grid sizes drawn uniformly from {n_lo, ..., n_hi}."""
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.integers(n_lo, n_hi + 1, size=count)]
+
+
+def ragged_instances(ns, seed: int, corr_len: float = 0.05, amplitude: float = 0.2):
+    """For each n: (freq = n/8, band-limited medium m, one seeded direction).
+    Instance q uses seed + q."""
+    out = []
+    for q, n in enumerate(ns):
+        m = bandlimited_medium(int(n), 2, corr_len, amplitude, seed + q)
+        d = plane_wave_directions(2, 1, seed=seed + 1000 + q)
+        out.append((n / 8.0, m, d))
+    return out

@@ -78,7 +78,7 @@ def test_n256_kernel_table_entries():
     e[0, 0] = 1.0
     col = (s.apply_A(to_dev(e[None])).cpu().numpy()[0] - e) / (0.5 * w.omega ** 2)
     kw = O.nystrom_weights(2, n, w.omega, n)
-    ref = kw[n:, n:]                       # offsets (i1, i2) >= 0
+    ref = kw[n:2 * n, n:2 * n]             # offsets (i1, i2) in 0..n-1
     assert np.abs(col - ref).max() <= 1e-13 * np.abs(ref).max()
     assert rel(col, ref) <= 1e-13
 

@@ -164,6 +164,26 @@ def test_ragged_small_grid_one_and_two_slabs():
         assert rel(s.apply_P(to_dev(x)).cpu().numpy()[0], pb.precondition(x[0])) <= 1e-10
 
 
+def test_mixed_precision_odd_total_width():
+    """n_tot = n + 2 + 2b odd (51 and 17): interface-map rows of odd length in
+    single precision, so the recurrence's map rows start on 8-byte
+    boundaries; the mixed sweep must still match the oracle to 1e-4 and the
+    mixed solve converge within two iterations of FP64."""
+    from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED
+    for n, freq, b in ((37, 4.625, 6), (9, 2.0, 3)):
+        s32, m, om = make(n, freq, medium_seed=5, b_pml=b, precision=LSS_MIXED, gauss=(3, 0.15, (0.8, 1.2)))
+        s64, _, _ = make(n, freq, medium_seed=5, b_pml=b, gauss=(3, 0.15, (0.8, 1.2)))
+        assert s32.n_tot % 2 == 1
+        pb = O.Problem2D(n, om, m, O.Params(b_pml=b, b_slab=4))
+        x = crand((1, n, n), 12)
+        assert rel(s32.apply_P(to_dev(x)).cpu().numpy()[0], pb.precondition(x[0])) <= 1e-4
+        assert rel(s32.apply_P(to_dev(x), transpose=True).cpu().numpy()[0], pb.precondition_transpose(x[0])) <= 1e-4
+        g = s64.plane_wave_rhs([(0.6, 0.8)])
+        _, st64 = s64.solve(g, GmresOptions(30, 1e-8, 200))
+        _, st32 = s32.solve(g, GmresOptions(30, 1e-8, 200))
+        assert st32[0]["relres_true"] <= 1e-8 and st32[0]["iters"] <= st64[0]["iters"] + 2
+
+
 def test_zero_medium_gives_zero_solution():
     from paper_1705_09443_gb300 import GmresOptions
     s, m, om = make(16, 2.0, medium_seed=None, b_pml=4)
