@@ -224,8 +224,6 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         clk = ClockSampler(dev.index)
         clk.start()
-        solver.profile_read()
-        solver.profile(True)
         total_ms = 0.0
         stats = []
         for _ in range(args.steps):
@@ -238,10 +236,19 @@ def run_ours(args, rank, world):
             e1.synchronize()
             total_ms += e0.elapsed_time(e1)
             stats.append(st)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        # per-kernel-group breakdown and launch counts: the same steps again with
+        # CUDA events around every kernel group (iterations then run launch by
+        # launch, not from their graphs), outside the timed region
+        solver.profile_read()
+        solver.profile(True)
+        for _ in range(args.steps):
+            flush.zero_()
+            step()
         solver.profile(False)
         prof_ms, prof_n = solver.profile_read()
         torch.cuda.synchronize()
-        clocks = clk.stop()
         if world > 1:
             t = torch.tensor([total_ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -286,8 +293,27 @@ def run_ours(args, rank, world):
             t = torch.tensor([solve_ms, setup_ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             solve_ms, setup_ms = (float(x) for x in t.tolist())
+        graphs = solver.graph_count()
+        # the same solves with every kernel launched one by one (no iteration graphs)
+        solver.use_graphs(False)
+        for _ in range(args.warmup):
+            solver.solve(g, opts)
+        nog_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solver.solve(g, opts)
+            e1.record(stream)
+            e1.synchronize()
+            nog_ms += e0.elapsed_time(e1)
+        solver.use_graphs(True)
         res["solve_only"] = {"value": (R * args.steps * world) / (solve_ms / 1e3), "unit": "solves/s",
-                             "ms_per_solve_call": solve_ms / args.steps}
+                             "ms_per_solve_call": solve_ms / args.steps,
+                             "iteration_graphs": {"captured": graphs[0], "refused": graphs[1]},
+                             "without_iteration_graphs": {"value": (R * args.steps * world) / (nog_ms / 1e3),
+                                                          "ms_per_solve_call": nog_ms / args.steps}}
         res["setup_factor_ms"] = setup_ms / args.steps
         # e2e: medium from pinned host memory, solution back to pinned host memory
         m_host = torch.tensor(m, dtype=torch.float64).pin_memory()

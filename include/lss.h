@@ -254,6 +254,21 @@ enum {
     LSS_PROF_NCAT = 9
 };
 int lss_profile(lss_ctx *c, int enable);
+
+/*
+ * lss_set_graphs - replay the kernels of each GMRES iteration (preconditioner,
+ * operator, both Gram-Schmidt passes) from a CUDA graph (enable = 1, the
+ * default) or launch them one by one (0).  Graphs are captured per basis
+ * index, number of right-hand sides and transpose flag after a first solve
+ * with the same R has sized every workspace; they are dropped when a
+ * workspace is reallocated and are not used while profiling is on.  The
+ * results are the same either way.  On a batch context: every instance.
+ */
+int lss_set_graphs(lss_ctx *c, int enable);
+/* Iteration graphs held by the context (all instances of a batch): captured,
+ * and refused (bodies that cannot be captured, e.g. with the grid-synchronised
+ * recurrence of very many right-hand sides; those iterations run uncaptured). */
+int lss_graph_count(const lss_ctx *c, int *captured, int *refused);
 /* ms, launches: arrays of ncat entries (either may be NULL). */
 int lss_profile_read(lss_ctx *c, double *ms, long long *launches, int ncat);
 

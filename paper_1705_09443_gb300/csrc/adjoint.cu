@@ -405,3 +405,7 @@ int sweep_t_impl(lss_ctx* c, const double2* y, double2* r, int R, cudaStream_t s
 int lss_sweep_t(lss_ctx* c, const double2* y, double2* r, int R, cudaStream_t s) {
     return c->prec == LSS_FP64 ? sweep_t_impl<double>(c, y, r, R, s) : sweep_t_impl<float>(c, y, r, R, s);
 }
+
+int lss_prepare_sweep_t(lss_ctx* c, cudaStream_t s) {
+    return c->prec == LSS_FP64 ? build_maps_t<double>(c, s) : build_maps_t<float>(c, s);
+}

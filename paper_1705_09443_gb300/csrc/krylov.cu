@@ -3,10 +3,14 @@
 // preconditioner is applied in reduced precision).  Right preconditioning,
 // x0 = 0, classical Gram-Schmidt with one re-orthogonalisation (CGS2), Givens
 // rotations on the host, all vector work in FP64 kernels, R right-hand sides
-// advanced together with independent Hessenberg matrices.
+// advanced together with independent Hessenberg matrices.  The kernels of one
+// iteration (preconditioner, operator, both Gram-Schmidt passes) are replayed
+// from a CUDA graph per basis index once the workspaces exist.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
+#include <string>
 #include <vector>
 
 #include "lss_common.cuh"
@@ -103,9 +107,6 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
                cudaStream_t s, int transpose) {
     // transpose: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T
     const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
-    auto precond = [&](const double2* x, double2* y) {
-        return transpose ? lss_sweep_t(c, x, y, R, s) : lss_sweep(c, x, y, R, s);
-    };
     const long long N = (long long)c->n * c->n;
     const int m = o->restart;
     const double tol = o->tol;
@@ -134,6 +135,74 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     const int gs = std::max(1, std::min(4 * c->num_sms, (int)((RN + 255) / 256)));
 
     double2* hnorm = K.hnorm;
+    if (transpose && (rc = lss_prepare_sweep_t(c, s))) return rc;
+
+    // Iteration body for basis vector j on stream bs: Z_j = P V_j, w = A Z_j,
+    // two Gram-Schmidt passes against V_0..V_j, ||w||^2.
+    auto body = [&](int j, cudaStream_t bs) -> int {
+        Krylov Kb = K;
+        Kb.s = bs;
+        const double2* Vj = V + (size_t)j * RN;
+        double2* Zj = Z + (size_t)j * RN;
+        int r = transpose ? lss_sweep_t(c, Vj, Zj, R, bs) : lss_sweep(c, Vj, Zj, R, bs);
+        if (!r) r = lss_matvec(c, Zj, w, R, mv_in, mv_out, nullptr, nullptr, bs);
+        if (r) return r;
+        dots(Kb, V, RN, j + 1, w, K.hdev, 0);
+        { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.hdev, j + 1, w, N, R, -1.0); }
+        dots(Kb, V, RN, j + 1, w, K.h2dev, 0);
+        { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.h2dev, j + 1, w, N, R, -1.0); }
+        dots(Kb, w, 0, 1, w, hnorm, 0);
+        return lss_check_cuda(c, cudaGetLastError(), "arnoldi");
+    };
+    // Graphs: only once a solve with this R and transpose ran uncaptured at the
+    // current workspace generation (every buffer the body touches exists), and
+    // not while profiling (the profile records events around kernel groups).
+    const bool use_graph = c->graphs_on && !c->prof_on;
+    bool warm = false;
+    for (const auto& k : c->graph_warm)
+        warm |= k[0] == R && k[1] == transpose && (unsigned long long)k[2] == c->buf_gen;
+    warm &= use_graph;
+    auto graph_for = [&](int j) -> cudaGraphExec_t {
+        for (const auto& g : c->graphs)
+            if (g.j == j && g.R == R && g.transpose == transpose && g.gen == c->buf_gen) return g.exec;
+        std::vector<lss_ctx::GraphRec> keep;   // drop graphs of older workspaces
+        for (const auto& g : c->graphs) {
+            if (g.gen == c->buf_gen) keep.push_back(g);
+            else if (g.exec) cudaGraphExecDestroy(g.exec);
+        }
+        c->graphs.swap(keep);
+        const unsigned long long gen0 = c->buf_gen;
+        const std::string err0 = c->err;
+        cudaGraphExec_t ex = nullptr;
+        if (c->cap_stream || !cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) {
+            cudaGraph_t gr = nullptr;
+            if (!cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)) {
+                const int brc = body(j, c->cap_stream);
+                cudaError_t e = cudaStreamEndCapture(c->cap_stream, &gr);
+                if (!brc && !e && gr && c->buf_gen == gen0 && cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess)
+                    ex = nullptr;
+                if (brc || e || c->buf_gen != gen0) {
+                    if (ex) cudaGraphExecDestroy(ex);
+                    ex = nullptr;
+                }
+                if (gr) cudaGraphDestroy(gr);
+            }
+        }
+        cudaGetLastError();   // a refused capture leaves no error behind
+        c->err = err0;
+        // a body that cannot be captured (e.g. the grid-synchronised recurrence)
+        // is remembered as such and runs uncaptured
+        c->graphs.push_back({j, R, transpose, gen0, ex});
+        return ex;
+    };
+    auto iteration = [&](int j) -> int {
+        if (warm) {
+            cudaGraphExec_t ex = graph_for(j);
+            if (ex) return lss_check_cuda(c, cudaGraphLaunch(ex, s), "iteration graph");
+        }
+        return body(j, s);
+    };
+
     std::vector<double2> hh((size_t)(m + 2) * R);
     std::vector<double> sc(R);
     auto fetch = [&](const double2* src, size_t count) -> int {
@@ -177,15 +246,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); scale_kernel<<<dim3(g1, R), 256, 0, s>>>(rv, V, K.scdev, N); }
         int j = 0;
         for (; j < m && total < maxit; ++j) {
-            double2* Vj = V + (size_t)j * RN;
-            double2* Zj = Z + (size_t)j * RN;
-            if ((rc = precond(Vj, Zj))) return rc;
-            if ((rc = lss_matvec(c, Zj, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
-            dots(K, V, RN, j + 1, w, K.hdev, 0);
-            { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, s>>>(V, RN, K.hdev, j + 1, w, N, R, -1.0); }
-            dots(K, V, RN, j + 1, w, K.h2dev, 0);
-            { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, s>>>(V, RN, K.h2dev, j + 1, w, N, R, -1.0); }
-            dots(K, w, 0, 1, w, hnorm, 0);
+            if ((rc = iteration(j))) return rc;
             // fetch h (first pass), h2 (second pass) and ||w||^2
             const size_t cnt = (size_t)(j + 1) * R;
             std::vector<double2> h1(cnt), h2v(cnt), hn(R);
@@ -279,5 +340,12 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         }
     }
     if ((rc = lss_check_device_err(c, s))) return rc;
+    if (use_graph && !warm) {   // later solves with this R and transpose replay captured iterations
+        std::vector<std::array<long long, 3>> keep;
+        for (const auto& k : c->graph_warm)
+            if ((unsigned long long)k[2] == c->buf_gen && !(k[0] == R && k[1] == transpose)) keep.push_back(k);
+        keep.push_back({(long long)R, (long long)transpose, (long long)c->buf_gen});
+        c->graph_warm.swap(keep);
+    }
     return conv ? LSS_OK : lss_fail(c, LSS_ERR_NOCONVERGE, "GMRES reached max_iter before tol");
 }

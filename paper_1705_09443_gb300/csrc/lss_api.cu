@@ -21,6 +21,9 @@ __global__ void cast_c128_c64(const double2* __restrict__ a, float2* __restrict_
 void free_ctx(lss_ctx* c) {
     if (!c) return;
     if (!c->inst.empty() || c->fork_ev) lss_batch_free(c);
+    for (auto& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);   // refused captures are kept as null entries
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
@@ -113,6 +116,7 @@ int lss_check_device_err(lss_ctx* c, cudaStream_t s) {
 
 int lss_grow(lss_ctx* c, void** p, size_t* cap, size_t bytes) {
     if (bytes <= *cap && *p) return LSS_OK;
+    ++c->buf_gen;   // captured graphs that point into the old buffer are stale
     if (*p) cudaFree(*p);
     *p = nullptr;
     *cap = 0;
@@ -279,6 +283,28 @@ int lss_profile(lss_ctx* c, int enable) {
     if (!c) return LSS_ERR_ARG;
     for (lss_ctx* ci : c->inst) lss_profile(ci, enable);
     c->prof_on = enable != 0;
+    return LSS_OK;
+}
+
+int lss_set_graphs(lss_ctx* c, int enable) {
+    if (!c) return LSS_ERR_ARG;
+    for (lss_ctx* ci : c->inst) lss_set_graphs(ci, enable);
+    c->graphs_on = enable != 0;
+    return LSS_OK;
+}
+
+int lss_graph_count(const lss_ctx* c, int* captured, int* refused) {
+    if (!c) return LSS_ERR_ARG;
+    int a = 0, b = 0;
+    for (const auto& g : c->graphs) (g.exec ? a : b) += 1;
+    for (const lss_ctx* ci : c->inst) {
+        int x = 0, y = 0;
+        lss_graph_count(ci, &x, &y);
+        a += x;
+        b += y;
+    }
+    if (captured) *captured = a;
+    if (refused) *refused = b;
     return LSS_OK;
 }
 

@@ -159,6 +159,18 @@ struct lss_ctx {
     std::vector<void*> chunk_dev;
     int num_sms = 0;
 
+    // CUDA graphs of the FGMRES iteration body (preconditioner, operator,
+    // CGS2 of basis vector j), one per (j, R, transpose), captured on
+    // cap_stream once a first uncaptured solve with the same R and transpose
+    // has grown every workspace; a graph is dropped when a workspace moves
+    // (buf_gen changes).
+    struct GraphRec { int j, R, transpose; unsigned long long gen; cudaGraphExec_t exec; };
+    bool graphs_on = true;
+    unsigned long long buf_gen = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphRec> graphs;
+    std::vector<std::array<long long, 3>> graph_warm;   // (R, transpose, buf_gen) solved once uncaptured
+
     // ragged batch (lss_setup_batch): one full context per instance, each with
     // its own stream and completion event; empty for an ordinary context
     std::vector<lss_ctx*> inst;
@@ -240,6 +252,9 @@ int lss_recurrences(lss_ctx* c, const void* maps, void* lam, void* phi, const vo
 
 // adjoint.cu: the transposed preconditioner P^T = Q^T Sweep^T E^T
 int lss_sweep_t(lss_ctx* c, const double2* y, double2* r, int R, cudaStream_t s);
+// builds the transposed interface maps now if the factorization changed (the
+// sweep would otherwise build them on first use)
+int lss_prepare_sweep_t(lss_ctx* c, cudaStream_t s);
 // gradient of a data misfit with respect to m from adjoint states mu (stencil.cu)
 int lss_gradient_m(lss_ctx* c, const double2* Kmu, const double2* u, const double* dirs_dev, double* grad, int R,
                    cudaStream_t s);

@@ -1589,6 +1589,10 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
         }
         if (rc != LSS_ERR_UNSUPPORTED) return rc;
     }
+    // a grid-synchronised kernel is not put into a captured graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (cap != cudaStreamCaptureStatusNone) return LSS_ERR_UNSUPPORTED;
     static int grid = 0;
     int grid_now;
     {

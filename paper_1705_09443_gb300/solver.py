@@ -80,6 +80,16 @@ class LSSolver:
     def profile(self, enable: bool = True):
         self._check(self.lib.lss_profile(self.ctx, int(enable)))
 
+    def use_graphs(self, enable: bool = True):
+        """Replay each GMRES iteration from a CUDA graph (lss_set_graphs)."""
+        self._check(self.lib.lss_set_graphs(self.ctx, int(enable)))
+
+    def graph_count(self):
+        """(captured, refused) iteration graphs held by the context."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lss_graph_count(self.ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def profile_read(self):
         """Device milliseconds and launch counts per kernel group since the last read."""
         k = len(_lib.PROF_CATEGORIES)
@@ -249,6 +259,9 @@ class LSSolverBatch:
 
     def profile(self, enable: bool = True):
         self._check(self.lib.lss_profile(self.ctx, int(enable)))
+
+    def use_graphs(self, enable: bool = True):
+        self._check(self.lib.lss_set_graphs(self.ctx, int(enable)))
 
     def profile_read(self):
         k = len(_lib.PROF_CATEGORIES)
