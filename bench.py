@@ -207,7 +207,8 @@ def run_ours(args, rank, world):
     results = {}
     arms = [a for a in (("mixed", LSS_MIXED), ("fp64", LSS_FP64)) if a[0] in args.arms.split(",")]
     for prec_name, prec in arms:
-        solver = LSSolver(n, w.omega, mt, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec, factor=False)
+        solver = LSSolver(n, w.omega, mt, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec)
+        tuned = solver.autotune(R)   # launch parameters for this workload, picked by timing
         stream = torch.cuda.current_stream()
 
         def step():
@@ -260,7 +261,7 @@ def run_ours(args, rank, world):
                    iters=float(np.mean(iters)), relres_true_max=relres, converged=conv, clocks=clocks,
                    prof_ms={k: v / args.steps for k, v in prof_ms.items()},
                    prof_launches={k: v // args.steps for k, v in prof_n.items()},
-                   gpu_launches=int(sum(prof_n.values())), solver=solver,
+                   gpu_launches=int(sum(prof_n.values())), solver=solver, autotune=tuned,
                    prec_bytes=8 if prec == LSS_FP64 else 4)
         # solve only (the metric's lss_solve time): factors in place, right-hand side resident
         solver.set_medium(mt)
@@ -360,7 +361,8 @@ def run_batched(args, dev, world):
     mt = torch.tensor(m, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = GmresOptions(30, 1e-8, 300)
-    solver = LSSolver(wb.n, wb.omega, mt, b_pml=wb.b_pml, b_slab=wb.b_slab, precision=LSS_MIXED, factor=False)
+    solver = LSSolver(wb.n, wb.omega, mt, b_pml=wb.b_pml, b_slab=wb.b_slab, precision=LSS_MIXED)
+    tuned = solver.autotune(R)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -400,7 +402,7 @@ def run_batched(args, dev, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total, solve_ms = (float(x) for x in t.tolist())
     relres = max(s["relres_true"] for st in stats for s in st)
-    return {"workload": args.batched, "R": R, "value": R * args.steps * world / (total / 1e3),
+    return {"workload": args.batched, "R": R, "autotune": tuned, "value": R * args.steps * world / (total / 1e3),
             "unit": "solves/s", "ms_per_step": total / args.steps,
             "solve_only": {"value": R * args.steps * world / (solve_ms / 1e3), "ms_per_solve_call": solve_ms / args.steps},
             "iters_mean": float(np.mean([s["iters"] for st in stats for s in st])), "relres_true_max": relres,
@@ -424,8 +426,11 @@ def run_ragged(args, dev, world):
     opts = GmresOptions(30, 1e-8, 300)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    batch = LSSolverBatch(ns, oms, ms, precision=LSS_MIXED, factor=False)
-    single = [LSSolver(n, om, m, precision=LSS_MIXED, factor=False) for n, om, m in zip(ns, oms, ms)]
+    batch = LSSolverBatch(ns, oms, ms, precision=LSS_MIXED)
+    batch.autotune(1)
+    single = [LSSolver(n, om, m, precision=LSS_MIXED) for n, om, m in zip(ns, oms, ms)]
+    for s in single:
+        s.autotune(1)
 
     def step_batch():
         batch.factor()
@@ -598,7 +603,7 @@ def main():
         "clocks": mix["clocks"], "roofline": dict(kernel=dom, **roof), "cpu_baseline": cpu,
         "iters": mix["iters"], "relres_true_max": mix["relres_true_max"],
         "step": "set_medium + factor (setup) + plane-wave RHS + FGMRES solve, per medium and batch",
-        "solve_only": mix["solve_only"], "setup_factor_ms": mix["setup_factor_ms"],
+        "solve_only": mix["solve_only"], "setup_factor_ms": mix["setup_factor_ms"], "autotune": mix["autotune"],
         "plain_fp64": {"value": f64["value"], "ms_per_step": f64["ms_per_step"], "iters": f64["iters"],
                        "relres_true_max": f64["relres_true_max"], "e2e": f64["e2e"],
                        "solve_only": f64["solve_only"], "setup_factor_ms": f64["setup_factor_ms"],

@@ -265,6 +265,21 @@ int lss_profile(lss_ctx *c, int enable);
  * results are the same either way.  On a batch context: every instance.
  */
 int lss_set_graphs(lss_ctx *c, int enable);
+/*
+ * lss_autotune - pick launch parameters for R right-hand sides by timing this
+ * context's own operations (CUDA events, a few runs per candidate): the FFT
+ * column group of the LS operator, the slab-solve shared-memory plan (ring
+ * stages; right-hand sides in shared or global memory) and the recurrence's
+ * ring depth.  None of them changes any result (same arithmetic, same order),
+ * so later solves agree bit for bit with untuned ones; only their speed
+ * changes.  Requires a factored context; allocates and frees two vectors;
+ * blocks the host.  On a batch: every instance.
+ *   chosen  host, 4 ints (may be NULL): column group, right-hand sides in
+ *           global memory (0) or automatic (-1), ring stages (0 = automatic),
+ *           recurrence stages
+ */
+int lss_autotune(lss_ctx *c, int R, int *chosen, void *stream);
+
 /* Iteration graphs held by the context (all instances of a batch): captured,
  * and refused (bodies that cannot be captured, e.g. with the grid-synchronised
  * recurrence of very many right-hand sides; those iterations run uncaptured). */

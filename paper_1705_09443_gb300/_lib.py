@@ -21,7 +21,7 @@ ERRORS = {
 SYMBOLS = [
     "lss_setup", "lss_set_medium", "lss_factor", "lss_plane_wave_rhs", "lss_apply_A", "lss_apply_P", "lss_solve",
     "lss_adjoint_solve", "lss_medium_gradient", "lss_solve_host", "lss_apply_slab", "lss_apply_slab_noalloc", "lss_info", "lss_slab_info", "lss_get_stencils",
-    "lss_profile", "lss_profile_read", "lss_set_graphs", "lss_graph_count", "lss_setup_batch", "lss_batch_info", "lss_batch_instance", "lss_last_error",
+    "lss_profile", "lss_profile_read", "lss_set_graphs", "lss_graph_count", "lss_autotune", "lss_setup_batch", "lss_batch_info", "lss_batch_instance", "lss_last_error",
     "lss_destroy",
 ]
 PROF_CATEGORIES = ["matvec", "sparsify", "slab_a", "recur", "slab_e", "factor", "iface", "krylov", "setup"]
@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
     lib.lss_profile_read.argtypes = [vp, vp, vp, i]
     lib.lss_set_graphs.argtypes = [vp, i]
     lib.lss_graph_count.argtypes = [vp, P(i), P(i)]
+    lib.lss_autotune.argtypes = [vp, i, P(i), vp]
     lib.lss_plane_wave_rhs.argtypes = [vp, vp, i, vp, vp, vp]
     lib.lss_apply_A.argtypes = [vp, vp, vp, i, i, vp]
     lib.lss_apply_P.argtypes = [vp, vp, vp, i, i, vp]

@@ -164,8 +164,20 @@ __global__ void mv_rows_inv(const double2* __restrict__ buf, const double2* __re
 
 int col_group(int L) { return L >= 2048 ? 1 : 2; }
 int line_threads(int L) { return L / 4 < 32 ? 32 : L / 4; }
+constexpr int kFftSmax = 200 * 1024;   // dynamic shared memory the FFT kernels are opted into
+
+int col_group(const lss_ctx* c) { return c->tune.fft_C ? c->tune.fft_C : col_group(c->L); }
 
 }  // namespace
+
+std::vector<int> lss_fft_col_candidates(const lss_ctx* c) {
+    std::vector<int> out;
+    const int L = c->L;
+    for (int C : {1, 2, 4, 8})
+        if (L % C == 0 && C * line_threads(L) <= 1024 && 2 * (size_t)C * L * sizeof(double2) <= (size_t)kFftSmax)
+            out.push_back(C);
+    return out;
+}
 
 int lss_matvec(lss_ctx* c, const double2* x, double2* y, int R, int in_mode, int out_mode,
                const double* dirs_dev, double2* uI, cudaStream_t s) {
@@ -193,7 +205,7 @@ int lss_matvec(lss_ctx* c, const double2* x, double2* y, int R, int in_mode, int
         default:
             return lss_fail(c, LSS_ERR_ARG, "matvec: bad input mode");
     }
-    const int C = col_group(L);
+    const int C = col_group(c);
     const size_t sh2 = 2 * (size_t)C * L * sizeof(double2);
     mv_cols<true><<<dim3(L / C, R), C * nt, sh2, s>>>(c->mv_buf, c->khatT, nullptr, c->tw, n, L, lg, C, 1.0);
     switch (out_mode) {
@@ -232,7 +244,7 @@ int lss_fft_configure(lss_ctx* c) {
     std::lock_guard<std::mutex> lock(lss_config_mutex());
     static bool done = false;
     if (done) return LSS_OK;
-    const int smax = 200 * 1024;
+    const int smax = kFftSmax;
     cudaError_t e = cudaSuccess;
     e = cudaFuncSetAttribute(mv_rows_fwd<MV_IN_MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     if (!e) e = cudaFuncSetAttribute(mv_rows_fwd<MV_IN_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);

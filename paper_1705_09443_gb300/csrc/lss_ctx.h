@@ -159,6 +159,14 @@ struct lss_ctx {
     std::vector<void*> chunk_dev;
     int num_sms = 0;
 
+    // launch parameters picked by lss_autotune (0 / -1: the built-in choice)
+    struct Tune {
+        int fft_C = 0;        // columns per CTA of the FFT column pass
+        int solve_bsm = -1;   // 0: slab-solve right-hand sides in global memory even when they fit shared
+        int solve_nst = 0;    // slab-solve ring stages (the stages then share the free shared memory)
+        int rec_nb = 0;       // ring stages of the TMA recurrence
+    } tune;
+
     // CUDA graphs of the FGMRES iteration body (preconditioner, operator,
     // CGS2 of basis vector j), one per (j, R, transpose), captured on
     // cap_stream once a first uncaptured solve with the same R and transpose
@@ -233,6 +241,9 @@ int lss_matvec(lss_ctx* c, const double2* x, double2* y, int R, int in_mode, int
                const double* dirs_dev, double2* uI, cudaStream_t s);
 int lss_fft_kernel_table(lss_ctx* c, const double2* kc, cudaStream_t s);  // kc: L x L -> khatT
 int lss_fft_configure(lss_ctx* c);
+std::vector<int> lss_fft_col_candidates(const lss_ctx* c);   // admissible column groups (autotuner)
+// slab.cu: chunk tables of every solve plan under the current launch parameters
+int lss_prepare_solve_tables(lss_ctx* c, cudaStream_t s);
 
 // stencil.cu: gamma tables, slab assembly, Q
 int lss_build_gamma_phys(lss_ctx* c, cudaStream_t s);

@@ -1283,13 +1283,18 @@ template <typename C>
 bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, SolvePlan* P) {
     const size_t min_stage = sizeof(C) * (size_t)max_row_ent(c);
     const size_t want = std::max<size_t>(48 * 1024, min_stage);
+    if (c->tune.solve_bsm == 0) allow_smem_b = false;
+    const int tn = c->tune.solve_nst;
     for (int bsm = allow_smem_b ? 1 : 0; bsm >= 0; --bsm) {
         const size_t fixed = tb + (bsm ? bb : 0);
         if (fixed + 2 * min_stage > kSmemBudget) continue;
         const size_t avail = kSmemBudget - fixed;
         int nst = (int)std::min<size_t>(4, avail / want);
         size_t stage = want;
-        if (nst < 2) {
+        if (tn >= 2 && avail / tn >= min_stage) {   // tuned: tn stages sharing the free shared memory
+            nst = tn;
+            stage = (avail / tn) / 16 * 16;
+        } else if (nst < 2) {
             nst = 2;
             stage = (avail / 2) / 16 * 16;
         }
@@ -1542,7 +1547,7 @@ int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     }
     const int cl = cl_size;
     lock.unlock();
-    int nb = 3;
+    int nb = c->tune.rec_nb ? std::min(c->tune.rec_nb, 4) : 3;   // full[] holds at most 4 stages
     while (nb >= 2 && smem_for(cl, nb) > (size_t)220 * 1024) --nb;
     if (nb < 2) return LSS_ERR_UNSUPPORTED;
     attr[0].val.clusterDim.x = cl;
@@ -1667,6 +1672,10 @@ int slab_apply_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, v
 }
 
 }  // namespace
+
+int lss_prepare_solve_tables(lss_ctx* c, cudaStream_t s) {
+    return c->prec == LSS_FP64 ? prepare_chunk_tables<double>(c, s) : prepare_chunk_tables<float>(c, s);
+}
 
 int lss_factor_slabs(lss_ctx* c, cudaStream_t s) {
     c->iface_t_valid = false;

@@ -84,6 +84,12 @@ class LSSolver:
         """Replay each GMRES iteration from a CUDA graph (lss_set_graphs)."""
         self._check(self.lib.lss_set_graphs(self.ctx, int(enable)))
 
+    def autotune(self, R: int = 1, stream=None):
+        """Launch parameters for R right-hand sides, picked by timing (lss_autotune)."""
+        ch = (ctypes.c_int * 4)()
+        self._check(self.lib.lss_autotune(self.ctx, int(R), ch, _stream_ptr(stream)))
+        return dict(fft_col_group=ch[0], solve_rhs_global=ch[1] == 0, solve_stages=ch[2], recur_stages=ch[3])
+
     def graph_count(self):
         """(captured, refused) iteration graphs held by the context."""
         a, b = ctypes.c_int(), ctypes.c_int()
@@ -262,6 +268,12 @@ class LSSolverBatch:
 
     def use_graphs(self, enable: bool = True):
         self._check(self.lib.lss_set_graphs(self.ctx, int(enable)))
+
+    def autotune(self, R: int = 1, stream=None):
+        """Tune every instance for R right-hand sides (lss_autotune); returns instance 0's choice."""
+        ch = (ctypes.c_int * 4)()
+        self._check(self.lib.lss_autotune(self.ctx, int(R), ch, _stream_ptr(stream)))
+        return dict(fft_col_group=ch[0], solve_rhs_global=ch[1] == 0, solve_stages=ch[2], recur_stages=ch[3])
 
     def profile_read(self):
         k = len(_lib.PROF_CATEGORIES)
