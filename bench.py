@@ -184,7 +184,8 @@ def algorithmic(solver, R, prec_bytes):
     return {
         "slab_a": dict(bytes=a_ent * cb + rhs_bytes, flops=8 * a_mac * R, launches_per_apply=1),
         "slab_e": dict(bytes=e_ent * cb + rhs_bytes, flops=8 * e_mac * R, launches_per_apply=1),
-        "iface": dict(bytes=3 * ns * nt * nt * cb, flops=8 * if_mac, launches_per_apply=3 * len(Ks) + 2),
+        # one factorization per step: its launches are the step's iface launches
+        "iface": dict(bytes=3 * ns * nt * nt * cb, flops=8 * if_mac, launches_per_apply=None),
         "matvec": dict(bytes=mv_bytes, flops=fft_flops, launches_per_apply=3),
         "recur": dict(bytes=recur_bytes * R, flops=recur_bytes // cb * 8 * R, launches_per_apply=3),
         "factor": dict(bytes=sum(nt * 3 * w * w * cb for w in ws), flops=factor_flops, launches_per_apply=None),
@@ -476,7 +477,7 @@ def run_ragged(args, dev, world):
 
 # DRAM traffic per launch group from ncu captures (profiles/iface_maps_2d_n256_mixed.md):
 # key (kernel group, workload, precision).  Stale once those kernels change.
-MEASURED_TRAFFIC = {("iface", "2d_n256", "mixed"): 2.503e9}
+MEASURED_TRAFFIC = {}
 
 
 def roofline(res, hbm_peak, hbm_src, workload="2d_n256", prec="mixed"):

@@ -184,14 +184,117 @@ __device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int ph
     }
 }
 
-// Back substitution of level l for the odd rows, all columns:
-// x_k = [y_k on its window] - (D^{-1}C)_k x_{k-s} - (D^{-1}B)_k x_{k+s};
-// level 0 (bands, rows na and w-1 of D^{-1}) writes layers na and w-1 only.
+// Back substitution of level 0 for the odd rows, layers na and w-1 only:
+// x_k[q] = y_k[q] - (D^{-1})_k[q,:] (C_k x_{k-1} + B_k x_{k+1}) for q = na, w-1.
+// The two kept rows of D^{-1} are folded into the bands once per CTA,
+// u_q = (D^{-1})_k[q,:] C_k and v_q = (D^{-1})_k[q,:] B_k (G-vectors, C and B
+// tridiagonal in the layers), so each column is four dot products of length G;
+// one thread per column, results into the compact arrays W0 (layer na) and W1
+// (layer w-1).  The thread also copies those layers of the even row k-1 (and
+// of row K-1 when it is an unpaired even row).
+constexpr int kB0N = 128;   // columns (threads) per CTA
+
 template <typename T, int G>
-__device__ void bwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l) {
+__device__ void bwd0_body(const IfArgs<cx<T>>& A, const IfProb& pr) {
     using C = cx<T>;
+    __shared__ C sb[8 * 32];     // bands of row k (6G), rows na and w-1 of its D^{-1} (2G)
+    __shared__ C uv[4][32];      // u_na, v_na, u_{w-1}, v_{w-1}
+    const int K = A.K;
+    const SlabDev sd = A.slabs[pr.slab];
+    const int bs = G * G;
+    const C* F = A.fac + sd.fac_off;
+    const int r = blockIdx.y;
+    const int k = 2 * r + 1;
+    const int j0 = blockIdx.x * kB0N;
+    if (k >= K || j0 >= K) return;   // uniform over the CTA
+    const int tid = threadIdx.x;
+    const C* bands = F + cr_t0_off(K, bs) + ((long long)(K + 1) / 2 + r) * 6 * G;
+    const C* p0 = F + cr_p0_off(K, bs, G) + (long long)r * 2 * G;
+    for (int e = tid; e < 8 * G; e += kB0N) sb[e] = e < 6 * G ? bands[e] : p0[e - 6 * G];
+    __syncthreads();
+    if (tid < G) {   // coefficient of x[a]: sum over p = a - da of D^{-1}[q][p] band[(da+1)G + p]
+        const int a = tid;
+        C u0 = czero<C>(), v0 = czero<C>(), u1 = czero<C>(), v1 = czero<C>();
+#pragma unroll
+        for (int da = -1; da <= 1; ++da) {
+            const int p = a - da;
+            if (p < 0 || p >= G) continue;
+            const C cC = sb[(da + 1) * G + p], cB = sb[3 * G + (da + 1) * G + p];
+            const C q0 = sb[6 * G + p], q1 = sb[7 * G + p];
+            u0 = cfma(q0, cC, u0);
+            v0 = cfma(q0, cB, v0);
+            u1 = cfma(q1, cC, u1);
+            v1 = cfma(q1, cB, v1);
+        }
+        uv[0][a] = u0;
+        uv[1][a] = v0;
+        uv[2][a] = u1;
+        uv[3][a] = v1;
+    }
+    __syncthreads();
+    const int j = j0 + tid;
+    if (j >= K) return;
+    const int na = sd.na, wl = sd.w - 1;
+    const bool hasR = k + 1 < K;
+    C* X = A.X + pr.xoff;
+    const C* xm = X + ((long long)(k - 1) * K + j) * G;
+    const C* xp = X + ((long long)(k + 1) * K + j) * G;
+    C d0 = czero<C>(), d1 = czero<C>(), em0 = czero<C>(), em1 = czero<C>(), ep0 = czero<C>(), ep1 = czero<C>();
+#pragma unroll
+    for (int a = 0; a < G; ++a) {
+        const C x = xm[a];
+        d0 = cfma(uv[0][a], x, d0);
+        d1 = cfma(uv[2][a], x, d1);
+        if (a == na) em0 = x;
+        if (a == wl) em1 = x;
+    }
+    if (hasR) {
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+            const C x = xp[a];
+            d0 = cfma(uv[1][a], x, d0);
+            d1 = cfma(uv[3][a], x, d1);
+            if (a == na) ep0 = x;
+            if (a == wl) ep1 = x;
+        }
+    }
+    C* W0 = A.W + pr.woff;
+    C* W1 = W0 + (long long)K * K;
+    const long long o = (long long)k * K + j;
+    C y0 = czero<C>(), y1 = czero<C>();
+    if (j == k) {   // y_k is non-zero in column k only
+        const C* yk = X + ((long long)k * K + j) * G;
+        y0 = yk[na];
+        y1 = yk[wl];
+    }
+    W0[o] = y0 - d0;
+    W1[o] = (wl == na) ? y0 - d0 : y1 - d1;
+    W0[o - K] = em0;
+    W1[o - K] = em1;
+    if (k + 1 == K - 1) {
+        W0[o + K] = ep0;
+        W1[o + K] = ep1;
+    }
+}
+
+// Back substitution of level l >= 1, register-tiled: the CTA stages
+// (D^{-1}C)_k, (D^{-1}B)_k and the column tiles of x_{k-s}, x_{k+s} (transposed
+// to [layer][column], rows padded to kBtN + 1 entries: conflict-free for both
+// the transposing store and the column reads) in shared memory; thread
+// (row group rg, column group cg) owns layers rg*TP .. rg*TP+TP-1 of columns
+// cg + 16 t, t < TJ, and subtracts the products from y in the same order as
+// the untiled loop (block C then B, layer a ascending).
+constexpr int kBtN = 64;                 // columns per CTA
+constexpr int kBtThreads = 128;          // 8 row groups x 16 column groups
+constexpr int kBtNP = kBtN + 1;
+
+template <typename T, int G>
+__device__ void bwd_tiled_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l) {
+    using C = cx<T>;
+    constexpr int RG = 8, CGN = 16, TP = G / RG, TJ = kBtN / CGN;
     extern __shared__ __align__(16) unsigned char smi[];
-    C* Ms = reinterpret_cast<C*>(smi);
+    C* Ms = reinterpret_cast<C*>(smi);   // [2][G * G], column-major blocks
+    C* Xs = Ms + 2 * G * G;              // [2][G][kBtNP]
     const int K = A.K;
     const SlabDev sd = A.slabs[pr.slab];
     const int bs = G * G;
@@ -201,87 +304,62 @@ __device__ void bwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l) {
     const int r = blockIdx.y;
     if (r >= lv.K / 2) return;
     const int k = (2 * r + 1) * s;
-    const int j0 = blockIdx.x * kIfTN;
+    const int j0 = blockIdx.x * kBtN;
     if (j0 >= K) return;
+    const int nj = min(kBtN, K - j0);
+    const int nb = k + s < K ? 2 : 1;
     C* X = A.X + pr.xoff;
-    auto at = [&](int kk, int j) { return X + ((long long)kk * K + j) * G; };
-    const int p = threadIdx.x % G, cg = threadIdx.x / G;
-    constexpr int NCG = kIfT / G, CPT = kIfTN / NCG;
-    const bool hasR = k + s < K;
+    const int tid = threadIdx.x;
+    const C* Mg = F + (lv.dcdb + 2LL * r) * bs;
+    for (int e = tid; e < nb * bs; e += kBtThreads) Ms[e] = Mg[e];
+    for (int b = 0; b < nb; ++b) {
+        const C* src = X + ((long long)(b == 0 ? k - s : k + s) * K + j0) * G;
+        C* dst = Xs + b * G * kBtNP;
+        for (int e = tid; e < nj * G; e += kBtThreads) dst[(e % G) * kBtNP + e / G] = src[e];
+    }
+    const int rg = tid / CGN, cg = tid % CGN;
     const int ylo = win_lo(k, l), yhi = win_hi(k, l, K);
-    if (l > 0) {
-        stage(Ms, F + (lv.dcdb + 2LL * r) * bs, 2 * bs);
-        __syncthreads();
+    C acc[TP][TJ];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int j = j0 + cg * CPT + q;
-            if (j >= K) continue;
-            C acc = (j >= ylo && j <= yhi) ? at(k, j)[p] : czero<C>();
-            const C* xm = at(k - s, j);
+    for (int t = 0; t < TJ; ++t) {
+        const int jj = cg + CGN * t, j = j0 + jj;
+        const bool iny = jj < nj && j >= ylo && j <= yhi;
+        const C* y = X + ((long long)k * K + j) * G + rg * TP;
 #pragma unroll
-            for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[a * G + p], xm[a], acc);
-            if (hasR) {
-                const C* xp = at(k + s, j);
-#pragma unroll
-                for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[bs + a * G + p], xp[a], acc);
-            }
-            at(k, j)[p] = acc;
-        }
-        return;
+        for (int q = 0; q < TP; ++q) acc[q][t] = iny ? y[q] : czero<C>();
     }
-    // level 0: t = C_k x_{k-1} + B_k x_{k+1} (bands), then layers na and w-1 by
-    // shuffle reductions over the lanes of a column, into the compact arrays W0
-    // (layer na) and W1 (layer w-1); the CTA also copies those layers of the
-    // even row k-1 (and of row K-1 when it is an unpaired even row).
-    stage(Ms, F + cr_t0_off(K, bs) + ((long long)(K + 1) / 2 + r) * 6 * G, 6 * G);
-    stage(Ms + 6 * G, F + cr_p0_off(K, bs, G) + (long long)r * 2 * G, 2 * G);
     __syncthreads();
-    C* W0 = A.W + pr.woff;
-    C* W1 = W0 + (long long)K * K;
-    const int na = sd.na, wl = sd.w - 1;
+    for (int b = 0; b < nb; ++b) {
+        const C* M = Ms + b * bs + rg * TP;
+        const C* Xb = Xs + b * G * kBtNP + cg;
+#pragma unroll 4
+        for (int a = 0; a < G; ++a) {
+            C m[TP], x[TJ];
 #pragma unroll
-    for (int q = 0; q < CPT; ++q) {
-        const int j = j0 + cg * CPT + q;
-        const bool on = j < K;
-        const int jc = on ? j : K - 1;
-        C t = czero<C>();
-        const C* xm = at(k - 1, jc);
+            for (int q = 0; q < TP; ++q) m[q] = M[a * G + q];
 #pragma unroll
-        for (int da = -1; da <= 1; ++da)
-            if (p + da >= 0 && p + da < G) t = cfma(Ms[(da + 1) * G + p], xm[p + da], t);
-        if (hasR) {
-            const C* xp = at(k + 1, jc);
+            for (int t = 0; t < TJ; ++t) x[t] = Xb[a * kBtNP + CGN * t];
 #pragma unroll
-            for (int da = -1; da <= 1; ++da)
-                if (p + da >= 0 && p + da < G) t = cfma(Ms[(3 + da + 1) * G + p], xp[p + da], t);
-        }
-        C d0 = Ms[6 * G + p] * t, d1 = Ms[7 * G + p] * t;
+            for (int q = 0; q < TP; ++q)
 #pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            d0.x += __shfl_xor_sync(0xffffffffu, d0.x, off, G);
-            d0.y += __shfl_xor_sync(0xffffffffu, d0.y, off, G);
-            d1.x += __shfl_xor_sync(0xffffffffu, d1.x, off, G);
-            d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
-        }
-        if (on && p == 0) {
-            const long long o = (long long)k * K + j;
-            C y0 = czero<C>(), y1 = czero<C>();
-            if (j == k) {   // y_k is non-zero in column k only
-                y0 = at(k, j)[na];
-                y1 = at(k, j)[wl];
-            }
-            W0[o] = y0 - d0;
-            W1[o] = (wl == na) ? y0 - d0 : y1 - d1;
-            const C* xe = at(k - 1, j);
-            W0[o - K] = xe[na];
-            W1[o - K] = xe[wl];
-            if (k + 1 == K - 1) {
-                const C* xl = at(K - 1, j);
-                W0[o + K] = xl[na];
-                W1[o + K] = xl[wl];
-            }
+                for (int t = 0; t < TJ; ++t) acc[q][t] = cfnma_i(m[q], x[t], acc[q][t]);
         }
     }
+#pragma unroll
+    for (int t = 0; t < TJ; ++t) {
+        const int jj = cg + CGN * t;
+        if (jj >= nj) continue;
+        C* xo = X + ((long long)k * K + j0 + jj) * G + rg * TP;
+#pragma unroll
+        for (int q = 0; q < TP; ++q) xo[q] = acc[q][t];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBtThreads) if_bwdt_kernel(IfArgs<cx<T>> A, int l, int zoff) {
+    const IfProb pr = A.probs[zoff + blockIdx.z];
+    if (pr.G == 16) bwd_tiled_body<T, 16>(A, pr, l);
+    else bwd_tiled_body<T, 32>(A, pr, l);
 }
 
 template <typename T>
@@ -292,10 +370,10 @@ __global__ void __launch_bounds__(kIfT) if_fwd_kernel(IfArgs<cx<T>> A, int l, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kIfT) if_bwd_kernel(IfArgs<cx<T>> A, int l) {
+__global__ void __launch_bounds__(kB0N) if_bwd0_kernel(IfArgs<cx<T>> A) {
     const IfProb pr = A.probs[blockIdx.z];
-    if (pr.G == 16) bwd_body<T, 16>(A, pr, l);
-    else bwd_body<T, 32>(A, pr, l);
+    if (pr.G == 16) bwd0_body<T, 16>(A, pr);
+    else bwd0_body<T, 32>(A, pr);
 }
 
 // Maps from the two kept layers and the coupling, tridiagonal in the columns.
@@ -336,17 +414,22 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     const int K = c->n_tot, ns = c->n_slabs;
     if (ns == 1) return LSS_OK;
     // problems: side 0 for slabs 1..l-1, side 1 for slabs 1..l-2
+    // (16-wide blocks first, then 32-wide, so that the tiled back substitution
+    // can size its shared memory per block width)
     std::vector<IfProb> probs;
     long long xoff = 0, woff = 0;
-    int gmax = 16;
-    for (int side = 0; side < 2; ++side)
-        for (int i = 1; i <= (side == 0 ? ns - 1 : ns - 2); ++i) {
-            IfProb p{i, side, c->slabs[i].ldw, 0, xoff, woff};
-            xoff += (long long)K * K * p.G;
-            woff += 2LL * K * K;
-            gmax = std::max(gmax, p.G);
-            probs.push_back(p);
-        }
+    int gmax = 16, n16 = 0;
+    for (int g : {16, 32})
+        for (int side = 0; side < 2; ++side)
+            for (int i = 1; i <= (side == 0 ? ns - 1 : ns - 2); ++i) {
+                if (c->slabs[i].ldw != g) continue;
+                IfProb p{i, side, g, 0, xoff, woff};
+                xoff += (long long)K * K * p.G;
+                woff += 2LL * K * K;
+                gmax = std::max(gmax, p.G);
+                n16 += g == 16;
+                probs.push_back(p);
+            }
     const int np = (int)probs.size();
     int rc = lss_grow(c, &c->ifx_buf, &c->ifx_cap, (size_t)(xoff + woff) * sizeof(C));
     if (rc) return rc;
@@ -371,7 +454,7 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     A.W = A.X + xoff;
     A.maps = (C*)c->iface;
     const size_t sh = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)8 * gmax);
-    static size_t cfg_f = 0, cfg_b = 0;
+    static size_t cfg_f = 0;
     std::unique_lock<std::mutex> lock(lss_config_mutex());
     if (sh > cfg_f) {
         cudaError_t e = cudaFuncSetAttribute(if_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -379,16 +462,19 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
         if (e) return lss_check_cuda(c, e, "interface attribute");
         cfg_f = sh;
     }
-    if (sh > cfg_b) {
-        cudaError_t e = cudaFuncSetAttribute(if_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)std::max<size_t>(sh, 48 * 1024));
+    const size_t sht = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)2 * gmax * kBtNP);
+    static size_t cfg_t = 0;
+    if (sht > cfg_t) {
+        cudaError_t e = cudaFuncSetAttribute(if_bwdt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::max<size_t>(sht, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "interface attribute");
-        cfg_b = sh;
+        cfg_t = sht;
     }
     lock.unlock();
     const int L = cr_levels(K);
     const int kt = (K + kIfTN - 1) / kIfTN;
-    ProfScope ps(c, s, LSS_PROF_IFACE, 3 * L + 2);
+    const int ncls = (n16 > 0) + (np > n16);
+    ProfScope ps(c, s, LSS_PROF_IFACE, 2 * L + 3 + (L - 1) * ncls);
     for (int l = 0; l < L; ++l) {
         const int Kl = cr_level(K, l).K;
         const int wt0 = ((1 << (l + 1)) - 1 + kIfTN - 1) / kIfTN;   // tiles of a level-l window
@@ -397,9 +483,18 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
         if_fwd_kernel<T><<<dim3(std::min(wt1, kt), (Kl + 1) / 2, np), kIfT, sh, s>>>(A, l, 1);
     }
     if_fwd_kernel<T><<<dim3(kt, 1, np), kIfT, sh, s>>>(A, L, 2);
+    const int ktt = (K + kBtN - 1) / kBtN;
     for (int l = L - 1; l >= 0; --l) {
         const int Kl = cr_level(K, l).K;
-        if_bwd_kernel<T><<<dim3(kt, std::max(1, Kl / 2), np), kIfT, sh, s>>>(A, l);
+        if (l > 0) {
+            const size_t sh16 = sizeof(C) * ((size_t)2 * 16 * 16 + (size_t)2 * 16 * kBtNP);
+            if (n16 > 0)
+                if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), n16), kBtThreads, sh16, s>>>(A, l, 0);
+            if (np > n16)
+                if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), np - n16), kBtThreads, sht, s>>>(A, l, n16);
+        } else {
+            if_bwd0_kernel<T><<<dim3((K + kB0N - 1) / kB0N, std::max(1, Kl / 2), np), kB0N, 0, s>>>(A);
+        }
     }
     if_maps_kernel<T><<<dim3((unsigned)std::min<long long>(((long long)K * K + 255) / 256, 1024), np), 256, 0,
                         s>>>(A);
