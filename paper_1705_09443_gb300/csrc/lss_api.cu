@@ -23,6 +23,9 @@ void free_ctx(lss_ctx* c) {
     if (!c->inst.empty() || c->fork_ev) lss_batch_free(c);
     for (auto& g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);   // refused captures are kept as null entries
+    for (auto st : c->aux_stream) cudaStreamDestroy(st);
+    for (auto ev : c->aux_event) cudaEventDestroy(ev);
+    if (c->fork_event) cudaEventDestroy(c->fork_event);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);

@@ -159,6 +159,12 @@ struct lss_ctx {
     std::vector<void*> chunk_dev;
     int num_sms = 0;
 
+    // auxiliary streams (and their completion events) on which slabs of other
+    // block widths factor concurrently with the first run of slabs
+    std::vector<cudaStream_t> aux_stream;
+    std::vector<cudaEvent_t> aux_event;
+    cudaEvent_t fork_event = nullptr;
+
     // launch parameters picked by lss_autotune (0 / -1: the built-in choice)
     struct Tune {
         int fft_C = 0;        // columns per CTA of the FFT column pass

@@ -113,13 +113,13 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kGjWarps) cr_gj_kernel(const SlabDev* __restrict__ slabs,
                                                               cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
                                                               long long work_len, int K0, int l, int per_slab,
-                                                              int n_slabs, int top, int rs, int* err) {
+                                                              int slab0, int n_slabs, int top, int rs, int* err) {
     using C = cx<T>;
     extern __shared__ __align__(16) unsigned char smg[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int task = blockIdx.x * kGjWarps + warp;
     if (task >= per_slab * n_slabs) return;   // the whole warp leaves
-    const int si = task / per_slab, o = task % per_slab;
+    const int si = slab0 + task / per_slab, o = task % per_slab;
     const SlabDev sd = slabs[si];
     const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
     C* M = reinterpret_cast<C*>(smg) + (size_t)warp * 32 * rs;
@@ -329,12 +329,13 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kGj0Warps) cr_gj0_kernel(const SlabDev* __restrict__ slabs,
                                                                 const cx<T>* __restrict__ coef,
                                                                 cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
-                                                                int K0, int per_slab, int n_slabs, int* err) {
+                                                                int K0, int per_slab, int slab0, int n_slabs,
+                                                                int* err) {
     __shared__ Gt0Sm<T> sm[kGj0Warps];
     const int warp = threadIdx.x >> 5;
     const int task = blockIdx.x * kGj0Warps + warp;
     if (task >= per_slab * n_slabs) return;   // the whole warp leaves
-    const SlabDev sd = slabs[task / per_slab];
+    const SlabDev sd = slabs[slab0 + task / per_slab];
     const int o = task % per_slab;
     if (sd.w <= 16) gj0_body<T, 16>(sd, coef, fac, work, K0, o, sm[warp], err);
     else gj0_body<T, 32>(sd, coef, fac, work, K0, o, sm[warp], err);
@@ -349,14 +350,13 @@ template <typename T>
 __global__ void __launch_bounds__(32 * kEvWarps) cr_even_kernel(const SlabDev* __restrict__ slabs,
                                                                 cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
                                                                 long long work_len, int K0, int l, int per_slab,
-                                                                int n_slabs, int nlev) {
+                                                                int slab0, int n_slabs, int nlev, int LS) {
     using C = cx<T>;
-    constexpr int LS = 33;
     extern __shared__ __align__(16) unsigned char sme[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int task = blockIdx.x * kEvWarps + warp;
     if (task >= per_slab * n_slabs) return;
-    const int si = task / per_slab, t = task % per_slab;
+    const int si = slab0 + task / per_slab, t = task % per_slab;
     const SlabDev sd = slabs[si];
     const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
     const int K = cr_level(K0, l).K;
@@ -1417,33 +1417,73 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
     if (rc0) return rc0;
     using C = cx<T>;
     const int K0 = c->n_tot, ns = c->n_slabs, nlev = cr_levels(K0);
-    const int wmax = wmax_of(c);
     C* fac = (C*)c->fac;
     C* work = (C*)c->cr_work;
-    const int rs = 4 * wmax + 1;
-    const size_t shg = sizeof(C) * (size_t)kGjWarps * 32 * rs;
-    const size_t she = sizeof(C) * (size_t)kEvWarps * 2 * 32 * 33;
+    // runs of consecutive slabs with the same block width: each run's launches
+    // size their shared memory for the run's widest slab (occupancy)
+    struct Run { int s0, n, w; };
+    std::vector<Run> runs;
+    for (int i = 0; i < ns; ++i) {
+        if (runs.empty() || c->slabs[i].ldw != c->slabs[runs.back().s0].ldw) runs.push_back({i, 0, 0});
+        runs.back().n += 1;
+        runs.back().w = std::max(runs.back().w, c->slabs[i].w);
+    }
+    auto shg_of = [](int w) { return sizeof(C) * (size_t)kGjWarps * 32 * (4 * w + 1); };
+    auto she_of = [](int w) { return sizeof(C) * (size_t)kEvWarps * 2 * 32 * (w + 1); };
+    size_t shg = 0, she = 0;
+    for (const Run& u : runs) {
+        shg = std::max(shg, shg_of(u.w));
+        she = std::max(she, she_of(u.w));
+    }
     static size_t cfg_g = 0, cfg_e = 0;
     int rc = set_smem(c, cr_gj_kernel<T>, shg, &cfg_g);
     if (!rc) rc = set_smem(c, cr_even_kernel<T>, she, &cfg_e);
     if (rc) return rc;
-    {
-        ProfScope ps(c, s, LSS_PROF_FACTOR, 2 * nlev + 2);
-        cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
-        for (int l = 0; l < nlev; ++l) {
-            const int K = cr_level(K0, l).K;
-            const int nodd = K / 2, nev = (K + 1) / 2;
-            if (l == 0)
-                cr_gj0_kernel<T><<<(nodd * ns + kGj0Warps - 1) / kGj0Warps, 32 * kGj0Warps, 0, s>>>(
-                    c->d_slabs, (const C*)c->coef, fac, work, K0, nodd, ns, c->d_err);
-            else
-                cr_gj_kernel<T><<<(nodd * ns + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg, s>>>(
-                    c->d_slabs, fac, work, c->work_len, K0, l, nodd, ns, 0, rs, c->d_err);
-            cr_even_kernel<T><<<(nev * ns + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she, s>>>(
-                c->d_slabs, fac, work, c->work_len, K0, l, nev, ns, nlev);
+    // slabs factor independently: run 0 on s, every other run on an auxiliary
+    // stream of its own, forked after the level-0 blocks are built and joined
+    // before the interface maps
+    while (c->aux_stream.size() + 1 < runs.size()) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e) {
+            if (st) cudaStreamDestroy(st);
+            return lss_check_cuda(c, e, "factor streams");
         }
-        cr_gj_kernel<T><<<(ns + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg, s>>>(c->d_slabs, fac, work, c->work_len,
-                                                                                  K0, nlev, 1, ns, 1, rs, c->d_err);
+        c->aux_stream.push_back(st);
+        c->aux_event.push_back(ev);
+    }
+    if (!c->fork_event && (rc = lss_check_cuda(c, cudaEventCreateWithFlags(&c->fork_event, cudaEventDisableTiming),
+                                                "factor streams")))
+        return rc;
+    {
+        ProfScope ps(c, s, LSS_PROF_FACTOR, 2 + (2 * nlev) * (int)runs.size());
+        cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
+        cudaEventRecord(c->fork_event, s);
+        for (size_t ri = 0; ri < runs.size(); ++ri) {
+            const Run& u = runs[ri];
+            cudaStream_t su = ri == 0 ? s : c->aux_stream[ri - 1];
+            if (ri > 0) cudaStreamWaitEvent(su, c->fork_event, 0);
+            for (int l = 0; l < nlev; ++l) {
+                const int K = cr_level(K0, l).K;
+                const int nodd = K / 2, nev = (K + 1) / 2;
+                if (l == 0)
+                    cr_gj0_kernel<T><<<(nodd * u.n + kGj0Warps - 1) / kGj0Warps, 32 * kGj0Warps, 0, su>>>(
+                        c->d_slabs, (const C*)c->coef, fac, work, K0, nodd, u.s0, u.n, c->d_err);
+                else
+                    cr_gj_kernel<T><<<(nodd * u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
+                        c->d_slabs, fac, work, c->work_len, K0, l, nodd, u.s0, u.n, 0, 4 * u.w + 1, c->d_err);
+                cr_even_kernel<T><<<(nev * u.n + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she_of(u.w), su>>>(
+                    c->d_slabs, fac, work, c->work_len, K0, l, nev, u.s0, u.n, nlev, u.w + 1);
+            }
+            cr_gj_kernel<T><<<(u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
+                c->d_slabs, fac, work, c->work_len, K0, nlev, 1, u.s0, u.n, 1, 4 * u.w + 1, c->d_err);
+            if (ri > 0) {
+                cudaEventRecord(c->aux_event[ri - 1], su);
+                cudaStreamWaitEvent(s, c->aux_event[ri - 1], 0);
+            }
+        }
     }
     rc = lss_check_cuda(c, cudaGetLastError(), "factor launch");
     if (rc || ns == 1) return rc;
