@@ -464,6 +464,213 @@ __global__ void __launch_bounds__(32 * kEvWarps) cr_even_kernel(const SlabDev* _
     }
 }
 
+// Wide slabs (more than 16 layers) have few block rows per level and each
+// of them would keep one warp busy for a long dependent chain; these two
+// kernels give a block row a whole CTA instead.
+constexpr int kWideThreads = 256;
+
+// Gauss-Jordan of cr_gj_kernel (same pivot rule: largest modulus in the
+// column, lowest row on ties) with a CTA per block row: warp 0 picks the
+// pivot, the threads swap and scale row jj column-wise, then thread
+// (column q, row parity) eliminates every other row i = parity, parity+2, ...
+template <typename T>
+__global__ void __launch_bounds__(kWideThreads) cr_gjw_kernel(const SlabDev* __restrict__ slabs,
+                                                             cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
+                                                             long long work_len, int K0, int l, int per_slab,
+                                                             int slab0, int top, int rs, int* err) {
+    using C = cx<T>;
+    extern __shared__ __align__(16) unsigned char smw[];
+    __shared__ int s_piv;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int task = blockIdx.x;
+    const int si = slab0 + task / per_slab, o = task % per_slab;
+    const SlabDev sd = slabs[si];
+    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
+    C* M = reinterpret_cast<C*>(smw);
+    const CrLevelOffs lo = cr_level(K0, l);
+    const int K = lo.K;
+    C* W = work + sd.work_off + (l & 1) * work_len;
+    C* F = fac + sd.fac_off;
+    const int j = top ? 0 : 2 * o + 1;
+    const int ncol = top ? 2 * w : 4 * w;
+    const C* Ab = W + (long long)j * bs;
+    const C* Cb = W + ((long long)K0 + 2LL * j) * bs;
+    const C* Bb = Cb + bs;
+    const bool hasB = !top && j + 1 < K;
+    for (int e = tid; e < w * ncol; e += kWideThreads) {
+        const int i = e / ncol, q = e % ncol;
+        C v = czero<C>();
+        if (q < w) v = Ab[(long long)q * ldw + i];
+        else if (q < 2 * w) { if (q - w == i) v.x = T(1); }
+        else if (q < 3 * w) v = Cb[(long long)(q - 2 * w) * ldw + i];
+        else if (hasB) v = Bb[(long long)(q - 3 * w) * ldw + i];
+        M[i * rs + q] = v;
+    }
+    __syncthreads();
+    const int tq = tid % 128, par = tid / 128;
+    for (int jj = 0; jj < w; ++jj) {
+        if (tid < 32) {
+            T val = (lane >= jj && lane < w) ? cabs2(M[lane * rs + jj]) : T(-1);
+            if (!(val >= T(0)) || !isfinite(val)) val = (lane >= jj && lane < w) ? T(0) : T(-1);
+            int best = lane;
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ov = __shfl_xor_sync(0xffffffffu, val, off);
+                const int ob = __shfl_xor_sync(0xffffffffu, best, off);
+                if (ov > val || (ov == val && ob < best)) { val = ov; best = ob; }
+            }
+            if (lane == 0) s_piv = best;
+        }
+        __syncthreads();
+        const int r = s_piv;
+        if (r != jj)
+            for (int q = jj + tid; q < ncol; q += kWideThreads) {
+                const C t = M[jj * rs + q];
+                M[jj * rs + q] = M[r * rs + q];
+                M[r * rs + q] = t;
+            }
+        __syncthreads();
+        C pv = M[jj * rs + jj];
+        const T a2 = cabs2(pv);
+        if (!(a2 > T(0)) || !isfinite(a2)) {
+            if (tid == 0) atomicOr(err, LSS_DERR_SINGULAR);
+            pv = czero<C>();
+            pv.x = T(1);
+        }
+        const C pinv = crecip(pv);
+        __syncthreads();   // every thread has read the pivot before row jj is scaled
+        for (int q = jj + 1 + tid; q < ncol; q += kWideThreads) M[jj * rs + q] = M[jj * rs + q] * pinv;
+        __syncthreads();
+        // column jj is not written below and not read after this pivot
+        for (int q = jj + 1 + tq; q < ncol; q += 128) {
+            const C mj = M[jj * rs + q];
+            for (int i = par; i < w; i += 2)
+                if (i != jj) M[i * rs + q] = cfnma(M[i * rs + jj], mj, M[i * rs + q]);
+        }
+        __syncthreads();
+    }
+    C* Dout = F + (lo.dinv + (top ? 0 : o)) * bs;
+    C* DCw = W + (3LL * K0 + 2LL * o) * bs;
+    C* DCf = (!top && l >= 1) ? F + (lo.dcdb + 2LL * o) * bs : nullptr;
+    for (int e = tid; e < bs; e += kWideThreads) {
+        const int q = e / ldw, p = e % ldw;
+        const bool in = p < w && q < w;
+        Dout[e] = in ? M[p * rs + w + q] : czero<C>();
+        if (!top) {
+            const C dc = in ? M[p * rs + 2 * w + q] : czero<C>();
+            const C db = in ? M[p * rs + 3 * w + q] : czero<C>();
+            DCw[e] = dc;
+            DCw[bs + e] = db;
+            if (DCf) {
+                DCf[e] = dc;
+                DCf[bs + e] = db;
+            }
+        }
+    }
+}
+
+// Even rows of cr_even_kernel with a CTA per block row: C_e, B_e row-major
+// and the four right factors transposed (row a of a factor holds its entries
+// (a, q) for all columns q) in shared memory; thread (column q, row group g)
+// computes rows g, g+8, g+16, g+24 of column q of A', C', B', summing over a
+// in ascending order as the warp version does.
+template <typename T>
+__global__ void __launch_bounds__(kWideThreads) cr_evenw_kernel(const SlabDev* __restrict__ slabs,
+                                                               cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
+                                                               long long work_len, int K0, int l, int per_slab,
+                                                               int slab0, int nlev) {
+    using C = cx<T>;
+    constexpr int LS = 33;
+    extern __shared__ __align__(16) unsigned char smv[];
+    const int tid = threadIdx.x;
+    const int si = slab0 + blockIdx.x / per_slab, t = blockIdx.x % per_slab;
+    const SlabDev sd = slabs[si];
+    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
+    const int K = cr_level(K0, l).K;
+    const C* W = work + sd.work_off + (l & 1) * work_len;
+    C* Wn = work + sd.work_off + ((l + 1) & 1) * work_len;
+    C* F = fac + sd.fac_off;
+    const int e = 2 * t;
+    const bool hasL = e >= 1, hasR = e + 1 < K;
+    const C* Ae = W + (long long)e * bs;
+    const C* Ce = W + ((long long)K0 + 2LL * e) * bs;
+    const C* Be = Ce + bs;
+    const C* DCm = W + (3LL * K0 + 2LL * (t - 1)) * bs;   // odd row e-1
+    const C* DCp = W + (3LL * K0 + 2LL * t) * bs;         // odd row e+1
+    C* An = Wn + (long long)t * bs;
+    const bool next_cb = l + 1 < nlev;
+    C* Cn = Wn + ((long long)K0 + 2LL * t) * bs;
+    C* Bn = Cn + bs;
+    C* Cf = nullptr;
+    if (next_cb && (t & 1) == 0) Cf = F + (cr_level(K0, l + 1).cbe + 2LL * (t >> 1)) * bs;
+    C* L0 = reinterpret_cast<C*>(smv);   // C_e, row-major, stride LS
+    C* L1 = L0 + 32 * LS;                // B_e
+    C* Rt = L1 + 32 * LS;                // 4 right factors, transposed, stride LS
+    const C* rsrc[4] = {DCm + bs, DCp, DCm, DCp + bs};   // (D^{-1}B)_{e-1}, (D^{-1}C)_{e+1}, (D^{-1}C)_{e-1}, (D^{-1}B)_{e+1}
+    const bool rhas[4] = {hasL, hasR, hasL && next_cb, hasR && next_cb};
+    for (int x = tid; x < w * w; x += kWideThreads) {
+        const int p = x % w, a = x / w;
+        L0[p * LS + a] = Ce[(long long)a * ldw + p];
+        L1[p * LS + a] = Be[(long long)a * ldw + p];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)   // entry (p, a) of column a of factor f -> row p of its transpose
+            if (rhas[f]) Rt[f * 32 * LS + p * LS + a] = rsrc[f][(long long)a * ldw + p];
+    }
+    __syncthreads();
+    const int q = tid & 31, g = tid >> 5;
+    // out (rows g + 8 u) = init - L R_f for the staged left factor L
+    auto product = [&](const C* L, int f, C (&out)[4]) {
+        const C* R = Rt + f * 32 * LS;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pp = g + 8 * u;
+            if (pp >= w) break;
+            C acc = czero<C>();
+            if (l == 0) {
+#pragma unroll
+                for (int da = -1; da <= 1; ++da)
+                    if (pp + da >= 0 && pp + da < w) acc = cfma(L[pp * LS + pp + da], R[(pp + da) * LS + q], acc);
+            } else {
+                for (int a = 0; a < w; ++a) acc = cfma(L[pp * LS + a], R[a * LS + q], acc);
+            }
+            out[u] = out[u] - acc;
+        }
+    };
+    if (q < ldw) {
+        C oa[4], oc[4], ob[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pp = g + 8 * u;
+            oa[u] = (q < w && pp < w) ? Ae[(long long)q * ldw + pp] : czero<C>();
+            oc[u] = czero<C>();
+            ob[u] = czero<C>();
+        }
+        if (q < w) {
+            if (hasL) product(L0, 0, oa);
+            if (hasR) product(L1, 1, oa);
+            if (next_cb) {
+                if (hasL) product(L0, 2, oc);
+                if (hasR) product(L1, 3, ob);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int pp = g + 8 * u;
+            if (pp >= ldw) break;
+            const bool in = q < w && pp < w;
+            const long long o = (long long)q * ldw + pp;
+            An[o] = in ? oa[u] : czero<C>();
+            if (next_cb) {
+                Cn[o] = in ? oc[u] : czero<C>();
+                Bn[o] = in ? ob[u] : czero<C>();
+                if (Cf) {
+                    Cf[o] = in ? oc[u] : czero<C>();
+                    Cf[bs + o] = in ? ob[u] : czero<C>();
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- slab solves
 // One kernel for the three uses of T~_i:
 //   CR_A    sweep, first pass: a_i = T~_i f_i, first and last layers kept;
@@ -1435,9 +1642,13 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
         shg = std::max(shg, shg_of(u.w));
         she = std::max(she, she_of(u.w));
     }
-    static size_t cfg_g = 0, cfg_e = 0;
+    auto shgw_of = [](int w) { return sizeof(C) * (size_t)w * (4 * w + 1); };
+    const size_t shew = sizeof(C) * (size_t)6 * 32 * 33;
+    static size_t cfg_g = 0, cfg_e = 0, cfg_gw = 0, cfg_ew = 0;
     int rc = set_smem(c, cr_gj_kernel<T>, shg, &cfg_g);
     if (!rc) rc = set_smem(c, cr_even_kernel<T>, she, &cfg_e);
+    if (!rc) rc = set_smem(c, cr_gjw_kernel<T>, shgw_of(32), &cfg_gw);
+    if (!rc) rc = set_smem(c, cr_evenw_kernel<T>, shew, &cfg_ew);
     if (rc) return rc;
     // slabs factor independently: run 0 on s, every other run on an auxiliary
     // stream of its own, forked after the level-0 blocks are built and joined
@@ -1465,20 +1676,32 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
             const Run& u = runs[ri];
             cudaStream_t su = ri == 0 ? s : c->aux_stream[ri - 1];
             if (ri > 0) cudaStreamWaitEvent(su, c->fork_event, 0);
+            const bool wide = u.w > 16;   // a CTA per block row
             for (int l = 0; l < nlev; ++l) {
                 const int K = cr_level(K0, l).K;
                 const int nodd = K / 2, nev = (K + 1) / 2;
                 if (l == 0)
                     cr_gj0_kernel<T><<<(nodd * u.n + kGj0Warps - 1) / kGj0Warps, 32 * kGj0Warps, 0, su>>>(
                         c->d_slabs, (const C*)c->coef, fac, work, K0, nodd, u.s0, u.n, c->d_err);
+                else if (wide)
+                    cr_gjw_kernel<T><<<nodd * u.n, kWideThreads, shgw_of(u.w), su>>>(
+                        c->d_slabs, fac, work, c->work_len, K0, l, nodd, u.s0, 0, 4 * u.w + 1, c->d_err);
                 else
                     cr_gj_kernel<T><<<(nodd * u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
                         c->d_slabs, fac, work, c->work_len, K0, l, nodd, u.s0, u.n, 0, 4 * u.w + 1, c->d_err);
-                cr_even_kernel<T><<<(nev * u.n + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she_of(u.w), su>>>(
-                    c->d_slabs, fac, work, c->work_len, K0, l, nev, u.s0, u.n, nlev, u.w + 1);
+                if (wide)
+                    cr_evenw_kernel<T><<<nev * u.n, kWideThreads, shew, su>>>(c->d_slabs, fac, work, c->work_len,
+                                                                             K0, l, nev, u.s0, nlev);
+                else
+                    cr_even_kernel<T><<<(nev * u.n + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she_of(u.w), su>>>(
+                        c->d_slabs, fac, work, c->work_len, K0, l, nev, u.s0, u.n, nlev, u.w + 1);
             }
-            cr_gj_kernel<T><<<(u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
-                c->d_slabs, fac, work, c->work_len, K0, nlev, 1, u.s0, u.n, 1, 4 * u.w + 1, c->d_err);
+            if (wide)
+                cr_gjw_kernel<T><<<u.n, kWideThreads, shgw_of(u.w), su>>>(c->d_slabs, fac, work, c->work_len, K0,
+                                                                          nlev, 1, u.s0, 1, 4 * u.w + 1, c->d_err);
+            else
+                cr_gj_kernel<T><<<(u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
+                    c->d_slabs, fac, work, c->work_len, K0, nlev, 1, u.s0, u.n, 1, 4 * u.w + 1, c->d_err);
             if (ri > 0) {
                 cudaEventRecord(c->aux_event[ri - 1], su);
                 cudaStreamWaitEvent(s, c->aux_event[ri - 1], 0);
