@@ -73,25 +73,40 @@ __device__ void gamma_from_F(double2 F[9][8], double2 out[9]) {
 
 // Stencil for stretch triples s1, s2 (sigma at offsets -1, 0, +1 along x1, x2)
 // and local frequency w: F[o][r] = exp(i w r.(dp_o + i dsigma_o)) over the
-// 8 normalised neighbour directions r.
+// 8 normalised neighbour directions r.  The exponential factors into an x1
+// and an x2 part, E1(da, sc ra) E2(db, sc rb) with E(d, v) = exp(i w v (d h +
+// i dsigma_d)), and E(d, -v) has the conjugate phase and the reciprocal
+// modulus of E(d, v): 2 x 3 x 2 complex exponentials give all 72 entries.
 __device__ void pml_stencil(const double s1[3], const double s2[3], double w, double h, double2 out[9]) {
-    double2 F[9][8];
     const double is2 = 0.70710678118654752440;
+    // E[axis][d + 1][scale][sign]: scale 0 -> v = 1, 1 -> v = 1/sqrt(2); sign 0 -> +v, 1 -> -v
+    double2 E[2][3][2][2];
+    for (int ax = 0; ax < 2; ++ax) {
+        const double* sg = ax == 0 ? s1 : s2;
+        for (int d = -1; d <= 1; ++d) {
+            const double re = d * h, im = sg[d + 1] - sg[1];
+            for (int sc = 0; sc < 2; ++sc) {
+                const double v = sc ? is2 : 1.0;
+                double sn, cs;
+                sincos(w * v * re, &sn, &cs);
+                const double mag = exp(-w * v * im);
+                const double inv = 1.0 / mag;
+                E[ax][d + 1][sc][0] = mk(mag * cs, mag * sn);
+                E[ax][d + 1][sc][1] = mk(inv * cs, -inv * sn);
+            }
+        }
+    }
+    double2 F[9][8];
     for (int o = 0; o < 9; ++o) {
         const int da = o / 3 - 1, db = o % 3 - 1;
-        const double re1 = da * h, im1 = s1[da + 1] - s1[1];
-        const double re2 = db * h, im2 = s2[db + 1] - s2[1];
         int col = 0;
         for (int ra = -1; ra <= 1; ++ra)
             for (int rb = -1; rb <= 1; ++rb) {
                 if (ra == 0 && rb == 0) continue;
-                const double sc = (ra != 0 && rb != 0) ? is2 : 1.0;
-                const double pr = sc * (ra * re1 + rb * re2);   // real part of r.dz
-                const double pi = sc * (ra * im1 + rb * im2);   // imaginary part
-                double sn, cs;
-                sincos(w * pr, &sn, &cs);
-                const double mag = exp(-w * pi);
-                F[o][col++] = mk(mag * cs, mag * sn);
+                const int sc = (ra != 0 && rb != 0) ? 1 : 0;
+                const double2 e1 = ra == 0 ? mk(1.0, 0.0) : E[0][da + 1][sc][ra < 0];
+                const double2 e2 = rb == 0 ? mk(1.0, 0.0) : E[1][db + 1][sc][rb < 0];
+                F[o][col++] = e1 * e2;
             }
     }
     gamma_from_F(F, out);
