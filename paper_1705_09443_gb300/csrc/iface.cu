@@ -232,32 +232,41 @@ __device__ void bwd0_body(const IfArgs<cx<T>>& A, const IfProb& pr) {
         uv[3][a] = v1;
     }
     __syncthreads();
-    const int j = j0 + tid;
-    if (j >= K) return;
+    // the neighbours' column tiles go through shared memory (coalesced loads,
+    // rows padded to G + 1 entries so that each thread's column reads are
+    // conflict-free), one neighbour at a time
+    extern __shared__ __align__(16) unsigned char smb[];
+    C* tile = reinterpret_cast<C*>(smb);   // kB0N x (G + 1)
     const int na = sd.na, wl = sd.w - 1;
     const bool hasR = k + 1 < K;
+    const int nj = min(kB0N, K - j0);
     C* X = A.X + pr.xoff;
-    const C* xm = X + ((long long)(k - 1) * K + j) * G;
-    const C* xp = X + ((long long)(k + 1) * K + j) * G;
+    const int j = j0 + tid;
+    const bool on = tid < nj;
     C d0 = czero<C>(), d1 = czero<C>(), em0 = czero<C>(), em1 = czero<C>(), ep0 = czero<C>(), ep1 = czero<C>();
+    for (int side = 0; side < (hasR ? 2 : 1); ++side) {
+        const C* src = X + ((long long)(side == 0 ? k - 1 : k + 1) * K + j0) * G;
+        if (side) __syncthreads();   // the previous tile is consumed
+        for (int e = tid; e < nj * G; e += kB0N) tile[(e / G) * (G + 1) + e % G] = src[e];
+        __syncthreads();
+        if (on) {
+            const C* x = tile + tid * (G + 1);
+            const C* u = uv[side == 0 ? 0 : 1];
+            const C* v = uv[side == 0 ? 2 : 3];
+            C c0 = czero<C>(), c1 = czero<C>();
 #pragma unroll
-    for (int a = 0; a < G; ++a) {
-        const C x = xm[a];
-        d0 = cfma(uv[0][a], x, d0);
-        d1 = cfma(uv[2][a], x, d1);
-        if (a == na) em0 = x;
-        if (a == wl) em1 = x;
-    }
-    if (hasR) {
-#pragma unroll
-        for (int a = 0; a < G; ++a) {
-            const C x = xp[a];
-            d0 = cfma(uv[1][a], x, d0);
-            d1 = cfma(uv[3][a], x, d1);
-            if (a == na) ep0 = x;
-            if (a == wl) ep1 = x;
+            for (int a = 0; a < G; ++a) {
+                const C xa = x[a];
+                d0 = cfma(u[a], xa, d0);
+                d1 = cfma(v[a], xa, d1);
+                if (a == na) c0 = xa;
+                if (a == wl) c1 = xa;
+            }
+            if (side == 0) { em0 = c0; em1 = c1; }
+            else { ep0 = c0; ep1 = c1; }
         }
     }
+    if (!on) return;
     C* W0 = A.W + pr.woff;
     C* W1 = W0 + (long long)K * K;
     const long long o = (long long)k * K + j;
@@ -463,7 +472,14 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
         cfg_f = sh;
     }
     const size_t sht = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)2 * gmax * kBtNP);
-    static size_t cfg_t = 0;
+    const size_t sh0 = sizeof(C) * (size_t)kB0N * (gmax + 1);
+    static size_t cfg_t = 0, cfg_0 = 0;
+    if (sh0 > cfg_0) {
+        cudaError_t e = cudaFuncSetAttribute(if_bwd0_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::max<size_t>(sh0, 48 * 1024));
+        if (e) return lss_check_cuda(c, e, "interface attribute");
+        cfg_0 = sh0;
+    }
     if (sht > cfg_t) {
         cudaError_t e = cudaFuncSetAttribute(if_bwdt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sht, 48 * 1024));
@@ -493,7 +509,7 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
             if (np > n16)
                 if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), np - n16), kBtThreads, sht, s>>>(A, l, n16);
         } else {
-            if_bwd0_kernel<T><<<dim3((K + kB0N - 1) / kB0N, std::max(1, Kl / 2), np), kB0N, 0, s>>>(A);
+            if_bwd0_kernel<T><<<dim3((K + kB0N - 1) / kB0N, std::max(1, Kl / 2), np), kB0N, sh0, s>>>(A);
         }
     }
     if_maps_kernel<T><<<dim3((unsigned)std::min<long long>(((long long)K * K + 255) / 256, 1024), np), 256, 0,
