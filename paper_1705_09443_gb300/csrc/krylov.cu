@@ -42,14 +42,21 @@ __global__ void __launch_bounds__(kRedThreads) dots_kernel(const double2* __rest
     if (threadIdx.x == 0) part[((long long)i * R + r) * nblk + blockIdx.x] = red[0];
 }
 
-// h[i*R + r] (+)= sum_blk part[...]   (fixed order: deterministic)
-__global__ void reduce_kernel(const double2* __restrict__ part, int nblk, int JR, double2* __restrict__ h,
-                              int accumulate) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= JR) return;
+// h[e] (+)= sum_blk part[e * nblk + blk], e = i*R + r: one CTA per e, strided
+// partial sums then a fixed tree (deterministic: the same order every call)
+__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double2* __restrict__ part, int nblk,
+                                                             double2* __restrict__ h, int accumulate) {
+    __shared__ double2 red[kRedThreads];
+    const int e = blockIdx.x;
     double2 acc = mk(0.0, 0.0);
-    for (int b = 0; b < nblk; ++b) acc = acc + part[(long long)e * nblk + b];
-    h[e] = accumulate ? h[e] + acc : acc;
+    for (int b = threadIdx.x; b < nblk; b += kRedThreads) acc = acc + part[(long long)e * nblk + b];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) h[e] = accumulate ? h[e] + red[0] : red[0];
 }
 
 // w[r][x] += sign * sum_{i<J} h[i*R + r] V_i[r][x]
@@ -98,7 +105,7 @@ void dots(Krylov& K, const double2* V, long long vstride, int J, const double2* 
     ProfScope ps(K.c, K.s, LSS_PROF_KRYLOV, 2);
     dots_kernel<<<dim3(K.nblk, K.R, J), kRedThreads, 0, K.s>>>(V, vstride, w, K.N, K.R, K.part);
     const int JR = J * K.R;
-    reduce_kernel<<<(JR + 127) / 128, 128, 0, K.s>>>(K.part, K.nblk, JR, h, accumulate);
+    reduce_kernel<<<JR, kRedThreads, 0, K.s>>>(K.part, K.nblk, h, accumulate);
 }
 
 }  // namespace
