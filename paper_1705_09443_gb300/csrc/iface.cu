@@ -136,14 +136,25 @@ __device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int ph
         }
         return;
     }
-    // even rows: b_k -= C_k y_{k-s} + B_k y_{k+s}
+    // even rows: b_k -= C_k y_{k-s} + B_k y_{k+s}; a row that is odd at level
+    // l+1 (index r odd there) or the top row then applies its next-level
+    // D^{-1} in place (the phase 0 of level l+1, or phase 2, fused: the
+    // layers of a column are the G lanes of one column group)
     const bool hasL = k - s >= 0, hasR = k + s < K;
+    const int L = cr_levels(K);
+    const bool top_next = l + 1 == L && r == 0;
+    // (single precision only: in double precision the shuffles cost more than
+    // the separate launches they save)
+    const bool fuse = sizeof(T) == 4 && (top_next || (l + 1 < L && (r & 1)));
+    C* Dn = Ms + 2 * bs;   // the next-level D^{-1} (2 bs >= 6G for the bands of level 0)
     if (l == 0) {
         const C* t0 = F + cr_t0_off(K, bs) + (long long)r * 6 * G;   // even row r's bands
         stage(Ms, t0, 6 * G);
     } else {
         stage(Ms, F + (lv.cbe + 2LL * r) * bs, 2 * bs);
     }
+    if (fuse)
+        stage(Dn, F + (top_next ? cr_level(K, L).dinv : cr_level(K, l + 1).dinv + (r - 1) / 2) * bs, bs);
     __syncthreads();
     const int llo = win_lo(k, l), lhi = win_hi(k, l, K);
     const int mlo = win_lo(k - s, l), mhi = hasL ? win_hi(k - s, l, K) : -1;
@@ -151,14 +162,16 @@ __device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int ph
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
         const int j = j0 + cg * CPT + q;
-        if (j > hi || j >= j0 + kIfTN) continue;
+        const bool valid = j <= hi && j < j0 + kIfTN;   // uniform over the column group
         C acc = czero<C>();
-        if (l == 0) {
+        if (!valid) {
+            // nothing to compute; the group still takes part in the shuffles below
+        } else if (l == 0) {
             if (j == k && p == pin) acc.x = T(1);
         } else if (j >= llo && j <= lhi) {
             acc = at(k, j)[p];
         }
-        if (hasL && j >= mlo && j <= mhi) {
+        if (valid && hasL && j >= mlo && j <= mhi) {
             const C* x = at(k - s, j);
             if (l == 0) {
 #pragma unroll
@@ -169,7 +182,7 @@ __device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int ph
                 for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[a * G + p], x[a], acc);
             }
         }
-        if (hasR && j >= plo && j <= phi) {
+        if (valid && hasR && j >= plo && j <= phi) {
             const C* x = at(k + s, j);
             if (l == 0) {
 #pragma unroll
@@ -180,7 +193,18 @@ __device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int ph
                 for (int a = 0; a < G; ++a) acc = cfnma_i(Ms[bs + a * G + p], x[a], acc);
             }
         }
-        at(k, j)[p] = acc;
+        if (fuse) {   // y = D^{-1} b over the layers of the column
+            C y = czero<C>();
+#pragma unroll
+            for (int a = 0; a < G; ++a) {
+                C ba;
+                ba.x = __shfl_sync(0xffffffffu, acc.x, a, G);
+                ba.y = __shfl_sync(0xffffffffu, acc.y, a, G);
+                y = cfma(Dn[a * G + p], ba, y);
+            }
+            acc = y;
+        }
+        if (valid) at(k, j)[p] = acc;
     }
 }
 
@@ -244,13 +268,18 @@ __device__ void bwd0_body(const IfArgs<cx<T>>& A, const IfProb& pr) {
     const int j = j0 + tid;
     const bool on = tid < nj;
     C d0 = czero<C>(), d1 = czero<C>(), em0 = czero<C>(), em1 = czero<C>(), ep0 = czero<C>(), ep1 = czero<C>();
+    // (double precision reads its columns directly: its 16-byte entries already
+    // make the per-thread column walk efficient, and the tile costs occupancy)
+    constexpr bool staged = sizeof(T) == 4;
     for (int side = 0; side < (hasR ? 2 : 1); ++side) {
         const C* src = X + ((long long)(side == 0 ? k - 1 : k + 1) * K + j0) * G;
-        if (side) __syncthreads();   // the previous tile is consumed
-        for (int e = tid; e < nj * G; e += kB0N) tile[(e / G) * (G + 1) + e % G] = src[e];
-        __syncthreads();
+        if (staged) {
+            if (side) __syncthreads();   // the previous tile is consumed
+            for (int e = tid; e < nj * G; e += kB0N) tile[(e / G) * (G + 1) + e % G] = src[e];
+            __syncthreads();
+        }
         if (on) {
-            const C* x = tile + tid * (G + 1);
+            const C* x = staged ? tile + tid * (G + 1) : src + (long long)tid * G;
             const C* u = uv[side == 0 ? 0 : 1];
             const C* v = uv[side == 0 ? 2 : 3];
             C c0 = czero<C>(), c1 = czero<C>();
@@ -462,7 +491,7 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     A.X = (C*)c->ifx_buf;
     A.W = A.X + xoff;
     A.maps = (C*)c->iface;
-    const size_t sh = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)8 * gmax);
+    const size_t sh = sizeof(C) * ((size_t)3 * gmax * gmax + (size_t)8 * gmax);
     static size_t cfg_f = 0;
     std::unique_lock<std::mutex> lock(lss_config_mutex());
     if (sh > cfg_f) {
@@ -472,9 +501,9 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
         cfg_f = sh;
     }
     const size_t sht = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)2 * gmax * kBtNP);
-    const size_t sh0 = sizeof(C) * (size_t)kB0N * (gmax + 1);
+    const size_t sh0 = sizeof(T) == 4 ? sizeof(C) * (size_t)kB0N * (gmax + 1) : 0;
     static size_t cfg_t = 0, cfg_0 = 0;
-    if (sh0 > cfg_0) {
+    if (sizeof(T) == 4 && sh0 > cfg_0) {
         cudaError_t e = cudaFuncSetAttribute(if_bwd0_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh0, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "interface attribute");
@@ -490,15 +519,19 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     const int L = cr_levels(K);
     const int kt = (K + kIfTN - 1) / kIfTN;
     const int ncls = (n16 > 0) + (np > n16);
-    ProfScope ps(c, s, LSS_PROF_IFACE, 2 * L + 3 + (L - 1) * ncls);
+    ProfScope ps(c, s, LSS_PROF_IFACE, (sizeof(T) == 4 ? L + 3 : 2 * L + 3) + (L - 1) * ncls);
+    // level 0's odd rows, then per level the even rows; in single precision the
+    // next level's odd rows (and finally the top row) are fused into them
+    constexpr bool fused = sizeof(T) == 4;
     for (int l = 0; l < L; ++l) {
         const int Kl = cr_level(K, l).K;
         const int wt0 = ((1 << (l + 1)) - 1 + kIfTN - 1) / kIfTN;   // tiles of a level-l window
         const int wt1 = ((1 << (l + 2)) - 1 + kIfTN - 1) / kIfTN;   // tiles of a level-(l+1) window
-        if_fwd_kernel<T><<<dim3(std::min(wt0, kt), std::max(1, Kl / 2), np), kIfT, sh, s>>>(A, l, 0);
+        if (l == 0 || !fused)
+            if_fwd_kernel<T><<<dim3(std::min(wt0, kt), std::max(1, Kl / 2), np), kIfT, sh, s>>>(A, l, 0);
         if_fwd_kernel<T><<<dim3(std::min(wt1, kt), (Kl + 1) / 2, np), kIfT, sh, s>>>(A, l, 1);
     }
-    if_fwd_kernel<T><<<dim3(kt, 1, np), kIfT, sh, s>>>(A, L, 2);
+    if (!fused) if_fwd_kernel<T><<<dim3(kt, 1, np), kIfT, sh, s>>>(A, L, 2);
     const int ktt = (K + kBtN - 1) / kBtN;
     for (int l = L - 1; l >= 0; --l) {
         const int Kl = cr_level(K, l).K;
