@@ -477,7 +477,7 @@ def run_ragged(args, dev, world):
 
 # DRAM traffic per launch group from ncu captures (profiles/iface_maps_2d_n256_mixed.md):
 # key (kernel group, workload, precision).  Stale once those kernels change.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("iface", "2d_n256", "mixed"): 2.444e9}
 
 
 def roofline(res, hbm_peak, hbm_src, workload="2d_n256", prec="mixed"):
