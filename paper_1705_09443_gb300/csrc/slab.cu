@@ -1386,9 +1386,11 @@ __global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, i
                 dst[(cur ^ 1) * vec + e] = val;
             }
         }
-        __syncthreads();   // the stage is no longer read
+        // once every thread of the cluster has arrived, this CTA's reads of the
+        // stage and all remote stores of the new vector are done: refill the
+        // stage with the rows of step s + nb
+        cl.barrier_wait(cl.barrier_arrive());
         if (threadIdx.x == 0 && nrow > 0 && s + nb < nsteps) issue(s + nb);
-        cl.sync();
         cur ^= 1;
     }
     if (!ok && threadIdx.x == 0) {
