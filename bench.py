@@ -402,8 +402,15 @@ def run_batched(args, dev, world):
         t = torch.tensor([total, solve_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total, solve_ms = (float(x) for x in t.tolist())
+    # per-group breakdown of one step, outside the timed region
+    solver.profile_read()
+    solver.profile(True)
+    step()
+    solver.profile(False)
+    prof_ms, _ = solver.profile_read()
     relres = max(s["relres_true"] for st in stats for s in st)
-    return {"workload": args.batched, "R": R, "autotune": tuned, "value": R * args.steps * world / (total / 1e3),
+    return {"workload": args.batched, "R": R, "autotune": tuned, "breakdown_ms": prof_ms,
+            "value": R * args.steps * world / (total / 1e3),
             "unit": "solves/s", "ms_per_step": total / args.steps,
             "solve_only": {"value": R * args.steps * world / (solve_ms / 1e3), "ms_per_solve_call": solve_ms / args.steps},
             "iters_mean": float(np.mean([s["iters"] for st in stats for s in st])), "relres_true_max": relres,

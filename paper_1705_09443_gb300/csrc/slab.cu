@@ -1118,6 +1118,47 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
 // ---------------------------------------------------------------- interface recurrences
 // Grid-wide version (cooperative launch, bounded grid barrier): the fallback
 // when the vectors or rows do not fit the cluster kernel below.
+// Tiles of the grid-synchronised recurrence: each step is a product of an
+// n_tot x n_tot map with the n_tot x R block of current vectors; a CTA forms a
+// kGtR x kGtC tile of it (one entry per thread) over K chunks of kGtK staged
+// in shared memory (coalesced loads of map rows and vector rows).
+constexpr int kGtR = 16, kGtC = 16, kGtK = 32;
+
+template <typename T>
+__device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
+                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T> (*Ms)[kGtK + 1],
+                                           cx<T> (*Xs)[kGtC + 1]) {
+    using C = cx<T>;
+    const int tid = threadIdx.x;
+    const int tr = tid / kGtC, tc = tid % kGtC;
+    const int row = rt * kGtR + tr, r = ct * kGtC + tc;
+    C acc = czero<C>();
+    for (int k0 = 0; k0 < n_tot; k0 += kGtK) {
+        for (int e = tid; e < kGtR * kGtK; e += 256) {   // map rows rt*16.., columns k0..
+            const int a = e / kGtK, b = e % kGtK;
+            const int gr = rt * kGtR + a, gk = k0 + b;
+            Ms[a][b] = (gr < n_tot && gk < n_tot) ? M[(long long)gr * n_tot + gk] : czero<C>();
+        }
+        for (int e = tid; e < kGtK * kGtC; e += 256) {   // vector rows k0.., right-hand sides ct*16..
+            const int b = e / kGtC, c = e % kGtC;
+            const int gk = k0 + b, gc = ct * kGtC + c;
+            Xs[b][c] = (gk < n_tot && gc < R) ? x[(long long)gk * R + gc] : czero<C>();
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int b = 0; b < kGtK; ++b) acc = cfma(Ms[tr][b], Xs[b][tc], acc);
+        __syncthreads();
+    }
+    if (row < n_tot && r < R) {
+        const long long e = (long long)row * R + r;
+        out[e] = base[e] - acc;
+    }
+}
+
+// Recurrences of all slabs with one cooperative grid when the vectors do not
+// fit the cluster kernels (many right-hand sides): lambda and mu, then phi,
+// one step per slab, a grid barrier between steps; the tiles of a step are
+// spread over the CTAs.
 template <typename T>
 __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot, int R,
                                                          const cx<T>* __restrict__ iface,
@@ -1125,53 +1166,34 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
                                                          const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                          unsigned* bar, int* err) {
     using C = cx<T>;
+    __shared__ C Ms[kGtR][kGtK + 1];
+    __shared__ C Xs[kGtK][kGtC + 1];
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nrt = (n_tot + kGtR - 1) / kGtR, nct = (R + kGtC - 1) / kGtC;
+    const int ntile = nrt * nct;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vec;
          e += (long long)gridDim.x * blockDim.x)
         lam[e] = a_last[e];
     for (int i = 1; i < n_slabs; ++i) {
         const C* lp = (i == 1) ? a_last : lam + (long long)(i - 1) * vec;
         const int nwhich = (i <= n_slabs - 2) ? 2 : 1;
-        const long long ntask = nwhich * vec;
-        for (long long task = gw; task < ntask; task += nw) {
-            const int which = (int)(task / vec);
-            const long long rem = task % vec;
-            const int row = (int)(rem / R), r = (int)(rem % R);
-            const C* Mrow = iface + ((long long)(which == 0 ? 1 : 0) * n_slabs + i) * nt2 + (long long)row * n_tot;
-            C acc = czero<C>();
-            for (int j = lane; j < n_tot; j += 32) acc = cfma(Mrow[j], lp[(long long)j * R + r], acc);
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-            }
-            if (lane == 0) {
-                const long long e = (long long)i * vec + (long long)row * R + r;
-                if (which == 0) phi[e] = a_first[e] - acc;  // mu_i
-                else lam[e] = a_last[e] - acc;              // lambda_i
-            }
+        for (int task = blockIdx.x; task < nwhich * ntile; task += gridDim.x) {   // uniform per CTA
+            const int which = task / ntile, t = task % ntile;
+            if (which == 0)   // mu_i = first(a_i) - Gamma_i lambda_{i-1}
+                recur_tile<T>(iface + (1LL * n_slabs + i) * nt2, lp, a_first + (long long)i * vec,
+                              phi + (long long)i * vec, n_tot, R, t / nct, t % nct, Ms, Xs);
+            else              // lambda_i = last(a_i) - Lambda_i lambda_{i-1}
+                recur_tile<T>(iface + (long long)i * nt2, lp, a_last + (long long)i * vec,
+                              lam + (long long)i * vec, n_tot, R, t / nct, t % nct, Ms, Xs);
         }
         grid_barrier(bar, gridDim.x, err);
     }
-    for (int i = n_slabs - 2; i >= 1; --i) {
-        const C* pn = phi + (long long)(i + 1) * vec;
-        for (long long task = gw; task < vec; task += nw) {
-            const int row = (int)(task / R), r = (int)(task % R);
-            const C* Mrow = iface + (2LL * n_slabs + i) * nt2 + (long long)row * n_tot;
-            C acc = czero<C>();
-            for (int j = lane; j < n_tot; j += 32) acc = cfma(Mrow[j], pn[(long long)j * R + r], acc);
-            for (int off = 16; off > 0; off >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
-            }
-            if (lane == 0) {
-                const long long e = (long long)i * vec + (long long)row * R + r;
-                phi[e] = phi[e] - acc;
-            }
-        }
+    for (int i = n_slabs - 2; i >= 1; --i) {   // phi_i = mu_i - Phi_i phi_{i+1}
+        for (int task = blockIdx.x; task < ntile; task += gridDim.x)
+            recur_tile<T>(iface + (2LL * n_slabs + i) * nt2, phi + (long long)(i + 1) * vec,
+                          phi + (long long)i * vec, phi + (long long)i * vec, n_tot, R, task / nct, task % nct, Ms,
+                          Xs);
         grid_barrier(bar, gridDim.x, err);
     }
 }
@@ -1874,7 +1896,8 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
         }
         grid_now = grid;
     }
-    int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, (2 * vec + 7) / 8));
+    const long long tiles = 2LL * ((c->n_tot + kGtR - 1) / kGtR) * ((R + kGtC - 1) / kGtC);
+    int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, tiles));
     int nsl = c->n_slabs, nt = c->n_tot;
     unsigned* bar = c->d_bar;
     int* err = c->d_err;
