@@ -1122,7 +1122,8 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
 // n_tot x n_tot map with the n_tot x R block of current vectors; a CTA forms a
 // kGtR x kGtC tile of it (one entry per thread) over K chunks of kGtK staged
 // in shared memory (coalesced loads of map rows and vector rows).
-constexpr int kGtR = 16, kGtC = 16, kGtK = 32;
+constexpr int kGtR = 16, kGtC = 16, kGtK = 64;
+constexpr int kGtLd = kGtR * kGtK / 256;   // map entries a thread stages per chunk (= kGtK * kGtC / 256)
 
 template <typename T>
 __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
@@ -1132,20 +1133,33 @@ __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx
     const int tid = threadIdx.x;
     const int tr = tid / kGtC, tc = tid % kGtC;
     const int row = rt * kGtR + tr, r = ct * kGtC + tc;
-    C acc = czero<C>();
-    for (int k0 = 0; k0 < n_tot; k0 += kGtK) {
-        for (int e = tid; e < kGtR * kGtK; e += 256) {   // map rows rt*16.., columns k0..
+    // the next chunk's entries are loaded into registers while the current
+    // one is multiplied
+    C pm[kGtLd], px[kGtLd];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int u = 0; u < kGtLd; ++u) {
+            const int e = tid + 256 * u;
             const int a = e / kGtK, b = e % kGtK;
             const int gr = rt * kGtR + a, gk = k0 + b;
-            Ms[a][b] = (gr < n_tot && gk < n_tot) ? M[(long long)gr * n_tot + gk] : czero<C>();
+            pm[u] = (gr < n_tot && gk < n_tot) ? M[(long long)gr * n_tot + gk] : czero<C>();
+            const int bb = e / kGtC, c = e % kGtC;
+            const int gk2 = k0 + bb, gc = ct * kGtC + c;
+            px[u] = (gk2 < n_tot && gc < R) ? x[(long long)gk2 * R + gc] : czero<C>();
         }
-        for (int e = tid; e < kGtK * kGtC; e += 256) {   // vector rows k0.., right-hand sides ct*16..
-            const int b = e / kGtC, c = e % kGtC;
-            const int gk = k0 + b, gc = ct * kGtC + c;
-            Xs[b][c] = (gk < n_tot && gc < R) ? x[(long long)gk * R + gc] : czero<C>();
+    };
+    C acc = czero<C>();
+    load(0);
+    for (int k0 = 0; k0 < n_tot; k0 += kGtK) {
+#pragma unroll
+        for (int u = 0; u < kGtLd; ++u) {
+            const int e = tid + 256 * u;
+            Ms[e / kGtK][e % kGtK] = pm[u];
+            Xs[e / kGtC][e % kGtC] = px[u];
         }
         __syncthreads();
-#pragma unroll 8
+        if (k0 + kGtK < n_tot) load(k0 + kGtK);
+#pragma unroll 16
         for (int b = 0; b < kGtK; ++b) acc = cfma(Ms[tr][b], Xs[b][tc], acc);
         __syncthreads();
     }
