@@ -282,9 +282,9 @@ __global__ void __launch_bounds__(kTThreads) cr_solve_t_kernel(TArgs<cx<T>> A) {
         const int n0 = (A.n_slabs - 1) * A.nch;
         if (t < n0) { i = 1 + t / A.nch; j = t % A.nch; }
         else { t -= n0; side = 1; i = 1 + t / A.nch; j = t % A.nch; }
-    } else {
-        i = blockIdx.x;
-        r = blockIdx.y;
+    } else {   // slab-major grid: a slab's right-hand sides share its factor stream in L2
+        i = blockIdx.y;
+        r = blockIdx.x;
     }
     const long long cta = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     C* b = A.bsm ? reinterpret_cast<C*>(smt) : A.bg + cta * A.bstride;
@@ -382,7 +382,7 @@ int sweep_t_impl(lss_ctx* c, const double2* y, double2* r, int R, cudaStream_t s
     A.lam = lam;
     A.phi = phi;
     A.X = (C*)c->f_buf;
-    const dim3 grid(c->n_slabs, R);
+    const dim3 grid(R, c->n_slabs);
     if (c->n_slabs > 1) {
         {
             ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);

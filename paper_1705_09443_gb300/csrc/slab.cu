@@ -1103,7 +1103,8 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
     int i, r;
     long long cta;
     if (MODE == CR_TEST) { i = A.slab; r = blockIdx.x; cta = blockIdx.x; }
-    else { i = blockIdx.x; r = blockIdx.y; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
+    // slab-major grid: a slab's right-hand sides run together and share its factor stream in L2
+    else { i = blockIdx.y; r = blockIdx.x; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
     const SlabDev sd = A.slabs[i];
     C* b = A.bsm ? reinterpret_cast<C*>(sms) : A.bg + cta * A.bstride;
     if (sd.w <= 16) cr_body<C, MODE, 16>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
@@ -1944,7 +1945,7 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     A.phi = phi;
     A.y = y;
     const long long per_cta = (long long)c->n_tot * ldwmax_of(c);
-    const dim3 grid(c->n_slabs, R);
+    const dim3 grid(R, c->n_slabs);
     if (c->n_slabs > 1) {
         {
             ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
