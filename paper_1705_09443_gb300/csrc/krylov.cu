@@ -128,7 +128,8 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     double2* w = Z + (size_t)m * RN;
     double2* rv = w + RN;
     Krylov K{c, s, N, R, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-    K.nblk = std::max(1, std::min(2 * c->num_sms, (int)((N + kRedThreads - 1) / kRedThreads)));
+    // grids sized for the whole batch: about two CTAs per SM over all right-hand sides
+    K.nblk = std::max(1, std::min(2 * c->num_sms / R, (int)((N + kRedThreads - 1) / kRedThreads)));
     const size_t red_bytes = (size_t)(m + 1) * R * K.nblk * sizeof(double2) +
                              (size_t)(2 * (m + 1) + 1) * R * sizeof(double2) + (size_t)R * sizeof(double) + 64;
     rc = lss_grow(c, (void**)&c->red_buf, &c->red_cap, red_bytes);
@@ -138,7 +139,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     K.h2dev = K.hdev + (size_t)(m + 1) * R;
     K.hnorm = K.h2dev + (size_t)(m + 1) * R;
     K.scdev = reinterpret_cast<double*>(K.hnorm + R);
-    const int g1 = std::max(1, std::min(4 * c->num_sms, (int)((N + 255) / 256)));
+    const int g1 = std::max(1, std::min(4 * c->num_sms / R, (int)((N + 255) / 256)));
     const int gs = std::max(1, std::min(4 * c->num_sms, (int)((RN + 255) / 256)));
 
     double2* hnorm = K.hnorm;
