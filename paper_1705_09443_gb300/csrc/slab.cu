@@ -720,6 +720,7 @@ struct CrArgs {
     long long bstride;       // entries of b per CTA
     int bsm;
     int nst, stage_ent;      // ring stages and complex entries per stage
+    int slab0;               // CR_A / CR_E: first slab of the launch (grid y = slab - slab0)
     int* err;
 };
 
@@ -866,10 +867,14 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
 
     // ---- first chunks in flight while the right-hand side is written; thread
     // 0 publishes each chunk's descriptor beside its stage (kind -1: the end)
+    // thread 0 keeps the descriptor of the next chunk to issue in registers,
+    // loaded one chunk ahead, so that no table load sits between two barriers
+    CrChunk pre{};
     auto issue_next = [&](int g) {
         const int st = g % A.nst;
         if (g < ntab) {
-            const CrChunk ch = tab[g];
+            const CrChunk ch = g >= A.nst ? pre : tab[g];
+            if (g >= A.nst - 1 && g + 1 < ntab) pre = tab[g + 1];
             desc[st] = make_int4(ch.kind, ch.l, ch.r0, ch.r1);
             C* dst = ring + (size_t)st * A.stage_ent;
             mbar_expect_tx(&full[st], (unsigned)((ch.ent + ch.ent2) * (int)sizeof(C)));
@@ -1104,7 +1109,7 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
     long long cta;
     if (MODE == CR_TEST) { i = A.slab; r = blockIdx.x; cta = blockIdx.x; }
     // slab-major grid: a slab's right-hand sides run together and share its factor stream in L2
-    else { i = blockIdx.y; r = blockIdx.x; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
+    else { i = A.slab0 + blockIdx.y; r = blockIdx.x; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
     const SlabDev sd = A.slabs[i];
     C* b = A.bsm ? reinterpret_cast<C*>(sms) : A.bg + cta * A.bstride;
     if (sd.w <= 16) cr_body<C, MODE, 16>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
@@ -1525,9 +1530,12 @@ struct SolvePlan {
     int bsm, nst, stage_ent;
     size_t sh;
 };
+// ldw > 0: plan for slabs of that block width only.
 template <typename C>
-bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, SolvePlan* P) {
-    const size_t min_stage = sizeof(C) * (size_t)max_row_ent(c);
+bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, SolvePlan* P, int ldw = 0) {
+    const long long row_ent = ldw > 0 ? std::max<long long>(2LL * ldw * ldw, 6LL * ldw + (long long)ldw * ldw)
+                                      : max_row_ent(c);
+    const size_t min_stage = sizeof(C) * (size_t)row_ent;
     const size_t want = std::max<size_t>(48 * 1024, min_stage);
     if (c->tune.solve_bsm == 0) allow_smem_b = false;
     const int tn = c->tune.solve_nst;
@@ -1594,15 +1602,18 @@ int chunk_tables(lss_ctx* c, bool part, int stage_ent, CrArgsTables* out, cudaSt
 // sides per CTA: in shared memory when they fit (and no fixed scratch is
 // given), else in global scratch (the fixed array `scratch`, or the context's
 // growable buffer).
+// ldw > 0: the launch covers slabs of that block width only (its right-hand
+// sides and stages are sized for it); z_off: byte offset of this launch's part
+// of the context's global right-hand-side scratch.
 template <typename T, int MODE>
 int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void* scratch, size_t scratch_bytes,
-                 cudaStream_t s) {
+                 cudaStream_t s, int ldw = 0, size_t z_off = 0) {
     using C = cx<T>;
     auto kern = cr_solve_kernel<T, MODE>;
     const size_t tb = sizeof(C) * ((size_t)kSolveThreads + kSplitRows * 4 * 32);
     const size_t bb = sizeof(C) * (size_t)per_cta;
     SolvePlan P;
-    if (!plan_solve<C>(c, bb, tb, scratch == nullptr, &P))
+    if (!plan_solve<C>(c, bb, tb, scratch == nullptr, &P, ldw))
         return lss_fail(c, LSS_ERR_UNSUPPORTED, "slab solve: the factor stream does not fit in shared memory");
     A.bstride = per_cta;
     A.bsm = P.bsm;
@@ -1627,34 +1638,107 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
                                     " bytes of scratch, the fixed scratch holds " + std::to_string(scratch_bytes) +
                                     " (use fewer right-hand sides per call)");
             A.bg = (C*)scratch;
-        } else {
-            rc = lss_grow(c, &c->z_buf, &c->z_cap, need);
+        } else {   // z_off: this launch's part of a scratch shared by concurrent launches
+            rc = lss_grow(c, &c->z_buf, &c->z_cap, z_off + need);
             if (rc) return rc;
-            A.bg = (C*)c->z_buf;
+            A.bg = (C*)((char*)c->z_buf + z_off);
         }
     }
     kern<<<grid, kSolveThreads, P.sh, s>>>(A);
     return lss_check_cuda(c, cudaGetLastError(), "slab solve launch");
 }
 
+// The sweep's slab solves run per run of consecutive slabs with the same
+// block width, concurrently (run 0 on the caller's stream, the others on
+// auxiliary streams): each launch sizes its right-hand sides and ring stages
+// for its width (16-wide slabs need half the shared memory of 32-wide ones).
+struct SweepRun { int s0, n, ldw; };
+std::vector<SweepRun> sweep_runs(const lss_ctx* c) {
+    std::vector<SweepRun> runs;
+    for (int i = 0; i < c->n_slabs; ++i) {
+        const int ldw = c->slabs[i].ldw;
+        if (runs.empty() || runs.back().ldw != ldw) runs.push_back({i, 0, ldw});
+        runs.back().n += 1;
+    }
+    return runs;
+}
+
+// Auxiliary streams (and their events) for n concurrent runs.
+int ensure_aux(lss_ctx* c, size_t n) {
+    while (c->aux_stream.size() + 1 < n) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e) {
+            if (st) cudaStreamDestroy(st);
+            return lss_check_cuda(c, e, "auxiliary streams");
+        }
+        c->aux_stream.push_back(st);
+        c->aux_event.push_back(ev);
+    }
+    if (!c->fork_event)
+        return lss_check_cuda(c, cudaEventCreateWithFlags(&c->fork_event, cudaEventDisableTiming), "auxiliary streams");
+    return LSS_OK;
+}
+
 // Chunk tables of every solve plan the entry points can use (right-hand sides
-// in shared or in global memory, all layers or first/last only), built at
-// factorization so that no later call allocates.
+// in shared or in global memory, all layers or first/last only, and the plans
+// of the sweep's runs), built at factorization so that no later call allocates.
 template <typename T>
 int prepare_chunk_tables(lss_ctx* c, cudaStream_t s) {
     using C = cx<T>;
     const size_t tb = sizeof(C) * ((size_t)kSolveThreads + kSplitRows * 4 * 32);
     const size_t bb = sizeof(C) * (size_t)c->n_tot * ldwmax_of(c);
+    std::vector<SolvePlan> plans;
     for (int smem_b = 0; smem_b < 2; ++smem_b) {
         SolvePlan P;
-        if (!plan_solve<C>(c, bb, tb, smem_b == 1, &P)) continue;
+        if (plan_solve<C>(c, bb, tb, smem_b == 1, &P)) plans.push_back(P);
+    }
+    for (const SweepRun& u : sweep_runs(c)) {
+        SolvePlan P;
+        for (int smem_b = 0; smem_b < 2; ++smem_b)
+            if (plan_solve<C>(c, sizeof(C) * (size_t)c->n_tot * u.ldw, tb, smem_b == 1, &P, u.ldw))
+                plans.push_back(P);
+    }
+    for (const SolvePlan& P : plans)
         for (int part = 0; part < 2; ++part) {
             CrArgsTables t;
             const int rc = chunk_tables(c, part == 1, P.stage_ent, &t, s);
             if (rc) return rc;
         }
-    }
     return LSS_OK;
+}
+
+// One sweep pass (MODE CR_A or CR_E) over every slab, run by run.
+template <typename T, int MODE>
+int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s) {
+    const std::vector<SweepRun> runs = sweep_runs(c);
+    int rc = ensure_aux(c, runs.size());
+    if (rc) return rc;
+    // global right-hand-side scratch of every run, grown before any launch so
+    // that concurrent runs use disjoint parts of one buffer
+    size_t ztot = 0;
+    std::vector<size_t> zoff(runs.size());
+    for (size_t ri = 0; ri < runs.size(); ++ri) {
+        zoff[ri] = ztot;
+        ztot += sizeof(cx<T>) * (size_t)c->n_tot * runs[ri].ldw * R * runs[ri].n;
+    }
+    if ((rc = lss_grow(c, &c->z_buf, &c->z_cap, ztot))) return rc;
+    if (runs.size() > 1) cudaEventRecord(c->fork_event, s);
+    for (size_t ri = 0; ri < runs.size() && !rc; ++ri) {
+        const SweepRun& u = runs[ri];
+        cudaStream_t su = ri == 0 ? s : c->aux_stream[ri - 1];
+        if (ri > 0) cudaStreamWaitEvent(su, c->fork_event, 0);
+        CrArgs<cx<T>> Ar = A;
+        Ar.slab0 = u.s0;
+        rc = launch_solve<T, MODE>(c, Ar, dim3(R, u.n), (long long)c->n_tot * u.ldw, nullptr, 0, su, u.ldw, zoff[ri]);
+        if (ri > 0) {
+            cudaEventRecord(c->aux_event[ri - 1], su);
+            cudaStreamWaitEvent(s, c->aux_event[ri - 1], 0);
+        }
+    }
+    return rc;
 }
 
 template <typename T>
@@ -1692,21 +1776,7 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
     // slabs factor independently: run 0 on s, every other run on an auxiliary
     // stream of its own, forked after the level-0 blocks are built and joined
     // before the interface maps
-    while (c->aux_stream.size() + 1 < runs.size()) {
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
-        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e) {
-            if (st) cudaStreamDestroy(st);
-            return lss_check_cuda(c, e, "factor streams");
-        }
-        c->aux_stream.push_back(st);
-        c->aux_event.push_back(ev);
-    }
-    if (!c->fork_event && (rc = lss_check_cuda(c, cudaEventCreateWithFlags(&c->fork_event, cudaEventDisableTiming),
-                                                "factor streams")))
-        return rc;
+    if ((rc = ensure_aux(c, runs.size()))) return rc;
     {
         ProfScope ps(c, s, LSS_PROF_FACTOR, 2 + (2 * nlev) * (int)runs.size());
         cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
@@ -1944,19 +2014,18 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     A.lam = lam;
     A.phi = phi;
     A.y = y;
-    const long long per_cta = (long long)c->n_tot * ldwmax_of(c);
-    const dim3 grid(R, c->n_slabs);
+    const int nrun = (int)sweep_runs(c).size();
     if (c->n_slabs > 1) {
         {
-            ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
-            rc = launch_solve<T, CR_A>(c, A, grid, per_cta, nullptr, 0, s);
+            ProfScope ps(c, s, LSS_PROF_SLAB_A, nrun);
+            rc = sweep_pass<T, CR_A>(c, A, R, s);
         }
         if (rc) return rc;
         rc = launch_recur<T>(c, (const C*)c->iface, lam, phi, A.a_first, A.a_last, R, s);
         if (rc) return rc;
     }
-    ProfScope ps(c, s, LSS_PROF_SLAB_E, 1);
-    return launch_solve<T, CR_E>(c, A, grid, per_cta, nullptr, 0, s);
+    ProfScope ps(c, s, LSS_PROF_SLAB_E, nrun);
+    return sweep_pass<T, CR_E>(c, A, R, s);
 }
 
 template <typename T>
