@@ -532,19 +532,29 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
         if_fwd_kernel<T><<<dim3(std::min(wt1, kt), (Kl + 1) / 2, np), kIfT, sh, s>>>(A, l, 1);
     }
     if (!fused) if_fwd_kernel<T><<<dim3(kt, 1, np), kIfT, sh, s>>>(A, L, 2);
+    // back substitution, levels L-1..1: the 16-wide problems on s, the 32-wide
+    // ones (few, each a long chain of levels) concurrently on an auxiliary
+    // stream; level 0 over all problems after the join
     const int ktt = (K + kBtN - 1) / kBtN;
-    for (int l = L - 1; l >= 0; --l) {
-        const int Kl = cr_level(K, l).K;
-        if (l > 0) {
-            const size_t sh16 = sizeof(C) * ((size_t)2 * 16 * 16 + (size_t)2 * 16 * kBtNP);
-            if (n16 > 0)
-                if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), n16), kBtThreads, sh16, s>>>(A, l, 0);
-            if (np > n16)
-                if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), np - n16), kBtThreads, sht, s>>>(A, l, n16);
-        } else {
-            if_bwd0_kernel<T><<<dim3((K + kB0N - 1) / kB0N, std::max(1, Kl / 2), np), kB0N, sh0, s>>>(A);
-        }
+    const bool two = n16 > 0 && np > n16;
+    if (two) {
+        if (int rc2 = lss_ensure_aux(c, 2)) return rc2;
+        cudaEventRecord(c->fork_event, s);
+        cudaStreamWaitEvent(c->aux_stream[0], c->fork_event, 0);
     }
+    cudaStream_t s32 = two ? c->aux_stream[0] : s;
+    const size_t sh16 = sizeof(C) * ((size_t)2 * 16 * 16 + (size_t)2 * 16 * kBtNP);
+    for (int l = L - 1; l > 0; --l) {
+        const int Kl = cr_level(K, l).K;
+        if (n16 > 0) if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), n16), kBtThreads, sh16, s>>>(A, l, 0);
+        if (np > n16)
+            if_bwdt_kernel<T><<<dim3(ktt, std::max(1, Kl / 2), np - n16), kBtThreads, sht, s32>>>(A, l, n16);
+    }
+    if (two) {
+        cudaEventRecord(c->aux_event[0], s32);
+        cudaStreamWaitEvent(s, c->aux_event[0], 0);
+    }
+    if_bwd0_kernel<T><<<dim3((K + kB0N - 1) / kB0N, std::max(1, K / 2), np), kB0N, sh0, s>>>(A);
     if_maps_kernel<T><<<dim3((unsigned)std::min<long long>(((long long)K * K + 255) / 256, 1024), np), 256, 0,
                         s>>>(A);
     return lss_check_cuda(c, cudaGetLastError(), "interface launch");

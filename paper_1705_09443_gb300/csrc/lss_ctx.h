@@ -250,6 +250,8 @@ int lss_fft_configure(lss_ctx* c);
 std::vector<int> lss_fft_col_candidates(const lss_ctx* c);   // admissible column groups (autotuner)
 // slab.cu: chunk tables of every solve plan under the current launch parameters
 int lss_prepare_solve_tables(lss_ctx* c, cudaStream_t s);
+// slab.cu: at least n - 1 auxiliary streams (with events) and the fork event
+int lss_ensure_aux(lss_ctx* c, size_t n);
 
 // stencil.cu: gamma tables, slab assembly, Q
 int lss_build_gamma_phys(lss_ctx* c, cudaStream_t s);

@@ -1663,25 +1663,6 @@ std::vector<SweepRun> sweep_runs(const lss_ctx* c) {
     return runs;
 }
 
-// Auxiliary streams (and their events) for n concurrent runs.
-int ensure_aux(lss_ctx* c, size_t n) {
-    while (c->aux_stream.size() + 1 < n) {
-        cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
-        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e) {
-            if (st) cudaStreamDestroy(st);
-            return lss_check_cuda(c, e, "auxiliary streams");
-        }
-        c->aux_stream.push_back(st);
-        c->aux_event.push_back(ev);
-    }
-    if (!c->fork_event)
-        return lss_check_cuda(c, cudaEventCreateWithFlags(&c->fork_event, cudaEventDisableTiming), "auxiliary streams");
-    return LSS_OK;
-}
-
 // Chunk tables of every solve plan the entry points can use (right-hand sides
 // in shared or in global memory, all layers or first/last only, and the plans
 // of the sweep's runs), built at factorization so that no later call allocates.
@@ -1714,7 +1695,7 @@ int prepare_chunk_tables(lss_ctx* c, cudaStream_t s) {
 template <typename T, int MODE>
 int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s) {
     const std::vector<SweepRun> runs = sweep_runs(c);
-    int rc = ensure_aux(c, runs.size());
+    int rc = lss_ensure_aux(c, runs.size());
     if (rc) return rc;
     // global right-hand-side scratch of every run, grown before any launch so
     // that concurrent runs use disjoint parts of one buffer
@@ -1776,7 +1757,7 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
     // slabs factor independently: run 0 on s, every other run on an auxiliary
     // stream of its own, forked after the level-0 blocks are built and joined
     // before the interface maps
-    if ((rc = ensure_aux(c, runs.size()))) return rc;
+    if ((rc = lss_ensure_aux(c, runs.size()))) return rc;
     {
         ProfScope ps(c, s, LSS_PROF_FACTOR, 2 + (2 * nlev) * (int)runs.size());
         cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
@@ -2044,6 +2025,25 @@ int slab_apply_impl(lss_ctx* c, int slab, const double2* v, double2* w, int R, v
 }
 
 }  // namespace
+
+// Auxiliary streams (and their events) for n concurrent runs.
+int lss_ensure_aux(lss_ctx* c, size_t n) {
+    while (c->aux_stream.size() + 1 < n) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e) {
+            if (st) cudaStreamDestroy(st);
+            return lss_check_cuda(c, e, "auxiliary streams");
+        }
+        c->aux_stream.push_back(st);
+        c->aux_event.push_back(ev);
+    }
+    if (!c->fork_event)
+        return lss_check_cuda(c, cudaEventCreateWithFlags(&c->fork_event, cudaEventDisableTiming), "auxiliary streams");
+    return LSS_OK;
+}
 
 int lss_prepare_solve_tables(lss_ctx* c, cudaStream_t s) {
     return c->prec == LSS_FP64 ? prepare_chunk_tables<double>(c, s) : prepare_chunk_tables<float>(c, s);

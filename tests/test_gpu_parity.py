@@ -184,6 +184,32 @@ def test_mixed_precision_odd_total_width():
         assert st32[0]["relres_true"] <= 1e-8 and st32[0]["iters"] <= st64[0]["iters"] + 2
 
 
+def test_three_runs_of_block_widths():
+    """b_pml = 14, b_aux = 10, b_slab = 4: the first slab has 18 layers (32-wide
+    blocks), the middle slabs 14 (16-wide), the last one 10 + 14 + a remainder
+    (32-wide), so the factorization and both sweep passes run three launches on
+    three streams.  FP64 and mixed preconditioners against the oracle, the
+    transposed one too, and the FP64 solve."""
+    from paper_1705_09443_gb300 import GmresOptions, LSSolver, LSS_MIXED
+    n, freq = 40, 5.0
+    om = 2 * math.pi * freq
+    m = synth.gaussian_medium(n, 2, 4, 0.1, (0.8, 1.2), 77)
+    pb = O.Problem2D(n, om, m, O.Params(b_pml=14, b_slab=4, b_aux=10))
+    widths = [pb.n_aux[i] + pb.slab_last[i] - pb.slab_first[i] + 1 for i in range(pb.n_slabs)]
+    assert widths[0] > 16 and widths[1] <= 16 and widths[-1] > 16
+    x = crand((1, n, n), 13)
+    for prec, tol in ((0, 1e-10), (LSS_MIXED, 1e-4)):
+        s = LSSolver(n, om, torch.tensor(m, dtype=torch.float64, device="cuda"), b_pml=14, b_slab=4, b_aux=10,
+                     precision=prec)
+        assert rel(s.apply_P(to_dev(x)).cpu().numpy()[0], pb.precondition(x[0])) <= tol
+        assert rel(s.apply_P(to_dev(x), transpose=True).cpu().numpy()[0], pb.precondition_transpose(x[0])) <= tol
+        if prec == 0:
+            g = s.plane_wave_rhs([(0.6, 0.8)])
+            u, st = s.solve(g, GmresOptions(30, 1e-12, 200))
+            ref, _, _, _ = O.solve(n, om, m, (0.6, 0.8), tol=1e-12, problem=pb)
+            assert rel(u[0].cpu().numpy(), ref.x) <= 1e-10
+
+
 def test_zero_medium_gives_zero_solution():
     from paper_1705_09443_gb300 import GmresOptions
     s, m, om = make(16, 2.0, medium_seed=None, b_pml=4)
