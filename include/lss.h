@@ -274,9 +274,10 @@ int lss_set_graphs(lss_ctx *c, int enable);
  * so later solves agree bit for bit with untuned ones; only their speed
  * changes.  Requires a factored context; allocates and frees two vectors;
  * blocks the host.  On a batch: every instance.
- *   chosen  host, 4 ints (may be NULL): column group, right-hand sides in
+ *   chosen  host, 5 ints (may be NULL): column group, right-hand sides in
  *           global memory (0) or automatic (-1), ring stages (0 = automatic),
- *           recurrence stages
+ *           recurrence stages, ring stages of the 32-wide slabs' launches
+ *           (0 = as the others)
  */
 int lss_autotune(lss_ctx *c, int R, int *chosen, void *stream);
 

@@ -170,6 +170,7 @@ struct lss_ctx {
         int fft_C = 0;        // columns per CTA of the FFT column pass
         int solve_bsm = -1;   // 0: slab-solve right-hand sides in global memory even when they fit shared
         int solve_nst = 0;    // slab-solve ring stages (the stages then share the free shared memory)
+        int solve_nst_w = 0;  // the same for launches of 32-wide slabs only (0: as solve_nst)
         int rec_nb = 0;       // ring stages of the TMA recurrence
     } tune;
 

@@ -1538,7 +1538,7 @@ bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, Solve
     const size_t min_stage = sizeof(C) * (size_t)row_ent;
     const size_t want = std::max<size_t>(48 * 1024, min_stage);
     if (c->tune.solve_bsm == 0) allow_smem_b = false;
-    const int tn = c->tune.solve_nst;
+    const int tn = (ldw == 32 && c->tune.solve_nst_w) ? c->tune.solve_nst_w : c->tune.solve_nst;
     for (int bsm = allow_smem_b ? 1 : 0; bsm >= 0; --bsm) {
         const size_t fixed = tb + (bsm ? bb : 0);
         if (fixed + 2 * min_stage > kSmemBudget) continue;

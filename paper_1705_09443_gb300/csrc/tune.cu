@@ -84,6 +84,22 @@ int tune_one(lss_ctx* c, int R, cudaStream_t s) {
             }
         c->tune = pick;
     }
+    {   // ring stages of the 32-wide slabs' own launches (they set each pass's critical path)
+        bool wide = false;
+        for (const auto& sd : c->slabs) wide |= sd.ldw == 32;
+        bool narrow = false;
+        for (const auto& sd : c->slabs) narrow |= sd.ldw == 16;
+        if (wide && narrow) {
+            float best = -1;
+            int pick = 0;
+            for (int nst : {0, 2, 3, 4}) {
+                c->tune.solve_nst_w = nst;
+                const float ms = time_ms(t, s, 3, sweep);
+                if (ms > 0 && (best < 0 || ms < best)) { best = ms; pick = nst; }
+            }
+            c->tune.solve_nst_w = pick;
+        }
+    }
     {
         float best = -1;
         int pick = c->tune.rec_nb;
@@ -128,6 +144,7 @@ extern "C" int lss_autotune(lss_ctx* c, int R, int* chosen, void* stream) {
         chosen[1] = t.solve_bsm;
         chosen[2] = t.solve_nst;
         chosen[3] = t.rec_nb;
+        chosen[4] = t.solve_nst_w;
     }
     return LSS_OK;
 }
