@@ -46,8 +46,6 @@
 namespace {
 
 constexpr int kSolveThreads = 384;
-constexpr int kGjWarps = 2;
-constexpr int kEvWarps = 2;
 constexpr size_t kSmemBudget = size_t(220) * 1024;
 
 // acc - a*b
@@ -102,109 +100,6 @@ __global__ void cr_build0_kernel(const SlabDev* __restrict__ slabs, const cx<T>*
         const bool has = bnd < 3 ? k > 0 : k + 1 < K0;
         if (p < w && p + da >= 0 && p + da < w && has) v = ck[p * 9 + (da + 1) * 3 + slot];
         band[e] = v;
-    }
-}
-
-// Gauss-Jordan with partial pivoting on [A | I | C | B] for the odd rows of
-// level l (giving D^{-1}, D^{-1}C, D^{-1}B), or on [A | I] for the top row.
-// One warp per block row; the augmented matrix sits row-major in shared memory
-// (row stride rs) and the lanes own its columns.
-template <typename T>
-__global__ void __launch_bounds__(32 * kGjWarps) cr_gj_kernel(const SlabDev* __restrict__ slabs,
-                                                              cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
-                                                              long long work_len, int K0, int l, int per_slab,
-                                                              int slab0, int n_slabs, int top, int rs, int* err) {
-    using C = cx<T>;
-    extern __shared__ __align__(16) unsigned char smg[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int task = blockIdx.x * kGjWarps + warp;
-    if (task >= per_slab * n_slabs) return;   // the whole warp leaves
-    const int si = slab0 + task / per_slab, o = task % per_slab;
-    const SlabDev sd = slabs[si];
-    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
-    C* M = reinterpret_cast<C*>(smg) + (size_t)warp * 32 * rs;
-    const CrLevelOffs lo = cr_level(K0, l);
-    const int K = lo.K;
-    C* W = work + sd.work_off + (l & 1) * work_len;
-    C* F = fac + sd.fac_off;
-    const int j = top ? 0 : 2 * o + 1;
-    const int ncol = top ? 2 * w : 4 * w;
-    const C* Ab = W + (long long)j * bs;
-    const C* Cb = W + ((long long)K0 + 2LL * j) * bs;
-    const C* Bb = Cb + bs;
-    const bool hasB = !top && j + 1 < K;
-    for (int e = lane; e < w * ncol; e += 32) {
-        const int i = e / ncol, q = e % ncol;
-        C v = czero<C>();
-        if (q < w) v = Ab[(long long)q * ldw + i];
-        else if (q < 2 * w) { if (q - w == i) v.x = T(1); }
-        else if (q < 3 * w) v = Cb[(long long)(q - 2 * w) * ldw + i];
-        else if (hasB) v = Bb[(long long)(q - 3 * w) * ldw + i];
-        M[i * rs + q] = v;
-    }
-    __syncwarp();
-    for (int jj = 0; jj < w; ++jj) {
-        T val = (lane >= jj && lane < w) ? cabs2(M[lane * rs + jj]) : T(-1);
-        if (!(val >= T(0)) || !isfinite(val)) val = (lane >= jj && lane < w) ? T(0) : T(-1);
-        int best = lane;
-        for (int off = 16; off > 0; off >>= 1) {
-            const T ov = __shfl_xor_sync(0xffffffffu, val, off);
-            const int ob = __shfl_xor_sync(0xffffffffu, best, off);
-            if (ov > val || (ov == val && ob < best)) { val = ov; best = ob; }
-        }
-        const int r = __shfl_sync(0xffffffffu, best, 0);
-        if (r != jj) {
-            for (int q = jj + lane; q < ncol; q += 32) {
-                const C t = M[jj * rs + q];
-                M[jj * rs + q] = M[r * rs + q];
-                M[r * rs + q] = t;
-            }
-        }
-        __syncwarp();
-        C pv = M[jj * rs + jj];
-        const T a2 = cabs2(pv);
-        if (!(a2 > T(0)) || !isfinite(a2)) {
-            if (lane == 0) atomicOr(err, LSS_DERR_SINGULAR);
-            pv = czero<C>();
-            pv.x = T(1);
-        }
-        const C pinv = crecip(pv);
-        __syncwarp();
-        for (int q = jj + 1 + lane; q < ncol; q += 32) M[jj * rs + q] = M[jj * rs + q] * pinv;
-        __syncwarp();
-        // column jj is not written below and not read after this pivot
-        for (int q = jj + 1 + lane; q < ncol; q += 32) {
-            const C mj = M[jj * rs + q];
-            for (int i = 0; i < w; ++i)
-                if (i != jj) M[i * rs + q] = cfnma(M[i * rs + jj], mj, M[i * rs + q]);
-        }
-        __syncwarp();
-    }
-    // [I | D^{-1} | D^{-1}C | D^{-1}B]: column-major blocks
-    C* Dout = F + (lo.dinv + (top ? 0 : o)) * bs;
-    C* DCw = W + (3LL * K0 + 2LL * o) * bs;
-    C* DCf = (!top && l >= 1) ? F + (lo.dcdb + 2LL * o) * bs : nullptr;
-    for (int e = lane; e < bs; e += 32) {
-        const int q = e / ldw, p = e % ldw;
-        const bool in = p < w && q < w;
-        Dout[e] = in ? M[p * rs + w + q] : czero<C>();
-        if (!top) {
-            const C dc = in ? M[p * rs + 2 * w + q] : czero<C>();
-            const C db = in ? M[p * rs + 3 * w + q] : czero<C>();
-            DCw[e] = dc;
-            DCw[bs + e] = db;
-            if (DCf) {
-                DCf[e] = dc;
-                DCf[bs + e] = db;
-            }
-        }
-    }
-    if (!top && l == 0) {   // rows na and w-1 of D^{-1} for the solves that keep only those layers
-        C* P0 = F + cr_p0_off(K0, bs, ldw) + 2LL * o * ldw;
-        for (int e = lane; e < 2 * ldw; e += 32) {
-            const int a = e % ldw, pr = e < ldw ? sd.na : w - 1;
-            P0[e] = a < w ? M[pr * rs + w + a] : czero<C>();
-        }
     }
 }
 
@@ -341,138 +236,17 @@ __global__ void __launch_bounds__(32 * kGj0Warps) cr_gj0_kernel(const SlabDev* _
     else gj0_body<T, 32>(sd, coef, fac, work, K0, o, sm[warp], err);
 }
 
-// Even rows of level l: A'_e, C'_e, B'_e of level l+1 from D^{-1}C and D^{-1}B
-// of the neighbouring odd rows, into the other work parity (and, for the even
-// rows of level l+1, C' and B' into the factors).  One warp per block row; C_e
-// and B_e are staged row-major in shared memory, lane q computes column q of
-// each product with the right factor's column in registers.
-template <typename T>
-__global__ void __launch_bounds__(32 * kEvWarps) cr_even_kernel(const SlabDev* __restrict__ slabs,
-                                                                cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
-                                                                long long work_len, int K0, int l, int per_slab,
-                                                                int slab0, int n_slabs, int nlev, int LS) {
-    using C = cx<T>;
-    extern __shared__ __align__(16) unsigned char sme[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int task = blockIdx.x * kEvWarps + warp;
-    if (task >= per_slab * n_slabs) return;
-    const int si = slab0 + task / per_slab, t = task % per_slab;
-    const SlabDev sd = slabs[si];
-    const int w = sd.w, ldw = sd.ldw, bs = sd.bs;
-    const int K = cr_level(K0, l).K;
-    const C* W = work + sd.work_off + (l & 1) * work_len;
-    C* Wn = work + sd.work_off + ((l + 1) & 1) * work_len;
-    C* F = fac + sd.fac_off;
-    const int e = 2 * t;
-    const bool hasL = e >= 1, hasR = e + 1 < K;
-    const C* Ae = W + (long long)e * bs;
-    const C* Ce = W + ((long long)K0 + 2LL * e) * bs;
-    const C* Be = Ce + bs;
-    const C* DCm = W + (3LL * K0 + 2LL * (t - 1)) * bs;   // odd row e-1
-    const C* DCp = W + (3LL * K0 + 2LL * t) * bs;         // odd row e+1
-    C* An = Wn + (long long)t * bs;
-    const bool next_cb = l + 1 < nlev;                     // level l+1 has more than one row
-    C* Cn = Wn + ((long long)K0 + 2LL * t) * bs;
-    C* Bn = Cn + bs;
-    C* Cf = nullptr;
-    if (next_cb && (t & 1) == 0) Cf = F + (cr_level(K0, l + 1).cbe + 2LL * (t >> 1)) * bs;
-    C* L0 = reinterpret_cast<C*>(sme) + (size_t)warp * 2 * 32 * LS;
-    C* L1 = L0 + 32 * LS;
-    for (int x = lane; x < w * w; x += 32) {
-        const int p = x % w, a = x / w;
-        L0[p * LS + a] = Ce[(long long)a * ldw + p];
-        L1[p * LS + a] = Be[(long long)a * ldw + p];
-    }
-    __syncwarp();
-    const int q = lane;
-    if (q >= w && q < ldw) {   // padding columns of the produced blocks
-        for (int p = 0; p < ldw; ++p) {
-            An[(long long)q * ldw + p] = czero<C>();
-            if (next_cb) {
-                Cn[(long long)q * ldw + p] = czero<C>();
-                Bn[(long long)q * ldw + p] = czero<C>();
-                if (Cf) {
-                    Cf[(long long)q * ldw + p] = czero<C>();
-                    Cf[bs + (long long)q * ldw + p] = czero<C>();
-                }
-            }
-        }
-    }
-    if (q < w) {
-        C R[32];
-        auto load_col = [&](const C* blk) {
-#pragma unroll
-            for (int a = 0; a < 32; ++a) R[a] = a < w ? blk[(long long)q * ldw + a] : czero<C>();
-        };
-        auto dot = [&](const C* Lrow) {   // row p of (L R) for the staged left factor L
-            C acc = czero<C>();
-#pragma unroll
-            for (int a = 0; a < 32; ++a)
-                if (a < w) acc = cfma(Lrow[a], R[a], acc);
-            return acc;
-        };
-        // Out[p] -= (L R)[p] for every p, L staged row-major; at level 0 L is
-        // tridiagonal (the stencil couplings), so only the band is summed
-        auto sub_product = [&](const C* L, C* Out) {
-            if (l == 0) {
-#pragma unroll
-                for (int pp = 0; pp < 32; ++pp) {
-                    if (pp >= w) break;
-                    C v = czero<C>();
-#pragma unroll
-                    for (int da = -1; da <= 1; ++da)
-                        if (pp + da >= 0 && pp + da < 32 && pp + da < w) v = cfma(L[pp * LS + pp + da], R[pp + da], v);
-                    Out[pp] = Out[pp] - v;
-                }
-            } else {
-                for (int pp = 0; pp < w; ++pp) Out[pp] = Out[pp] - dot(L + pp * LS);
-            }
-        };
-        C* Acol = An + (long long)q * ldw;
-        for (int p = 0; p < ldw; ++p) Acol[p] = p < w ? Ae[(long long)q * ldw + p] : czero<C>();
-        if (hasL) {
-            load_col(DCm + bs);   // D^{-1}B of row e-1
-            sub_product(L0, Acol);
-        }
-        if (hasR) {
-            load_col(DCp);        // D^{-1}C of row e+1
-            sub_product(L1, Acol);
-        }
-        if (next_cb) {
-            C* Ccol = Cn + (long long)q * ldw;
-            C* Bcol = Bn + (long long)q * ldw;
-            for (int p = 0; p < w; ++p) {
-                Ccol[p] = czero<C>();
-                Bcol[p] = czero<C>();
-            }
-            if (hasL) {
-                load_col(DCm);    // D^{-1}C of row e-1
-                sub_product(L0, Ccol);
-            }
-            if (hasR) {
-                load_col(DCp + bs);   // D^{-1}B of row e+1
-                sub_product(L1, Bcol);
-            }
-            for (int p = w; p < ldw; ++p) { Ccol[p] = czero<C>(); Bcol[p] = czero<C>(); }
-            if (Cf) {
-                for (int p = 0; p < ldw; ++p) {
-                    Cf[(long long)q * ldw + p] = Ccol[p];
-                    Cf[bs + (long long)q * ldw + p] = Bcol[p];
-                }
-            }
-        }
-    }
-}
-
-// Wide slabs (more than 16 layers) have few block rows per level and each
-// of them would keep one warp busy for a long dependent chain; these two
-// kernels give a block row a whole CTA instead.
+// Levels >= 1 of the factorization: a CTA per block row (a warp per row left
+// each row's dependent elimination chain exposed; the levels with few rows
+// and the wide slabs set the factorization time).
 constexpr int kWideThreads = 256;
 
-// Gauss-Jordan of cr_gj_kernel (same pivot rule: largest modulus in the
-// column, lowest row on ties) with a CTA per block row: warp 0 picks the
-// pivot, the threads swap and scale row jj column-wise, then thread
-// (column q, row parity) eliminates every other row i = parity, parity+2, ...
+// Gauss-Jordan with partial pivoting (largest modulus in the column, lowest
+// row on ties) on [A | I | C | B] for the odd rows of level l, giving D^{-1},
+// D^{-1}C and D^{-1}B, or on [A | I] for the top row.  The augmented matrix
+// sits row-major in shared memory (row stride rs); warp 0 picks the pivot,
+// the threads swap and scale row jj column-wise, then thread (column q, row
+// parity) eliminates every other row i = parity, parity+2, ...
 template <typename T>
 __global__ void __launch_bounds__(kWideThreads) cr_gjw_kernel(const SlabDev* __restrict__ slabs,
                                                              cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
@@ -568,11 +342,13 @@ __global__ void __launch_bounds__(kWideThreads) cr_gjw_kernel(const SlabDev* __r
     }
 }
 
-// Even rows of cr_even_kernel with a CTA per block row: C_e, B_e row-major
-// and the four right factors transposed (row a of a factor holds its entries
-// (a, q) for all columns q) in shared memory; thread (column q, row group g)
-// computes rows g, g+8, g+16, g+24 of column q of A', C', B', summing over a
-// in ascending order as the warp version does.
+// Even rows of level l: A'_e, C'_e, B'_e of level l+1 from D^{-1}C and D^{-1}B
+// of the neighbouring odd rows, into the other work parity (and, for the even
+// rows of level l+1, C' and B' into the factors).  C_e, B_e row-major and the
+// four right factors transposed (row a of a factor holds its entries (a, q)
+// for all columns q) in shared memory; thread (column q, row group g) computes
+// rows g, g+8, g+16, g+24 of column q of A', C', B', summing over a in
+// ascending order (at level 0, where C and B are tridiagonal, over the band).
 template <typename T>
 __global__ void __launch_bounds__(kWideThreads) cr_evenw_kernel(const SlabDev* __restrict__ slabs,
                                                                cx<T>* __restrict__ fac, cx<T>* __restrict__ work,
@@ -1475,11 +1251,6 @@ __global__ void __launch_bounds__(256) recur_mu_kernel(int n_slabs, int n_tot, i
 }
 
 // ---------------------------------------------------------------- host helpers
-int wmax_of(const lss_ctx* c) {
-    int w = 0;
-    for (const auto& s : c->slabs) w = std::max(w, s.w);
-    return w;
-}
 int ldwmax_of(const lss_ctx* c) {
     int w = 0;
     for (const auto& s : c->slabs) w = std::max(w, s.ldw);
@@ -1739,19 +1510,10 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
         runs.back().n += 1;
         runs.back().w = std::max(runs.back().w, c->slabs[i].w);
     }
-    auto shg_of = [](int w) { return sizeof(C) * (size_t)kGjWarps * 32 * (4 * w + 1); };
-    auto she_of = [](int w) { return sizeof(C) * (size_t)kEvWarps * 2 * 32 * (w + 1); };
-    size_t shg = 0, she = 0;
-    for (const Run& u : runs) {
-        shg = std::max(shg, shg_of(u.w));
-        she = std::max(she, she_of(u.w));
-    }
     auto shgw_of = [](int w) { return sizeof(C) * (size_t)w * (4 * w + 1); };
     const size_t shew = sizeof(C) * (size_t)6 * 32 * 33;
-    static size_t cfg_g = 0, cfg_e = 0, cfg_gw = 0, cfg_ew = 0;
-    int rc = set_smem(c, cr_gj_kernel<T>, shg, &cfg_g);
-    if (!rc) rc = set_smem(c, cr_even_kernel<T>, she, &cfg_e);
-    if (!rc) rc = set_smem(c, cr_gjw_kernel<T>, shgw_of(32), &cfg_gw);
+    static size_t cfg_gw = 0, cfg_ew = 0;
+    int rc = set_smem(c, cr_gjw_kernel<T>, shgw_of(32), &cfg_gw);
     if (!rc) rc = set_smem(c, cr_evenw_kernel<T>, shew, &cfg_ew);
     if (rc) return rc;
     // slabs factor independently: run 0 on s, every other run on an auxiliary
@@ -1766,32 +1528,20 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
             const Run& u = runs[ri];
             cudaStream_t su = ri == 0 ? s : c->aux_stream[ri - 1];
             if (ri > 0) cudaStreamWaitEvent(su, c->fork_event, 0);
-            const bool wide = u.w > 16;   // a CTA per block row
             for (int l = 0; l < nlev; ++l) {
                 const int K = cr_level(K0, l).K;
                 const int nodd = K / 2, nev = (K + 1) / 2;
                 if (l == 0)
                     cr_gj0_kernel<T><<<(nodd * u.n + kGj0Warps - 1) / kGj0Warps, 32 * kGj0Warps, 0, su>>>(
                         c->d_slabs, (const C*)c->coef, fac, work, K0, nodd, u.s0, u.n, c->d_err);
-                else if (wide)
+                else
                     cr_gjw_kernel<T><<<nodd * u.n, kWideThreads, shgw_of(u.w), su>>>(
                         c->d_slabs, fac, work, c->work_len, K0, l, nodd, u.s0, 0, 4 * u.w + 1, c->d_err);
-                else
-                    cr_gj_kernel<T><<<(nodd * u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
-                        c->d_slabs, fac, work, c->work_len, K0, l, nodd, u.s0, u.n, 0, 4 * u.w + 1, c->d_err);
-                if (wide)
-                    cr_evenw_kernel<T><<<nev * u.n, kWideThreads, shew, su>>>(c->d_slabs, fac, work, c->work_len,
-                                                                             K0, l, nev, u.s0, nlev);
-                else
-                    cr_even_kernel<T><<<(nev * u.n + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, she_of(u.w), su>>>(
-                        c->d_slabs, fac, work, c->work_len, K0, l, nev, u.s0, u.n, nlev, u.w + 1);
+                cr_evenw_kernel<T><<<nev * u.n, kWideThreads, shew, su>>>(c->d_slabs, fac, work, c->work_len, K0,
+                                                                         l, nev, u.s0, nlev);
             }
-            if (wide)
-                cr_gjw_kernel<T><<<u.n, kWideThreads, shgw_of(u.w), su>>>(c->d_slabs, fac, work, c->work_len, K0,
-                                                                          nlev, 1, u.s0, 1, 4 * u.w + 1, c->d_err);
-            else
-                cr_gj_kernel<T><<<(u.n + kGjWarps - 1) / kGjWarps, 32 * kGjWarps, shg_of(u.w), su>>>(
-                    c->d_slabs, fac, work, c->work_len, K0, nlev, 1, u.s0, u.n, 1, 4 * u.w + 1, c->d_err);
+            cr_gjw_kernel<T><<<u.n, kWideThreads, shgw_of(u.w), su>>>(c->d_slabs, fac, work, c->work_len, K0, nlev, 1,
+                                                                      u.s0, 1, 4 * u.w + 1, c->d_err);
             if (ri > 0) {
                 cudaEventRecord(c->aux_event[ri - 1], su);
                 cudaStreamWaitEvent(s, c->aux_event[ri - 1], 0);
