@@ -26,48 +26,51 @@ __device__ __forceinline__ double sigma_phys(int q, int n, int b, double Cw) {
 
 // Null vector of F^T for a 9 x 8 complex F (gamma^* F = 0): last column of the
 // unitary factor of a Householder QR of F.  Returns conj(gamma), unit norm,
-// centre entry real positive.
-__device__ void gamma_from_F(double2 F[9][8], double2 out[9]) {
-    double vn2[8];
+// centre entry real positive.  R: working precision (double, or float for the
+// moving-PML stencils of the single-precision preconditioner).
+template <typename R>
+__device__ void gamma_from_F(cx<R> F[9][8], double2 out[9]) {
+    using C = cx<R>;
+    R vn2[8];
     for (int k = 0; k < 8; ++k) {
-        double nx = 0;
+        R nx = 0;
         for (int i = k; i < 9; ++i) nx += cabs2(F[i][k]);
         nx = sqrt(nx);
-        const double2 fkk = F[k][k];
-        const double afk = sqrt(cabs2(fkk));
-        const double2 ph = afk > 0 ? mk(fkk.x / afk, fkk.y / afk) : mk(1.0, 0.0);
-        const double2 alpha = mk(-ph.x * nx, -ph.y * nx);
+        const C fkk = F[k][k];
+        const R afk = sqrt(cabs2(fkk));
+        const C ph = afk > 0 ? mk(fkk.x / afk, fkk.y / afk) : mk(R(1), R(0));
+        const C alpha = mk(-ph.x * nx, -ph.y * nx);
         F[k][k] = fkk - alpha;  // v stored in column k, rows k..8
-        double v2 = 0;
+        R v2 = 0;
         for (int i = k; i < 9; ++i) v2 += cabs2(F[i][k]);
         vn2[k] = v2;
         if (v2 == 0) continue;
         for (int j = k + 1; j < 8; ++j) {
-            double2 dot = mk(0.0, 0.0);
+            C dot = czero<C>();
             for (int i = k; i < 9; ++i) dot = cfma_conj(F[i][k], F[i][j], dot);
-            const double s = 2.0 / v2;
-            for (int i = k; i < 9; ++i) F[i][j] = F[i][j] - (s * dot) * F[i][k];
+            const R sc = R(2) / v2;
+            for (int i = k; i < 9; ++i) F[i][j] = F[i][j] - (sc * dot) * F[i][k];
         }
     }
-    double2 q[9];
-    for (int i = 0; i < 9; ++i) q[i] = mk(0.0, 0.0);
-    q[8] = mk(1.0, 0.0);
+    C q[9];
+    for (int i = 0; i < 9; ++i) q[i] = czero<C>();
+    q[8] = mk(R(1), R(0));
     for (int k = 7; k >= 0; --k) {
         if (vn2[k] == 0) continue;
-        double2 dot = mk(0.0, 0.0);
+        C dot = czero<C>();
         for (int i = k; i < 9; ++i) dot = cfma_conj(F[i][k], q[i], dot);
-        const double s = 2.0 / vn2[k];
-        for (int i = k; i < 9; ++i) q[i] = q[i] - (s * dot) * F[i][k];
+        const R sc = R(2) / vn2[k];
+        for (int i = k; i < 9; ++i) q[i] = q[i] - (sc * dot) * F[i][k];
     }
-    double nq = 0;
+    R nq = 0;
     for (int i = 0; i < 9; ++i) nq += cabs2(q[i]);
     nq = sqrt(nq);
-    const double a4 = sqrt(cabs2(q[4]));
-    const double2 ph = mk(q[4].x / a4, -q[4].y / a4);  // |q4| / q4
+    const R a4 = sqrt(cabs2(q[4]));
+    const C ph = mk(q[4].x / a4, -q[4].y / a4);  // |q4| / q4
     for (int i = 0; i < 9; ++i) {
-        double2 g = (1.0 / nq) * (q[i] * ph);
-        if (i == 4) g = mk(a4 / nq, 0.0);
-        out[i] = conjc(g);
+        C g = (R(1) / nq) * (q[i] * ph);
+        if (i == 4) g = mk(a4 / nq, R(0));
+        out[i] = mk((double)g.x, -(double)g.y);   // conj(gamma)
     }
 }
 
@@ -77,26 +80,28 @@ __device__ void gamma_from_F(double2 F[9][8], double2 out[9]) {
 // and an x2 part, E1(da, sc ra) E2(db, sc rb) with E(d, v) = exp(i w v (d h +
 // i dsigma_d)), and E(d, -v) has the conjugate phase and the reciprocal
 // modulus of E(d, v): 2 x 3 x 2 complex exponentials give all 72 entries.
+template <typename R>
 __device__ void pml_stencil(const double s1[3], const double s2[3], double w, double h, double2 out[9]) {
-    const double is2 = 0.70710678118654752440;
+    using C = cx<R>;
+    const R is2 = R(0.70710678118654752440);
     // E[axis][d + 1][scale][sign]: scale 0 -> v = 1, 1 -> v = 1/sqrt(2); sign 0 -> +v, 1 -> -v
-    double2 E[2][3][2][2];
+    C E[2][3][2][2];
     for (int ax = 0; ax < 2; ++ax) {
         const double* sg = ax == 0 ? s1 : s2;
         for (int d = -1; d <= 1; ++d) {
-            const double re = d * h, im = sg[d + 1] - sg[1];
+            const R re = R(d * h), im = R(sg[d + 1] - sg[1]);
             for (int sc = 0; sc < 2; ++sc) {
-                const double v = sc ? is2 : 1.0;
-                double sn, cs;
-                sincos(w * v * re, &sn, &cs);
-                const double mag = exp(-w * v * im);
-                const double inv = 1.0 / mag;
+                const R v = sc ? is2 : R(1);
+                R sn, cs;
+                sincos(R(w) * v * re, &sn, &cs);
+                const R mag = exp(-R(w) * v * im);
+                const R inv = R(1) / mag;
                 E[ax][d + 1][sc][0] = mk(mag * cs, mag * sn);
                 E[ax][d + 1][sc][1] = mk(inv * cs, -inv * sn);
             }
         }
     }
-    double2 F[9][8];
+    C F[9][8];
     for (int o = 0; o < 9; ++o) {
         const int da = o / 3 - 1, db = o % 3 - 1;
         int col = 0;
@@ -104,12 +109,12 @@ __device__ void pml_stencil(const double s1[3], const double s2[3], double w, do
             for (int rb = -1; rb <= 1; ++rb) {
                 if (ra == 0 && rb == 0) continue;
                 const int sc = (ra != 0 && rb != 0) ? 1 : 0;
-                const double2 e1 = ra == 0 ? mk(1.0, 0.0) : E[0][da + 1][sc][ra < 0];
-                const double2 e2 = rb == 0 ? mk(1.0, 0.0) : E[1][db + 1][sc][rb < 0];
+                const C e1 = ra == 0 ? mk(R(1), R(0)) : E[0][da + 1][sc][ra < 0];
+                const C e2 = rb == 0 ? mk(R(1), R(0)) : E[1][db + 1][sc][rb < 0];
                 F[o][col++] = e1 * e2;
             }
     }
-    gamma_from_F(F, out);
+    gamma_from_F<R>(F, out);
 }
 
 // Class of a grid index along one axis: 0 interior (all three sigmas zero),
@@ -141,7 +146,7 @@ __global__ void gamma_phys_kernel(double2* out, int n, int b, double Cw, double 
             s1[t] = sigma_phys(q1 - 1 + t, n, b, Cw);
             s2[t] = sigma_phys(q2 - 1 + t, n, b, Cw);
         }
-        pml_stencil(s1, s2, omega, h, g);
+        pml_stencil<double>(s1, s2, omega, h, g);
     }
     for (int o = 0; o < 9; ++o) out[(size_t)e * 9 + o] = g[o];
 }
@@ -149,6 +154,9 @@ __global__ void gamma_phys_kernel(double2* out, int n, int b, double Cw, double 
 // Auxiliary (moving) PML stencils: per frequency sample k, auxiliary layer
 // t = 1..b_aux (distance from D_i) and x2 class.  Along x1 the left profile of
 // width b_aux translated so that D_i's first layer plays the role of index 0.
+// R = float for the single-precision preconditioner (these stencils enter only
+// the slab subproblems, which it factors in single precision).
+template <typename R>
 __global__ void gamma_aux_kernel(double2* out, int n, int b, int baux, int ns, double s_lo, double s_hi,
                                  double Cw, double h) {
     const int nc = 2 * b + 1;
@@ -170,7 +178,7 @@ __global__ void gamma_aux_kernel(double2* out, int n, int b, int baux, int ns, d
         s2[u] = sigma_phys(q2 - 1 + u, n, b, Cw);
     }
     double2 g[9];
-    pml_stencil(s1, s2, w, h, g);
+    pml_stencil<R>(s1, s2, w, h, g);
     for (int o = 0; o < 9; ++o) out[(size_t)e * 9 + o] = g[o];
 }
 
@@ -304,8 +312,13 @@ int lss_build_gamma_aux(lss_ctx* c, cudaStream_t s) {
     const int nc = 2 * c->b + 1;
     const double Cw = c->pml.C / c->omega;
     const long long tot = (long long)c->ns_eff * c->b_aux * nc;
-    gamma_aux_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, s>>>(c->gam_aux, c->n, c->b, c->b_aux, c->ns_eff,
-                                                                  c->s_lo, c->s_hi, Cw, c->h);
+    const unsigned grid = (unsigned)((tot + 127) / 128);
+    if (c->prec == LSS_FP64)
+        gamma_aux_kernel<double><<<grid, 128, 0, s>>>(c->gam_aux, c->n, c->b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi,
+                                                      Cw, c->h);
+    else
+        gamma_aux_kernel<float><<<grid, 128, 0, s>>>(c->gam_aux, c->n, c->b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi,
+                                                     Cw, c->h);
     return lss_check_cuda(c, cudaGetLastError(), "gamma tables");
 }
 
