@@ -263,6 +263,8 @@ int lss_profile(lss_ctx *c, int enable);
  * with the same R has sized every workspace; they are dropped when a
  * workspace is reallocated and are not used while profiling is on.  The
  * results are the same either way.  On a batch context: every instance.
+ * The paper has no counterpart: this is how the library launches Sec. 2.5's
+ * GMRES iterations, not part of the method.
  */
 int lss_set_graphs(lss_ctx *c, int enable);
 /*
@@ -273,7 +275,8 @@ int lss_set_graphs(lss_ctx *c, int enable);
  * ring depth.  None of them changes any result (same arithmetic, same order),
  * so later solves agree bit for bit with untuned ones; only their speed
  * changes.  Requires a factored context; allocates and frees two vectors;
- * blocks the host.  On a batch: every instance.
+ * blocks the host.  On a batch: every instance.  The paper has no
+ * counterpart (launch configuration only).
  *   chosen  host, 5 ints (may be NULL): column group, right-hand sides in
  *           global memory (0) or automatic (-1), ring stages (0 = automatic),
  *           recurrence stages, ring stages of the 32-wide slabs' launches
