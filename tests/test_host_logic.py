@@ -1,0 +1,52 @@
+"""Host-side logic that needs no GPU: the seeded input recipes and the bench's
+reference arm (its JSON line follows the bench contract)."""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_ragged_instance_recipe():
+    ns = synth.ragged_sizes(**synth.RAGGED_32)
+    assert len(ns) == 32 and all(128 <= n <= 384 for n in ns)
+    assert ns == synth.ragged_sizes(**synth.RAGGED_32)          # seeded
+    inst = synth.ragged_instances(ns[:3], synth.RAGGED_32["seed"])
+    for n, (f, m, d) in zip(ns[:3], inst):
+        assert f == n / 8.0 and m.shape == (n, n) and d.shape == (1, 2)
+        c = 1.0 / np.sqrt(1.0 - m)
+        assert c.min() >= 0.8 - 1e-12 and c.max() <= 1.2 + 1e-12
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-14
+        edge = max(np.abs(m[0]).max(), np.abs(m[-1]).max(), np.abs(m[:, 0]).max(), np.abs(m[:, -1]).max())
+        assert edge <= 0.1 * np.abs(m).max()                        # c tapers to 1 towards the box boundary
+
+
+def test_workload_recipes_are_seeded():
+    for name in ("2d_n64", "2d_n256", "2d_n512_r64", "2d_n256_r16"):
+        w = synth.WORKLOADS[name]
+        m1, d1 = synth.make_workload(w)
+        m2, d2 = synth.make_workload(w)
+        assert np.array_equal(m1, m2) and np.array_equal(d1, d2)
+        assert m1.shape == (w.n, w.n) and d1.shape == (w.n_rhs, 2)
+        assert math.isclose(w.omega, 2 * math.pi * w.freq)
+
+
+def test_bench_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the oracle on the host (about 15 s)."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert "workload" in line["config"]
