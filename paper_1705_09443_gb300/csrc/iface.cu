@@ -28,7 +28,7 @@
 namespace {
 
 constexpr int kIfT = 256;   // threads per CTA: G lanes per column (one per layer) x column groups
-constexpr int kIfTN = 64;   // columns per CTA
+constexpr int kIfTN = 16;   // columns per CTA (a short chain per thread: 1 column of 16-wide blocks, 2 of 32-wide)
 
 struct IfProb {
     int slab, side, G, pad;
