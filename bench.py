@@ -193,6 +193,17 @@ def algorithmic(solver, R, prec_bytes):
 
 
 # ---------------------------------------------------------------- our arm
+def max_over_ranks(vals, dev, world):
+    """Element-wise maximum of per-rank timings over all ranks (one all-reduce;
+    a single rank returns its own values)."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1705_09443_gb300 import GmresOptions, LSS_FP64, LSS_MIXED, LSSolver
@@ -251,10 +262,7 @@ def run_ours(args, rank, world):
         solver.profile(False)
         prof_ms, prof_n = solver.profile_read()
         torch.cuda.synchronize()
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms, = max_over_ranks([total_ms], dev, world)
         iters = [s["iters"] for st in stats for s in st]
         relres = max(s["relres_true"] for st in stats for s in st)
         conv = all(s["relres_true"] <= 1e-8 for st in stats for s in st)
@@ -291,10 +299,7 @@ def run_ours(args, rank, world):
             e1.record(stream)
             e1.synchronize()
             setup_ms += e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([solve_ms, setup_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            solve_ms, setup_ms = (float(x) for x in t.tolist())
+        solve_ms, setup_ms = max_over_ranks([solve_ms, setup_ms], dev, world)
         graphs = solver.graph_count()
         # the same solves with every kernel launched one by one (no iteration graphs)
         solver.use_graphs(False)
@@ -337,10 +342,7 @@ def run_ours(args, rank, world):
             e1.synchronize()
             if k >= args.warmup:
                 e2e_ms += e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms, = max_over_ranks([e2e_ms], dev, world)
         res["e2e"] = {"value": (R * args.steps * world) / (e2e_ms / 1e3), "unit": "solves/s",
                       "h2d_bytes_per_step": int(n * n * 8 + R * 16), "d2h_bytes_per_step": int(R * n * n * 16)}
         results[prec_name] = res
@@ -398,10 +400,7 @@ def run_batched(args, dev, world):
         e1.record(stream)
         e1.synchronize()
         solve_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([total, solve_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total, solve_ms = (float(x) for x in t.tolist())
+    total, solve_ms = max_over_ranks([total, solve_ms], dev, world)
     # per-group breakdown of one step, outside the timed region
     solver.profile_read()
     solver.profile(True)
@@ -466,10 +465,7 @@ def run_ragged(args, dev, world):
             e1.record(stream)
             e1.synchronize()
             total += e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total, = max_over_ranks([total], dev, world)
         flat = [x for st in stats for q in st for x in q]
         out[name] = {"value": len(ns) * args.steps * world / (total / 1e3), "ms_per_step": total / args.steps,
                      "iters_mean": float(np.mean([x["iters"] for x in flat])),
