@@ -8,7 +8,7 @@ Liu & Ying, "Sparsify and sweep: an efficient preconditioner for the
 Lippmann-Schwinger equation" (arXiv:1705.09443).  Every function follows the
 paper's definitions in the paper's order and notation, in plain numpy/scipy
 (complex128).  Readings where the paper is silent or garbled are marked
-READING and listed in the project's design notes:
+READING; they are:
 
   * k_0 (Sec. 2.1): the paper cites a Duan-Rokhlin correction without weights;
     here k_0 is the integral of G over the grid cell [-h/2, h/2]^d.
@@ -570,6 +570,269 @@ class Problem2D:
 
 
 # --------------------------------------------------------------------------
+# Sec. 3.1: the same construction in 3D (27-point stencils, 26 directions)
+# --------------------------------------------------------------------------
+
+
+class Problem3D:
+    """The 3D sparsified system and its non-recursive sweeping preconditioner
+    (Sec. 3.1): alpha/beta on the 27-point neighbourhood, gamma annihilating the
+    26 normalised directions of {-1,0,1}^3 minus 0, slabs of x1-layers (each a
+    quasi-2D problem) swept exactly as in Algorithm 2.  Each slab subproblem is
+    factored here by a sparse LU (partial pivoting); the paper's nested
+    dissection is a different direct solver for the same subproblem.
+
+    Index convention: grid index (i1, i2, i3) in I^{h+eta} = {-b..n+1+b}^3,
+    stored at [i1+b, i2+b, i3+b]; vectors on I are (n, n, n) arrays at
+    [i1-1, i2-1, i3-1].  A layer is the (n_tot, n_tot) plane of fixed x1.
+    """
+
+    def __init__(self, n: int, omega: float, m: np.ndarray, params: Params | None = None):
+        self.p = params or Params()
+        self.n, self.omega, self.m = n, float(omega), np.asarray(m, dtype=np.float64)
+        self.h = 1.0 / (n + 1)
+        self.b = self.p.b_pml
+        self.b_aux = self.p.b_aux if self.p.b_aux is not None else self.b
+        self.n_tot = n + 2 + 2 * self.b
+        self.kw = nystrom_weights(3, n, omega, n)
+        self.alpha, self.beta, self.sv = interior_stencils(3, n, omega)
+        ns = self.p.n_samples if self.p.n_samples is not None else n
+        self.samples = frequency_samples(self.m, self.omega, ns)
+        self._gcache: dict = {}
+        self._slabs()
+        self._factor()
+
+    def m_at(self, i1: int, i2: int, i3: int) -> float:
+        n = self.n
+        if 1 <= i1 <= n and 1 <= i2 <= n and 1 <= i3 <= n:
+            return float(self.m[i1 - 1, i2 - 1, i3 - 1])
+        return 0.0
+
+    def sigma(self, idx):
+        return pml_sigma(idx, self.n, self.b, self.p.C, self.omega)
+
+    def _gamma(self, key, omega_loc, s1, s2, s3):
+        g = self._gcache.get(key)
+        if g is None:
+            g = pml_stencil(omega_loc, self.h, [np.asarray(s1), np.asarray(s2), np.asarray(s3)]).reshape(3, 3, 3)
+            self._gcache[key] = g
+        return g
+
+    def row(self, i1: int, i2: int, i3: int) -> np.ndarray:
+        """Coefficients c[d1+1, d2+1, d3+1] of H's row at (i1, i2, i3): on I^h
+        conj(alpha_o) + omega^2 conj(beta_o) m_{i+o}; on the PML conj(gamma_i)."""
+        n = self.n
+        if 0 <= i1 <= n + 1 and 0 <= i2 <= n + 1 and 0 <= i3 <= n + 1:
+            c = np.empty(27, dtype=np.complex128)
+            for a, o in enumerate(neighbourhood_offsets(3)):
+                c[a] = np.conj(self.alpha[a]) + self.omega ** 2 * np.conj(self.beta[a]) * \
+                    self.m_at(i1 + o[0], i2 + o[1], i3 + o[2])
+            return c.reshape(3, 3, 3)
+        s1 = self.sigma([i1 - 1, i1, i1 + 1])
+        s2 = self.sigma([i2 - 1, i2, i2 + 1])
+        s3 = self.sigma([i3 - 1, i3, i3 + 1])
+        return self._gamma(("phys", tuple(s1), tuple(s2), tuple(s3)), self.omega, s1, s2, s3)
+
+    def aux_row(self, s: int, t: int, i2: int, i3: int) -> np.ndarray:
+        """Row of the auxiliary PML point t layers left of D_i (first layer s),
+        at true position (s-t, i2, i3): x1 profile of the left PML of width
+        b_aux translated to end at layer s, physical sigma along x2 and x3,
+        local frequency the sample nearest omega^2 (1 - m(s-t, i2, i3))."""
+        a1 = s - t
+        s1 = pml_sigma(np.array([a1 - 1, a1, a1 + 1]) - s, self.n, self.b_aux, self.p.C, self.omega)
+        s2 = self.sigma([i2 - 1, i2, i2 + 1])
+        s3 = self.sigma([i3 - 1, i3, i3 + 1])
+        k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(a1, i2, i3)))
+        return self._gamma(("aux", k, tuple(s1), tuple(s2), tuple(s3)), math.sqrt(self.samples[k]), s1, s2, s3)
+
+    def _range(self):
+        return range(-self.b, self.n + 2 + self.b)
+
+    def assemble_H(self) -> sp.csr_matrix:
+        """H on I^{h+eta}, zero Dirichlet values on its boundary dropped."""
+        b, nt, lo, hi = self.b, self.n_tot, -self.b, self.n + 1 + self.b
+        rows, cols, vals = [], [], []
+        for i1 in self._range():
+            for i2 in self._range():
+                for i3 in self._range():
+                    c = self.row(i1, i2, i3)
+                    r = ((i1 + b) * nt + (i2 + b)) * nt + (i3 + b)
+                    for o in neighbourhood_offsets(3):
+                        j = (i1 + o[0], i2 + o[1], i3 + o[2])
+                        if all(lo <= v <= hi for v in j):
+                            rows.append(r)
+                            cols.append(((j[0] + b) * nt + (j[1] + b)) * nt + (j[2] + b))
+                            vals.append(c[o[0] + 1, o[1] + 1, o[2] + 1])
+        return sp.csr_matrix((vals, (rows, cols)), shape=(nt ** 3, nt ** 3))
+
+    def sparsify_rhs(self, r: np.ndarray) -> np.ndarray:
+        """f = Q r: f_i = alpha^* r_{mu_i} on I^h, 0 on the PML, r zero off I."""
+        n, b, nt = self.n, self.b, self.n_tot
+        rp = np.zeros((n + 4,) * 3, dtype=np.complex128)     # indices -1..n+2
+        rp[2:n + 2, 2:n + 2, 2:n + 2] = r
+        f = np.zeros((nt,) * 3, dtype=np.complex128)
+        ac = np.conj(self.alpha).reshape(3, 3, 3)
+        for o in neighbourhood_offsets(3):
+            f[b:b + n + 2, b:b + n + 2, b:b + n + 2] += ac[o[0] + 1, o[1] + 1, o[2] + 1] * \
+                rp[1 + o[0]:n + 3 + o[0], 1 + o[1]:n + 3 + o[1], 1 + o[2]:n + 3 + o[2]]
+        return f
+
+    def _slabs(self):
+        """Slabs of x1-layers, exactly as in 2D (Sec. 3.1, Sec. 2.3)."""
+        n, b, bs = self.n, self.b, self.p.b_slab
+        nl = -(-(n + 2) // bs)
+        self.n_slabs = nl
+        self.slab_first, self.slab_last = [], []
+        for i in range(nl):
+            self.slab_first.append(-b if i == 0 else i * bs)
+            self.slab_last.append(n + 1 + b if i == nl - 1 else (i + 1) * bs - 1)
+
+    def subproblem(self, i: int):
+        """Matrix of slab i's subproblem (Eq. Hwv_approx in 3D): b_aux virtual
+        auxiliary layers then D_i's layers (none for the first slab); couplings
+        leaving the layer set are dropped.  Returns (matrix, layers, n_aux)."""
+        b, nt, lo, hi = self.b, self.n_tot, -self.b, self.n + 1 + self.b
+        s, e = self.slab_first[i], self.slab_last[i]
+        aux = [] if i == 0 else list(range(s - self.b_aux, s))
+        layers = aux + list(range(s, e + 1))
+        pos = {x1: a for a, x1 in enumerate(layers)}
+        rows, cols, vals = [], [], []
+        for a, x1 in enumerate(layers):
+            for i2 in self._range():
+                for i3 in self._range():
+                    c = self.aux_row(s, s - x1, i2, i3) if x1 < s else self.row(x1, i2, i3)
+                    r = (a * nt + (i2 + b)) * nt + (i3 + b)
+                    for o in neighbourhood_offsets(3):
+                        ja = pos.get(x1 + o[0])
+                        j2, j3 = i2 + o[1], i3 + o[2]
+                        if ja is None or not (lo <= j2 <= hi and lo <= j3 <= hi):
+                            continue
+                        rows.append(r)
+                        cols.append((ja * nt + (j2 + b)) * nt + (j3 + b))
+                        vals.append(c[o[0] + 1, o[1] + 1, o[2] + 1])
+        sz = len(layers) * nt * nt
+        return sp.csr_matrix((vals, (rows, cols)), shape=(sz, sz)), layers, len(aux)
+
+    def _factor(self):
+        """Algorithm 1 in 3D: an LU of every slab subproblem."""
+        self.lu, self.n_aux = [], []
+        for i in range(self.n_slabs):
+            M, layers, na = self.subproblem(i)
+            self.lu.append(spla.splu(M.tocsc()))
+            self.n_aux.append(na)
+
+    def _T(self, i, v, trans):
+        nt2 = self.n_tot ** 2
+        na = self.n_aux[i]
+        rhs = np.zeros(((na + v.shape[0]) * nt2,), dtype=np.complex128)
+        rhs[na * nt2:] = v.reshape(-1)
+        w = self.lu[i].solve(rhs, trans=trans)
+        return w[na * nt2:].reshape(v.shape)
+
+    def T(self, i: int, v: np.ndarray) -> np.ndarray:
+        """T~_i v: zero auxiliary layers, solve, restrict to D_i."""
+        return self._T(i, v, "N")
+
+    def T_transpose(self, i: int, v: np.ndarray) -> np.ndarray:
+        return self._T(i, v, "T")
+
+    def _layer_coupling(self, x1: int, plane: np.ndarray, side: int, transpose: bool) -> np.ndarray:
+        """Apply the x1-offset `side` (-1 or +1) part of the rows of layer x1 to
+        the neighbouring layer's values `plane` (or its transpose)."""
+        b, nt, lo, hi = self.b, self.n_tot, -self.b, self.n + 1 + self.b
+        out = np.zeros((nt, nt), dtype=np.complex128)
+        for i2 in self._range():
+            for i3 in self._range():
+                c = self.row(x1, i2, i3)[side + 1]
+                for d2 in (-1, 0, 1):
+                    for d3 in (-1, 0, 1):
+                        j2, j3 = i2 + d2, i3 + d3
+                        if lo <= j2 <= hi and lo <= j3 <= hi:
+                            if transpose:
+                                out[j2 + b, j3 + b] += c[d2 + 1, d3 + 1] * plane[i2 + b, i3 + b]
+                            else:
+                                out[i2 + b, i3 + b] += c[d2 + 1, d3 + 1] * plane[j2 + b, j3 + b]
+        return out
+
+    def couple_left(self, i, u_prev_last):
+        """H_{[i,i-1]} u_{[i-1]}: rows of D_i's first layer, x1-offset -1."""
+        return self._layer_coupling(self.slab_first[i], u_prev_last, -1, False)
+
+    def couple_right(self, i, u_next_first):
+        """H_{[i,i+1]} u_{[i+1]}: rows of D_i's last layer, x1-offset +1."""
+        return self._layer_coupling(self.slab_last[i], u_next_first, +1, False)
+
+    def slab_view(self, f, i):
+        b = self.b
+        return f[self.slab_first[i] + b:self.slab_last[i] + b + 1]
+
+    def sweep(self, f, T=None):
+        """Algorithm 2 (forward then backward sweep) on 3D slabs."""
+        T = T or self.T
+        nl = self.n_slabs
+        u = [None] * nl
+        u[0] = T(0, self.slab_view(f, 0))
+        for i in range(1, nl):
+            v = self.slab_view(f, i).copy()
+            v[0] -= self.couple_left(i, u[i - 1][-1])
+            u[i] = T(i, v)
+        for i in range(nl - 2, -1, -1):
+            v = np.zeros_like(u[i])
+            v[-1] = self.couple_right(i, u[i + 1][0])
+            u[i] = u[i] - T(i, v)
+        return np.concatenate(u, axis=0)
+
+    def extract(self, ut):
+        b, n = self.b, self.n
+        return ut[b + 1:b + 1 + n, b + 1:b + 1 + n, b + 1:b + 1 + n]
+
+    def precondition(self, r):
+        """P r: f = Q r, sweep, extract on I."""
+        return self.extract(self.sweep(self.sparsify_rhs(r)))
+
+    def precondition_transpose(self, y):
+        """P^T y = Q^T Sweep^T E^T y, the two passes of the sweep transposed
+        and taken in reverse (as in 2D)."""
+        b, n, nt = self.b, self.n, self.n_tot
+        v = np.zeros((nt,) * 3, dtype=np.complex128)
+        v[b + 1:b + 1 + n, b + 1:b + 1 + n, b + 1:b + 1 + n] = y
+        nl = self.n_slabs
+        z = [self.slab_view(v, i).copy() for i in range(nl)]
+        for i in range(1, nl):
+            # H_{[i-1,i]}^T: slab i-1's last-layer rows (x1-offset +1), transposed
+            t = self.T_transpose(i - 1, z[i - 1])
+            z[i][0] -= self._layer_coupling(self.slab_last[i - 1], t[-1], +1, True)
+        x = [None] * nl
+        x[nl - 1] = self.T_transpose(nl - 1, z[nl - 1])
+        for i in range(nl - 2, -1, -1):
+            # H_{[i+1,i]}^T: slab i+1's first-layer rows (x1-offset -1), transposed
+            w = z[i].copy()
+            w[-1] -= self._layer_coupling(self.slab_first[i + 1], x[i + 1][0], -1, True)
+            x[i] = self.T_transpose(i, w)
+        ut = np.concatenate(x, axis=0)
+        ac = np.conj(self.alpha).reshape(3, 3, 3)
+        out = np.zeros((n, n, n), dtype=np.complex128)
+        for o in neighbourhood_offsets(3):
+            out += ac[o[0] + 1, o[1] + 1, o[2] + 1] * \
+                ut[b + 1 - o[0]:b + 1 + n - o[0], b + 1 - o[1]:b + 1 + n - o[1], b + 1 - o[2]:b + 1 + n - o[2]]
+        return out
+
+    def exact_T_ops(self):
+        """T_[i] as the restriction of H_{[1:i,1:i]}^{-1} to D_i (Eq. Hwv), dense."""
+        H = self.assemble_H().toarray()
+        b, nt2 = self.b, self.n_tot ** 2
+        inv = []
+        for i in range(self.n_slabs):
+            e = (self.slab_last[i] + b + 1) * nt2
+            s0 = (self.slab_first[i] + b) * nt2
+            inv.append(np.linalg.inv(H[:e, :e])[s0:, s0:])
+
+        def T(i, v):
+            return (inv[i] @ v.reshape(-1)).reshape(v.shape)
+        return T
+
+
+# --------------------------------------------------------------------------
 # GMRES (Sec. 2.5: standard restarted GMRES, relative tolerance)
 # --------------------------------------------------------------------------
 
@@ -650,10 +913,16 @@ def gmres(apply_A, apply_P, g: np.ndarray, restart: int = 30, tol: float = 1e-8,
 # --------------------------------------------------------------------------
 
 
+def make_problem(n, omega, m, params: Params | None = None):
+    """Problem2D or Problem3D by the dimension of m."""
+    m = np.asarray(m)
+    return (Problem3D if m.ndim == 3 else Problem2D)(n, omega, m, params)
+
+
 def solve(n, omega, m, direction, params: Params | None = None, restart=30, tol=1e-8,
-          max_iter=500, problem: Problem2D | None = None):
+          max_iter=500, problem=None):
     """Scattered field u on I for one incident plane wave."""
-    pb = problem or Problem2D(n, omega, m, params)
+    pb = problem or make_problem(n, omega, m, params)
     g = ls_rhs(m, omega, pb.kw, direction)
     A = lambda u: ls_apply(u, m, omega, pb.kw)  # noqa: E731
     res = gmres(A, pb.precondition, g, restart, tol, max_iter)
@@ -664,11 +933,55 @@ def solve(n, omega, m, direction, params: Params | None = None, restart=30, tol=
 
 def dense_ls_matrix(n, omega, m, kw):
     """I + omega^2 K M as a dense matrix (pins on tiny grids)."""
-    N = n * n
+    shape = np.asarray(m).shape
+    N = int(np.prod(shape))
     A = np.zeros((N, N), dtype=np.complex128)
     e = np.zeros(N, dtype=np.complex128)
     for j in range(N):
         e[:] = 0
         e[j] = 1
-        A[:, j] = ls_apply(e.reshape(n, n), m, omega, kw).reshape(-1)
+        A[:, j] = ls_apply(e.reshape(shape), m, omega, kw).reshape(-1)
     return A
+
+
+# --------------------------------------------------------------------------
+# Gradient of a receiver misfit with respect to m (adjoint of Eq. LS_d)
+# --------------------------------------------------------------------------
+
+
+def misfit(n, omega, m, dirs, receivers, data, kw=None):
+    """L = 1/2 sum_s sum_r |u_s(receiver r) - d_{s,r}|^2, u_s the scattered field
+    of the plane wave with direction dirs[s], solved densely (tiny grids).
+    receivers: integer grid indices into the (n,)*d arrays, shape (n_rcv, d)."""
+    kw = kw if kw is not None else nystrom_weights(np.asarray(m).ndim, n, omega, n)
+    A = dense_ls_matrix(n, omega, m, kw)
+    idx = tuple(np.asarray(receivers).T)
+    L = 0.0
+    for s, d in enumerate(dirs):
+        g = ls_rhs(m, omega, kw, d)
+        u = np.linalg.solve(A, g.reshape(-1)).reshape(g.shape)
+        L += 0.5 * float(np.sum(np.abs(u[idx] - data[s]) ** 2))
+    return L
+
+
+def misfit_gradient_dense(n, omega, m, dirs, receivers, data, kw=None):
+    """dL/dm by the dense adjoint: with A = I + omega^2 K M and g = -omega^2 K M u_I
+    (Eq. LS_d), A du/dm_x = -omega^2 K e_x (u + u_I)_x; so with
+    A^T lambda = R^T conj(u(receivers) - d) (R = restriction to the receivers),
+    dL/dm_x = Re(-omega^2 (K lambda)_x (u + u_I)_x), summed over the waves."""
+    m = np.asarray(m, dtype=np.float64)
+    kw = kw if kw is not None else nystrom_weights(m.ndim, n, omega, n)
+    A = dense_ls_matrix(n, omega, m, kw)
+    idx = tuple(np.asarray(receivers).T)
+    grad = np.zeros(m.shape)
+    one = np.ones_like(m)
+    for s, d in enumerate(dirs):
+        uI = plane_wave(n, omega, d)
+        g = ls_rhs(m, omega, kw, d)
+        u = np.linalg.solve(A, g.reshape(-1)).reshape(g.shape)
+        rt = np.zeros(m.shape, dtype=np.complex128)
+        np.add.at(rt, idx, np.conj(u[idx] - data[s]))
+        lam = np.linalg.solve(A.T, rt.reshape(-1)).reshape(m.shape)
+        Klam_w2 = ls_apply(lam, one, omega, kw) - lam           # omega^2 K lambda
+        grad += np.real(-Klam_w2 * (u + uI))
+    return grad
