@@ -14,8 +14,14 @@
  *
  * Conventions for every entry point:
  *  - Vectors on I are complex128 (interleaved re, im doubles), row-major with
- *    x1 slowest: element (i1, i2) at offset (i1-1)*n + (i2-1).  A batch of R
+ *    x1 slowest: element (i1, i2) at offset (i1-1)*n + (i2-1) in 2D, element
+ *    (i1, i2, i3) at ((i1-1)*n + (i2-1))*n + (i3-1) in 3D.  A batch of R
  *    vectors is R such arrays back to back (stride n^d complex numbers).
+ *  - 3D grids (Sec. 3.1) use the same construction with the 27-point
+ *    neighbourhood and the 26 PML directions; their slab subproblems are block
+ *    tridiagonal along x2 with dense blocks of (slab layers) x n_tot unknowns,
+ *    factored by block Gaussian elimination whose pivot blocks are inverted
+ *    explicitly (Gauss-Jordan with partial pivoting inside each block).
  *  - Pointers named *_dev are device pointers owned by the caller; *_host are
  *    host pointers owned by the caller.  The library never frees them and keeps
  *    no reference after the call returns.
@@ -36,8 +42,8 @@ extern "C" {
 
 typedef struct lss_ctx lss_ctx;
 
-/* Grid (Sec. 2.1): dimension d (2; 3 is rejected with LSS_ERR_UNSUPPORTED),
- * n points per unit length, h = 1/(n+1), p_i = i h. */
+/* Grid (Sec. 2.1, Sec. 3.1): dimension d (2 or 3), n points per unit length,
+ * h = 1/(n+1), p_i = i h. */
 typedef struct { int dim; int n; } lss_grid;
 
 /* PML (Sec. 2.2.2): b_pml layers (eta = b_pml h) and the strength C of
@@ -85,11 +91,13 @@ enum {
  * (Sec. 2.3), the slab partition, and assembles every slab subproblem
  * (Eq. Hwv_approx).
  *   out        receives the new context (NULL on failure)
- *   g          grid; n in [4, 2048]
+ *   g          grid; 2D: n in [4, 2048]; 3D: n in [3, 128]
  *   omega      angular frequency > 0
  *   m_dev      device, n^d float64, m = 1 - 1/c^2 on I (row-major, x1 slowest)
- *   pml, slab  parameters above; every slab subproblem must be at most 32
- *              layers wide: b_aux + b_slab + b_pml <= 32 (the last slab)
+ *   pml, slab  parameters above; 2D: every slab subproblem must be at most 32
+ *              layers wide: b_aux + b_slab + b_pml <= 32 (the last slab);
+ *              3D: (layers of the widest subproblem) x (n + 2 + 2 b_pml) must
+ *              not exceed 1600 (LSS_ERR_UNSUPPORTED otherwise)
  *   precision  LSS_FP64 (all FP64) or LSS_MIXED (slab factors, sweep and the
  *              interface matrices in FP32; LS matvec, Arnoldi, Givens and the
  *              true residual in FP64; solves use flexible GMRES either way)
@@ -111,7 +119,9 @@ int lss_set_medium(lss_ctx *c, const double *m_dev, void *stream);
 /*
  * lss_factor - Algorithm 1 steps 4-8: block-tridiagonal LU (along x2, pivoting
  * inside each block) of every slab subproblem, all slabs in one launch, then
- * the interface maps that let the sweep of Algorithm 2 run slab-parallel.
+ * (2D) the interface maps that let the sweep of Algorithm 2 run slab-parallel.
+ * In 3D every slab's pivot blocks D_k = A_k - C_k D_{k-1}^{-1} B_{k-1} are
+ * inverted explicitly and stored; all slabs advance together.
  * Returns LSS_ERR_SINGULAR if a block pivot vanished.  Blocks the host.
  */
 int lss_factor(lss_ctx *c, void *stream);
@@ -144,7 +154,9 @@ int lss_apply_A(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose
  * x_i = T~_i^T (w_i - H_{[i+1,i]}^T first(x_{i+1}))), then Q^T (conj(alpha)
  * rows transposed).  The first transposed call after lss_factor also builds
  * the transposed sweep's interface maps.  Requires lss_factor.
- * x_dev, y_dev: R x n^d c128.
+ * x_dev, y_dev: R x n^d c128.  3D: transpose = 1 returns LSS_ERR_UNSUPPORTED;
+ * the sweep of Algorithm 2 runs as one grid-synchronised launch (slab after
+ * slab, block row after block row).
  */
 int lss_apply_P(lss_ctx *c, const void *x_dev, void *y_dev, int R, int transpose,
                 void *stream);
@@ -169,6 +181,7 @@ int lss_solve(lss_ctx *c, const void *g_dev, void *u_dev, int R, const lss_gmres
  * a solution u of lss_solve, rhs = conj(dL/du) (dL/du = dL/dRe u + i dL/dIm u)
  * gives mu with dL/dm = Re((-omega^2 K mu) . (u + u_I)) (lss_medium_gradient).
  *   rhs_dev, mu_dev  device, R x n^d complex128
+ * 2D grids only (LSS_ERR_UNSUPPORTED on a 3D context).
  */
 int lss_adjoint_solve(lss_ctx *c, const void *rhs_dev, void *mu_dev, int R, const lss_gmres *o,
                       lss_stats *stats, void *stream);
@@ -181,6 +194,7 @@ int lss_adjoint_solve(lss_ctx *c, const void *rhs_dev, void *mu_dev, int R, cons
  *   mu_dev, u_dev  device, R x n^d complex128
  *   dirs_host      host, R x 2 unit directions
  *   grad_dev       device, n^d float64 (output)
+ * 2D grids only (LSS_ERR_UNSUPPORTED on a 3D context).
  */
 int lss_medium_gradient(lss_ctx *c, const void *mu_dev, const void *u_dev, const double *dirs_host,
                         int R, double *grad_dev, void *stream);
@@ -199,7 +213,8 @@ int lss_solve_host(lss_ctx *c, const void *g_host, void *u_host, int R,
  * subproblem with the stored factors, restrict to D_i).
  *   slab       0-based slab index
  *   v_dev, w_dev  device, R x (layers of D_i) x n_tot complex128 with
- *              n_tot = n + 2 + 2 b_pml, x1 layer slowest
+ *              n_tot = n + 2 + 2 b_pml, x1 layer slowest; in 3D
+ *              R x (layers of D_i) x n_tot x n_tot (x1, then x2, then x3)
  */
 int lss_apply_slab(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
                    void *stream);
@@ -220,9 +235,13 @@ int lss_apply_slab(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
  * last call's contents (nothing in it needs to start at zero): calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  A call that would need more than 8 MiB of scratch
- * (R x n_tot x the widest slab's width rounded up to even, in complex entries
- * of the working precision) returns LSS_ERR_UNSUPPORTED without launching.
- * Arguments, layouts and ownership as for lss_apply_slab.
+ * (R x n_tot x P complex entries of the working precision, P = 16 when the
+ * widest slab subproblem has at most 16 layers, else 32) returns
+ * LSS_ERR_UNSUPPORTED without launching.
+ * Arguments, layouts and ownership as for lss_apply_slab.  2D contexts only
+ * (LSS_ERR_UNSUPPORTED on a 3D context); LSS_ERR_ARG on a batch context.
+ * The cached address is valid while the device's primary context lives: do
+ * not call this entry point again after cudaDeviceReset.
  */
 int lss_apply_slab_noalloc(lss_ctx *c, int slab, const void *v_dev, void *w_dev, int R,
                            void *stream);
@@ -232,8 +251,9 @@ int lss_apply_slab_noalloc(lss_ctx *c, int slab, const void *v_dev, void *w_dev,
 int lss_info(const lss_ctx *c, int *n_tot, int *n_slabs, int *fft_len);
 int lss_slab_info(const lss_ctx *c, int slab, int *first_x1, int *n_layers, int *n_aux);
 
-/* Interior stencils alpha, beta (Eq. alpha, Eq. beta) as 9 (2D) complex128
- * each, copied to host arrays; lexicographic offsets, x1 slowest. */
+/* Interior stencils alpha, beta (Eq. alpha, Eq. beta) as 3^d complex128 each
+ * (9 in 2D, 27 in 3D), copied to host arrays; lexicographic offsets, x1
+ * slowest. */
 int lss_get_stencils(const lss_ctx *c, double *alpha_host, double *beta_host);
 
 /* Profiling.  lss_profile(c, 1) starts recording CUDA events (on the
@@ -272,7 +292,7 @@ int lss_set_graphs(lss_ctx *c, int enable);
  * context's own operations (CUDA events, a few runs per candidate): the FFT
  * column group of the LS operator, the slab-solve shared-memory plan (ring
  * stages; right-hand sides in shared or global memory) and the recurrence's
- * ring depth.  None of them changes any result (same arithmetic, same order),
+ * ring depth.  2D grids only (LSS_ERR_UNSUPPORTED on a 3D context).  None of them changes any result (same arithmetic, same order),
  * so later solves agree bit for bit with untuned ones; only their speed
  * changes.  Requires a factored context; allocates and frees two vectors;
  * blocks the host.  On a batch: every instance.  The paper has no
@@ -299,7 +319,7 @@ int lss_profile_read(lss_ctx *c, double *ms, long long *launches, int ncat);
  * the caller's stream, drives every instance concurrently (one host thread
  * per instance, up to 32) and joins back, so small instances share the GPU.
  *
- * lss_setup_batch - lss_setup for n_inst instances.
+ * lss_setup_batch - lss_setup for n_inst instances (2D grids only).
  *   g, omega, m_dev  arrays of n_inst entries (grid, angular frequency, device
  *                    pointer to that instance's n_q^2 float64 medium)
  *   pml, slab, precision  shared by all instances

@@ -135,6 +135,8 @@ int lss_setup_batch(lss_ctx** out, int n_inst, const lss_grid* g, const double* 
     if (n_inst < 1 || !g || !omega || !m_dev || !pml || !slab)
         return lss_fail(nullptr, LSS_ERR_ARG, "setup_batch: bad arguments");
     for (int q = 0; q < n_inst; ++q)
+        if (g[q].dim != 2) return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "setup_batch: 2D instances only");
+    for (int q = 0; q < n_inst; ++q)
         if (!m_dev[q]) return lss_fail(nullptr, LSS_ERR_ARG, "setup_batch: m of instance " + std::to_string(q) + " is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     lss_ctx* c = new lss_ctx();

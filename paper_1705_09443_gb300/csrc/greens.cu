@@ -6,6 +6,7 @@
 
 #include "lss_common.cuh"
 #include "lss_ctx.h"
+#include "lss3d.h"
 
 using cd = std::complex<double>;
 
@@ -204,9 +205,11 @@ __global__ void gram_partial(const double2* __restrict__ kx, int n, double2* __r
     if (threadIdx.x == 0) part[(long long)pair * gridDim.x + blockIdx.x] = red[0];
 }
 
+}  // namespace
+
 // Cyclic Jacobi eigen-decomposition of a real symmetric matrix (n x n,
 // row-major); returns eigenvalues in d and eigenvectors as columns of V.
-void jacobi_eigen(std::vector<double> A, int n, std::vector<double>& d, std::vector<double>& V) {
+void lss_jacobi_eigen(std::vector<double> A, int n, std::vector<double>& d, std::vector<double>& V) {
     V.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
     for (int sweep = 0; sweep < 100; ++sweep) {
@@ -246,8 +249,6 @@ void jacobi_eigen(std::vector<double> A, int n, std::vector<double>& d, std::vec
     d.resize(n);
     for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
 }
-
-}  // namespace
 
 // k table, twiddles, FFT of the kernel.
 int lss_build_kernel(lss_ctx* c, cudaStream_t s) {
@@ -322,7 +323,7 @@ int lss_build_interior_stencils(lss_ctx* c, cudaStream_t s) {
             A[(9 + a) * 18 + 9 + b] = Gm[a][b].real();
         }
     std::vector<double> d, V;
-    jacobi_eigen(A, 18, d, V);
+    lss_jacobi_eigen(A, 18, d, V);
     int imin = 0;
     for (int i = 1; i < 18; ++i)
         if (d[i] < d[imin]) imin = i;

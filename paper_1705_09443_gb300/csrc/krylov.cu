@@ -114,7 +114,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
                cudaStream_t s, int transpose) {
     // transpose: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T
     const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
-    const long long N = (long long)c->n * c->n;
+    const long long N = c->npts();
     const int m = o->restart;
     const double tol = o->tol;
     const int maxit = o->max_iter;
@@ -165,7 +165,8 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     // Graphs: only once a solve with this R and transpose ran uncaptured at the
     // current workspace generation (every buffer the body touches exists), and
     // not while profiling (the profile records events around kernel groups).
-    const bool use_graph = c->graphs_on && !c->prof_on;
+    // (the 3D sweep is a cooperative grid-synchronised launch: run uncaptured)
+    const bool use_graph = c->graphs_on && !c->prof_on && c->dim == 2;
     bool warm = false;
     for (const auto& k : c->graph_warm)
         warm |= k[0] == R && k[1] == transpose && (unsigned long long)k[2] == c->buf_gen;

@@ -1,0 +1,1453 @@
+// The 3D path (Sec. 3.1): Nystrom weights and their FFT on the L^3 grid, the
+// 27-point interior stencils, the 26-direction PML stencils, slabs of
+// x1-layers whose subproblems are block tridiagonal along x2 with dense
+// blocks of w * n_tot unknowns (layer a, x3 index c), their factorization by
+// block Gaussian elimination with every pivot block inverted by blocked
+// Gauss-Jordan elimination with partial pivoting, and the sweep of
+// Algorithm 2 as one persistent grid-synchronised kernel.
+//
+// Layouts (complex entries):
+//  - vectors on I: n^3, x1 slowest;  grid vectors on I^{h+eta}: n_tot^3,
+//    [X1][X2][X3] with X = x + b.
+//  - slab i's coefficient table: block row k (X2 = k), part p = d2+1
+//    (0: coupling to block k-1, 1: the block itself, 2: block k+1), row
+//    q = a * n_tot + c (a = layer of the subproblem, c = X3), 9 entries
+//    (d1+1)*3 + (d3+1):  ((k*3 + p) * M + q) * 9 + ...,  M = w * n_tot.
+//  - factors: per slab and block row k the dense M x M inverse of the pivot
+//    block D_k, row-major.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "fft_line.cuh"
+#include "lss_common.cuh"
+#include "lss_ctx.h"
+#include "lss3d.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr int kMaxBlock3 = 1600;      // largest pivot block M = w * n_tot (panel kernel shared memory)
+constexpr int kNB64 = 8;              // Gauss-Jordan panel width, FP64
+constexpr int kNB32 = 16;             // Gauss-Jordan panel width, FP32
+constexpr int kSweepThreads = 512;
+constexpr int kSweepRB = 4;           // right-hand sides per sweep launch
+
+int line_threads3(int L) { return L / 4 < 32 ? 32 : L / 4; }
+int col_group3(int L) { return L >= 1024 ? 1 : (L >= 256 ? 2 : 4); }
+
+// ---------------------------------------------------------------- kernel table (Sec. 2.1 in 3D)
+
+// k_j = G(|p_j|) h^3 = h^3 exp(i omega r) / (4 pi r)
+__device__ __forceinline__ double2 k_weight_3d(double r, double omega, double h3) {
+    double sn, cs;
+    sincos(omega * r, &sn, &cs);
+    const double s = h3 / (4.0 * M_PI * r);
+    return mk(s * cs, s * sn);
+}
+
+// Circular L^3 table: offsets |o_a| <= n-1 at o_a mod L, zero elsewhere; [j1][j2][j3].
+__global__ void k3_table_circ(double2* kc, int n, int L, double omega, double h, double2 k0) {
+    const long long tot = (long long)L * L * L;
+    const double h3 = h * h * h;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j1 = (int)(e / ((long long)L * L)), j2 = (int)((e / L) % L), j3 = (int)(e % L);
+        const int o1 = j1 < L / 2 ? j1 : j1 - L, o2 = j2 < L / 2 ? j2 : j2 - L, o3 = j3 < L / 2 ? j3 : j3 - L;
+        double2 v = mk(0.0, 0.0);
+        if (abs(o1) <= n - 1 && abs(o2) <= n - 1 && abs(o3) <= n - 1) {
+            if (o1 == 0 && o2 == 0 && o3 == 0) v = k0;
+            else v = k_weight_3d(h * sqrt((double)o1 * o1 + (double)o2 * o2 + (double)o3 * o3), omega, h3);
+        }
+        kc[e] = v;
+    }
+}
+
+// Offsets {-(n+1)..n+1}^3, index ((o1+n+1)*S + o2+n+1)*S + o3+n+1, S = 2n+3.
+__global__ void k3_table_ext(double2* kx, int n, double omega, double h, double2 k0) {
+    const int S = 2 * n + 3;
+    const long long tot = (long long)S * S * S;
+    const double h3 = h * h * h;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int o1 = (int)(e / ((long long)S * S)) - (n + 1), o2 = (int)((e / S) % S) - (n + 1),
+                  o3 = (int)(e % S) - (n + 1);
+        kx[e] = (o1 == 0 && o2 == 0 && o3 == 0)
+                    ? k0
+                    : k_weight_3d(h * sqrt((double)o1 * o1 + (double)o2 * o2 + (double)o3 * o3), omega, h3);
+    }
+}
+
+// Gram matrix of K_{mu,mu^c} (Eq. alpha in 3D): G_ab = sum_{j in mu^c} k_{o_a-j} conj(k_{o_b-j}),
+// mu^c = {-n..n}^3 minus mu; pairs a <= b of the 27 offsets; block partial sums.
+__global__ void gram3_partial(const double2* __restrict__ kx, int n, double2* __restrict__ part) {
+    __shared__ double2 red[256];
+    int pair = blockIdx.y, a = 0;
+    while (pair >= 27 - a) { pair -= 27 - a; ++a; }
+    const int b = a + pair;
+    const int a1 = a / 9 - 1, a2 = (a / 3) % 3 - 1, a3 = a % 3 - 1;
+    const int b1 = b / 9 - 1, b2 = (b / 3) % 3 - 1, b3 = b % 3 - 1;
+    const long long S = 2 * n + 3, Mw = 2 * n + 1;
+    const long long tot = Mw * Mw * Mw;
+    double2 acc = mk(0.0, 0.0);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j1 = (int)(e / (Mw * Mw)) - n, j2 = (int)((e / Mw) % Mw) - n, j3 = (int)(e % Mw) - n;
+        if (abs(j1) <= 1 && abs(j2) <= 1 && abs(j3) <= 1) continue;
+        const double2 ka = kx[((a1 - j1 + n + 1) * S + (a2 - j2 + n + 1)) * S + (a3 - j3 + n + 1)];
+        const double2 kb = kx[((b1 - j1 + n + 1) * S + (b2 - j2 + n + 1)) * S + (b3 - j3 + n + 1)];
+        acc = cfma(ka, conjc(kb), acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// ---------------------------------------------------------------- LS operator in 3D (pruned FFT convolution)
+
+// Pass over contiguous x3 lines.  Forward: grid (n^2 or L^2 lines, R); line
+// (i1, i2) of the input (m.*u, u, m.*u_I, or a raw L-line) -> buf[r][line][L].
+template <int IN>
+__global__ void mv3_rows_fwd(const double2* __restrict__ x, const double* __restrict__ m,
+                             const double* __restrict__ dirs, double2* __restrict__ uI, double2* __restrict__ buf,
+                             const double2* __restrict__ tw, int n, int lines, int L, int lg, double omega,
+                             double h) {
+    extern __shared__ double2 sm[];
+    double2* A = sm;
+    double2* B = sm + L;
+    const int line = blockIdx.x, r = blockIdx.y, t = threadIdx.x, nt = blockDim.x;
+    const long long N = (long long)n * n * n;
+    for (int j = t; j < L; j += nt) {
+        double2 v = mk(0.0, 0.0);
+        if (IN == MV_IN_RAW) {
+            v = x[(long long)line * L + j];
+        } else if (j < n) {
+            const long long e = (long long)line * n + j;
+            if (IN == MV_IN_MU) {
+                v = m[e] * x[r * N + e];
+            } else if (IN == MV_IN_U) {
+                v = x[r * N + e];
+            } else {   // u_I = exp(i omega d.p), p = ((i1+1) h, (i2+1) h, (j+1) h)
+                const int i1 = line / n, i2 = line % n;
+                const double* d = dirs + 3 * r;
+                const double ph = omega * h * (d[0] * (i1 + 1) + d[1] * (i2 + 1) + d[2] * (j + 1));
+                double sn, cs;
+                sincos(ph, &sn, &cs);
+                if (uI) uI[r * N + e] = mk(cs, sn);
+                v = m[e] * mk(cs, sn);
+            }
+        }
+        A[j] = v;
+    }
+    __syncthreads();
+    double2* res = fft_line<false>(A, B, L, lg, tw, t, nt);
+    double2* out = buf + ((long long)r * lines + line) * L;
+    for (int j = t; j < L; j += nt) out[j] = res[j];
+}
+
+// Inverse pass over contiguous x3 lines, n kept, fused epilogue.  grid (n^2, R).
+template <int OUT>
+__global__ void mv3_rows_inv(const double2* __restrict__ buf, const double2* __restrict__ x,
+                             const double* __restrict__ m, double2* __restrict__ y, const double2* __restrict__ tw,
+                             int n, int L, int lg) {
+    extern __shared__ double2 sm[];
+    double2* A = sm;
+    double2* B = sm + L;
+    const int line = blockIdx.x, r = blockIdx.y, t = threadIdx.x, nt = blockDim.x;
+    const long long N = (long long)n * n * n;
+    const double2* in = buf + ((long long)r * n * n + line) * L;
+    for (int j = t; j < L; j += nt) A[j] = in[j];
+    __syncthreads();
+    double2* res = fft_line<true>(A, B, L, lg, tw, t, nt);
+    for (int j = t; j < n; j += nt) {
+        const long long e = (long long)line * n + j;
+        const double2 v = res[j];
+        if (OUT == MV_OUT_A) y[r * N + e] = x[r * N + e] + v;
+        else if (OUT == MV_OUT_AT) y[r * N + e] = x[r * N + e] + m[e] * v;
+        else y[r * N + e] = mk(-v.x, -v.y);
+    }
+}
+
+enum { COL_FWD = 0, COL_CONV = 1, COL_INV = 2, COL_KHAT = 3 };
+
+// Strided-line pass.  The input is viewed as [r][p][row][q] with rows_in rows
+// (row stride Q); line (p, q) is FFT'd along row.  C consecutive q per CTA
+// (coalesced).  grid (Q / C, P, R), block C * nt.
+//  COL_FWD:  rows_in nonzero -> L rows of out[r][p][k][q]
+//  COL_CONV: in place (out == in): forward, * khat[q * L + k], inverse, keep rows_out rows
+//  COL_INV:  inverse of L rows, keep rows_out rows of out[r][p][row][q]
+//  COL_KHAT: forward, out[q * L + k] = scale * result (kernel transform, transposed)
+template <int MODE>
+__global__ void mv3_cols(const double2* __restrict__ in, double2* __restrict__ out, const double2* __restrict__ khat,
+                         const double2* __restrict__ tw, int P, int rows_in, int rows_out, long long Q, int L,
+                         int lg, int C, double scale) {
+    extern __shared__ double2 sm[];
+    double2* A = sm;
+    double2* B = sm + (size_t)C * L;
+    const long long q0 = (long long)blockIdx.x * C;
+    const int p = blockIdx.y, r = blockIdx.z;
+    const int nt = blockDim.x / C, g = threadIdx.x / nt, t = threadIdx.x % nt;
+    const double2* ib = in + ((long long)r * P + p) * rows_in * Q;
+    for (int idx = threadIdx.x; idx < L * C; idx += blockDim.x) {
+        const int row = idx / C, c = idx % C;
+        A[(size_t)c * L + row] = row < rows_in ? ib[(long long)row * Q + q0 + c] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+    double2* res = (MODE == COL_INV) ? fft_line<true>(A + (size_t)g * L, B + (size_t)g * L, L, lg, tw, t, nt)
+                                     : fft_line<false>(A + (size_t)g * L, B + (size_t)g * L, L, lg, tw, t, nt);
+    const long long q = q0 + g;
+    if (MODE == COL_KHAT) {
+        for (int k = t; k < L; k += nt) out[q * L + k] = scale * res[k];
+        return;
+    }
+    if (MODE == COL_CONV) {
+        const double2* kh = khat + q * L;
+        for (int k = t; k < L; k += nt) res[k] = res[k] * __ldg(&kh[k]);
+        __syncthreads();
+        double2* other = (res == A + (size_t)g * L) ? B + (size_t)g * L : A + (size_t)g * L;
+        res = fft_line<true>(res, other, L, lg, tw, t, nt);
+    }
+    // every group's result sits in the same half (A or B)
+    const double2* base = (res == A + (size_t)g * L) ? A : B;
+    const int rows_o = (MODE == COL_FWD) ? L : rows_out;
+    const int rows_tot = (MODE == COL_FWD) ? L : rows_out;
+    double2* ob = out + ((long long)r * P + p) * rows_tot * Q;
+    for (int idx = threadIdx.x; idx < rows_o * C; idx += blockDim.x) {
+        const int row = idx / C, c = idx % C;
+        ob[(long long)row * Q + q0 + c] = base[(size_t)c * L + row];
+    }
+}
+
+// ---------------------------------------------------------------- PML stencils (Eq. gamma in 3D)
+
+__device__ __forceinline__ double sigma_phys3(int q, int n, int b, double Cw) {
+    if (q <= -1) { const double t = (q + 1.0) / b; return -Cw * t * t; }
+    if (q >= n + 2) { const double t = (q - n - 2.0) / b; return Cw * t * t; }
+    return 0.0;
+}
+__device__ __forceinline__ int pml_class3(int q, int n, int b) {
+    if (q <= -1) return q + b + 1;
+    if (q >= n + 2) return b + 1 + (q - n - 2);
+    return 0;
+}
+__device__ __forceinline__ int class_index3(int cl, int n, int b) {
+    if (cl == 0) return 0;
+    if (cl <= b) return cl - b - 1;
+    return n + 2 + (cl - b - 1);
+}
+
+constexpr int kGamWarps = 4;
+struct GamSmem {
+    double2 F[27][26];
+    double2 E[3][3][3][2];   // [axis][d+1][scale][sign]
+    double vn2[26];
+    double2 q[27];
+};
+
+// One warp computes one stencil.  sig[axis][0..2] = sigma at offsets -1, 0, +1;
+// w = local frequency.  F[o][r] = exp(i w r.(dp_o + i dsigma_o)) over the 26
+// normalised directions r of {-1,0,1}^3 minus 0 (columns in lexicographic
+// order); the exponential factors per axis, E(d, v) = exp(i w v (d h + i
+// dsigma_d)) with v = +-1/sqrt(nnz(r)), and E(d, -v) has the conjugate phase
+// and the reciprocal modulus of E(d, v).  The null vector of F^T is the last
+// column of the unitary factor of a Householder QR of F (lane = column in the
+// reflector updates).  out[o] = conj(gamma_o), unit norm, centre real positive;
+// o = (d1+1)*9 + (d2+1)*3 + (d3+1).
+__device__ void gamma3_warp(const double sig[3][3], double w, double h, GamSmem& S, double2* out) {
+    const int lane = threadIdx.x & 31;
+    if (lane < 27) {
+        const int ax = lane / 9, d = (lane / 3) % 3 - 1, sc = lane % 3;
+        const double v = sc == 0 ? 1.0 : (sc == 1 ? 0.70710678118654752440 : 0.57735026918962576451);
+        const double re = d * h, im = sig[ax][d + 1] - sig[ax][1];
+        double sn, cs;
+        sincos(w * v * re, &sn, &cs);
+        const double mag = exp(-w * v * im);
+        S.E[ax][d + 1][sc][0] = mk(mag * cs, mag * sn);
+        S.E[ax][d + 1][sc][1] = mk(cs / mag, -sn / mag);
+    }
+    __syncwarp();
+    for (int e = lane; e < 27 * 26; e += 32) {
+        const int o = e / 26, col = e % 26;
+        const int rr = col < 13 ? col : col + 1;     // skip the zero direction
+        const int r[3] = {rr / 9 - 1, (rr / 3) % 3 - 1, rr % 3 - 1};
+        const int nnz = (r[0] != 0) + (r[1] != 0) + (r[2] != 0);
+        const int dd[3] = {o / 9 - 1, (o / 3) % 3 - 1, o % 3 - 1};
+        double2 f = mk(1.0, 0.0);
+        for (int ax = 0; ax < 3; ++ax)
+            if (r[ax] != 0) f = f * S.E[ax][dd[ax] + 1][nnz - 1][r[ax] < 0];
+        S.F[o][col] = f;
+    }
+    __syncwarp();
+    for (int k = 0; k < 26; ++k) {
+        double2 x = lane >= k && lane < 27 ? S.F[lane][k] : mk(0.0, 0.0);
+        double nx = cabs2(x);
+        for (int o = 16; o > 0; o >>= 1) nx += __shfl_xor_sync(0xffffffffu, nx, o);
+        nx = sqrt(nx);
+        const double2 fkk = S.F[k][k];
+        const double afk = sqrt(cabs2(fkk));
+        const double2 ph = afk > 0 ? mk(fkk.x / afk, fkk.y / afk) : mk(1.0, 0.0);
+        __syncwarp();
+        if (lane == 0) S.F[k][k] = fkk - mk(-ph.x * nx, -ph.y * nx);   // v = x - alpha e_k
+        __syncwarp();
+        x = lane >= k && lane < 27 ? S.F[lane][k] : mk(0.0, 0.0);
+        double v2 = cabs2(x);
+        for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        if (lane == 0) S.vn2[k] = v2;
+        if (v2 > 0 && lane > k && lane < 26) {
+            double2 dot = mk(0.0, 0.0);
+            for (int i = k; i < 27; ++i) dot = cfma_conj(S.F[i][k], S.F[i][lane], dot);
+            const double2 sd = (2.0 / v2) * dot;
+            for (int i = k; i < 27; ++i) S.F[i][lane] = S.F[i][lane] - sd * S.F[i][k];
+        }
+        __syncwarp();
+    }
+    double2 q = lane == 26 ? mk(1.0, 0.0) : mk(0.0, 0.0);
+    for (int k = 25; k >= 0; --k) {
+        const double v2 = S.vn2[k];
+        if (v2 == 0) continue;
+        double2 t = lane >= k && lane < 27 ? S.F[lane][k] : mk(0.0, 0.0);
+        double2 dot = lane >= k && lane < 27 ? mk(t.x * q.x + t.y * q.y, t.x * q.y - t.y * q.x) : mk(0.0, 0.0);
+        for (int o = 16; o > 0; o >>= 1) {
+            dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
+            dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
+        }
+        if (lane >= k && lane < 27) q = q - ((2.0 / v2) * dot) * t;
+    }
+    double nq = lane < 27 ? cabs2(q) : 0.0;
+    for (int o = 16; o > 0; o >>= 1) nq += __shfl_xor_sync(0xffffffffu, nq, o);
+    nq = sqrt(nq);
+    const double2 qc = mk(__shfl_sync(0xffffffffu, q.x, 13), __shfl_sync(0xffffffffu, q.y, 13));
+    const double ac = sqrt(cabs2(qc));
+    const double2 ph = mk(qc.x / ac, -qc.y / ac);
+    if (lane < 27) {
+        double2 g = (1.0 / nq) * (q * ph);
+        if (lane == 13) g = mk(ac / nq, 0.0);
+        out[lane] = conjc(g);
+    }
+    __syncwarp();
+}
+
+// Physical PML stencils: one per (class x1, class x2, class x3), global omega.
+__global__ void __launch_bounds__(32 * kGamWarps) gamma3_phys_kernel(double2* out, int n, int b, double Cw,
+                                                                      double omega, double h) {
+    __shared__ GamSmem S[kGamWarps];
+    const int nc = 2 * b + 1;
+    const int wid = threadIdx.x / 32;
+    const int e = blockIdx.x * kGamWarps + wid;
+    if (e >= nc * nc * nc) return;
+    const int c1 = e / (nc * nc), c2 = (e / nc) % nc, c3 = e % nc;
+    if (c1 == 0 && c2 == 0 && c3 == 0) {
+        if ((threadIdx.x & 31) < 27) out[(size_t)e * 27 + (threadIdx.x & 31)] = mk(0.0, 0.0);
+        return;
+    }
+    double sig[3][3];
+    const int q[3] = {class_index3(c1, n, b), class_index3(c2, n, b), class_index3(c3, n, b)};
+    for (int a = 0; a < 3; ++a)
+        for (int t = 0; t < 3; ++t) sig[a][t] = sigma_phys3(q[a] - 1 + t, n, b, Cw);
+    gamma3_warp(sig, omega, h, S[wid], out + (size_t)e * 27);
+}
+
+// Moving-PML stencils: per (sample k, auxiliary layer t = 1..b_aux, class x2,
+// class x3); along x1 the left profile of width b_aux translated so that D_i's
+// first layer plays the role of index 0; local frequency sqrt(s_k).
+__global__ void __launch_bounds__(32 * kGamWarps) gamma3_aux_kernel(double2* out, int n, int b, int baux, int ns,
+                                                                     double s_lo, double s_hi, double Cw, double h) {
+    __shared__ GamSmem S[kGamWarps];
+    const int nc = 2 * b + 1;
+    const int wid = threadIdx.x / 32;
+    const long long e = (long long)blockIdx.x * kGamWarps + wid;
+    const long long tot = (long long)ns * baux * nc * nc;
+    if (e >= tot) return;
+    const int c3 = (int)(e % nc), c2 = (int)((e / nc) % nc);
+    const int t = (int)((e / ((long long)nc * nc)) % baux) + 1;
+    const int k = (int)(e / ((long long)nc * nc * baux));
+    const double sk = (ns == 1) ? s_lo : (k == ns - 1 ? s_hi : s_lo + k * ((s_hi - s_lo) / (ns - 1)));
+    double sig[3][3];
+    const int q2 = class_index3(c2, n, b), q3 = class_index3(c3, n, b);
+    for (int u = 0; u < 3; ++u) {
+        const int q1 = -t - 1 + u;
+        double v = 0;
+        if (q1 <= -1) { const double tt = (q1 + 1.0) / baux; v = -Cw * tt * tt; }
+        sig[0][u] = v;
+        sig[1][u] = sigma_phys3(q2 - 1 + u, n, b, Cw);
+        sig[2][u] = sigma_phys3(q3 - 1 + u, n, b, Cw);
+    }
+    gamma3_warp(sig, sqrt(sk), h, S[wid], out + (size_t)e * 27);
+}
+
+// ---------------------------------------------------------------- assembly, Q, extraction
+
+struct Stencil27 {
+    double2 a_conj[27];
+    double2 b_conj[27];
+};
+
+__device__ __forceinline__ double m3_at(const double* m, int n, int i1, int i2, int i3) {
+    return (i1 >= 1 && i1 <= n && i2 >= 1 && i2 <= n && i3 >= 1 && i3 <= n)
+               ? m[((size_t)(i1 - 1) * n + (i2 - 1)) * n + (i3 - 1)]
+               : 0.0;
+}
+
+// Row coefficients of every slab subproblem.  grid (blocks, n_slabs); thread
+// per row (k, a, c).  Layout in the file comment.
+__global__ void assemble3_kernel(const Slab3* __restrict__ slabs, const double* __restrict__ m,
+                                 const double2* __restrict__ gphys, const double2* __restrict__ gaux, Stencil27 st,
+                                 double2* __restrict__ coef, int n, int b, int baux, int n_tot, int ns, double s_lo,
+                                 double s_hi, double omega) {
+    const Slab3 sd = slabs[blockIdx.y];
+    const long long rows = (long long)n_tot * sd.M;
+    const int nc = 2 * b + 1;
+    const double w2 = omega * omega;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < rows;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / sd.M), qr = (int)(e % sd.M);
+        const int a = qr / n_tot, c = qr % n_tot;
+        const int x1 = sd.s - sd.na + a, i2 = k - b, i3 = c - b;
+        double2 row[27];
+        if (a < sd.na) {
+            const int t = sd.na - a;
+            const double v = w2 * (1.0 - m3_at(m, n, x1, i2, i3));
+            int kk = 0;
+            if (ns > 1) {
+                const double x = (v - s_lo) / ((s_hi - s_lo) / (ns - 1));
+                kk = (int)ceil(x - 0.5);   // nearest sample, ties to the lower one
+                kk = kk < 0 ? 0 : (kk > ns - 1 ? ns - 1 : kk);
+            }
+            const double2* g =
+                gaux + ((((size_t)kk * baux + (t - 1)) * nc + pml_class3(i2, n, b)) * nc + pml_class3(i3, n, b)) * 27;
+            for (int o = 0; o < 27; ++o) row[o] = g[o];
+        } else if (x1 >= 0 && x1 <= n + 1 && i2 >= 0 && i2 <= n + 1 && i3 >= 0 && i3 <= n + 1) {
+            for (int o = 0; o < 27; ++o) {
+                const double mm = m3_at(m, n, x1 + o / 9 - 1, i2 + (o / 3) % 3 - 1, i3 + o % 3 - 1);
+                row[o] = st.a_conj[o] + (w2 * mm) * st.b_conj[o];
+            }
+        } else {
+            const double2* g =
+                gphys + (((size_t)pml_class3(x1, n, b) * nc + pml_class3(i2, n, b)) * nc + pml_class3(i3, n, b)) * 27;
+            for (int o = 0; o < 27; ++o) row[o] = g[o];
+        }
+        double2* out = coef + sd.cf_off;
+        for (int o = 0; o < 27; ++o) {
+            const int d1 = o / 9, d2 = (o / 3) % 3, d3 = o % 3;
+            out[(((long long)k * 3 + d2) * sd.M + qr) * 9 + d1 * 3 + d3] = row[o];
+        }
+    }
+}
+
+// f = Q r on the n_tot^3 grid: f_i = sum_o conj(alpha_o) r_{i+o} on I^h, zero on the PML.
+template <typename C>
+__global__ void sparsify3_kernel(const double2* __restrict__ r, C* __restrict__ f, Stencil27 st, int n, int b,
+                                 int n_tot) {
+    const long long tot = (long long)n_tot * n_tot * n_tot;
+    const long long N = (long long)n * n * n;
+    const int rr = blockIdx.y;
+    const double2* rv = r + rr * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i1 = (int)(e / ((long long)n_tot * n_tot)) - b, i2 = (int)((e / n_tot) % n_tot) - b,
+                  i3 = (int)(e % n_tot) - b;
+        double2 acc = mk(0.0, 0.0);
+        if (i1 >= 0 && i1 <= n + 1 && i2 >= 0 && i2 <= n + 1 && i3 >= 0 && i3 <= n + 1) {
+            for (int o = 0; o < 27; ++o) {
+                const int j1 = i1 + o / 9 - 1, j2 = i2 + (o / 3) % 3 - 1, j3 = i3 + o % 3 - 1;
+                if (j1 >= 1 && j1 <= n && j2 >= 1 && j2 <= n && j3 >= 1 && j3 <= n)
+                    acc = cfma(st.a_conj[o], rv[((long long)(j1 - 1) * n + (j2 - 1)) * n + (j3 - 1)], acc);
+            }
+        }
+        f[rr * tot + e] = to_c<C>(acc);
+    }
+}
+
+// y (on I) = the sweep solution restricted to I.
+template <typename C>
+__global__ void extract3_kernel(const C* __restrict__ ut, double2* __restrict__ y, int n, int b, int n_tot) {
+    const long long N = (long long)n * n * n, G = (long long)n_tot * n_tot * n_tot;
+    const int rr = blockIdx.y;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i1 = (int)(e / ((long long)n * n)), i2 = (int)((e / n) % n), i3 = (int)(e % n);
+        y[rr * N + e] = to_d(ut[rr * G + ((long long)(i1 + 1 + b) * n_tot + (i2 + 1 + b)) * n_tot + (i3 + 1 + b)]);
+    }
+}
+
+__global__ void cast3_kernel(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// ---------------------------------------------------------------- factorization (block LU along x2)
+
+// W = A_k: the 9-point (d1, d3) block of coefficients with d2 = 0.
+template <typename C>
+__global__ void f3_init_A(const Slab3* __restrict__ slabs, const C* __restrict__ coef, C* __restrict__ W, int n_tot,
+                          int k) {
+    const Slab3 sd = slabs[blockIdx.y];
+    const int M = sd.M;
+    const long long MM = (long long)M * M;
+    C* w = W + sd.w_off;
+    const C* cf = coef + sd.cf_off + ((long long)k * 3 + 1) * M * 9;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MM;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / M), j = (int)(e % M);
+        const int ai = i / n_tot, ci = i % n_tot, aj = j / n_tot, cj = j % n_tot;
+        const int d1 = aj - ai, d3 = cj - ci;
+        C v = czero<C>();
+        if (d1 >= -1 && d1 <= 1 && d3 >= -1 && d3 <= 1) v = cf[(long long)i * 9 + (d1 + 1) * 3 + (d3 + 1)];
+        w[e] = v;
+    }
+}
+
+// X = D_{k-1}^{-1} B_{k-1}: X[q][j] = sum_{d1,d3} Dinv[q][p] Bc[p][(d1,d3)], p = j - (d1, d3).
+template <typename C>
+__global__ void f3_schur_X(const Slab3* __restrict__ slabs, const C* __restrict__ coef, const C* __restrict__ fac,
+                           C* __restrict__ X, int n_tot, int k) {
+    const Slab3 sd = slabs[blockIdx.y];
+    const int M = sd.M, w = sd.w;
+    const long long MM = (long long)M * M;
+    const C* Dinv = fac + sd.fac_off + (long long)(k - 1) * MM;
+    const C* bc = coef + sd.cf_off + ((long long)(k - 1) * 3 + 2) * M * 9;
+    C* x = X + sd.w_off;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MM;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(e / M), j = (int)(e % M);
+        const int aj = j / n_tot, cj = j % n_tot;
+        C acc = czero<C>();
+        for (int d1 = -1; d1 <= 1; ++d1) {
+            const int ap = aj - d1;
+            if (ap < 0 || ap >= w) continue;
+            for (int d3 = -1; d3 <= 1; ++d3) {
+                const int cp = cj - d3;
+                if (cp < 0 || cp >= n_tot) continue;
+                const int p = ap * n_tot + cp;
+                acc = cfma(Dinv[(long long)q * M + p], bc[(long long)p * 9 + (d1 + 1) * 3 + (d3 + 1)], acc);
+            }
+        }
+        x[e] = acc;
+    }
+}
+
+// W = A_k - C_k X: W[i][j] = A_k[i][j] - sum_{d1,d3} Cc[i][(d1,d3)] X[i + (d1, d3)][j].
+template <typename C>
+__global__ void f3_schur_D(const Slab3* __restrict__ slabs, const C* __restrict__ coef, const C* __restrict__ X,
+                           C* __restrict__ W, int n_tot, int k) {
+    const Slab3 sd = slabs[blockIdx.y];
+    const int M = sd.M, w = sd.w;
+    const long long MM = (long long)M * M;
+    const C* cc = coef + sd.cf_off + ((long long)k * 3 + 0) * M * 9;
+    const C* ac = coef + sd.cf_off + ((long long)k * 3 + 1) * M * 9;
+    const C* x = X + sd.w_off;
+    C* wm = W + sd.w_off;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MM;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / M), j = (int)(e % M);
+        const int ai = i / n_tot, ci = i % n_tot, aj = j / n_tot, cj = j % n_tot;
+        C v = czero<C>();
+        if (aj - ai >= -1 && aj - ai <= 1 && cj - ci >= -1 && cj - ci <= 1)
+            v = ac[(long long)i * 9 + (aj - ai + 1) * 3 + (cj - ci + 1)];
+        for (int d1 = -1; d1 <= 1; ++d1) {
+            const int aq = ai + d1;
+            if (aq < 0 || aq >= w) continue;
+            for (int d3 = -1; d3 <= 1; ++d3) {
+                const int cq = ci + d3;
+                if (cq < 0 || cq >= n_tot) continue;
+                const C cv = cc[(long long)i * 9 + (d1 + 1) * 3 + (d3 + 1)];
+                const C xv = x[(long long)(aq * n_tot + cq) * M + j];
+                v = v - cv * xv;
+            }
+        }
+        wm[e] = v;
+    }
+}
+
+__global__ void f3_rowid_init(const Slab3* __restrict__ slabs, int* __restrict__ rowid, int Mmax) {
+    const int s = blockIdx.y;
+    const int M = slabs[s].M;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < M; r += gridDim.x * blockDim.x)
+        rowid[(long long)s * Mmax + r] = r;
+}
+
+// Gauss-Jordan elimination of the panel columns J = [j0, j0+nbp) of W (one CTA
+// per slab, the M x NB panel in shared memory).  Pivot j = j0 + jj is the
+// largest |W[r][j]| over rows r >= j (ties to the lower row); rows j and r are
+// swapped inside the panel (the rest of the rows later, by f3_swap_extract),
+// recorded in piv and in rowid.  After the panel the columns J hold the
+// eliminated values: rows R = [j0, j0+nbp) the inverse E of the pivot block,
+// the other rows -P_O E.
+template <typename C, int NB>
+__global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs, C* __restrict__ W, int* __restrict__ piv,
+                                                int* __restrict__ rowid, int j0, int Mmax, int* err) {
+    using R = decltype(C{}.x);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* P = reinterpret_cast<C*>(smraw);
+    __shared__ R red_v[32];
+    __shared__ int red_i[32];
+    __shared__ int s_piv;
+    const int slab = blockIdx.x;
+    const Slab3 sd = slabs[slab];
+    const int M = sd.M;
+    if (j0 >= M) return;
+    const int nbp = min(NB, M - j0);
+    C* w = W + sd.w_off;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < M * nbp; e += nt) {
+        const int r = e / nbp, q = e % nbp;
+        P[r * NB + q] = w[(long long)r * M + j0 + q];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < nbp; ++jj) {
+        const int j = j0 + jj;
+        R best = -1;
+        int bi = M;
+        for (int r = j + tid; r < M; r += nt) {
+            const R v = cabs2(P[r * NB + jj]);
+            if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+        __syncthreads();
+        if (tid < 32) {
+            best = tid < nt / 32 ? red_v[tid] : R(-1);
+            bi = tid < nt / 32 ? red_i[tid] : M;
+            for (int o = 16; o > 0; o >>= 1) {
+                const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+            }
+            if (tid == 0) {
+                if (!(best > 0) || !isfinite(best) || bi >= M) {
+                    atomicOr(err, LSS_DERR_SINGULAR);
+                    bi = j;
+                }
+                s_piv = bi;
+                piv[slab * NB + jj] = bi;
+                if (bi != j) {
+                    int* rid = rowid + (long long)slab * Mmax;
+                    const int t = rid[j];
+                    rid[j] = rid[bi];
+                    rid[bi] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != j && tid < nbp) {
+            const C t = P[j * NB + tid];
+            P[j * NB + tid] = P[pr * NB + tid];
+            P[pr * NB + tid] = t;
+        }
+        __syncthreads();
+        const C d = crecip(P[j * NB + jj]);
+        __syncthreads();
+        if (tid < nbp) P[j * NB + tid] = (tid == jj) ? d : P[j * NB + tid] * d;
+        __syncthreads();
+        for (int i = tid; i < M; i += nt) {
+            if (i == j) continue;
+            const C l = P[i * NB + jj];
+            for (int q = 0; q < nbp; ++q)
+                if (q != jj) P[i * NB + q] = P[i * NB + q] - l * P[j * NB + q];
+            P[i * NB + jj] = czero<C>() - l * d;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < M * nbp; e += nt) {
+        const int r = e / nbp, q = e % nbp;
+        w[(long long)r * M + j0 + q] = P[r * NB + q];
+    }
+}
+
+// Outside the panel columns: apply the panel's row swaps, move the pivot rows'
+// entries into T (T[jj][c], zero for c in J) and zero them in W.
+template <typename C, int NB>
+__global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__ W, const int* __restrict__ piv,
+                                C* __restrict__ T, int j0, int Tld) {
+    const int slab = blockIdx.y;
+    const Slab3 sd = slabs[slab];
+    const int M = sd.M;
+    if (j0 >= M) return;
+    const int nbp = min(NB, M - j0);
+    C* w = W + sd.w_off;
+    C* t = T + (long long)slab * NB * Tld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        if (c >= j0 && c < j0 + nbp) {
+            for (int jj = 0; jj < nbp; ++jj) t[(long long)jj * Tld + c] = czero<C>();
+            continue;
+        }
+        for (int jj = 0; jj < nbp; ++jj) {
+            const int r = piv[slab * NB + jj], j = j0 + jj;
+            if (r != j) {
+                const C a = w[(long long)j * M + c];
+                w[(long long)j * M + c] = w[(long long)r * M + c];
+                w[(long long)r * M + c] = a;
+            }
+        }
+        for (int jj = 0; jj < nbp; ++jj) {
+            t[(long long)jj * Tld + c] = w[(long long)(j0 + jj) * M + c];
+            w[(long long)(j0 + jj) * M + c] = czero<C>();
+        }
+    }
+}
+
+// W[i][c] += sum_kk W[i][j0+kk] T[kk][c] for c outside J (CUDA cores).
+// 64 x 64 output tiles, 256 threads, 4 x 4 entries each.  grid (tiles, slabs).
+template <typename C, int NB>
+__global__ void __launch_bounds__(256) f3_update_cc(const Slab3* __restrict__ slabs, C* __restrict__ W,
+                                                    const C* __restrict__ T, int j0, int Tld) {
+    __shared__ C As[64][NB];
+    __shared__ C Ts[NB][64];
+    const int slab = blockIdx.y;
+    const Slab3 sd = slabs[slab];
+    const int M = sd.M;
+    if (j0 >= M) return;
+    const int nbp = min(NB, M - j0);
+    const int tiles = (M + 63) / 64;
+    if ((int)blockIdx.x >= tiles * tiles) return;
+    const int i0 = (blockIdx.x / tiles) * 64, c0 = (blockIdx.x % tiles) * 64;
+    C* w = W + sd.w_off;
+    const C* t = T + (long long)slab * NB * Tld;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 64 * NB; e += 256) {
+        const int i = e / NB, q = e % NB;
+        As[i][q] = (i0 + i < M && q < nbp) ? w[(long long)(i0 + i) * M + j0 + q] : czero<C>();
+    }
+    for (int e = tid; e < NB * 64; e += 256) {
+        const int q = e / 64, c = e % 64;
+        Ts[q][c] = (c0 + c < M && q < nbp) ? t[(long long)q * Tld + c0 + c] : czero<C>();
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    C acc[4][4];
+    for (int u = 0; u < 4; ++u)
+        for (int v = 0; v < 4; ++v) acc[u][v] = czero<C>();
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        C a[4], b[4];
+        for (int u = 0; u < 4; ++u) a[u] = As[ty + 16 * u][q];
+        for (int v = 0; v < 4; ++v) b[v] = Ts[q][tx + 16 * v];
+        for (int u = 0; u < 4; ++u)
+            for (int v = 0; v < 4; ++v) acc[u][v] = cfma(a[u], b[v], acc[u][v]);
+    }
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty + 16 * u;
+        if (i >= M) continue;
+        for (int v = 0; v < 4; ++v) {
+            const int c = c0 + tx + 16 * v;
+            if (c >= M || (c >= j0 && c < j0 + nbp)) continue;
+            C* p = w + (long long)i * M + c;
+            *p = *p + acc[u][v];
+        }
+    }
+}
+
+// Dinv_k[i][rowid[r]] = W[i][r]: the column permutation undoing the row
+// interchanges, stored as factor block k.
+template <typename C>
+__global__ void f3_finalize(const Slab3* __restrict__ slabs, const C* __restrict__ W, const int* __restrict__ rowid,
+                            C* __restrict__ fac, int k, int Mmax) {
+    extern __shared__ int inv[];
+    const int slab = blockIdx.y;
+    const Slab3 sd = slabs[slab];
+    const int M = sd.M;
+    const int* rid = rowid + (long long)slab * Mmax;
+    for (int r = threadIdx.x; r < M; r += blockDim.x) inv[rid[r]] = r;
+    __syncthreads();
+    const long long MM = (long long)M * M;
+    const C* w = W + sd.w_off;
+    C* out = fac + sd.fac_off + (long long)k * MM;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < MM;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / M), j = (int)(e % M);
+        out[e] = w[(long long)i * M + inv[j]];
+    }
+}
+
+// ---------------------------------------------------------------- sweep (Algorithm 2, 3D slabs)
+
+struct Sweep3Args {
+    const Slab3* slabs;
+    int n_slabs, n_tot, b, Mmax;
+    const void* coef;
+    const void* fac;
+    const void* f;      // sparsified right-hand sides on the grid (R)
+    void* ut;           // sweep solution on the grid (R)
+    void* Y;            // block substitution vectors: [r][k][Mmax]
+    int R;              // right-hand sides in this launch (<= kSweepRB)
+    long long G;        // n_tot^3
+    int only;           // -1: whole sweep; else solve slab `only` alone (T~_i f_i, no couplings)
+    unsigned* bar;
+    int* err;
+};
+
+// One CTA per SM, persistent.  Each step of a slab solve: every CTA forms the
+// whole input t of the step in shared memory (the right-hand side of block k
+// and its coupling to the neighbouring block's solution), multiplies its
+// share of the rows of D_k^{-1} with it, and the grid synchronises.
+// Forward substitution y_k = D_k^{-1}(v_k - C_k y_{k-1}), backward
+// x_k = y_k - D_k^{-1} B_k x_{k+1}.  Slab i's right-hand side in the forward
+// sweep is f on D_i's layers minus H_{[i,i-1]} u_{i-1} on its first layer; in
+// the backward sweep it is H_{[i,i+1]} u_{i+1} on its last layer, and the
+// result is subtracted.
+template <typename C>
+__global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
+    using Rl = decltype(C{}.x);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* t = reinterpret_cast<C*>(smraw);                    // [R][Mmax]
+    C* part = t + (size_t)A.R * A.Mmax;                    // [warps][R]
+    const C* coef = (const C*)A.coef;
+    const C* fac = (const C*)A.fac;
+    const C* f = (const C*)A.f;
+    C* ut = (C*)A.ut;
+    C* Y = (C*)A.Y;
+    const int nt = A.n_tot, K = A.n_tot, G = gridDim.x, tid = threadIdx.x;
+    const int nwarps = blockDim.x / 32, wid = tid / 32, lane = tid & 31;
+    const int first = A.only >= 0 ? A.only : 0;
+    const int nl_total = A.only >= 0 ? 1 : A.n_slabs;
+    const int phases = (A.only >= 0 || A.n_slabs == 1) ? 1 : 2;
+    for (int phase = 0; phase < phases; ++phase) {
+        const int cnt = phase == 0 ? nl_total : A.n_slabs - 1;
+        for (int ii = 0; ii < cnt; ++ii) {
+            const int i = phase == 0 ? first + ii : A.n_slabs - 2 - ii;
+            const Slab3 sd = A.slabs[i];
+            const int M = sd.M, w = sd.w, na = sd.na;
+            const int X1s = sd.s + A.b;              // grid X1 of D_i's first layer
+            const C* cf = coef + sd.cf_off;
+            const int r0 = (int)((long long)blockIdx.x * M / G), r1 = (int)((long long)(blockIdx.x + 1) * M / G);
+            const int nrows = r1 - r0;
+            const int P = nrows > 0 ? max(1, nwarps / nrows) : 1;
+            for (int dir = 0; dir < 2; ++dir) {
+                const int ksteps = dir == 0 ? K : K - 1;
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    const int k = dir == 0 ? kk : K - 2 - kk;
+                    // ---- t = input of this step
+                    for (int e = tid; e < A.R * M; e += blockDim.x) {
+                        const int r = e / M, q = e % M;
+                        const int a = q / nt, c = q % nt;
+                        const C* Yr = Y + (long long)r * K * A.Mmax;
+                        C v = czero<C>();
+                        if (dir == 0) {
+                            if (phase == 0) {
+                                if (a >= na) v = f[r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c];
+                                if (A.only < 0 && i > 0 && a == na) {   // - H_{[i,i-1]} u_{i-1}
+                                    const C* rowc = cf + (long long)k * 3 * M * 9;
+                                    for (int d2 = -1; d2 <= 1; ++d2) {
+                                        const int k2 = k + d2;
+                                        if (k2 < 0 || k2 >= K) continue;
+                                        for (int d3 = -1; d3 <= 1; ++d3) {
+                                            const int c3 = c + d3;
+                                            if (c3 < 0 || c3 >= nt) continue;
+                                            const C cv = rowc[((long long)(d2 + 1) * M + q) * 9 + 0 * 3 + (d3 + 1)];
+                                            const C uv = ut[r * A.G + ((long long)(X1s - 1) * nt + k2) * nt + c3];
+                                            v = v - cv * uv;
+                                        }
+                                    }
+                                }
+                            } else if (a == w - 1) {                  // H_{[i,i+1]} u_{i+1}
+                                const C* rowc = cf + (long long)k * 3 * M * 9;
+                                const int X1n = X1s + sd.nl;          // first layer of slab i+1
+                                for (int d2 = -1; d2 <= 1; ++d2) {
+                                    const int k2 = k + d2;
+                                    if (k2 < 0 || k2 >= K) continue;
+                                    for (int d3 = -1; d3 <= 1; ++d3) {
+                                        const int c3 = c + d3;
+                                        if (c3 < 0 || c3 >= nt) continue;
+                                        const C cv = rowc[((long long)(d2 + 1) * M + q) * 9 + 2 * 3 + (d3 + 1)];
+                                        const C uv = ut[r * A.G + ((long long)X1n * nt + k2) * nt + c3];
+                                        v = v + cv * uv;
+                                    }
+                                }
+                            }
+                            if (k > 0) {                              // - C_k y_{k-1}
+                                const C* cc = cf + ((long long)k * 3 + 0) * M * 9 + (long long)q * 9;
+                                const C* yp = Yr + (long long)(k - 1) * A.Mmax;
+                                for (int d1 = -1; d1 <= 1; ++d1) {
+                                    const int a1 = a + d1;
+                                    if (a1 < 0 || a1 >= w) continue;
+                                    for (int d3 = -1; d3 <= 1; ++d3) {
+                                        const int c3 = c + d3;
+                                        if (c3 < 0 || c3 >= nt) continue;
+                                        v = v - cc[(d1 + 1) * 3 + (d3 + 1)] * yp[a1 * nt + c3];
+                                    }
+                                }
+                            }
+                        } else {                                      // B_k x_{k+1}
+                            const C* bc = cf + ((long long)k * 3 + 2) * M * 9 + (long long)q * 9;
+                            const C* xn = Yr + (long long)(k + 1) * A.Mmax;
+                            for (int d1 = -1; d1 <= 1; ++d1) {
+                                const int a1 = a + d1;
+                                if (a1 < 0 || a1 >= w) continue;
+                                for (int d3 = -1; d3 <= 1; ++d3) {
+                                    const int c3 = c + d3;
+                                    if (c3 < 0 || c3 >= nt) continue;
+                                    v = cfma(bc[(d1 + 1) * 3 + (d3 + 1)], xn[a1 * nt + c3], v);
+                                }
+                            }
+                        }
+                        t[(size_t)r * A.Mmax + q] = v;
+                    }
+                    __syncthreads();
+                    // ---- rows [r0, r1) of D_k^{-1} t
+                    const C* D = fac + sd.fac_off + (long long)k * M * M;
+                    if (nrows > 0 && wid < nrows * P) {
+                        const int lr = wid / P, pp = wid % P;
+                        const int row = r0 + lr;
+                        const int cb = (int)((long long)pp * M / P), ce = (int)((long long)(pp + 1) * M / P);
+                        C acc[kSweepRB];
+                        for (int r = 0; r < kSweepRB; ++r) acc[r] = czero<C>();
+                        const C* Drow = D + (long long)row * M;
+#pragma unroll 4
+                        for (int j = cb + lane; j < ce; j += 32) {
+                            const C dv = Drow[j];
+                            for (int r = 0; r < kSweepRB; ++r)
+                                if (r < A.R) acc[r] = cfma(dv, t[(size_t)r * A.Mmax + j], acc[r]);
+                        }
+                        for (int r = 0; r < kSweepRB; ++r) {
+                            if (r >= A.R) break;
+                            for (int o = 16; o > 0; o >>= 1) {
+                                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+                            }
+                            if (lane == 0) part[(size_t)wid * kSweepRB + r] = acc[r];
+                        }
+                    }
+                    __syncthreads();
+                    for (int e = tid; e < nrows * A.R; e += blockDim.x) {
+                        const int lr = e / A.R, r = e % A.R;
+                        const int row = r0 + lr;
+                        C s = czero<C>();
+                        for (int pp = 0; pp < P; ++pp) s = s + part[(size_t)(lr * P + pp) * kSweepRB + r];
+                        C* yk = Y + (long long)r * K * A.Mmax + (long long)k * A.Mmax + row;
+                        C val;
+                        if (dir == 0) val = s;
+                        else val = *yk - s;
+                        *yk = val;
+                        const bool final_x = dir == 1 || k == K - 1;
+                        const int a = row / nt, c = row % nt;
+                        if (final_x && a >= na) {
+                            C* up = ut + r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c;
+                            *up = (phase == 0) ? val : *up - val;
+                        }
+                    }
+                    grid_barrier(A.bar, G, A.err);
+                }
+            }
+        }
+    }
+}
+
+__global__ void f2_to_d2_kernel(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        b[e] = make_double2(a[e].x, a[e].y);
+}
+
+void extract_f2_to_d2(double2* dst, const float2* src, long long n, int num_sms, cudaStream_t s) {
+    f2_to_d2_kernel<<<2 * num_sms, 256, 0, s>>>(src, dst, n);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+void lss3_free(lss_ctx* c) {
+    Ctx3* d = c->d3;
+    if (!d) return;
+    void* ptrs[] = {d->d_slabs, d->khat, d->gam_phys, d->gam_aux, d->coef64, d->coef == d->coef64 ? nullptr : d->coef,
+                    d->fac, d->W, d->X, d->T, d->piv, d->rowid, d->f, d->ut, d->Y, d->mvA, d->mvB};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete d;
+    c->d3 = nullptr;
+}
+
+long long lss3_N(const lss_ctx* c) { return (long long)c->n * c->n * c->n; }
+
+namespace {
+
+int dalloc3(lss_ctx* c, void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return lss_fail(c, LSS_ERR_OOM, std::string("device allocation failed: ") + what);
+    }
+    return LSS_OK;
+}
+
+int configure3(lss_ctx* c) {
+    std::lock_guard<std::mutex> lock(lss_config_mutex());
+    int dev = 0;
+    cudaGetDevice(&dev);
+    static std::vector<int> done_dev;
+    for (int d : done_dev)
+        if (d == dev) return LSS_OK;
+    const int smax = 200 * 1024;
+    cudaError_t e = cudaSuccess;
+    e = cudaFuncSetAttribute(mv3_rows_fwd<MV_IN_MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_rows_fwd<MV_IN_U>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_rows_fwd<MV_IN_PLANEWAVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_rows_fwd<MV_IN_RAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_rows_inv<MV_OUT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_rows_inv<MV_OUT_AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_rows_inv<MV_OUT_NEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_cols<COL_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_cols<COL_CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_cols<COL_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (!e) e = cudaFuncSetAttribute(mv3_cols<COL_KHAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    const int psm = 210 * 1024;
+    if (!e) e = cudaFuncSetAttribute(f3_panel<double2, kNB64>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    if (!e) e = cudaFuncSetAttribute(f3_panel<float2, kNB32>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    if (!e) e = cudaFuncSetAttribute(sweep3_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    if (!e) e = cudaFuncSetAttribute(sweep3_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    if (e) return lss_check_cuda(c, e, "3D kernel attributes");
+    done_dev.push_back(dev);
+    return LSS_OK;
+}
+
+// Kernel transform: khat[(k2*L + k3)*L + k1] = omega^2/L^3 FFT3(kc)[k1][k2][k3].
+int build_kernel3(lss_ctx* c, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const int L = c->L, lg = c->lgL;
+    std::vector<double2> tw(L);
+    for (int k = 0; k < L; ++k) {
+        const long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)k / (long double)L;
+        tw[k] = make_double2((double)cosl(a), (double)sinl(a));
+    }
+    int rc = lss_check_cuda(c, cudaMemcpyAsync(c->tw, tw.data(), L * sizeof(double2), cudaMemcpyHostToDevice, s),
+                            "twiddles");
+    if (rc) return rc;
+    const cd k0 = lss_cell_integral_G(3, c->omega, c->h);
+    const long long L3 = (long long)L * L * L;
+    double2 *kc = nullptr, *tmp = nullptr;
+    rc = dalloc3(c, (void**)&kc, L3 * sizeof(double2), "k table");
+    if (!rc) rc = dalloc3(c, (void**)&tmp, L3 * sizeof(double2), "k table fft");
+    if (rc) { if (kc) cudaFree(kc); return rc; }
+    const int nt = line_threads3(L);
+    const size_t sh = 2 * (size_t)L * sizeof(double2);
+    const int C = col_group3(L);
+    {
+        ProfScope ps(c, s, LSS_PROF_SETUP, 4);
+        k3_table_circ<<<4 * c->num_sms, 256, 0, s>>>(kc, c->n, L, c->omega, c->h, make_double2(k0.real(), k0.imag()));
+        mv3_rows_fwd<MV_IN_RAW><<<dim3(L * L, 1), nt, sh, s>>>(kc, nullptr, nullptr, nullptr, tmp, c->tw, c->n, L * L,
+                                                              L, lg, c->omega, c->h);
+        // along x2: [j1][j2][k3] -> [j1][k2][k3]
+        mv3_cols<COL_FWD><<<dim3(L / C, L, 1), C * nt, 2 * (size_t)C * L * sizeof(double2), s>>>(
+            tmp, kc, nullptr, c->tw, L, L, L, L, L, lg, C, 1.0);
+        // along x1, stored transposed and scaled
+        const double scale = c->omega * c->omega / ((double)L * L * L);
+        mv3_cols<COL_KHAT><<<dim3((unsigned)((long long)L * L / C), 1, 1), C * nt, 2 * (size_t)C * L * sizeof(double2),
+                             s>>>(kc, d->khat, nullptr, c->tw, 1, L, L, (long long)L * L, L, lg, C, scale);
+    }
+    rc = lss_check_cuda(c, cudaGetLastError(), "3D kernel table");
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(kc);
+    cudaFree(tmp);
+    if (!rc) rc = lss_check_cuda(c, e, "3D kernel table");
+    return rc;
+}
+
+// alpha (smallest eigenvector of the 27 x 27 Gram matrix of K_{mu,mu^c}) and
+// beta^* = alpha^* K_{mu,mu} (Eq. alpha, Eq. beta in 3D).
+int build_interior3(lss_ctx* c, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const int n = c->n, S = 2 * n + 3;
+    const cd k0 = lss_cell_integral_G(3, c->omega, c->h);
+    const int nblk = 2 * c->num_sms, npair = 27 * 28 / 2;
+    double2 *kx = nullptr, *part = nullptr;
+    int rc = dalloc3(c, (void**)&kx, (size_t)S * S * S * sizeof(double2), "k ext 3D");
+    if (!rc) rc = dalloc3(c, (void**)&part, (size_t)npair * nblk * sizeof(double2), "gram 3D");
+    if (rc) { if (kx) cudaFree(kx); return rc; }
+    {
+        ProfScope ps(c, s, LSS_PROF_SETUP, 2);
+        k3_table_ext<<<4 * c->num_sms, 256, 0, s>>>(kx, n, c->omega, c->h, make_double2(k0.real(), k0.imag()));
+        gram3_partial<<<dim3(nblk, npair), 256, 0, s>>>(kx, n, part);
+    }
+    std::vector<double2> hp((size_t)npair * nblk), k5(125);
+    cudaError_t e = cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double2), cudaMemcpyDeviceToHost, s);
+    for (int u = 0; u < 5 && !e; ++u)
+        for (int v = 0; v < 5 && !e; ++v)
+            e = cudaMemcpyAsync(&k5[(u * 5 + v) * 5], kx + ((size_t)(n - 1 + u) * S + (n - 1 + v)) * S + (n - 1),
+                                5 * sizeof(double2), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    cudaFree(kx);
+    cudaFree(part);
+    if (e) return lss_check_cuda(c, e, "gram 3D");
+    std::vector<cd> Gm(27 * 27);
+    int pair = 0;
+    for (int a = 0; a < 27; ++a)
+        for (int b = a; b < 27; ++b, ++pair) {
+            cd acc = 0;
+            for (int q = 0; q < nblk; ++q) acc += cd(hp[(size_t)pair * nblk + q].x, hp[(size_t)pair * nblk + q].y);
+            Gm[a * 27 + b] = acc;
+            Gm[b * 27 + a] = std::conj(acc);
+        }
+    std::vector<double> A(54 * 54);
+    for (int a = 0; a < 27; ++a)
+        for (int b = 0; b < 27; ++b) {
+            A[a * 54 + b] = Gm[a * 27 + b].real();
+            A[a * 54 + 27 + b] = -Gm[a * 27 + b].imag();
+            A[(27 + a) * 54 + b] = Gm[a * 27 + b].imag();
+            A[(27 + a) * 54 + 27 + b] = Gm[a * 27 + b].real();
+        }
+    std::vector<double> ev, V;
+    lss_jacobi_eigen(A, 54, ev, V);
+    int imin = 0;
+    for (int i = 1; i < 54; ++i)
+        if (ev[i] < ev[imin]) imin = i;
+    cd al[27];
+    double nrm = 0;
+    for (int a = 0; a < 27; ++a) {
+        al[a] = cd(V[a * 54 + imin], V[(27 + a) * 54 + imin]);
+        nrm += std::norm(al[a]);
+    }
+    nrm = std::sqrt(nrm);
+    const cd ph = std::abs(al[13]) / al[13];
+    for (int a = 0; a < 27; ++a) al[a] = al[a] * ph / nrm;
+    al[13] = cd(std::abs(al[13]), 0.0);
+    for (int b = 0; b < 27; ++b) {
+        cd acc = 0;
+        for (int a = 0; a < 27; ++a) {
+            const int e1 = a / 9 - b / 9, e2 = (a / 3) % 3 - (b / 3) % 3, e3 = a % 3 - b % 3;
+            const double2 kab = k5[((e1 + 2) * 5 + (e2 + 2)) * 5 + (e3 + 2)];
+            acc += al[a] * std::conj(cd(kab.x, kab.y));   // beta_b = sum_a alpha_a conj(K_ab)
+        }
+        d->beta[b] = acc;
+    }
+    for (int a = 0; a < 27; ++a) d->alpha[a] = al[a];
+    return LSS_OK;
+}
+
+Stencil27 stencil_args(const Ctx3* d, double omega) {
+    (void)omega;
+    Stencil27 st;
+    for (int o = 0; o < 27; ++o) {
+        st.a_conj[o] = make_double2(d->alpha[o].real(), -d->alpha[o].imag());
+        st.b_conj[o] = make_double2(d->beta[o].real(), -d->beta[o].imag());
+    }
+    return st;
+}
+
+}  // namespace
+
+int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
+    Ctx3* d = new Ctx3();
+    c->d3 = d;
+    const int n = c->n, b = c->b, bs = c->slab.b_slab;
+    const int nl = (n + 2 + bs - 1) / bs;
+    c->n_slabs = nl;
+    long long cf = 0, fo = 0, wo = 0;
+    d->Mmax = 0;
+    for (int i = 0; i < nl; ++i) {
+        Slab3 sd{};
+        if (i == 0) {
+            sd.s = -b;
+            sd.nl = (nl == 1) ? c->n_tot : b + bs;
+            sd.na = 0;
+        } else {
+            sd.s = i * bs;
+            sd.nl = (i == nl - 1) ? (n + 2 - i * bs) + b : bs;
+            sd.na = c->b_aux;
+        }
+        sd.w = sd.na + sd.nl;
+        sd.M = sd.w * c->n_tot;
+        if (sd.M > kMaxBlock3)
+            return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D: a slab block (layers x n_tot) exceeds 1600 unknowns");
+        sd.cf_off = cf;
+        sd.fac_off = fo;
+        sd.w_off = wo;
+        cf += (long long)c->n_tot * 3 * sd.M * 9;
+        fo += (long long)c->n_tot * sd.M * sd.M;
+        wo += (long long)sd.M * sd.M;
+        d->Mmax = std::max(d->Mmax, sd.M);
+        d->slabs.push_back(sd);
+    }
+    d->coef_len = cf;
+    d->fac_len = fo;
+    d->w_len = wo;
+    const int nc = 2 * b + 1;
+    const size_t cs = c->csize();
+    const long long L3 = (long long)c->L * c->L * c->L;
+    const int NB = c->prec == LSS_FP64 ? kNB64 : kNB32;
+    int rc = LSS_OK;
+    rc = rc ? rc : dalloc3(c, (void**)&c->m, (size_t)lss3_N(c) * sizeof(double), "m");
+    rc = rc ? rc : dalloc3(c, (void**)&c->tw, (size_t)c->L * sizeof(double2), "twiddles");
+    rc = rc ? rc : dalloc3(c, (void**)&d->khat, (size_t)L3 * sizeof(double2), "kernel transform");
+    rc = rc ? rc : dalloc3(c, (void**)&d->gam_phys, (size_t)nc * nc * nc * 27 * sizeof(double2), "gamma");
+    rc = rc ? rc : dalloc3(c, (void**)&d->gam_aux, (size_t)c->n_samples * c->b_aux * nc * nc * 27 * sizeof(double2),
+                           "gamma aux");
+    rc = rc ? rc : dalloc3(c, (void**)&d->coef64, (size_t)cf * sizeof(double2), "coefficients");
+    if (!rc) {
+        if (c->prec == LSS_FP64) d->coef = d->coef64;
+        else rc = dalloc3(c, &d->coef, (size_t)cf * cs, "coefficients fp32");
+    }
+    rc = rc ? rc : dalloc3(c, &d->fac, (size_t)fo * cs, "slab factors");
+    rc = rc ? rc : dalloc3(c, &d->W, (size_t)wo * cs, "pivot blocks");
+    rc = rc ? rc : dalloc3(c, &d->X, (size_t)wo * cs, "Schur scratch");
+    rc = rc ? rc : dalloc3(c, &d->T, (size_t)nl * NB * d->Mmax * cs, "panel rows");
+    rc = rc ? rc : dalloc3(c, (void**)&d->piv, (size_t)nl * NB * sizeof(int), "pivots");
+    rc = rc ? rc : dalloc3(c, (void**)&d->rowid, (size_t)nl * d->Mmax * sizeof(int), "row ids");
+    rc = rc ? rc : dalloc3(c, (void**)&d->d_slabs, nl * sizeof(Slab3), "slabs");
+    rc = rc ? rc : dalloc3(c, (void**)&c->d_err, sizeof(int), "status");
+    rc = rc ? rc : dalloc3(c, (void**)&c->d_bar, 2 * sizeof(unsigned), "barrier");
+    if (rc) return rc;
+    cudaMemcpyAsync(d->d_slabs, d->slabs.data(), nl * sizeof(Slab3), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), s);
+    cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), s);
+    rc = configure3(c);
+    if (!rc) rc = build_kernel3(c, s);
+    if (!rc) rc = build_interior3(c, s);
+    if (!rc) {
+        ProfScope ps(c, s, LSS_PROF_SETUP, 1);
+        const int tot = nc * nc * nc;
+        gamma3_phys_kernel<<<(tot + kGamWarps - 1) / kGamWarps, 32 * kGamWarps, 0, s>>>(
+            d->gam_phys, n, b, c->pml.C / c->omega, c->omega, c->h);
+        rc = lss_check_cuda(c, cudaGetLastError(), "gamma 3D");
+    }
+    return rc;
+}
+
+// Medium-dependent part (after the sample range is set): moving-PML stencils,
+// slab coefficients (and their single-precision copy).
+int lss3_set_medium(lss_ctx* c, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const int n = c->n, b = c->b, nc = 2 * b + 1;
+    const long long tot = (long long)c->ns_eff * c->b_aux * nc * nc;
+    ProfScope ps(c, s, LSS_PROF_SETUP, c->prec == LSS_MIXED ? 3 : 2);
+    gamma3_aux_kernel<<<(unsigned)((tot + kGamWarps - 1) / kGamWarps), 32 * kGamWarps, 0, s>>>(
+        d->gam_aux, n, b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi, c->pml.C / c->omega, c->h);
+    const Stencil27 st = stencil_args(d, c->omega);
+    assemble3_kernel<<<dim3(2 * c->num_sms, c->n_slabs), 256, 0, s>>>(d->d_slabs, c->m, d->gam_phys, d->gam_aux, st,
+                                                                     d->coef64, n, b, c->b_aux, c->n_tot, c->ns_eff,
+                                                                     c->s_lo, c->s_hi, c->omega);
+    if (c->prec == LSS_MIXED)
+        cast3_kernel<<<4 * c->num_sms, 256, 0, s>>>(d->coef64, (float2*)d->coef, d->coef_len);
+    return lss_check_cuda(c, cudaGetLastError(), "3D set_medium");
+}
+
+namespace {
+
+template <typename C, int NB>
+int factor3_t(lss_ctx* c, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const int K = c->n_tot, nl = c->n_slabs, Mmax = d->Mmax;
+    const C* coef = (const C*)d->coef;
+    C* fac = (C*)d->fac;
+    C* W = (C*)d->W;
+    C* X = (C*)d->X;
+    C* T = (C*)d->T;
+    const long long MM = (long long)Mmax * Mmax;
+    const int ew_blocks = (int)std::min<long long>(8LL * c->num_sms / std::max(1, nl) + 1, (MM + 255) / 256);
+    const int tiles = (Mmax + 63) / 64;
+    const int npanel = (Mmax + NB - 1) / NB;
+    const size_t psm = (size_t)Mmax * NB * sizeof(C);
+    bool use_tc = false;
+    if constexpr (std::is_same<C, float2>::value) use_tc = lss3_use_tc();
+    ProfScope ps(c, s, LSS_PROF_FACTOR, 0);
+    for (int k = 0; k < K; ++k) {
+        if (k == 0) {
+            f3_init_A<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(d->d_slabs, coef, W, c->n_tot, 0);
+            c->launches[LSS_PROF_FACTOR] += 1;
+        } else {
+            f3_schur_X<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(d->d_slabs, coef, fac, X, c->n_tot, k);
+            f3_schur_D<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(d->d_slabs, coef, X, W, c->n_tot, k);
+            c->launches[LSS_PROF_FACTOR] += 2;
+        }
+        f3_rowid_init<<<dim3(1, nl), 256, 0, s>>>(d->d_slabs, d->rowid, Mmax);
+        for (int p = 0; p < npanel; ++p) {
+            const int j0 = p * NB;
+            f3_panel<C, NB><<<nl, 512, psm, s>>>(d->d_slabs, W, d->piv, d->rowid, j0, Mmax, c->d_err);
+            f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, d->piv, T, j0, Mmax);
+            if constexpr (std::is_same<C, float2>::value) {
+                if (use_tc) {
+                    const int rc = lss3_update_tc(c, W, T, j0, s);
+                    if (rc) return rc;
+                    continue;
+                }
+            }
+            f3_update_cc<C, NB><<<dim3(tiles * tiles, nl), 256, 0, s>>>(d->d_slabs, W, T, j0, Mmax);
+        }
+        f3_finalize<C><<<dim3(ew_blocks, nl), 256, Mmax * sizeof(int), s>>>(d->d_slabs, W, d->rowid, fac, k, Mmax);
+        c->launches[LSS_PROF_FACTOR] += 2 + 3LL * npanel;
+        const int rc = lss_check_cuda(c, cudaGetLastError(), "3D factorization launch");
+        if (rc) return rc;
+    }
+    return LSS_OK;
+}
+
+template <typename C>
+int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const double2* fin, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const long long G = (long long)c->n_tot * c->n_tot * c->n_tot;
+    const size_t cs = sizeof(C);
+    const int RB = std::min(R, kSweepRB);
+    int rc = lss_grow(c, &d->f, &d->f_cap, (size_t)RB * G * cs);
+    if (!rc) rc = lss_grow(c, &d->ut, &d->ut_cap, (size_t)RB * G * cs);
+    if (!rc) rc = lss_grow(c, &d->Y, &d->Y_cap, (size_t)RB * c->n_tot * d->Mmax * cs);
+    if (rc) return rc;
+    const Stencil27 st = stencil_args(d, c->omega);
+    const long long N = lss3_N(c);
+    const size_t smem = ((size_t)RB * d->Mmax + (size_t)(kSweepThreads / 32) * kSweepRB) * cs;
+    int grid = c->num_sms;
+    {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep3_kernel<C>, kSweepThreads, smem);
+        if (per < 1) return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D sweep kernel does not fit on an SM");
+    }
+    for (int r0 = 0; r0 < R; r0 += RB) {
+        const int Rc = std::min(RB, R - r0);
+        {
+            ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+            if (fin) {   // lss_apply_slab: the slab's layers given directly
+                cudaMemsetAsync(d->f, 0, (size_t)Rc * G * cs, s);
+            } else {
+                sparsify3_kernel<C><<<dim3(2 * c->num_sms, Rc), 256, 0, s>>>(r + r0 * N, (C*)d->f, st, c->n, c->b,
+                                                                            c->n_tot);
+            }
+        }
+        if (fin) {
+            // v (nl layers x n_tot^2 per right-hand side) into the slab's layers of f
+            const Slab3& sd = d->slabs[only];
+            const long long per = (long long)sd.nl * c->n_tot * c->n_tot;
+            const long long X1 = sd.s + c->b;
+            for (int q = 0; q < Rc; ++q) {
+                if (sizeof(C) == sizeof(double2)) {
+                    cudaMemcpyAsync((C*)d->f + q * G + X1 * c->n_tot * c->n_tot, fin + (r0 + q) * per,
+                                    per * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+                } else {
+                    cast3_kernel<<<2 * c->num_sms, 256, 0, s>>>(fin + (r0 + q) * per,
+                                                               (float2*)d->f + q * G + X1 * c->n_tot * c->n_tot, per);
+                }
+            }
+        }
+        cudaMemsetAsync(d->ut, 0, (size_t)Rc * G * cs, s);
+        Sweep3Args a{};
+        a.slabs = d->d_slabs;
+        a.n_slabs = c->n_slabs;
+        a.n_tot = c->n_tot;
+        a.b = c->b;
+        a.Mmax = d->Mmax;
+        a.coef = d->coef;
+        a.fac = d->fac;
+        a.f = d->f;
+        a.ut = d->ut;
+        a.Y = d->Y;
+        a.R = Rc;
+        a.G = G;
+        a.only = only;
+        a.bar = c->d_bar;
+        a.err = c->d_err;
+        void* args[] = {&a};
+        {
+            ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
+            cudaError_t e = cudaLaunchCooperativeKernel((const void*)sweep3_kernel<C>, dim3(grid), dim3(kSweepThreads),
+                                                        args, smem, s);
+            if (e) return lss_check_cuda(c, e, "3D sweep launch");
+        }
+        if (!fin) {
+            ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+            extract3_kernel<C><<<dim3(2 * c->num_sms, Rc), 256, 0, s>>>((const C*)d->ut, y + r0 * N, c->n, c->b,
+                                                                        c->n_tot);
+        } else {
+            const Slab3& sd = d->slabs[only];
+            const long long per = (long long)sd.nl * c->n_tot * c->n_tot;
+            const long long X1 = sd.s + c->b;
+            for (int q = 0; q < Rc; ++q) {
+                if (sizeof(C) == sizeof(double2)) {
+                    cudaMemcpyAsync(y + (r0 + q) * per, (C*)d->ut + q * G + X1 * c->n_tot * c->n_tot,
+                                    per * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+                } else {
+                    extract_f2_to_d2(y + (r0 + q) * per, (const float2*)d->ut + q * G + X1 * c->n_tot * c->n_tot,
+                                     per, c->num_sms, s);
+                }
+            }
+        }
+    }
+    return lss_check_cuda(c, cudaGetLastError(), "3D sweep");
+}
+
+}  // namespace
+
+int lss3_factor(lss_ctx* c, cudaStream_t s) {
+    if (c->prec == LSS_FP64) return factor3_t<double2, kNB64>(c, s);
+    return factor3_t<float2, kNB32>(c, s);
+}
+
+int lss3_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
+    if (c->prec == LSS_FP64) return sweep3_t<double2>(c, r, y, R, -1, nullptr, s);
+    return sweep3_t<float2>(c, r, y, R, -1, nullptr, s);
+}
+
+int lss3_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
+    if (c->prec == LSS_FP64) return sweep3_t<double2>(c, nullptr, w, R, slab, v, s);
+    return sweep3_t<float2>(c, nullptr, w, R, slab, v, s);
+}
+
+int lss3_matvec(lss_ctx* c, const double2* x, double2* y, int R, int in_mode, int out_mode, const double* dirs_dev,
+                double2* uI, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const int n = c->n, L = c->L, lg = c->lgL;
+    int rc = lss_grow(c, (void**)&d->mvA, &d->mvA_cap, (size_t)n * n * L * R * sizeof(double2));
+    if (!rc) rc = lss_grow(c, (void**)&d->mvB, &d->mvB_cap, (size_t)n * L * L * R * sizeof(double2));
+    if (rc) return rc;
+    const int nt = line_threads3(L);
+    const size_t sh = 2 * (size_t)L * sizeof(double2);
+    const int C = col_group3(L);
+    const size_t sh2 = 2 * (size_t)C * L * sizeof(double2);
+    dim3 g1(n * n, R);
+    ProfScope ps(c, s, LSS_PROF_MATVEC, 5);
+    switch (in_mode) {
+        case MV_IN_MU:
+            mv3_rows_fwd<MV_IN_MU><<<g1, nt, sh, s>>>(x, c->m, nullptr, nullptr, d->mvA, c->tw, n, n * n, L, lg,
+                                                    c->omega, c->h);
+            break;
+        case MV_IN_U:
+            mv3_rows_fwd<MV_IN_U><<<g1, nt, sh, s>>>(x, c->m, nullptr, nullptr, d->mvA, c->tw, n, n * n, L, lg,
+                                                   c->omega, c->h);
+            break;
+        case MV_IN_PLANEWAVE:
+            mv3_rows_fwd<MV_IN_PLANEWAVE><<<g1, nt, sh, s>>>(x, c->m, dirs_dev, uI, d->mvA, c->tw, n, n * n, L, lg,
+                                                           c->omega, c->h);
+            break;
+        default:
+            return lss_fail(c, LSS_ERR_ARG, "matvec: bad input mode");
+    }
+    // x2: A[r][i1][i2][k3] (n rows) -> B[r][i1][k2][k3] (L rows)
+    mv3_cols<COL_FWD><<<dim3(L / C, n, R), C * nt, sh2, s>>>(d->mvA, d->mvB, nullptr, c->tw, n, n, L, L, L, lg, C, 1.0);
+    // x1: B[r][i1][(k2,k3)] in place, n rows kept
+    mv3_cols<COL_CONV><<<dim3((unsigned)((long long)L * L / C), 1, R), C * nt, sh2, s>>>(
+        d->mvB, d->mvB, d->khat, c->tw, 1, n, n, (long long)L * L, L, lg, C, 1.0);
+    // x2 inverse: B[r][i1][k2][k3] (L rows) -> A[r][i1][i2][k3] (n rows)
+    mv3_cols<COL_INV><<<dim3(L / C, n, R), C * nt, sh2, s>>>(d->mvB, d->mvA, nullptr, c->tw, n, L, n, L, L, lg, C, 1.0);
+    switch (out_mode) {
+        case MV_OUT_A:
+            mv3_rows_inv<MV_OUT_A><<<g1, nt, sh, s>>>(d->mvA, x, c->m, y, c->tw, n, L, lg);
+            break;
+        case MV_OUT_AT:
+            mv3_rows_inv<MV_OUT_AT><<<g1, nt, sh, s>>>(d->mvA, x, c->m, y, c->tw, n, L, lg);
+            break;
+        default:
+            mv3_rows_inv<MV_OUT_NEG><<<g1, nt, sh, s>>>(d->mvA, x, c->m, y, c->tw, n, L, lg);
+            break;
+    }
+    return lss_check_cuda(c, cudaGetLastError(), "3D matvec launch");
+}
+
+int lss3_get_stencils(const lss_ctx* c, double* alpha, double* beta) {
+    const Ctx3* d = c->d3;
+    for (int o = 0; o < 27; ++o) {
+        alpha[2 * o] = d->alpha[o].real();
+        alpha[2 * o + 1] = d->alpha[o].imag();
+        beta[2 * o] = d->beta[o].real();
+        beta[2 * o + 1] = d->beta[o].imag();
+    }
+    return LSS_OK;
+}

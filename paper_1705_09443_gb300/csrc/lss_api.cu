@@ -8,6 +8,7 @@
 
 #include "lss_common.cuh"
 #include "lss_ctx.h"
+#include "lss3d.h"
 
 namespace {
 
@@ -21,6 +22,7 @@ __global__ void cast_c128_c64(const double2* __restrict__ a, float2* __restrict_
 void free_ctx(lss_ctx* c) {
     if (!c) return;
     if (!c->inst.empty() || c->fork_ev) lss_batch_free(c);
+    if (c->d3) lss3_free(c);
     for (auto& g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);   // refused captures are kept as null entries
     for (auto st : c->aux_stream) cudaStreamDestroy(st);
@@ -133,9 +135,8 @@ int lss_grow(lss_ctx* c, void** p, size_t* cap, size_t bytes) {
 // [omega^2(1 - max m), omega^2(1 - min m)] (m on I and 0, Sec. 2.3), the
 // moving-PML stencils per sample and the slab subproblems.
 int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s) {
-    const int n = c->n;
     c->factored = false;
-    std::vector<double> mh((size_t)n * n);
+    std::vector<double> mh((size_t)c->npts());
     cudaError_t e = cudaMemcpyAsync(c->m, m_dev, mh.size() * sizeof(double), cudaMemcpyDeviceToDevice, s);
     if (!e) e = cudaMemcpyAsync(mh.data(), m_dev, mh.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);
@@ -149,6 +150,7 @@ int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s) {
     c->ns_eff = (mmax == mmin) ? 1 : c->n_samples;
     c->s_lo = c->omega * c->omega * (1.0 - mmax);
     c->s_hi = c->omega * c->omega * (1.0 - mmin);
+    if (c->dim == 3) return lss3_set_medium(c, s);
     int rc = lss_build_gamma_aux(c, s);
     if (!rc) rc = lss_assemble_slabs(c, s);
     if (!rc && c->prec == LSS_MIXED) {
@@ -167,9 +169,11 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     if (!out) return lss_fail(nullptr, LSS_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!g || !m_dev || !pml || !slab) return lss_fail(nullptr, LSS_ERR_ARG, "NULL argument");
-    if (g->dim == 3) return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "3D grids are not supported by this build");
-    if (g->dim != 2) return lss_fail(nullptr, LSS_ERR_ARG, "dim must be 2");
-    if (g->n < 4 || g->n > 2048) return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "n must be in [4, 2048]");
+    if (g->dim != 2 && g->dim != 3) return lss_fail(nullptr, LSS_ERR_ARG, "dim must be 2 or 3");
+    if (g->dim == 2 && (g->n < 4 || g->n > 2048))
+        return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "n must be in [4, 2048]");
+    if (g->dim == 3 && (g->n < 3 || g->n > 128))
+        return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "3D: n must be in [3, 128]");
     if (!(omega > 0) || !std::isfinite(omega)) return lss_fail(nullptr, LSS_ERR_ARG, "omega must be positive");
     if (pml->b_pml < 1 || !(pml->C > 0)) return lss_fail(nullptr, LSS_ERR_ARG, "b_pml >= 1 and C > 0 required");
     if (slab->b_slab < 1 || slab->b_aux < 0 || slab->n_samples < 0)
@@ -178,7 +182,7 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     cudaStream_t s = (cudaStream_t)stream;
 
     lss_ctx* c = new lss_ctx();
-    c->dim = 2;
+    c->dim = g->dim;
     c->n = g->n;
     c->omega = omega;
     c->h = 1.0 / (g->n + 1);
@@ -196,6 +200,15 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     c->L = 8;
     c->lgL = 3;
     while (c->L < 2 * c->n - 1) { c->L <<= 1; ++c->lgL; }
+    if (c->dim == 3) {   // Sec. 3.1: the same construction on 3D slabs (lss3d.cu)
+        int rc = lss3_setup(c, m_dev, s);
+        if (!rc) rc = lss_set_medium_impl(c, m_dev, s);
+        if (!rc) rc = lss_check_cuda(c, cudaStreamSynchronize(s), "setup");
+        if (!rc) rc = lss_check_device_err(c, s);
+        if (rc) { std::string m = c->err; free_ctx(c); return lss_fail(nullptr, rc, m); }
+        *out = c;
+        return LSS_OK;
+    }
 
     // slabs along x1 (Sec. 2.3): first = left PML + b_slab layers, middle b_slab,
     // last = the remaining normal layers + right PML
@@ -351,7 +364,7 @@ int lss_factor(lss_ctx* c, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (is_batch(c)) return lss_batch_factor(c, s);
     c->factored = false;
-    int rc = lss_factor_slabs(c, s);
+    int rc = c->dim == 3 ? lss3_factor(c, s) : lss_factor_slabs(c, s);
     if (!rc) rc = lss_check_cuda(c, cudaStreamSynchronize(s), "factor");
     if (!rc) rc = lss_check_device_err(c, s);
     if (rc) return rc;
@@ -364,9 +377,9 @@ int lss_plane_wave_rhs(lss_ctx* c, const double* dirs_host, int R, void* g_dev, 
     if (!dirs_host || !g_dev || R < 1) return lss_fail(c, LSS_ERR_ARG, "plane_wave_rhs: bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
     if (is_batch(c)) return lss_batch_plane_wave_rhs(c, dirs_host, R, (double2*)g_dev, (double2*)uI_dev, s);
-    int rc = lss_grow(c, &c->dir_buf, &c->dir_cap, (size_t)R * 2 * sizeof(double));
+    int rc = lss_grow(c, &c->dir_buf, &c->dir_cap, (size_t)R * c->dim * sizeof(double));
     if (rc) return rc;
-    rc = lss_check_cuda(c, cudaMemcpyAsync(c->dir_buf, dirs_host, (size_t)R * 2 * sizeof(double),
+    rc = lss_check_cuda(c, cudaMemcpyAsync(c->dir_buf, dirs_host, (size_t)R * c->dim * sizeof(double),
                                            cudaMemcpyHostToDevice, s), "directions");
     if (rc) return rc;
     return lss_matvec(c, nullptr, (double2*)g_dev, R, MV_IN_PLANEWAVE, MV_OUT_NEG, (const double*)c->dir_buf,
@@ -386,6 +399,8 @@ int lss_apply_P(lss_ctx* c, const void* x, void* y, int R, int transpose, void* 
     if (!x || !y || R < 1) return lss_fail(c, LSS_ERR_ARG, "apply_P: bad arguments");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_P before lss_factor");
     if (is_batch(c)) return lss_batch_apply(c, 1, (const double2*)x, (double2*)y, R, transpose, (cudaStream_t)stream);
+    if (transpose && c->dim == 3)
+        return lss_fail(c, LSS_ERR_UNSUPPORTED, "apply_P: the transposed sweep is built for 2D grids only");
     if (transpose) return lss_sweep_t(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
     return lss_sweep(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
 }
@@ -407,6 +422,7 @@ int lss_adjoint_solve(lss_ctx* c, const void* rhs, void* mu, int R, const lss_gm
     if (o->restart < 1 || o->restart > 200 || !(o->tol > 0) || o->max_iter < 1)
         return lss_fail(c, LSS_ERR_ARG, "adjoint_solve: bad GMRES options");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "adjoint_solve before lss_factor");
+    if (c->dim == 3) return lss_fail(c, LSS_ERR_UNSUPPORTED, "adjoint_solve: 2D grids only");
     if (is_batch(c))
         return lss_batch_solve(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
     return lss_fgmres(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
@@ -416,6 +432,7 @@ int lss_medium_gradient(lss_ctx* c, const void* mu, const void* u, const double*
                         void* stream) {
     if (!c) return LSS_ERR_ARG;
     if (!mu || !u || !dirs_host || !grad || R < 1) return lss_fail(c, LSS_ERR_ARG, "medium_gradient: bad arguments");
+    if (c->dim == 3) return lss_fail(c, LSS_ERR_UNSUPPORTED, "medium_gradient: 2D grids only");
     cudaStream_t s = (cudaStream_t)stream;
     if (is_batch(c)) return lss_batch_gradient(c, (const double2*)mu, (const double2*)u, dirs_host, R, grad, s);
     const size_t bytes = (size_t)R * c->n * c->n * sizeof(double2);
@@ -437,11 +454,11 @@ int lss_solve_host(lss_ctx* c, const void* g_host, void* u_host, int R, const ls
     if (!g_host || !u_host || R < 1) return lss_fail(c, LSS_ERR_ARG, "solve_host: bad arguments");
     if (is_batch(c)) return batch_only_per_instance(c, "solve_host");
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t bytes = (size_t)R * c->n * c->n * sizeof(double2);
+    const size_t bytes = (size_t)R * c->npts() * sizeof(double2);
     int rc = lss_grow(c, &c->io_buf, &c->io_cap, 2 * bytes);
     if (rc) return rc;
     double2* gd = (double2*)c->io_buf;
-    double2* ud = gd + (size_t)R * c->n * c->n;
+    double2* ud = gd + (size_t)R * c->npts();
     rc = lss_check_cuda(c, cudaMemcpyAsync(gd, g_host, bytes, cudaMemcpyHostToDevice, s), "solve_host upload");
     if (rc) return rc;
     rc = lss_solve(c, gd, ud, R, o, stats, stream);
@@ -470,6 +487,13 @@ int lss_info(const lss_ctx* c, int* n_tot, int* n_slabs, int* fft_len) {
 
 int lss_slab_info(const lss_ctx* c, int slab, int* first_x1, int* n_layers, int* n_aux) {
     if (!c || is_batch(c) || slab < 0 || slab >= c->n_slabs) return LSS_ERR_ARG;
+    if (c->dim == 3) {
+        const Slab3& sd = c->d3->slabs[slab];
+        if (first_x1) *first_x1 = sd.s;
+        if (n_layers) *n_layers = sd.nl;
+        if (n_aux) *n_aux = sd.na;
+        return LSS_OK;
+    }
     const SlabDev& sd = c->slabs[slab];
     if (first_x1) *first_x1 = sd.s;
     if (n_layers) *n_layers = sd.nl;
@@ -479,6 +503,7 @@ int lss_slab_info(const lss_ctx* c, int slab, int* first_x1, int* n_layers, int*
 
 int lss_get_stencils(const lss_ctx* c, double* alpha, double* beta) {
     if (!c || is_batch(c) || !alpha || !beta) return LSS_ERR_ARG;
+    if (c->dim == 3) return lss3_get_stencils(c, alpha, beta);
     for (int o = 0; o < 9; ++o) {
         alpha[2 * o] = c->alpha[o].real();
         alpha[2 * o + 1] = c->alpha[o].imag();

@@ -105,6 +105,8 @@ LSS_HD inline long long cr_p0_off(int K0, int bs, int ldw) { return cr_t0_off(K0
 // every row, D^{-1}C and D^{-1}B of the odd rows (2 (K_0 / 2)).
 LSS_HD inline long long cr_work_blocks(int K0) { return 4LL * K0; }
 
+struct Ctx3;
+
 struct lss_ctx {
     // problem
     int dim = 2, n = 0, prec = LSS_FP64;
@@ -201,7 +203,12 @@ struct lss_ctx {
     std::vector<cudaEvent_t> ev_pool;
     long long launches[LSS_PROF_NCAT] = {};
 
+    // the 3D path's data (lss3d.cu); null for a 2D context
+    Ctx3* d3 = nullptr;
+
     size_t csize() const { return prec == LSS_FP64 ? sizeof(double2) : sizeof(float2); }
+    // points of I: n^dim
+    long long npts() const { return dim == 3 ? (long long)n * n * n : (long long)n * n; }
 };
 
 // Records CUDA events around a kernel group when profiling is on and counts

@@ -42,6 +42,7 @@
 
 #include "lss_common.cuh"
 #include "lss_ctx.h"
+#include "lss3d.h"
 
 namespace {
 
@@ -1814,10 +1815,12 @@ int lss_recurrences(lss_ctx* c, const void* maps, void* lam, void* phi, const vo
 }
 
 int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
+    if (c->dim == 3) return lss3_sweep(c, r, y, R, s);
     return c->prec == LSS_FP64 ? sweep_impl<double>(c, r, y, R, s) : sweep_impl<float>(c, r, y, R, s);
 }
 
 int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
+    if (c->dim == 3) return lss3_slab_apply(c, slab, v, w, R, s);
     return c->prec == LSS_FP64 ? slab_apply_impl<double>(c, slab, v, w, R, nullptr, 0, s)
                                : slab_apply_impl<float>(c, slab, v, w, R, nullptr, 0, s);
 }
@@ -1837,7 +1840,9 @@ void* g_fixed_ptr[kMaxDevices] = {};
 
 // Device address of g_fixed_scratch for the current device.  In host code the
 // symbol names a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The cached
+// address stays valid while the device's primary context lives; after
+// cudaDeviceReset the process must not call this entry point again.
 int fixed_scratch(lss_ctx* c, void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1858,6 +1863,10 @@ int fixed_scratch(lss_ctx* c, void** out) {
 
 extern "C" int lss_apply_slab_noalloc(lss_ctx* c, int slab, const void* v_dev, void* w_dev, int R, void* stream) {
     if (!c) return LSS_ERR_ARG;
+    if (!c->inst.empty())
+        return lss_fail(c, LSS_ERR_ARG, "apply_slab_noalloc: not defined on a batch context; call it on an "
+                                         "instance (lss_batch_instance)");
+    if (c->dim != 2) return lss_fail(c, LSS_ERR_UNSUPPORTED, "apply_slab_noalloc: 2D contexts only");
     if (!v_dev || !w_dev || R < 1 || slab < 0 || slab >= c->n_slabs)
         return lss_fail(c, LSS_ERR_ARG, "apply_slab_noalloc: bad arguments");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "apply_slab_noalloc before lss_factor");

@@ -129,6 +129,7 @@ extern "C" int lss_autotune(lss_ctx* c, int R, int* chosen, void* stream) {
     if (!c) return LSS_ERR_ARG;
     if (R < 1) return lss_fail(c, LSS_ERR_ARG, "autotune: R must be positive");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "autotune before lss_factor");
+    if (c->dim == 3) return lss_fail(c, LSS_ERR_UNSUPPORTED, "autotune: 2D grids only");
     cudaStream_t s = (cudaStream_t)stream;
     for (lss_ctx* ci : c->inst) {
         const int rc = lss_autotune(ci, R, nullptr, s);

@@ -2,7 +2,8 @@
 
 Device memory and streams come from PyTorch; every step of the solve runs in
 the library's kernels.  Vectors are complex128 CUDA tensors of shape
-(R, n, n) (or (n, n) for one right-hand side).
+(R, n, n) in 2D or (R, n, n, n) in 3D (or without the leading R for one
+right-hand side); the grid's dimension is that of m.
 """
 from __future__ import annotations
 
@@ -46,11 +47,14 @@ class LSSolver:
                  factor: bool = True, stream=None):
         self.lib = _lib.load()
         self.n, self.omega = int(n), float(omega)
-        if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != (n, n):
-            raise TypeError("m must be a (n, n) float64 CUDA tensor")
+        self.dim = m.dim()
+        if m.dtype != torch.float64 or not m.is_cuda or self.dim not in (2, 3) or \
+                tuple(m.shape) != (n,) * self.dim:
+            raise TypeError("m must be a (n, n) or (n, n, n) float64 CUDA tensor")
+        self.shape = (self.n,) * self.dim
         m = m.contiguous()
         ctx = ctypes.c_void_p()
-        g = _lib.Grid(2, self.n)
+        g = _lib.Grid(self.dim, self.n)
         p = _lib.Pml(int(b_pml), float(C))
         s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples))
         check(self.lib.lss_setup(ctypes.byref(ctx), ctypes.byref(g), self.omega, m.data_ptr(), ctypes.byref(p),
@@ -73,8 +77,8 @@ class LSSolver:
         return check(code, self.ctx)
 
     def set_medium(self, m: torch.Tensor, stream=None):
-        if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != (self.n, self.n):
-            raise TypeError("m must be a (n, n) float64 CUDA tensor")
+        if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != self.shape:
+            raise TypeError("m must be a float64 CUDA tensor of the grid's shape")
         self._check(self.lib.lss_set_medium(self.ctx, m.contiguous().data_ptr(), _stream_ptr(stream)))
 
     def profile(self, enable: bool = True):
@@ -114,18 +118,19 @@ class LSSolver:
         return s.value, nl.value, na.value
 
     def stencils(self):
-        a = np.zeros(18)
-        b = np.zeros(18)
+        """alpha, beta: 3^dim complex entries each (Eq. alpha, Eq. beta)."""
+        a = np.zeros(2 * 3 ** self.dim)
+        b = np.zeros(2 * 3 ** self.dim)
         self._check(self.lib.lss_get_stencils(self.ctx, a.ctypes.data, b.ctypes.data))
         return a.view(np.complex128), b.view(np.complex128)
 
     def _batch(self, x):
-        return x if x.dim() == 3 else x.unsqueeze(0)
+        return x if x.dim() == self.dim + 1 else x.unsqueeze(0)
 
     def plane_wave_rhs(self, dirs, with_incident: bool = False, stream=None):
-        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 2))
+        d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, self.dim))
         R = d.shape[0]
-        g = torch.empty((R, self.n, self.n), dtype=torch.complex128, device="cuda")
+        g = torch.empty((R,) + self.shape, dtype=torch.complex128, device="cuda")
         uI = torch.empty_like(g) if with_incident else None
         self._check(self.lib.lss_plane_wave_rhs(self.ctx, d.ctypes.data, R, g.data_ptr(),
                                                 uI.data_ptr() if uI is not None else None, _stream_ptr(stream)))
@@ -195,7 +200,7 @@ class LSSolver:
     def solve_host(self, g_host: torch.Tensor, u_host: torch.Tensor, opts: GmresOptions | None = None,
                    stream=None):
         o = opts or GmresOptions()
-        R = g_host.shape[0] if g_host.dim() == 3 else 1
+        R = g_host.shape[0] if g_host.dim() == self.dim + 1 else 1
         st = (_lib.Stats * R)()
         go = _lib.Gmres(o.restart, o.tol, o.max_iter)
         self._check(self.lib.lss_solve_host(self.ctx, g_host.data_ptr(), u_host.data_ptr(), R, ctypes.byref(go),

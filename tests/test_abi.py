@@ -42,9 +42,13 @@ def test_setup_argument_errors_without_gpu_work():
     from paper_1705_09443_gb300 import _lib
     lib = _lib.load()
     ctx = ctypes.c_void_p()
-    g = _lib.Grid(3, 16)
     p = _lib.Pml(4, 10.0)
     s = _lib.Slab(4, 0, 0)
+    g = _lib.Grid(4, 16)
+    rc = lib.lss_setup(ctypes.byref(ctx), ctypes.byref(g), 10.0, ctypes.c_void_p(16), ctypes.byref(p),
+                       ctypes.byref(s), 0, None)
+    assert rc == -1 and ctx.value is None and b"dim" in lib.lss_last_error(None)
+    g = _lib.Grid(3, 200)          # 3D grids up to n = 128
     rc = lib.lss_setup(ctypes.byref(ctx), ctypes.byref(g), 10.0, ctypes.c_void_p(16), ctypes.byref(p),
                        ctypes.byref(s), 0, None)
     assert rc == -8 and ctx.value is None
