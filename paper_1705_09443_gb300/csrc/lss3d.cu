@@ -575,7 +575,8 @@ __global__ void f3_rowid_init(const Slab3* __restrict__ slabs, int* __restrict__
 }
 
 // Gauss-Jordan elimination of the panel columns J = [j0, j0+nbp) of W (one CTA
-// per slab, the M x NB panel in shared memory).  Pivot j = j0 + jj is the
+// per slab, the M x NB panel in shared memory, column-major so that the
+// threads of a warp, which own consecutive rows, touch consecutive words).  Pivot j = j0 + jj is the
 // largest |W[r][j]| over rows r >= j (ties to the lower row); rows j and r are
 // swapped inside the panel (the rest of the rows later, by f3_swap_extract),
 // recorded in piv and in rowid.  After the panel the columns J hold the
@@ -599,7 +600,7 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < M * nbp; e += nt) {
         const int r = e / nbp, q = e % nbp;
-        P[r * NB + q] = w[(long long)r * M + j0 + q];
+        P[q * M + r] = w[(long long)r * M + j0 + q];
     }
     __syncthreads();
     for (int jj = 0; jj < nbp; ++jj) {
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
         R best = -1;
         int bi = M;
         for (int r = j + tid; r < M; r += nt) {
-            const R v = cabs2(P[r * NB + jj]);
+            const R v = cabs2(P[jj * M + r]);
             if (v > best) { best = v; bi = r; }
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -643,40 +644,70 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
         __syncthreads();
         const int pr = s_piv;
         if (pr != j && tid < nbp) {
-            const C t = P[j * NB + tid];
-            P[j * NB + tid] = P[pr * NB + tid];
-            P[pr * NB + tid] = t;
+            const C t = P[tid * M + j];
+            P[tid * M + j] = P[tid * M + pr];
+            P[tid * M + pr] = t;
         }
         __syncthreads();
-        const C d = crecip(P[j * NB + jj]);
+        const C d = crecip(P[jj * M + j]);
         __syncthreads();
-        if (tid < nbp) P[j * NB + tid] = (tid == jj) ? d : P[j * NB + tid] * d;
+        if (tid < nbp) P[tid * M + j] = (tid == jj) ? d : P[tid * M + j] * d;
         __syncthreads();
+        C pj[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) pj[q] = q < nbp ? P[q * M + j] : czero<C>();
         for (int i = tid; i < M; i += nt) {
             if (i == j) continue;
-            const C l = P[i * NB + jj];
-            for (int q = 0; q < nbp; ++q)
-                if (q != jj) P[i * NB + q] = P[i * NB + q] - l * P[j * NB + q];
-            P[i * NB + jj] = czero<C>() - l * d;
+            const C l = P[jj * M + i];
+#pragma unroll
+            for (int q = 0; q < NB; ++q)
+                if (q < nbp && q != jj) P[q * M + i] = P[q * M + i] - l * pj[q];
+            P[jj * M + i] = czero<C>() - l * d;
         }
         __syncthreads();
     }
     for (int e = tid; e < M * nbp; e += nt) {
         const int r = e / nbp, q = e % nbp;
-        w[(long long)r * M + j0 + q] = P[r * NB + q];
+        w[(long long)r * M + j0 + q] = P[q * M + r];
     }
 }
 
 // Outside the panel columns: apply the panel's row swaps, move the pivot rows'
-// entries into T (T[jj][c], zero for c in J) and zero them in W.
+// entries into T (T[jj][c], zero for c in J) and zero them in W.  The swaps
+// touch at most 2 nbp rows; their composition (row x receives the old row
+// src[x]) is worked out once per CTA, then every column is a gather: all
+// loads first, then the stores.
 template <typename C, int NB>
 __global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__ W, const int* __restrict__ piv,
                                 C* __restrict__ T, int j0, int Tld) {
+    __shared__ int rows[2 * NB], src[2 * NB], nrows_s;
     const int slab = blockIdx.y;
     const Slab3 sd = slabs[slab];
     const int M = sd.M;
     if (j0 >= M) return;
     const int nbp = min(NB, M - j0);
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int jj = 0; jj < nbp; ++jj) rows[na++] = j0 + jj;
+        for (int jj = 0; jj < nbp; ++jj) {
+            const int r = piv[slab * NB + jj];
+            bool seen = false;
+            for (int q = 0; q < na; ++q) seen |= rows[q] == r;
+            if (!seen) rows[na++] = r;
+        }
+        for (int q = 0; q < na; ++q) src[q] = rows[q];
+        for (int jj = 0; jj < nbp; ++jj) {
+            const int r = piv[slab * NB + jj];
+            int pr = 0;
+            while (rows[pr] != r) ++pr;
+            const int tmp = src[jj];
+            src[jj] = src[pr];
+            src[pr] = tmp;
+        }
+        nrows_s = na;
+    }
+    __syncthreads();
+    const int na = nrows_s;
     C* w = W + sd.w_off;
     C* t = T + (long long)slab * NB * Tld;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
@@ -684,17 +715,19 @@ __global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__
             for (int jj = 0; jj < nbp; ++jj) t[(long long)jj * Tld + c] = czero<C>();
             continue;
         }
-        for (int jj = 0; jj < nbp; ++jj) {
-            const int r = piv[slab * NB + jj], j = j0 + jj;
-            if (r != j) {
-                const C a = w[(long long)j * M + c];
-                w[(long long)j * M + c] = w[(long long)r * M + c];
-                w[(long long)r * M + c] = a;
+        C v[2 * NB];
+#pragma unroll
+        for (int q = 0; q < 2 * NB; ++q)
+            if (q < na) v[q] = w[(long long)src[q] * M + c];
+#pragma unroll
+        for (int q = 0; q < 2 * NB; ++q) {
+            if (q >= na) break;
+            if (q < nbp) {
+                t[(long long)q * Tld + c] = v[q];
+                w[(long long)rows[q] * M + c] = czero<C>();
+            } else {
+                w[(long long)rows[q] * M + c] = v[q];
             }
-        }
-        for (int jj = 0; jj < nbp; ++jj) {
-            t[(long long)jj * Tld + c] = w[(long long)(j0 + jj) * M + c];
-            w[(long long)(j0 + jj) * M + c] = czero<C>();
         }
     }
 }
@@ -774,175 +807,253 @@ __global__ void f3_finalize(const Slab3* __restrict__ slabs, const C* __restrict
 
 // ---------------------------------------------------------------- sweep (Algorithm 2, 3D slabs)
 
+// One step of a slab solve: phase 0 = forward sweep (slab i gets f_i minus the
+// coupling to u_{i-1}), phase 1 = backward sweep (slab i gets the coupling to
+// u_{i+1}; the result is subtracted); dir 0 = forward substitution at block
+// row k, dir 1 = backward substitution.
+struct Step3 { int phase, slab, dir, k; };
+
 struct Sweep3Args {
     const Slab3* slabs;
-    int n_slabs, n_tot, b, Mmax;
+    const Step3* steps;
+    int nsteps, n_tot, b, Mmax;
     const void* coef;
     const void* fac;
     const void* f;      // sparsified right-hand sides on the grid (R)
     void* ut;           // sweep solution on the grid (R)
     void* Y;            // block substitution vectors: [r][k][Mmax]
+    void* TB;           // split mode: the step input t, [r][Mmax]
     int R;              // right-hand sides in this launch (<= kSweepRB)
     long long G;        // n_tot^3
-    int only;           // -1: whole sweep; else solve slab `only` alone (T~_i f_i, no couplings)
+    int couple;         // 1: whole sweep (couplings between slabs); 0: one slab alone
+    unsigned dcap;      // bytes of the shared-memory buffer for D_k^{-1} rows
     unsigned* bar;
     int* err;
 };
 
-// One CTA per SM, persistent.  Each step of a slab solve: every CTA forms the
-// whole input t of the step in shared memory (the right-hand side of block k
-// and its coupling to the neighbouring block's solution), multiplies its
-// share of the rows of D_k^{-1} with it, and the grid synchronises.
-// Forward substitution y_k = D_k^{-1}(v_k - C_k y_{k-1}), backward
-// x_k = y_k - D_k^{-1} B_k x_{k+1}.  Slab i's right-hand side in the forward
-// sweep is f on D_i's layers minus H_{[i,i-1]} u_{i-1} on its first layer; in
-// the backward sweep it is H_{[i,i+1]} u_{i+1} on its last layer, and the
-// result is subtracted.
+// Input t_q of one step for right-hand side r, entry q = (a, c) of block k.
 template <typename C>
-__global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
-    using Rl = decltype(C{}.x);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* t = reinterpret_cast<C*>(smraw);                    // [R][Mmax]
-    C* part = t + (size_t)A.R * A.Mmax;                    // [warps][R]
+__device__ __forceinline__ C step_input(const Sweep3Args& A, const Slab3& sd, const Step3& st, int r, int q) {
     const C* coef = (const C*)A.coef;
-    const C* fac = (const C*)A.fac;
     const C* f = (const C*)A.f;
-    C* ut = (C*)A.ut;
-    C* Y = (C*)A.Y;
-    const int nt = A.n_tot, K = A.n_tot, G = gridDim.x, tid = threadIdx.x;
-    const int nwarps = blockDim.x / 32, wid = tid / 32, lane = tid & 31;
-    const int first = A.only >= 0 ? A.only : 0;
-    const int nl_total = A.only >= 0 ? 1 : A.n_slabs;
-    const int phases = (A.only >= 0 || A.n_slabs == 1) ? 1 : 2;
-    for (int phase = 0; phase < phases; ++phase) {
-        const int cnt = phase == 0 ? nl_total : A.n_slabs - 1;
-        for (int ii = 0; ii < cnt; ++ii) {
-            const int i = phase == 0 ? first + ii : A.n_slabs - 2 - ii;
-            const Slab3 sd = A.slabs[i];
-            const int M = sd.M, w = sd.w, na = sd.na;
-            const int X1s = sd.s + A.b;              // grid X1 of D_i's first layer
-            const C* cf = coef + sd.cf_off;
-            const int r0 = (int)((long long)blockIdx.x * M / G), r1 = (int)((long long)(blockIdx.x + 1) * M / G);
-            const int nrows = r1 - r0;
-            const int P = nrows > 0 ? max(1, nwarps / nrows) : 1;
-            for (int dir = 0; dir < 2; ++dir) {
-                const int ksteps = dir == 0 ? K : K - 1;
-                for (int kk = 0; kk < ksteps; ++kk) {
-                    const int k = dir == 0 ? kk : K - 2 - kk;
-                    // ---- t = input of this step
-                    for (int e = tid; e < A.R * M; e += blockDim.x) {
-                        const int r = e / M, q = e % M;
-                        const int a = q / nt, c = q % nt;
-                        const C* Yr = Y + (long long)r * K * A.Mmax;
-                        C v = czero<C>();
-                        if (dir == 0) {
-                            if (phase == 0) {
-                                if (a >= na) v = f[r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c];
-                                if (A.only < 0 && i > 0 && a == na) {   // - H_{[i,i-1]} u_{i-1}
-                                    const C* rowc = cf + (long long)k * 3 * M * 9;
-                                    for (int d2 = -1; d2 <= 1; ++d2) {
-                                        const int k2 = k + d2;
-                                        if (k2 < 0 || k2 >= K) continue;
-                                        for (int d3 = -1; d3 <= 1; ++d3) {
-                                            const int c3 = c + d3;
-                                            if (c3 < 0 || c3 >= nt) continue;
-                                            const C cv = rowc[((long long)(d2 + 1) * M + q) * 9 + 0 * 3 + (d3 + 1)];
-                                            const C uv = ut[r * A.G + ((long long)(X1s - 1) * nt + k2) * nt + c3];
-                                            v = v - cv * uv;
-                                        }
-                                    }
-                                }
-                            } else if (a == w - 1) {                  // H_{[i,i+1]} u_{i+1}
-                                const C* rowc = cf + (long long)k * 3 * M * 9;
-                                const int X1n = X1s + sd.nl;          // first layer of slab i+1
-                                for (int d2 = -1; d2 <= 1; ++d2) {
-                                    const int k2 = k + d2;
-                                    if (k2 < 0 || k2 >= K) continue;
-                                    for (int d3 = -1; d3 <= 1; ++d3) {
-                                        const int c3 = c + d3;
-                                        if (c3 < 0 || c3 >= nt) continue;
-                                        const C cv = rowc[((long long)(d2 + 1) * M + q) * 9 + 2 * 3 + (d3 + 1)];
-                                        const C uv = ut[r * A.G + ((long long)X1n * nt + k2) * nt + c3];
-                                        v = v + cv * uv;
-                                    }
-                                }
-                            }
-                            if (k > 0) {                              // - C_k y_{k-1}
-                                const C* cc = cf + ((long long)k * 3 + 0) * M * 9 + (long long)q * 9;
-                                const C* yp = Yr + (long long)(k - 1) * A.Mmax;
-                                for (int d1 = -1; d1 <= 1; ++d1) {
-                                    const int a1 = a + d1;
-                                    if (a1 < 0 || a1 >= w) continue;
-                                    for (int d3 = -1; d3 <= 1; ++d3) {
-                                        const int c3 = c + d3;
-                                        if (c3 < 0 || c3 >= nt) continue;
-                                        v = v - cc[(d1 + 1) * 3 + (d3 + 1)] * yp[a1 * nt + c3];
-                                    }
-                                }
-                            }
-                        } else {                                      // B_k x_{k+1}
-                            const C* bc = cf + ((long long)k * 3 + 2) * M * 9 + (long long)q * 9;
-                            const C* xn = Yr + (long long)(k + 1) * A.Mmax;
-                            for (int d1 = -1; d1 <= 1; ++d1) {
-                                const int a1 = a + d1;
-                                if (a1 < 0 || a1 >= w) continue;
-                                for (int d3 = -1; d3 <= 1; ++d3) {
-                                    const int c3 = c + d3;
-                                    if (c3 < 0 || c3 >= nt) continue;
-                                    v = cfma(bc[(d1 + 1) * 3 + (d3 + 1)], xn[a1 * nt + c3], v);
-                                }
-                            }
-                        }
-                        t[(size_t)r * A.Mmax + q] = v;
+    const C* ut = (const C*)A.ut;
+    const C* Yr = (const C*)A.Y + (long long)r * A.n_tot * A.Mmax;
+    const int nt = A.n_tot, K = A.n_tot, M = sd.M, w = sd.w, na = sd.na, k = st.k;
+    const int a = q / nt, c = q % nt;
+    const int X1s = sd.s + A.b;
+    const C* cf = coef + sd.cf_off;
+    C v = czero<C>();
+    if (st.dir == 0) {
+        if (st.phase == 0) {
+            if (a >= na) v = f[r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c];
+            if (A.couple && st.slab > 0 && a == na) {   // - H_{[i,i-1]} u_{i-1}
+                const C* rowc = cf + (long long)k * 3 * M * 9;
+                for (int d2 = -1; d2 <= 1; ++d2) {
+                    const int k2 = k + d2;
+                    if (k2 < 0 || k2 >= K) continue;
+                    for (int d3 = -1; d3 <= 1; ++d3) {
+                        const int c3 = c + d3;
+                        if (c3 < 0 || c3 >= nt) continue;
+                        v = v - rowc[((long long)(d2 + 1) * M + q) * 9 + (d3 + 1)] *
+                                    ut[r * A.G + ((long long)(X1s - 1) * nt + k2) * nt + c3];
                     }
-                    __syncthreads();
-                    // ---- rows [r0, r1) of D_k^{-1} t
-                    const C* D = fac + sd.fac_off + (long long)k * M * M;
-                    if (nrows > 0 && wid < nrows * P) {
-                        const int lr = wid / P, pp = wid % P;
-                        const int row = r0 + lr;
-                        const int cb = (int)((long long)pp * M / P), ce = (int)((long long)(pp + 1) * M / P);
-                        C acc[kSweepRB];
-                        for (int r = 0; r < kSweepRB; ++r) acc[r] = czero<C>();
-                        const C* Drow = D + (long long)row * M;
-#pragma unroll 4
-                        for (int j = cb + lane; j < ce; j += 32) {
-                            const C dv = Drow[j];
-                            for (int r = 0; r < kSweepRB; ++r)
-                                if (r < A.R) acc[r] = cfma(dv, t[(size_t)r * A.Mmax + j], acc[r]);
-                        }
-                        for (int r = 0; r < kSweepRB; ++r) {
-                            if (r >= A.R) break;
-                            for (int o = 16; o > 0; o >>= 1) {
-                                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
-                                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
-                            }
-                            if (lane == 0) part[(size_t)wid * kSweepRB + r] = acc[r];
-                        }
-                    }
-                    __syncthreads();
-                    for (int e = tid; e < nrows * A.R; e += blockDim.x) {
-                        const int lr = e / A.R, r = e % A.R;
-                        const int row = r0 + lr;
-                        C s = czero<C>();
-                        for (int pp = 0; pp < P; ++pp) s = s + part[(size_t)(lr * P + pp) * kSweepRB + r];
-                        C* yk = Y + (long long)r * K * A.Mmax + (long long)k * A.Mmax + row;
-                        C val;
-                        if (dir == 0) val = s;
-                        else val = *yk - s;
-                        *yk = val;
-                        const bool final_x = dir == 1 || k == K - 1;
-                        const int a = row / nt, c = row % nt;
-                        if (final_x && a >= na) {
-                            C* up = ut + r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c;
-                            *up = (phase == 0) ? val : *up - val;
-                        }
-                    }
-                    grid_barrier(A.bar, G, A.err);
+                }
+            }
+        } else if (a == w - 1) {                          // H_{[i,i+1]} u_{i+1}
+            const C* rowc = cf + (long long)k * 3 * M * 9;
+            const int X1n = X1s + sd.nl;
+            for (int d2 = -1; d2 <= 1; ++d2) {
+                const int k2 = k + d2;
+                if (k2 < 0 || k2 >= K) continue;
+                for (int d3 = -1; d3 <= 1; ++d3) {
+                    const int c3 = c + d3;
+                    if (c3 < 0 || c3 >= nt) continue;
+                    v = cfma(rowc[((long long)(d2 + 1) * M + q) * 9 + 6 + (d3 + 1)],
+                             ut[r * A.G + ((long long)X1n * nt + k2) * nt + c3], v);
                 }
             }
         }
+        if (k > 0) {                                      // - C_k y_{k-1}
+            const C* cc = cf + ((long long)k * 3 + 0) * M * 9 + (long long)q * 9;
+            const C* yp = Yr + (long long)(k - 1) * A.Mmax;
+            for (int d1 = -1; d1 <= 1; ++d1) {
+                const int a1 = a + d1;
+                if (a1 < 0 || a1 >= w) continue;
+                for (int d3 = -1; d3 <= 1; ++d3) {
+                    const int c3 = c + d3;
+                    if (c3 < 0 || c3 >= nt) continue;
+                    v = v - cc[(d1 + 1) * 3 + (d3 + 1)] * yp[a1 * nt + c3];
+                }
+            }
+        }
+    } else {                                              // B_k x_{k+1}
+        const C* bc = cf + ((long long)k * 3 + 2) * M * 9 + (long long)q * 9;
+        const C* xn = Yr + (long long)(k + 1) * A.Mmax;
+        for (int d1 = -1; d1 <= 1; ++d1) {
+            const int a1 = a + d1;
+            if (a1 < 0 || a1 >= w) continue;
+            for (int d3 = -1; d3 <= 1; ++d3) {
+                const int c3 = c + d3;
+                if (c3 < 0 || c3 >= nt) continue;
+                v = cfma(bc[(d1 + 1) * 3 + (d3 + 1)], xn[a1 * nt + c3], v);
+            }
+        }
     }
+    return v;
+}
+
+// Rows [r0, r1) of D_k^{-1} of a step as a 16-byte aligned byte window
+// [lo, lo + bytes) of the factor array; off = byte offset of the first row.
+struct RowWin { unsigned long long lo; unsigned bytes, off; int r0, r1; };
+template <typename C>
+__device__ __forceinline__ RowWin row_window(const Sweep3Args& A, const Step3& st, int G) {
+    const Slab3 sd = A.slabs[st.slab];
+    const int M = sd.M;
+    RowWin wdw;
+    wdw.r0 = (int)((long long)blockIdx.x * M / G);
+    wdw.r1 = (int)((long long)(blockIdx.x + 1) * M / G);
+    const unsigned long long a = (unsigned long long)((const C*)A.fac + sd.fac_off + (long long)st.k * M * M +
+                                                      (long long)wdw.r0 * M);
+    const unsigned long long e = a + (unsigned long long)(wdw.r1 - wdw.r0) * M * sizeof(C);
+    wdw.lo = a & ~15ull;
+    wdw.bytes = (unsigned)(((e + 15ull) & ~15ull) - wdw.lo);
+    wdw.off = (unsigned)(a - wdw.lo);
+    return wdw;
+}
+
+// One CTA per SM, persistent, walking the host-built step table.  Each step:
+// the input t of the step in shared memory, this CTA's rows of D_k^{-1} t
+// (the rows arrive by a bulk copy issued before the previous step's grid
+// barrier whenever they fit the buffer), the outputs, a grid barrier.
+// Forward substitution y_k = D_k^{-1}(v_k - C_k y_{k-1}), backward
+// x_k = y_k - D_k^{-1} B_k x_{k+1}.  SPLIT: each CTA forms only its own
+// rows of t, exchanged through global memory and a second grid barrier
+// (FP64, where forming the whole t in every CTA would cost more arithmetic
+// than the product itself); otherwise every CTA forms all of t.
+template <typename C, bool SPLIT>
+__global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw);
+    unsigned char* dbuf = smraw + 128;
+    C* t = reinterpret_cast<C*>(dbuf + A.dcap);            // [R][Mmax]
+    C* part = t + (size_t)A.R * A.Mmax;                    // [warps][kSweepRB]
+    C* ut = (C*)A.ut;
+    C* Y = (C*)A.Y;
+    C* TB = (C*)A.TB;
+    const int nt = A.n_tot, K = A.n_tot, G = gridDim.x, tid = threadIdx.x;
+    const int nwarps = blockDim.x / 32, wid = tid / 32, lane = tid & 31;
+    unsigned nbar = 0;   // grid barriers passed (the arrival counter starts at zero)
+    // s_pending: thread 0 issued the bulk copy of the current step's rows
+    // (decided by thread 0 alone, read by all after a barrier, so that the
+    // whole CTA agrees; no copy is issued once a wait has expired)
+    __shared__ int s_pending;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        fence_mbar_init();
+        s_pending = 0;
+        if (A.nsteps > 0) {
+            const RowWin wn = row_window<C>(A, A.steps[0], G);
+            if (wn.r1 > wn.r0 && wn.bytes <= A.dcap) {
+                mbar_expect_tx(mbar, wn.bytes);
+                tma_load_1d(dbuf, (const void*)wn.lo, wn.bytes, mbar);
+                s_pending = 1;
+            }
+        }
+    }
+    __syncthreads();
+    unsigned pcount = 0;   // bulk copies completed so far (mbarrier phase)
+    for (int s = 0; s < A.nsteps; ++s) {
+        const Step3 st = A.steps[s];
+        const Slab3 sd = A.slabs[st.slab];
+        const int M = sd.M, k = st.k, na = sd.na;
+        const int X1s = sd.s + A.b;
+        const RowWin wn = row_window<C>(A, st, G);
+        const int r0 = wn.r0, nrows = wn.r1 - wn.r0;
+        const int P = nrows > 0 ? max(1, nwarps / nrows) : 1;
+        // ---- t
+        if (SPLIT) {
+            for (int e = tid; e < nrows * A.R; e += blockDim.x) {
+                const int r = e / nrows, q = r0 + e % nrows;
+                TB[(size_t)r * A.Mmax + q] = step_input<C>(A, sd, st, r, q);
+            }
+            grid_barrier_count(A.bar, (++nbar) * (unsigned)G, A.err);
+            for (int e = tid; e < A.R * M; e += blockDim.x) {
+                const int r = e / M, q = e % M;
+                t[(size_t)r * A.Mmax + q] = TB[(size_t)r * A.Mmax + q];
+            }
+        } else {
+            const int tot = A.R * M;
+            for (int e = tid; e < tot; e += 2 * blockDim.x) {
+                const int e2 = e + blockDim.x;
+                const C v1 = step_input<C>(A, sd, st, e / M, e % M);
+                C v2 = czero<C>();
+                if (e2 < tot) v2 = step_input<C>(A, sd, st, e2 / M, e2 % M);
+                t[(size_t)(e / M) * A.Mmax + e % M] = v1;
+                if (e2 < tot) t[(size_t)(e2 / M) * A.Mmax + e2 % M] = v2;
+            }
+        }
+        __syncthreads();
+        // ---- this CTA's rows of D_k^{-1} t
+        const C* Dg = (const C*)A.fac + sd.fac_off + (long long)k * M * M;
+        const C* Drows = Dg + (long long)r0 * M;
+        if (s_pending) {
+            if (mbar_wait(mbar, pcount & 1u, A.err)) Drows = reinterpret_cast<const C*>(dbuf + wn.off);
+            ++pcount;     // (expired: read the rows from global memory)
+        }
+        if (nrows > 0 && wid < nrows * P) {
+            const int lr = wid / P, pp = wid % P;
+            const int cb = (int)((long long)pp * M / P), ce = (int)((long long)(pp + 1) * M / P);
+            C acc[kSweepRB];
+            for (int r = 0; r < kSweepRB; ++r) acc[r] = czero<C>();
+            const C* Drow = Drows + (long long)lr * M;
+#pragma unroll 4
+            for (int j = cb + lane; j < ce; j += 32) {
+                const C dv = Drow[j];
+                for (int r = 0; r < kSweepRB; ++r)
+                    if (r < A.R) acc[r] = cfma(dv, t[(size_t)r * A.Mmax + j], acc[r]);
+            }
+            for (int r = 0; r < kSweepRB; ++r) {
+                if (r >= A.R) break;
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                    acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+                }
+                if (lane == 0) part[(size_t)wid * kSweepRB + r] = acc[r];
+            }
+        }
+        __syncthreads();
+        // ---- the next step's rows: the buffer is free again
+        if (tid == 0) {
+            s_pending = 0;
+            if (s + 1 < A.nsteps && !(*(volatile int*)A.err & LSS_DERR_TIMEOUT)) {
+                const RowWin nx = row_window<C>(A, A.steps[s + 1], G);
+                if (nx.r1 > nx.r0 && nx.bytes <= A.dcap) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx(mbar, nx.bytes);
+                    tma_load_1d(dbuf, (const void*)nx.lo, nx.bytes, mbar);
+                    s_pending = 1;
+                }
+            }
+        }
+        // ---- outputs
+        for (int e = tid; e < nrows * A.R; e += blockDim.x) {
+            const int lr = e / A.R, r = e % A.R;
+            const int row = r0 + lr;
+            C sum = czero<C>();
+            for (int pp = 0; pp < P; ++pp) sum = sum + part[(size_t)(lr * P + pp) * kSweepRB + r];
+            C* yk = Y + (long long)r * K * A.Mmax + (long long)k * A.Mmax + row;
+            const C val = st.dir == 0 ? sum : *yk - sum;
+            *yk = val;
+            const bool final_x = st.dir == 1 || k == K - 1;
+            const int a = row / nt, c = row % nt;
+            if (final_x && a >= na) {
+                C* up = ut + r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c;
+                *up = (st.phase == 0) ? val : *up - val;
+            }
+        }
+        grid_barrier_count(A.bar, (++nbar) * (unsigned)G, A.err);
+    }
+    if (s_pending) mbar_wait(mbar, pcount & 1u, A.err);   // nothing may stay in flight at exit
 }
 
 __global__ void f2_to_d2_kernel(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
@@ -962,7 +1073,8 @@ void lss3_free(lss_ctx* c) {
     Ctx3* d = c->d3;
     if (!d) return;
     void* ptrs[] = {d->d_slabs, d->khat, d->gam_phys, d->gam_aux, d->coef64, d->coef == d->coef64 ? nullptr : d->coef,
-                    d->fac, d->W, d->X, d->T, d->piv, d->rowid, d->f, d->ut, d->Y, d->mvA, d->mvB};
+                    d->fac, d->W, d->X, d->T, d->piv, d->rowid, d->f, d->ut, d->Y, d->mvA, d->mvB, d->TB,
+                    d->steps_all, d->steps_one};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete d;
@@ -1006,8 +1118,8 @@ int configure3(lss_ctx* c) {
     const int psm = 210 * 1024;
     if (!e) e = cudaFuncSetAttribute(f3_panel<double2, kNB64>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
     if (!e) e = cudaFuncSetAttribute(f3_panel<float2, kNB32>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
-    if (!e) e = cudaFuncSetAttribute(sweep3_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
-    if (!e) e = cudaFuncSetAttribute(sweep3_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    if (!e) e = cudaFuncSetAttribute(sweep3_kernel<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    if (!e) e = cudaFuncSetAttribute(sweep3_kernel<float2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
     if (e) return lss_check_cuda(c, e, "3D kernel attributes");
     done_dev.push_back(dev);
     return LSS_OK;
@@ -1189,7 +1301,9 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
         if (c->prec == LSS_FP64) d->coef = d->coef64;
         else rc = dalloc3(c, &d->coef, (size_t)cf * cs, "coefficients fp32");
     }
-    rc = rc ? rc : dalloc3(c, &d->fac, (size_t)fo * cs, "slab factors");
+    // 64 bytes of slack: the sweep copies 16-byte aligned windows of rows that
+    // may end up to 15 bytes past the last factor entry
+    rc = rc ? rc : dalloc3(c, &d->fac, (size_t)fo * cs + 64, "slab factors");
     rc = rc ? rc : dalloc3(c, &d->W, (size_t)wo * cs, "pivot blocks");
     rc = rc ? rc : dalloc3(c, &d->X, (size_t)wo * cs, "Schur scratch");
     rc = rc ? rc : dalloc3(c, &d->T, (size_t)nl * NB * d->Mmax * cs, "panel rows");
@@ -1283,23 +1397,63 @@ int factor3_t(lss_ctx* c, cudaStream_t s) {
     return LSS_OK;
 }
 
+// Step table of the whole sweep (only < 0) or of one slab solve.
+std::vector<Step3> step_table(int n_slabs, int K, int only) {
+    std::vector<Step3> v;
+    auto slab_solve = [&](int phase, int i) {
+        for (int k = 0; k < K; ++k) v.push_back({phase, i, 0, k});
+        for (int k = K - 2; k >= 0; --k) v.push_back({phase, i, 1, k});
+    };
+    if (only >= 0) {
+        slab_solve(0, only);
+        return v;
+    }
+    for (int i = 0; i < n_slabs; ++i) slab_solve(0, i);
+    for (int i = n_slabs - 2; i >= 0; --i) slab_solve(1, i);
+    return v;
+}
+
 template <typename C>
 int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const double2* fin, cudaStream_t s) {
     Ctx3* d = c->d3;
+    constexpr bool kSplit = std::is_same<C, double2>::value;
     const long long G = (long long)c->n_tot * c->n_tot * c->n_tot;
     const size_t cs = sizeof(C);
     const int RB = std::min(R, kSweepRB);
     int rc = lss_grow(c, &d->f, &d->f_cap, (size_t)RB * G * cs);
     if (!rc) rc = lss_grow(c, &d->ut, &d->ut_cap, (size_t)RB * G * cs);
     if (!rc) rc = lss_grow(c, &d->Y, &d->Y_cap, (size_t)RB * c->n_tot * d->Mmax * cs);
+    if (!rc && kSplit) rc = lss_grow(c, &d->TB, &d->TB_cap, (size_t)RB * d->Mmax * cs);
     if (rc) return rc;
+    // step tables (device, cached: the whole sweep and the last single slab asked for)
+    const std::vector<Step3> tab = step_table(c->n_slabs, c->n_tot, only);
+    void** tab_dev = only < 0 ? &d->steps_all : &d->steps_one;
+    size_t* tab_cap = only < 0 ? &d->steps_all_cap : &d->steps_one_cap;
+    int* tab_key = only < 0 ? &d->steps_all_key : &d->steps_one_key;
+    if (*tab_key != only || !*tab_dev) {
+        rc = lss_grow(c, tab_dev, tab_cap, tab.size() * sizeof(Step3));
+        if (!rc) rc = lss_check_cuda(c, cudaMemcpyAsync(*tab_dev, tab.data(), tab.size() * sizeof(Step3),
+                                                        cudaMemcpyHostToDevice, s), "step table");
+        if (!rc) rc = lss_check_cuda(c, cudaStreamSynchronize(s), "step table");
+        if (rc) return rc;
+        *tab_key = only;
+    }
     const Stencil27 st = stencil_args(d, c->omega);
     const long long N = lss3_N(c);
-    const size_t smem = ((size_t)RB * d->Mmax + (size_t)(kSweepThreads / 32) * kSweepRB) * cs;
-    int grid = c->num_sms;
+    const int grid = c->num_sms;
+    // shared memory: mbarrier (128 B), the D_k^{-1} row buffer, t (RB x Mmax), warp partials
+    const size_t fixed = 128 + ((size_t)RB * d->Mmax + (size_t)(kSweepThreads / 32) * kSweepRB) * cs;
+    size_t want = 0;
+    for (const Slab3& sd : d->slabs) {
+        const size_t rows = ((size_t)sd.M + grid - 1) / grid + 1;
+        want = std::max(want, rows * sd.M * cs + 32);
+    }
+    const size_t budget = 210 * 1024;
+    const size_t dcap = fixed >= budget ? 0 : (std::min(want, budget - fixed) & ~(size_t)15);
+    const size_t smem = fixed + dcap;
     {
         int per = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep3_kernel<C>, kSweepThreads, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep3_kernel<C, kSplit>, kSweepThreads, smem);
         if (per < 1) return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D sweep kernel does not fit on an SM");
     }
     for (int r0 = 0; r0 < R; r0 += RB) {
@@ -1329,9 +1483,11 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
             }
         }
         cudaMemsetAsync(d->ut, 0, (size_t)Rc * G * cs, s);
+        cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), s);   // arrival counter of the grid barriers
         Sweep3Args a{};
         a.slabs = d->d_slabs;
-        a.n_slabs = c->n_slabs;
+        a.steps = (const Step3*)*tab_dev;
+        a.nsteps = (int)tab.size();
         a.n_tot = c->n_tot;
         a.b = c->b;
         a.Mmax = d->Mmax;
@@ -1340,16 +1496,18 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
         a.f = d->f;
         a.ut = d->ut;
         a.Y = d->Y;
+        a.TB = d->TB;
         a.R = Rc;
         a.G = G;
-        a.only = only;
+        a.couple = only < 0 ? 1 : 0;
+        a.dcap = (unsigned)dcap;
         a.bar = c->d_bar;
         a.err = c->d_err;
         void* args[] = {&a};
         {
             ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
-            cudaError_t e = cudaLaunchCooperativeKernel((const void*)sweep3_kernel<C>, dim3(grid), dim3(kSweepThreads),
-                                                        args, smem, s);
+            cudaError_t e = cudaLaunchCooperativeKernel((const void*)sweep3_kernel<C, kSplit>, dim3(grid),
+                                                        dim3(kSweepThreads), args, smem, s);
             if (e) return lss_check_cuda(c, e, "3D sweep launch");
         }
         if (!fin) {

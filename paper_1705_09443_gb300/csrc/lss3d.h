@@ -41,6 +41,9 @@ struct Ctx3 {
     void* Y = nullptr; size_t Y_cap = 0;          // block substitution vectors n_tot x Mmax per RHS
     double2* mvA = nullptr; size_t mvA_cap = 0;   // FFT scratch n^2 x L per RHS
     double2* mvB = nullptr; size_t mvB_cap = 0;   // FFT scratch n x L^2 per RHS
+    void* TB = nullptr; size_t TB_cap = 0;        // sweep step input exchanged between CTAs (FP64)
+    void* steps_all = nullptr; size_t steps_all_cap = 0; int steps_all_key = -2;   // step table, whole sweep
+    void* steps_one = nullptr; size_t steps_one_cap = 0; int steps_one_key = -2;   // step table, one slab
 };
 
 void lss3_free(lss_ctx* c);

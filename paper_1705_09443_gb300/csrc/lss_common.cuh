@@ -120,6 +120,28 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, in
     __syncthreads();
 }
 
+// Bounded grid barrier on a monotonic arrival counter (zeroed before the
+// launch): the n-th barrier of a launch waits until the counter reaches
+// n * nblocks.  Each CTA adds with a release reduction and polls with acquire
+// loads; the error word and the clock are looked at every 64 polls.  On
+// expiry sets LSS_DERR_TIMEOUT and returns; once the flag is set later
+// barriers do not wait.
+__device__ __forceinline__ void grid_barrier_count(unsigned* count, unsigned target, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        const long long t0 = clock64();
+        for (unsigned it = 0;; ++it) {
+            if (ld_acquire_u32(count) >= target) break;
+            if ((it & 63u) == 63u) {
+                if (*(volatile int*)err & LSS_DERR_TIMEOUT) break;
+                if (clock64() - t0 > LSS_WAIT_CYCLES) { atomicOr(err, LSS_DERR_TIMEOUT); break; }
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- TMA bulk copy + mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -201,21 +201,28 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (!ok) break;
 
-        // ---- epilogue: row (32 warp + lane) of the tile, 8 chunks of 16 complex columns
-        const int i = i0 + tid;
+        // ---- epilogue, 8 chunks of 16 complex columns: each thread moves its
+        // accumulator row (tcgen05.ld) into shared memory (row stride 33
+        // floats, no bank conflicts), then the CTA adds the chunk to W with
+        // consecutive threads on consecutive columns of a row
+        float* S = reinterpret_cast<float*>(sm);   // the operands are consumed
         for (int ch = 0; ch < kTileN / 32; ++ch) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32), v);
-            if (i >= M) continue;
-            float2* wr = w + (long long)i * M;
-            for (int q = 0; q < 16; ++q) {
-                const int c = c0 + ch * 16 + q;
-                if (c >= M || (c >= j0 && c < j0 + nbp)) continue;
-                float2 o = wr[c];
-                o.x += v[2 * q];
-                o.y += v[2 * q + 1];
-                wr[c] = o;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) S[tid * 33 + j] = v[j];
+            __syncthreads();
+            for (int e = tid; e < 128 * 16; e += 128) {
+                const int row = e >> 4, q = e & 15;
+                const int i = i0 + row, c = c0 + ch * 16 + q;
+                if (i >= M || c >= M || (c >= j0 && c < j0 + nbp)) continue;
+                float2* p = w + (long long)i * M + c;
+                float2 o = *p;
+                o.x += S[row * 33 + 2 * q];
+                o.y += S[row * 33 + 2 * q + 1];
+                *p = o;
             }
+            __syncthreads();
         }
         // the next tile's operand writes must not overtake this tile's reads
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -38,9 +38,10 @@ def test_workload_recipes_are_seeded():
 
 
 def test_bench_reference_arm_prints_the_contract_line():
-    """`bench.py --impl reference` times the oracle on the host (about 15 s)."""
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
-                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    """`bench.py --impl reference` times the oracle on the host (the n = 64
+    workload here, a few seconds; the default n = 512 workload takes minutes)."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "0",
+                        "--workload", "2d_n64"], cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -50,6 +51,39 @@ def test_bench_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+    assert line["steps"] == 2 and line["oracle_iters"] >= 1
+
+
+def test_method_work_counts_match_the_stated_sizes():
+    """The bench's algorithmic work model against the sizes stated for the
+    workloads: n = 512 factorization about 3.1 GFLOP, 3D n = 64 factors about
+    11.6 GB in FP32 per full read, the sweep reading them twice per slab solve."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Fake:
+        def __init__(self, n, dim, b, bs, L):
+            self.n, self.dim, self.fft_len = n, dim, L
+            self.n_tot = n + 2 + 2 * b
+            self.n_slabs = -(-(n + 2) // bs)
+            self.b, self.bs = b, bs
+
+        def slab_info(self, i):
+            n, b, bs, ns = self.n, self.b, self.bs, self.n_slabs
+            if i == 0:
+                return -b, b + bs, 0
+            return i * bs, (n + 2 - i * bs) + b if i == ns - 1 else bs, b
+
+    w2 = bench.method_work(Fake(512, 2, 12, 4, 1024), 4)
+    # 128 slabs of width 16 and the last of width 26 (2 remainder + 12 PML + 12 auxiliary), n_y = 538
+    exp = 538 * (8 / 3 + 8) * (128 * 16 ** 3 + 26 ** 3)
+    assert abs(w2["factor"]["flops"] / exp - 1) < 1e-12 and abs(exp / 3.0e9 - 1) < 0.04
+    assert abs(w2["matvec"]["flops"] / 210e6 - 1) < 0.01
+    w3 = bench.method_work(Fake(64, 3, 8, 4, 128), 4)
+    # sum over slabs of n_tot M^2 complex64 entries (16 x 984^2 + 1476^2) x 82 x 8 B = 11.6 GB
+    fac = 82 * (16 * 984 ** 2 + 1476 ** 2) * 8
+    assert abs(fac / 11.6e9 - 1) < 0.02
+    assert w3["sweep"]["bytes"] == 2 * 82 * 8 * (2 * 16 * 984 ** 2 + 1476 ** 2)
 
 
 def _max_worker(rank, world, port, out_dir):
