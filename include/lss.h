@@ -346,6 +346,21 @@ int lss_batch_info(const lss_ctx *c, int *n_inst, long long *elems_per_rhs);
 /* Instance q of a batch (owned by the batch: do not destroy it). */
 int lss_batch_instance(lss_ctx *c, int q, lss_ctx **inst);
 
+/*
+ * lss_test_inject - fault injection for tests; the paper has no counterpart.
+ * Nothing here touches memory outside the context's own arrays.
+ *   what = 1  zero the coefficients of block row b (the x2 index + b_pml) of
+ *             slab a's subproblem (its diagonal block in 3D); the context
+ *             returns to the unfactored state, and the next lss_factor meets
+ *             a zero pivot and returns LSS_ERR_SINGULAR
+ *   what = 2  run the library's bounded device waits on conditions nothing
+ *             satisfies (a grid barrier one arrival short, an mbarrier nobody
+ *             arrives at); each gives up after the wait limit (about 2 s) and
+ *             the call returns LSS_ERR_TIMEOUT; the context stays usable
+ * Returns LSS_ERR_ARG for other values or on a batch context.
+ */
+int lss_test_inject(lss_ctx *c, int what, int a, long long b, void *stream);
+
 /* Message of the last failure on this context ("" if none). */
 const char *lss_last_error(const lss_ctx *c);
 

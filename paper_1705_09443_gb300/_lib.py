@@ -21,7 +21,7 @@ ERRORS = {
 SYMBOLS = [
     "lss_setup", "lss_set_medium", "lss_factor", "lss_plane_wave_rhs", "lss_apply_A", "lss_apply_P", "lss_solve",
     "lss_adjoint_solve", "lss_medium_gradient", "lss_solve_host", "lss_apply_slab", "lss_apply_slab_noalloc", "lss_info", "lss_slab_info", "lss_get_stencils",
-    "lss_profile", "lss_profile_read", "lss_set_graphs", "lss_graph_count", "lss_autotune", "lss_setup_batch", "lss_batch_info", "lss_batch_instance", "lss_last_error",
+    "lss_profile", "lss_profile_read", "lss_set_graphs", "lss_graph_count", "lss_autotune", "lss_setup_batch", "lss_batch_info", "lss_batch_instance", "lss_test_inject", "lss_last_error",
     "lss_destroy",
 ]
 PROF_CATEGORIES = ["matvec", "sparsify", "slab_a", "recur", "slab_e", "factor", "iface", "krylov", "setup"]
@@ -90,6 +90,7 @@ def load() -> ctypes.CDLL:
     lib.lss_setup_batch.argtypes = [P(vp), i, P(Grid), P(d), P(vp), P(Pml), P(Slab), i, vp]
     lib.lss_batch_info.argtypes = [vp, P(i), P(ctypes.c_longlong)]
     lib.lss_batch_instance.argtypes = [vp, i, P(vp)]
+    lib.lss_test_inject.argtypes = [vp, i, i, ctypes.c_longlong, vp]
     lib.lss_last_error.argtypes = [vp]
     lib.lss_last_error.restype = ctypes.c_char_p
     lib.lss_destroy.argtypes = [vp]

@@ -1,11 +1,16 @@
 // Flexible restarted GMRES (Sec. 2.5 uses standard restarted GMRES; flexible
 // GMRES equals it for a fixed linear preconditioner and stays valid when the
 // preconditioner is applied in reduced precision).  Right preconditioning,
-// x0 = 0, classical Gram-Schmidt with one re-orthogonalisation (CGS2), Givens
-// rotations on the host, all vector work in FP64 kernels, R right-hand sides
-// advanced together with independent Hessenberg matrices.  The kernels of one
-// iteration (preconditioner, operator, both Gram-Schmidt passes) are replayed
-// from a CUDA graph per basis index once the workspaces exist.
+// x0 = 0, classical Gram-Schmidt with one re-orthogonalisation (CGS2), R
+// right-hand sides advanced together with independent Hessenberg matrices.
+// Everything runs in FP64 kernels on the device: the vector work, the
+// Hessenberg columns, the Givens rotations, the residual estimates and the
+// per-RHS convergence masks, and the triangular solve for the update.  The
+// host reads the device state once per restart cycle.  Each iteration
+// (preconditioner, operator, both Gram-Schmidt passes, Givens update,
+// normalisation) is replayed from a CUDA graph per basis index, guarded by a
+// conditional node that skips it once every right-hand side has converged,
+// so a whole cycle is enqueued without waiting for the device.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -87,6 +92,145 @@ __global__ void sub_kernel(const double2* __restrict__ a, const double2* __restr
         y[e] = a[e] - b[e];
 }
 
+// ---------------------------------------------------------------- device GMRES state
+// Per right-hand side r (R of them), restart length m:
+//   H[(r*(m+1) + i)*m + j]   Hessenberg matrix after the rotations (upper triangular part)
+//   cs, sn[r*m + j]          Givens rotations
+//   rho[r*(m+1) + i]         rotated residual vector
+//   gnorm, est, tol          ||g||, |rho_{k}|/||g||, tolerance (state[0])
+//   kc, iters, done          steps in this cycle, steps in total, converged flag
+//   any                      some right-hand side is still active
+struct GState {
+    double2 *H, *cs, *sn, *rho;
+    double *gnorm, *est, *tol;
+    int *kc, *iters, *done, *any;
+};
+
+size_t gstate_bytes(int m, int R) {
+    return (size_t)R * ((size_t)(m + 1) * m + 2 * (size_t)m + (m + 1)) * sizeof(double2) +
+           (size_t)(2 * R + 1) * sizeof(double) + (size_t)(3 * R + 1) * sizeof(int) + 256;
+}
+
+GState gstate_at(void* base, int m, int R) {
+    GState g;
+    char* p = (char*)base;
+    auto take = [&](size_t bytes) { char* q = p; p += (bytes + 15) & ~(size_t)15; return (void*)q; };
+    g.H = (double2*)take((size_t)R * (m + 1) * m * sizeof(double2));
+    g.cs = (double2*)take((size_t)R * m * sizeof(double2));
+    g.sn = (double2*)take((size_t)R * m * sizeof(double2));
+    g.rho = (double2*)take((size_t)R * (m + 1) * sizeof(double2));
+    g.gnorm = (double*)take(R * sizeof(double));
+    g.est = (double*)take(R * sizeof(double));
+    g.tol = (double*)take(sizeof(double));
+    g.kc = (int*)take(R * sizeof(int));
+    g.iters = (int*)take(R * sizeof(int));
+    g.done = (int*)take(R * sizeof(int));
+    g.any = (int*)take(sizeof(int));
+    return g;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double cabsd(double2 a) { return hypot(a.x, a.y); }
+
+// Start of a restart cycle: beta_r = ||r_r|| (from the norm reduction bn2),
+// rho = beta e_1, scales 1/beta for the first basis vector.  first: also
+// ||g||, the convergence flags and the step counters.  One block.
+__global__ void cycle_init_kernel(GState gs, const double2* __restrict__ bn2, double* __restrict__ sc, int R, int m,
+                                  int first, double tol) {
+    int act = 0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const double beta = sqrt(fmax(0.0, bn2[r].x));
+        if (first) {
+            gs.gnorm[r] = beta;
+            gs.done[r] = beta == 0.0;
+            gs.iters[r] = 0;
+            gs.est[r] = 0.0;
+        }
+        gs.rho[(size_t)r * (m + 1)] = mk(beta, 0.0);
+        for (int i = 1; i <= m; ++i) gs.rho[(size_t)r * (m + 1) + i] = mk(0.0, 0.0);
+        gs.kc[r] = 0;
+        const bool a = !gs.done[r] && beta > 0.0;
+        sc[r] = a ? 1.0 / beta : 0.0;
+        act |= a;
+    }
+    act = __syncthreads_or(act);
+    if (threadIdx.x == 0) {
+        gs.any[0] = act;
+        if (first) gs.tol[0] = tol;
+    }
+}
+
+// Step j of the Arnoldi process for every active right-hand side: Hessenberg
+// column j = h1 + h2 (the two Gram-Schmidt passes) with H(j+1, j) = ||w||,
+// the previous rotations applied, a new rotation annihilating H(j+1, j), the
+// rotated residual and its estimate |rho_{j+1}|/||g||; a right-hand side stops
+// when the estimate reaches tol (or w vanished).  sc = 1/||w|| for the next
+// basis vector (0 once stopped).  One block.
+__global__ void givens_kernel(GState gs, const double2* __restrict__ h1, const double2* __restrict__ h2,
+                              const double2* __restrict__ hn, double* __restrict__ sc, int R, int m, int j) {
+    int act = 0;
+    const double tol = gs.tol[0];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        if (gs.done[r]) { sc[r] = 0.0; continue; }
+        double2* Hr = gs.H + (size_t)r * (m + 1) * m;
+        double2* cs = gs.cs + (size_t)r * m;
+        double2* sn = gs.sn + (size_t)r * m;
+        double2* rho = gs.rho + (size_t)r * (m + 1);
+        for (int i = 0; i <= j; ++i) Hr[(size_t)i * m + j] = h1[(size_t)i * R + r] + h2[(size_t)i * R + r];
+        const double hnr = sqrt(fmax(0.0, hn[r].x));
+        Hr[(size_t)(j + 1) * m + j] = mk(hnr, 0.0);
+        for (int i = 0; i < j; ++i) {
+            const double2 a = Hr[(size_t)i * m + j], b = Hr[(size_t)(i + 1) * m + j];
+            const double2 cc = cs[i], ss = sn[i];
+            Hr[(size_t)i * m + j] = cmul(cc, a) + cmul(ss, b);
+            Hr[(size_t)(i + 1) * m + j] = cmul(conjc(cc), b) - cmul(conjc(ss), a);
+        }
+        const double2 a = Hr[(size_t)j * m + j], b = Hr[(size_t)(j + 1) * m + j];
+        const double den = sqrt(cabs2(a) + cabs2(b));
+        const double2 cc = den > 0 ? mk(a.x / den, -a.y / den) : mk(1.0, 0.0);
+        const double2 ss = den > 0 ? mk(b.x / den, -b.y / den) : mk(0.0, 0.0);
+        cs[j] = cc;
+        sn[j] = ss;
+        Hr[(size_t)j * m + j] = cmul(cc, a) + cmul(ss, b);
+        Hr[(size_t)(j + 1) * m + j] = mk(0.0, 0.0);
+        const double2 rj = rho[j];
+        rho[j + 1] = mk(0.0, 0.0) - cmul(conjc(ss), rj);
+        rho[j] = cmul(cc, rj);
+        gs.iters[r] += 1;
+        gs.kc[r] = j + 1;
+        const double e = cabsd(rho[j + 1]) / gs.gnorm[r];
+        gs.est[r] = e;
+        const bool stop = e <= tol || hnr == 0.0;
+        gs.done[r] = stop;
+        sc[r] = (!stop && hnr > 0) ? 1.0 / hnr : 0.0;
+        act |= !stop;
+    }
+    act = __syncthreads_or(act);
+    if (threadIdx.x == 0) gs.any[0] = act;
+}
+
+// y = R^{-1} rho for the kc[r] steps of this cycle of every right-hand side
+// (back substitution with the rotated upper-triangular H), written as
+// y[i*R + r] for i < J (zero beyond kc[r]).  One block.
+__global__ void backsolve_kernel(GState gs, double2* __restrict__ y, int R, int m, int J) {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const int k = gs.kc[r];
+        const double2* Hr = gs.H + (size_t)r * (m + 1) * m;
+        const double2* rho = gs.rho + (size_t)r * (m + 1);
+        for (int i = J - 1; i >= 0; --i) {
+            if (i >= k) { y[(size_t)i * R + r] = mk(0.0, 0.0); continue; }
+            double2 acc = rho[i];
+            for (int l = i + 1; l < k; ++l) acc = acc - cmul(Hr[(size_t)i * m + l], y[(size_t)l * R + r]);
+            y[(size_t)i * R + r] = cmul(acc, crecip(Hr[(size_t)i * m + i]));
+        }
+    }
+}
+
+// Runs the iteration that follows only while some right-hand side is active.
+__global__ void gate_kernel(const int* __restrict__ any, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, any[0] != 0 ? 1u : 0u);
+}
+
 struct Krylov {
     lss_ctx* c;
     cudaStream_t s;
@@ -116,7 +260,6 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
     const long long N = c->npts();
     const int m = o->restart;
-    const double tol = o->tol;
     const int maxit = o->max_iter;
     const long long RN = (long long)R * N;
     // storage: V (m+1), Z (m), w, r
@@ -133,20 +276,24 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     const size_t red_bytes = (size_t)(m + 1) * R * K.nblk * sizeof(double2) +
                              (size_t)(2 * (m + 1) + 1) * R * sizeof(double2) + (size_t)R * sizeof(double) + 64;
     rc = lss_grow(c, (void**)&c->red_buf, &c->red_cap, red_bytes);
+    if (!rc) rc = lss_grow(c, &c->gm_buf, &c->gm_cap, gstate_bytes(m, R));
     if (rc) return rc;
     K.part = c->red_buf;
     K.hdev = K.part + (size_t)(m + 1) * R * K.nblk;
     K.h2dev = K.hdev + (size_t)(m + 1) * R;
     K.hnorm = K.h2dev + (size_t)(m + 1) * R;
     K.scdev = reinterpret_cast<double*>(K.hnorm + R);
+    const GState gs = gstate_at(c->gm_buf, m, R);
     const int g1 = std::max(1, std::min(4 * c->num_sms / R, (int)((N + 255) / 256)));
-    const int gs = std::max(1, std::min(4 * c->num_sms, (int)((RN + 255) / 256)));
+    const int gs_grid = std::max(1, std::min(4 * c->num_sms, (int)((RN + 255) / 256)));
+    const int small = std::min(1024, std::max(32, (R + 31) / 32 * 32));
 
     double2* hnorm = K.hnorm;
     if (transpose && (rc = lss_prepare_sweep_t(c, s))) return rc;
 
-    // Iteration body for basis vector j on stream bs: Z_j = P V_j, w = A Z_j,
-    // two Gram-Schmidt passes against V_0..V_j, ||w||^2.
+    // Iteration j on stream bs: Z_j = P V_j, w = A Z_j, two Gram-Schmidt passes
+    // against V_0..V_j, ||w||^2, the Givens update of every right-hand side,
+    // V_{j+1} = w / ||w||.
     auto body = [&](int j, cudaStream_t bs) -> int {
         Krylov Kb = K;
         Kb.s = bs;
@@ -160,186 +307,169 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         dots(Kb, V, RN, j + 1, w, K.h2dev, 0);
         { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.h2dev, j + 1, w, N, R, -1.0); }
         dots(Kb, w, 0, 1, w, hnorm, 0);
+        {
+            ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 2);
+            givens_kernel<<<1, small, 0, bs>>>(gs, K.hdev, K.h2dev, hnorm, K.scdev, R, m, j);
+            scale_kernel<<<dim3(g1, R), 256, 0, bs>>>(w, V + (size_t)(j + 1) * RN, K.scdev, N);
+        }
         return lss_check_cuda(c, cudaGetLastError(), "arnoldi");
     };
-    // Graphs: only once a solve with this R and transpose ran uncaptured at the
-    // current workspace generation (every buffer the body touches exists), and
-    // not while profiling (the profile records events around kernel groups).
-    // (the 3D sweep is a cooperative grid-synchronised launch: run uncaptured)
+    // Graphs: only once a solve with this R, transpose and restart length ran
+    // uncaptured at the current workspace generation (every buffer the body
+    // touches exists), not while profiling (events around kernel groups), and
+    // not for the 3D sweep (a cooperative grid-synchronised launch).
     const bool use_graph = c->graphs_on && !c->prof_on && c->dim == 2;
     bool warm = false;
     for (const auto& k : c->graph_warm)
-        warm |= k[0] == R && k[1] == transpose && (unsigned long long)k[2] == c->buf_gen;
+        warm |= k[0] == R && k[1] == transpose && (unsigned long long)k[2] == c->buf_gen && k[3] == m;
     warm &= use_graph;
+    // graph of iteration j: a gate kernel (sets the condition from gs.any)
+    // followed by an IF node whose body is the captured iteration
     auto graph_for = [&](int j) -> cudaGraphExec_t {
-        for (const auto& g : c->graphs)
-            if (g.j == j && g.R == R && g.transpose == transpose && g.gen == c->buf_gen) return g.exec;
+        for (const auto& gr : c->graphs)
+            if (gr.j == j && gr.R == R && gr.transpose == transpose && gr.gen == c->buf_gen && gr.m == m)
+                return gr.exec;
         std::vector<lss_ctx::GraphRec> keep;   // drop graphs of older workspaces
-        for (const auto& g : c->graphs) {
-            if (g.gen == c->buf_gen) keep.push_back(g);
-            else if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (const auto& gr : c->graphs) {
+            if (gr.gen == c->buf_gen) keep.push_back(gr);
+            else if (gr.exec) cudaGraphExecDestroy(gr.exec);
         }
         c->graphs.swap(keep);
         const unsigned long long gen0 = c->buf_gen;
         const std::string err0 = c->err;
         cudaGraphExec_t ex = nullptr;
-        if (c->cap_stream || !cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) {
-            cudaGraph_t gr = nullptr;
-            if (!cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal)) {
-                const int brc = body(j, c->cap_stream);
-                cudaError_t e = cudaStreamEndCapture(c->cap_stream, &gr);
-                if (!brc && !e && gr && c->buf_gen == gen0 && cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess)
-                    ex = nullptr;
-                if (brc || e || c->buf_gen != gen0) {
-                    if (ex) cudaGraphExecDestroy(ex);
-                    ex = nullptr;
-                }
-                if (gr) cudaGraphDestroy(gr);
-            }
+        cudaGraph_t graph = nullptr;
+        bool ok = (c->cap_stream || !cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) &&
+                  !cudaGraphCreate(&graph, 0);
+        cudaGraphConditionalHandle hcond = 0;
+        cudaGraphNode_t gate = nullptr, cond = nullptr;
+        if (ok) ok = !cudaGraphConditionalHandleCreate(&hcond, graph, 0, 0);
+        if (ok) {
+            void* args[] = {(void*)&gs.any, (void*)&hcond};
+            cudaKernelNodeParams kp{};
+            kp.func = (void*)gate_kernel;
+            kp.gridDim = dim3(1);
+            kp.blockDim = dim3(1);
+            kp.kernelParams = args;
+            ok = !cudaGraphAddKernelNode(&gate, graph, nullptr, 0, &kp);
         }
+        cudaGraph_t bodyg = nullptr;
+        if (ok) {
+            cudaGraphNodeParams cp{};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hcond;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            ok = !cudaGraphAddNode(&cond, graph, &gate, nullptr, 1, &cp);
+            if (ok) bodyg = cp.conditional.phGraph_out[0];
+        }
+        if (ok) ok = !cudaStreamBeginCaptureToGraph(c->cap_stream, bodyg, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeThreadLocal);
+        if (ok) {
+            const int brc = body(j, c->cap_stream);
+            cudaGraph_t out = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &out);
+            ok = !brc && !e && c->buf_gen == gen0;
+            if (ok && cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) ex = nullptr;
+        }
+        if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();   // a refused capture leaves no error behind
         c->err = err0;
         // a body that cannot be captured (e.g. the grid-synchronised recurrence)
         // is remembered as such and runs uncaptured
-        c->graphs.push_back({j, R, transpose, gen0, ex});
-        return ex;
+        c->graphs.push_back({j, R, transpose, m, gen0, ok ? ex : nullptr});
+        return ok ? ex : nullptr;
     };
-    auto iteration = [&](int j) -> int {
+    auto launch_iteration = [&](int j, bool& graphed) -> int {
+        graphed = false;
         if (warm) {
             cudaGraphExec_t ex = graph_for(j);
-            if (ex) return lss_check_cuda(c, cudaGraphLaunch(ex, s), "iteration graph");
+            if (ex) {
+                graphed = true;
+                return lss_check_cuda(c, cudaGraphLaunch(ex, s), "iteration graph");
+            }
         }
         return body(j, s);
     };
 
-    std::vector<double2> hh((size_t)(m + 2) * R);
-    std::vector<double> sc(R);
-    auto fetch = [&](const double2* src, size_t count) -> int {
-        cudaError_t e = cudaMemcpyAsync(hh.data(), src, count * sizeof(double2), cudaMemcpyDeviceToHost, s);
-        if (!e) e = cudaStreamSynchronize(s);
-        return lss_check_cuda(c, e, "krylov fetch");
-    };
-    auto set_scale = [&]() -> int {
-        return lss_check_cuda(c, cudaMemcpyAsync(K.scdev, sc.data(), R * sizeof(double), cudaMemcpyHostToDevice, s),
-                              "krylov scale");
-    };
-
-    // ||g||
+    // ||g||, cycle 0
     dots(K, g, 0, 1, g, K.hdev, 0);
-    if ((rc = fetch(K.hdev, R))) return rc;
-    std::vector<double> gnorm(R), beta(R);
-    for (int r = 0; r < R; ++r) gnorm[r] = beta[r] = std::sqrt(std::max(0.0, hh[r].x));
+    { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); cycle_init_kernel<<<1, small, 0, s>>>(gs, K.hdev, K.scdev, R, m, 1, o->tol); }
     cudaMemsetAsync(u, 0, RN * sizeof(double2), s);
     cudaMemcpyAsync(rv, g, RN * sizeof(double2), cudaMemcpyDeviceToDevice, s);
 
-    std::vector<int> iters(R, 0), done(R, 0);
-    std::vector<double> est(R, 0.0);
-    for (int r = 0; r < R; ++r)
-        if (gnorm[r] == 0.0) done[r] = 1;
-    int total = 0;
-    std::vector<cd> H((size_t)(m + 1) * m * R), cs((size_t)m * R), sn((size_t)m * R), rho((size_t)(m + 1) * R);
-    auto Hix = [&](int i, int j, int r) -> cd& { return H[((size_t)r * (m + 1) + i) * m + j]; };
-
+    std::vector<int> kc(R), done(R), iters(R);
+    std::vector<double> est(R), gnorm(R);
+    int total = 0, any = 1;
+    // pipeline of graphed iterations: after iteration j the device copies its
+    // "some RHS active" flag to pinned host memory and records an event; the
+    // host launches iteration j + 1 while j - 1 may still run, and looks at
+    // the flag of iteration j - kAhead before launching more (an iteration
+    // launched after convergence is skipped by its conditional node)
+    constexpr int kAhead = 2;
+    if (!c->host_flags && cudaHostAlloc((void**)&c->host_flags, 8 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->host_flags = nullptr;
+    }
+    for (int q = 0; q < 8 && c->host_flags; ++q)
+        if (!c->iter_ev[q] && cudaEventCreateWithFlags(&c->iter_ev[q], cudaEventDisableTiming) != cudaSuccess)
+            return lss_check_cuda(c, cudaGetLastError(), "iteration events");
     while (true) {
+        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); scale_kernel<<<dim3(g1, R), 256, 0, s>>>(rv, V, K.scdev, N); }
+        const int nj = std::min(m, maxit - total);
+        for (int j = 0; j < nj; ++j) {
+            bool graphed = false;
+            if ((rc = launch_iteration(j, graphed))) return rc;
+            if (!graphed || !c->host_flags) {   // kernel by kernel: stop as soon as every RHS converged
+                cudaError_t e = cudaMemcpyAsync(&any, gs.any, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (!e) e = cudaStreamSynchronize(s);
+                if ((rc = lss_check_cuda(c, e, "arnoldi status"))) return rc;
+                if (!any) break;
+                continue;
+            }
+            cudaError_t e = cudaMemcpyAsync(c->host_flags + (j & 7), gs.any, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (!e) e = cudaEventRecord(c->iter_ev[j & 7], s);
+            if (!e && j >= kAhead) e = cudaEventSynchronize(c->iter_ev[(j - kAhead) & 7]);
+            if ((rc = lss_check_cuda(c, e, "arnoldi status"))) return rc;
+            if (j >= kAhead && !*(volatile int*)(c->host_flags + ((j - kAhead) & 7))) break;
+        }
+        // once per cycle: steps taken, convergence
+        cudaError_t e = cudaMemcpyAsync(kc.data(), gs.kc, R * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaMemcpyAsync(done.data(), gs.done, R * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (!e) e = cudaStreamSynchronize(s);
+        if ((rc = lss_check_cuda(c, e, "krylov cycle state"))) return rc;
+        const int J = *std::max_element(kc.begin(), kc.end());
+        total += J;
+        if (J > 0) {   // x += Z y with y from each RHS's triangular system
+            ProfScope ps_(c, s, LSS_PROF_KRYLOV, 2);
+            backsolve_kernel<<<1, small, 0, s>>>(gs, K.hdev, R, m, J);
+            update_kernel<<<dim3(g1, R), 256, 0, s>>>(Z, RN, K.hdev, J, u, N, R, +1.0);
+        }
         bool all_done = true;
         for (int r = 0; r < R; ++r) all_done &= (bool)done[r];
-        if (all_done || total >= maxit) break;
-        std::vector<int> active(R), kr(R, 0);
-        for (int r = 0; r < R; ++r) {
-            active[r] = !done[r];
-            sc[r] = active[r] ? 1.0 / beta[r] : 0.0;
-            rho[(size_t)r * (m + 1)] = beta[r];
-            for (int i = 1; i <= m; ++i) rho[(size_t)r * (m + 1) + i] = 0.0;
-        }
-        if ((rc = set_scale())) return rc;
-        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); scale_kernel<<<dim3(g1, R), 256, 0, s>>>(rv, V, K.scdev, N); }
-        int j = 0;
-        for (; j < m && total < maxit; ++j) {
-            if ((rc = iteration(j))) return rc;
-            // fetch h (first pass), h2 (second pass) and ||w||^2
-            const size_t cnt = (size_t)(j + 1) * R;
-            std::vector<double2> h1(cnt), h2v(cnt), hn(R);
-            cudaError_t e = cudaMemcpyAsync(h1.data(), K.hdev, cnt * sizeof(double2), cudaMemcpyDeviceToHost, s);
-            if (!e) e = cudaMemcpyAsync(h2v.data(), K.h2dev, cnt * sizeof(double2), cudaMemcpyDeviceToHost, s);
-            if (!e) e = cudaMemcpyAsync(hn.data(), hnorm, R * sizeof(double2), cudaMemcpyDeviceToHost, s);
-            if (!e) e = cudaStreamSynchronize(s);
-            if ((rc = lss_check_cuda(c, e, "arnoldi fetch"))) return rc;
-            ++total;
-            for (int r = 0; r < R; ++r) {
-                if (!active[r]) { sc[r] = 0.0; continue; }
-                for (int i = 0; i <= j; ++i)
-                    Hix(i, j, r) = cd(h1[(size_t)i * R + r].x + h2v[(size_t)i * R + r].x,
-                                      h1[(size_t)i * R + r].y + h2v[(size_t)i * R + r].y);
-                const double hnr = std::sqrt(std::max(0.0, hn[r].x));
-                Hix(j + 1, j, r) = hnr;
-                sc[r] = hnr > 0 ? 1.0 / hnr : 0.0;
-                for (int i = 0; i < j; ++i) {
-                    const cd a = Hix(i, j, r), b = Hix(i + 1, j, r);
-                    const cd cc = cs[(size_t)r * m + i], ss = sn[(size_t)r * m + i];
-                    Hix(i, j, r) = cc * a + ss * b;
-                    Hix(i + 1, j, r) = -std::conj(ss) * a + std::conj(cc) * b;
-                }
-                const cd a = Hix(j, j, r), b = Hix(j + 1, j, r);
-                const double den = std::sqrt(std::norm(a) + std::norm(b));
-                const cd cc = den > 0 ? std::conj(a) / den : cd(1.0);
-                const cd ss = den > 0 ? std::conj(b) / den : cd(0.0);
-                cs[(size_t)r * m + j] = cc;
-                sn[(size_t)r * m + j] = ss;
-                Hix(j, j, r) = cc * a + ss * b;
-                Hix(j + 1, j, r) = 0.0;
-                cd& rj = rho[(size_t)r * (m + 1) + j];
-                rho[(size_t)r * (m + 1) + j + 1] = -std::conj(ss) * rj;
-                rj = cc * rj;
-                iters[r] += 1;
-                kr[r] = j + 1;
-                est[r] = std::abs(rho[(size_t)r * (m + 1) + j + 1]) / gnorm[r];
-                if (est[r] <= tol || hnr == 0.0) {
-                    done[r] = 1;
-                    active[r] = 0;
-                }
-            }
-            if ((rc = set_scale())) return rc;
-            { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); scale_kernel<<<dim3(g1, R), 256, 0, s>>>(w, V + (size_t)(j + 1) * RN, K.scdev, N); }
-            bool any = false;
-            for (int r = 0; r < R; ++r) any |= (bool)active[r];
-            if (!any) { ++j; break; }
-        }
-        // x += Z y with y from the triangular system of each RHS
-        const int J = *std::max_element(kr.begin(), kr.end());
-        if (J > 0) {
-            std::vector<double2> yh((size_t)J * R, make_double2(0, 0));
-            for (int r = 0; r < R; ++r) {
-                const int k = kr[r];
-                std::vector<cd> y(k);
-                for (int i = k - 1; i >= 0; --i) {
-                    cd acc = rho[(size_t)r * (m + 1) + i];
-                    for (int l = i + 1; l < k; ++l) acc -= Hix(i, l, r) * y[l];
-                    y[i] = acc / Hix(i, i, r);
-                }
-                for (int i = 0; i < k; ++i) yh[(size_t)i * R + r] = make_double2(y[i].real(), y[i].imag());
-            }
-            cudaMemcpyAsync(K.hdev, yh.data(), yh.size() * sizeof(double2), cudaMemcpyHostToDevice, s);
-            { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, s>>>(Z, RN, K.hdev, J, u, N, R, +1.0); }
-        }
-        all_done = true;
-        for (int r = 0; r < R; ++r) all_done &= (bool)done[r];
-        if (all_done || total >= maxit) break;
+        if (all_done || total >= maxit || J == 0) break;
         // restart: r = g - A u
         if ((rc = lss_matvec(c, u, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
-        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs, 256, 0, s>>>(g, w, rv, RN); }
+        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs_grid, 256, 0, s>>>(g, w, rv, RN); }
         dots(K, rv, 0, 1, rv, K.hdev, 0);
-        if ((rc = fetch(K.hdev, R))) return rc;
-        for (int r = 0; r < R; ++r) beta[r] = std::sqrt(std::max(0.0, hh[r].x));
+        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); cycle_init_kernel<<<1, small, 0, s>>>(gs, K.hdev, K.scdev, R, m, 0, o->tol); }
     }
     // true residual
     if ((rc = lss_matvec(c, u, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
-    { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs, 256, 0, s>>>(g, w, rv, RN); }
+    { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs_grid, 256, 0, s>>>(g, w, rv, RN); }
     dots(K, rv, 0, 1, rv, K.hdev, 0);
-    if ((rc = fetch(K.hdev, R))) return rc;
+    std::vector<double2> hh(R);
+    cudaError_t e = cudaMemcpyAsync(hh.data(), K.hdev, R * sizeof(double2), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(iters.data(), gs.iters, R * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(est.data(), gs.est, R * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(gnorm.data(), gs.gnorm, R * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaMemcpyAsync(done.data(), gs.done, R * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if ((rc = lss_check_cuda(c, e, "krylov fetch"))) return rc;
     bool conv = true;
     for (int r = 0; r < R; ++r) {
         const double rt = gnorm[r] > 0 ? std::sqrt(std::max(0.0, hh[r].x)) / gnorm[r] : 0.0;
-        const bool cv = gnorm[r] == 0.0 || est[r] <= tol;
+        const bool cv = gnorm[r] == 0.0 || est[r] <= o->tol;
         conv &= cv;
         if (st) {
             st[r].iters = iters[r];
@@ -349,11 +479,12 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         }
     }
     if ((rc = lss_check_device_err(c, s))) return rc;
-    if (use_graph && !warm) {   // later solves with this R and transpose replay captured iterations
-        std::vector<std::array<long long, 3>> keep;
+    if (use_graph && !warm) {   // later solves with this R, transpose and m replay captured iterations
+        std::vector<std::array<long long, 4>> keep;
         for (const auto& k : c->graph_warm)
-            if ((unsigned long long)k[2] == c->buf_gen && !(k[0] == R && k[1] == transpose)) keep.push_back(k);
-        keep.push_back({(long long)R, (long long)transpose, (long long)c->buf_gen});
+            if ((unsigned long long)k[2] == c->buf_gen && !(k[0] == R && k[1] == transpose && k[3] == m))
+                keep.push_back(k);
+        keep.push_back({(long long)R, (long long)transpose, (long long)c->buf_gen, (long long)m});
         c->graph_warm.swap(keep);
     }
     return conv ? LSS_OK : lss_fail(c, LSS_ERR_NOCONVERGE, "GMRES reached max_iter before tol");

@@ -34,6 +34,7 @@ namespace {
 constexpr int kMaxBlock3 = 1600;      // largest pivot block M = w * n_tot (panel kernel shared memory)
 constexpr int kNB64 = 8;              // Gauss-Jordan panel width, FP64
 constexpr int kNB32 = 16;             // Gauss-Jordan panel width, FP32
+constexpr int kNO = 64;               // outer panel width of the tensor-core path
 constexpr int kSweepThreads = 512;
 constexpr int kSweepRB = 4;           // right-hand sides per sweep launch
 
@@ -672,14 +673,15 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
     }
 }
 
-// Outside the panel columns: apply the panel's row swaps, move the pivot rows'
-// entries into T (T[jj][c], zero for c in J) and zero them in W.  The swaps
-// touch at most 2 nbp rows; their composition (row x receives the old row
-// src[x]) is worked out once per CTA, then every column is a gather: all
+// Outside the panel columns: apply the panel's row swaps; for the columns in
+// [c_lo, c_hi) also move the pivot rows' entries into T (T[jj][c], zero for c
+// in J) and zero them in W (the columns the following update covers).  The
+// swaps touch at most 2 nbp rows; their composition (row x receives the old
+// row src[x]) is worked out once per CTA, then every column is a gather: all
 // loads first, then the stores.
 template <typename C, int NB>
 __global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__ W, const int* __restrict__ piv,
-                                C* __restrict__ T, int j0, int Tld) {
+                                C* __restrict__ T, int j0, int Tld, int c_lo, int c_hi) {
     __shared__ int rows[2 * NB], src[2 * NB], nrows_s;
     const int slab = blockIdx.y;
     const Slab3 sd = slabs[slab];
@@ -711,8 +713,10 @@ __global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__
     C* w = W + sd.w_off;
     C* t = T + (long long)slab * NB * Tld;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        const bool local = c >= c_lo && c < c_hi;
         if (c >= j0 && c < j0 + nbp) {
-            for (int jj = 0; jj < nbp; ++jj) t[(long long)jj * Tld + c] = czero<C>();
+            if (local)
+                for (int jj = 0; jj < nbp; ++jj) t[(long long)jj * Tld + c] = czero<C>();
             continue;
         }
         C v[2 * NB];
@@ -722,7 +726,7 @@ __global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__
 #pragma unroll
         for (int q = 0; q < 2 * NB; ++q) {
             if (q >= na) break;
-            if (q < nbp) {
+            if (q < nbp && local) {
                 t[(long long)q * Tld + c] = v[q];
                 w[(long long)rows[q] * M + c] = czero<C>();
             } else {
@@ -732,11 +736,12 @@ __global__ void f3_swap_extract(const Slab3* __restrict__ slabs, C* __restrict__
     }
 }
 
-// W[i][c] += sum_kk W[i][j0+kk] T[kk][c] for c outside J (CUDA cores).
-// 64 x 64 output tiles, 256 threads, 4 x 4 entries each.  grid (tiles, slabs).
+// W[i][c] += sum_kk W[i][j0+kk] T[kk][c] for c in [c_lo, c_hi) outside J
+// (CUDA cores).  64 x 64 output tiles, 256 threads, 4 x 4 entries each.
+// grid (row tiles x column tiles of the range, slabs).
 template <typename C, int NB>
 __global__ void __launch_bounds__(256) f3_update_cc(const Slab3* __restrict__ slabs, C* __restrict__ W,
-                                                    const C* __restrict__ T, int j0, int Tld) {
+                                                    const C* __restrict__ T, int j0, int Tld, int c_lo, int c_hi) {
     __shared__ C As[64][NB];
     __shared__ C Ts[NB][64];
     const int slab = blockIdx.y;
@@ -744,9 +749,11 @@ __global__ void __launch_bounds__(256) f3_update_cc(const Slab3* __restrict__ sl
     const int M = sd.M;
     if (j0 >= M) return;
     const int nbp = min(NB, M - j0);
-    const int tiles = (M + 63) / 64;
-    if ((int)blockIdx.x >= tiles * tiles) return;
-    const int i0 = (blockIdx.x / tiles) * 64, c0 = (blockIdx.x % tiles) * 64;
+    const int ce = min(c_hi, M);
+    if (ce <= c_lo) return;
+    const int tiles = (M + 63) / 64, ctiles = (ce - c_lo + 63) / 64;
+    if ((int)blockIdx.x >= tiles * ctiles) return;
+    const int i0 = (blockIdx.x / ctiles) * 64, c0 = c_lo + (blockIdx.x % ctiles) * 64;
     C* w = W + sd.w_off;
     const C* t = T + (long long)slab * NB * Tld;
     const int tid = threadIdx.x;
@@ -756,7 +763,7 @@ __global__ void __launch_bounds__(256) f3_update_cc(const Slab3* __restrict__ sl
     }
     for (int e = tid; e < NB * 64; e += 256) {
         const int q = e / 64, c = e % 64;
-        Ts[q][c] = (c0 + c < M && q < nbp) ? t[(long long)q * Tld + c0 + c] : czero<C>();
+        Ts[q][c] = (c0 + c < ce && q < nbp) ? t[(long long)q * Tld + c0 + c] : czero<C>();
     }
     __syncthreads();
     const int tx = tid % 16, ty = tid / 16;
@@ -776,9 +783,32 @@ __global__ void __launch_bounds__(256) f3_update_cc(const Slab3* __restrict__ sl
         if (i >= M) continue;
         for (int v = 0; v < 4; ++v) {
             const int c = c0 + tx + 16 * v;
-            if (c >= M || (c >= j0 && c < j0 + nbp)) continue;
+            if (c >= ce || (c >= j0 && c < j0 + nbp)) continue;
             C* p = w + (long long)i * M + c;
             *p = *p + acc[u][v];
+        }
+    }
+}
+
+// The outer panel [J0, J0 + nbo) is eliminated (its rows are already swapped
+// everywhere): for the columns outside it move the pivot rows into T64
+// (T64[kk][c], kk < nbo) and zero them in W; zero T64 inside the panel.
+template <typename C>
+__global__ void f3_extract_outer(const Slab3* __restrict__ slabs, C* __restrict__ W, C* __restrict__ T64, int J0,
+                                 int NO, int Tld) {
+    const int slab = blockIdx.y;
+    const Slab3 sd = slabs[slab];
+    const int M = sd.M;
+    if (J0 >= M) return;
+    const int nbo = min(NO, M - J0);
+    C* w = W + sd.w_off;
+    C* t = T64 + (long long)slab * NO * Tld;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+        const bool inside = c >= J0 && c < J0 + nbo;
+        for (int kk = 0; kk < nbo; ++kk) {
+            C* p = w + (long long)(J0 + kk) * M + c;
+            t[(long long)kk * Tld + c] = inside ? czero<C>() : *p;
+            if (!inside) *p = czero<C>();
         }
     }
 }
@@ -1074,7 +1104,7 @@ void lss3_free(lss_ctx* c) {
     if (!d) return;
     void* ptrs[] = {d->d_slabs, d->khat, d->gam_phys, d->gam_aux, d->coef64, d->coef == d->coef64 ? nullptr : d->coef,
                     d->fac, d->W, d->X, d->T, d->piv, d->rowid, d->f, d->ut, d->Y, d->mvA, d->mvB, d->TB,
-                    d->steps_all, d->steps_one};
+                    d->steps_all, d->steps_one, d->T64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete d;
@@ -1307,6 +1337,7 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
     rc = rc ? rc : dalloc3(c, &d->W, (size_t)wo * cs, "pivot blocks");
     rc = rc ? rc : dalloc3(c, &d->X, (size_t)wo * cs, "Schur scratch");
     rc = rc ? rc : dalloc3(c, &d->T, (size_t)nl * NB * d->Mmax * cs, "panel rows");
+    if (c->prec == LSS_MIXED) rc = rc ? rc : dalloc3(c, &d->T64, (size_t)nl * kNO * d->Mmax * cs, "outer panel rows");
     rc = rc ? rc : dalloc3(c, (void**)&d->piv, (size_t)nl * NB * sizeof(int), "pivots");
     rc = rc ? rc : dalloc3(c, (void**)&d->rowid, (size_t)nl * d->Mmax * sizeof(int), "row ids");
     rc = rc ? rc : dalloc3(c, (void**)&d->d_slabs, nl * sizeof(Slab3), "slabs");
@@ -1376,21 +1407,43 @@ int factor3_t(lss_ctx* c, cudaStream_t s) {
             c->launches[LSS_PROF_FACTOR] += 2;
         }
         f3_rowid_init<<<dim3(1, nl), 256, 0, s>>>(d->d_slabs, d->rowid, Mmax);
-        for (int p = 0; p < npanel; ++p) {
-            const int j0 = p * NB;
-            f3_panel<C, NB><<<nl, 512, psm, s>>>(d->d_slabs, W, d->piv, d->rowid, j0, Mmax, c->d_err);
-            f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, d->piv, T, j0, Mmax);
-            if constexpr (std::is_same<C, float2>::value) {
-                if (use_tc) {
-                    const int rc = lss3_update_tc(c, W, T, j0, s);
-                    if (rc) return rc;
-                    continue;
-                }
+        if (!use_tc) {
+            for (int p = 0; p < npanel; ++p) {
+                const int j0 = p * NB;
+                f3_panel<C, NB><<<nl, 512, psm, s>>>(d->d_slabs, W, d->piv, d->rowid, j0, Mmax, c->d_err);
+                f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, d->piv, T, j0,
+                                                                                   Mmax, 0, Mmax);
+                f3_update_cc<C, NB><<<dim3(tiles * tiles, nl), 256, 0, s>>>(d->d_slabs, W, T, j0, Mmax, 0, Mmax);
             }
-            f3_update_cc<C, NB><<<dim3(tiles * tiles, nl), 256, 0, s>>>(d->d_slabs, W, T, j0, Mmax);
+            c->launches[LSS_PROF_FACTOR] += 3LL * npanel;
+        } else if constexpr (std::is_same<C, float2>::value) {
+            // outer panels of kNO columns: four NB-wide Gauss-Jordan sub-panels,
+            // each applying its row swaps to every column and its update to the
+            // outer panel's columns only, then one rank-kNO update of all other
+            // columns on the tensor cores
+            const int nouter = (Mmax + kNO - 1) / kNO;
+            const int otiles = (kNO + 63) / 64;
+            for (int P = 0; P < nouter; ++P) {
+                const int J0 = P * kNO;
+                for (int q = 0; q < kNO / NB; ++q) {
+                    const int j0 = J0 + q * NB;
+                    if (j0 >= Mmax) break;
+                    f3_panel<C, NB><<<nl, 512, psm, s>>>(d->d_slabs, W, d->piv, d->rowid, j0, Mmax, c->d_err);
+                    f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, d->piv, T,
+                                                                                       j0, Mmax, J0, J0 + kNO);
+                    f3_update_cc<C, NB><<<dim3(tiles * otiles, nl), 256, 0, s>>>(d->d_slabs, W, T, j0, Mmax, J0,
+                                                                               J0 + kNO);
+                    c->launches[LSS_PROF_FACTOR] += 3;
+                }
+                f3_extract_outer<C><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, (C*)d->T64, J0, kNO,
+                                                                                Mmax);
+                const int rc = lss3_update_tc(c, (float2*)W, (const float2*)d->T64, J0, kNO, s);
+                if (rc) return rc;
+                c->launches[LSS_PROF_FACTOR] += 2;
+            }
         }
         f3_finalize<C><<<dim3(ew_blocks, nl), 256, Mmax * sizeof(int), s>>>(d->d_slabs, W, d->rowid, fac, k, Mmax);
-        c->launches[LSS_PROF_FACTOR] += 2 + 3LL * npanel;
+        c->launches[LSS_PROF_FACTOR] += 2;
         const int rc = lss_check_cuda(c, cudaGetLastError(), "3D factorization launch");
         if (rc) return rc;
     }

@@ -33,6 +33,7 @@ struct Ctx3 {
     void* W = nullptr;            // pivot block being inverted, one per slab
     void* X = nullptr;            // Schur scratch D_{k-1}^{-1} B_{k-1}, one per slab
     void* T = nullptr;            // pivot rows of the current panel, per slab NB x Mmax
+    void* T64 = nullptr;          // pivot rows of the current outer panel (tensor-core path), per slab 64 x Mmax
     int* piv = nullptr;           // pivot rows of the current panel, per slab NB
     int* rowid = nullptr;         // original row of each position, per slab Mmax
     long long w_len = 0;
@@ -57,7 +58,7 @@ int lss3_matvec(lss_ctx* c, const double2* x, double2* y, int R, int in_mode, in
                 double2* uI, cudaStream_t s);
 int lss3_get_stencils(const lss_ctx* c, double* alpha, double* beta);
 // tc_update.cu: rank-16 Gauss-Jordan update of the FP32 pivot blocks on the tensor cores (3xTF32)
-int lss3_update_tc(lss_ctx* c, float2* W, const float2* T, int j0, cudaStream_t s);
+int lss3_update_tc(lss_ctx* c, float2* W, const float2* T64, int J0, int NO, cudaStream_t s);
 bool lss3_use_tc();
 
 // greens.cu: cyclic Jacobi eigen-decomposition of a real symmetric matrix

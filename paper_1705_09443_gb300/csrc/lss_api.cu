@@ -31,10 +31,13 @@ void free_ctx(lss_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto e : c->iter_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->host_flags) cudaFreeHost(c->host_flags);
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
                     c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->iface_t, c->d_slabs,
                     c->d_err, c->d_bar, c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf,
-                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf};
+                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->chunk_dev)
@@ -43,6 +46,21 @@ void free_ctx(lss_ctx* c) {
 }
 
 bool is_batch(const lss_ctx* c) { return !c->inst.empty(); }
+
+// Waits on a grid barrier one arrival short of its target and on an mbarrier
+// nobody arrives at: both expire after the library's wait limit and set
+// LSS_DERR_TIMEOUT; a third wait then returns at once (the flag is set).
+__global__ void wait_selftest_kernel(unsigned* counter, int* err) {
+    __shared__ uint64_t bar;
+    grid_barrier_count(counter, 2u, err);     // one block: the second arrival never comes
+    if (threadIdx.x == 0) {
+        atomicAnd(err, ~LSS_DERR_TIMEOUT);    // re-arm for the mbarrier wait
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_wait(&bar, 0u, err);             // nothing arrives on phase 0
+        grid_barrier_count(counter, 4u, err); // flag set: returns without waiting
+    }
+}
 
 int batch_only_per_instance(lss_ctx* c, const char* what) {
     return lss_fail(c, LSS_ERR_ARG, std::string(what) + ": not defined on a batch context; call it on an instance "
@@ -511,6 +529,39 @@ int lss_get_stencils(const lss_ctx* c, double* alpha, double* beta) {
         beta[2 * o + 1] = c->beta[o].imag();
     }
     return LSS_OK;
+}
+
+int lss_test_inject(lss_ctx* c, int what, int a, long long b, void* stream) {
+    if (!c || is_batch(c)) return LSS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (what == 1) {   // zero the coefficients of block row b of slab a
+        if (a < 0 || a >= c->n_slabs || b < 0 || b >= c->n_tot) return lss_fail(c, LSS_ERR_ARG, "test_inject: bad slab/row");
+        if (c->dim == 3) {
+            const Slab3& sd = c->d3->slabs[a];
+            const long long off = sd.cf_off + (b * 3 + 1) * (long long)sd.M * 9, len = (long long)sd.M * 9;
+            cudaMemsetAsync(c->d3->coef64 + off, 0, len * sizeof(double2), s);
+            if (c->d3->coef != c->d3->coef64) cudaMemsetAsync((float2*)c->d3->coef + off, 0, len * sizeof(float2), s);
+        } else {
+            const SlabDev& sd = c->slabs[a];
+            const long long off = sd.coef_off + b * (long long)sd.cstride, len = sd.cstride;
+            cudaMemsetAsync(c->coef64 + off, 0, len * sizeof(double2), s);
+            if (c->coef != c->coef64) cudaMemsetAsync((float2*)c->coef + off, 0, len * sizeof(float2), s);
+        }
+        c->factored = false;
+        return lss_check_cuda(c, cudaStreamSynchronize(s), "test_inject");
+    }
+    if (what == 2) {   // bounded device waits that expire
+        unsigned* counter = nullptr;
+        int rc = dalloc(c, (void**)&counter, sizeof(unsigned), "test counter");
+        if (rc) return rc;
+        cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+        wait_selftest_kernel<<<1, 32, 0, s>>>(counter, c->d_err);
+        rc = lss_check_cuda(c, cudaStreamSynchronize(s), "wait self-test");
+        cudaFree(counter);
+        if (rc) return rc;
+        return lss_check_device_err(c, s);
+    }
+    return lss_fail(c, LSS_ERR_ARG, "test_inject: unknown injection");
 }
 
 const char* lss_last_error(const lss_ctx* c) { return c ? c->err.c_str() : g_setup_error.c_str(); }

@@ -181,12 +181,15 @@ struct lss_ctx {
     // cap_stream once a first uncaptured solve with the same R and transpose
     // has grown every workspace; a graph is dropped when a workspace moves
     // (buf_gen changes).
-    struct GraphRec { int j, R, transpose; unsigned long long gen; cudaGraphExec_t exec; };
+    struct GraphRec { int j, R, transpose, m; unsigned long long gen; cudaGraphExec_t exec; };
     bool graphs_on = true;
     unsigned long long buf_gen = 0;
     cudaStream_t cap_stream = nullptr;
     std::vector<GraphRec> graphs;
-    std::vector<std::array<long long, 3>> graph_warm;   // (R, transpose, buf_gen) solved once uncaptured
+    std::vector<std::array<long long, 4>> graph_warm;   // (R, transpose, buf_gen, m) solved once uncaptured
+    void* gm_buf = nullptr; size_t gm_cap = 0;          // device GMRES state (Hessenberg, rotations, masks)
+    int* host_flags = nullptr;                          // pinned host copies of the "RHS active" flag per iteration
+    cudaEvent_t iter_ev[8] = {};                        // completion of the last iterations' flag copies
 
     // ragged batch (lss_setup_batch): one full context per instance, each with
     // its own stream and completion event; empty for an ordinary context

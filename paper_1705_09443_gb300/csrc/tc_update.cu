@@ -1,9 +1,11 @@
-// Tensor-core rank-NB update of the 3D pivot-block inversion (mixed precision):
-//     W[i][c] += sum_{kk < nbp} W[i][j0 + kk] T[kk][c]      (c outside the panel)
-// for every slab, complex FP32, as one real product per 128 x 128 complex tile:
-// A' (128 x 2nbp, the panel rows' re/im interleaved, exactly their FP32
-// layout) times B' (2nbp x 256, each T entry as the 2 x 2 block
-// [[re, im], [-im, re]]), accumulated in FP32 in tensor memory.  Each operand
+// Tensor-core update of the 3D pivot-block inversion (mixed precision) after an
+// outer panel of up to 64 columns J = [J0, J0 + nbo) has been eliminated:
+//     W[i][c] += sum_{kk < nbo} W[i][J0 + kk] T64[kk][c]      (c outside J)
+// for every slab, complex FP32, as one real product per 128 x 128 complex tile,
+// taken in K chunks of 16 complex columns accumulated in tensor memory:
+// A' (128 x 32 per chunk, the panel rows' re/im interleaved, exactly their
+// FP32 layout) times B' (32 x 256 per chunk, each T64 entry as the 2 x 2
+// block [[re, im], [-im, re]]).  Each operand
 // is split into TF32 parts x = big + small (big = x rounded to TF32, small =
 // the FP32 remainder) and the product taken as big*big + big*small +
 // small*big (3xTF32), which keeps about 22 bits of every product.
@@ -85,8 +87,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // Persistent: CTA loops over (slab, row tile, column tile) slots.  128 threads.
 __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ slabs, int n_slabs,
-                                                     float2* __restrict__ W, const float2* __restrict__ T, int j0,
-                                                     int Tld, int tmax, int* err) {
+                                                     float2* __restrict__ W, const float2* __restrict__ T64, int J0,
+                                                     int NO, int Tld, int tmax, int* err) {
     extern __shared__ __align__(1024) unsigned char sm[];
     unsigned char* Abig = sm;
     unsigned char* Asml = sm + kABytes;
@@ -119,14 +121,18 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
         const int rem = (int)(slot % ((long long)tmax * tmax));
         const Slab3 sd = slabs[slab];
         const int M = sd.M;
-        if (j0 >= M) continue;
+        if (J0 >= M) continue;
         const int tiles = (M + 127) / 128;
         const int ti = rem / tmax, tj = rem % tmax;
         if (ti >= tiles || tj >= tiles) continue;
-        const int nbp = min(kTcNB, M - j0);
+        const int nbo = min(NO, M - J0);
         const int i0 = ti * 128, c0 = tj * 128;
         float2* w = W + sd.w_off;
-        const float2* t = T + (long long)slab * kTcNB * Tld;
+        const float2* t64 = T64 + (long long)slab * NO * Tld;
+        const int nk = (nbo + kTcNB - 1) / kTcNB;
+        for (int kc = 0; kc < nk && ok; ++kc) {
+        const int j0 = J0 + kc * kTcNB, nbp = min(kTcNB, nbo - kc * kTcNB);
+        const float2* t = t64 + (long long)kc * kTcNB * Tld;
 
         // ---- operands into shared memory
         {   // A: row tid of the tile, panel columns j0.. (2 nbp reals, zero beyond)
@@ -183,7 +189,7 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
         // ---- 3xTF32 product: big*big + big*small + small*big, K = 8 per instruction
         if (tid == 0) {
             const uint32_t ab = smem_u32(Abig), as = smem_u32(Asml), bb = smem_u32(Bbig), bs = smem_u32(Bsml);
-            uint32_t acc = 0;
+            uint32_t acc = kc > 0;
             for (int part = 0; part < 3; ++part) {
                 const uint32_t pa = part == 2 ? as : ab;
                 const uint32_t pb = part == 1 ? bs : bb;
@@ -199,6 +205,9 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
         if (!mbar_wait(bar, phase, err)) ok = false;
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the next chunk's operand writes must not overtake this chunk's products
+        __syncthreads();
+        }   // K chunks
         if (!ok) break;
 
         // ---- epilogue, 8 chunks of 16 complex columns: each thread moves its
@@ -215,7 +224,7 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
             for (int e = tid; e < 128 * 16; e += 128) {
                 const int row = e >> 4, q = e & 15;
                 const int i = i0 + row, c = c0 + ch * 16 + q;
-                if (i >= M || c >= M || (c >= j0 && c < j0 + nbp)) continue;
+                if (i >= M || c >= M || (c >= J0 && c < J0 + nbo)) continue;
                 float2* p = w + (long long)i * M + c;
                 float2 o = *p;
                 o.x += S[row * 33 + 2 * q];
@@ -242,8 +251,9 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
 
 }  // namespace
 
-// Launches the tensor-core update for panel j0 of every slab (FP32 factors).
-int lss3_update_tc(lss_ctx* c, float2* W, const float2* T, int j0, cudaStream_t s) {
+// Launches the tensor-core update for the outer panel [J0, J0 + NO) of every
+// slab (FP32 factors).
+int lss3_update_tc(lss_ctx* c, float2* W, const float2* T64, int J0, int NO, cudaStream_t s) {
     Ctx3* d = c->d3;
     static int configured_dev = -1;
     int dev = 0;
@@ -256,13 +266,14 @@ int lss3_update_tc(lss_ctx* c, float2* W, const float2* T, int j0, cudaStream_t 
     const int tmax = (d->Mmax + 127) / 128;
     const long long slots = (long long)c->n_slabs * tmax * tmax;
     const int grid = (int)std::min<long long>(slots, 2LL * c->num_sms);
-    f3_update_tc<<<grid, 128, kTcSmem, s>>>(d->d_slabs, c->n_slabs, W, T, j0, d->Mmax, tmax, c->d_err);
+    f3_update_tc<<<grid, 128, kTcSmem, s>>>(d->d_slabs, c->n_slabs, W, T64, J0, NO, d->Mmax, tmax, c->d_err);
     return lss_check_cuda(c, cudaGetLastError(), "tensor-core update launch");
 }
 
-// The tensor-core update runs when LSS_TC_UPDATE=1 is set in the
-// environment; otherwise the CUDA-core FP32 update runs.
+// The 3D mixed-precision factorization uses the tensor-core update unless
+// LSS_TC_UPDATE=0 is set in the environment (the CUDA-core FP32 update with
+// 16-column panels then runs; both reach the same factors to about 2e-6).
 bool lss3_use_tc() {
     const char* v = std::getenv("LSS_TC_UPDATE");
-    return v && v[0] == '1';
+    return !(v && v[0] == '0');
 }

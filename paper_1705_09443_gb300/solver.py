@@ -157,6 +157,12 @@ class LSSolver:
                                             _stream_ptr(stream)))
         return w
 
+    def test_inject(self, what: int, a: int = 0, b: int = 0, stream=None):
+        """Fault injection for tests (lss_test_inject): 1 = zero block row b of
+        slab a (the next factor meets a zero pivot), 2 = bounded device waits
+        that expire (returns LSS_ERR_TIMEOUT)."""
+        self._check(self.lib.lss_test_inject(self.ctx, int(what), int(a), int(b), _stream_ptr(stream)))
+
     def solve(self, g: torch.Tensor, opts: GmresOptions | None = None, stream=None, raise_on_noconv=True):
         o = opts or GmresOptions()
         g = _c128(self._batch(g))

@@ -129,6 +129,23 @@ def test_solution_matches_oracle_fp64(n8):
     assert abs(st8[0]["iters"] - ref8.iters) <= 1
 
 
+def test_mixed_factorization_paths_agree(n8, monkeypatch):
+    """The mixed 3D factorization on the tensor cores (3xTF32 rank-64 updates,
+    the default) and on CUDA cores (FP32 rank-16 updates) give the same P to
+    single-precision accuracy, both close to the oracle's FP64 P."""
+    s64, m, om, pb = n8
+    x = crand((8, 8, 8), 23)
+    ref = pb.precondition(x)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LSS_TC_UPDATE", flag)
+        from paper_1705_09443_gb300 import LSS_MIXED
+        s32, _, _ = case(8, 3, 3, precision=LSS_MIXED)
+        out.append(s32.apply_P(to_dev(x[None])).cpu().numpy()[0])
+    assert rel(out[0], out[1]) <= 1e-5
+    assert rel(out[0], ref) <= 1e-4 and rel(out[1], ref) <= 1e-4
+
+
 def test_mixed_precision_within_two_iterations(n8):
     from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED
     s64, m, om, pb = n8

@@ -156,3 +156,27 @@ def test_gradient_matches_central_differences():
                 vals.append(float(loss(ls_solve(mp, s, dirs, opts))))
         fd = (vals[0] - vals[1]) / (2 * step)
         assert abs(grad[a, b] - fd) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(grad).max()), (a, b, grad[a, b], fd)
+
+
+def test_gradient_matches_oracle_dense_adjoint():
+    """dL/dm through autograd (adjoint solve + lss_medium_gradient) against the
+    oracle's dense-adjoint gradient of the same receiver misfit (n = 14, two
+    plane waves, eight receivers; dense solves on the oracle side)."""
+    from paper_1705_09443_gb300 import GmresOptions, LSSolver, ls_solve
+    n = 14
+    om = 2 * math.pi * 2.0
+    m = synth.gaussian_medium(n, 2, 3, 0.12, (0.85, 1.15), 31)
+    dirs = np.array([[1.0, 0.0], [0.6, 0.8]])
+    rng = np.random.default_rng(32)
+    rcv = rng.integers(0, n, size=(8, 2))
+    data = (rng.standard_normal((2, 8)) + 1j * rng.standard_normal((2, 8))) * 1e-2
+    ref = O.misfit_gradient_dense(n, om, m, dirs, rcv, data)
+    mt = torch.tensor(m, dtype=torch.float64, device="cuda")
+    s = LSSolver(n, om, mt, b_pml=4, b_slab=3)
+    rows = torch.tensor(rcv[:, 0], device="cuda")
+    cols = torch.tensor(rcv[:, 1], device="cuda")
+    d = to_dev(data)
+    mg = mt.clone().requires_grad_(True)
+    u = ls_solve(mg, s, dirs, GmresOptions(30, 1e-13, 300))
+    (0.5 * (u[:, rows, cols] - d).abs().pow(2).sum()).backward()
+    assert rel(mg.grad.cpu().numpy(), ref) <= 1e-8
