@@ -985,3 +985,42 @@ def misfit_gradient_dense(n, omega, m, dirs, receivers, data, kw=None):
         Klam_w2 = ls_apply(lam, one, omega, kw) - lam           # omega^2 K lambda
         grad += np.real(-Klam_w2 * (u + uI))
     return grad
+
+
+# --------------------------------------------------------------------------
+# Sec. 4: the sparsifying scheme as a direct discretization of Helmholtz
+# --------------------------------------------------------------------------
+
+
+def helmholtz_rhs(pb, f):
+    """F = beta^* f_{mu_i} on I^h, 0 on the PML, f zero off I (Sec. 4: the
+    right-hand side of alpha^* u_{mu_i} = beta^* f_{mu_i}).  2D grid (n_tot, n_tot)."""
+    n, b, nt = pb.n, pb.b, pb.n_tot
+    fp = np.zeros((n + 4, n + 4), dtype=np.complex128)     # indices -1..n+2
+    fp[2:n + 2, 2:n + 2] = f
+    F = np.zeros((nt, nt), dtype=np.complex128)
+    bc = np.conj(pb.beta).reshape(3, 3)
+    for da in (-1, 0, 1):
+        for db in (-1, 0, 1):
+            F[b:b + n + 2, b:b + n + 2] += bc[da + 1, db + 1] * fp[1 + da:n + 3 + da, 1 + db:n + 3 + db]
+    return F
+
+
+def helmholtz_direct(pb, f):
+    """Solve the sparsified system H u~ = beta^* f (Sec. 4) exactly (sparse LU)
+    for a source f on I; H has the alpha rows (with the medium's beta terms,
+    so a medium m gives the heterogeneous equation) and the PML rows.
+    Returns u on I and the full grid solution."""
+    H = pb.assemble_H().tocsc()
+    F = helmholtz_rhs(pb, f)
+    ut = spla.spsolve(H, F.reshape(-1)).reshape(F.shape)
+    return pb.extract(ut), ut
+
+
+def delta_source(n, point):
+    """Discrete delta of unit mass at the grid point `point` (indices 1..n):
+    f = 1/h^2 there, 0 elsewhere."""
+    h = 1.0 / (n + 1)
+    f = np.zeros((n, n), dtype=np.complex128)
+    f[point[0] - 1, point[1] - 1] = 1.0 / (h * h)
+    return f
