@@ -252,7 +252,8 @@ def make_solver(w, m_dev, prec, dev):
 def run_headline(args, dev, world, flush):
     """Mixed precision, all right-hand sides of the workload in one solve call;
     full steps timed; profiling pass; solve-only; error against FP64; e2e
-    through the host-buffer entry point."""
+    through the host-buffer entry point (the last three skipped with
+    --only-headline)."""
     import torch
     from paper_1705_09443_gb300 import GmresOptions, LSS_FP64, LSS_MIXED
     w = synth.WORKLOADS[args.workload]
@@ -283,6 +284,9 @@ def run_headline(args, dev, world, flush):
                iters=iters, relres_true_max=max(x["relres_true"] for x in flat),
                converged=all(x["relres_true"] <= 1e-8 for x in flat), clocks=clocks, autotune=tuned,
                prof_ms=prof_ms, prof_launches=prof_n, gpu_launches_per_step=int(sum(prof_n.values())))
+    if args.only_headline:
+        res["solver"] = s
+        return w, R, res
     # solve only (factors in place, right-hand sides resident)
     g = s.plane_wave_rhs(dirs)
     ts_s, _ = timed(lambda: s.solve(g, opts), args.steps, 1, flush, stream)
@@ -577,6 +581,9 @@ def main():
     ap.add_argument("--fp64-sample", type=int, default=8, help="single-RHS FP64 solves timed (scaled to R)")
     ap.add_argument("--legs", default="2d_n256,3d_n64", help="further full-step legs ('' to skip)")
     ap.add_argument("--ragged", type=int, default=32, help="instances of the ragged batch line (0 to skip)")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="run the headline workload's steps only (warm-up, timed steps, the profiling pass) and "
+                         "print its breakdown; for profiler launch lists, not a bench line")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -596,13 +603,19 @@ def main():
     hbm, bf16, peak_src = peaks()
 
     w, R, head = run_headline(args, dev, world, flush)
+    if args.only_headline:
+        if rank == 0:
+            print(json.dumps({"only_headline": args.workload, "solves_per_s": head["value"],
+                              "ms_per_step": head["ms_per_step"], "iters": head["iters"],
+                              "breakdown_ms": head["prof_ms"], "launches_per_step": head["prof_launches"]}))
+        return
     s64, plain = run_plain_fp64(args, dev, world, flush, w, R)
     groups = group_roofline(head["solver"], head, 4, R, head["iters"], hbm, bf16)
     fp64_groups = group_roofline(s64, {"prof_ms": plain["solve_breakdown_ms"],
                                        "prof_launches": plain["solve_launches"]}, 8, 1, plain["iters"], hbm, bf16)
     del head["solver"], s64
     legs = {}
-    for wname in [x for x in args.legs.split(",") if x]:
+    for wname in [x for x in args.legs.split(",") if x and x != "none"]:
         wl = synth.WORKLOADS[wname]
         for pname, prec in (("mixed", LSS_MIXED), ("fp64", LSS_FP64)):
             heavy = wl.dim == 3 and prec == LSS_FP64

@@ -200,6 +200,23 @@ int lss_medium_gradient(lss_ctx *c, const void *mu_dev, const void *u_dev, const
                         int R, double *grad_dev, void *stream);
 
 /*
+ * lss_helmholtz_solve - the sparsifying scheme as a direct discretization of
+ * the Helmholtz equation (Sec. 4): solve the sparsified system
+ *        H u~ = beta^* f   on the n_tot^2 grid,
+ * i.e. alpha^* u_{mu_i} + omega^2 beta^* (m u)_{mu_i} = beta^* f_{mu_i} on I^h with
+ * the PML rows of H, for R sources f (a discrete delta f = 1/h^2 at one point
+ * gives about the Green's function, Sec. 4; with a medium m the equation is
+ * (-Laplace - omega^2 (1 - m)) u = f).  Flexible GMRES on H (FP64, the
+ * context's subproblem rows) right-preconditioned by the moving-PML sweep on
+ * grid vectors; same options and statistics as lss_solve (relres is measured
+ * with H on the grid).  2D grids only; requires lss_factor.
+ *   f_dev      device, R x n^2 complex128 source values on I
+ *   u_dev      device, R x n^2 complex128 (output): u~ restricted to I
+ */
+int lss_helmholtz_solve(lss_ctx *c, const void *f_dev, void *u_dev, int R, const lss_gmres *o,
+                        lss_stats *stats, void *stream);
+
+/*
  * lss_solve_host - the same solve with host buffers: copies g_host to the
  * device, solves, copies u back.  g_host, u_host: R x n^d complex128 (pinned
  * memory gives asynchronous copies).  Blocks the host.

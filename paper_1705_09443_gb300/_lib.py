@@ -20,7 +20,7 @@ ERRORS = {
 # every symbol include/lss.h declares
 SYMBOLS = [
     "lss_setup", "lss_set_medium", "lss_factor", "lss_plane_wave_rhs", "lss_apply_A", "lss_apply_P", "lss_solve",
-    "lss_adjoint_solve", "lss_medium_gradient", "lss_solve_host", "lss_apply_slab", "lss_apply_slab_noalloc", "lss_info", "lss_slab_info", "lss_get_stencils",
+    "lss_adjoint_solve", "lss_medium_gradient", "lss_helmholtz_solve", "lss_solve_host", "lss_apply_slab", "lss_apply_slab_noalloc", "lss_info", "lss_slab_info", "lss_get_stencils",
     "lss_profile", "lss_profile_read", "lss_set_graphs", "lss_graph_count", "lss_autotune", "lss_setup_batch", "lss_batch_info", "lss_batch_instance", "lss_test_inject", "lss_last_error",
     "lss_destroy",
 ]
@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
     lib.lss_solve_host.argtypes = [vp, vp, vp, i, P(Gmres), P(Stats), vp]
     lib.lss_adjoint_solve.argtypes = [vp, vp, vp, i, P(Gmres), P(Stats), vp]
     lib.lss_medium_gradient.argtypes = [vp, vp, vp, vp, i, vp, vp]
+    lib.lss_helmholtz_solve.argtypes = [vp, vp, vp, i, P(Gmres), P(Stats), vp]
     lib.lss_apply_slab.argtypes = [vp, i, vp, vp, i, vp]
     lib.lss_apply_slab_noalloc.argtypes = [vp, i, vp, vp, i, vp]
     lib.lss_info.argtypes = [vp, P(i), P(i), P(i)]

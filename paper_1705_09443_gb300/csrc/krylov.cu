@@ -256,9 +256,15 @@ void dots(Krylov& K, const double2* V, long long vstride, int J, const double2* 
 
 int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
                cudaStream_t s, int transpose) {
-    // transpose: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T
+    // transpose = 1: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T;
+    // transpose = 2: the sparsified system H x = g on the n_tot^2 grid (Sec. 4)
+    // preconditioned by the sweep on grid vectors
     const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
-    const long long N = c->npts();
+    const bool grid = transpose == 2;
+    const long long N = grid ? (long long)c->n_tot * c->n_tot : c->npts();
+    auto apply_A = [&](const double2* x, double2* y, cudaStream_t st_) -> int {
+        return grid ? lss_apply_H(c, x, y, R, st_) : lss_matvec(c, x, y, R, mv_in, mv_out, nullptr, nullptr, st_);
+    };
     const int m = o->restart;
     const int maxit = o->max_iter;
     const long long RN = (long long)R * N;
@@ -289,7 +295,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     const int small = std::min(1024, std::max(32, (R + 31) / 32 * 32));
 
     double2* hnorm = K.hnorm;
-    if (transpose && (rc = lss_prepare_sweep_t(c, s))) return rc;
+    if (transpose == 1 && (rc = lss_prepare_sweep_t(c, s))) return rc;
 
     // Iteration j on stream bs: Z_j = P V_j, w = A Z_j, two Gram-Schmidt passes
     // against V_0..V_j, ||w||^2, the Givens update of every right-hand side,
@@ -299,8 +305,9 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         Kb.s = bs;
         const double2* Vj = V + (size_t)j * RN;
         double2* Zj = Z + (size_t)j * RN;
-        int r = transpose ? lss_sweep_t(c, Vj, Zj, R, bs) : lss_sweep(c, Vj, Zj, R, bs);
-        if (!r) r = lss_matvec(c, Zj, w, R, mv_in, mv_out, nullptr, nullptr, bs);
+        int r = grid ? lss_sweep_grid(c, Vj, Zj, R, bs)
+                     : (transpose ? lss_sweep_t(c, Vj, Zj, R, bs) : lss_sweep(c, Vj, Zj, R, bs));
+        if (!r) r = apply_A(Zj, w, bs);
         if (r) return r;
         dots(Kb, V, RN, j + 1, w, K.hdev, 0);
         { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.hdev, j + 1, w, N, R, -1.0); }
@@ -449,13 +456,13 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         for (int r = 0; r < R; ++r) all_done &= (bool)done[r];
         if (all_done || total >= maxit || J == 0) break;
         // restart: r = g - A u
-        if ((rc = lss_matvec(c, u, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
+        if ((rc = apply_A(u, w, s))) return rc;
         { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs_grid, 256, 0, s>>>(g, w, rv, RN); }
         dots(K, rv, 0, 1, rv, K.hdev, 0);
         { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); cycle_init_kernel<<<1, small, 0, s>>>(gs, K.hdev, K.scdev, R, m, 0, o->tol); }
     }
     // true residual
-    if ((rc = lss_matvec(c, u, w, R, mv_in, mv_out, nullptr, nullptr, s))) return rc;
+    if ((rc = apply_A(u, w, s))) return rc;
     { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); sub_kernel<<<gs_grid, 256, 0, s>>>(g, w, rv, RN); }
     dots(K, rv, 0, 1, rv, K.hdev, 0);
     std::vector<double2> hh(R);

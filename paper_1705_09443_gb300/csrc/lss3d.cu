@@ -591,7 +591,8 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
     C* P = reinterpret_cast<C*>(smraw);
     __shared__ R red_v[32];
     __shared__ int red_i[32];
-    __shared__ int s_piv;
+    __shared__ C s_pj[NB], s_oj[NB], s_d;
+    __shared__ int s_pr;
     const int slab = blockIdx.x;
     const Slab3 sd = slabs[slab];
     const int M = sd.M;
@@ -604,8 +605,12 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
         P[q * M + r] = w[(long long)r * M + j0 + q];
     }
     __syncthreads();
+    const int nw = nt / 32;
     for (int jj = 0; jj < nbp; ++jj) {
         const int j = j0 + jj;
+        // pivot: the largest |P[jj][r]| over rows r >= j (ties to the lower row);
+        // each warp reduces its rows, then every thread reduces the warps'
+        // results itself (no second barrier)
         R best = -1;
         int bi = M;
         for (int r = j + tid; r < M; r += nt) {
@@ -619,51 +624,59 @@ __global__ void __launch_bounds__(512) f3_panel(const Slab3* __restrict__ slabs,
         }
         if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
         __syncthreads();
+        // warp 0: the pivot over the warps' results, the pivot row (old row pr)
+        // scaled by d = 1 / pivot and the old row j (which moves to position pr)
         if (tid < 32) {
-            best = tid < nt / 32 ? red_v[tid] : R(-1);
-            bi = tid < nt / 32 ? red_i[tid] : M;
+            best = tid < nw ? red_v[tid] : R(-1);
+            bi = tid < nw ? red_i[tid] : M;
             for (int o = 16; o > 0; o >>= 1) {
                 const R ov = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
             }
+            const bool sing = !(best > 0) || !isfinite(best) || bi >= M;
+            const int pr = sing ? j : bi;
+            const C d = crecip(P[jj * M + pr]);
+            if (tid < nbp) {
+                s_pj[tid] = (tid == jj) ? d : P[tid * M + pr] * d;
+                s_oj[tid] = P[tid * M + j];
+            }
             if (tid == 0) {
-                if (!(best > 0) || !isfinite(best) || bi >= M) {
-                    atomicOr(err, LSS_DERR_SINGULAR);
-                    bi = j;
-                }
-                s_piv = bi;
-                piv[slab * NB + jj] = bi;
-                if (bi != j) {
+                if (sing) atomicOr(err, LSS_DERR_SINGULAR);
+                s_pr = pr;
+                s_d = d;
+                piv[slab * NB + jj] = pr;
+                if (pr != j) {
                     int* rid = rowid + (long long)slab * Mmax;
                     const int t = rid[j];
-                    rid[j] = rid[bi];
-                    rid[bi] = t;
+                    rid[j] = rid[pr];
+                    rid[pr] = t;
                 }
             }
         }
         __syncthreads();
-        const int pr = s_piv;
-        if (pr != j && tid < nbp) {
-            const C t = P[tid * M + j];
-            P[tid * M + j] = P[tid * M + pr];
-            P[tid * M + pr] = t;
-        }
-        __syncthreads();
-        const C d = crecip(P[jj * M + j]);
-        __syncthreads();
-        if (tid < nbp) P[tid * M + j] = (tid == jj) ? d : P[tid * M + j] * d;
-        __syncthreads();
+        // new row j = the scaled pivot row; every other row i (row pr taking
+        // the old row j's values) eliminated: x_q -= l pj_q, x_jj = -l d
+        const int pr = s_pr;
+        const C d = s_d;
         C pj[NB];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) pj[q] = q < nbp ? P[q * M + j] : czero<C>();
+        for (int q = 0; q < NB; ++q) pj[q] = q < nbp ? s_pj[q] : czero<C>();
         for (int i = tid; i < M; i += nt) {
-            if (i == j) continue;
-            const C l = P[jj * M + i];
+            if (i == j) {
 #pragma unroll
-            for (int q = 0; q < NB; ++q)
-                if (q < nbp && q != jj) P[q * M + i] = P[q * M + i] - l * pj[q];
-            P[jj * M + i] = czero<C>() - l * d;
+                for (int q = 0; q < NB; ++q)
+                    if (q < nbp) P[q * M + i] = pj[q];
+                continue;
+            }
+            const bool sw = i == pr;
+            const C l = sw ? s_oj[jj] : P[jj * M + i];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                if (q >= nbp) break;
+                const C x = sw ? s_oj[q] : P[q * M + i];
+                P[q * M + i] = (q == jj) ? czero<C>() - l * d : x - l * pj[q];
+            }
         }
         __syncthreads();
     }
@@ -805,10 +818,17 @@ __global__ void f3_extract_outer(const Slab3* __restrict__ slabs, C* __restrict_
     C* t = T64 + (long long)slab * NO * Tld;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
         const bool inside = c >= J0 && c < J0 + nbo;
-        for (int kk = 0; kk < nbo; ++kk) {
-            C* p = w + (long long)(J0 + kk) * M + c;
-            t[(long long)kk * Tld + c] = inside ? czero<C>() : *p;
-            if (!inside) *p = czero<C>();
+        for (int k0 = 0; k0 < nbo; k0 += 16) {   // 16 independent loads, then the stores
+            C v[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                v[u] = (!inside && k0 + u < nbo) ? w[(long long)(J0 + k0 + u) * M + c] : czero<C>();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                if (k0 + u >= nbo) break;
+                t[(long long)(k0 + u) * Tld + c] = v[u];
+                if (!inside) w[(long long)(J0 + k0 + u) * M + c] = czero<C>();
+            }
         }
     }
 }

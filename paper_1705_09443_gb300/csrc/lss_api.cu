@@ -37,7 +37,7 @@ void free_ctx(lss_ctx* c) {
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
                     c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->iface_t, c->d_slabs,
                     c->d_err, c->d_bar, c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf,
-                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf};
+                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf, c->hz_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->chunk_dev)
@@ -444,6 +444,28 @@ int lss_adjoint_solve(lss_ctx* c, const void* rhs, void* mu, int R, const lss_gm
     if (is_batch(c))
         return lss_batch_solve(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
     return lss_fgmres(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
+}
+
+int lss_helmholtz_solve(lss_ctx* c, const void* f, void* u, int R, const lss_gmres* o, lss_stats* stats,
+                        void* stream) {
+    if (!c) return LSS_ERR_ARG;
+    if (!f || !u || !o || R < 1) return lss_fail(c, LSS_ERR_ARG, "helmholtz_solve: bad arguments");
+    if (o->restart < 1 || o->restart > 200 || !(o->tol > 0) || o->max_iter < 1)
+        return lss_fail(c, LSS_ERR_ARG, "helmholtz_solve: bad GMRES options");
+    if (is_batch(c)) return batch_only_per_instance(c, "helmholtz_solve");
+    if (c->dim != 2) return lss_fail(c, LSS_ERR_UNSUPPORTED, "helmholtz_solve: 2D grids only");
+    if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "helmholtz_solve before lss_factor");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t G = (size_t)R * c->n_tot * c->n_tot;
+    int rc = lss_grow(c, &c->hz_buf, &c->hz_cap, 2 * G * sizeof(double2));
+    if (rc) return rc;
+    double2* F = (double2*)c->hz_buf;
+    double2* U = F + G;
+    rc = lss_sparsify_beta(c, (const double2*)f, F, R, s);
+    if (!rc) rc = lss_fgmres(c, F, U, R, o, stats, s, 2);
+    if (rc && rc != LSS_ERR_NOCONVERGE) return rc;
+    const int rc2 = lss_extract_grid(c, U, (double2*)u, R, s);
+    return rc2 ? rc2 : rc;
 }
 
 int lss_medium_gradient(lss_ctx* c, const void* mu, const void* u, const double* dirs_host, int R, double* grad,

@@ -152,6 +152,7 @@ struct lss_ctx {
     void* io_buf = nullptr; size_t io_cap = 0;         // host-buffer solve staging
     void* dir_buf = nullptr; size_t dir_cap = 0;       // plane-wave directions
     void* gr_buf = nullptr; size_t gr_cap = 0;         // -omega^2 K mu for the medium gradient
+    void* hz_buf = nullptr; size_t hz_cap = 0;         // direct Helmholtz solve: beta^* f and u on the grid
     void* ifx_buf = nullptr; size_t ifx_cap = 0;       // interface-map column blocks (all slabs, both sides)
     void* ifp_buf = nullptr; size_t ifp_cap = 0;       // interface-map problem table
     int ifp_n = 0;                                     // problems uploaded to ifp_buf
@@ -289,6 +290,12 @@ int lss_prepare_sweep_t(lss_ctx* c, cudaStream_t s);
 int lss_gradient_m(lss_ctx* c, const double2* Kmu, const double2* u, const double* dirs_dev, double* grad, int R,
                    cudaStream_t s);
 int lss_sparsify_t(lss_ctx* c, const void* X, double2* r, int R, cudaStream_t s);
+// Sec. 4 direct solver (2D): beta^* f on the grid, H on grid vectors, the sweep
+// on a grid right-hand side, grid -> I
+int lss_sparsify_beta(lss_ctx* c, const double2* f, double2* F, int R, cudaStream_t s);
+int lss_apply_H(lss_ctx* c, const double2* x, double2* y, int R, cudaStream_t s);
+int lss_sweep_grid(lss_ctx* c, const double2* F, double2* y, int R, cudaStream_t s);
+int lss_extract_grid(lss_ctx* c, const double2* U, double2* u, int R, cudaStream_t s);
 
 // krylov.cu: FGMRES
 int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s);

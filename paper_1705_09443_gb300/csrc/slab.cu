@@ -486,7 +486,8 @@ struct CrArgs {
     C* a_last;
     const C* lam;            // CR_E inputs, [slab][k][R]
     const C* phi;
-    double2* y;              // CR_E output, R x n^2
+    double2* y;              // CR_E output, R x n^2 (or R x n_tot^2 when y_grid)
+    int y_grid;              // CR_E: write every point of D_i on the grid (x2 slowest) instead of I
     int slab;                // CR_TEST
     const double2* v_in;     // R x (layers of D_i) x n_tot
     double2* w_out;
@@ -849,7 +850,9 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         for (int e = tid; e < nl * K; e += nth) {
             const int k = e % K, pp = na + e / K;
             const int x1 = sd.s + (pp - na), i2 = k - A.b;
-            if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
+            if (A.y_grid)
+                A.y[(long long)r * A.n_tot * A.n_tot + (long long)k * A.n_tot + (x1 + A.b)] = to_d(row(k)[pp]);
+            else if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
                 A.y[(long long)r * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(row(k)[pp]);
         }
     } else {
@@ -1724,8 +1727,16 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     return lss_check_cuda(c, e, "recurrence launch");
 }
 
+__global__ void grid_to_working(const double2* __restrict__ a, float2* __restrict__ b, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        b[e] = make_float2((float)a[e].x, (float)a[e].y);
+}
+
+// The sweep of Algorithm 2: on r (vectors on I: f = Q r, result restricted to
+// I), or, with grid_in, on a right-hand side given on the grid, the result
+// then on the grid too (every point of every D_i, x2 slowest).
 template <typename T>
-int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
+int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s, const double2* grid_in = nullptr) {
     using C = cx<T>;
     const long long nt2 = (long long)c->n_tot * c->n_tot;
     int rc = lss_grow(c, &c->f_buf, &c->f_cap, (size_t)R * nt2 * sizeof(C));
@@ -1733,7 +1744,18 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     const long long vec = (long long)c->n_tot * R;
     rc = lss_grow(c, &c->side_buf, &c->side_cap, 4 * (size_t)c->n_slabs * vec * sizeof(C));
     if (rc) return rc;
-    rc = lss_sparsify(c, r, c->f_buf, R, s);
+    if (grid_in) {
+        ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+        if constexpr (sizeof(T) == 8)
+            rc = lss_check_cuda(c, cudaMemcpyAsync(c->f_buf, grid_in, (size_t)R * nt2 * sizeof(double2),
+                                                   cudaMemcpyDeviceToDevice, s), "grid right-hand side");
+        else {
+            grid_to_working<<<4 * c->num_sms, 256, 0, s>>>(grid_in, (float2*)c->f_buf, (long long)R * nt2);
+            rc = lss_check_cuda(c, cudaGetLastError(), "grid right-hand side");
+        }
+    } else {
+        rc = lss_sparsify(c, r, c->f_buf, R, s);
+    }
     if (rc) return rc;
     C* side = (C*)c->side_buf;
     CrArgs<C> A = base_args<C>(c);
@@ -1746,6 +1768,7 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) 
     A.lam = lam;
     A.phi = phi;
     A.y = y;
+    A.y_grid = grid_in ? 1 : 0;
     const int nrun = (int)sweep_runs(c).size();
     if (c->n_slabs > 1) {
         {
@@ -1817,6 +1840,11 @@ int lss_recurrences(lss_ctx* c, const void* maps, void* lam, void* phi, const vo
 int lss_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
     if (c->dim == 3) return lss3_sweep(c, r, y, R, s);
     return c->prec == LSS_FP64 ? sweep_impl<double>(c, r, y, R, s) : sweep_impl<float>(c, r, y, R, s);
+}
+
+int lss_sweep_grid(lss_ctx* c, const double2* F, double2* y, int R, cudaStream_t s) {
+    if (c->dim != 2) return lss_fail(c, LSS_ERR_UNSUPPORTED, "grid sweep: 2D grids only");
+    return c->prec == LSS_FP64 ? sweep_impl<double>(c, nullptr, y, R, s, F) : sweep_impl<float>(c, nullptr, y, R, s, F);
 }
 
 int lss_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {

@@ -288,6 +288,42 @@ __global__ void gradient_kernel(const double2* __restrict__ Kmu, const double2* 
     }
 }
 
+// y = H x on the n_tot^2 grid (x2 slowest): every point's row from the
+// subproblem table of the slab whose D_i holds it (those rows are H's rows,
+// Eq. Hwv_approx), FP64; neighbours outside the grid are the zero Dirichlet
+// values.
+__global__ void apply_H_kernel(const SlabDev* __restrict__ slabs, int n_slabs, const double2* __restrict__ coef,
+                               const double2* __restrict__ x, double2* __restrict__ y, int n_tot, int b, int bs) {
+    const long long tot = (long long)n_tot * n_tot;
+    const int rr = blockIdx.y;
+    const double2* xv = x + rr * tot;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int X2 = (int)(e / n_tot), X1 = (int)(e % n_tot);
+        const int x1 = X1 - b;
+        int i = x1 < 0 ? 0 : x1 / bs;
+        if (i > n_slabs - 1) i = n_slabs - 1;
+        const SlabDev sd = slabs[i];
+        const double2* row = coef + sd.coef_off + (long long)X2 * sd.cstride + (sd.na + (x1 - sd.s)) * 9;
+        double2 acc = mk(0.0, 0.0);
+        for (int o = 0; o < 9; ++o) {
+            const int Y1 = X1 + o / 3 - 1, Y2 = X2 + o % 3 - 1;
+            if (Y1 >= 0 && Y1 < n_tot && Y2 >= 0 && Y2 < n_tot) acc = cfma(row[o], xv[(long long)Y2 * n_tot + Y1], acc);
+        }
+        y[rr * tot + e] = acc;
+    }
+}
+
+// u on I from a grid vector (x2 slowest).
+__global__ void extract_grid_kernel(const double2* __restrict__ U, double2* __restrict__ u, int n, int b, int n_tot) {
+    const long long N = (long long)n * n, tot = (long long)n_tot * n_tot;
+    const int rr = blockIdx.y;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const int i1 = (int)(e / n) + 1, i2 = (int)(e % n) + 1;
+        u[rr * N + e] = U[rr * tot + (long long)(i2 + b) * n_tot + (i1 + b)];
+    }
+}
+
 StencilArgs stencil_args(const lss_ctx* c) {
     StencilArgs st;
     for (int o = 0; o < 9; ++o) {
@@ -342,6 +378,33 @@ int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s) {
         sparsify_kernel<float2><<<dim3(blocks, R), 256, 0, s>>>(r, (float2*)f, stencil_args(c), c->n, c->b,
                                                                  c->n_tot);
     return lss_check_cuda(c, cudaGetLastError(), "sparsify");
+}
+
+// F = beta^* f on I^h (Sec. 4), FP64, grid layout of the sparsified right-hand side.
+int lss_sparsify_beta(lss_ctx* c, const double2* f, double2* F, int R, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+    const long long tot = (long long)c->n_tot * c->n_tot;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4LL * c->num_sms);
+    StencilArgs st = stencil_args(c);
+    for (int o = 0; o < 9; ++o) st.a_conj[o] = st.b_conj[o];
+    sparsify_kernel<double2><<<dim3(blocks, R), 256, 0, s>>>(f, F, st, c->n, c->b, c->n_tot);
+    return lss_check_cuda(c, cudaGetLastError(), "sparsify beta");
+}
+
+int lss_apply_H(lss_ctx* c, const double2* x, double2* y, int R, cudaStream_t s) {
+    ProfScope ps(c, s, LSS_PROF_MATVEC, 1);
+    const long long tot = (long long)c->n_tot * c->n_tot;
+    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4LL * c->num_sms);
+    apply_H_kernel<<<dim3(blocks, R), 256, 0, s>>>(c->d_slabs, c->n_slabs, c->coef64, x, y, c->n_tot, c->b,
+                                                   c->slab.b_slab);
+    return lss_check_cuda(c, cudaGetLastError(), "apply H");
+}
+
+int lss_extract_grid(lss_ctx* c, const double2* U, double2* u, int R, cudaStream_t s) {
+    const long long N = (long long)c->n * c->n;
+    const int blocks = (int)std::min<long long>((N + 255) / 256, 4LL * c->num_sms);
+    extract_grid_kernel<<<dim3(blocks, R), 256, 0, s>>>(U, u, c->n, c->b, c->n_tot);
+    return lss_check_cuda(c, cudaGetLastError(), "extract");
 }
 
 int lss_sparsify_t(lss_ctx* c, const void* X, double2* r, int R, cudaStream_t s) {

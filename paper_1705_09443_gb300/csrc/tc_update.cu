@@ -221,15 +221,20 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
 #pragma unroll
             for (int j = 0; j < 32; ++j) S[tid * 33 + j] = v[j];
             __syncthreads();
-            for (int e = tid; e < 128 * 16; e += 128) {
-                const int row = e >> 4, q = e & 15;
+            float2 o[16];   // 16 independent loads, then the adds and stores
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = tid + u * 128, row = e >> 4, q = e & 15;
+                const int i = i0 + row, c = c0 + ch * 16 + q;
+                const bool ok_ = i < M && c < M && !(c >= J0 && c < J0 + nbo);
+                o[u] = ok_ ? w[(long long)i * M + c] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = tid + u * 128, row = e >> 4, q = e & 15;
                 const int i = i0 + row, c = c0 + ch * 16 + q;
                 if (i >= M || c >= M || (c >= J0 && c < J0 + nbo)) continue;
-                float2* p = w + (long long)i * M + c;
-                float2 o = *p;
-                o.x += S[row * 33 + 2 * q];
-                o.y += S[row * 33 + 2 * q + 1];
-                *p = o;
+                w[(long long)i * M + c] = make_float2(o[u].x + S[row * 33 + 2 * q], o[u].y + S[row * 33 + 2 * q + 1]);
             }
             __syncthreads();
         }

@@ -193,6 +193,21 @@ class LSSolver:
         return mu, [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
                          relres_true=s.relres_true) for s in st]
 
+    def helmholtz_solve(self, f: torch.Tensor, opts: GmresOptions | None = None, stream=None):
+        """u with alpha^* u + omega^2 beta^* (m u) = beta^* f on I^h and the PML rows
+        (Sec. 4, lss_helmholtz_solve): the sparsified discretization of
+        (-Laplace - omega^2 (1 - m)) u = f.  f: (R, n, n) or (n, n) complex128."""
+        o = opts or GmresOptions()
+        f = _c128(self._batch(f))
+        u = torch.empty_like(f)
+        R = f.shape[0]
+        st = (_lib.Stats * R)()
+        go = _lib.Gmres(o.restart, o.tol, o.max_iter)
+        self._check(self.lib.lss_helmholtz_solve(self.ctx, f.data_ptr(), u.data_ptr(), R, ctypes.byref(go), st,
+                                                 _stream_ptr(stream)))
+        return u, [dict(iters=s.iters, converged=bool(s.converged), relres_est=s.relres_est,
+                        relres_true=s.relres_true) for s in st]
+
     def medium_gradient(self, mu: torch.Tensor, u: torch.Tensor, dirs, stream=None) -> torch.Tensor:
         """sum_r Re((-omega^2 K mu_r) . (u_r + u_I,r)) on I (lss_medium_gradient)."""
         mu = _c128(self._batch(mu))

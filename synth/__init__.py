@@ -138,6 +138,10 @@ WORKLOADS = {
                        1, 1709, (1.0, 1.0, 1.0)),
     "2d_n256_r16": Workload("2d_n256_r16", 2, 256, 32.0, 12, 4, "gauss", 16, 0.05,
                             (0.75, 1.25), 16, 1707, None),
+    # the 3D workload at n = 32 (same medium recipe, seed and points per
+    # wavelength): a small case for profiler captures of the 3D kernels
+    "3d_n32": Workload("3d_n32", 3, 32, 33.0 / 8.0, 8, 4, "gauss", 8, 0.1, (0.8, 1.2),
+                       1, 1709, (1.0, 1.0, 1.0)),
 }
 
 
