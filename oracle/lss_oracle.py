@@ -263,9 +263,92 @@ class Params:
     b_aux: int | None = None      # READING: defaults to b_pml (Sec. 2.3 uses b for both)
     C: float = 10.0
     n_samples: int | None = None  # defaults to n (Sec. 2.3)
+    fronts: int = 1               # 2: two sweeping fronts meeting in the middle slab (Sec. 2.4 remark 1)
 
 
-class Problem2D:
+class _TwoFronts:
+    """The sweep with two fronts (Sec. 2.4 remark 1, the setting of Sec. 2.5):
+    the slabs left of the middle slab c = (l-1)//2 carry their moving PML on
+    the left (as in Algorithm 2), the slabs right of it on the right, and c
+    is padded with auxiliary PML on both sides.  Both fronts eliminate toward
+    c, c is solved with the couplings from both neighbours, then both fronts
+    substitute back toward the boundaries.  With the exact Schur inverses
+    this is block Gaussian elimination from both ends, i.e. H^{-1}."""
+
+    def aux_sides(self, i: int):
+        """(auxiliary layers on the left, on the right) of slab i's subproblem."""
+        nl = self.n_slabs
+        if self.p.fronts != 2:
+            return i > 0, False
+        c = (nl - 1) // 2
+        return (0 < i <= c), (c <= i < nl - 1)
+
+    def right_sigma(self, e: int, a1: int):
+        """sigma along x1 at a1 - 1, a1, a1 + 1 for the auxiliary PML right of
+        D_i's last layer e: the right PML profile of width b_aux translated so
+        that layer e plays the role of index n + 1 (the mirror image of the
+        left auxiliary profile)."""
+        return pml_sigma(np.array([a1 - 1, a1, a1 + 1]) - e + self.n + 1, self.n, self.b_aux, self.p.C,
+                         self.omega)
+
+    def sweep_two_fronts(self, f, T=None):
+        T = T or self.T
+        nl = self.n_slabs
+        c = (nl - 1) // 2
+        u = [None] * nl
+        for i in range(0, c):                              # left front, toward c
+            v = self.slab_view(f, i).copy()
+            if i > 0:
+                v[0] -= self.couple_left(i, u[i - 1][-1])
+            u[i] = T(i, v)
+        for i in range(nl - 1, c, -1):                     # right front, toward c
+            v = self.slab_view(f, i).copy()
+            if i < nl - 1:
+                v[-1] -= self.couple_right(i, u[i + 1][0])
+            u[i] = T(i, v)
+        v = self.slab_view(f, c).copy()                    # the middle slab
+        if c > 0:
+            v[0] -= self.couple_left(c, u[c - 1][-1])
+        if c < nl - 1:
+            v[-1] -= self.couple_right(c, u[c + 1][0])
+        u[c] = T(c, v)
+        for i in range(c - 1, -1, -1):                     # back toward the left boundary
+            w = np.zeros_like(u[i])
+            w[-1] = self.couple_right(i, u[i + 1][0])
+            u[i] = u[i] - T(i, w)
+        for i in range(c + 1, nl):                         # back toward the right boundary
+            w = np.zeros_like(u[i])
+            w[0] = self.couple_left(i, u[i - 1][-1])
+            u[i] = u[i] - T(i, w)
+        return np.concatenate(u, axis=0)
+
+    def exact_T_ops_two_fronts(self):
+        """The exact Schur inverses of the two-front elimination: restrictions
+        to D_i of H_{[0:i]}^{-1} (slabs left of c), H_{[i:l]}^{-1} (slabs right
+        of c) and H^{-1} (the middle slab c)."""
+        H = self.assemble_H().toarray()
+        per = self.n_tot ** (self.m.ndim - 1)
+        b, nl = self.b, self.n_slabs
+        c = (nl - 1) // 2
+        starts = [(self.slab_first[i] + b) * per for i in range(nl)]
+        ends = [(self.slab_last[i] + b + 1) * per for i in range(nl)]
+        inv = []
+        for i in range(nl):
+            if i < c:
+                lo, hi = 0, ends[i]
+            elif i > c:
+                lo, hi = starts[i], H.shape[0]
+            else:
+                lo, hi = 0, H.shape[0]
+            Hi = np.linalg.inv(H[lo:hi, lo:hi])
+            inv.append(Hi[starts[i] - lo:ends[i] - lo, starts[i] - lo:ends[i] - lo])
+
+        def T(i, v):
+            return (inv[i] @ v.reshape(-1)).reshape(v.shape)
+        return T
+
+
+class Problem2D(_TwoFronts):
     """The 2D sparsified system and its sweeping preconditioner.
 
     Index convention: grid index (i1, i2) with i in I^{h+eta} = {-b..n+1+b}^2
@@ -333,6 +416,17 @@ class Problem2D:
         k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(a1, i2)))
         return self._gamma(("aux", k, tuple(s1), tuple(s2)), math.sqrt(self.samples[k]), s1, s2)
 
+    def aux_row_right(self, e: int, t: int, i2: int) -> np.ndarray:
+        """Row of the auxiliary PML point t = 1..b_aux layers right of D_i's last
+        layer e (two fronts), at true position (e+t, i2): the mirrored profile
+        along x1, the physical sigma along x2, the sample nearest
+        omega^2 (1 - m(e+t, i2))."""
+        a1 = e + t
+        s1 = self.right_sigma(e, a1)
+        s2 = self.sigma([i2 - 1, i2, i2 + 1])
+        k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(a1, i2)))
+        return self._gamma(("auxr", k, tuple(s1), tuple(s2)), math.sqrt(self.samples[k]), s1, s2)
+
     # ---- assembled H and f = Q r -------------------------------------------------
     def assemble_H(self) -> sp.csr_matrix:
         """H on I^{h+eta}, zero Dirichlet values on its boundary dropped (Eq. Huf)."""
@@ -385,18 +479,28 @@ class Problem2D:
 
         Unknowns: b_aux virtual auxiliary layers (x1 = s-b_aux..s-1) then the
         layers of D_i; for i = 0 there are no auxiliary layers (T~_1 = T_1).
-        Couplings leaving the layer set are dropped (zero Dirichlet values).
-        Returns (matrix, x1 list of layers, offset of D_i within the layers).
+        With two fronts the slabs from the middle one rightward take their
+        b_aux auxiliary layers (x1 = e+1..e+b_aux) on the right instead (the
+        middle slab on both sides).  Couplings leaving the layer set are
+        dropped (zero Dirichlet values).  Returns (matrix, x1 list of layers,
+        offset of D_i within the layers).
         """
         b, nt = self.b, self.n_tot
         s, e = self.slab_first[i], self.slab_last[i]
-        aux = [] if i == 0 else list(range(s - self.b_aux, s))
-        layers = aux + list(range(s, e + 1))
+        left, right = self.aux_sides(i)
+        aux = list(range(s - self.b_aux, s)) if left else []
+        aux_r = list(range(e + 1, e + 1 + self.b_aux)) if right else []
+        layers = aux + list(range(s, e + 1)) + aux_r
         pos = {x1: a for a, x1 in enumerate(layers)}
         rows, cols, vals = [], [], []
         for a, x1 in enumerate(layers):
             for i2 in range(-b, self.n + 2 + b):
-                c = self.aux_row(s, s - x1, i2) if x1 < s else self.row(x1, i2)
+                if x1 < s:
+                    c = self.aux_row(s, s - x1, i2)
+                elif x1 > e:
+                    c = self.aux_row_right(e, x1 - e, i2)
+                else:
+                    c = self.row(x1, i2)
                 r = a * nt + (i2 + b)
                 for da in (-1, 0, 1):
                     ja = pos.get(x1 + da)
@@ -413,29 +517,28 @@ class Problem2D:
 
     def _factor(self):
         """Algorithm 1 steps 5-8: LU of every subproblem (sparse LU, partial pivoting)."""
-        self.lu, self.n_aux = [], []
+        self.lu, self.n_aux, self.n_layers = [], [], []
         for i in range(self.n_slabs):
             M, layers, na = self.subproblem(i)
             self.lu.append(spla.splu(M.tocsc()))
             self.n_aux.append(na)
+            self.n_layers.append(len(layers))
+
+    def _T(self, i, v, trans):
+        nt = self.n_tot
+        na, nd = self.n_aux[i], v.shape[0]
+        rhs = np.zeros((self.n_layers[i] * nt,), dtype=np.complex128)
+        rhs[na * nt:(na + nd) * nt] = v.reshape(-1)
+        w = self.lu[i].solve(rhs, trans=trans)
+        return w[na * nt:(na + nd) * nt].reshape(v.shape)
 
     def T(self, i: int, v: np.ndarray) -> np.ndarray:
         """T~_i v: pad v (layers of D_i x n_tot) with zeros on the auxiliary
         layers, solve the subproblem, restrict to D_i (Eq. Hwv_approx)."""
-        nt = self.n_tot
-        na = self.n_aux[i]
-        rhs = np.zeros(((na + v.shape[0]) * nt,), dtype=np.complex128)
-        rhs[na * nt:] = v.reshape(-1)
-        w = self.lu[i].solve(rhs)
-        return w[na * nt:].reshape(v.shape)
+        return self._T(i, v, "N")
 
     def T_transpose(self, i: int, v: np.ndarray) -> np.ndarray:
-        nt = self.n_tot
-        na = self.n_aux[i]
-        rhs = np.zeros(((na + v.shape[0]) * nt,), dtype=np.complex128)
-        rhs[na * nt:] = v.reshape(-1)
-        w = self.lu[i].solve(rhs, trans="T")
-        return w[na * nt:].reshape(v.shape)
+        return self._T(i, v, "T")
 
     def couple_left(self, i: int, u_prev_last: np.ndarray) -> np.ndarray:
         """H_{[i,i-1]} u_{[i-1]}: rows of D_i's first layer, x1-offset -1."""
@@ -469,6 +572,8 @@ class Problem2D:
 
     def sweep(self, f: np.ndarray, T=None) -> np.ndarray:
         """Algorithm 2 steps 3-9: forward then backward sweep with T~_i."""
+        if self.p.fronts == 2:
+            return self.sweep_two_fronts(f, T)
         T = T or self.T
         nl = self.n_slabs
         u = [None] * nl
@@ -494,7 +599,10 @@ class Problem2D:
     def precondition_transpose(self, y: np.ndarray) -> np.ndarray:
         """P^T y = Q^T Sweep^T E^T y, with Sweep^T the two passes in reverse:
         z_1 = v_1, z_i = v_i - H_{[i-1,i]}^T T~_{i-1}^T z_{i-1};
-        x_l = T~_l^T z_l, x_i = T~_i^T (z_i - H_{[i+1,i]}^T x_{i+1})."""
+        x_l = T~_l^T z_l, x_i = T~_i^T (z_i - H_{[i+1,i]}^T x_{i+1}).
+        Written for one sweeping front."""
+        if self.p.fronts != 1:
+            raise ValueError("the transposed sweep is written for one front")
         b, n, nt = self.b, self.n, self.n_tot
         v = np.zeros((nt, nt), dtype=np.complex128)
         v[b + 1:b + 1 + n, b + 1:b + 1 + n] = y
@@ -574,7 +682,7 @@ class Problem2D:
 # --------------------------------------------------------------------------
 
 
-class Problem3D:
+class Problem3D(_TwoFronts):
     """The 3D sparsified system and its non-recursive sweeping preconditioner
     (Sec. 3.1): alpha/beta on the 27-point neighbourhood, gamma annihilating the
     26 normalised directions of {-1,0,1}^3 minus 0, slabs of x1-layers (each a
@@ -645,6 +753,17 @@ class Problem3D:
         k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(a1, i2, i3)))
         return self._gamma(("aux", k, tuple(s1), tuple(s2), tuple(s3)), math.sqrt(self.samples[k]), s1, s2, s3)
 
+    def aux_row_right(self, e: int, t: int, i2: int, i3: int) -> np.ndarray:
+        """Row of the auxiliary PML point t layers right of D_i's last layer e
+        (two fronts): the mirrored profile along x1."""
+        a1 = e + t
+        s1 = self.right_sigma(e, a1)
+        s2 = self.sigma([i2 - 1, i2, i2 + 1])
+        s3 = self.sigma([i3 - 1, i3, i3 + 1])
+        k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(a1, i2, i3)))
+        return self._gamma(("auxr", k, tuple(s1), tuple(s2), tuple(s3)), math.sqrt(self.samples[k]), s1, s2,
+                           s3)
+
     def _range(self):
         return range(-self.b, self.n + 2 + self.b)
 
@@ -689,18 +808,27 @@ class Problem3D:
 
     def subproblem(self, i: int):
         """Matrix of slab i's subproblem (Eq. Hwv_approx in 3D): b_aux virtual
-        auxiliary layers then D_i's layers (none for the first slab); couplings
-        leaving the layer set are dropped.  Returns (matrix, layers, n_aux)."""
+        auxiliary layers then D_i's layers (none for the first slab), and with
+        two fronts the right-side auxiliary layers of the slabs from the middle
+        one rightward; couplings leaving the layer set are dropped.  Returns
+        (matrix, layers, n_aux)."""
         b, nt, lo, hi = self.b, self.n_tot, -self.b, self.n + 1 + self.b
         s, e = self.slab_first[i], self.slab_last[i]
-        aux = [] if i == 0 else list(range(s - self.b_aux, s))
-        layers = aux + list(range(s, e + 1))
+        left, right = self.aux_sides(i)
+        aux = list(range(s - self.b_aux, s)) if left else []
+        aux_r = list(range(e + 1, e + 1 + self.b_aux)) if right else []
+        layers = aux + list(range(s, e + 1)) + aux_r
         pos = {x1: a for a, x1 in enumerate(layers)}
         rows, cols, vals = [], [], []
         for a, x1 in enumerate(layers):
             for i2 in self._range():
                 for i3 in self._range():
-                    c = self.aux_row(s, s - x1, i2, i3) if x1 < s else self.row(x1, i2, i3)
+                    if x1 < s:
+                        c = self.aux_row(s, s - x1, i2, i3)
+                    elif x1 > e:
+                        c = self.aux_row_right(e, x1 - e, i2, i3)
+                    else:
+                        c = self.row(x1, i2, i3)
                     r = (a * nt + (i2 + b)) * nt + (i3 + b)
                     for o in neighbourhood_offsets(3):
                         ja = pos.get(x1 + o[0])
@@ -715,19 +843,20 @@ class Problem3D:
 
     def _factor(self):
         """Algorithm 1 in 3D: an LU of every slab subproblem."""
-        self.lu, self.n_aux = [], []
+        self.lu, self.n_aux, self.n_layers = [], [], []
         for i in range(self.n_slabs):
             M, layers, na = self.subproblem(i)
             self.lu.append(spla.splu(M.tocsc()))
             self.n_aux.append(na)
+            self.n_layers.append(len(layers))
 
     def _T(self, i, v, trans):
         nt2 = self.n_tot ** 2
-        na = self.n_aux[i]
-        rhs = np.zeros(((na + v.shape[0]) * nt2,), dtype=np.complex128)
-        rhs[na * nt2:] = v.reshape(-1)
+        na, nd = self.n_aux[i], v.shape[0]
+        rhs = np.zeros((self.n_layers[i] * nt2,), dtype=np.complex128)
+        rhs[na * nt2:(na + nd) * nt2] = v.reshape(-1)
         w = self.lu[i].solve(rhs, trans=trans)
-        return w[na * nt2:].reshape(v.shape)
+        return w[na * nt2:(na + nd) * nt2].reshape(v.shape)
 
     def T(self, i: int, v: np.ndarray) -> np.ndarray:
         """T~_i v: zero auxiliary layers, solve, restrict to D_i."""
@@ -768,6 +897,8 @@ class Problem3D:
 
     def sweep(self, f, T=None):
         """Algorithm 2 (forward then backward sweep) on 3D slabs."""
+        if self.p.fronts == 2:
+            return self.sweep_two_fronts(f, T)
         T = T or self.T
         nl = self.n_slabs
         u = [None] * nl
@@ -792,7 +923,9 @@ class Problem3D:
 
     def precondition_transpose(self, y):
         """P^T y = Q^T Sweep^T E^T y, the two passes of the sweep transposed
-        and taken in reverse (as in 2D)."""
+        and taken in reverse (as in 2D).  Written for one sweeping front."""
+        if self.p.fronts != 1:
+            raise ValueError("the transposed sweep is written for one front")
         b, n, nt = self.b, self.n, self.n_tot
         v = np.zeros((nt,) * 3, dtype=np.complex128)
         v[b + 1:b + 1 + n, b + 1:b + 1 + n, b + 1:b + 1 + n] = y
