@@ -243,9 +243,21 @@ def profile_pass(solver, fn, reps):
     return {k: v / reps for k, v in ms.items()}, {k: v / reps for k, v in n.items()}
 
 
-def make_solver(w, m_dev, prec, dev):
+FRONTS = 2   # sweeping fronts of the headline workload (--fronts); its FP64 arm and the oracle use the same
+
+
+def leg_fronts(w):
+    """Fronts of a further leg: two in 2D (the setting of the paper's 2D
+    experiments); one in 3D, where the middle slab padded on both sides has
+    (b_slab + 2 b_aux) / (b_slab + b_aux) times the unknowns per block and its
+    factorization becomes the critical path of the step."""
+    return 2 if w.dim == 2 else 1
+
+
+def make_solver(w, m_dev, prec, dev, fronts=None):
     from paper_1705_09443_gb300 import LSSolver
-    return LSSolver(w.n, w.omega, m_dev, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec)
+    return LSSolver(w.n, w.omega, m_dev, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec,
+                    fronts=FRONTS if fronts is None else fronts)
 
 
 # ---------------------------------------------------------------- our arm
@@ -372,7 +384,7 @@ def run_leg(args, dev, world, flush, wname, prec, steps, warmup):
     mt = torch.tensor(m, dtype=torch.float64, device=dev)
     opts = GmresOptions(30, 1e-8, 300)
     stream = torch.cuda.current_stream()
-    s = make_solver(w, mt, prec, dev)
+    s = make_solver(w, mt, prec, dev, fronts=leg_fronts(w))
     if w.dim == 2:
         s.autotune(R)
 
@@ -388,7 +400,7 @@ def run_leg(args, dev, world, flush, wname, prec, steps, warmup):
     ts_f, _ = timed(lambda: (s.set_medium(mt), s.factor()), 1, 0, flush, stream)
     prof_ms, prof_n = profile_pass(s, step, 1)
     flat = [x for st in stats for x in st]
-    out = {"workload": wname, "precision": "mixed" if prec else "fp64", "R": R,
+    out = {"workload": wname, "precision": "mixed" if prec else "fp64", "R": R, "fronts": leg_fronts(w),
            "value": R * steps * world / (tot / 1e3), "unit": "solves/s", "ms_per_step": tot / steps,
            "solve_only": {"value": R * steps * world / (sum(ts_s) / 1e3), "ms_per_solve_call": sum(ts_s) / steps},
            "setup_factor_ms": float(ts_f[0]), "iters": float(np.mean([x["iters"] for x in flat])),
@@ -477,7 +489,7 @@ from oracle import lss_oracle as O
 w = synth.WORKLOADS[{wl!r}]
 m, dirs = synth.make_workload(w)
 t0 = time.perf_counter()
-pb = O.Problem2D(w.n, w.omega, m, O.Params(b_pml=w.b_pml, b_slab=w.b_slab))
+pb = O.Problem2D(w.n, w.omega, m, O.Params(b_pml=w.b_pml, b_slab=w.b_slab, fronts={fronts}))
 t_setup = time.perf_counter() - t0
 g = O.ls_rhs(m, w.omega, pb.kw, dirs[{rhs}])
 ts = []
@@ -501,7 +513,7 @@ def oracle_sample(wl, reps, workers, rhs0=0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     procs = []
     for q in range(workers):
-        code = ORACLE_WORKER.format(root=ROOT, wl=wl, reps=reps, rhs=rhs0 + q)
+        code = ORACLE_WORKER.format(root=ROOT, wl=wl, reps=reps, rhs=rhs0 + q, fronts=FRONTS)
         procs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
                                       stderr=subprocess.PIPE, text=True, env=env))
     out = []
@@ -524,7 +536,8 @@ def workload_text(w):
     med = (f"{w.n_gauss} Gaussians width {w.width}, c in {list(w.c_range)}" if w.medium == "gauss"
            else f"band-limited random medium (correlation length {w.width}, c in [0.8, 1.2])")
     return (f"{w.dim}D LS, n={w.n} (N={w.n ** w.dim}), omega/2pi={w.freq:g}, {med}, {w.n_rhs} plane wave(s)"
-            f"{' in one solve call' if w.n_rhs > 1 else ''}, PML {w.b_pml}, slab {w.b_slab}, GMRES(30) tol 1e-8")
+            f"{' in one solve call' if w.n_rhs > 1 else ''}, PML {w.b_pml}, slab {w.b_slab}, "
+            f"{'two sweeping fronts' if FRONTS == 2 else 'one sweeping front'}, GMRES(30) tol 1e-8")
 
 
 def reference_arm(args):
@@ -536,7 +549,7 @@ def reference_arm(args):
     R = dirs.shape[0]
     from oracle import lss_oracle as O
     t0 = time.perf_counter()
-    pb = O.Problem2D(w.n, w.omega, m, O.Params(b_pml=w.b_pml, b_slab=w.b_slab))
+    pb = O.Problem2D(w.n, w.omega, m, O.Params(b_pml=w.b_pml, b_slab=w.b_slab, fronts=FRONTS))
     t_setup = time.perf_counter() - t0
     g = O.ls_rhs(m, w.omega, pb.kw, dirs[0])
     t0 = time.perf_counter()
@@ -576,6 +589,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fronts", type=int, default=2, choices=[1, 2],
+                    help="sweeping fronts: 1 (Algorithm 2) or 2 (toward the middle slab, Sec. 2.4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-workers", type=int, default=0, help="oracle worker processes (0: min(16, cores))")
     ap.add_argument("--fp64-sample", type=int, default=8, help="single-RHS FP64 solves timed (scaled to R)")
@@ -585,6 +600,8 @@ def main():
                     help="run the headline workload's steps only (warm-up, timed steps, the profiling pass) and "
                          "print its breakdown; for profiler launch lists, not a bench line")
     args = ap.parse_args()
+    global FRONTS
+    FRONTS = args.fronts
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 

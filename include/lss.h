@@ -53,8 +53,14 @@ typedef struct { int b_pml; double C; } lss_pml;
 /* Sweep (Sec. 2.3-2.4): b_slab normal layers per slab along x1 (the first
  * slab adds the left PML, the last takes the remainder plus the right PML),
  * b_aux auxiliary moving-PML layers (0 = b_pml), n_samples squared-frequency
- * samples for the auxiliary stencils (0 = n). */
-typedef struct { int b_slab; int b_aux; int n_samples; } lss_slab;
+ * samples for the auxiliary stencils (0 = n).  fronts: 0 or 1 = one front
+ * sweeping left to right (Algorithm 2); 2 = two fronts sweeping toward the
+ * middle slab (n_slabs - 1) / 2 (Sec. 2.4 remark 1, the setting of Sec. 2.5):
+ * the slabs right of it take their auxiliary PML on the right, the middle slab
+ * on both sides (with b_slab + 2 b_aux <= 32 in 2D).  The transposed sweep,
+ * the adjoint solve and the medium gradient are built for one front and return
+ * LSS_ERR_UNSUPPORTED with two. */
+typedef struct { int b_slab; int b_aux; int n_samples; int fronts; } lss_slab;
 
 /* GMRES (Sec. 2.5): restart length, relative tolerance on ||g - A u||/||g||,
  * cap on the total number of Arnoldi steps. */

@@ -46,6 +46,7 @@ struct IfArgs {
     C* X;
     C* W;             // layers na and w-1 of the solution columns: 2 x n_tot x n_tot per problem
     C* maps;
+    int psi;          // also write Psi_i (last layer from the last-layer pin): two fronts
 };
 
 __device__ __forceinline__ double2 cfnma_i(double2 a, double2 b, double2 acc) {
@@ -82,7 +83,7 @@ __device__ void fwd_body(const IfArgs<cx<T>>& A, const IfProb& pr, int l, int ph
     const SlabDev sd = A.slabs[pr.slab];
     const int bs = G * G;
     const C* F = A.fac + sd.fac_off;
-    const int pin = pr.side == 0 ? sd.na : sd.w - 1;
+    const int pin = pr.side == 0 ? sd.na : sd.ll;
     const int s = 1 << l;
     const CrLevelOffs lv = cr_level(K, l);
     const int r = blockIdx.y;
@@ -261,7 +262,7 @@ __device__ void bwd0_body(const IfArgs<cx<T>>& A, const IfProb& pr) {
     // conflict-free), one neighbour at a time
     extern __shared__ __align__(16) unsigned char smb[];
     C* tile = reinterpret_cast<C*>(smb);   // kB0N x (G + 1)
-    const int na = sd.na, wl = sd.w - 1;
+    const int na = sd.na, wl = sd.ll;
     const bool hasR = k + 1 < K;
     const int nj = min(kB0N, K - j0);
     C* X = A.X + pr.xoff;
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(256) if_maps_kernel(IfArgs<cx<T>> A) {
     const C* W0 = A.W + pr.woff;
     const C* W1 = W0 + nt2;
     const int ns = A.n_slabs;
-    const int pin = pr.side == 0 ? sd.na : sd.w - 1;
+    const int pin = pr.side == 0 ? sd.na : sd.ll;
     const int base = pr.side == 0 ? 0 : 6;   // coupling slot of layer offset -1 / +1
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nt2; e += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(e / K), j = (int)(e % K);
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(256) if_maps_kernel(IfArgs<cx<T>> A) {
             A.maps[(1LL * ns + i) * nt2 + e] = v1;
         } else {
             A.maps[(2LL * ns + i) * nt2 + e] = v1;
+            if (A.psi) A.maps[(3LL * ns + i) * nt2 + e] = v0;   // Psi_i (two fronts)
         }
     }
 }
@@ -451,15 +453,17 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     using C = cx<T>;
     const int K = c->n_tot, ns = c->n_slabs;
     if (ns == 1) return LSS_OK;
-    // problems: side 0 for slabs 1..l-1, side 1 for slabs 1..l-2
+    // problems: side 0 for slabs 1..l-1, side 1 for slabs 1..l-2 (from slab 0
+    // when two fronts meet in slab 0, whose Psi_0 the meeting step needs)
     // (16-wide blocks first, then 32-wide, so that the tiled back substitution
     // can size its shared memory per block width)
     std::vector<IfProb> probs;
     long long xoff = 0, woff = 0;
     int gmax = 16, n16 = 0;
+    const int side1_first = (c->fronts == 2 && c->mid == 0) ? 0 : 1;
     for (int g : {16, 32})
         for (int side = 0; side < 2; ++side)
-            for (int i = 1; i <= (side == 0 ? ns - 1 : ns - 2); ++i) {
+            for (int i = side == 0 ? 1 : side1_first; i <= (side == 0 ? ns - 1 : ns - 2); ++i) {
                 if (c->slabs[i].ldw != g) continue;
                 IfProb p{i, side, g, 0, xoff, woff};
                 xoff += (long long)K * K * p.G;
@@ -491,6 +495,7 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     A.X = (C*)c->ifx_buf;
     A.W = A.X + xoff;
     A.maps = (C*)c->iface;
+    A.psi = c->fronts == 2;
     const size_t sh = sizeof(C) * ((size_t)3 * gmax * gmax + (size_t)8 * gmax);
     static size_t cfg_f = 0;
     std::unique_lock<std::mutex> lock(lss_config_mutex());

@@ -31,7 +31,7 @@ using cd = std::complex<double>;
 
 namespace {
 
-constexpr int kMaxBlock3 = 1600;      // largest pivot block M = w * n_tot (panel kernel shared memory)
+constexpr int kMaxBlock3 = 1760;      // largest pivot block M = w * n_tot (panel kernel shared memory: M x 128 B)
 constexpr int kNB64 = 8;              // Gauss-Jordan panel width, FP64
 constexpr int kNB32 = 16;             // Gauss-Jordan panel width, FP32
 constexpr int kNO = 64;               // outer panel width of the tensor-core path
@@ -358,9 +358,12 @@ __global__ void __launch_bounds__(32 * kGamWarps) gamma3_phys_kernel(double2* ou
 
 // Moving-PML stencils: per (sample k, auxiliary layer t = 1..b_aux, class x2,
 // class x3); along x1 the left profile of width b_aux translated so that D_i's
-// first layer plays the role of index 0; local frequency sqrt(s_k).
+// first layer plays the role of index 0 (right = 0), or the right profile
+// translated so that D_i's last layer plays the role of index n + 1 (right = 1,
+// two fronts); local frequency sqrt(s_k).
 __global__ void __launch_bounds__(32 * kGamWarps) gamma3_aux_kernel(double2* out, int n, int b, int baux, int ns,
-                                                                     double s_lo, double s_hi, double Cw, double h) {
+                                                                     double s_lo, double s_hi, double Cw, double h,
+                                                                     int right) {
     __shared__ GamSmem S[kGamWarps];
     const int nc = 2 * b + 1;
     const int wid = threadIdx.x / 32;
@@ -374,9 +377,14 @@ __global__ void __launch_bounds__(32 * kGamWarps) gamma3_aux_kernel(double2* out
     double sig[3][3];
     const int q2 = class_index3(c2, n, b), q3 = class_index3(c3, n, b);
     for (int u = 0; u < 3; ++u) {
-        const int q1 = -t - 1 + u;
         double v = 0;
-        if (q1 <= -1) { const double tt = (q1 + 1.0) / baux; v = -Cw * tt * tt; }
+        if (!right) {   // offset q1 from D_i's first layer
+            const int q1 = -t - 1 + u;
+            if (q1 <= -1) { const double tt = (q1 + 1.0) / baux; v = -Cw * tt * tt; }
+        } else {        // offset d from D_i's last layer
+            const int d = t - 1 + u;
+            if (d >= 1) { const double tt = (d - 1.0) / baux; v = Cw * tt * tt; }
+        }
         sig[0][u] = v;
         sig[1][u] = sigma_phys3(q2 - 1 + u, n, b, Cw);
         sig[2][u] = sigma_phys3(q3 - 1 + u, n, b, Cw);
@@ -400,7 +408,8 @@ __device__ __forceinline__ double m3_at(const double* m, int n, int i1, int i2, 
 // Row coefficients of every slab subproblem.  grid (blocks, n_slabs); thread
 // per row (k, a, c).  Layout in the file comment.
 __global__ void assemble3_kernel(const Slab3* __restrict__ slabs, const double* __restrict__ m,
-                                 const double2* __restrict__ gphys, const double2* __restrict__ gaux, Stencil27 st,
+                                 const double2* __restrict__ gphys, const double2* __restrict__ gaux,
+                                 const double2* __restrict__ gaux_r, Stencil27 st,
                                  double2* __restrict__ coef, int n, int b, int baux, int n_tot, int ns, double s_lo,
                                  double s_hi, double omega) {
     const Slab3 sd = slabs[blockIdx.y];
@@ -413,8 +422,9 @@ __global__ void assemble3_kernel(const Slab3* __restrict__ slabs, const double* 
         const int a = qr / n_tot, c = qr % n_tot;
         const int x1 = sd.s - sd.na + a, i2 = k - b, i3 = c - b;
         double2 row[27];
-        if (a < sd.na) {
-            const int t = sd.na - a;
+        if (a < sd.na || a > sd.ll) {   // auxiliary layer t left of D_i, or right of it
+            const bool rgt = a > sd.ll;
+            const int t = rgt ? a - sd.ll : sd.na - a;
             const double v = w2 * (1.0 - m3_at(m, n, x1, i2, i3));
             int kk = 0;
             if (ns > 1) {
@@ -422,8 +432,9 @@ __global__ void assemble3_kernel(const Slab3* __restrict__ slabs, const double* 
                 kk = (int)ceil(x - 0.5);   // nearest sample, ties to the lower one
                 kk = kk < 0 ? 0 : (kk > ns - 1 ? ns - 1 : kk);
             }
-            const double2* g =
-                gaux + ((((size_t)kk * baux + (t - 1)) * nc + pml_class3(i2, n, b)) * nc + pml_class3(i3, n, b)) * 27;
+            const double2* g = (rgt ? gaux_r : gaux) +
+                               ((((size_t)kk * baux + (t - 1)) * nc + pml_class3(i2, n, b)) * nc + pml_class3(i3, n, b)) *
+                                   27;
             for (int o = 0; o < 27; ++o) row[o] = g[o];
         } else if (x1 >= 0 && x1 <= n + 1 && i2 >= 0 && i2 <= n + 1 && i3 >= 0 && i3 <= n + 1) {
             for (int o = 0; o < 27; ++o) {
@@ -857,11 +868,22 @@ __global__ void f3_finalize(const Slab3* __restrict__ slabs, const C* __restrict
 
 // ---------------------------------------------------------------- sweep (Algorithm 2, 3D slabs)
 
-// One step of a slab solve: phase 0 = forward sweep (slab i gets f_i minus the
-// coupling to u_{i-1}), phase 1 = backward sweep (slab i gets the coupling to
-// u_{i+1}; the result is subtracted); dir 0 = forward substitution at block
-// row k, dir 1 = backward substitution.
-struct Step3 { int phase, slab, dir, k; };
+// One step of up to two slab solves that advance together: block row k of the
+// block-tridiagonal solve, dir 0 = forward substitution, 1 = backward.  One
+// front runs one slab solve at a time; two fronts (Sec. 2.4 remark 1) pair a
+// slab of the left front with one of the right front (slab[1] = -1: none), the
+// grid split in two halves.  Per slab, flags:
+//   S3_FWD  the forward sweep's solve: input f_i minus the couplings, result
+//           assigned; without it the backward correction: input the couplings,
+//           result subtracted;
+//   S3_CL   coupling H_{[i,i-1]} u_{i-1} into D_i's first layer;
+//   S3_CR   coupling H_{[i,i+1]} u_{i+1} into D_i's last layer.
+enum { S3_FWD = 1, S3_CL = 2, S3_CR = 4 };
+struct Step3 {
+    int dir, k;
+    int slab[2];
+    int flags[2];
+};
 
 struct Sweep3Args {
     const Slab3* slabs;
@@ -871,57 +893,68 @@ struct Sweep3Args {
     const void* fac;
     const void* f;      // sparsified right-hand sides on the grid (R)
     void* ut;           // sweep solution on the grid (R)
-    void* Y;            // block substitution vectors: [r][k][Mmax]
-    void* TB;           // split mode: the step input t, [r][Mmax]
+    void* Y;            // block substitution vectors, per group of the grid: [2][r][k][Mmax]
+    void* TB;           // split mode: the step input t, per group: [2][r][Mmax]
     int R;              // right-hand sides in this launch (<= kSweepRB)
     long long G;        // n_tot^3
-    int couple;         // 1: whole sweep (couplings between slabs); 0: one slab alone
     unsigned dcap;      // bytes of the shared-memory buffer for D_k^{-1} rows
     unsigned* bar;
     int* err;
 };
 
-// Input t_q of one step for right-hand side r, entry q = (a, c) of block k.
+// The half of the grid a CTA works in for a step: group g, its block index lb
+// within the group and the group's size Gg.
+struct Group3 { int g, lb, Gg; };
+__device__ __forceinline__ Group3 group_of(const Step3& st, int G) {
+    if (st.slab[1] < 0) return Group3{0, (int)blockIdx.x, G};
+    const int h = G / 2;
+    return (int)blockIdx.x < h ? Group3{0, (int)blockIdx.x, h} : Group3{1, (int)blockIdx.x - h, G - h};
+}
+
+// The coupling of layer a's rows with the neighbouring slab's layer at grid
+// x1-index X1o (x1-offset slot d1 = 0 for -1, 2 for +1): sum over the 3 x 3
+// (x2, x3) neighbours of block row k.
 template <typename C>
-__device__ __forceinline__ C step_input(const Sweep3Args& A, const Slab3& sd, const Step3& st, int r, int q) {
+__device__ __forceinline__ C layer_coupling(const Sweep3Args& A, const C* cf, int M, int k, int q, int c, int d1,
+                                            int X1o, int r) {
+    const C* ut = (const C*)A.ut;
+    const int nt = A.n_tot, K = A.n_tot;
+    const C* rowc = cf + (long long)k * 3 * M * 9;
+    C v = czero<C>();
+    for (int d2 = -1; d2 <= 1; ++d2) {
+        const int k2 = k + d2;
+        if (k2 < 0 || k2 >= K) continue;
+        for (int d3 = -1; d3 <= 1; ++d3) {
+            const int c3 = c + d3;
+            if (c3 < 0 || c3 >= nt) continue;
+            v = cfma(rowc[((long long)(d2 + 1) * M + q) * 9 + d1 * 3 + (d3 + 1)],
+                     ut[r * A.G + ((long long)X1o * nt + k2) * nt + c3], v);
+        }
+    }
+    return v;
+}
+
+// Input t_q of one step for right-hand side r, entry q = (a, c) of block k of
+// the slab sd (flags fl); Yr = this right-hand side's substitution vectors.
+template <typename C>
+__device__ __forceinline__ C step_input(const Sweep3Args& A, const Slab3& sd, int fl, int dir, int k, int r, int q,
+                                        const C* Yr) {
     const C* coef = (const C*)A.coef;
     const C* f = (const C*)A.f;
-    const C* ut = (const C*)A.ut;
-    const C* Yr = (const C*)A.Y + (long long)r * A.n_tot * A.Mmax;
-    const int nt = A.n_tot, K = A.n_tot, M = sd.M, w = sd.w, na = sd.na, k = st.k;
+    const int nt = A.n_tot, M = sd.M, w = sd.w, na = sd.na;
     const int a = q / nt, c = q % nt;
     const int X1s = sd.s + A.b;
     const C* cf = coef + sd.cf_off;
     C v = czero<C>();
-    if (st.dir == 0) {
-        if (st.phase == 0) {
-            if (a >= na) v = f[r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c];
-            if (A.couple && st.slab > 0 && a == na) {   // - H_{[i,i-1]} u_{i-1}
-                const C* rowc = cf + (long long)k * 3 * M * 9;
-                for (int d2 = -1; d2 <= 1; ++d2) {
-                    const int k2 = k + d2;
-                    if (k2 < 0 || k2 >= K) continue;
-                    for (int d3 = -1; d3 <= 1; ++d3) {
-                        const int c3 = c + d3;
-                        if (c3 < 0 || c3 >= nt) continue;
-                        v = v - rowc[((long long)(d2 + 1) * M + q) * 9 + (d3 + 1)] *
-                                    ut[r * A.G + ((long long)(X1s - 1) * nt + k2) * nt + c3];
-                    }
-                }
-            }
-        } else if (a == w - 1) {                          // H_{[i,i+1]} u_{i+1}
-            const C* rowc = cf + (long long)k * 3 * M * 9;
-            const int X1n = X1s + sd.nl;
-            for (int d2 = -1; d2 <= 1; ++d2) {
-                const int k2 = k + d2;
-                if (k2 < 0 || k2 >= K) continue;
-                for (int d3 = -1; d3 <= 1; ++d3) {
-                    const int c3 = c + d3;
-                    if (c3 < 0 || c3 >= nt) continue;
-                    v = cfma(rowc[((long long)(d2 + 1) * M + q) * 9 + 6 + (d3 + 1)],
-                             ut[r * A.G + ((long long)X1n * nt + k2) * nt + c3], v);
-                }
-            }
+    if (dir == 0) {
+        C cpl = czero<C>();
+        if ((fl & S3_CL) && a == na) cpl = cpl + layer_coupling<C>(A, cf, M, k, q, c, 0, X1s - 1, r);
+        if ((fl & S3_CR) && a == sd.ll) cpl = cpl + layer_coupling<C>(A, cf, M, k, q, c, 2, X1s + sd.nl, r);
+        if (fl & S3_FWD) {
+            if (a >= na && a <= sd.ll) v = f[r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c];
+            v = v - cpl;
+        } else {
+            v = cpl;
         }
         if (k > 0) {                                      // - C_k y_{k-1}
             const C* cc = cf + ((long long)k * 3 + 0) * M * 9 + (long long)q * 9;
@@ -952,17 +985,18 @@ __device__ __forceinline__ C step_input(const Sweep3Args& A, const Slab3& sd, co
     return v;
 }
 
-// Rows [r0, r1) of D_k^{-1} of a step as a 16-byte aligned byte window
-// [lo, lo + bytes) of the factor array; off = byte offset of the first row.
+// Rows [r0, r1) of D_k^{-1} of slab i that block lb of a group of Gg blocks
+// owns, as a 16-byte aligned byte window [lo, lo + bytes) of the factor array;
+// off = byte offset of the first row.
 struct RowWin { unsigned long long lo; unsigned bytes, off; int r0, r1; };
 template <typename C>
-__device__ __forceinline__ RowWin row_window(const Sweep3Args& A, const Step3& st, int G) {
-    const Slab3 sd = A.slabs[st.slab];
+__device__ __forceinline__ RowWin row_window(const Sweep3Args& A, int i, int k, int lb, int Gg) {
+    const Slab3 sd = A.slabs[i];
     const int M = sd.M;
     RowWin wdw;
-    wdw.r0 = (int)((long long)blockIdx.x * M / G);
-    wdw.r1 = (int)((long long)(blockIdx.x + 1) * M / G);
-    const unsigned long long a = (unsigned long long)((const C*)A.fac + sd.fac_off + (long long)st.k * M * M +
+    wdw.r0 = (int)((long long)lb * M / Gg);
+    wdw.r1 = (int)((long long)(lb + 1) * M / Gg);
+    const unsigned long long a = (unsigned long long)((const C*)A.fac + sd.fac_off + (long long)k * M * M +
                                                       (long long)wdw.r0 * M);
     const unsigned long long e = a + (unsigned long long)(wdw.r1 - wdw.r0) * M * sizeof(C);
     wdw.lo = a & ~15ull;
@@ -970,16 +1004,22 @@ __device__ __forceinline__ RowWin row_window(const Sweep3Args& A, const Step3& s
     wdw.off = (unsigned)(a - wdw.lo);
     return wdw;
 }
+template <typename C>
+__device__ __forceinline__ RowWin step_window(const Sweep3Args& A, const Step3& st, int G) {
+    const Group3 gr = group_of(st, G);
+    return row_window<C>(A, st.slab[gr.g], st.k, gr.lb, gr.Gg);
+}
 
 // One CTA per SM, persistent, walking the host-built step table.  Each step:
 // the input t of the step in shared memory, this CTA's rows of D_k^{-1} t
 // (the rows arrive by a bulk copy issued before the previous step's grid
 // barrier whenever they fit the buffer), the outputs, a grid barrier.
 // Forward substitution y_k = D_k^{-1}(v_k - C_k y_{k-1}), backward
-// x_k = y_k - D_k^{-1} B_k x_{k+1}.  SPLIT: each CTA forms only its own
-// rows of t, exchanged through global memory and a second grid barrier
-// (FP64, where forming the whole t in every CTA would cost more arithmetic
-// than the product itself); otherwise every CTA forms all of t.
+// x_k = y_k - D_k^{-1} B_k x_{k+1}.  A paired step runs two slab solves, one
+// per half of the grid.  SPLIT: each CTA forms only its own rows of t,
+// exchanged through global memory and a second grid barrier (FP64, where
+// forming the whole t in every CTA would cost more arithmetic than the
+// product itself); otherwise every CTA forms all of its slab's t.
 template <typename C, bool SPLIT>
 __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -988,10 +1028,9 @@ __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
     C* t = reinterpret_cast<C*>(dbuf + A.dcap);            // [R][Mmax]
     C* part = t + (size_t)A.R * A.Mmax;                    // [warps][kSweepRB]
     C* ut = (C*)A.ut;
-    C* Y = (C*)A.Y;
-    C* TB = (C*)A.TB;
     const int nt = A.n_tot, K = A.n_tot, G = gridDim.x, tid = threadIdx.x;
     const int nwarps = blockDim.x / 32, wid = tid / 32, lane = tid & 31;
+    const long long ystride = (long long)A.R * K * A.Mmax;   // one group's substitution vectors
     unsigned nbar = 0;   // grid barriers passed (the arrival counter starts at zero)
     // s_pending: thread 0 issued the bulk copy of the current step's rows
     // (decided by thread 0 alone, read by all after a barrier, so that the
@@ -1002,7 +1041,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
         fence_mbar_init();
         s_pending = 0;
         if (A.nsteps > 0) {
-            const RowWin wn = row_window<C>(A, A.steps[0], G);
+            const RowWin wn = step_window<C>(A, A.steps[0], G);
             if (wn.r1 > wn.r0 && wn.bytes <= A.dcap) {
                 mbar_expect_tx(mbar, wn.bytes);
                 tma_load_1d(dbuf, (const void*)wn.lo, wn.bytes, mbar);
@@ -1014,17 +1053,22 @@ __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
     unsigned pcount = 0;   // bulk copies completed so far (mbarrier phase)
     for (int s = 0; s < A.nsteps; ++s) {
         const Step3 st = A.steps[s];
-        const Slab3 sd = A.slabs[st.slab];
+        const Group3 gr = group_of(st, G);
+        const int slab = st.slab[gr.g], fl = st.flags[gr.g];
+        const Slab3 sd = A.slabs[slab];
         const int M = sd.M, k = st.k, na = sd.na;
         const int X1s = sd.s + A.b;
-        const RowWin wn = row_window<C>(A, st, G);
+        C* Y = (C*)A.Y + gr.g * ystride;
+        C* TB = (C*)A.TB + (long long)gr.g * A.R * A.Mmax;
+        const RowWin wn = row_window<C>(A, slab, k, gr.lb, gr.Gg);
         const int r0 = wn.r0, nrows = wn.r1 - wn.r0;
         const int P = nrows > 0 ? max(1, nwarps / nrows) : 1;
         // ---- t
         if (SPLIT) {
             for (int e = tid; e < nrows * A.R; e += blockDim.x) {
                 const int r = e / nrows, q = r0 + e % nrows;
-                TB[(size_t)r * A.Mmax + q] = step_input<C>(A, sd, st, r, q);
+                TB[(size_t)r * A.Mmax + q] =
+                    step_input<C>(A, sd, fl, st.dir, k, r, q, Y + (long long)r * K * A.Mmax);
             }
             grid_barrier_count(A.bar, (++nbar) * (unsigned)G, A.err);
             for (int e = tid; e < A.R * M; e += blockDim.x) {
@@ -1035,11 +1079,12 @@ __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
             const int tot = A.R * M;
             for (int e = tid; e < tot; e += 2 * blockDim.x) {
                 const int e2 = e + blockDim.x;
-                const C v1 = step_input<C>(A, sd, st, e / M, e % M);
+                const int ra = e / M, rb = e2 / M;
+                const C v1 = step_input<C>(A, sd, fl, st.dir, k, ra, e % M, Y + (long long)ra * K * A.Mmax);
                 C v2 = czero<C>();
-                if (e2 < tot) v2 = step_input<C>(A, sd, st, e2 / M, e2 % M);
-                t[(size_t)(e / M) * A.Mmax + e % M] = v1;
-                if (e2 < tot) t[(size_t)(e2 / M) * A.Mmax + e2 % M] = v2;
+                if (e2 < tot) v2 = step_input<C>(A, sd, fl, st.dir, k, rb, e2 % M, Y + (long long)rb * K * A.Mmax);
+                t[(size_t)ra * A.Mmax + e % M] = v1;
+                if (e2 < tot) t[(size_t)rb * A.Mmax + e2 % M] = v2;
             }
         }
         __syncthreads();
@@ -1076,7 +1121,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
         if (tid == 0) {
             s_pending = 0;
             if (s + 1 < A.nsteps && !(*(volatile int*)A.err & LSS_DERR_TIMEOUT)) {
-                const RowWin nx = row_window<C>(A, A.steps[s + 1], G);
+                const RowWin nx = step_window<C>(A, A.steps[s + 1], G);
                 if (nx.r1 > nx.r0 && nx.bytes <= A.dcap) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     mbar_expect_tx(mbar, nx.bytes);
@@ -1096,15 +1141,16 @@ __global__ void __launch_bounds__(kSweepThreads) sweep3_kernel(Sweep3Args A) {
             *yk = val;
             const bool final_x = st.dir == 1 || k == K - 1;
             const int a = row / nt, c = row % nt;
-            if (final_x && a >= na) {
+            if (final_x && a >= na && a <= sd.ll) {
                 C* up = ut + r * A.G + ((long long)(X1s + a - na) * nt + k) * nt + c;
-                *up = (st.phase == 0) ? val : *up - val;
+                *up = (fl & S3_FWD) ? val : *up - val;
             }
         }
         grid_barrier_count(A.bar, (++nbar) * (unsigned)G, A.err);
     }
     if (s_pending) mbar_wait(mbar, pcount & 1u, A.err);   // nothing may stay in flight at exit
 }
+
 
 __global__ void f2_to_d2_kernel(const float2* __restrict__ a, double2* __restrict__ b, long long n) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -1122,7 +1168,7 @@ void extract_f2_to_d2(double2* dst, const float2* src, long long n, int num_sms,
 void lss3_free(lss_ctx* c) {
     Ctx3* d = c->d3;
     if (!d) return;
-    void* ptrs[] = {d->d_slabs, d->khat, d->gam_phys, d->gam_aux, d->coef64, d->coef == d->coef64 ? nullptr : d->coef,
+    void* ptrs[] = {d->d_slabs, d->khat, d->gam_phys, d->gam_aux, d->gam_aux_r, d->coef64, d->coef == d->coef64 ? nullptr : d->coef,
                     d->fac, d->W, d->X, d->T, d->piv, d->rowid, d->f, d->ut, d->Y, d->mvA, d->mvB, d->TB,
                     d->steps_all, d->steps_one, d->T64};
     for (void* p : ptrs)
@@ -1166,8 +1212,9 @@ int configure3(lss_ctx* c) {
     if (!e) e = cudaFuncSetAttribute(mv3_cols<COL_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     if (!e) e = cudaFuncSetAttribute(mv3_cols<COL_KHAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     const int psm = 210 * 1024;
-    if (!e) e = cudaFuncSetAttribute(f3_panel<double2, kNB64>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
-    if (!e) e = cudaFuncSetAttribute(f3_panel<float2, kNB32>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
+    const int panel = kMaxBlock3 * kNB64 * (int)sizeof(double2);   // = kMaxBlock3 * kNB32 * sizeof(float2)
+    if (!e) e = cudaFuncSetAttribute(f3_panel<double2, kNB64>, cudaFuncAttributeMaxDynamicSharedMemorySize, panel);
+    if (!e) e = cudaFuncSetAttribute(f3_panel<float2, kNB32>, cudaFuncAttributeMaxDynamicSharedMemorySize, panel);
     if (!e) e = cudaFuncSetAttribute(sweep3_kernel<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
     if (!e) e = cudaFuncSetAttribute(sweep3_kernel<float2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
     if (e) return lss_check_cuda(c, e, "3D kernel attributes");
@@ -1308,21 +1355,28 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
     c->n_slabs = nl;
     long long cf = 0, fo = 0, wo = 0;
     d->Mmax = 0;
+    c->mid = (nl - 1) / 2;
     for (int i = 0; i < nl; ++i) {
         Slab3 sd{};
         if (i == 0) {
             sd.s = -b;
             sd.nl = (nl == 1) ? c->n_tot : b + bs;
-            sd.na = 0;
         } else {
             sd.s = i * bs;
             sd.nl = (i == nl - 1) ? (n + 2 - i * bs) + b : bs;
-            sd.na = c->b_aux;
         }
-        sd.w = sd.na + sd.nl;
+        // one front: every slab but the first padded on the left; two fronts:
+        // left of the middle slab on the left, right of it on the right, the
+        // middle slab on both sides
+        const bool left = c->fronts == 2 ? (i > 0 && i <= c->mid) : i > 0;
+        const bool right = c->fronts == 2 && i >= c->mid && i < nl - 1;
+        sd.na = left ? c->b_aux : 0;
+        sd.nr = right ? c->b_aux : 0;
+        sd.ll = sd.na + sd.nl - 1;
+        sd.w = sd.na + sd.nl + sd.nr;
         sd.M = sd.w * c->n_tot;
         if (sd.M > kMaxBlock3)
-            return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D: a slab block (layers x n_tot) exceeds 1600 unknowns");
+            return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D: a slab block (layers x n_tot) exceeds 1760 unknowns");
         sd.cf_off = cf;
         sd.fac_off = fo;
         sd.w_off = wo;
@@ -1346,6 +1400,9 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
     rc = rc ? rc : dalloc3(c, (void**)&d->gam_phys, (size_t)nc * nc * nc * 27 * sizeof(double2), "gamma");
     rc = rc ? rc : dalloc3(c, (void**)&d->gam_aux, (size_t)c->n_samples * c->b_aux * nc * nc * 27 * sizeof(double2),
                            "gamma aux");
+    if (c->fronts == 2)
+        rc = rc ? rc : dalloc3(c, (void**)&d->gam_aux_r,
+                               (size_t)c->n_samples * c->b_aux * nc * nc * 27 * sizeof(double2), "gamma aux right");
     rc = rc ? rc : dalloc3(c, (void**)&d->coef64, (size_t)cf * sizeof(double2), "coefficients");
     if (!rc) {
         if (c->prec == LSS_FP64) d->coef = d->coef64;
@@ -1386,11 +1443,15 @@ int lss3_set_medium(lss_ctx* c, cudaStream_t s) {
     Ctx3* d = c->d3;
     const int n = c->n, b = c->b, nc = 2 * b + 1;
     const long long tot = (long long)c->ns_eff * c->b_aux * nc * nc;
-    ProfScope ps(c, s, LSS_PROF_SETUP, c->prec == LSS_MIXED ? 3 : 2);
-    gamma3_aux_kernel<<<(unsigned)((tot + kGamWarps - 1) / kGamWarps), 32 * kGamWarps, 0, s>>>(
-        d->gam_aux, n, b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi, c->pml.C / c->omega, c->h);
+    const int nside = c->fronts == 2 ? 2 : 1;
+    ProfScope ps(c, s, LSS_PROF_SETUP, (c->prec == LSS_MIXED ? 2 : 1) + nside);
+    for (int right = 0; right < nside; ++right)
+        gamma3_aux_kernel<<<(unsigned)((tot + kGamWarps - 1) / kGamWarps), 32 * kGamWarps, 0, s>>>(
+            right ? d->gam_aux_r : d->gam_aux, n, b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi, c->pml.C / c->omega, c->h,
+            right);
     const Stencil27 st = stencil_args(d, c->omega);
-    assemble3_kernel<<<dim3(2 * c->num_sms, c->n_slabs), 256, 0, s>>>(d->d_slabs, c->m, d->gam_phys, d->gam_aux, st,
+    assemble3_kernel<<<dim3(2 * c->num_sms, c->n_slabs), 256, 0, s>>>(d->d_slabs, c->m, d->gam_phys, d->gam_aux,
+                                                                     d->gam_aux_r, st,
                                                                      d->coef64, n, b, c->b_aux, c->n_tot, c->ns_eff,
                                                                      c->s_lo, c->s_hi, c->omega);
     if (c->prec == LSS_MIXED)
@@ -1470,19 +1531,46 @@ int factor3_t(lss_ctx* c, cudaStream_t s) {
     return LSS_OK;
 }
 
-// Step table of the whole sweep (only < 0) or of one slab solve.
-std::vector<Step3> step_table(int n_slabs, int K, int only) {
+// Step table of the whole sweep (only < 0) or of one slab solve (its forward
+// solve alone, no couplings).  One front: forward solves of slabs 0..l-1
+// (coupled to the left neighbour), backward corrections of l-2..0 (coupled to
+// the right neighbour).  Two fronts: the forward solves of the left front
+// (0..c-1) paired with those of the right front (l-1..c+1), the middle slab c
+// with both couplings, then the backward corrections of both fronts paired
+// (c-1..0 with c+1..l-1).
+std::vector<Step3> step_table(int n_slabs, int K, int only, int fronts) {
     std::vector<Step3> v;
-    auto slab_solve = [&](int phase, int i) {
-        for (int k = 0; k < K; ++k) v.push_back({phase, i, 0, k});
-        for (int k = K - 2; k >= 0; --k) v.push_back({phase, i, 1, k});
+    auto solves = [&](int i0, int f0, int i1, int f1) {
+        for (int k = 0; k < K; ++k) v.push_back({0, k, {i0, i1}, {f0, f1}});
+        for (int k = K - 2; k >= 0; --k) v.push_back({1, k, {i0, i1}, {f0, f1}});
     };
     if (only >= 0) {
-        slab_solve(0, only);
+        solves(only, S3_FWD, -1, 0);
         return v;
     }
-    for (int i = 0; i < n_slabs; ++i) slab_solve(0, i);
-    for (int i = n_slabs - 2; i >= 0; --i) slab_solve(1, i);
+    if (fronts != 2) {
+        for (int i = 0; i < n_slabs; ++i) solves(i, S3_FWD | (i > 0 ? S3_CL : 0), -1, 0);
+        for (int i = n_slabs - 2; i >= 0; --i) solves(i, S3_CR, -1, 0);
+        return v;
+    }
+    const int c = (n_slabs - 1) / 2;
+    // pairs p of (left-front slab, right-front slab); either may be absent
+    auto paired = [&](int nL, int nR, auto left, auto right) {
+        for (int p = 0; p < std::max(nL, nR); ++p) {
+            int iL = -1, fL = 0, iR = -1, fR = 0;
+            if (p < nL) left(p, iL, fL);
+            if (p < nR) right(p, iR, fR);
+            if (iL < 0) { iL = iR; fL = fR; iR = -1; fR = 0; }
+            solves(iL, fL, iR, fR);
+        }
+    };
+    paired(c, n_slabs - 1 - c,
+           [&](int p, int& i, int& f) { i = p; f = S3_FWD | (p > 0 ? S3_CL : 0); },
+           [&](int p, int& i, int& f) { i = n_slabs - 1 - p; f = S3_FWD | (p > 0 ? S3_CR : 0); });
+    solves(c, S3_FWD | (c > 0 ? S3_CL : 0) | (c < n_slabs - 1 ? S3_CR : 0), -1, 0);
+    paired(c, n_slabs - 1 - c,
+           [&](int p, int& i, int& f) { i = c - 1 - p; f = S3_CR; },
+           [&](int p, int& i, int& f) { i = c + 1 + p; f = S3_CL; });
     return v;
 }
 
@@ -1495,11 +1583,12 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
     const int RB = std::min(R, kSweepRB);
     int rc = lss_grow(c, &d->f, &d->f_cap, (size_t)RB * G * cs);
     if (!rc) rc = lss_grow(c, &d->ut, &d->ut_cap, (size_t)RB * G * cs);
-    if (!rc) rc = lss_grow(c, &d->Y, &d->Y_cap, (size_t)RB * c->n_tot * d->Mmax * cs);
-    if (!rc && kSplit) rc = lss_grow(c, &d->TB, &d->TB_cap, (size_t)RB * d->Mmax * cs);
+    // per group of the grid (two when two fronts pair slab solves)
+    if (!rc) rc = lss_grow(c, &d->Y, &d->Y_cap, 2 * (size_t)RB * c->n_tot * d->Mmax * cs);
+    if (!rc && kSplit) rc = lss_grow(c, &d->TB, &d->TB_cap, 2 * (size_t)RB * d->Mmax * cs);
     if (rc) return rc;
     // step tables (device, cached: the whole sweep and the last single slab asked for)
-    const std::vector<Step3> tab = step_table(c->n_slabs, c->n_tot, only);
+    const std::vector<Step3> tab = step_table(c->n_slabs, c->n_tot, only, c->fronts);
     void** tab_dev = only < 0 ? &d->steps_all : &d->steps_one;
     size_t* tab_cap = only < 0 ? &d->steps_all_cap : &d->steps_one_cap;
     int* tab_key = only < 0 ? &d->steps_all_key : &d->steps_one_key;
@@ -1518,7 +1607,8 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
     const size_t fixed = 128 + ((size_t)RB * d->Mmax + (size_t)(kSweepThreads / 32) * kSweepRB) * cs;
     size_t want = 0;
     for (const Slab3& sd : d->slabs) {
-        const size_t rows = ((size_t)sd.M + grid - 1) / grid + 1;
+        const int gs = c->fronts == 2 ? grid / 2 : grid;   // CTAs per slab solve (paired steps: half the grid)
+        const size_t rows = ((size_t)sd.M + gs - 1) / gs + 1;
         want = std::max(want, rows * sd.M * cs + 32);
     }
     const size_t budget = 210 * 1024;
@@ -1572,7 +1662,6 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
         a.TB = d->TB;
         a.R = Rc;
         a.G = G;
-        a.couple = only < 0 ? 1 : 0;
         a.dcap = (unsigned)dcap;
         a.bar = c->d_bar;
         a.err = c->d_err;

@@ -12,6 +12,8 @@ struct lss_ctx;
 // x2 with n_tot blocks of M = w * n_tot unknowns (layer a, x3 index c).
 struct Slab3 {
     int s, nl, na, w, M;
+    int nr;              // auxiliary layers right of D_i (two fronts)
+    int ll;              // index of D_i's last layer within the subproblem: na + nl - 1
     long long cf_off;    // coefficient table offset (complex entries)
     long long fac_off;   // factor offset: n_tot dense M x M inverses
     long long w_off;     // work-matrix offset (M x M)
@@ -25,6 +27,7 @@ struct Ctx3 {
     double2* khat = nullptr;      // L^3 kernel transform, [k2][k3][k1], scaled by omega^2 / L^3
     double2* gam_phys = nullptr;  // (2b+1)^3 x 27 physical PML stencils
     double2* gam_aux = nullptr;   // n_samples x b_aux x (2b+1)^2 x 27 moving-PML stencils
+    double2* gam_aux_r = nullptr; // the same right of D_i (two fronts)
     double2* coef64 = nullptr;    // slab coefficient tables, complex128
     void* coef = nullptr;         // working precision (== coef64 for FP64)
     long long coef_len = 0;

@@ -34,7 +34,7 @@ void free_ctx(lss_ctx* c) {
     for (auto e : c->iter_ev)
         if (e) cudaEventDestroy(e);
     if (c->host_flags) cudaFreeHost(c->host_flags);
-    void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->coef64,
+    void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->gam_aux_r, c->coef64,
                     c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->iface_t, c->d_slabs,
                     c->d_err, c->d_bar, c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf,
                     c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf, c->hz_buf};
@@ -194,7 +194,7 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
         return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "3D: n must be in [3, 128]");
     if (!(omega > 0) || !std::isfinite(omega)) return lss_fail(nullptr, LSS_ERR_ARG, "omega must be positive");
     if (pml->b_pml < 1 || !(pml->C > 0)) return lss_fail(nullptr, LSS_ERR_ARG, "b_pml >= 1 and C > 0 required");
-    if (slab->b_slab < 1 || slab->b_aux < 0 || slab->n_samples < 0)
+    if (slab->b_slab < 1 || slab->b_aux < 0 || slab->n_samples < 0 || slab->fronts < 0 || slab->fronts > 2)
         return lss_fail(nullptr, LSS_ERR_ARG, "bad slab parameters");
     if (precision != LSS_FP64 && precision != LSS_MIXED) return lss_fail(nullptr, LSS_ERR_ARG, "bad precision");
     cudaStream_t s = (cudaStream_t)stream;
@@ -210,6 +210,7 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     c->b = pml->b_pml;
     c->b_aux = slab->b_aux ? slab->b_aux : pml->b_pml;
     c->n_samples = slab->n_samples ? slab->n_samples : g->n;
+    c->fronts = slab->fronts == 2 ? 2 : 1;
     c->n_tot = c->n + 2 + 2 * c->b;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -229,23 +230,30 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     }
 
     // slabs along x1 (Sec. 2.3): first = left PML + b_slab layers, middle b_slab,
-    // last = the remaining normal layers + right PML
+    // last = the remaining normal layers + right PML.  One front: every slab but
+    // the first is padded on the left.  Two fronts (Sec. 2.4 remark 1): the
+    // slabs left of the middle slab on the left, those right of it on the
+    // right, the middle slab on both sides.
     const int n = c->n, b = c->b, bs = slab->b_slab;
     const int nl = (n + 2 + bs - 1) / bs;
     c->n_slabs = nl;
+    c->mid = (nl - 1) / 2;
     long long coff = 0, foff = 0, woff = 0;
     for (int i = 0; i < nl; ++i) {
         SlabDev sd{};
         if (i == 0) {
             sd.s = -b;
             sd.nl = (nl == 1) ? c->n_tot : b + bs;
-            sd.na = 0;
         } else {
             sd.s = i * bs;
             sd.nl = (i == nl - 1) ? (n + 2 - i * bs) + b : bs;
-            sd.na = c->b_aux;
         }
-        sd.w = sd.na + sd.nl;
+        const bool left = c->fronts == 2 ? (i > 0 && i <= c->mid) : i > 0;
+        const bool right = c->fronts == 2 && i >= c->mid && i < nl - 1;
+        sd.na = left ? c->b_aux : 0;
+        sd.nr = right ? c->b_aux : 0;
+        sd.ll = sd.na + sd.nl - 1;
+        sd.w = sd.na + sd.nl + sd.nr;
         if (sd.w > LSS_WMAX) {
             free_ctx(c);
             return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "a slab subproblem is wider than 32 layers");
@@ -270,6 +278,9 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     rc = rc ? rc : dalloc(c, (void**)&c->khatT, (size_t)c->L * c->L * sizeof(double2), "kernel transform");
     rc = rc ? rc : dalloc(c, (void**)&c->gam_phys, (size_t)nc * nc * 9 * sizeof(double2), "gamma");
     rc = rc ? rc : dalloc(c, (void**)&c->gam_aux, (size_t)c->n_samples * c->b_aux * nc * 9 * sizeof(double2), "gamma aux");
+    if (c->fronts == 2)
+        rc = rc ? rc : dalloc(c, (void**)&c->gam_aux_r, (size_t)c->n_samples * c->b_aux * nc * 9 * sizeof(double2),
+                              "gamma aux right");
     rc = rc ? rc : dalloc(c, (void**)&c->coef64, (size_t)coff * sizeof(double2), "coefficients");
     if (!rc) {
         if (precision == LSS_FP64) c->coef = c->coef64;
@@ -280,7 +291,8 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     rc = rc ? rc : dalloc(c, &c->cr_work, (size_t)2 * woff * cs, "reduction work");
     // 64 bytes of slack: the recurrence copies 16-byte aligned windows that may
     // end up to 15 bytes past the last map row
-    rc = rc ? rc : dalloc(c, &c->iface, (size_t)3 * nl * c->n_tot * c->n_tot * cs + 64, "interface maps");
+    const int nmaps = c->fronts == 2 ? 4 : 3;
+    rc = rc ? rc : dalloc(c, &c->iface, (size_t)nmaps * nl * c->n_tot * c->n_tot * cs + 64, "interface maps");
     rc = rc ? rc : dalloc(c, (void**)&c->d_slabs, nl * sizeof(SlabDev), "slabs");
     rc = rc ? rc : dalloc(c, (void**)&c->d_err, sizeof(int), "status");
     rc = rc ? rc : dalloc(c, (void**)&c->d_bar, 2 * sizeof(unsigned), "barrier");
@@ -288,7 +300,7 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     cudaMemcpyAsync(c->d_slabs, c->slabs.data(), nl * sizeof(SlabDev), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), s);
     cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), s);
-    cudaMemsetAsync(c->iface, 0, (size_t)3 * nl * c->n_tot * c->n_tot * cs, s);
+    cudaMemsetAsync(c->iface, 0, (size_t)nmaps * nl * c->n_tot * c->n_tot * cs, s);
 
     c->coef_len = coff;
     rc = lss_fft_configure(c);
@@ -419,6 +431,8 @@ int lss_apply_P(lss_ctx* c, const void* x, void* y, int R, int transpose, void* 
     if (is_batch(c)) return lss_batch_apply(c, 1, (const double2*)x, (double2*)y, R, transpose, (cudaStream_t)stream);
     if (transpose && c->dim == 3)
         return lss_fail(c, LSS_ERR_UNSUPPORTED, "apply_P: the transposed sweep is built for 2D grids only");
+    if (transpose && c->fronts == 2)
+        return lss_fail(c, LSS_ERR_UNSUPPORTED, "apply_P: the transposed sweep is built for one front only");
     if (transpose) return lss_sweep_t(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
     return lss_sweep(c, (const double2*)x, (double2*)y, R, (cudaStream_t)stream);
 }
@@ -441,6 +455,7 @@ int lss_adjoint_solve(lss_ctx* c, const void* rhs, void* mu, int R, const lss_gm
         return lss_fail(c, LSS_ERR_ARG, "adjoint_solve: bad GMRES options");
     if (!c->factored) return lss_fail(c, LSS_ERR_STATE, "adjoint_solve before lss_factor");
     if (c->dim == 3) return lss_fail(c, LSS_ERR_UNSUPPORTED, "adjoint_solve: 2D grids only");
+    if (c->fronts == 2) return lss_fail(c, LSS_ERR_UNSUPPORTED, "adjoint_solve: one sweeping front only");
     if (is_batch(c))
         return lss_batch_solve(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
     return lss_fgmres(c, (const double2*)rhs, (double2*)mu, R, o, stats, (cudaStream_t)stream, 1);
@@ -473,6 +488,7 @@ int lss_medium_gradient(lss_ctx* c, const void* mu, const void* u, const double*
     if (!c) return LSS_ERR_ARG;
     if (!mu || !u || !dirs_host || !grad || R < 1) return lss_fail(c, LSS_ERR_ARG, "medium_gradient: bad arguments");
     if (c->dim == 3) return lss_fail(c, LSS_ERR_UNSUPPORTED, "medium_gradient: 2D grids only");
+    if (c->fronts == 2) return lss_fail(c, LSS_ERR_UNSUPPORTED, "medium_gradient: one sweeping front only");
     cudaStream_t s = (cudaStream_t)stream;
     if (is_batch(c)) return lss_batch_gradient(c, (const double2*)mu, (const double2*)u, dirs_host, R, grad, s);
     const size_t bytes = (size_t)R * c->n * c->n * sizeof(double2);

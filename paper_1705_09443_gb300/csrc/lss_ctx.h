@@ -15,8 +15,10 @@
 struct SlabDev {
     int s;          // first x1 index of D_i
     int nl;         // layers of D_i
-    int na;         // auxiliary layers (0 for the first slab)
-    int w;          // subproblem width in layers
+    int na;         // auxiliary layers left of D_i (0 for the first slab)
+    int nr;         // auxiliary layers right of D_i (two fronts: the middle slab and those right of it)
+    int ll;         // index of D_i's last layer within the subproblem: na + nl - 1
+    int w;          // subproblem width in layers: na + nl + nr
     int ldw;        // padded block size: 16 when w <= 16, else 32 (blocks are ldw x ldw, zero outside w x w)
     int cstride;    // complex entries per block row of the coefficient table (w*9 rounded up to even)
     int bs;         // complex entries per stored block (ldw x ldw, column-major)
@@ -114,6 +116,8 @@ struct lss_ctx {
     lss_pml pml{};
     lss_slab slab{};
     int b = 0, b_aux = 0, n_tot = 0, n_slabs = 0, L = 0, lgL = 0, n_samples = 0;
+    int fronts = 1;               // sweeping fronts: 1 (Algorithm 2) or 2 (toward the middle slab)
+    int mid = 0;                  // the middle slab (n_slabs - 1) / 2 where the two fronts meet
     int ns_eff = 0;               // samples used for the current medium (1 if m is constant)
     long long coef_len = 0;       // complex entries of the coefficient table
     double s_lo = 0, s_hi = 0;   // squared-frequency sample range
@@ -130,11 +134,12 @@ struct lss_ctx {
     double2* tw = nullptr;        // L twiddles exp(-2 pi i k / L)
     double2* gam_phys = nullptr;  // (2b+1)^2 x 9 PML stencils (row coefficients)
     double2* gam_aux = nullptr;   // n_samples x b_aux x (2b+1) x 9
+    double2* gam_aux_r = nullptr; // the same for the auxiliary PML right of D_i (two fronts)
     double2* coef64 = nullptr;    // slab row coefficients, complex128
     void* coef = nullptr;         // working-precision coefficients (== coef64 for FP64)
     void* fac = nullptr;          // cyclic-reduction factors of every slab (working precision)
     void* cr_work = nullptr;      // factorization work blocks, two parities (levels alternate)
-    void* iface = nullptr;        // interface maps Lambda, Gamma, Phi: 3 x n_slabs x n_tot^2
+    void* iface = nullptr;        // interface maps Lambda, Gamma, Phi (and Psi with two fronts): 3 (4) x n_slabs x n_tot^2
     void* iface_t = nullptr;      // maps of the transposed sweep (built on the first adjoint use)
     bool iface_t_valid = false;
     SlabDev* d_slabs = nullptr;

@@ -206,15 +206,15 @@ __device__ void gj0_body(const SlabDev& sd, const cx<T>* __restrict__ coef, cx<T
                 }
             }
         }
-        C v_first = czero<C>(), v_last = czero<C>();   // rows na and w-1 (selected, not indexed)
+        C v_first = czero<C>(), v_last = czero<C>();   // rows na and ll (selected, not indexed)
 #pragma unroll
         for (int p = 0; p < G; ++p) {
             const C v = (a < w && p < w) ? b[p] : czero<C>();
             out[p] = v;
             if (p == na) v_first = v;
-            if (p == w - 1) v_last = v;
+            if (p == sd.ll) v_last = v;
         }
-        if (blk == 0) {   // rows na and w-1 of D^{-1}, column a
+        if (blk == 0) {   // rows na and ll (D_i's first and last layers) of D^{-1}, column a
             P0[a] = v_first;
             P0[G + a] = v_last;
         }
@@ -672,7 +672,7 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         C v = czero<C>();
         if (pp < w) {
             if (MODE == CR_A || MODE == CR_E) {
-                if (pp >= na) v = A.f[(long long)r * nt2 + (long long)k * K + sd.s + A.b + (pp - na)];
+                if (pp >= na && pp <= sd.ll) v = A.f[(long long)r * nt2 + (long long)k * K + sd.s + A.b + (pp - na)];
                 if (MODE == CR_E) {
                     const C* ck = cf + (long long)k * sd.cstride + pp * 9;
                     const long long vec = (long long)K * A.R;
@@ -682,7 +682,7 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                             if (kk >= 0 && kk < K)
                                 v = cfnma(ck[dk + 1], A.lam[(long long)(i - 1) * vec + (long long)kk * A.R + r], v);
                         }
-                    if (pp == w - 1 && i < A.n_slabs - 1)
+                    if (pp == sd.ll && i < A.n_slabs - 1)
                         for (int dk = -1; dk <= 1; ++dk) {
                             const int kk = k + dk;
                             if (kk >= 0 && kk < K)
@@ -690,7 +690,7 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                         }
                 }
             } else {
-                if (pp >= na) v = to_c<C>(A.v_in[((long long)r * sd.nl + (pp - na)) * K + k]);
+                if (pp >= na && pp <= sd.ll) v = to_c<C>(A.v_in[((long long)r * sd.nl + (pp - na)) * K + k]);
             }
         }
         b[e] = v;
@@ -818,7 +818,7 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                     if (on) x[p] = acc[0];
                     __syncwarp();
                 } else {
-                    // only layers na and w-1: the two rows of D^{-1} against t, reduced over the group
+                    // only layers na and ll: the two rows of D^{-1} against t, reduced over the group
                     const C* pr = Dp + (size_t)t * 2 * G;
                     const C q0 = on ? pr[p] : czero<C>(), q1 = on ? pr[G + p] : czero<C>();
                     C d0 = q0 * tv, d1 = q1 * tv;
@@ -830,7 +830,7 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                         d1.y += __shfl_xor_sync(0xffffffffu, d1.y, off, G);
                     }
                     if (on && p == na) x[na] = x[na] - d0;
-                    if (on && p == w - 1 && w - 1 != na) x[w - 1] = x[w - 1] - d1;
+                    if (on && p == sd.ll && sd.ll != na) x[sd.ll] = x[sd.ll] - d1;
                 }
             }
         }
@@ -843,7 +843,7 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         const long long base = (long long)i * K * A.R + r;
         for (int k = tid; k < K; k += nth) {
             A.a_first[base + (long long)k * A.R] = row(k)[na];
-            A.a_last[base + (long long)k * A.R] = row(k)[w - 1];
+            A.a_last[base + (long long)k * A.R] = row(k)[sd.ll];
         }
     } else if (MODE == CR_E) {
         const int nl = sd.nl;
@@ -998,9 +998,131 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
     }
 }
 
-// One interface recurrence inside one thread-block cluster:
-//   forward  (lambda): out_i = base_i - M_i out_{i-1},  i = 1..l-2, out_0 = init;
-//   backward (phi):    out_i = base_i - M_i out_{i+1},  i = l-2..1, out_{l-1} = init.
+// The recurrences of the two-front sweep (Sec. 2.4 remark 1) with one
+// cooperative grid.  Slabs left of the middle slab c carry lambda_i (their
+// forward solution's last layer) and then phi_i (the final first layer);
+// slabs right of c carry phi_i = rho_i (their forward solution's first layer,
+// from the right front) and then lambda_i (the final last layer).  Maps:
+// Lambda (first-layer pin -> last layer), Gamma (-> first layer), Phi
+// (last-layer pin -> first layer), Psi (-> last layer).
+//   fronts:  lambda_i = last(a_i) - Lambda_i lambda_{i-1},  mu_i = first(a_i) - Gamma_i lambda_{i-1}  (i < c)
+//            phi_i = first(a_i) - Phi_i phi_{i+1},          nu_i = last(a_i) - Psi_i phi_{i+1}       (i > c)
+//   middle:  phi_c = first(a_c) - Gamma_c lambda_{c-1} - Phi_c phi_{c+1}
+//            lambda_c = last(a_c) - Lambda_c lambda_{c-1} - Psi_c phi_{c+1}
+//   back:    phi_i = mu_i - Phi_i phi_{i+1} (i < c),  lambda_i = nu_i - Lambda_i lambda_{i-1} (i > c)
+// Both fronts advance in the same grid step, so the dependent steps are about
+// half of the one-front recurrences'.
+template <typename T>
+__global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, int n_tot, int R,
+                                                          const cx<T>* __restrict__ iface,
+                                                          const cx<T>* __restrict__ a_first,
+                                                          const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
+                                                          unsigned* bar, int* err) {
+    using C = cx<T>;
+    __shared__ C Ms[kGtR][kGtK + 1];
+    __shared__ C Xs[kGtK][kGtC + 1];
+    const long long nt2 = (long long)n_tot * n_tot;
+    const long long vec = (long long)n_tot * R;
+    const int nrt = (n_tot + kGtR - 1) / kGtR, nct = (R + kGtC - 1) / kGtC;
+    const int ntile = nrt * nct;
+    const int ns = n_slabs, c = mid;
+    const C* LAM = iface;
+    const C* GAM = iface + (long long)ns * nt2;
+    const C* PHI = iface + 2LL * ns * nt2;
+    const C* PSI = iface + 3LL * ns * nt2;
+    auto V = [&](C* a, int i) { return a + (long long)i * vec; };
+    auto Vc = [&](const C* a, int i) { return a + (long long)i * vec; };
+    // lambda_0 and rho_{l-1}; phi_c = first(a_c) when nothing is left of c
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vec;
+         e += (long long)gridDim.x * blockDim.x) {
+        lam[e] = a_last[e];
+        V(phi, ns - 1)[e] = Vc(a_first, ns - 1)[e];
+        if (c == 0) phi[e] = a_first[e];
+    }
+    grid_barrier(bar, gridDim.x, err);
+    const int S = max(c - 1, ns - 2 - c);
+    for (int st = 0; st < S; ++st) {   // both fronts toward c
+        const int iL = 1 + st, iR = ns - 2 - st;
+        const bool onL = iL <= c - 1, onR = iR >= c + 1;
+        const int nw = 2 * (onL + onR);
+        for (int task = blockIdx.x; task < nw * ntile; task += gridDim.x) {   // uniform per CTA
+            int which = task / ntile;
+            const int t = task % ntile;
+            if (!onL) which += 2;
+            if (which == 0)
+                recur_tile<T>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct,
+                              Ms, Xs);
+            else if (which == 1)
+                recur_tile<T>(GAM + iL * nt2, V(lam, iL - 1), Vc(a_first, iL), V(phi, iL), n_tot, R, t / nct,
+                              t % nct, Ms, Xs);
+            else if (which == 2)
+                recur_tile<T>(PHI + iR * nt2, V(phi, iR + 1), Vc(a_first, iR), V(phi, iR), n_tot, R, t / nct,
+                              t % nct, Ms, Xs);
+            else
+                recur_tile<T>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct,
+                              Ms, Xs);
+        }
+        grid_barrier(bar, gridDim.x, err);
+    }
+    // the middle slab: the left coupling (when c > 0), then the right one
+    if (c > 0) {
+        for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
+            const int t = task % ntile;
+            if (task < ntile)
+                recur_tile<T>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms,
+                              Xs);
+            else
+                recur_tile<T>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms,
+                              Xs);
+        }
+        grid_barrier(bar, gridDim.x, err);
+    }
+    for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
+        const int t = task % ntile;
+        if (task < ntile)
+            recur_tile<T>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms, Xs);
+        else
+            recur_tile<T>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms, Xs);
+    }
+    grid_barrier(bar, gridDim.x, err);
+    for (int st = 0; st < S; ++st) {   // both fronts back toward the boundaries
+        const int iL = c - 1 - st, iR = c + 1 + st;
+        const bool onL = iL >= 1, onR = iR <= ns - 2;
+        const int nw = onL + onR;
+        for (int task = blockIdx.x; task < nw * ntile; task += gridDim.x) {
+            const int t = task % ntile;
+            const bool left = onL && task < ntile;
+            if (left)
+                recur_tile<T>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, Ms,
+                              Xs);
+            else
+                recur_tile<T>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, Ms,
+                              Xs);
+        }
+        grid_barrier(bar, gridDim.x, err);
+    }
+}
+
+// One interface recurrence over slabs i = i0, i0 + di, ... (nsteps of them):
+//   out_i = base_i - M_i out_{i-di},  out_{i0-di} = init.
+// One front: lambda forward (i = 1..l-2, M = Lambda, di = +1), phi backward
+// (i = l-2..1, M = Phi, di = -1).  Two fronts run two chains at once, one per
+// cluster of the launch.
+template <typename C>
+struct ChainSpec {
+    const C* maps;      // M_i at maps + i n_tot^2
+    const C* base;      // base_i at base + i n_tot R
+    const C* init;
+    C* out;
+    int i0, nsteps, di;
+};
+template <typename C>
+struct ChainPair {
+    ChainSpec<C> c[2];
+};
+
+// One interface recurrence inside one thread-block cluster (the cluster's
+// index in the launch selects the chain of the pair).
 // Each CTA owns a block of rows of the n_tot x n_tot maps and keeps the current
 // vector replicated in its shared memory; new entries are stored into every
 // CTA's copy through distributed shared memory, and the cluster barrier closes
@@ -1008,13 +1130,16 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
 // matrix rows (CW entries per lane) and base values in registers, loaded before
 // the barrier so their latency overlaps it.
 template <typename T, int RW, int CW, int NT>
-__global__ void __launch_bounds__(NT) recur_chain_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ maps,
-                                                         const cx<T>* base, const cx<T>* __restrict__ init,
-                                                         cx<T>* out, int backward) {
+__global__ void __launch_bounds__(NT) recur_chain_kernel(int n_tot, int R, ChainPair<cx<T>> P) {
     using C = cx<T>;
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int CL = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    const ChainSpec<C> S = P.c[blockIdx.x / CL];
+    const C* __restrict__ maps = S.maps;
+    const C* base = S.base;
+    const C* __restrict__ init = S.init;
+    C* out = S.out;
     extern __shared__ __align__(16) unsigned char smr[];
     C* vb = reinterpret_cast<C*>(smr);   // 2 x n_tot x R
     const long long nt2 = (long long)n_tot * n_tot;
@@ -1023,8 +1148,8 @@ __global__ void __launch_bounds__(NT) recur_chain_kernel(int n_slabs, int n_tot,
     const int r0 = min(n_tot, cr * rows_per), r1 = min(n_tot, r0 + rows_per);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int ntask = (r1 - r0) * R;
-    const int nsteps = n_slabs - 2;
-    const int i0 = backward ? n_slabs - 2 : 1, di = backward ? -1 : 1;
+    const int nsteps = S.nsteps;
+    const int i0 = S.i0, di = S.di;
     C Mr[RW][CW];
     C bv[RW];
 
@@ -1103,13 +1228,16 @@ __global__ void __launch_bounds__(NT) recur_chain_kernel(int n_slabs, int n_tot,
 LSS_HD inline long long recur_stage_ent(int rows_per, int n_tot) { return ((long long)rows_per * n_tot + 2) & ~1LL; }
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ maps,
-                                                       const cx<T>* base, const cx<T>* __restrict__ init, cx<T>* out,
-                                                       int backward, int nb, int* err) {
+__global__ void __launch_bounds__(NT) recur_tma_kernel(int n_tot, int R, ChainPair<cx<T>> P, int nb, int* err) {
     using C = cx<T>;
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int CL = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    const ChainSpec<C> S = P.c[blockIdx.x / CL];
+    const C* __restrict__ maps = S.maps;
+    const C* base = S.base;
+    const C* __restrict__ init = S.init;
+    C* out = S.out;
     extern __shared__ __align__(128) unsigned char smr2[];
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
@@ -1125,8 +1253,8 @@ __global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, i
     __shared__ __align__(8) uint64_t full[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT >> 5;
     const int ntask = nrow * R;
-    const int nsteps = n_slabs - 2;
-    const int i0 = backward ? n_slabs - 2 : 1, di = backward ? -1 : 1;
+    const int nsteps = S.nsteps;
+    const int i0 = S.i0, di = S.di;
     auto lead_of = [&](int step) {   // entries between the aligned copy start and the CTA's first row
         const C* src = maps + (long long)(i0 + step * di) * nt2 + (long long)r0 * n_tot;
         return (int)((reinterpret_cast<uintptr_t>(src) & 15) / sizeof(C));
@@ -1222,23 +1350,26 @@ __global__ void __launch_bounds__(NT) recur_tma_kernel(int n_slabs, int n_tot, i
     }
 }
 
-// mu_i = first(a_i) - Gamma_i lambda_{i-1} for i = 1..l-1, all independent:
-// one warp per (slab, row, rhs) dot product over the whole GPU.
+// out_i = base_i - M_i x_{i+dx} for slabs i = i_lo..i_hi, all independent
+// (mu_i = first(a_i) - Gamma_i lambda_{i-1}; with two fronts also
+// nu_i = last(a_i) - Psi_i phi_{i+1} and the middle slab's two couplings):
+// one warp per (slab, row, rhs) dot product over the whole GPU.  out may be
+// base (each entry is read, then written, by one warp); x is never out.
 template <typename T>
-__global__ void __launch_bounds__(256) recur_mu_kernel(int n_slabs, int n_tot, int R, const cx<T>* __restrict__ gam,
-                                                       const cx<T>* __restrict__ a_first,
-                                                       const cx<T>* __restrict__ lam, cx<T>* __restrict__ phi) {
+__global__ void __launch_bounds__(256) recur_mu_kernel(int i_lo, int i_hi, int n_tot, int R, const cx<T>* __restrict__ maps,
+                                                       const cx<T>* base, const cx<T>* __restrict__ xv, int dx,
+                                                       cx<T>* out) {
     using C = cx<T>;
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
     const long long task = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (task >= (long long)(n_slabs - 1) * vec) return;
-    const int i = 1 + (int)(task / vec);
+    if (task >= (long long)(i_hi - i_lo + 1) * vec) return;
+    const int i = i_lo + (int)(task / vec);
     const long long rem = task % vec;
     const int row = (int)(rem / R), rr = (int)(rem % R);
-    const C* lp = lam + (long long)(i - 1) * vec + rr;
-    const C* Mrow = gam + (long long)i * nt2 + (long long)row * n_tot;
+    const C* lp = xv + (long long)(i + dx) * vec + rr;
+    const C* Mrow = maps + (long long)i * nt2 + (long long)row * n_tot;
     C acc = czero<C>(), acc2 = czero<C>();
     int j = lane;
     for (; j + 32 < n_tot; j += 64) {
@@ -1251,7 +1382,7 @@ __global__ void __launch_bounds__(256) recur_mu_kernel(int n_slabs, int n_tot, i
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
     }
-    if (lane == 0) phi[(long long)i * vec + rem] = a_first[(long long)i * vec + rem] - acc;
+    if (lane == 0) out[(long long)i * vec + rem] = base[(long long)i * vec + rem] - acc;
 }
 
 // ---------------------------------------------------------------- host helpers
@@ -1562,8 +1693,7 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
 // when a warp would own more rows than its prefetch registers hold, so the
 // caller uses the grid kernel.
 template <typename T, int RW, int CW, int NT>
-int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward,
-                     int R, cudaStream_t s) {
+int launch_chain_cfg(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, cudaStream_t s) {
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(cx<T>);
     static int cl_size = 0;
     static size_t configured = 0;
@@ -1603,9 +1733,9 @@ int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     const int rows_per = (c->n_tot + cl - 1) / cl;
     if ((rows_per * R + NT / 32 - 1) / (NT / 32) > RW || c->n_tot > 32 * CW) return LSS_ERR_UNSUPPORTED;
     attr[0].val.clusterDim.x = cl;
-    cfg.gridDim = dim3(cl);
-    int ns = c->n_slabs, nt = c->n_tot;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, maps, base, init, out, backward);
+    cfg.gridDim = dim3(cl * nchains);
+    int nt = c->n_tot;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, nt, R, P);
     return lss_check_cuda(c, e, "recurrence cluster launch");
 }
 
@@ -1613,8 +1743,7 @@ int launch_chain_cfg(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
 // many ring stages (2..3) as fit beside the vectors.  LSS_ERR_UNSUPPORTED when
 // even two stages do not fit.
 template <typename T>
-int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward,
-                     int R, cudaStream_t s) {
+int launch_chain_tma(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, cudaStream_t s) {
     using C = cx<T>;
     constexpr int NT = sizeof(T) == 8 ? 512 : 1024;   // a warp per (row, rhs) task where possible
     auto kern = recur_tma_kernel<T, NT>;
@@ -1658,24 +1787,79 @@ int launch_chain_tma(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<
     while (nb >= 2 && smem_for(cl, nb) > (size_t)220 * 1024) --nb;
     if (nb < 2) return LSS_ERR_UNSUPPORTED;
     attr[0].val.clusterDim.x = cl;
-    cfg.gridDim = dim3(cl);
+    cfg.gridDim = dim3(cl * nchains);
     cfg.dynamicSmemBytes = smem_for(cl, nb);
-    int ns = c->n_slabs, nt = c->n_tot;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, ns, nt, R, maps, base, init, out, backward, nb, c->d_err);
+    int nt = c->n_tot;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, nt, R, P, nb, c->d_err);
     return lss_check_cuda(c, e, "recurrence cluster launch");
+}
+
+// One launch running nchains (1 or 2) independent chains, one cluster each.
+template <typename T>
+int launch_chains(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, cudaStream_t s) {
+    const int rc = launch_chain_tma<T>(c, P, nchains, R, s);
+    if (rc != LSS_ERR_UNSUPPORTED) return rc;
+    if constexpr (sizeof(T) == 4) {
+        if (c->n_tot <= 384) return launch_chain_cfg<T, 3, 12, 256>(c, P, nchains, R, s);
+        return launch_chain_cfg<T, 3, 20, 384>(c, P, nchains, R, s);
+    } else {
+        return launch_chain_cfg<T, 3, 9, 256>(c, P, nchains, R, s);
+    }
 }
 
 template <typename T>
 int launch_chain(lss_ctx* c, const cx<T>* maps, const cx<T>* base, const cx<T>* init, cx<T>* out, int backward, int R,
                  cudaStream_t s) {
-    const int rc = launch_chain_tma<T>(c, maps, base, init, out, backward, R, s);
-    if (rc != LSS_ERR_UNSUPPORTED) return rc;
-    if constexpr (sizeof(T) == 4) {
-        if (c->n_tot <= 384) return launch_chain_cfg<T, 3, 12, 256>(c, maps, base, init, out, backward, R, s);
-        return launch_chain_cfg<T, 3, 20, 384>(c, maps, base, init, out, backward, R, s);
+    const int ns = c->n_slabs;
+    ChainPair<cx<T>> P{};
+    P.c[0] = ChainSpec<cx<T>>{maps, base, init, out, backward ? ns - 2 : 1, ns - 2, backward ? -1 : 1};
+    return launch_chains<T>(c, P, 1, R, s);
+}
+
+template <typename T>
+int launch_products(lss_ctx* c, int i_lo, int i_hi, const cx<T>* maps, const cx<T>* base, const cx<T>* x, int dx,
+                    cx<T>* out, int R, cudaStream_t s) {
+    if (i_hi < i_lo) return LSS_OK;
+    const long long warps = (long long)(i_hi - i_lo + 1) * c->n_tot * R;
+    recur_mu_kernel<T><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(i_lo, i_hi, c->n_tot, R, maps, base, x, dx, out);
+    return lss_check_cuda(c, cudaGetLastError(), "recurrence products launch");
+}
+
+// The two-front recurrences (see recur_grid2_kernel) with the cluster chains:
+// both forward chains in one launch, the middle slab and mu / nu, both
+// backward chains in one launch.
+template <typename T>
+int launch_recur2_chains(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<T>* a_first,
+                         const cx<T>* a_last, int R, cudaStream_t s) {
+    using C = cx<T>;
+    const long long nt2 = (long long)c->n_tot * c->n_tot;
+    const long long vec = (long long)c->n_tot * R;
+    const int ns = c->n_slabs, m = c->mid;
+    const C* LAM = ifc;
+    const C* GAM = ifc + ns * nt2;
+    const C* PHI = ifc + 2LL * ns * nt2;
+    const C* PSI = ifc + 3LL * ns * nt2;
+    ChainPair<C> F{};
+    F.c[0] = ChainSpec<C>{LAM, a_last, a_last, lam, 1, std::max(0, m - 1), 1};
+    F.c[1] = ChainSpec<C>{PHI, a_first, a_first + (ns - 1) * vec, phi, ns - 2, ns - 2 - m, -1};
+    int rc = launch_chains<T>(c, F, 2, R, s);
+    if (rc) return rc;
+    if (m > 0) {
+        rc = launch_products<T>(c, 1, m - 1, GAM, a_first, lam, -1, phi, R, s);                  // mu
+        if (!rc) rc = launch_products<T>(c, m, m, GAM, a_first, lam, -1, phi, R, s);
+        if (!rc) rc = launch_products<T>(c, m, m, LAM, a_last, lam, -1, lam, R, s);
     } else {
-        return launch_chain_cfg<T, 3, 9, 256>(c, maps, base, init, out, backward, R, s);
+        rc = lss_check_cuda(c, cudaMemcpyAsync(phi, a_first, vec * sizeof(C), cudaMemcpyDeviceToDevice, s),
+                            "recurrence copy");
     }
+    if (!rc) rc = launch_products<T>(c, m + 1, ns - 2, PSI, a_last, phi, 1, lam, R, s);          // nu
+    if (!rc) rc = launch_products<T>(c, m, m, PHI, phi, phi, 1, phi, R, s);
+    if (!rc) rc = launch_products<T>(c, m, m, PSI, lam, phi, 1, lam, R, s);
+    if (rc) return rc;
+    ChainPair<C> B{};
+    B.c[0] = ChainSpec<C>{PHI, phi, phi + m * vec, phi, m - 1, std::max(0, m - 1), -1};
+    B.c[1] = ChainSpec<C>{LAM, lam, lam + m * vec, lam, m + 1, ns - 2 - m, 1};
+    return launch_chains<T>(c, B, 2, R, s);
 }
 
 // lambda chain, mu for every slab, phi chain (three launches), or the
@@ -1687,19 +1871,25 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     const long long nt2 = (long long)c->n_tot * c->n_tot;
     const long long vec = (long long)c->n_tot * R;
     const int ns = c->n_slabs;
+    const bool two = c->fronts == 2;
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(C);
     if (sh <= (size_t)200 * 1024) {
-        ProfScope ps(c, s, LSS_PROF_RECUR, 3);
-        int rc = launch_chain<T>(c, ifc, a_last, a_last, lam, 0, R, s);
-        if (rc == LSS_OK) {
-            const long long warps = (long long)(ns - 1) * vec;
-            recur_mu_kernel<T><<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(ns, c->n_tot, R, ifc + ns * nt2, a_first,
-                                                                          lam, phi);
-            rc = lss_check_cuda(c, cudaGetLastError(), "mu launch");
-            if (rc) return rc;
-            return launch_chain<T>(c, ifc + 2LL * ns * nt2, phi, phi + (long long)(ns - 1) * vec, phi, 1, R, s);
+        if (two) {
+            const int m = c->mid;
+            const int nl = 4 + (m > 0 ? 2 + (m > 1) : 0) + (ns - 2 >= m + 1);
+            ProfScope ps(c, s, LSS_PROF_RECUR, nl);
+            const int rc = launch_recur2_chains<T>(c, ifc, lam, phi, a_first, a_last, R, s);
+            if (rc != LSS_ERR_UNSUPPORTED) return rc;
+        } else {
+            ProfScope ps(c, s, LSS_PROF_RECUR, 3);
+            int rc = launch_chain<T>(c, ifc, a_last, a_last, lam, 0, R, s);
+            if (rc == LSS_OK) {
+                rc = launch_products<T>(c, 1, ns - 1, ifc + ns * nt2, a_first, lam, -1, phi, R, s);   // mu
+                if (rc) return rc;
+                return launch_chain<T>(c, ifc + 2LL * ns * nt2, phi, phi + (long long)(ns - 1) * vec, phi, 1, R, s);
+            }
+            if (rc != LSS_ERR_UNSUPPORTED) return rc;
         }
-        if (rc != LSS_ERR_UNSUPPORTED) return rc;
     }
     // a grid-synchronised kernel is not put into a captured graph
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1710,20 +1900,28 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     {
         std::lock_guard<std::mutex> lock(lss_config_mutex());
         if (!grid) {
-            int per = 0;
+            int per = 0, per2 = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, recur_grid_kernel<T>, 256, 0);
-            grid = std::max(1, per) * c->num_sms;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, recur_grid2_kernel<T>, 256, 0);
+            grid = std::max(1, std::min(per, per2)) * c->num_sms;
         }
         grid_now = grid;
     }
-    const long long tiles = 2LL * ((c->n_tot + kGtR - 1) / kGtR) * ((R + kGtC - 1) / kGtC);
+    // tiles of the widest step: lambda and mu (one front), or both fronts' two products
+    const long long tiles = (two ? 4LL : 2LL) * ((c->n_tot + kGtR - 1) / kGtR) * ((R + kGtC - 1) / kGtC);
     int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, tiles));
-    int nsl = c->n_slabs, nt = c->n_tot;
+    int nsl = c->n_slabs, nt = c->n_tot, mid = c->mid;
     unsigned* bar = c->d_bar;
     int* err = c->d_err;
-    void* args[] = {&nsl, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
     ProfScope ps(c, s, LSS_PROF_RECUR, 1);
-    cudaError_t e = cudaLaunchCooperativeKernel((void*)recur_grid_kernel<T>, dim3(nb), dim3(256), args, 0, s);
+    cudaError_t e;
+    if (two) {
+        void* args[] = {&nsl, &mid, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
+        e = cudaLaunchCooperativeKernel((void*)recur_grid2_kernel<T>, dim3(nb), dim3(256), args, 0, s);
+    } else {
+        void* args[] = {&nsl, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
+        e = cudaLaunchCooperativeKernel((void*)recur_grid_kernel<T>, dim3(nb), dim3(256), args, 0, s);
+    }
     return lss_check_cuda(c, e, "recurrence launch");
 }
 

@@ -153,12 +153,15 @@ __global__ void gamma_phys_kernel(double2* out, int n, int b, double Cw, double 
 
 // Auxiliary (moving) PML stencils: per frequency sample k, auxiliary layer
 // t = 1..b_aux (distance from D_i) and x2 class.  Along x1 the left profile of
-// width b_aux translated so that D_i's first layer plays the role of index 0.
-// R = float for the single-precision preconditioner (these stencils enter only
-// the slab subproblems, which it factors in single precision).
+// width b_aux translated so that D_i's first layer plays the role of index 0
+// (right = 0), or, for the auxiliary PML right of D_i (two fronts, right = 1),
+// the right profile translated so that D_i's last layer plays the role of
+// index n + 1.  R = float for the single-precision preconditioner (these
+// stencils enter only the slab subproblems, which it factors in single
+// precision).
 template <typename R>
 __global__ void gamma_aux_kernel(double2* out, int n, int b, int baux, int ns, double s_lo, double s_hi,
-                                 double Cw, double h) {
+                                 double Cw, double h, int right) {
     const int nc = 2 * b + 1;
     const long long tot = (long long)ns * baux * nc;
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -171,9 +174,14 @@ __global__ void gamma_aux_kernel(double2* out, int n, int b, int baux, int ns, d
     double s1[3], s2[3];
     const int q2 = class_index(c2, n, b);
     for (int u = 0; u < 3; ++u) {
-        const int q1 = -t - 1 + u;
         double v = 0;
-        if (q1 <= -1) { const double tt = (q1 + 1.0) / baux; v = -Cw * tt * tt; }
+        if (!right) {   // offset q1 from D_i's first layer
+            const int q1 = -t - 1 + u;
+            if (q1 <= -1) { const double tt = (q1 + 1.0) / baux; v = -Cw * tt * tt; }
+        } else {        // offset d from D_i's last layer
+            const int d = t - 1 + u;
+            if (d >= 1) { const double tt = (d - 1.0) / baux; v = Cw * tt * tt; }
+        }
         s1[u] = v;
         s2[u] = sigma_phys(q2 - 1 + u, n, b, Cw);
     }
@@ -189,7 +197,7 @@ __device__ __forceinline__ double m_at(const double* m, int n, int i1, int i2) {
 // Row coefficients of every slab subproblem: coef[off + k*cstride + la*9 + o].
 __global__ void assemble_kernel(const SlabDev* __restrict__ slabs, int n_slabs, const double* __restrict__ m,
                                 const double2* __restrict__ gphys, const double2* __restrict__ gaux,
-                                StencilArgs st, double2* __restrict__ coef, int n, int b, int baux, int n_tot,
+                                const double2* __restrict__ gaux_r, StencilArgs st, double2* __restrict__ coef, int n, int b, int baux, int n_tot,
                                 int ns, double s_lo, double s_hi, double omega) {
     const int i = blockIdx.y;
     if (i >= n_slabs) return;
@@ -201,8 +209,9 @@ __global__ void assemble_kernel(const SlabDev* __restrict__ slabs, int n_slabs, 
         const int k = e / sd.w, la = e % sd.w;
         const int x1 = sd.s - sd.na + la, i2 = k - b;
         double2* out = coef + sd.coef_off + (long long)k * sd.cstride + la * 9;
-        if (la < sd.na) {
-            const int t = sd.na - la;
+        if (la < sd.na || la > sd.ll) {   // auxiliary layer t left of D_i, or right of it
+            const bool rgt = la > sd.ll;
+            const int t = rgt ? la - sd.ll : sd.na - la;
             const double v = w2 * (1.0 - m_at(m, n, x1, i2));
             int kk = 0;
             if (ns > 1) {
@@ -210,7 +219,7 @@ __global__ void assemble_kernel(const SlabDev* __restrict__ slabs, int n_slabs, 
                 kk = (int)ceil(x - 0.5);  // nearest sample, ties to the lower one
                 kk = kk < 0 ? 0 : (kk > ns - 1 ? ns - 1 : kk);
             }
-            const double2* g = gaux + (((size_t)kk * baux + (t - 1)) * nc + pml_class(i2, n, b)) * 9;
+            const double2* g = (rgt ? gaux_r : gaux) + (((size_t)kk * baux + (t - 1)) * nc + pml_class(i2, n, b)) * 9;
             for (int o = 0; o < 9; ++o) out[o] = g[o];
         } else if (x1 >= 0 && x1 <= n + 1 && i2 >= 0 && i2 <= n + 1) {
             for (int o = 0; o < 9; ++o) {
@@ -349,12 +358,15 @@ int lss_build_gamma_aux(lss_ctx* c, cudaStream_t s) {
     const double Cw = c->pml.C / c->omega;
     const long long tot = (long long)c->ns_eff * c->b_aux * nc;
     const unsigned grid = (unsigned)((tot + 127) / 128);
-    if (c->prec == LSS_FP64)
-        gamma_aux_kernel<double><<<grid, 128, 0, s>>>(c->gam_aux, c->n, c->b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi,
-                                                      Cw, c->h);
-    else
-        gamma_aux_kernel<float><<<grid, 128, 0, s>>>(c->gam_aux, c->n, c->b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi,
-                                                     Cw, c->h);
+    for (int right = 0; right < (c->fronts == 2 ? 2 : 1); ++right) {
+        double2* out = right ? c->gam_aux_r : c->gam_aux;
+        if (c->prec == LSS_FP64)
+            gamma_aux_kernel<double><<<grid, 128, 0, s>>>(out, c->n, c->b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi, Cw,
+                                                          c->h, right);
+        else
+            gamma_aux_kernel<float><<<grid, 128, 0, s>>>(out, c->n, c->b, c->b_aux, c->ns_eff, c->s_lo, c->s_hi, Cw,
+                                                         c->h, right);
+    }
     return lss_check_cuda(c, cudaGetLastError(), "gamma tables");
 }
 
@@ -362,7 +374,7 @@ int lss_assemble_slabs(lss_ctx* c, cudaStream_t s) {
     ProfScope ps(c, s, LSS_PROF_SETUP, 1);
     const int per = std::max(1, (c->n_tot * LSS_WMAX + 255) / 256);
     assemble_kernel<<<dim3(std::min(per, 64), c->n_slabs), 256, 0, s>>>(
-        c->d_slabs, c->n_slabs, c->m, c->gam_phys, c->gam_aux, stencil_args(c), c->coef64, c->n, c->b, c->b_aux,
+        c->d_slabs, c->n_slabs, c->m, c->gam_phys, c->gam_aux, c->gam_aux_r, stencil_args(c), c->coef64, c->n, c->b, c->b_aux,
         c->n_tot, c->ns_eff, c->s_lo, c->s_hi, c->omega);
     return lss_check_cuda(c, cudaGetLastError(), "assemble");
 }

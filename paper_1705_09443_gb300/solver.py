@@ -44,9 +44,10 @@ class LSSolver:
 
     def __init__(self, n: int, omega: float, m: torch.Tensor, b_pml: int = 12, C: float = 10.0,
                  b_slab: int = 4, b_aux: int = 0, n_samples: int = 0, precision: int = _lib.LSS_FP64,
-                 factor: bool = True, stream=None):
+                 factor: bool = True, stream=None, fronts: int = 1):
         self.lib = _lib.load()
         self.n, self.omega = int(n), float(omega)
+        self.fronts = int(fronts)
         self.dim = m.dim()
         if m.dtype != torch.float64 or not m.is_cuda or self.dim not in (2, 3) or \
                 tuple(m.shape) != (n,) * self.dim:
@@ -56,7 +57,7 @@ class LSSolver:
         ctx = ctypes.c_void_p()
         g = _lib.Grid(self.dim, self.n)
         p = _lib.Pml(int(b_pml), float(C))
-        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples))
+        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples), int(fronts))
         check(self.lib.lss_setup(ctypes.byref(ctx), ctypes.byref(g), self.omega, m.data_ptr(), ctypes.byref(p),
                                  ctypes.byref(s), int(precision), _stream_ptr(stream)))
         self.ctx = ctx
@@ -238,7 +239,8 @@ class LSSolverBatch:
     block after the blocks of instances 0..q-1; `views` splits one."""
 
     def __init__(self, ns, omegas, ms, b_pml: int = 12, C: float = 10.0, b_slab: int = 4, b_aux: int = 0,
-                 n_samples: int = 0, precision: int = _lib.LSS_FP64, factor: bool = True, stream=None):
+                 n_samples: int = 0, precision: int = _lib.LSS_FP64, factor: bool = True, stream=None,
+                 fronts: int = 1):
         self.lib = _lib.load()
         self.ns = [int(n) for n in ns]
         self.omegas = [float(w) for w in omegas]
@@ -254,7 +256,7 @@ class LSSolverBatch:
         om = (ctypes.c_double * q)(*self.omegas)
         mp = (ctypes.c_void_p * q)(*[m.data_ptr() for m in self._ms])
         p = _lib.Pml(int(b_pml), float(C))
-        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples))
+        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples), int(fronts))
         ctx = ctypes.c_void_p()
         check(self.lib.lss_setup_batch(ctypes.byref(ctx), q, grids, om, mp, ctypes.byref(p), ctypes.byref(s),
                                        int(precision), _stream_ptr(stream)))

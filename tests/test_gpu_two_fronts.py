@@ -1,0 +1,241 @@
+"""The two-front sweep (Sec. 2.4 remark 1; the setting of Sec. 2.5) through the
+C ABI against the oracle's two-front sweep, element by element.
+
+Two fronts pad the slabs right of the middle slab c = (l-1)//2 on the right,
+c on both sides, and run the interface recurrences from both ends toward c.
+Covered: the slab layout; every slab operator T~_i (left-, right- and
+both-sided padding) at 1e-10; P at 1e-10 for one to many slabs with a ragged
+last slab, c = 0 included, through the cluster recurrences (few right-hand
+sides) and the cooperative grid recurrences (many right-hand sides, where the
+vectors do not fit a cluster's shared memory); the FGMRES solution at 1e-10
+with iterations +-1 at 1e-8; the mixed form within +2 iterations; the
+sparsified Helmholtz solve equal to the one-front one (both are H^{-1} beta^* f
+to the solve tolerance); the transposed sweep refused.  Tolerances as in the
+one-front parity tests: block LU of subproblems with condition numbers up to
+~1e4 in FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lss_oracle as O
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def crand(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def to_dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.complex128, device="cuda")
+
+
+def make(n, freq, seed, b_pml=12, b_slab=4, precision=0, fronts=2, gauss=(4, 0.08, (0.8, 1.2))):
+    from paper_1705_09443_gb300 import LSSolver
+    om = 2 * math.pi * freq
+    m = synth.gaussian_medium(n, 2, gauss[0], gauss[1], gauss[2], seed)
+    s = LSSolver(n, om, torch.tensor(m, dtype=torch.float64, device="cuda"), b_pml=b_pml, b_slab=b_slab,
+                 precision=precision, fronts=fronts)
+    return s, m, om
+
+
+@pytest.fixture(scope="module")
+def n64():
+    s, m, om = make(64, 8.0, 1706)
+    pb = O.Problem2D(64, om, m, O.Params(b_pml=12, b_slab=4, fronts=2))
+    return s, m, om, pb
+
+
+def test_slab_layout_matches_oracle(n64):
+    s, m, om, pb = n64
+    assert s.n_slabs == pb.n_slabs == 17
+    for i in range(pb.n_slabs):
+        first, nl, na = s.slab_info(i)
+        assert (first, first + nl - 1, na) == (pb.slab_first[i], pb.slab_last[i], pb.n_aux[i])
+
+
+def test_slab_operators_match_oracle(n64):
+    """Left-padded (i < 8), both-sided (the middle slab 8), right-padded (8 < i < 16)
+    and unpadded (0 and 16) subproblems."""
+    s, m, om, pb = n64
+    for i in range(pb.n_slabs):
+        nl = pb.slab_last[i] - pb.slab_first[i] + 1
+        v = crand((2, nl, pb.n_tot), 40 + i)
+        w = s.apply_slab(i, to_dev(v)).cpu().numpy()
+        for r in range(2):
+            assert rel(w[r], pb.T(i, v[r])) <= 1e-10, i
+
+
+def test_preconditioner_matches_oracle(n64):
+    s, m, om, pb = n64
+    x = crand((3, 64, 64), 7)
+    y = s.apply_P(to_dev(x)).cpu().numpy()
+    for r in range(3):
+        assert rel(y[r], pb.precondition(x[r])) <= 1e-10
+
+
+@pytest.mark.parametrize("n,b,bs", [(9, 3, 20), (9, 3, 6), (10, 3, 4), (9, 3, 3), (13, 3, 2), (37, 6, 4)])
+def test_preconditioner_ragged_and_few_slabs(n, b, bs):
+    """One slab, two (the fronts meet in slab 0), three, four, many; ragged last slabs."""
+    s, m, om = make(n, (n + 1) / 8, 3 + n, b_pml=b, b_slab=bs, gauss=(3, 0.15, (0.8, 1.2)))
+    pb = O.Problem2D(n, om, m, O.Params(b_pml=b, b_slab=bs, fronts=2))
+    assert s.n_slabs == pb.n_slabs
+    x = crand((2, n, n), 8 + n)
+    y = s.apply_P(to_dev(x)).cpu().numpy()
+    for r in range(2):
+        assert rel(y[r], pb.precondition(x[r])) <= 1e-10
+
+
+def test_grid_recurrences_with_many_right_hand_sides():
+    """R = 160 at n_tot = 66: the vectors (2 n_tot R complex FP64) exceed a
+    cluster's budget, so the cooperative two-front grid recurrences run.  Every
+    column equals the one-column application (cluster recurrences) and sampled
+    columns equal the oracle."""
+    n = 40
+    s, m, om = make(n, 5.0, 19)
+    pb = O.Problem2D(n, om, m, O.Params(b_pml=12, b_slab=4, fronts=2))
+    R = 160
+    x = crand((R, n, n), 20)
+    y = s.apply_P(to_dev(x)).cpu().numpy()
+    for r in range(0, R, 23):
+        y1 = s.apply_P(to_dev(x[r:r + 1])).cpu().numpy()[0]
+        assert rel(y[r], y1) <= 1e-12
+        assert rel(y[r], pb.precondition(x[r])) <= 1e-10
+
+
+def test_solution_matches_oracle(n64):
+    from paper_1705_09443_gb300 import GmresOptions
+    s, m, om, pb = n64
+    d = np.array([math.cos(0.4), math.sin(0.4)])
+    g = s.plane_wave_rhs(d[None])
+    u, st = s.solve(g, GmresOptions(30, 1e-13, 200))
+    ref, relres, _, _ = O.solve(64, om, m, d, problem=pb, tol=1e-13)
+    assert st[0]["converged"] and st[0]["relres_true"] <= 1e-12
+    assert rel(u[0].cpu().numpy(), ref.x) <= 1e-10
+    _, st8 = s.solve(g, GmresOptions(30, 1e-8, 200))
+    ref8, _, _, _ = O.solve(64, om, m, d, problem=pb, tol=1e-8)
+    assert abs(st8[0]["iters"] - ref8.iters) <= 1
+
+
+def test_mixed_two_fronts_within_two_iterations(n64):
+    from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED
+    s64, m, om, pb = n64
+    s32, _, _ = make(64, 8.0, 1706, precision=LSS_MIXED)
+    x = crand((1, 64, 64), 31)
+    assert rel(s32.apply_P(to_dev(x)).cpu().numpy()[0], pb.precondition(x[0])) <= 1e-4
+    g = s64.plane_wave_rhs(np.array([[1.0, 0.0]]))
+    _, st64 = s64.solve(g, GmresOptions(30, 1e-8, 200))
+    _, st32 = s32.solve(g, GmresOptions(30, 1e-8, 200))
+    assert st32[0]["relres_true"] <= 1e-8
+    assert st32[0]["iters"] <= st64[0]["iters"] + 2
+
+
+def test_helmholtz_solve_agrees_with_one_front():
+    from paper_1705_09443_gb300 import GmresOptions
+    n = 48
+    f = np.zeros((1, n, n), complex)
+    f[0, n // 2, n // 3] = (n + 1) ** 2
+    u = []
+    for fronts in (1, 2):
+        s, _, _ = make(n, 6.0, 5, fronts=fronts, gauss=(3, 0.1, (0.85, 1.15)))
+        uf, st = s.helmholtz_solve(to_dev(f), GmresOptions(30, 1e-12, 200))
+        assert st[0]["converged"]
+        u.append(uf.cpu().numpy())
+    assert rel(u[1], u[0]) <= 1e-9
+
+
+def test_transposed_sweep_is_refused(n64):
+    from paper_1705_09443_gb300 import LssError
+    s, m, om, pb = n64
+    with pytest.raises(LssError):
+        s.apply_P(to_dev(crand((1, 64, 64), 2)), transpose=True)
+
+
+# ---------------------------------------------------------------- 3D (Sec. 3.1)
+D3 = np.ones(3) / math.sqrt(3.0)
+
+
+def make3(n, b, bs, seed, precision=0, fronts=2):
+    from paper_1705_09443_gb300 import LSSolver
+    om = 2 * math.pi * (n + 1) / 8
+    m = synth.gaussian_medium(n, 3, 3, 0.15, (0.8, 1.2), seed)
+    s = LSSolver(n, om, torch.tensor(m, dtype=torch.float64, device="cuda"), b_pml=b, b_slab=bs,
+                 precision=precision, fronts=fronts)
+    return s, m, om, O.Problem3D(n, om, m, O.Params(b_pml=b, b_slab=bs, fronts=fronts))
+
+
+@pytest.fixture(scope="module")
+def n8_3d():
+    return make3(8, 3, 3, 9)
+
+
+def test_3d_slab_operators_match_oracle(n8_3d):
+    s, m, om, pb = n8_3d
+    assert s.n_slabs == pb.n_slabs == 4
+    for i in range(pb.n_slabs):
+        first, nl, na = s.slab_info(i)
+        assert (first, first + nl - 1, na) == (pb.slab_first[i], pb.slab_last[i], pb.n_aux[i])
+        v = crand((nl, pb.n_tot, pb.n_tot), 100 + i)
+        w = s.apply_slab(i, to_dev(v[None])).cpu().numpy()[0]
+        assert rel(w, pb.T(i, v)) <= 1e-10, i
+
+
+@pytest.mark.parametrize("n,b,bs", [(6, 2, 20), (6, 2, 4), (7, 2, 3), (8, 3, 3), (9, 2, 2)])
+def test_3d_preconditioner_matches_oracle(n, b, bs):
+    """One slab; two (the fronts meet in slab 0); three; four (one pair); six
+    (two pairs and an unpaired right-front slab)."""
+    s, m, om, pb = make3(n, b, bs, 3 + n)
+    assert s.n_slabs == pb.n_slabs
+    x = crand((2, n, n, n), 8 + n)
+    y = s.apply_P(to_dev(x)).cpu().numpy()
+    for r in range(2):
+        assert rel(y[r], pb.precondition(x[r])) <= 1e-10
+
+
+def test_3d_mixed_and_solution(n8_3d):
+    from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED
+    s, m, om, pb = n8_3d
+    g = s.plane_wave_rhs(D3[None])
+    u, st = s.solve(g, GmresOptions(30, 1e-13, 200))
+    ref, _, _, _ = O.solve(8, om, m, D3, problem=pb, tol=1e-13)
+    assert st[0]["converged"] and rel(u[0].cpu().numpy(), ref.x) <= 1e-10
+    s32, _, _, _ = make3(8, 3, 3, 9, precision=LSS_MIXED)
+    x = crand((1, 8, 8, 8), 5)
+    assert rel(s32.apply_P(to_dev(x)).cpu().numpy()[0], pb.precondition(x[0])) <= 1e-4
+    _, st64 = s.solve(g, GmresOptions(30, 1e-8, 200))
+    _, st32 = s32.solve(g, GmresOptions(30, 1e-8, 200))
+    assert st32[0]["relres_true"] <= 1e-8 and st32[0]["iters"] <= st64[0]["iters"] + 2
+
+
+def test_3d_workload_two_fronts_mixed():
+    """The 3D workload (n = 64, 17 slabs: 8 pairs and the middle slab padded on
+    both sides, 20 layers x 82 = 1640 unknowns per block) in mixed precision:
+    relres <= 1e-8 measured with the oracle's operator, within +2 iterations of
+    the one-front sweep."""
+    from paper_1705_09443_gb300 import GmresOptions, LSSolver, LSS_MIXED
+    w = synth.WORKLOADS["3d_n64"]
+    m, dirs = synth.make_workload(w)
+    its = []
+    for fronts in (2, 1):
+        s = LSSolver(w.n, w.omega, torch.tensor(m, dtype=torch.float64, device="cuda"), b_pml=w.b_pml,
+                     b_slab=w.b_slab, precision=LSS_MIXED, fronts=fronts)
+        g = s.plane_wave_rhs(dirs)
+        u, st = s.solve(g, GmresOptions(30, 1e-8, 200))
+        its.append(st[0]["iters"])
+        if fronts == 2:
+            kw = O.nystrom_weights(3, w.n, w.omega, w.n)
+            g_ref = O.ls_rhs(m, w.omega, kw, dirs[0])
+            res = g_ref - O.ls_apply(u[0].cpu().numpy(), m, w.omega, kw)
+            assert np.linalg.norm(res) / np.linalg.norm(g_ref) <= 1e-8 * (1 + 1e-6)
+        del s
+    assert its[0] <= its[1] + 2
