@@ -264,6 +264,7 @@ class Params:
     C: float = 10.0
     n_samples: int | None = None  # defaults to n (Sec. 2.3)
     fronts: int = 1               # 2: two sweeping fronts meeting in the middle slab (Sec. 2.4 remark 1)
+    recursive: bool = False       # 3D: slab subproblems swept along x2 (the recursive approach, Sec. 3.1)
 
 
 class _TwoFronts:
@@ -709,6 +710,8 @@ class Problem3D(_TwoFronts):
         self._gcache: dict = {}
         self._slabs()
         self._factor()
+        if self.p.recursive:
+            self._inner_factor()
 
     def m_at(self, i1: int, i2: int, i3: int) -> float:
         n = self.n
@@ -842,13 +845,15 @@ class Problem3D(_TwoFronts):
         return sp.csr_matrix((vals, (rows, cols)), shape=(sz, sz)), layers, len(aux)
 
     def _factor(self):
-        """Algorithm 1 in 3D: an LU of every slab subproblem."""
-        self.lu, self.n_aux, self.n_layers = [], [], []
+        """Algorithm 1 in 3D: an LU of every slab subproblem (not needed by the
+        recursive approach, which sweeps each subproblem instead)."""
+        self.lu, self.n_aux, self.n_layers, self.slab_layers = [], [], [], []
         for i in range(self.n_slabs):
             M, layers, na = self.subproblem(i)
-            self.lu.append(spla.splu(M.tocsc()))
+            self.lu.append(None if self.p.recursive else spla.splu(M.tocsc()))
             self.n_aux.append(na)
             self.n_layers.append(len(layers))
+            self.slab_layers.append(layers)
 
     def _T(self, i, v, trans):
         nt2 = self.n_tot ** 2
@@ -859,11 +864,170 @@ class Problem3D(_TwoFronts):
         return w[na * nt2:(na + nd) * nt2].reshape(v.shape)
 
     def T(self, i: int, v: np.ndarray) -> np.ndarray:
-        """T~_i v: zero auxiliary layers, solve, restrict to D_i."""
+        """T~_i v: zero auxiliary layers, solve, restrict to D_i (with the
+        recursive approach the solve is the inner sweep along x2)."""
+        if self.p.recursive:
+            return self.T_recursive(i, v)
         return self._T(i, v, "N")
 
     def T_transpose(self, i: int, v: np.ndarray) -> np.ndarray:
+        if self.p.recursive:
+            raise ValueError("the transposed sweep is written for the non-recursive approach")
         return self._T(i, v, "T")
+
+    # ---- the recursive approach (Sec. 3.1): each quasi-2D slab subproblem S_i
+    # swept along x2 into quasi-1D sub-slab subproblems, padded with auxiliary
+    # PML along x2 exactly as the slabs are along x1.  The sub-slabs E_j use the
+    # same partition of x2 as the slabs D_i use of x1.
+    def sigma1_of(self, i: int, x1: int) -> np.ndarray:
+        """sigma along x1 at x1-1, x1, x1+1 for a layer of slab i's subproblem:
+        the auxiliary profile on its auxiliary layers, else the physical one."""
+        s, e = self.slab_first[i], self.slab_last[i]
+        idx = np.array([x1 - 1, x1, x1 + 1])
+        if x1 < s:
+            return pml_sigma(idx - s, self.n, self.b_aux, self.p.C, self.omega)
+        if x1 > e:
+            return self.right_sigma(e, x1)
+        return self.sigma(idx)
+
+    def slab_row(self, i: int, x1: int, i2: int, i3: int) -> np.ndarray:
+        """Row of slab i's subproblem S_i at (x1, i2, i3)."""
+        s, e = self.slab_first[i], self.slab_last[i]
+        if x1 < s:
+            return self.aux_row(s, s - x1, i2, i3)
+        if x1 > e:
+            return self.aux_row_right(e, x1 - e, i2, i3)
+        return self.row(x1, i2, i3)
+
+    def inner_aux_row(self, i: int, x1: int, f: int, t: int, i3: int) -> np.ndarray:
+        """Row of an inner auxiliary point t = 1..b_aux x2-layers before the
+        first x2-layer f of a sub-slab, at (x1, f-t, i3) of slab i's
+        subproblem: along x2 the left profile of width b_aux translated so that
+        f plays the role of index 0, along x1 the layer's own profile, along x3
+        the physical one; local frequency the sample nearest omega^2 (1 - m)."""
+        a2 = f - t
+        s1 = self.sigma1_of(i, x1)
+        s2 = pml_sigma(np.array([a2 - 1, a2, a2 + 1]) - f, self.n, self.b_aux, self.p.C, self.omega)
+        s3 = self.sigma([i3 - 1, i3, i3 + 1])
+        k = nearest_sample(self.samples, self.omega ** 2 * (1.0 - self.m_at(x1, a2, i3)))
+        return self._gamma(("aux2", k, tuple(s1), tuple(s2), tuple(s3)), math.sqrt(self.samples[k]), s1, s2, s3)
+
+    def inner_subproblem(self, i: int, j: int):
+        """Matrix of sub-slab j of slab i: x1 over slab i's subproblem layers,
+        x2 over b_aux auxiliary layers (none for j = 0) then E_j, x3 over the
+        whole range; rows on E_j are S_i's, rows on the auxiliary layers are
+        inner_aux_row's; couplings leaving the set are dropped.  Unknown order
+        (x1 layer, x2 layer, x3).  Returns (matrix, x2 list, n_aux2)."""
+        b, nt, lo, hi = self.b, self.n_tot, -self.b, self.n + 1 + self.b
+        layers1 = self.slab_layers[i]
+        f, e2 = self.slab_first[j], self.slab_last[j]
+        aux2 = list(range(f - self.b_aux, f)) if j > 0 else []
+        x2s = aux2 + list(range(f, e2 + 1))
+        p1 = {x: a for a, x in enumerate(layers1)}
+        p2 = {x: a for a, x in enumerate(x2s)}
+        n2 = len(x2s)
+        rows, cols, vals = [], [], []
+        for a1, x1 in enumerate(layers1):
+            for a2, x2 in enumerate(x2s):
+                for i3 in self._range():
+                    c = self.inner_aux_row(i, x1, f, f - x2, i3) if x2 < f else self.slab_row(i, x1, x2, i3)
+                    r = (a1 * n2 + a2) * nt + (i3 + b)
+                    for o in neighbourhood_offsets(3):
+                        j1, j2, j3 = p1.get(x1 + o[0]), p2.get(x2 + o[1]), i3 + o[2]
+                        if j1 is None or j2 is None or not (lo <= j3 <= hi):
+                            continue
+                        rows.append(r)
+                        cols.append((j1 * n2 + j2) * nt + (j3 + b))
+                        vals.append(c[o[0] + 1, o[1] + 1, o[2] + 1])
+        sz = len(layers1) * n2 * nt
+        return sp.csr_matrix((vals, (rows, cols)), shape=(sz, sz)), x2s, len(aux2)
+
+    def _inner_factor(self):
+        """A sparse LU of every sub-slab subproblem, and each slab's S_i (for the
+        couplings between its sub-slabs)."""
+        self.inner_lu, self.inner_na = [], []
+        self.S = []
+        for i in range(self.n_slabs):
+            self.S.append(self.subproblem(i)[0].tocsr())
+            lus, nas = [], []
+            for j in range(self.n_slabs):
+                M, x2s, na2 = self.inner_subproblem(i, j)
+                lus.append(spla.splu(M.tocsc()))
+                nas.append(na2)
+            self.inner_lu.append(lus)
+            self.inner_na.append(nas)
+
+    def _Tinner(self, i: int, j: int, v: np.ndarray) -> np.ndarray:
+        """T~_{i,j} v: v on (x1 layers of S_i, E_j, x3), zero on the auxiliary
+        x2-layers, solve, restrict to E_j."""
+        L1, nd, nt = v.shape
+        na2 = self.inner_na[i][j]
+        rhs = np.zeros((L1, na2 + nd, nt), dtype=np.complex128)
+        rhs[:, na2:] = v
+        w = self.inner_lu[i][j].solve(rhs.reshape(-1)).reshape(rhs.shape)
+        return w[:, na2:]
+
+    def _inner_couple(self, i: int, j: int, side: int, plane: np.ndarray) -> np.ndarray:
+        """S_i's coupling of sub-slab j's first (side -1) or last (side +1)
+        x2-layer with the neighbouring x2-layer, applied to that layer's values
+        plane (x1 layers of S_i, x3)."""
+        b, nt = self.b, self.n_tot
+        L1 = len(self.slab_layers[i])
+        x2r = self.slab_first[j] if side < 0 else self.slab_last[j]
+        x2c = x2r + side
+        a1 = np.arange(L1)[:, None]
+        i3 = np.arange(nt)[None, :]
+        r_idx = ((a1 * nt + (x2r + b)) * nt + i3).reshape(-1)
+        c_idx = ((a1 * nt + (x2c + b)) * nt + i3).reshape(-1)
+        return (self.S[i][r_idx][:, c_idx] @ plane.reshape(-1)).reshape(L1, nt)
+
+    def inner_sweep(self, i: int, V: np.ndarray, T=None) -> np.ndarray:
+        """Algorithm 2 along x2 on slab i's subproblem: V on (x1 layers of S_i,
+        x2, x3); forward then backward over the sub-slabs with T~_{i,j}."""
+        T = T or (lambda j, v: self._Tinner(i, j, v))
+        b = self.b
+        nl = self.n_slabs
+        E = [slice(self.slab_first[j] + b, self.slab_last[j] + b + 1) for j in range(nl)]
+        u = [None] * nl
+        for j in range(nl):
+            v = V[:, E[j], :].copy()
+            if j > 0:
+                v[:, 0, :] -= self._inner_couple(i, j, -1, u[j - 1][:, -1, :])
+            u[j] = T(j, v)
+        for j in range(nl - 2, -1, -1):
+            w = np.zeros_like(u[j])
+            w[:, -1, :] = self._inner_couple(i, j, +1, u[j + 1][:, 0, :])
+            u[j] = u[j] - T(j, w)
+        return np.concatenate(u, axis=1)
+
+    def T_recursive(self, i: int, v: np.ndarray, T=None) -> np.ndarray:
+        """The recursive approach's T~_i v: pad v with zeros on the auxiliary
+        x1-layers, apply the inner sweep, restrict to D_i."""
+        nt = self.n_tot
+        na, nd = self.n_aux[i], v.shape[0]
+        V = np.zeros((self.n_layers[i], nt, nt), dtype=np.complex128)
+        V[na:na + nd] = v
+        return self.inner_sweep(i, V, T)[na:na + nd]
+
+    def exact_inner_ops(self, i: int):
+        """The exact Schur inverses of slab i's inner elimination: restrictions
+        to E_j of (S_i restricted to x2 <= last x2-layer of E_j)^{-1}."""
+        b, nt = self.b, self.n_tot
+        S = self.S[i].toarray()
+        L1 = len(self.slab_layers[i])
+        ops = []
+        for j in range(self.n_slabs):
+            keep = np.array([(a1 * nt + x2) * nt + x3 for a1 in range(L1) for x2 in range(self.slab_last[j] + b + 1)
+                             for x3 in range(nt)])
+            Sinv = np.linalg.inv(S[np.ix_(keep, keep)])
+            x2j = range(self.slab_first[j] + b, self.slab_last[j] + b + 1)
+            pos = {k: q for q, k in enumerate(keep)}
+            sel = np.array([pos[(a1 * nt + x2) * nt + x3] for a1 in range(L1) for x2 in x2j for x3 in range(nt)])
+            ops.append(Sinv[np.ix_(sel, sel)])
+
+        def T(j, v):
+            return (ops[j] @ v.reshape(-1)).reshape(v.shape)
+        return T
 
     def _layer_coupling(self, x1: int, plane: np.ndarray, side: int, transpose: bool) -> np.ndarray:
         """Apply the x1-offset `side` (-1 or +1) part of the rows of layer x1 to
