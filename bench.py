@@ -254,10 +254,10 @@ def leg_fronts(w):
     return 2 if w.dim == 2 else 1
 
 
-def make_solver(w, m_dev, prec, dev, fronts=None):
+def make_solver(w, m_dev, prec, dev, fronts=None, recursive=False):
     from paper_1705_09443_gb300 import LSSolver
     return LSSolver(w.n, w.omega, m_dev, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec,
-                    fronts=FRONTS if fronts is None else fronts)
+                    fronts=FRONTS if fronts is None else fronts, recursive=recursive)
 
 
 # ---------------------------------------------------------------- our arm
@@ -374,8 +374,9 @@ def run_plain_fp64(args, dev, world, flush, w, R):
                "solve_breakdown_ms": prof_ms, "solve_launches": prof_n}
 
 
-def run_leg(args, dev, world, flush, wname, prec, steps, warmup):
-    """A full-step leg (set-up + factor + RHS + solve) on another workload."""
+def run_leg(args, dev, world, flush, wname, prec, steps, warmup, recursive=False):
+    """A full-step leg (set-up + factor + RHS + solve) on another workload
+    (3D: with the recursive approach of Sec. 3.1 when asked)."""
     import torch
     from paper_1705_09443_gb300 import GmresOptions
     w = synth.WORKLOADS[wname]
@@ -384,7 +385,7 @@ def run_leg(args, dev, world, flush, wname, prec, steps, warmup):
     mt = torch.tensor(m, dtype=torch.float64, device=dev)
     opts = GmresOptions(30, 1e-8, 300)
     stream = torch.cuda.current_stream()
-    s = make_solver(w, mt, prec, dev, fronts=leg_fronts(w))
+    s = make_solver(w, mt, prec, dev, fronts=leg_fronts(w), recursive=recursive)
     if w.dim == 2:
         s.autotune(R)
 
@@ -401,6 +402,7 @@ def run_leg(args, dev, world, flush, wname, prec, steps, warmup):
     prof_ms, prof_n = profile_pass(s, step, 1)
     flat = [x for st in stats for x in st]
     out = {"workload": wname, "precision": "mixed" if prec else "fp64", "R": R, "fronts": leg_fronts(w),
+           "slab_solver": "recursive (inner sweep along x2)" if recursive else "block LU of the whole slab",
            "value": R * steps * world / (tot / 1e3), "unit": "solves/s", "ms_per_step": tot / steps,
            "solve_only": {"value": R * steps * world / (sum(ts_s) / 1e3), "ms_per_solve_call": sum(ts_s) / steps},
            "setup_factor_ms": float(ts_f[0]), "iters": float(np.mean([x["iters"] for x in flat])),
@@ -594,7 +596,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-workers", type=int, default=0, help="oracle worker processes (0: min(16, cores))")
     ap.add_argument("--fp64-sample", type=int, default=8, help="single-RHS FP64 solves timed (scaled to R)")
-    ap.add_argument("--legs", default="2d_n256,3d_n64", help="further full-step legs ('' to skip)")
+    ap.add_argument("--legs", default="2d_n256,3d_n64,3d_n64:rec",
+                    help="further full-step legs (workload[:rec] for the 3D recursive approach; 'none' to skip)")
     ap.add_argument("--ragged", type=int, default=32, help="instances of the ragged batch line (0 to skip)")
     ap.add_argument("--only-headline", action="store_true",
                     help="run the headline workload's steps only (warm-up, timed steps, the profiling pass) and "
@@ -632,8 +635,20 @@ def main():
                                        "prof_launches": plain["solve_launches"]}, 8, 1, plain["iters"], hbm, bf16)
     del head["solver"], s64
     legs = {}
-    for wname in [x for x in args.legs.split(",") if x and x != "none"]:
+    for wspec in [x for x in args.legs.split(",") if x and x != "none"]:
+        wname, _, opt = wspec.partition(":")
         wl = synth.WORKLOADS[wname]
+        if opt == "rec":   # the recursive approach (Sec. 3.1), mixed precision, against the non-recursive leg
+            sv, leg = run_leg(args, dev, world, flush, wname, LSS_MIXED, 2, 1, recursive=True)
+            base = legs.get(f"{wname}_mixed")
+            if base:
+                leg["relative_to_non_recursive"] = {
+                    "setup_factor": leg["setup_factor_ms"] / base["setup_factor_ms"],
+                    "solve": leg["solve_only"]["ms_per_solve_call"] / base["solve_only"]["ms_per_solve_call"],
+                    "iters": [leg["iters"], base["iters"]]}
+            legs[f"{wname}_recursive_mixed"] = leg
+            del sv
+            continue
         for pname, prec in (("mixed", LSS_MIXED), ("fp64", LSS_FP64)):
             heavy = wl.dim == 3 and prec == LSS_FP64
             steps = 1 if heavy else (2 if wl.dim == 3 else args.steps)

@@ -59,8 +59,12 @@ typedef struct { int b_pml; double C; } lss_pml;
  * the slabs right of it take their auxiliary PML on the right, the middle slab
  * on both sides (with b_slab + 2 b_aux <= 32 in 2D).  The transposed sweep,
  * the adjoint solve and the medium gradient are built for one front and return
- * LSS_ERR_UNSUPPORTED with two. */
-typedef struct { int b_slab; int b_aux; int n_samples; int fronts; } lss_slab;
+ * LSS_ERR_UNSUPPORTED with two.  recursive (3D only; 0 in 2D, else
+ * LSS_ERR_UNSUPPORTED): 1 = the recursive approach of Sec. 3.1, every slab
+ * subproblem swept along x2 over quasi-1D sub-slab problems (the same
+ * partition of x2, each padded before its first x2 layer with b_aux auxiliary
+ * PML layers) instead of factored whole. */
+typedef struct { int b_slab; int b_aux; int n_samples; int fronts; int recursive; } lss_slab;
 
 /* GMRES (Sec. 2.5): restart length, relative tolerance on ||g - A u||/||g||,
  * cap on the total number of Arnoldi steps. */

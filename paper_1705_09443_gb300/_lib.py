@@ -36,7 +36,8 @@ class Pml(ctypes.Structure):
 
 
 class Slab(ctypes.Structure):
-    _fields_ = [("b_slab", ctypes.c_int), ("b_aux", ctypes.c_int), ("n_samples", ctypes.c_int), ("fronts", ctypes.c_int)]
+    _fields_ = [("b_slab", ctypes.c_int), ("b_aux", ctypes.c_int), ("n_samples", ctypes.c_int), ("fronts", ctypes.c_int),
+                ("recursive", ctypes.c_int)]
 
 
 class Gmres(ctypes.Structure):

@@ -26,6 +26,7 @@
 #include "lss_common.cuh"
 #include "lss_ctx.h"
 #include "lss3d.h"
+#include "stencil3.cuh"
 
 using cd = std::complex<double>;
 
@@ -229,113 +230,6 @@ __global__ void mv3_cols(const double2* __restrict__ in, double2* __restrict__ o
 
 // ---------------------------------------------------------------- PML stencils (Eq. gamma in 3D)
 
-__device__ __forceinline__ double sigma_phys3(int q, int n, int b, double Cw) {
-    if (q <= -1) { const double t = (q + 1.0) / b; return -Cw * t * t; }
-    if (q >= n + 2) { const double t = (q - n - 2.0) / b; return Cw * t * t; }
-    return 0.0;
-}
-__device__ __forceinline__ int pml_class3(int q, int n, int b) {
-    if (q <= -1) return q + b + 1;
-    if (q >= n + 2) return b + 1 + (q - n - 2);
-    return 0;
-}
-__device__ __forceinline__ int class_index3(int cl, int n, int b) {
-    if (cl == 0) return 0;
-    if (cl <= b) return cl - b - 1;
-    return n + 2 + (cl - b - 1);
-}
-
-constexpr int kGamWarps = 4;
-struct GamSmem {
-    double2 F[27][26];
-    double2 E[3][3][3][2];   // [axis][d+1][scale][sign]
-    double vn2[26];
-    double2 q[27];
-};
-
-// One warp computes one stencil.  sig[axis][0..2] = sigma at offsets -1, 0, +1;
-// w = local frequency.  F[o][r] = exp(i w r.(dp_o + i dsigma_o)) over the 26
-// normalised directions r of {-1,0,1}^3 minus 0 (columns in lexicographic
-// order); the exponential factors per axis, E(d, v) = exp(i w v (d h + i
-// dsigma_d)) with v = +-1/sqrt(nnz(r)), and E(d, -v) has the conjugate phase
-// and the reciprocal modulus of E(d, v).  The null vector of F^T is the last
-// column of the unitary factor of a Householder QR of F (lane = column in the
-// reflector updates).  out[o] = conj(gamma_o), unit norm, centre real positive;
-// o = (d1+1)*9 + (d2+1)*3 + (d3+1).
-__device__ void gamma3_warp(const double sig[3][3], double w, double h, GamSmem& S, double2* out) {
-    const int lane = threadIdx.x & 31;
-    if (lane < 27) {
-        const int ax = lane / 9, d = (lane / 3) % 3 - 1, sc = lane % 3;
-        const double v = sc == 0 ? 1.0 : (sc == 1 ? 0.70710678118654752440 : 0.57735026918962576451);
-        const double re = d * h, im = sig[ax][d + 1] - sig[ax][1];
-        double sn, cs;
-        sincos(w * v * re, &sn, &cs);
-        const double mag = exp(-w * v * im);
-        S.E[ax][d + 1][sc][0] = mk(mag * cs, mag * sn);
-        S.E[ax][d + 1][sc][1] = mk(cs / mag, -sn / mag);
-    }
-    __syncwarp();
-    for (int e = lane; e < 27 * 26; e += 32) {
-        const int o = e / 26, col = e % 26;
-        const int rr = col < 13 ? col : col + 1;     // skip the zero direction
-        const int r[3] = {rr / 9 - 1, (rr / 3) % 3 - 1, rr % 3 - 1};
-        const int nnz = (r[0] != 0) + (r[1] != 0) + (r[2] != 0);
-        const int dd[3] = {o / 9 - 1, (o / 3) % 3 - 1, o % 3 - 1};
-        double2 f = mk(1.0, 0.0);
-        for (int ax = 0; ax < 3; ++ax)
-            if (r[ax] != 0) f = f * S.E[ax][dd[ax] + 1][nnz - 1][r[ax] < 0];
-        S.F[o][col] = f;
-    }
-    __syncwarp();
-    for (int k = 0; k < 26; ++k) {
-        double2 x = lane >= k && lane < 27 ? S.F[lane][k] : mk(0.0, 0.0);
-        double nx = cabs2(x);
-        for (int o = 16; o > 0; o >>= 1) nx += __shfl_xor_sync(0xffffffffu, nx, o);
-        nx = sqrt(nx);
-        const double2 fkk = S.F[k][k];
-        const double afk = sqrt(cabs2(fkk));
-        const double2 ph = afk > 0 ? mk(fkk.x / afk, fkk.y / afk) : mk(1.0, 0.0);
-        __syncwarp();
-        if (lane == 0) S.F[k][k] = fkk - mk(-ph.x * nx, -ph.y * nx);   // v = x - alpha e_k
-        __syncwarp();
-        x = lane >= k && lane < 27 ? S.F[lane][k] : mk(0.0, 0.0);
-        double v2 = cabs2(x);
-        for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-        if (lane == 0) S.vn2[k] = v2;
-        if (v2 > 0 && lane > k && lane < 26) {
-            double2 dot = mk(0.0, 0.0);
-            for (int i = k; i < 27; ++i) dot = cfma_conj(S.F[i][k], S.F[i][lane], dot);
-            const double2 sd = (2.0 / v2) * dot;
-            for (int i = k; i < 27; ++i) S.F[i][lane] = S.F[i][lane] - sd * S.F[i][k];
-        }
-        __syncwarp();
-    }
-    double2 q = lane == 26 ? mk(1.0, 0.0) : mk(0.0, 0.0);
-    for (int k = 25; k >= 0; --k) {
-        const double v2 = S.vn2[k];
-        if (v2 == 0) continue;
-        double2 t = lane >= k && lane < 27 ? S.F[lane][k] : mk(0.0, 0.0);
-        double2 dot = lane >= k && lane < 27 ? mk(t.x * q.x + t.y * q.y, t.x * q.y - t.y * q.x) : mk(0.0, 0.0);
-        for (int o = 16; o > 0; o >>= 1) {
-            dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
-            dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
-        }
-        if (lane >= k && lane < 27) q = q - ((2.0 / v2) * dot) * t;
-    }
-    double nq = lane < 27 ? cabs2(q) : 0.0;
-    for (int o = 16; o > 0; o >>= 1) nq += __shfl_xor_sync(0xffffffffu, nq, o);
-    nq = sqrt(nq);
-    const double2 qc = mk(__shfl_sync(0xffffffffu, q.x, 13), __shfl_sync(0xffffffffu, q.y, 13));
-    const double ac = sqrt(cabs2(qc));
-    const double2 ph = mk(qc.x / ac, -qc.y / ac);
-    if (lane < 27) {
-        double2 g = (1.0 / nq) * (q * ph);
-        if (lane == 13) g = mk(ac / nq, 0.0);
-        out[lane] = conjc(g);
-    }
-    __syncwarp();
-}
-
 // Physical PML stencils: one per (class x1, class x2, class x3), global omega.
 __global__ void __launch_bounds__(32 * kGamWarps) gamma3_phys_kernel(double2* out, int n, int b, double Cw,
                                                                       double omega, double h) {
@@ -393,17 +287,6 @@ __global__ void __launch_bounds__(32 * kGamWarps) gamma3_aux_kernel(double2* out
 }
 
 // ---------------------------------------------------------------- assembly, Q, extraction
-
-struct Stencil27 {
-    double2 a_conj[27];
-    double2 b_conj[27];
-};
-
-__device__ __forceinline__ double m3_at(const double* m, int n, int i1, int i2, int i3) {
-    return (i1 >= 1 && i1 <= n && i2 >= 1 && i2 <= n && i3 >= 1 && i3 <= n)
-               ? m[((size_t)(i1 - 1) * n + (i2 - 1)) * n + (i3 - 1)]
-               : 0.0;
-}
 
 // Row coefficients of every slab subproblem.  grid (blocks, n_slabs); thread
 // per row (k, a, c).  Layout in the file comment.
@@ -497,12 +380,14 @@ __global__ void cast3_kernel(const double2* __restrict__ a, float2* __restrict__
 
 // ---------------------------------------------------------------- factorization (block LU along x2)
 
-// W = A_k: the 9-point (d1, d3) block of coefficients with d2 = 0.
+// W = A_k: the 9-point (d1, d3) block of coefficients with d2 = 0 (in-block
+// index (a, c), c < nc: for the slabs (x1 layer, x3), for the sub-slab
+// problems of the recursive approach (x2 layer, x1 layer) with the block index
+// along x3).
 template <typename C>
-__global__ void f3_init_A(const Slab3* __restrict__ slabs, const C* __restrict__ coef, C* __restrict__ W, int n_tot,
-                          int k) {
+__global__ void f3_init_A(const Slab3* __restrict__ slabs, const C* __restrict__ coef, C* __restrict__ W, int k) {
     const Slab3 sd = slabs[blockIdx.y];
-    const int M = sd.M;
+    const int M = sd.M, n_tot = sd.nc;
     const long long MM = (long long)M * M;
     C* w = W + sd.w_off;
     const C* cf = coef + sd.cf_off + ((long long)k * 3 + 1) * M * 9;
@@ -520,9 +405,9 @@ __global__ void f3_init_A(const Slab3* __restrict__ slabs, const C* __restrict__
 // X = D_{k-1}^{-1} B_{k-1}: X[q][j] = sum_{d1,d3} Dinv[q][p] Bc[p][(d1,d3)], p = j - (d1, d3).
 template <typename C>
 __global__ void f3_schur_X(const Slab3* __restrict__ slabs, const C* __restrict__ coef, const C* __restrict__ fac,
-                           C* __restrict__ X, int n_tot, int k) {
+                           C* __restrict__ X, int k) {
     const Slab3 sd = slabs[blockIdx.y];
-    const int M = sd.M, w = sd.w;
+    const int M = sd.M, w = sd.w, n_tot = sd.nc;
     const long long MM = (long long)M * M;
     const C* Dinv = fac + sd.fac_off + (long long)(k - 1) * MM;
     const C* bc = coef + sd.cf_off + ((long long)(k - 1) * 3 + 2) * M * 9;
@@ -549,9 +434,9 @@ __global__ void f3_schur_X(const Slab3* __restrict__ slabs, const C* __restrict_
 // W = A_k - C_k X: W[i][j] = A_k[i][j] - sum_{d1,d3} Cc[i][(d1,d3)] X[i + (d1, d3)][j].
 template <typename C>
 __global__ void f3_schur_D(const Slab3* __restrict__ slabs, const C* __restrict__ coef, const C* __restrict__ X,
-                           C* __restrict__ W, int n_tot, int k) {
+                           C* __restrict__ W, int k) {
     const Slab3 sd = slabs[blockIdx.y];
-    const int M = sd.M, w = sd.w;
+    const int M = sd.M, w = sd.w, n_tot = sd.nc;
     const long long MM = (long long)M * M;
     const C* cc = coef + sd.cf_off + ((long long)k * 3 + 0) * M * 9;
     const C* ac = coef + sd.cf_off + ((long long)k * 3 + 1) * M * 9;
@@ -1168,6 +1053,7 @@ void extract_f2_to_d2(double2* dst, const float2* src, long long n, int num_sms,
 void lss3_free(lss_ctx* c) {
     Ctx3* d = c->d3;
     if (!d) return;
+    lss3r_free(c);
     void* ptrs[] = {d->d_slabs, d->khat, d->gam_phys, d->gam_aux, d->gam_aux_r, d->coef64, d->coef == d->coef64 ? nullptr : d->coef,
                     d->fac, d->W, d->X, d->T, d->piv, d->rowid, d->f, d->ut, d->Y, d->mvA, d->mvB, d->TB,
                     d->steps_all, d->steps_one, d->T64};
@@ -1374,8 +1260,10 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
         sd.nr = right ? c->b_aux : 0;
         sd.ll = sd.na + sd.nl - 1;
         sd.w = sd.na + sd.nl + sd.nr;
+        sd.nc = c->n_tot;
+        sd.oi = i;
         sd.M = sd.w * c->n_tot;
-        if (sd.M > kMaxBlock3)
+        if (sd.M > kMaxBlock3 && !c->slab.recursive)
             return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D: a slab block (layers x n_tot) exceeds 1760 unknowns");
         sd.cf_off = cf;
         sd.fac_off = fo;
@@ -1408,15 +1296,18 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
         if (c->prec == LSS_FP64) d->coef = d->coef64;
         else rc = dalloc3(c, &d->coef, (size_t)cf * cs, "coefficients fp32");
     }
-    // 64 bytes of slack: the sweep copies 16-byte aligned windows of rows that
-    // may end up to 15 bytes past the last factor entry
-    rc = rc ? rc : dalloc3(c, &d->fac, (size_t)fo * cs + 64, "slab factors");
-    rc = rc ? rc : dalloc3(c, &d->W, (size_t)wo * cs, "pivot blocks");
-    rc = rc ? rc : dalloc3(c, &d->X, (size_t)wo * cs, "Schur scratch");
-    rc = rc ? rc : dalloc3(c, &d->T, (size_t)nl * NB * d->Mmax * cs, "panel rows");
-    if (c->prec == LSS_MIXED) rc = rc ? rc : dalloc3(c, &d->T64, (size_t)nl * kNO * d->Mmax * cs, "outer panel rows");
-    rc = rc ? rc : dalloc3(c, (void**)&d->piv, (size_t)nl * NB * sizeof(int), "pivots");
-    rc = rc ? rc : dalloc3(c, (void**)&d->rowid, (size_t)nl * d->Mmax * sizeof(int), "row ids");
+    if (!c->slab.recursive) {   // (the recursive approach factors the sub-slab problems instead)
+        // 64 bytes of slack: the sweep copies 16-byte aligned windows of rows that
+        // may end up to 15 bytes past the last factor entry
+        rc = rc ? rc : dalloc3(c, &d->fac, (size_t)fo * cs + 64, "slab factors");
+        rc = rc ? rc : dalloc3(c, &d->W, (size_t)wo * cs, "pivot blocks");
+        rc = rc ? rc : dalloc3(c, &d->X, (size_t)wo * cs, "Schur scratch");
+        rc = rc ? rc : dalloc3(c, &d->T, (size_t)nl * NB * d->Mmax * cs, "panel rows");
+        if (c->prec == LSS_MIXED)
+            rc = rc ? rc : dalloc3(c, &d->T64, (size_t)nl * kNO * d->Mmax * cs, "outer panel rows");
+        rc = rc ? rc : dalloc3(c, (void**)&d->piv, (size_t)nl * NB * sizeof(int), "pivots");
+        rc = rc ? rc : dalloc3(c, (void**)&d->rowid, (size_t)nl * d->Mmax * sizeof(int), "row ids");
+    }
     rc = rc ? rc : dalloc3(c, (void**)&d->d_slabs, nl * sizeof(Slab3), "slabs");
     rc = rc ? rc : dalloc3(c, (void**)&c->d_err, sizeof(int), "status");
     rc = rc ? rc : dalloc3(c, (void**)&c->d_bar, 2 * sizeof(unsigned), "barrier");
@@ -1427,6 +1318,7 @@ int lss3_setup(lss_ctx* c, const double* m_dev, cudaStream_t s) {
     rc = configure3(c);
     if (!rc) rc = build_kernel3(c, s);
     if (!rc) rc = build_interior3(c, s);
+    if (!rc && c->slab.recursive) rc = lss3r_setup(c, s);
     if (!rc) {
         ProfScope ps(c, s, LSS_PROF_SETUP, 1);
         const int tot = nc * nc * nc;
@@ -1456,45 +1348,47 @@ int lss3_set_medium(lss_ctx* c, cudaStream_t s) {
                                                                      c->s_lo, c->s_hi, c->omega);
     if (c->prec == LSS_MIXED)
         cast3_kernel<<<4 * c->num_sms, 256, 0, s>>>(d->coef64, (float2*)d->coef, d->coef_len);
-    return lss_check_cuda(c, cudaGetLastError(), "3D set_medium");
+    int rc = lss_check_cuda(c, cudaGetLastError(), "3D set_medium");
+    if (!rc && d->rec) rc = lss3r_set_medium(c, s);
+    return rc;
 }
 
 namespace {
 
 template <typename C, int NB>
-int factor3_t(lss_ctx* c, cudaStream_t s) {
-    Ctx3* d = c->d3;
-    const int K = c->n_tot, nl = c->n_slabs, Mmax = d->Mmax;
-    const C* coef = (const C*)d->coef;
-    C* fac = (C*)d->fac;
-    C* W = (C*)d->W;
-    C* X = (C*)d->X;
-    C* T = (C*)d->T;
+int factor_set_t(lss_ctx* c, const FactorSet3& fs, cudaStream_t s) {
+    const int K = c->n_tot, nl = fs.count, Mmax = fs.Mmax;
+    const Slab3* slabs = fs.d_slabs;
+    const C* coef = (const C*)fs.coef;
+    C* fac = (C*)fs.fac;
+    C* W = (C*)fs.W;
+    C* X = (C*)fs.X;
+    C* T = (C*)fs.T;
     const long long MM = (long long)Mmax * Mmax;
     const int ew_blocks = (int)std::min<long long>(8LL * c->num_sms / std::max(1, nl) + 1, (MM + 255) / 256);
     const int tiles = (Mmax + 63) / 64;
     const int npanel = (Mmax + NB - 1) / NB;
     const size_t psm = (size_t)Mmax * NB * sizeof(C);
     bool use_tc = false;
-    if constexpr (std::is_same<C, float2>::value) use_tc = lss3_use_tc();
+    if constexpr (std::is_same<C, float2>::value) use_tc = fs.tc && lss3_use_tc();
     ProfScope ps(c, s, LSS_PROF_FACTOR, 0);
     for (int k = 0; k < K; ++k) {
         if (k == 0) {
-            f3_init_A<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(d->d_slabs, coef, W, c->n_tot, 0);
+            f3_init_A<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(slabs, coef, W, 0);
             c->launches[LSS_PROF_FACTOR] += 1;
         } else {
-            f3_schur_X<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(d->d_slabs, coef, fac, X, c->n_tot, k);
-            f3_schur_D<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(d->d_slabs, coef, X, W, c->n_tot, k);
+            f3_schur_X<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(slabs, coef, fac, X, k);
+            f3_schur_D<C><<<dim3(ew_blocks, nl), 256, 0, s>>>(slabs, coef, X, W, k);
             c->launches[LSS_PROF_FACTOR] += 2;
         }
-        f3_rowid_init<<<dim3(1, nl), 256, 0, s>>>(d->d_slabs, d->rowid, Mmax);
+        f3_rowid_init<<<dim3(1, nl), 256, 0, s>>>(slabs, fs.rowid, Mmax);
         if (!use_tc) {
             for (int p = 0; p < npanel; ++p) {
                 const int j0 = p * NB;
-                f3_panel<C, NB><<<nl, 512, psm, s>>>(d->d_slabs, W, d->piv, d->rowid, j0, Mmax, c->d_err);
-                f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, d->piv, T, j0,
-                                                                                   Mmax, 0, Mmax);
-                f3_update_cc<C, NB><<<dim3(tiles * tiles, nl), 256, 0, s>>>(d->d_slabs, W, T, j0, Mmax, 0, Mmax);
+                f3_panel<C, NB><<<nl, 512, psm, s>>>(slabs, W, fs.piv, fs.rowid, j0, Mmax, c->d_err);
+                f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(slabs, W, fs.piv, T, j0, Mmax,
+                                                                                   0, Mmax);
+                f3_update_cc<C, NB><<<dim3(tiles * tiles, nl), 256, 0, s>>>(slabs, W, T, j0, Mmax, 0, Mmax);
             }
             c->launches[LSS_PROF_FACTOR] += 3LL * npanel;
         } else if constexpr (std::is_same<C, float2>::value) {
@@ -1509,21 +1403,21 @@ int factor3_t(lss_ctx* c, cudaStream_t s) {
                 for (int q = 0; q < kNO / NB; ++q) {
                     const int j0 = J0 + q * NB;
                     if (j0 >= Mmax) break;
-                    f3_panel<C, NB><<<nl, 512, psm, s>>>(d->d_slabs, W, d->piv, d->rowid, j0, Mmax, c->d_err);
-                    f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, d->piv, T,
-                                                                                       j0, Mmax, J0, J0 + kNO);
-                    f3_update_cc<C, NB><<<dim3(tiles * otiles, nl), 256, 0, s>>>(d->d_slabs, W, T, j0, Mmax, J0,
+                    f3_panel<C, NB><<<nl, 512, psm, s>>>(slabs, W, fs.piv, fs.rowid, j0, Mmax, c->d_err);
+                    f3_swap_extract<C, NB><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(slabs, W, fs.piv, T, j0,
+                                                                                       Mmax, J0, J0 + kNO);
+                    f3_update_cc<C, NB><<<dim3(tiles * otiles, nl), 256, 0, s>>>(slabs, W, T, j0, Mmax, J0,
                                                                                J0 + kNO);
                     c->launches[LSS_PROF_FACTOR] += 3;
                 }
-                f3_extract_outer<C><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(d->d_slabs, W, (C*)d->T64, J0, kNO,
+                f3_extract_outer<C><<<dim3((Mmax + 255) / 256, nl), 256, 0, s>>>(slabs, W, (C*)fs.T64, J0, kNO,
                                                                                 Mmax);
-                const int rc = lss3_update_tc(c, (float2*)W, (const float2*)d->T64, J0, kNO, s);
+                const int rc = lss3_update_tc(c, (float2*)W, (const float2*)fs.T64, J0, kNO, s);
                 if (rc) return rc;
                 c->launches[LSS_PROF_FACTOR] += 2;
             }
         }
-        f3_finalize<C><<<dim3(ew_blocks, nl), 256, Mmax * sizeof(int), s>>>(d->d_slabs, W, d->rowid, fac, k, Mmax);
+        f3_finalize<C><<<dim3(ew_blocks, nl), 256, Mmax * sizeof(int), s>>>(slabs, W, fs.rowid, fac, k, Mmax);
         c->launches[LSS_PROF_FACTOR] += 2;
         const int rc = lss_check_cuda(c, cudaGetLastError(), "3D factorization launch");
         if (rc) return rc;
@@ -1574,6 +1468,61 @@ std::vector<Step3> step_table(int n_slabs, int K, int only, int fronts) {
     return v;
 }
 
+// The sweep's grid right-hand sides for Rc vectors: f = Q r (r on I), or,
+// for lss_apply_slab (fin), the slab's layers of fin's vectors r0.. given
+// directly and zero elsewhere.
+template <typename C>
+void grid_in_t(lss_ctx* c, const double2* r, const double2* fin, int only, int r0, void* f, int Rc, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const long long G = (long long)c->n_tot * c->n_tot * c->n_tot;
+    ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+    if (!fin) {
+        sparsify3_kernel<C><<<dim3(2 * c->num_sms, Rc), 256, 0, s>>>(r, (C*)f, stencil_args(d, c->omega), c->n, c->b,
+                                                                    c->n_tot);
+        return;
+    }
+    cudaMemsetAsync(f, 0, (size_t)Rc * G * sizeof(C), s);
+    // v (nl layers x n_tot^2 per right-hand side) into the slab's layers of f
+    const Slab3& sd = d->slabs[only];
+    const long long per = (long long)sd.nl * c->n_tot * c->n_tot;
+    const long long X1 = sd.s + c->b;
+    for (int q = 0; q < Rc; ++q) {
+        if (sizeof(C) == sizeof(double2)) {
+            cudaMemcpyAsync((C*)f + q * G + X1 * c->n_tot * c->n_tot, fin + (r0 + q) * per, per * sizeof(double2),
+                            cudaMemcpyDeviceToDevice, s);
+        } else {
+            cast3_kernel<<<2 * c->num_sms, 256, 0, s>>>(fin + (r0 + q) * per,
+                                                       (float2*)f + q * G + X1 * c->n_tot * c->n_tot, per);
+        }
+    }
+}
+
+// The sweep's output for vectors r0..r0+Rc-1: ut restricted to I, or the
+// slab's layers (lss_apply_slab).
+template <typename C>
+void grid_out_t(lss_ctx* c, const void* ut, double2* y, int only, bool fin, int r0, int Rc, cudaStream_t s) {
+    Ctx3* d = c->d3;
+    const long long G = (long long)c->n_tot * c->n_tot * c->n_tot;
+    if (!fin) {
+        ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
+        extract3_kernel<C><<<dim3(2 * c->num_sms, Rc), 256, 0, s>>>((const C*)ut, y + r0 * lss3_N(c), c->n, c->b,
+                                                                    c->n_tot);
+        return;
+    }
+    const Slab3& sd = d->slabs[only];
+    const long long per = (long long)sd.nl * c->n_tot * c->n_tot;
+    const long long X1 = sd.s + c->b;
+    for (int q = 0; q < Rc; ++q) {
+        if (sizeof(C) == sizeof(double2)) {
+            cudaMemcpyAsync(y + (r0 + q) * per, (const C*)ut + q * G + X1 * c->n_tot * c->n_tot,
+                            per * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+        } else {
+            extract_f2_to_d2(y + (r0 + q) * per, (const float2*)ut + q * G + X1 * c->n_tot * c->n_tot, per,
+                             c->num_sms, s);
+        }
+    }
+}
+
 template <typename C>
 int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const double2* fin, cudaStream_t s) {
     Ctx3* d = c->d3;
@@ -1600,7 +1549,6 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
         if (rc) return rc;
         *tab_key = only;
     }
-    const Stencil27 st = stencil_args(d, c->omega);
     const long long N = lss3_N(c);
     const int grid = c->num_sms;
     // shared memory: mbarrier (128 B), the D_k^{-1} row buffer, t (RB x Mmax), warp partials
@@ -1621,30 +1569,7 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
     }
     for (int r0 = 0; r0 < R; r0 += RB) {
         const int Rc = std::min(RB, R - r0);
-        {
-            ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
-            if (fin) {   // lss_apply_slab: the slab's layers given directly
-                cudaMemsetAsync(d->f, 0, (size_t)Rc * G * cs, s);
-            } else {
-                sparsify3_kernel<C><<<dim3(2 * c->num_sms, Rc), 256, 0, s>>>(r + r0 * N, (C*)d->f, st, c->n, c->b,
-                                                                            c->n_tot);
-            }
-        }
-        if (fin) {
-            // v (nl layers x n_tot^2 per right-hand side) into the slab's layers of f
-            const Slab3& sd = d->slabs[only];
-            const long long per = (long long)sd.nl * c->n_tot * c->n_tot;
-            const long long X1 = sd.s + c->b;
-            for (int q = 0; q < Rc; ++q) {
-                if (sizeof(C) == sizeof(double2)) {
-                    cudaMemcpyAsync((C*)d->f + q * G + X1 * c->n_tot * c->n_tot, fin + (r0 + q) * per,
-                                    per * sizeof(double2), cudaMemcpyDeviceToDevice, s);
-                } else {
-                    cast3_kernel<<<2 * c->num_sms, 256, 0, s>>>(fin + (r0 + q) * per,
-                                                               (float2*)d->f + q * G + X1 * c->n_tot * c->n_tot, per);
-                }
-            }
-        }
+        grid_in_t<C>(c, r ? r + r0 * N : nullptr, fin, only, r0, d->f, Rc, s);
         cudaMemsetAsync(d->ut, 0, (size_t)Rc * G * cs, s);
         cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), s);   // arrival counter of the grid barriers
         Sweep3Args a{};
@@ -1672,41 +1597,46 @@ int sweep3_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const do
                                                         dim3(kSweepThreads), args, smem, s);
             if (e) return lss_check_cuda(c, e, "3D sweep launch");
         }
-        if (!fin) {
-            ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
-            extract3_kernel<C><<<dim3(2 * c->num_sms, Rc), 256, 0, s>>>((const C*)d->ut, y + r0 * N, c->n, c->b,
-                                                                        c->n_tot);
-        } else {
-            const Slab3& sd = d->slabs[only];
-            const long long per = (long long)sd.nl * c->n_tot * c->n_tot;
-            const long long X1 = sd.s + c->b;
-            for (int q = 0; q < Rc; ++q) {
-                if (sizeof(C) == sizeof(double2)) {
-                    cudaMemcpyAsync(y + (r0 + q) * per, (C*)d->ut + q * G + X1 * c->n_tot * c->n_tot,
-                                    per * sizeof(double2), cudaMemcpyDeviceToDevice, s);
-                } else {
-                    extract_f2_to_d2(y + (r0 + q) * per, (const float2*)d->ut + q * G + X1 * c->n_tot * c->n_tot,
-                                     per, c->num_sms, s);
-                }
-            }
-        }
+        grid_out_t<C>(c, d->ut, y, only, fin != nullptr, r0, Rc, s);
     }
     return lss_check_cuda(c, cudaGetLastError(), "3D sweep");
 }
 
 }  // namespace
 
+int lss3_factor_set(lss_ctx* c, const FactorSet3& fs, cudaStream_t s) {
+    if (c->prec == LSS_FP64) return factor_set_t<double2, kNB64>(c, fs, s);
+    return factor_set_t<float2, kNB32>(c, fs, s);
+}
+
+int lss3_dalloc(lss_ctx* c, void** p, size_t bytes, const char* what) { return dalloc3(c, p, bytes, what); }
+
+void lss3_grid_in(lss_ctx* c, const double2* r, const double2* fin, int only, int r0, void* f, int Rc,
+                  cudaStream_t s) {
+    if (c->prec == LSS_FP64) grid_in_t<double2>(c, r, fin, only, r0, f, Rc, s);
+    else grid_in_t<float2>(c, r, fin, only, r0, f, Rc, s);
+}
+
+void lss3_grid_out(lss_ctx* c, const void* ut, double2* y, int only, bool fin, int r0, int Rc, cudaStream_t s) {
+    if (c->prec == LSS_FP64) grid_out_t<double2>(c, ut, y, only, fin, r0, Rc, s);
+    else grid_out_t<float2>(c, ut, y, only, fin, r0, Rc, s);
+}
+
 int lss3_factor(lss_ctx* c, cudaStream_t s) {
-    if (c->prec == LSS_FP64) return factor3_t<double2, kNB64>(c, s);
-    return factor3_t<float2, kNB32>(c, s);
+    Ctx3* d = c->d3;
+    if (d->rec) return lss3r_factor(c, s);
+    FactorSet3 fs{d->d_slabs, c->n_slabs, d->Mmax, d->coef, d->fac, d->W, d->X, d->T, d->T64, d->piv, d->rowid, true};
+    return lss3_factor_set(c, fs, s);
 }
 
 int lss3_sweep(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s) {
+    if (c->d3->rec) return lss3r_sweep(c, r, y, R, -1, nullptr, s);
     if (c->prec == LSS_FP64) return sweep3_t<double2>(c, r, y, R, -1, nullptr, s);
     return sweep3_t<float2>(c, r, y, R, -1, nullptr, s);
 }
 
 int lss3_slab_apply(lss_ctx* c, int slab, const double2* v, double2* w, int R, cudaStream_t s) {
+    if (c->d3->rec) return lss3r_sweep(c, nullptr, w, R, slab, v, s);
     if (c->prec == LSS_FP64) return sweep3_t<double2>(c, nullptr, w, R, slab, v, s);
     return sweep3_t<float2>(c, nullptr, w, R, slab, v, s);
 }

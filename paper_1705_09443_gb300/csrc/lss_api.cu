@@ -194,8 +194,11 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
         return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "3D: n must be in [3, 128]");
     if (!(omega > 0) || !std::isfinite(omega)) return lss_fail(nullptr, LSS_ERR_ARG, "omega must be positive");
     if (pml->b_pml < 1 || !(pml->C > 0)) return lss_fail(nullptr, LSS_ERR_ARG, "b_pml >= 1 and C > 0 required");
-    if (slab->b_slab < 1 || slab->b_aux < 0 || slab->n_samples < 0 || slab->fronts < 0 || slab->fronts > 2)
+    if (slab->b_slab < 1 || slab->b_aux < 0 || slab->n_samples < 0 || slab->fronts < 0 || slab->fronts > 2 ||
+        slab->recursive < 0 || slab->recursive > 1)
         return lss_fail(nullptr, LSS_ERR_ARG, "bad slab parameters");
+    if (slab->recursive && g->dim != 3)
+        return lss_fail(nullptr, LSS_ERR_UNSUPPORTED, "the recursive approach is for 3D grids");
     if (precision != LSS_FP64 && precision != LSS_MIXED) return lss_fail(nullptr, LSS_ERR_ARG, "bad precision");
     cudaStream_t s = (cudaStream_t)stream;
 

@@ -44,10 +44,11 @@ class LSSolver:
 
     def __init__(self, n: int, omega: float, m: torch.Tensor, b_pml: int = 12, C: float = 10.0,
                  b_slab: int = 4, b_aux: int = 0, n_samples: int = 0, precision: int = _lib.LSS_FP64,
-                 factor: bool = True, stream=None, fronts: int = 1):
+                 factor: bool = True, stream=None, fronts: int = 1, recursive: bool = False):
         self.lib = _lib.load()
         self.n, self.omega = int(n), float(omega)
         self.fronts = int(fronts)
+        self.recursive = bool(recursive)
         self.dim = m.dim()
         if m.dtype != torch.float64 or not m.is_cuda or self.dim not in (2, 3) or \
                 tuple(m.shape) != (n,) * self.dim:
@@ -57,7 +58,7 @@ class LSSolver:
         ctx = ctypes.c_void_p()
         g = _lib.Grid(self.dim, self.n)
         p = _lib.Pml(int(b_pml), float(C))
-        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples), int(fronts))
+        s = _lib.Slab(int(b_slab), int(b_aux), int(n_samples), int(fronts), int(bool(recursive)))
         check(self.lib.lss_setup(ctypes.byref(ctx), ctypes.byref(g), self.omega, m.data_ptr(), ctypes.byref(p),
                                  ctypes.byref(s), int(precision), _stream_ptr(stream)))
         self.ctx = ctx
