@@ -244,6 +244,7 @@ def profile_pass(solver, fn, reps):
 
 
 FRONTS = 2   # sweeping fronts of the headline workload (--fronts); its FP64 arm and the oracle use the same
+RECURSIVE = False   # 3D headline workloads: the recursive approach of Sec. 3.1 (--recursive)
 
 
 def leg_fronts(w):
@@ -254,10 +255,11 @@ def leg_fronts(w):
     return 2 if w.dim == 2 else 1
 
 
-def make_solver(w, m_dev, prec, dev, fronts=None, recursive=False):
+def make_solver(w, m_dev, prec, dev, fronts=None, recursive=None):
     from paper_1705_09443_gb300 import LSSolver
     return LSSolver(w.n, w.omega, m_dev, b_pml=w.b_pml, b_slab=w.b_slab, precision=prec,
-                    fronts=FRONTS if fronts is None else fronts, recursive=recursive)
+                    fronts=FRONTS if fronts is None else fronts,
+                    recursive=(RECURSIVE and w.dim == 3) if recursive is None else recursive)
 
 
 # ---------------------------------------------------------------- our arm
@@ -591,6 +593,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--recursive", action="store_true",
+                    help="3D workloads: the recursive approach of Sec. 3.1 for the headline solver")
     ap.add_argument("--fronts", type=int, default=2, choices=[1, 2],
                     help="sweeping fronts: 1 (Algorithm 2) or 2 (toward the middle slab, Sec. 2.4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -603,8 +607,9 @@ def main():
                     help="run the headline workload's steps only (warm-up, timed steps, the profiling pass) and "
                          "print its breakdown; for profiler launch lists, not a bench line")
     args = ap.parse_args()
-    global FRONTS
+    global FRONTS, RECURSIVE
     FRONTS = args.fronts
+    RECURSIVE = args.recursive
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 

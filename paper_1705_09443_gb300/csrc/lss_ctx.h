@@ -179,6 +179,7 @@ struct lss_ctx {
         int solve_bsm = -1;   // 0: slab-solve right-hand sides in global memory even when they fit shared
         int solve_nst = 0;    // slab-solve ring stages (the stages then share the free shared memory)
         int solve_nst_w = 0;  // the same for launches of 32-wide slabs only (0: as solve_nst)
+        int solve_half = 0;   // 1: slab solves keep to half the shared memory (two CTAs per SM)
         int rec_nb = 0;       // ring stages of the TMA recurrence
     } tune;
 

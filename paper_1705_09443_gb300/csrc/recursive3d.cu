@@ -39,6 +39,9 @@
 namespace {
 
 constexpr int kRecThreads = 512;
+constexpr int kRecStages = 4;                     // ring of factor-row chunks in shared memory
+constexpr unsigned kRecStageMax = 48 * 1024;      // bytes per stage (less when the step vectors need the room)
+constexpr size_t kRecSmem = 220 * 1024;
 enum { R3_FWD = 1, R3_CL = 2, R3_CR = 4 };   // as the flags of the slab sweep's steps
 
 // Inner auxiliary stencils: per (sample k, auxiliary x2 layer t2, x1 kind,
@@ -161,7 +164,71 @@ struct RecArgs {
     long long vsz, sstride;
     const int2* steps;     // outer steps: (slab, flags)
     int nsteps;
+    int* err;
+    unsigned sb;           // bytes per ring stage (a multiple of 16, at least one row + 32)
 };
+
+// Rows of a pivot-block inverse (M columns) per chunk of the factor stream.
+__host__ __device__ __forceinline__ int rec_rows(int M, int esz, unsigned sb) {
+    const int r = (int)((sb - 32) / ((unsigned)M * esz));
+    return r < 1 ? 1 : r;
+}
+
+// The factor stream in the order the walk consumes it: for every outer step,
+// inner solve, direction and block row k, the rows of D_k^{-1} in chunks.
+// Thread 0 keeps one cursor kRecStages chunks ahead of the consumers.
+struct RecCursor {
+    int st, pass, jj, dir, kk, r0;
+    bool done;
+};
+
+template <typename C>
+__device__ __forceinline__ void cursor_chunk(const RecArgs& A, const RecCursor& cu, const C** src, int* rows, int* M) {
+    const int ns = A.n_slabs, K = A.n_tot;
+    const int i = A.steps[cu.st].x;
+    const int j = cu.pass == 0 ? cu.jj : ns - 2 - cu.jj;
+    const Slab3 P = A.probs[(long long)i * ns + j];
+    const int k = cu.dir == 0 ? cu.kk : K - 2 - cu.kk;
+    *M = P.M;
+    *rows = min(P.M - cu.r0, rec_rows(P.M, (int)sizeof(C), A.sb));
+    *src = (const C*)A.ifac + P.fac_off + (long long)k * P.M * P.M + (long long)cu.r0 * P.M;
+}
+
+template <typename C>
+__device__ __forceinline__ void cursor_advance(const RecArgs& A, RecCursor& cu) {
+    const int ns = A.n_slabs, K = A.n_tot;
+    const int i = A.steps[cu.st].x;
+    const int j = cu.pass == 0 ? cu.jj : ns - 2 - cu.jj;
+    const int M = A.probs[(long long)i * ns + j].M;
+    cu.r0 += rec_rows(M, (int)sizeof(C), A.sb);
+    if (cu.r0 < M) return;
+    cu.r0 = 0;
+    if (++cu.kk < (cu.dir == 0 ? K : K - 1)) return;
+    cu.kk = 0;
+    if (++cu.dir < 2) return;
+    cu.dir = 0;
+    if (++cu.jj < (cu.pass == 0 ? ns : ns - 1)) return;
+    cu.jj = 0;
+    if (++cu.pass == 1 && ns - 1 > 0) return;
+    cu.pass = 0;
+    if (++cu.st >= A.nsteps) cu.done = true;
+}
+
+// Issue the cursor's chunk into ring stage stg (16-byte aligned window).
+template <typename C>
+__device__ __forceinline__ void cursor_issue(const RecArgs& A, RecCursor& cu, unsigned char* ring, uint64_t* full,
+                                             int stg) {
+    const C* src;
+    int rows, M;
+    cursor_chunk<C>(A, cu, &src, &rows, &M);
+    const unsigned long long a = (unsigned long long)src;
+    const unsigned long long e = a + (unsigned long long)rows * M * sizeof(C);
+    const unsigned long long lo = a & ~15ull;
+    const unsigned bytes = (unsigned)(((e + 15ull) & ~15ull) - lo);
+    mbar_expect_tx(&full[stg], bytes);
+    tma_load_1d(ring + (size_t)stg * A.sb, (const void*)lo, bytes, &full[stg]);
+    cursor_advance<C>(A, cu);
+}
 
 // x1-coupling of the slab's row (a1, X3 = x3) in block X2 = x2 with the
 // neighbouring slab's layer at grid x1-index X1o (slot d1s = 0 for x1-1, 2 for
@@ -189,11 +256,23 @@ __device__ __forceinline__ C outer_coupling(const RecArgs& A, const Slab3& O, co
 // solve an inner sweep over the sub-slab problems, each of those a forward and
 // backward block substitution along x3.
 template <typename C>
-__global__ void __launch_bounds__(kRecThreads) rec3_kernel(RecArgs A) {
-    extern __shared__ __align__(16) unsigned char smr[];
-    C* tb = reinterpret_cast<C*>(smr);                 // step input t [Mmax]
+__global__ void __launch_bounds__(kRecThreads, 1) rec3_kernel(RecArgs A) {
+    extern __shared__ __align__(128) unsigned char smr[];
+    unsigned char* ring = smr;                                                  // kRecStages x A.sb
+    uint64_t* full = reinterpret_cast<uint64_t*>(smr + (size_t)kRecStages * A.sb);
+    C* tb = reinterpret_cast<C*>(full + kRecStages);   // step input t [Mmax]
     C* yb = tb + A.Mmax;                               // [2][Mmax]: the previous step's result, this step's
+    C* ab = yb + 2 * A.Mmax;                           // D_k^{-1} t [Mmax]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    RecCursor cu{0, 0, 0, 0, 0, 0, A.nsteps == 0};
+    if (tid == 0) {
+        for (int q = 0; q < kRecStages; ++q) mbar_init(&full[q], 1);
+        fence_mbar_init();
+        for (int q = 0; q < kRecStages && !cu.done; ++q) cursor_issue<C>(A, cu, ring, full, q);
+    }
+    __syncthreads();
+    unsigned g = 0;        // chunks consumed
+    bool stop = false;     // a wait expired: the walk ends (LSS_DERR_TIMEOUT is set)
     const int nt = A.n_tot, K = A.n_tot, ns = A.n_slabs, b = A.b;
     const int r = blockIdx.x;
     const C* f = (const C*)A.f + r * A.G;
@@ -204,7 +283,7 @@ __global__ void __launch_bounds__(kRecThreads) rec3_kernel(RecArgs A) {
     const C* ocoef = (const C*)A.ocoef;
     const C* icoef = (const C*)A.icoef;
     const C* ifac = (const C*)A.ifac;
-    for (int st = 0; st < A.nsteps; ++st) {
+    for (int st = 0; st < A.nsteps && !stop; ++st) {
         const int i = A.steps[st].x, fl = A.steps[st].y;
         const Slab3 O = A.oslabs[i];
         const int w1 = O.w;
@@ -224,17 +303,17 @@ __global__ void __launch_bounds__(kRecThreads) rec3_kernel(RecArgs A) {
         }
         __syncthreads();
         // ---- inner sweep along x2: forward over the sub-slabs, then backward
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < 2 && !stop; ++pass) {
             const int nsol = pass == 0 ? ns : ns - 1;
-            for (int jj = 0; jj < nsol; ++jj) {
+            for (int jj = 0; jj < nsol && !stop; ++jj) {
                 const int j = pass == 0 ? jj : ns - 2 - jj;
                 const int ifl = pass == 0 ? (R3_FWD | (j > 0 ? R3_CL : 0)) : R3_CR;
                 const Slab3 P = A.probs[(long long)i * ns + j];
                 const int M = P.M, w2 = P.w;
                 const C* cf = icoef + P.cf_off;
                 int cur = 0;
-                for (int dir = 0; dir < 2; ++dir) {
-                    for (int kk = 0; kk < (dir == 0 ? K : K - 1); ++kk) {
+                for (int dir = 0; dir < 2 && !stop; ++dir) {
+                    for (int kk = 0; kk < (dir == 0 ? K : K - 1) && !stop; ++kk) {
                         const int k = dir == 0 ? kk : K - 2 - kk;
                         const C* yp = yb + cur * A.Mmax;   // y_{k-1} (forward) or x_{k+1} (backward)
                         C* yn = yb + (cur ^ 1) * A.Mmax;
@@ -290,10 +369,17 @@ __global__ void __launch_bounds__(kRecThreads) rec3_kernel(RecArgs A) {
                             tb[q] = v;
                         }
                         __syncthreads();
-                        // D_k^{-1} t, a warp per row
+                        // D_k^{-1} t, a warp per row, the rows streamed through the ring
                         const C* D = ifac + P.fac_off + (long long)k * M * M;
-                        for (int row = wid; row < M; row += nw) {
-                            const C* Dr = D + (long long)row * M;
+                        const int rpc = rec_rows(M, (int)sizeof(C), A.sb);
+                        for (int r0 = 0; r0 < M && !stop; r0 += rpc) {
+                        const int r1 = min(M, r0 + rpc), stg = (int)(g % kRecStages);
+                        const bool ok = mbar_wait(&full[stg], (g / kRecStages) & 1u, A.err);
+                        if (__syncthreads_or(!ok)) { stop = true; break; }
+                        const unsigned off = (unsigned)((unsigned long long)(D + (long long)r0 * M) & 15ull);
+                        const C* Sg = reinterpret_cast<const C*>(ring + (size_t)stg * A.sb + off);
+                        for (int row = r0 + wid; row < r1; row += nw) {
+                            const C* Dr = Sg + (long long)(row - r0) * M;
                             C a0 = czero<C>(), a1v = czero<C>();
                             int p = lane;
                             for (; p + 32 < M; p += 64) {
@@ -306,17 +392,27 @@ __global__ void __launch_bounds__(kRecThreads) rec3_kernel(RecArgs A) {
                                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
                             }
-                            if (lane == 0) {
-                                C* yk = Y + (long long)k * A.Mmax + row;
-                                const C val = dir == 0 ? acc : *yk - acc;
-                                *yk = val;
-                                yn[row] = val;
-                                const bool final_x = dir == 1 || k == K - 1;
-                                const int a2 = row / w1, a1 = row % w1;
-                                if (final_x && a2 >= P.na && a2 <= P.ll) {
-                                    C* uu = U + ((long long)(P.s + b + (a2 - P.na)) * nt + k) * w1 + a1;
-                                    *uu = (ifl & R3_FWD) ? val : *uu - val;
-                                }
+                            if (lane == 0) ab[row] = acc;
+                        }
+                        __syncthreads();   // the stage is consumed
+                        if (tid == 0 && !cu.done) {
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            cursor_issue<C>(A, cu, ring, full, stg);
+                        }
+                        ++g;
+                        }
+                        if (stop) break;
+                        // outputs, a thread per row (their global reads overlap)
+                        const bool final_x = dir == 1 || k == K - 1;
+                        for (int row = tid; row < M; row += blockDim.x) {
+                            C* yk = Y + (long long)k * A.Mmax + row;
+                            const C val = dir == 0 ? ab[row] : *yk - ab[row];
+                            *yk = val;
+                            yn[row] = val;
+                            const int a2 = row / w1, a1 = row % w1;
+                            if (final_x && a2 >= P.na && a2 <= P.ll) {
+                                C* uu = U + ((long long)(P.s + b + (a2 - P.na)) * nt + k) * w1 + a1;
+                                *uu = (ifl & R3_FWD) ? val : *uu - val;
                             }
                         }
                         __syncthreads();
@@ -335,6 +431,11 @@ __global__ void __launch_bounds__(kRecThreads) rec3_kernel(RecArgs A) {
             *up = (fl & R3_FWD) ? uval : *up - uval;
         }
         __syncthreads();
+    }
+    if (stop && tid == 0) {
+        // a wait expired: give the copies already issued a bounded chance to land
+        const long long t0 = clock64();
+        while (clock64() - t0 < 2000000ll) __nanosleep(1000);
     }
 }
 
@@ -403,7 +504,9 @@ int lss3r_setup(lss_ctx* c, cudaStream_t s) {
         if (c->prec == LSS_FP64) q->coef = q->coef64;
         else rc = lss3_dalloc(c, &q->coef, (size_t)cf * cs, "sub-slab coefficients fp32");
     }
-    rc = rc ? rc : lss3_dalloc(c, &q->fac, (size_t)fo * cs, "sub-slab factors");
+    // 64 bytes of slack: the factor stream copies 16-byte aligned windows that
+    // may end up to 15 bytes past the last factor entry
+    rc = rc ? rc : lss3_dalloc(c, &q->fac, (size_t)fo * cs + 64, "sub-slab factors");
     rc = rc ? rc : lss3_dalloc(c, &q->W, (size_t)wo * cs, "sub-slab pivot blocks");
     rc = rc ? rc : lss3_dalloc(c, &q->X, (size_t)wo * cs, "sub-slab Schur scratch");
     rc = rc ? rc : lss3_dalloc(c, &q->T, (size_t)np * NB * q->Mmax * cs, "sub-slab panel rows");
@@ -510,9 +613,19 @@ int rec_sweep_t(lss_ctx* c, const double2* r, double2* y, int R, int only, const
     a.sstride = sstride;
     a.steps = (const int2*)q->steps;
     a.nsteps = (int)tab.size();
+    a.err = c->d_err;
     {
         ProfScope ps(c, s, LSS_PROF_SLAB_A, 1);
-        rec3_kernel<C><<<R, kRecThreads, 3 * q->Mmax * cs, s>>>(a);
+        const size_t vec = 4 * (size_t)q->Mmax * cs + kRecStages * sizeof(uint64_t);
+        size_t sb = std::min<size_t>(kRecStageMax, vec < kRecSmem ? (kRecSmem - vec) / kRecStages : 0) & ~(size_t)15;
+        if (sb < (size_t)q->Mmax * cs + 32)
+            return lss_fail(c, LSS_ERR_UNSUPPORTED, "3D recursive: a sub-slab block row does not fit a stage");
+        a.sb = (unsigned)sb;
+        const size_t smem = (size_t)kRecStages * sb + vec;
+        rc = lss_check_cuda(c, cudaFuncSetAttribute(rec3_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem), "recursive sweep attribute");
+        if (rc) return rc;
+        rec3_kernel<C><<<R, kRecThreads, smem, s>>>(a);
         rc = lss_check_cuda(c, cudaGetLastError(), "3D recursive sweep launch");
         if (rc) return rc;
     }

@@ -906,52 +906,75 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
 // when the vectors or rows do not fit the cluster kernel below.
 // Tiles of the grid-synchronised recurrence: each step is a product of an
 // n_tot x n_tot map with the n_tot x R block of current vectors; a CTA forms a
-// kGtR x kGtC tile of it (one entry per thread) over K chunks of kGtK staged
-// in shared memory (coalesced loads of map rows and vector rows).
-constexpr int kGtR = 16, kGtC = 16, kGtK = 64;
-constexpr int kGtLd = kGtR * kGtK / 256;   // map entries a thread stages per chunk (= kGtK * kGtC / 256)
+// kGtR x kGtC tile of it over K chunks of kGtK staged in shared memory
+// (coalesced loads of map rows and vector rows, the next chunk loaded into
+// registers while the current one is multiplied).  Each thread owns four rows
+// of one column, so a vector entry read from shared memory serves four
+// products and the map entries are read as broadcasts.
+// Tiles of TR = 64 rows (4 per thread) when a step has enough of them to
+// cover the SMs, else TR = 32 (2 per thread).
+constexpr int kGtR = 64, kGtC = 16, kGtK = 32;
+constexpr int kGtLdB = kGtK * kGtC / 256;   // vector entries a thread stages per chunk
 
-template <typename T>
+template <typename T, int TR>
 __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
-                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T> (*Ms)[kGtK + 1],
-                                           cx<T> (*Xs)[kGtC + 1]) {
+                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T> (*As)[kGtR + 1],
+                                           cx<T> (*Bs)[kGtC + 1]) {
     using C = cx<T>;
+    constexpr int RPT = TR / 16;                  // rows per thread
+    constexpr int kGtLdA = TR * kGtK / 256;       // map entries a thread stages per chunk
     const int tid = threadIdx.x;
-    const int tr = tid / kGtC, tc = tid % kGtC;
-    const int row = rt * kGtR + tr, r = ct * kGtC + tc;
-    // the next chunk's entries are loaded into registers while the current
-    // one is multiplied
-    C pm[kGtLd], px[kGtLd];
+    const int ty = tid / kGtC, tx = tid % kGtC;   // rows RPT ty .. RPT ty + RPT - 1, column tx
+    C pa[kGtLdA], pb[kGtLdB];
     auto load = [&](int k0) {
 #pragma unroll
-        for (int u = 0; u < kGtLd; ++u) {
+        for (int u = 0; u < kGtLdA; ++u) {
             const int e = tid + 256 * u;
-            const int a = e / kGtK, b = e % kGtK;
-            const int gr = rt * kGtR + a, gk = k0 + b;
-            pm[u] = (gr < n_tot && gk < n_tot) ? M[(long long)gr * n_tot + gk] : czero<C>();
-            const int bb = e / kGtC, c = e % kGtC;
-            const int gk2 = k0 + bb, gc = ct * kGtC + c;
-            px[u] = (gk2 < n_tot && gc < R) ? x[(long long)gk2 * R + gc] : czero<C>();
+            const int a = e / kGtK, kk = e % kGtK;
+            const int gr = rt * TR + a, gk = k0 + kk;
+            pa[u] = (gr < n_tot && gk < n_tot) ? M[(long long)gr * n_tot + gk] : czero<C>();
+        }
+#pragma unroll
+        for (int u = 0; u < kGtLdB; ++u) {
+            const int e = tid + 256 * u;
+            const int kk = e / kGtC, c = e % kGtC;
+            const int gk = k0 + kk, gc = ct * kGtC + c;
+            pb[u] = (gk < n_tot && gc < R) ? x[(long long)gk * R + gc] : czero<C>();
         }
     };
-    C acc = czero<C>();
+    C acc[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[i] = czero<C>();
     load(0);
     for (int k0 = 0; k0 < n_tot; k0 += kGtK) {
 #pragma unroll
-        for (int u = 0; u < kGtLd; ++u) {
+        for (int u = 0; u < kGtLdA; ++u) {
             const int e = tid + 256 * u;
-            Ms[e / kGtK][e % kGtK] = pm[u];
-            Xs[e / kGtC][e % kGtC] = px[u];
+            As[e % kGtK][e / kGtK] = pa[u];
+        }
+#pragma unroll
+        for (int u = 0; u < kGtLdB; ++u) {
+            const int e = tid + 256 * u;
+            Bs[e / kGtC][e % kGtC] = pb[u];
         }
         __syncthreads();
         if (k0 + kGtK < n_tot) load(k0 + kGtK);
-#pragma unroll 16
-        for (int b = 0; b < kGtK; ++b) acc = cfma(Ms[tr][b], Xs[b][tc], acc);
+#pragma unroll 8
+        for (int kk = 0; kk < kGtK; ++kk) {
+            const C bv = Bs[kk][tx];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) acc[i] = cfma(As[kk][RPT * ty + i], bv, acc[i]);
+        }
         __syncthreads();
     }
-    if (row < n_tot && r < R) {
-        const long long e = (long long)row * R + r;
-        out[e] = base[e] - acc;
+    const int col = ct * kGtC + tx;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+        const int row = rt * TR + RPT * ty + i;
+        if (row < n_tot && col < R) {
+            const long long e = (long long)row * R + col;
+            out[e] = base[e] - acc[i];
+        }
     }
 }
 
@@ -959,18 +982,18 @@ __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx
 // fit the cluster kernels (many right-hand sides): lambda and mu, then phi,
 // one step per slab, a grid barrier between steps; the tiles of a step are
 // spread over the CTAs.
-template <typename T>
+template <typename T, int TR>
 __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot, int R,
                                                          const cx<T>* __restrict__ iface,
                                                          const cx<T>* __restrict__ a_first,
                                                          const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                          unsigned* bar, int* err) {
     using C = cx<T>;
-    __shared__ C Ms[kGtR][kGtK + 1];
+    __shared__ C Ms[kGtK][kGtR + 1];
     __shared__ C Xs[kGtK][kGtC + 1];
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
-    const int nrt = (n_tot + kGtR - 1) / kGtR, nct = (R + kGtC - 1) / kGtC;
+    const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
     const int ntile = nrt * nct;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vec;
          e += (long long)gridDim.x * blockDim.x)
@@ -981,17 +1004,17 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
         for (int task = blockIdx.x; task < nwhich * ntile; task += gridDim.x) {   // uniform per CTA
             const int which = task / ntile, t = task % ntile;
             if (which == 0)   // mu_i = first(a_i) - Gamma_i lambda_{i-1}
-                recur_tile<T>(iface + (1LL * n_slabs + i) * nt2, lp, a_first + (long long)i * vec,
+                recur_tile<T, TR>(iface + (1LL * n_slabs + i) * nt2, lp, a_first + (long long)i * vec,
                               phi + (long long)i * vec, n_tot, R, t / nct, t % nct, Ms, Xs);
             else              // lambda_i = last(a_i) - Lambda_i lambda_{i-1}
-                recur_tile<T>(iface + (long long)i * nt2, lp, a_last + (long long)i * vec,
+                recur_tile<T, TR>(iface + (long long)i * nt2, lp, a_last + (long long)i * vec,
                               lam + (long long)i * vec, n_tot, R, t / nct, t % nct, Ms, Xs);
         }
         grid_barrier(bar, gridDim.x, err);
     }
     for (int i = n_slabs - 2; i >= 1; --i) {   // phi_i = mu_i - Phi_i phi_{i+1}
         for (int task = blockIdx.x; task < ntile; task += gridDim.x)
-            recur_tile<T>(iface + (2LL * n_slabs + i) * nt2, phi + (long long)(i + 1) * vec,
+            recur_tile<T, TR>(iface + (2LL * n_slabs + i) * nt2, phi + (long long)(i + 1) * vec,
                           phi + (long long)i * vec, phi + (long long)i * vec, n_tot, R, task / nct, task % nct, Ms,
                           Xs);
         grid_barrier(bar, gridDim.x, err);
@@ -1012,18 +1035,18 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
 //   back:    phi_i = mu_i - Phi_i phi_{i+1} (i < c),  lambda_i = nu_i - Lambda_i lambda_{i-1} (i > c)
 // Both fronts advance in the same grid step, so the dependent steps are about
 // half of the one-front recurrences'.
-template <typename T>
+template <typename T, int TR>
 __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, int n_tot, int R,
                                                           const cx<T>* __restrict__ iface,
                                                           const cx<T>* __restrict__ a_first,
                                                           const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                           unsigned* bar, int* err) {
     using C = cx<T>;
-    __shared__ C Ms[kGtR][kGtK + 1];
+    __shared__ C Ms[kGtK][kGtR + 1];
     __shared__ C Xs[kGtK][kGtC + 1];
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
-    const int nrt = (n_tot + kGtR - 1) / kGtR, nct = (R + kGtC - 1) / kGtC;
+    const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
     const int ntile = nrt * nct;
     const int ns = n_slabs, c = mid;
     const C* LAM = iface;
@@ -1050,16 +1073,16 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
             const int t = task % ntile;
             if (!onL) which += 2;
             if (which == 0)
-                recur_tile<T>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct,
+                recur_tile<T, TR>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct,
                               Ms, Xs);
             else if (which == 1)
-                recur_tile<T>(GAM + iL * nt2, V(lam, iL - 1), Vc(a_first, iL), V(phi, iL), n_tot, R, t / nct,
+                recur_tile<T, TR>(GAM + iL * nt2, V(lam, iL - 1), Vc(a_first, iL), V(phi, iL), n_tot, R, t / nct,
                               t % nct, Ms, Xs);
             else if (which == 2)
-                recur_tile<T>(PHI + iR * nt2, V(phi, iR + 1), Vc(a_first, iR), V(phi, iR), n_tot, R, t / nct,
+                recur_tile<T, TR>(PHI + iR * nt2, V(phi, iR + 1), Vc(a_first, iR), V(phi, iR), n_tot, R, t / nct,
                               t % nct, Ms, Xs);
             else
-                recur_tile<T>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct,
+                recur_tile<T, TR>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct,
                               Ms, Xs);
         }
         grid_barrier(bar, gridDim.x, err);
@@ -1069,10 +1092,10 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
         for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
             const int t = task % ntile;
             if (task < ntile)
-                recur_tile<T>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms,
+                recur_tile<T, TR>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms,
                               Xs);
             else
-                recur_tile<T>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms,
+                recur_tile<T, TR>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms,
                               Xs);
         }
         grid_barrier(bar, gridDim.x, err);
@@ -1080,9 +1103,9 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
     for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
         const int t = task % ntile;
         if (task < ntile)
-            recur_tile<T>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms, Xs);
+            recur_tile<T, TR>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms, Xs);
         else
-            recur_tile<T>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms, Xs);
+            recur_tile<T, TR>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms, Xs);
     }
     grid_barrier(bar, gridDim.x, err);
     for (int st = 0; st < S; ++st) {   // both fronts back toward the boundaries
@@ -1093,10 +1116,10 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
             const int t = task % ntile;
             const bool left = onL && task < ntile;
             if (left)
-                recur_tile<T>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, Ms,
+                recur_tile<T, TR>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, Ms,
                               Xs);
             else
-                recur_tile<T>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, Ms,
+                recur_tile<T, TR>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, Ms,
                               Xs);
         }
         grid_barrier(bar, gridDim.x, err);
@@ -1445,10 +1468,12 @@ bool plan_solve(const lss_ctx* c, size_t bb, size_t tb, bool allow_smem_b, Solve
     const size_t want = std::max<size_t>(48 * 1024, min_stage);
     if (c->tune.solve_bsm == 0) allow_smem_b = false;
     const int tn = (ldw == 32 && c->tune.solve_nst_w) ? c->tune.solve_nst_w : c->tune.solve_nst;
+    // half the budget leaves room for a second CTA on the SM (latency hiding)
+    const size_t budget = c->tune.solve_half ? kSmemBudget / 2 : kSmemBudget;
     for (int bsm = allow_smem_b ? 1 : 0; bsm >= 0; --bsm) {
         const size_t fixed = tb + (bsm ? bb : 0);
-        if (fixed + 2 * min_stage > kSmemBudget) continue;
-        const size_t avail = kSmemBudget - fixed;
+        if (fixed + 2 * min_stage > budget) continue;
+        const size_t avail = budget - fixed;
         int nst = (int)std::min<size_t>(4, avail / want);
         size_t stage = want;
         if (tn >= 2 && avail / tn >= min_stage) {   // tuned: tn stages sharing the free shared memory
@@ -1900,15 +1925,22 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     {
         std::lock_guard<std::mutex> lock(lss_config_mutex());
         if (!grid) {
-            int per = 0, per2 = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, recur_grid_kernel<T>, 256, 0);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, recur_grid2_kernel<T>, 256, 0);
-            grid = std::max(1, std::min(per, per2)) * c->num_sms;
+            int per = 1 << 30;
+            for (const void* k : {(const void*)recur_grid_kernel<T, 64>, (const void*)recur_grid_kernel<T, 32>,
+                                  (const void*)recur_grid2_kernel<T, 64>, (const void*)recur_grid2_kernel<T, 32>}) {
+                int p = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k, 256, 0);
+                per = std::min(per, p);
+            }
+            grid = std::max(1, per) * c->num_sms;
         }
         grid_now = grid;
     }
-    // tiles of the widest step: lambda and mu (one front), or both fronts' two products
-    const long long tiles = (two ? 4LL : 2LL) * ((c->n_tot + kGtR - 1) / kGtR) * ((R + kGtC - 1) / kGtC);
+    // tiles of the widest step (lambda and mu with one front, both fronts' two
+    // products with two): 64-row tiles when they cover the SMs, else 32-row
+    const long long prods = two ? 4 : 2, nct = (R + kGtC - 1) / kGtC;
+    const int TR = prods * ((c->n_tot + 63) / 64) * nct >= c->num_sms ? 64 : 32;
+    const long long tiles = prods * ((c->n_tot + TR - 1) / TR) * nct;
     int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, tiles));
     int nsl = c->n_slabs, nt = c->n_tot, mid = c->mid;
     unsigned* bar = c->d_bar;
@@ -1917,10 +1949,12 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     cudaError_t e;
     if (two) {
         void* args[] = {&nsl, &mid, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
-        e = cudaLaunchCooperativeKernel((void*)recur_grid2_kernel<T>, dim3(nb), dim3(256), args, 0, s);
+        const void* k = TR == 64 ? (const void*)recur_grid2_kernel<T, 64> : (const void*)recur_grid2_kernel<T, 32>;
+        e = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, 0, s);
     } else {
         void* args[] = {&nsl, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
-        e = cudaLaunchCooperativeKernel((void*)recur_grid_kernel<T>, dim3(nb), dim3(256), args, 0, s);
+        const void* k = TR == 64 ? (const void*)recur_grid_kernel<T, 64> : (const void*)recur_grid_kernel<T, 32>;
+        e = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, 0, s);
     }
     return lss_check_cuda(c, e, "recurrence launch");
 }
