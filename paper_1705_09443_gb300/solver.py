@@ -82,6 +82,7 @@ class LSSolver:
         if m.dtype != torch.float64 or not m.is_cuda or tuple(m.shape) != self.shape:
             raise TypeError("m must be a float64 CUDA tensor of the grid's shape")
         self._check(self.lib.lss_set_medium(self.ctx, m.contiguous().data_ptr(), _stream_ptr(stream)))
+        self.medium_version = getattr(self, "medium_version", 0) + 1
 
     def profile(self, enable: bool = True):
         self._check(self.lib.lss_profile(self.ctx, int(enable)))
