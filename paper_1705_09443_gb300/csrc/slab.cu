@@ -912,17 +912,22 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
 // of one column, so a vector entry read from shared memory serves four
 // products and the map entries are read as broadcasts.
 // Tiles of TR = 64 rows (4 per thread) when a step has enough of them to
-// cover the SMs, else TR = 32 (2 per thread).
-constexpr int kGtR = 64, kGtC = 16, kGtK = 32;
-constexpr int kGtLdB = kGtK * kGtC / 256;   // vector entries a thread stages per chunk
+// cover the SMs, else TR = 32 (2 per thread).  The K chunk is as long as the
+// static shared memory allows (fewer dependent load rounds per tile).
+constexpr int kGtC = 16;
+template <typename T, int TR>
+struct GtK { static constexpr int value = sizeof(T) == 4 ? (TR == 32 ? 96 : 48) : (TR == 32 ? 48 : 32); };
 
 template <typename T, int TR>
 __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
-                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T> (*As)[kGtR + 1],
+                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T> (*As)[TR + 1],
                                            cx<T> (*Bs)[kGtC + 1]) {
     using C = cx<T>;
+    constexpr int kGtK = GtK<T, TR>::value;
     constexpr int RPT = TR / 16;                  // rows per thread
     constexpr int kGtLdA = TR * kGtK / 256;       // map entries a thread stages per chunk
+    constexpr int kGtLdB = kGtK * kGtC / 256;     // vector entries a thread stages per chunk
+    static_assert(TR * kGtK % 256 == 0 && kGtK * kGtC % 256 == 0, "a chunk must split evenly over the threads");
     const int tid = threadIdx.x;
     const int ty = tid / kGtC, tx = tid % kGtC;   // rows RPT ty .. RPT ty + RPT - 1, column tx
     C pa[kGtLdA], pb[kGtLdB];
@@ -989,8 +994,8 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
                                                          const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                          unsigned* bar, int* err) {
     using C = cx<T>;
-    __shared__ C Ms[kGtK][kGtR + 1];
-    __shared__ C Xs[kGtK][kGtC + 1];
+    __shared__ C Ms[GtK<T, TR>::value][TR + 1];
+    __shared__ C Xs[GtK<T, TR>::value][kGtC + 1];
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
     const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
@@ -1042,8 +1047,8 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
                                                           const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                           unsigned* bar, int* err) {
     using C = cx<T>;
-    __shared__ C Ms[kGtK][kGtR + 1];
-    __shared__ C Xs[kGtK][kGtC + 1];
+    __shared__ C Ms[GtK<T, TR>::value][TR + 1];
+    __shared__ C Xs[GtK<T, TR>::value][kGtC + 1];
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
     const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;

@@ -96,18 +96,19 @@ def test_preconditioner_ragged_and_few_slabs(n, b, bs):
         assert rel(y[r], pb.precondition(x[r])) <= 1e-10
 
 
-def test_grid_recurrences_with_many_right_hand_sides():
-    """R = 160 at n_tot = 66: the vectors (2 n_tot R complex FP64) exceed a
-    cluster's budget, so the cooperative two-front grid recurrences run.  Every
-    column equals the one-column application (cluster recurrences) and sampled
-    columns equal the oracle."""
+@pytest.mark.parametrize("fronts,R", [(2, 160), (2, 320), (1, 160), (1, 640)])
+def test_grid_recurrences_with_many_right_hand_sides(fronts, R):
+    """R >= 160 at n_tot = 66: the vectors (2 n_tot R complex FP64) exceed a
+    cluster's budget, so the cooperative grid recurrences run (32-row tiles,
+    and 64-row tiles once a step has enough of them: two fronts at R = 320,
+    one front at R = 640).  Sampled columns equal the one-column application
+    (cluster recurrences) and the oracle."""
     n = 40
-    s, m, om = make(n, 5.0, 19)
-    pb = O.Problem2D(n, om, m, O.Params(b_pml=12, b_slab=4, fronts=2))
-    R = 160
+    s, m, om = make(n, 5.0, 19, fronts=fronts)
+    pb = O.Problem2D(n, om, m, O.Params(b_pml=12, b_slab=4, fronts=fronts))
     x = crand((R, n, n), 20)
     y = s.apply_P(to_dev(x)).cpu().numpy()
-    for r in range(0, R, 23):
+    for r in range(0, R, R // 7 + 1):
         y1 = s.apply_P(to_dev(x[r:r + 1])).cpu().numpy()[0]
         assert rel(y[r], y1) <= 1e-12
         assert rel(y[r], pb.precondition(x[r])) <= 1e-10
