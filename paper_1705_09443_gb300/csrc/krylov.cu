@@ -27,24 +27,55 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// part[(i*R + r)*nblk + blk] = sum over this block's x of conj(V_i[r][x]) w[r][x]
-__global__ void __launch_bounds__(kRedThreads) dots_kernel(const double2* __restrict__ V, long long vstride,
-                                                           const double2* __restrict__ w, long long N, int R,
-                                                           double2* __restrict__ part) {
-    __shared__ double2 red[kRedThreads];
-    const int r = blockIdx.y, i = blockIdx.z, nblk = gridDim.x;
-    const double2* vi = V + (long long)i * vstride + (long long)r * N;
-    const double2* wr = w + (long long)r * N;
-    double2 acc = mk(0.0, 0.0);
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += (long long)nblk * blockDim.x)
-        acc = cfma_conj(vi[x], wr[x], acc);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
-        __syncthreads();
+// part[(i*R + r)*nblk + blk] = sum over this block's x of conj(V_i[r][x]) w[r][x],
+// for Q basis vectors i0 .. i0+Q-1 per CTA, reading w once for all of them;
+// the block's sum in a fixed order (warp shuffles, then the warps in turn).
+// Q is a compile-time count so that no predicated-off FP64 work is issued.
+template <int Q>
+__device__ __forceinline__ void dots_body(const double2* __restrict__ vb, long long vstride,
+                                          const double2* __restrict__ wr, long long N, int R, int i0, int r,
+                                          double2* __restrict__ part, double2 (*red)[kRedThreads / 32]) {
+    const int nblk = gridDim.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double2 acc[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) acc[q] = mk(0.0, 0.0);
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += (long long)nblk * blockDim.x) {
+        const double2 wv = wr[x];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] = cfma_conj(vb[(long long)q * vstride + x], wv, acc[q]);
     }
-    if (threadIdx.x == 0) part[((long long)i * R + r) * nblk + blockIdx.x] = red[0];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        for (int off = 16; off > 0; off >>= 1) {
+            acc[q].x += __shfl_xor_sync(0xffffffffu, acc[q].x, off);
+            acc[q].y += __shfl_xor_sync(0xffffffffu, acc[q].y, off);
+        }
+        if (lane == 0) red[q][wid] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < Q) {
+        double2 t = mk(0.0, 0.0);
+        for (int k = 0; k < kRedThreads / 32; ++k) t = t + red[threadIdx.x][k];
+        part[((long long)(i0 + threadIdx.x) * R + r) * nblk + blockIdx.x] = t;
+    }
+}
+
+constexpr int kDotsQ = 4;   // basis vectors per CTA of the Gram-Schmidt inner products
+
+__global__ void __launch_bounds__(kRedThreads) dots_multi_kernel(const double2* __restrict__ V, long long vstride,
+                                                                 const double2* __restrict__ w, long long N, int R,
+                                                                 int J, double2* __restrict__ part) {
+    __shared__ double2 red[kDotsQ][kRedThreads / 32];
+    const int r = blockIdx.y, i0 = blockIdx.z * kDotsQ;
+    const double2* wr = w + (long long)r * N;
+    const double2* vb = V + (long long)i0 * vstride + (long long)r * N;
+    switch (min(kDotsQ, J - i0)) {
+        case 1: dots_body<1>(vb, vstride, wr, N, R, i0, r, part, red); break;
+        case 2: dots_body<2>(vb, vstride, wr, N, R, i0, r, part, red); break;
+        case 3: dots_body<3>(vb, vstride, wr, N, R, i0, r, part, red); break;
+        default: dots_body<4>(vb, vstride, wr, N, R, i0, r, part, red); break;
+    }
 }
 
 // h[e] (+)= sum_blk part[e * nblk + blk], e = i*R + r: one CTA per e, strided
@@ -247,7 +278,8 @@ struct Krylov {
 // h[0..J) for every r = V_i^H w  (accumulate: h += ...)
 void dots(Krylov& K, const double2* V, long long vstride, int J, const double2* w, double2* h, int accumulate) {
     ProfScope ps(K.c, K.s, LSS_PROF_KRYLOV, 2);
-    dots_kernel<<<dim3(K.nblk, K.R, J), kRedThreads, 0, K.s>>>(V, vstride, w, K.N, K.R, K.part);
+    dots_multi_kernel<<<dim3(K.nblk, K.R, (J + kDotsQ - 1) / kDotsQ), kRedThreads, 0, K.s>>>(V, vstride, w, K.N,
+                                                                                            K.R, J, K.part);
     const int JR = J * K.R;
     reduce_kernel<<<JR, kRedThreads, 0, K.s>>>(K.part, K.nblk, h, accumulate);
 }
@@ -277,8 +309,8 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     double2* w = Z + (size_t)m * RN;
     double2* rv = w + RN;
     Krylov K{c, s, N, R, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-    // grids sized for the whole batch: about two CTAs per SM over all right-hand sides
-    K.nblk = std::max(1, std::min(2 * c->num_sms / R, (int)((N + kRedThreads - 1) / kRedThreads)));
+    // grids sized for the whole batch: about four CTAs per SM over all right-hand sides
+    K.nblk = std::max(1, std::min(4 * c->num_sms / R, (int)((N + kRedThreads - 1) / kRedThreads)));
     const size_t red_bytes = (size_t)(m + 1) * R * K.nblk * sizeof(double2) +
                              (size_t)(2 * (m + 1) + 1) * R * sizeof(double2) + (size_t)R * sizeof(double) + 64;
     rc = lss_grow(c, (void**)&c->red_buf, &c->red_cap, red_bytes);

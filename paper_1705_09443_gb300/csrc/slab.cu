@@ -1942,9 +1942,10 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
         grid_now = grid;
     }
     // tiles of the widest step (lambda and mu with one front, both fronts' two
-    // products with two): 64-row tiles when they cover the SMs, else 32-row
+    // products with two): 64-row tiles when they cover at least half the SMs
+    // (two 32-row tiles on one SM take longer than one 64-row tile), else 32-row
     const long long prods = two ? 4 : 2, nct = (R + kGtC - 1) / kGtC;
-    const int TR = prods * ((c->n_tot + 63) / 64) * nct >= c->num_sms ? 64 : 32;
+    const int TR = 2 * prods * ((c->n_tot + 63) / 64) * nct >= c->num_sms ? 64 : 32;
     const long long tiles = prods * ((c->n_tot + TR - 1) / TR) * nct;
     int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, tiles));
     int nsl = c->n_slabs, nt = c->n_tot, mid = c->mid;

@@ -257,6 +257,44 @@ __global__ void sparsify_kernel(const double2* __restrict__ r, C* __restrict__ f
     }
 }
 
+// The same f = Q r by 32 x 32 tiles of the output: r (x1 slowest) is read
+// into shared memory along x2 and f (x2 slowest) written along x1, so both
+// sides are coalesced (the plain kernel reads r across rows).  The stencil
+// arithmetic runs in the working precision C of f: FP32 for the
+// single-precision sweep, whose input f is rounded to FP32 anyway (nine FP64
+// complex FMAs per point would make the kernel FP64-bound on this GPU).
+// grid (tiles along x1, tiles along x2, R), 256 threads.
+template <typename C>
+__global__ void __launch_bounds__(256) sparsify_tiled_kernel(const double2* __restrict__ r, C* __restrict__ f,
+                                                             StencilArgs st, int n, int b, int n_tot) {
+    __shared__ C P[34][35];
+    const int rr = blockIdx.z;
+    const double2* rv = r + (long long)rr * n * n;
+    const int a1_0 = blockIdx.x * 32, a2_0 = blockIdx.y * 32;     // grid indices of the tile's corner
+    const int i1_0 = a1_0 - b, i2_0 = a2_0 - b;
+    for (int e = threadIdx.x; e < 34 * 34; e += blockDim.x) {
+        const int p1 = e / 34, p2 = e % 34;
+        const int j1 = i1_0 - 1 + p1, j2 = i2_0 - 1 + p2;
+        P[p1][p2] = (j1 >= 1 && j1 <= n && j2 >= 1 && j2 <= n) ? to_c<C>(rv[(long long)(j1 - 1) * n + (j2 - 1)])
+                                                               : czero<C>();
+    }
+    C a[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) a[o] = to_c<C>(st.a_conj[o]);
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int a1 = a1_0 + tx, i1 = a1 - b;
+    for (int q = ty; q < 32; q += 8) {
+        const int a2 = a2_0 + q, i2 = a2 - b;
+        if (a1 >= n_tot || a2 >= n_tot) continue;
+        C acc = czero<C>();
+        if (i1 >= 0 && i1 <= n + 1 && i2 >= 0 && i2 <= n + 1)
+#pragma unroll
+            for (int o = 0; o < 9; ++o) acc = cfma(a[o], P[tx + o / 3][q + o % 3], acc);
+        f[(long long)rr * n_tot * n_tot + (long long)a2 * n_tot + a1] = acc;
+    }
+}
+
 // Q^T (Eq. Huf transposed): r_j = sum_o conj(alpha_o) X_{j-o} for j in I, X on the
 // grid rows of I^h (x2 slowest, like the sparsified right-hand side).
 template <typename C>
@@ -381,14 +419,12 @@ int lss_assemble_slabs(lss_ctx* c, cudaStream_t s) {
 
 int lss_sparsify(lss_ctx* c, const double2* r, void* f, int R, cudaStream_t s) {
     ProfScope ps(c, s, LSS_PROF_SPARSIFY, 1);
-    const long long tot = (long long)c->n_tot * c->n_tot;
-    const int blocks = (int)std::min<long long>((tot + 255) / 256, 4LL * c->num_sms);
+    const int tiles = (c->n_tot + 31) / 32;
+    const dim3 grid(tiles, tiles, R);
     if (c->prec == LSS_FP64)
-        sparsify_kernel<double2><<<dim3(blocks, R), 256, 0, s>>>(r, (double2*)f, stencil_args(c), c->n, c->b,
-                                                                  c->n_tot);
+        sparsify_tiled_kernel<double2><<<grid, 256, 0, s>>>(r, (double2*)f, stencil_args(c), c->n, c->b, c->n_tot);
     else
-        sparsify_kernel<float2><<<dim3(blocks, R), 256, 0, s>>>(r, (float2*)f, stencil_args(c), c->n, c->b,
-                                                                 c->n_tot);
+        sparsify_tiled_kernel<float2><<<grid, 256, 0, s>>>(r, (float2*)f, stencil_args(c), c->n, c->b, c->n_tot);
     return lss_check_cuda(c, cudaGetLastError(), "sparsify");
 }
 
