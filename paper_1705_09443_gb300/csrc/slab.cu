@@ -911,67 +911,89 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
 // registers while the current one is multiplied).  Each thread owns four rows
 // of one column, so a vector entry read from shared memory serves four
 // products and the map entries are read as broadcasts.
-// Tiles of TR = 64 rows (4 per thread) when a step has enough of them to
-// cover the SMs, else TR = 32 (2 per thread).  The K chunk is as long as the
-// static shared memory allows (fewer dependent load rounds per tile).
-constexpr int kGtC = 16;
-template <typename T, int TR>
-struct GtK { static constexpr int value = sizeof(T) == 4 ? (TR == 32 ? 96 : 48) : (TR == 32 ? 48 : 32); };
+// Tiles of TR = 64 rows (4 per thread) when a step has enough of them,
+// else TR = 32 (2 per thread).  The K chunks stream into a ring of kGtS
+// shared-memory stages by cp.async copies issued kGtS - 1 chunks ahead (many
+// bytes in flight per SM: the maps come from DRAM at every step).
+constexpr int kGtC = 16, kGtK = 32, kGtS = 4;
+
+template <typename C>
+__device__ __forceinline__ void cp_async_entry(C* dst, const C* src, bool valid) {
+    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "complex float or double");
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                     "r"(valid ? 8 : 0)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                     "r"(valid ? 16 : 0)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// entries of one ring stage: the map tile (TR rows, kGtK + 2 per row) and
+// the vector tile (kGtK rows, kGtC + 1 per row)
+template <int TR>
+constexpr int gt_stage_ent() { return TR * (kGtK + 2) + kGtK * (kGtC + 1); }
 
 template <typename T, int TR>
 __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
-                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T> (*As)[TR + 1],
-                                           cx<T> (*Bs)[kGtC + 1]) {
+                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T>* ring) {
     using C = cx<T>;
-    constexpr int kGtK = GtK<T, TR>::value;
     constexpr int RPT = TR / 16;                  // rows per thread
-    constexpr int kGtLdA = TR * kGtK / 256;       // map entries a thread stages per chunk
-    constexpr int kGtLdB = kGtK * kGtC / 256;     // vector entries a thread stages per chunk
+    constexpr int LA = TR * kGtK / 256;           // map entries a thread copies per chunk
+    constexpr int LB = kGtK * kGtC / 256;         // vector entries a thread copies per chunk
+    constexpr int SE = gt_stage_ent<TR>();
     static_assert(TR * kGtK % 256 == 0 && kGtK * kGtC % 256 == 0, "a chunk must split evenly over the threads");
     const int tid = threadIdx.x;
     const int ty = tid / kGtC, tx = tid % kGtC;   // rows RPT ty .. RPT ty + RPT - 1, column tx
-    C pa[kGtLdA], pb[kGtLdB];
-    auto load = [&](int k0) {
+    const int nch = (n_tot + kGtK - 1) / kGtK;
+    auto issue = [&](int ch) {
+        if (ch < nch) {
+            C* As = ring + (ch % kGtS) * SE;
+            C* Bs = As + TR * (kGtK + 2);
+            const int k0 = ch * kGtK;
 #pragma unroll
-        for (int u = 0; u < kGtLdA; ++u) {
-            const int e = tid + 256 * u;
-            const int a = e / kGtK, kk = e % kGtK;
-            const int gr = rt * TR + a, gk = k0 + kk;
-            pa[u] = (gr < n_tot && gk < n_tot) ? M[(long long)gr * n_tot + gk] : czero<C>();
-        }
+            for (int u = 0; u < LA; ++u) {
+                const int e = tid + 256 * u;
+                const int a = e / kGtK, kk = e % kGtK;
+                const int gr = rt * TR + a, gk = k0 + kk;
+                const bool ok = gr < n_tot && gk < n_tot;
+                cp_async_entry(As + a * (kGtK + 2) + kk, ok ? M + (long long)gr * n_tot + gk : M, ok);
+            }
 #pragma unroll
-        for (int u = 0; u < kGtLdB; ++u) {
-            const int e = tid + 256 * u;
-            const int kk = e / kGtC, c = e % kGtC;
-            const int gk = k0 + kk, gc = ct * kGtC + c;
-            pb[u] = (gk < n_tot && gc < R) ? x[(long long)gk * R + gc] : czero<C>();
+            for (int u = 0; u < LB; ++u) {
+                const int e = tid + 256 * u;
+                const int kk = e / kGtC, c = e % kGtC;
+                const int gk = k0 + kk, gc = ct * kGtC + c;
+                const bool ok = gk < n_tot && gc < R;
+                cp_async_entry(Bs + kk * (kGtC + 1) + c, ok ? x + (long long)gk * R + gc : x, ok);
+            }
         }
+        cp_async_commit();   // (an empty group past the last chunk keeps the count uniform)
     };
     C acc[RPT];
 #pragma unroll
     for (int i = 0; i < RPT; ++i) acc[i] = czero<C>();
-    load(0);
-    for (int k0 = 0; k0 < n_tot; k0 += kGtK) {
 #pragma unroll
-        for (int u = 0; u < kGtLdA; ++u) {
-            const int e = tid + 256 * u;
-            As[e % kGtK][e / kGtK] = pa[u];
-        }
-#pragma unroll
-        for (int u = 0; u < kGtLdB; ++u) {
-            const int e = tid + 256 * u;
-            Bs[e / kGtC][e % kGtC] = pb[u];
-        }
-        __syncthreads();
-        if (k0 + kGtK < n_tot) load(k0 + kGtK);
+    for (int q = 0; q < kGtS - 1; ++q) issue(q);
+    for (int ch = 0; ch < nch; ++ch) {
+        cp_async_wait<kGtS - 2>();   // chunk ch has landed (this thread's copies)
+        __syncthreads();             // ... and every thread's
+        const C* As = ring + (ch % kGtS) * SE;
+        const C* Bs = As + TR * (kGtK + 2);
 #pragma unroll 8
         for (int kk = 0; kk < kGtK; ++kk) {
-            const C bv = Bs[kk][tx];
+            const C bv = Bs[kk * (kGtC + 1) + tx];
 #pragma unroll
-            for (int i = 0; i < RPT; ++i) acc[i] = cfma(As[kk][RPT * ty + i], bv, acc[i]);
+            for (int i = 0; i < RPT; ++i) acc[i] = cfma(As[(RPT * ty + i) * (kGtK + 2) + kk], bv, acc[i]);
         }
-        __syncthreads();
+        __syncthreads();             // the stage of chunk ch may be refilled
+        issue(ch + kGtS - 1);
     }
+    cp_async_wait<0>();
     const int col = ct * kGtC + tx;
 #pragma unroll
     for (int i = 0; i < RPT; ++i) {
@@ -994,8 +1016,9 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
                                                          const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                          unsigned* bar, int* err) {
     using C = cx<T>;
-    __shared__ C Ms[GtK<T, TR>::value][TR + 1];
-    __shared__ C Xs[GtK<T, TR>::value][kGtC + 1];
+    extern __shared__ __align__(16) unsigned char gts[];
+    C* ring = reinterpret_cast<C*>(gts);   // kGtS stages of gt_stage_ent<TR>() entries
+    unsigned nbar = 0;                     // grid barriers passed (the arrival counter starts at zero)
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
     const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
@@ -1010,19 +1033,18 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
             const int which = task / ntile, t = task % ntile;
             if (which == 0)   // mu_i = first(a_i) - Gamma_i lambda_{i-1}
                 recur_tile<T, TR>(iface + (1LL * n_slabs + i) * nt2, lp, a_first + (long long)i * vec,
-                              phi + (long long)i * vec, n_tot, R, t / nct, t % nct, Ms, Xs);
+                              phi + (long long)i * vec, n_tot, R, t / nct, t % nct, ring);
             else              // lambda_i = last(a_i) - Lambda_i lambda_{i-1}
                 recur_tile<T, TR>(iface + (long long)i * nt2, lp, a_last + (long long)i * vec,
-                              lam + (long long)i * vec, n_tot, R, t / nct, t % nct, Ms, Xs);
+                              lam + (long long)i * vec, n_tot, R, t / nct, t % nct, ring);
         }
-        grid_barrier(bar, gridDim.x, err);
+        grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
     for (int i = n_slabs - 2; i >= 1; --i) {   // phi_i = mu_i - Phi_i phi_{i+1}
         for (int task = blockIdx.x; task < ntile; task += gridDim.x)
             recur_tile<T, TR>(iface + (2LL * n_slabs + i) * nt2, phi + (long long)(i + 1) * vec,
-                          phi + (long long)i * vec, phi + (long long)i * vec, n_tot, R, task / nct, task % nct, Ms,
-                          Xs);
-        grid_barrier(bar, gridDim.x, err);
+                          phi + (long long)i * vec, phi + (long long)i * vec, n_tot, R, task / nct, task % nct, ring);
+        grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
 }
 
@@ -1047,8 +1069,9 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
                                                           const cx<T>* __restrict__ a_last, cx<T>* lam, cx<T>* phi,
                                                           unsigned* bar, int* err) {
     using C = cx<T>;
-    __shared__ C Ms[GtK<T, TR>::value][TR + 1];
-    __shared__ C Xs[GtK<T, TR>::value][kGtC + 1];
+    extern __shared__ __align__(16) unsigned char gts[];
+    C* ring = reinterpret_cast<C*>(gts);   // kGtS stages of gt_stage_ent<TR>() entries
+    unsigned nbar = 0;                     // grid barriers passed (the arrival counter starts at zero)
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
     const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
@@ -1067,7 +1090,7 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
         V(phi, ns - 1)[e] = Vc(a_first, ns - 1)[e];
         if (c == 0) phi[e] = a_first[e];
     }
-    grid_barrier(bar, gridDim.x, err);
+    grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     const int S = max(c - 1, ns - 2 - c);
     for (int st = 0; st < S; ++st) {   // both fronts toward c
         const int iL = 1 + st, iR = ns - 2 - st;
@@ -1078,41 +1101,37 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
             const int t = task % ntile;
             if (!onL) which += 2;
             if (which == 0)
-                recur_tile<T, TR>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct,
-                              Ms, Xs);
+                recur_tile<T, TR>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct, ring);
             else if (which == 1)
                 recur_tile<T, TR>(GAM + iL * nt2, V(lam, iL - 1), Vc(a_first, iL), V(phi, iL), n_tot, R, t / nct,
-                              t % nct, Ms, Xs);
+                              t % nct, ring);
             else if (which == 2)
                 recur_tile<T, TR>(PHI + iR * nt2, V(phi, iR + 1), Vc(a_first, iR), V(phi, iR), n_tot, R, t / nct,
-                              t % nct, Ms, Xs);
+                              t % nct, ring);
             else
-                recur_tile<T, TR>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct,
-                              Ms, Xs);
+                recur_tile<T, TR>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct, ring);
         }
-        grid_barrier(bar, gridDim.x, err);
+        grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
     // the middle slab: the left coupling (when c > 0), then the right one
     if (c > 0) {
         for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
             const int t = task % ntile;
             if (task < ntile)
-                recur_tile<T, TR>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms,
-                              Xs);
+                recur_tile<T, TR>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, ring);
             else
-                recur_tile<T, TR>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms,
-                              Xs);
+                recur_tile<T, TR>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, ring);
         }
-        grid_barrier(bar, gridDim.x, err);
+        grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
     for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
         const int t = task % ntile;
         if (task < ntile)
-            recur_tile<T, TR>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, Ms, Xs);
+            recur_tile<T, TR>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, ring);
         else
-            recur_tile<T, TR>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, Ms, Xs);
+            recur_tile<T, TR>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, ring);
     }
-    grid_barrier(bar, gridDim.x, err);
+    grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     for (int st = 0; st < S; ++st) {   // both fronts back toward the boundaries
         const int iL = c - 1 - st, iR = c + 1 + st;
         const bool onL = iL >= 1, onR = iR <= ns - 2;
@@ -1121,13 +1140,11 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
             const int t = task % ntile;
             const bool left = onL && task < ntile;
             if (left)
-                recur_tile<T, TR>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, Ms,
-                              Xs);
+                recur_tile<T, TR>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, ring);
             else
-                recur_tile<T, TR>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, Ms,
-                              Xs);
+                recur_tile<T, TR>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, ring);
         }
-        grid_barrier(bar, gridDim.x, err);
+        grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
 }
 
@@ -1925,42 +1942,42 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     if (cap != cudaStreamCaptureStatusNone) return LSS_ERR_UNSUPPORTED;
-    static int grid = 0;
-    int grid_now;
-    {
-        std::lock_guard<std::mutex> lock(lss_config_mutex());
-        if (!grid) {
-            int per = 1 << 30;
-            for (const void* k : {(const void*)recur_grid_kernel<T, 64>, (const void*)recur_grid_kernel<T, 32>,
-                                  (const void*)recur_grid2_kernel<T, 64>, (const void*)recur_grid2_kernel<T, 32>}) {
-                int p = 0;
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k, 256, 0);
-                per = std::min(per, p);
-            }
-            grid = std::max(1, per) * c->num_sms;
-        }
-        grid_now = grid;
-    }
     // tiles of the widest step (lambda and mu with one front, both fronts' two
     // products with two): 64-row tiles when they cover at least half the SMs
     // (two 32-row tiles on one SM take longer than one 64-row tile), else 32-row
     const long long prods = two ? 4 : 2, nct = (R + kGtC - 1) / kGtC;
     const int TR = 2 * prods * ((c->n_tot + 63) / 64) * nct >= c->num_sms ? 64 : 32;
+    const size_t smem = (size_t)kGtS * (TR == 64 ? gt_stage_ent<64>() : gt_stage_ent<32>()) * sizeof(C);
+    const void* k = two ? (TR == 64 ? (const void*)recur_grid2_kernel<T, 64> : (const void*)recur_grid2_kernel<T, 32>)
+                        : (TR == 64 ? (const void*)recur_grid_kernel<T, 64> : (const void*)recur_grid_kernel<T, 32>);
+    static int grid[2][2] = {{0, 0}, {0, 0}};   // per (fronts, tile height), this process's device
+    int grid_now;
+    {
+        std::lock_guard<std::mutex> lock(lss_config_mutex());
+        int& g = grid[two][TR == 64];
+        if (!g) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e) return lss_check_cuda(c, e, "recurrence attribute");
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, smem);
+            g = std::max(1, per) * c->num_sms;
+        }
+        grid_now = g;
+    }
     const long long tiles = prods * ((c->n_tot + TR - 1) / TR) * nct;
     int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, tiles));
     int nsl = c->n_slabs, nt = c->n_tot, mid = c->mid;
     unsigned* bar = c->d_bar;
     int* err = c->d_err;
     ProfScope ps(c, s, LSS_PROF_RECUR, 1);
-    cudaError_t e;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);   // the barriers' arrival counter
+    if (e) return lss_check_cuda(c, e, "recurrence barrier");
     if (two) {
         void* args[] = {&nsl, &mid, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
-        const void* k = TR == 64 ? (const void*)recur_grid2_kernel<T, 64> : (const void*)recur_grid2_kernel<T, 32>;
-        e = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, 0, s);
+        e = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, smem, s);
     } else {
         void* args[] = {&nsl, &nt, &R, &ifc, (void*)&a_first, (void*)&a_last, &lam, &phi, &bar, &err};
-        const void* k = TR == 64 ? (const void*)recur_grid_kernel<T, 64> : (const void*)recur_grid_kernel<T, 32>;
-        e = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, 0, s);
+        e = cudaLaunchCooperativeKernel(k, dim3(nb), dim3(256), args, smem, s);
     }
     return lss_check_cuda(c, e, "recurrence launch");
 }
