@@ -324,11 +324,12 @@ int lss_set_graphs(lss_ctx *c, int enable);
  * changes.  Requires a factored context; allocates and frees two vectors;
  * blocks the host.  On a batch: every instance.  The paper has no
  * counterpart (launch configuration only).
- *   chosen  host, 6 ints (may be NULL): column group, right-hand sides in
+ *   chosen  host, 7 ints (may be NULL): column group, right-hand sides in
  *           global memory (0) or automatic (-1), ring stages (0 = automatic),
  *           recurrence stages, ring stages of the 32-wide slabs' launches
  *           (0 = as the others), slab solves within half the shared memory
- *           so that two CTAs share an SM (1) or not (0)
+ *           so that two CTAs share an SM (1) or not (0), right-hand sides
+ *           per slab-solve CTA on 16-wide slabs (1 or 2)
  */
 int lss_autotune(lss_ctx *c, int R, int *chosen, void *stream);
 

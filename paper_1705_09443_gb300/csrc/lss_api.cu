@@ -2,6 +2,7 @@
 // orchestration of the kernels in the other translation units.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -214,6 +215,10 @@ int lss_setup(lss_ctx** out, const lss_grid* g, double omega, const double* m_de
     c->b_aux = slab->b_aux ? slab->b_aux : pml->b_pml;
     c->n_samples = slab->n_samples ? slab->n_samples : g->n;
     c->fronts = slab->fronts == 2 ? 2 : 1;
+    {   // LSS_SOLVE_NR=2: two right-hand sides per slab-solve CTA from the start (else the autotuner decides)
+        const char* v = std::getenv("LSS_SOLVE_NR");
+        if (v && v[0] == '2') c->tune.solve_nr = 2;
+    }
     c->n_tot = c->n + 2 + 2 * c->b;
     int dev = 0;
     cudaGetDevice(&dev);

@@ -13,6 +13,7 @@
 #define LSS_DERR_SINGULAR 1
 #define LSS_DERR_TIMEOUT 2
 #define LSS_DERR_NONFINITE 4
+#define LSS_DERR_CONFIG 8      // a kernel was launched with a configuration it does not handle
 
 // ---------------------------------------------------------------- complex
 template <typename T> struct cplx_t;

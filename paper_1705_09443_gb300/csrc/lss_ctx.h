@@ -180,6 +180,7 @@ struct lss_ctx {
         int solve_nst = 0;    // slab-solve ring stages (the stages then share the free shared memory)
         int solve_nst_w = 0;  // the same for launches of 32-wide slabs only (0: as solve_nst)
         int solve_half = 0;   // 1: slab solves keep to half the shared memory (two CTAs per SM)
+        int solve_nr = 1;     // right-hand sides per slab-solve CTA on 16-wide slabs (1 or 2)
         int rec_nb = 0;       // ring stages of the TMA recurrence
     } tune;
 

@@ -623,9 +623,13 @@ std::vector<CrChunk> cr_chunk_table(int K, int G, bool part, int stage_ent, int 
     return out;
 }
 
-template <typename C, int MODE, int G>
+// One CTA solves slab i's subproblem for NR right-hand sides r, r+1, ..,
+// each factor chunk serving all of them (NR = 2 only with 16-wide blocks);
+// b holds the NR right-hand sides one after another.
+template <typename C, int MODE, int G, int NR>
 __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, int i, int r, C* b, C* tb, C* ring,
                                         uint64_t* full, int4* desc, const CrLv* lv, bool& ok) {
+    static_assert(NR == 1 || G == 16, "several right-hand sides per CTA with 16-wide blocks only");
     const int K = A.n_tot, w = sd.w, bs = sd.bs, na = sd.na;
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nth >> 5;
@@ -666,11 +670,13 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         for (int st = 0; st < A.nst; ++st) issue_next(st);
 
     // ---- right-hand side
-    for (int e = tid; e < K * lw; e += nth) {   // block row k = e / lw
+    for (int e = tid; e < NR * K * lw; e += nth) {   // right-hand side r + e / (K lw), block row k
         const int pp = e % lw;
-        const int k = e / lw;
+        const int k = (e / lw) % K;
+        const int rq = r + e / (K * lw);
         C v = czero<C>();
-        if (pp < w) {
+        if (pp < w && rq < A.R) {
+            const int r = rq;
             if (MODE == CR_A || MODE == CR_E) {
                 if (pp >= na && pp <= sd.ll) v = A.f[(long long)r * nt2 + (long long)k * K + sd.s + A.b + (pp - na)];
                 if (MODE == CR_E) {
@@ -759,10 +765,15 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
                 x[p] = (kind == PH_FODD || kind == PH_TOP) ? sum : x[p] - sum;
             }
         } else
-        for (int t0 = warp * GPW; t0 < cnt; t0 += nw * GPW) {
-            const int t = t0 + grp;
-            const bool on = t < cnt;
-            const int rr = r0 + (on ? t : 0);
+        for (int t0 = warp * GPW; t0 < cnt * NR; t0 += nw * GPW) {
+            // task = (right-hand side q, row t of the chunk)
+            const int tq = t0 + grp;
+            const bool on = tq < cnt * NR;
+            const int q = on ? tq / cnt : 0;
+            const int t = on ? tq - q * cnt : 0;
+            C* const bq = b + (long long)q * K * lw;
+            auto row = [&](int k) { return bq + (long long)k * lw; };
+            const int rr = r0 + t;
             C acc[CPT];
             if (kind == PH_FODD || kind == PH_TOP) {
                 // y_o = D_o^{-1} b_o (top: x_0 = D^{-1} b_0); the group reads its row first
@@ -838,33 +849,39 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         if (tid == 0) issue_next(g + A.nst);
     }
 
-    // ---- outputs
-    if (MODE == CR_A) {
-        const long long base = (long long)i * K * A.R + r;
-        for (int k = tid; k < K; k += nth) {
-            A.a_first[base + (long long)k * A.R] = row(k)[na];
-            A.a_last[base + (long long)k * A.R] = row(k)[sd.ll];
-        }
-    } else if (MODE == CR_E) {
-        const int nl = sd.nl;
-        for (int e = tid; e < nl * K; e += nth) {
-            const int k = e % K, pp = na + e / K;
-            const int x1 = sd.s + (pp - na), i2 = k - A.b;
-            if (A.y_grid)
-                A.y[(long long)r * A.n_tot * A.n_tot + (long long)k * A.n_tot + (x1 + A.b)] = to_d(row(k)[pp]);
-            else if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
-                A.y[(long long)r * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(row(k)[pp]);
-        }
-    } else {
-        const int nl = sd.nl;
-        for (int e = tid; e < nl * K; e += nth) {
-            const int k = e % K, pp = na + e / K;
-            A.w_out[((long long)r * nl + (pp - na)) * K + k] = to_d(row(k)[pp]);
+    // ---- outputs, per right-hand side
+    for (int q = 0; q < NR; ++q) {
+        const int rq = r + q;
+        if (rq >= A.R) break;
+        C* const bq = b + (long long)q * K * lw;
+        auto rowo = [&](int k) { return bq + (long long)k * lw; };
+        if (MODE == CR_A) {
+            const long long base = (long long)i * K * A.R + rq;
+            for (int k = tid; k < K; k += nth) {
+                A.a_first[base + (long long)k * A.R] = rowo(k)[na];
+                A.a_last[base + (long long)k * A.R] = rowo(k)[sd.ll];
+            }
+        } else if (MODE == CR_E) {
+            const int nl = sd.nl;
+            for (int e = tid; e < nl * K; e += nth) {
+                const int k = e % K, pp = na + e / K;
+                const int x1 = sd.s + (pp - na), i2 = k - A.b;
+                if (A.y_grid)
+                    A.y[(long long)rq * A.n_tot * A.n_tot + (long long)k * A.n_tot + (x1 + A.b)] = to_d(rowo(k)[pp]);
+                else if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
+                    A.y[(long long)rq * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(rowo(k)[pp]);
+            }
+        } else {
+            const int nl = sd.nl;
+            for (int e = tid; e < nl * K; e += nth) {
+                const int k = e % K, pp = na + e / K;
+                A.w_out[((long long)rq * nl + (pp - na)) * K + k] = to_d(rowo(k)[pp]);
+            }
         }
     }
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int NR = 1>
 __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A) {
     using C = cx<T>;
     __shared__ CrLv lv[33];
@@ -889,11 +906,12 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
     long long cta;
     if (MODE == CR_TEST) { i = A.slab; r = blockIdx.x; cta = blockIdx.x; }
     // slab-major grid: a slab's right-hand sides run together and share its factor stream in L2
-    else { i = A.slab0 + blockIdx.y; r = blockIdx.x; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
+    else { i = A.slab0 + blockIdx.y; r = blockIdx.x * NR; cta = (long long)blockIdx.y * gridDim.x + blockIdx.x; }
     const SlabDev sd = A.slabs[i];
     C* b = A.bsm ? reinterpret_cast<C*>(sms) : A.bg + cta * A.bstride;
-    if (sd.w <= 16) cr_body<C, MODE, 16>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
-    else cr_body<C, MODE, 32>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
+    if (sd.w <= 16) cr_body<C, MODE, 16, NR>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
+    else if constexpr (NR == 1) cr_body<C, MODE, 32, 1>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
+    else if (threadIdx.x == 0) atomicOr(A.err, LSS_DERR_CONFIG);   // the host launches NR > 1 for 16-wide slabs only
     if (!ok && threadIdx.x == 0) {
         // a wait expired: give the copies already issued a bounded chance to land
         const long long t0 = clock64();
@@ -1558,11 +1576,11 @@ int chunk_tables(lss_ctx* c, bool part, int stage_ent, CrArgsTables* out, cudaSt
 // ldw > 0: the launch covers slabs of that block width only (its right-hand
 // sides and stages are sized for it); z_off: byte offset of this launch's part
 // of the context's global right-hand-side scratch.
-template <typename T, int MODE>
+template <typename T, int MODE, int NR = 1>
 int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void* scratch, size_t scratch_bytes,
                  cudaStream_t s, int ldw = 0, size_t z_off = 0) {
     using C = cx<T>;
-    auto kern = cr_solve_kernel<T, MODE>;
+    auto kern = cr_solve_kernel<T, MODE, NR>;
     const size_t tb = sizeof(C) * ((size_t)kSolveThreads + kSplitRows * 4 * 32);
     const size_t bb = sizeof(C) * (size_t)per_cta;
     SolvePlan P;
@@ -1631,9 +1649,10 @@ int prepare_chunk_tables(lss_ctx* c, cudaStream_t s) {
     }
     for (const SweepRun& u : sweep_runs(c)) {
         SolvePlan P;
-        for (int smem_b = 0; smem_b < 2; ++smem_b)
-            if (plan_solve<C>(c, sizeof(C) * (size_t)c->n_tot * u.ldw, tb, smem_b == 1, &P, u.ldw))
-                plans.push_back(P);
+        for (int nr = 1; nr <= (u.ldw == 16 ? 2 : 1); ++nr)   // one or two right-hand sides per CTA
+            for (int smem_b = 0; smem_b < 2; ++smem_b)
+                if (plan_solve<C>(c, sizeof(C) * (size_t)nr * c->n_tot * u.ldw, tb, smem_b == 1, &P, u.ldw))
+                    plans.push_back(P);
     }
     for (const SolvePlan& P : plans)
         for (int part = 0; part < 2; ++part) {
@@ -1652,11 +1671,14 @@ int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s) {
     if (rc) return rc;
     // global right-hand-side scratch of every run, grown before any launch so
     // that concurrent runs use disjoint parts of one buffer
+    // right-hand sides per CTA: two on 16-wide runs when the autotuner chose so
+    auto nr_of = [&](const SweepRun& u) { return (c->tune.solve_nr == 2 && u.ldw == 16 && R >= 2) ? 2 : 1; };
     size_t ztot = 0;
     std::vector<size_t> zoff(runs.size());
     for (size_t ri = 0; ri < runs.size(); ++ri) {
+        const int nr = nr_of(runs[ri]);
         zoff[ri] = ztot;
-        ztot += sizeof(cx<T>) * (size_t)c->n_tot * runs[ri].ldw * R * runs[ri].n;
+        ztot += sizeof(cx<T>) * (size_t)c->n_tot * runs[ri].ldw * nr * ((R + nr - 1) / nr) * runs[ri].n;
     }
     if ((rc = lss_grow(c, &c->z_buf, &c->z_cap, ztot))) return rc;
     if (runs.size() > 1) cudaEventRecord(c->fork_event, s);
@@ -1666,7 +1688,12 @@ int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s) {
         if (ri > 0) cudaStreamWaitEvent(su, c->fork_event, 0);
         CrArgs<cx<T>> Ar = A;
         Ar.slab0 = u.s0;
-        rc = launch_solve<T, MODE>(c, Ar, dim3(R, u.n), (long long)c->n_tot * u.ldw, nullptr, 0, su, u.ldw, zoff[ri]);
+        if (nr_of(u) == 2)
+            rc = launch_solve<T, MODE, 2>(c, Ar, dim3((R + 1) / 2, u.n), 2LL * c->n_tot * u.ldw, nullptr, 0, su, u.ldw,
+                                          zoff[ri]);
+        else
+            rc = launch_solve<T, MODE>(c, Ar, dim3(R, u.n), (long long)c->n_tot * u.ldw, nullptr, 0, su, u.ldw,
+                                       zoff[ri]);
         if (ri > 0) {
             cudaEventRecord(c->aux_event[ri - 1], su);
             cudaStreamWaitEvent(s, c->aux_event[ri - 1], 0);

@@ -75,15 +75,18 @@ int tune_one(lss_ctx* c, int R, cudaStream_t s) {
     {
         float best = -1;
         lss_ctx::Tune pick = c->tune;
-        for (int half : {0, 1})
-            for (int bsm : {-1, 0})
-                for (int nst : {0, 2, 3, 4}) {
-                    c->tune.solve_half = half;
-                    c->tune.solve_bsm = bsm;
-                    c->tune.solve_nst = nst;
-                    const float ms = time_ms(t, s, 3, sweep);
-                    if (ms > 0 && (best < 0 || ms < best)) { best = ms; pick = c->tune; }
-                }
+        for (int nr : {1, 2})
+            for (int half : {0, 1})
+                for (int bsm : {-1, 0})
+                    for (int nst : {0, 2, 3, 4}) {
+                        if (nr == 2 && (R < 2 || half)) continue;   // two right-hand sides need the whole budget
+                        c->tune.solve_nr = nr;
+                        c->tune.solve_half = half;
+                        c->tune.solve_bsm = bsm;
+                        c->tune.solve_nst = nst;
+                        const float ms = time_ms(t, s, 3, sweep);
+                        if (ms > 0 && (best < 0 || ms < best)) { best = ms; pick = c->tune; }
+                    }
         c->tune = pick;
     }
     {   // ring stages of the 32-wide slabs' own launches (they set each pass's critical path)
@@ -149,6 +152,7 @@ extern "C" int lss_autotune(lss_ctx* c, int R, int* chosen, void* stream) {
         chosen[3] = t.rec_nb;
         chosen[4] = t.solve_nst_w;
         chosen[5] = t.solve_half;
+        chosen[6] = t.solve_nr;
     }
     return LSS_OK;
 }

@@ -93,10 +93,10 @@ class LSSolver:
 
     def autotune(self, R: int = 1, stream=None):
         """Launch parameters for R right-hand sides, picked by timing (lss_autotune)."""
-        ch = (ctypes.c_int * 6)()
+        ch = (ctypes.c_int * 7)()
         self._check(self.lib.lss_autotune(self.ctx, int(R), ch, _stream_ptr(stream)))
         return dict(fft_col_group=ch[0], solve_rhs_global=ch[1] == 0, solve_stages=ch[2], recur_stages=ch[3],
-                    wide_solve_stages=ch[4], solve_two_per_sm=ch[5] == 1)
+                    wide_solve_stages=ch[4], solve_two_per_sm=ch[5] == 1, solve_rhs_per_cta=ch[6])
 
     def graph_count(self):
         """(captured, refused) iteration graphs held by the context."""
@@ -302,10 +302,10 @@ class LSSolverBatch:
 
     def autotune(self, R: int = 1, stream=None):
         """Tune every instance for R right-hand sides (lss_autotune); returns instance 0's choice."""
-        ch = (ctypes.c_int * 6)()
+        ch = (ctypes.c_int * 7)()
         self._check(self.lib.lss_autotune(self.ctx, int(R), ch, _stream_ptr(stream)))
         return dict(fft_col_group=ch[0], solve_rhs_global=ch[1] == 0, solve_stages=ch[2], recur_stages=ch[3],
-                    wide_solve_stages=ch[4], solve_two_per_sm=ch[5] == 1)
+                    wide_solve_stages=ch[4], solve_two_per_sm=ch[5] == 1, solve_rhs_per_cta=ch[6])
 
     def profile_read(self):
         k = len(_lib.PROF_CATEGORIES)

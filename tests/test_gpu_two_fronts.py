@@ -240,3 +240,19 @@ def test_3d_workload_two_fronts_mixed():
             assert np.linalg.norm(res) / np.linalg.norm(g_ref) <= 1e-8 * (1 + 1e-6)
         del s
     assert its[0] <= its[1] + 2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_right_hand_sides_per_slab_solve_cta(monkeypatch, precision):
+    """LSS_SOLVE_NR=2: every 16-wide slab solve serves two right-hand sides per
+    CTA (an odd count leaves the last CTA half empty): bit for bit the result
+    of one right-hand side per CTA."""
+    n = 64
+    x = crand((5, n, n), 77)
+    out = []
+    for nr in ("1", "2"):
+        monkeypatch.setenv("LSS_SOLVE_NR", nr)
+        s, m, om = make(n, 8.0, 1706, precision=precision)
+        out.append(s.apply_P(to_dev(x)).cpu())
+        del s
+    assert torch.equal(out[0], out[1])
