@@ -417,9 +417,11 @@ def run_leg(args, dev, world, flush, wname, prec, steps, warmup, recursive=False
 def run_ragged(args, dev, world, flush):
     """Form (2), ragged instances: independent problems with n uniform on
     {128..384}, omega/2pi = n/8, band-limited media, one plane wave each, all
-    behind one batch context (instances run concurrently); against it the same
-    instances solved one after another, each by its own context.  Mixed
-    precision; a step is factor + plane-wave RHS + solve of every instance."""
+    behind one batch context, solved by the lockstep driver (one set of Krylov
+    vectors with a segment per instance); beside it the threaded driver (each
+    instance's own solve on a host thread) and the same instances solved one
+    after another, each by its own context.  Mixed precision; a step is
+    factor + plane-wave RHS + solve of every instance."""
     import torch
     from paper_1705_09443_gb300 import GmresOptions, LSS_MIXED, LSSolver, LSSolverBatch
     spec = dict(synth.RAGGED_32, count=args.ragged)
@@ -448,8 +450,11 @@ def run_ragged(args, dev, world, flush):
         return st
 
     out = {}
-    for name, step in (("batch", step_batch), ("sequential", step_seq)):
+    for name, step in (("batch", step_batch), ("threaded", step_batch), ("sequential", step_seq)):
+        if name == "threaded":
+            os.environ["LSS_BATCH_THREADS"] = "1"
         ts, stats = timed(step, args.steps, 1, flush, stream)
+        os.environ.pop("LSS_BATCH_THREADS", None)
         total, = max_over_ranks([sum(ts)], dev, world)
         flat = [x for st in stats for q in st for x in q]
         out[name] = {"value": len(ns) * args.steps * world / (total / 1e3), "ms_per_step": total / args.steps,
@@ -459,7 +464,7 @@ def run_ragged(args, dev, world, flush):
     del batch, single
     return {"instances": len(ns), "unit": "instances solved/s",
             "step": "factor + plane-wave RHS + FGMRES solve of every instance (mixed precision)",
-            **out["batch"], "sequential": out["sequential"],
+            "driver": "lockstep", **out["batch"], "threaded": out["threaded"], "sequential": out["sequential"],
             "batch_over_sequential": out["batch"]["value"] / out["sequential"]["value"]}
 
 
@@ -603,6 +608,8 @@ def main():
     ap.add_argument("--legs", default="2d_n256,3d_n64,3d_n64:rec",
                     help="further full-step legs (workload[:rec] for the 3D recursive approach; 'none' to skip)")
     ap.add_argument("--ragged", type=int, default=32, help="instances of the ragged batch line (0 to skip)")
+    ap.add_argument("--only-ragged", action="store_true",
+                    help="run the ragged batch line only and print it; not a bench line")
     ap.add_argument("--only-headline", action="store_true",
                     help="run the headline workload's steps only (warm-up, timed steps, the profiling pass) and "
                          "print its breakdown; for profiler launch lists, not a bench line")
@@ -626,6 +633,11 @@ def main():
     torch.cuda.set_device(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     hbm, bf16, peak_src = peaks()
+    if args.only_ragged:
+        ragged = run_ragged(args, dev, world, flush)
+        if rank == 0:
+            print(json.dumps({"only_ragged": ragged}))
+        return
 
     w, R, head = run_headline(args, dev, world, flush)
     if args.only_headline:

@@ -13,6 +13,7 @@
 // gradient holds instance q's n_q^2 values at element n_0^2 + ... + n_{q-1}^2.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <functional>
 #include <string>
 #include <thread>
@@ -73,6 +74,31 @@ long long off(const lss_ctx* c, int q, int R) { return (long long)R * c->inst_of
 
 }  // namespace
 
+// One host thread issues every instance's launches, each on its own stream,
+// between a fork from s and a join into s (no host synchronisation inside: the
+// lockstep Krylov driver calls this once per iteration).
+int lss_batch_op(lss_ctx* c, int which, const double2* x, double2* y, int R, int transpose, cudaStream_t s) {
+    const int nq = (int)c->inst.size();
+    int rc = lss_check_cuda(c, cudaEventRecord(c->fork_ev, s), "batch fork");
+    for (int q = 0; q < nq && !rc; ++q) {
+        lss_ctx* ci = c->inst[q];
+        cudaStream_t sq = c->inst_stream[q];
+        rc = lss_check_cuda(c, cudaStreamWaitEvent(sq, c->fork_ev, 0), "batch fork");
+        if (rc) break;
+        const long long o = off(c, q, R);
+        if (which == 0)
+            rc = lss_matvec(ci, x + o, y + o, R, transpose ? MV_IN_U : MV_IN_MU, transpose ? MV_OUT_AT : MV_OUT_A,
+                            nullptr, nullptr, sq);
+        else
+            rc = transpose ? lss_sweep_t(ci, x + o, y + o, R, sq) : lss_sweep(ci, x + o, y + o, R, sq);
+        if (rc) rc = lss_fail(c, rc, "instance " + std::to_string(q) + ": " + ci->err);
+        cudaError_t e = cudaEventRecord(c->inst_done[q], sq);
+        if (!e) e = cudaStreamWaitEvent(s, c->inst_done[q], 0);
+        if (e && !rc) rc = lss_check_cuda(c, e, "batch join");
+    }
+    return rc;
+}
+
 void lss_batch_free(lss_ctx* c) {
     for (lss_ctx* ci : c->inst)
         if (ci) lss_destroy(ci);
@@ -110,6 +136,16 @@ int lss_batch_apply(lss_ctx* c, int which, const double2* x, double2* y, int R, 
 
 int lss_batch_solve(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
                     cudaStream_t s, int adjoint) {
+    // default: every instance's right-hand sides in one lockstep Krylov
+    // iteration; LSS_BATCH_THREADS=1 drives each instance's own solve from a
+    // host thread instead
+    const char* ev = std::getenv("LSS_BATCH_THREADS");
+    if (!(ev && ev[0] == '1')) {
+        int rc = LSS_OK;
+        if (adjoint)
+            rc = batch_run(c, s, [](int, lss_ctx* ci, cudaStream_t sq) { return lss_prepare_sweep_t(ci, sq); });
+        return rc ? rc : lss_fgmres_batch(c, g, u, R, o, st, s, adjoint ? 1 : 0);
+    }
     return batch_run(c, s, [&](int q, lss_ctx* ci, cudaStream_t sq) {
         const long long v = off(c, q, R);
         lss_stats* sq_st = st ? st + (size_t)q * R : nullptr;
@@ -141,6 +177,11 @@ int lss_setup_batch(lss_ctx** out, int n_inst, const lss_grid* g, const double* 
     cudaStream_t s = (cudaStream_t)stream;
     lss_ctx* c = new lss_ctx();
     c->prec = precision;
+    c->fronts = slab->fronts == 2 ? 2 : 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c->num_sms <= 0)
+        c->num_sms = 1;
     c->inst.assign(n_inst, nullptr);
     c->inst_stream.assign(n_inst, nullptr);
     c->inst_done.assign(n_inst, nullptr);

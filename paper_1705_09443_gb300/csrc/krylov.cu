@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <functional>
 #include <complex>
 #include <string>
 #include <vector>
@@ -27,6 +28,14 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
+// Right-hand side r of a vector: entries [offs[r], offs[r+1]) when the
+// right-hand sides have different lengths (the instances of a ragged batch
+// side by side), else [r N, (r+1) N).
+__device__ __forceinline__ void seg_of(const long long* offs, long long N, int r, long long& o, long long& len) {
+    if (offs) { o = offs[r]; len = offs[r + 1] - o; }
+    else { o = (long long)r * N; len = N; }
+}
+
 // part[(i*R + r)*nblk + blk] = sum over this block's x of conj(V_i[r][x]) w[r][x],
 // for Q basis vectors i0 .. i0+Q-1 per CTA, reading w once for all of them;
 // the block's sum in a fixed order (warp shuffles, then the warps in turn).
@@ -35,6 +44,7 @@ template <int Q>
 __device__ __forceinline__ void dots_body(const double2* __restrict__ vb, long long vstride,
                                           const double2* __restrict__ wr, long long N, int R, int i0, int r,
                                           double2* __restrict__ part, double2 (*red)[kRedThreads / 32]) {
+    // (vb, wr: this right-hand side's entries; N: their count)
     const int nblk = gridDim.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double2 acc[Q];
@@ -65,16 +75,19 @@ constexpr int kDotsQ = 4;   // basis vectors per CTA of the Gram-Schmidt inner p
 
 __global__ void __launch_bounds__(kRedThreads) dots_multi_kernel(const double2* __restrict__ V, long long vstride,
                                                                  const double2* __restrict__ w, long long N, int R,
-                                                                 int J, double2* __restrict__ part) {
+                                                                 int J, double2* __restrict__ part,
+                                                                 const long long* __restrict__ offs) {
     __shared__ double2 red[kDotsQ][kRedThreads / 32];
     const int r = blockIdx.y, i0 = blockIdx.z * kDotsQ;
-    const double2* wr = w + (long long)r * N;
-    const double2* vb = V + (long long)i0 * vstride + (long long)r * N;
+    long long o, len;
+    seg_of(offs, N, r, o, len);
+    const double2* wr = w + o;
+    const double2* vb = V + (long long)i0 * vstride + o;
     switch (min(kDotsQ, J - i0)) {
-        case 1: dots_body<1>(vb, vstride, wr, N, R, i0, r, part, red); break;
-        case 2: dots_body<2>(vb, vstride, wr, N, R, i0, r, part, red); break;
-        case 3: dots_body<3>(vb, vstride, wr, N, R, i0, r, part, red); break;
-        default: dots_body<4>(vb, vstride, wr, N, R, i0, r, part, red); break;
+        case 1: dots_body<1>(vb, vstride, wr, len, R, i0, r, part, red); break;
+        case 2: dots_body<2>(vb, vstride, wr, len, R, i0, r, part, red); break;
+        case 3: dots_body<3>(vb, vstride, wr, len, R, i0, r, part, red); break;
+        default: dots_body<4>(vb, vstride, wr, len, R, i0, r, part, red); break;
     }
 }
 
@@ -97,23 +110,30 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double2* __re
 
 // w[r][x] += sign * sum_{i<J} h[i*R + r] V_i[r][x]
 __global__ void update_kernel(const double2* __restrict__ V, long long vstride, const double2* __restrict__ h,
-                              int J, double2* __restrict__ w, long long N, int R, double sign) {
+                              int J, double2* __restrict__ w, long long N, int R, double sign,
+                              const long long* __restrict__ offs) {
     const int r = blockIdx.y;
-    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < N; x += (long long)gridDim.x * blockDim.x) {
+    long long o, len;
+    seg_of(offs, N, r, o, len);
+    for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < len;
+         x += (long long)gridDim.x * blockDim.x) {
         double2 acc = mk(0.0, 0.0);
-        for (int i = 0; i < J; ++i) acc = cfma(h[i * R + r], V[(long long)i * vstride + (long long)r * N + x], acc);
-        double2 wv = w[(long long)r * N + x];
-        w[(long long)r * N + x] = mk(wv.x + sign * acc.x, wv.y + sign * acc.y);
+        for (int i = 0; i < J; ++i) acc = cfma(h[i * R + r], V[(long long)i * vstride + o + x], acc);
+        double2 wv = w[o + x];
+        w[o + x] = mk(wv.x + sign * acc.x, wv.y + sign * acc.y);
     }
 }
 
 // y[r] = x[r] * scale[r]  (scale = 0 leaves zeros)
 __global__ void scale_kernel(const double2* __restrict__ x, double2* __restrict__ y, const double* __restrict__ sc,
-                             long long N) {
+                             long long N, const long long* __restrict__ offs) {
     const int r = blockIdx.y;
     const double s = sc[r];
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
-        y[(long long)r * N + e] = s * x[(long long)r * N + e];
+    long long o, len;
+    seg_of(offs, N, r, o, len);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+         e += (long long)gridDim.x * blockDim.x)
+        y[o + e] = s * x[o + e];
 }
 
 // y = a - b
@@ -273,33 +293,47 @@ struct Krylov {
     double2* hnorm;  // R: ||w||^2
     double* scdev;   // R scales
     int grid1d;
+    const long long* offs;   // per right-hand side segments (null: uniform length N)
 };
 
 // h[0..J) for every r = V_i^H w  (accumulate: h += ...)
 void dots(Krylov& K, const double2* V, long long vstride, int J, const double2* w, double2* h, int accumulate) {
     ProfScope ps(K.c, K.s, LSS_PROF_KRYLOV, 2);
     dots_multi_kernel<<<dim3(K.nblk, K.R, (J + kDotsQ - 1) / kDotsQ), kRedThreads, 0, K.s>>>(V, vstride, w, K.N,
-                                                                                            K.R, J, K.part);
+                                                                                            K.R, J, K.part, K.offs);
     const int JR = J * K.R;
     reduce_kernel<<<JR, kRedThreads, 0, K.s>>>(K.part, K.nblk, h, accumulate);
 }
 
-}  // namespace
+// The FGMRES driver over R right-hand sides of one operator: the vectors
+// (RN entries each) hold the right-hand sides side by side, in segments of
+// N entries or given by offs; apply_A and precond act on a whole vector.
+struct FgOps {
+    long long N;              // entries per right-hand side (the longest with offs)
+    long long RN;             // entries of a whole vector
+    const long long* offs;    // device, R + 1 segment offsets, or null
+    std::function<int(const double2*, double2*, cudaStream_t)> apply_A, precond;
+    bool graphs;              // iterations may be captured into CUDA graphs
+    int key;                  // graph key beside R and the restart length
+};
 
-int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
-               cudaStream_t s, int transpose) {
-    // transpose = 1: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T;
-    // transpose = 2: the sparsified system H x = g on the n_tot^2 grid (Sec. 4)
-    // preconditioned by the sweep on grid vectors
-    const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
-    const bool grid = transpose == 2;
-    const long long N = grid ? (long long)c->n_tot * c->n_tot : c->npts();
-    auto apply_A = [&](const double2* x, double2* y, cudaStream_t st_) -> int {
-        return grid ? lss_apply_H(c, x, y, R, st_) : lss_matvec(c, x, y, R, mv_in, mv_out, nullptr, nullptr, st_);
-    };
+// Workspace generation that captured graphs depend on: a batch's own buffers
+// and every instance's (each counter only grows, so the sum changes whenever
+// any of them does).
+unsigned long long gen_of(const lss_ctx* c) {
+    unsigned long long g = c->buf_gen;
+    for (const lss_ctx* ci : c->inst) g += ci->buf_gen;
+    return g;
+}
+
+int fgmres_core(lss_ctx* c, const FgOps& F, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
+                cudaStream_t s) {
+    const long long N = F.N;
+    const int transpose = F.key;
+    auto apply_A = F.apply_A;
     const int m = o->restart;
     const int maxit = o->max_iter;
-    const long long RN = (long long)R * N;
+    const long long RN = F.RN;
     // storage: V (m+1), Z (m), w, r
     const size_t nvec = (size_t)(m + 1) + m + 2;
     int rc = lss_grow(c, (void**)&c->kr_buf, &c->kr_cap, nvec * RN * sizeof(double2));
@@ -308,7 +342,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     double2* Z = V + (size_t)(m + 1) * RN;
     double2* w = Z + (size_t)m * RN;
     double2* rv = w + RN;
-    Krylov K{c, s, N, R, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    Krylov K{c, s, N, R, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, F.offs};
     // grids sized for the whole batch: about four CTAs per SM over all right-hand sides
     K.nblk = std::max(1, std::min(4 * c->num_sms / R, (int)((N + kRedThreads - 1) / kRedThreads)));
     const size_t red_bytes = (size_t)(m + 1) * R * K.nblk * sizeof(double2) +
@@ -327,7 +361,6 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     const int small = std::min(1024, std::max(32, (R + 31) / 32 * 32));
 
     double2* hnorm = K.hnorm;
-    if (transpose == 1 && (rc = lss_prepare_sweep_t(c, s))) return rc;
 
     // Iteration j on stream bs: Z_j = P V_j, w = A Z_j, two Gram-Schmidt passes
     // against V_0..V_j, ||w||^2, the Givens update of every right-hand side,
@@ -337,19 +370,18 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         Kb.s = bs;
         const double2* Vj = V + (size_t)j * RN;
         double2* Zj = Z + (size_t)j * RN;
-        int r = grid ? lss_sweep_grid(c, Vj, Zj, R, bs)
-                     : (transpose ? lss_sweep_t(c, Vj, Zj, R, bs) : lss_sweep(c, Vj, Zj, R, bs));
+        int r = F.precond(Vj, Zj, bs);
         if (!r) r = apply_A(Zj, w, bs);
         if (r) return r;
         dots(Kb, V, RN, j + 1, w, K.hdev, 0);
-        { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.hdev, j + 1, w, N, R, -1.0); }
+        { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.hdev, j + 1, w, N, R, -1.0, F.offs); }
         dots(Kb, V, RN, j + 1, w, K.h2dev, 0);
-        { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.h2dev, j + 1, w, N, R, -1.0); }
+        { ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 1); update_kernel<<<dim3(g1, R), 256, 0, bs>>>(V, RN, K.h2dev, j + 1, w, N, R, -1.0, F.offs); }
         dots(Kb, w, 0, 1, w, hnorm, 0);
         {
             ProfScope ps_(c, bs, LSS_PROF_KRYLOV, 2);
             givens_kernel<<<1, small, 0, bs>>>(gs, K.hdev, K.h2dev, hnorm, K.scdev, R, m, j);
-            scale_kernel<<<dim3(g1, R), 256, 0, bs>>>(w, V + (size_t)(j + 1) * RN, K.scdev, N);
+            scale_kernel<<<dim3(g1, R), 256, 0, bs>>>(w, V + (size_t)(j + 1) * RN, K.scdev, N, F.offs);
         }
         return lss_check_cuda(c, cudaGetLastError(), "arnoldi");
     };
@@ -357,24 +389,24 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     // uncaptured at the current workspace generation (every buffer the body
     // touches exists), not while profiling (events around kernel groups), and
     // not for the 3D sweep (a cooperative grid-synchronised launch).
-    const bool use_graph = c->graphs_on && !c->prof_on && c->dim == 2;
+    const bool use_graph = F.graphs && c->graphs_on && !c->prof_on;
     bool warm = false;
     for (const auto& k : c->graph_warm)
-        warm |= k[0] == R && k[1] == transpose && (unsigned long long)k[2] == c->buf_gen && k[3] == m;
+        warm |= k[0] == R && k[1] == transpose && (unsigned long long)k[2] == gen_of(c) && k[3] == m;
     warm &= use_graph;
     // graph of iteration j: a gate kernel (sets the condition from gs.any)
     // followed by an IF node whose body is the captured iteration
     auto graph_for = [&](int j) -> cudaGraphExec_t {
         for (const auto& gr : c->graphs)
-            if (gr.j == j && gr.R == R && gr.transpose == transpose && gr.gen == c->buf_gen && gr.m == m)
+            if (gr.j == j && gr.R == R && gr.transpose == transpose && gr.gen == gen_of(c) && gr.m == m)
                 return gr.exec;
         std::vector<lss_ctx::GraphRec> keep;   // drop graphs of older workspaces
         for (const auto& gr : c->graphs) {
-            if (gr.gen == c->buf_gen) keep.push_back(gr);
+            if (gr.gen == gen_of(c)) keep.push_back(gr);
             else if (gr.exec) cudaGraphExecDestroy(gr.exec);
         }
         c->graphs.swap(keep);
-        const unsigned long long gen0 = c->buf_gen;
+        const unsigned long long gen0 = gen_of(c);
         const std::string err0 = c->err;
         cudaGraphExec_t ex = nullptr;
         cudaGraph_t graph = nullptr;
@@ -408,7 +440,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
             const int brc = body(j, c->cap_stream);
             cudaGraph_t out = nullptr;
             const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &out);
-            ok = !brc && !e && c->buf_gen == gen0;
+            ok = !brc && !e && gen_of(c) == gen0;
             if (ok && cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) ex = nullptr;
         }
         if (graph) cudaGraphDestroy(graph);
@@ -454,7 +486,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         if (!c->iter_ev[q] && cudaEventCreateWithFlags(&c->iter_ev[q], cudaEventDisableTiming) != cudaSuccess)
             return lss_check_cuda(c, cudaGetLastError(), "iteration events");
     while (true) {
-        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); scale_kernel<<<dim3(g1, R), 256, 0, s>>>(rv, V, K.scdev, N); }
+        { ProfScope ps_(c, s, LSS_PROF_KRYLOV, 1); scale_kernel<<<dim3(g1, R), 256, 0, s>>>(rv, V, K.scdev, N, F.offs); }
         const int nj = std::min(m, maxit - total);
         for (int j = 0; j < nj; ++j) {
             bool graphed = false;
@@ -482,7 +514,7 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
         if (J > 0) {   // x += Z y with y from each RHS's triangular system
             ProfScope ps_(c, s, LSS_PROF_KRYLOV, 2);
             backsolve_kernel<<<1, small, 0, s>>>(gs, K.hdev, R, m, J);
-            update_kernel<<<dim3(g1, R), 256, 0, s>>>(Z, RN, K.hdev, J, u, N, R, +1.0);
+            update_kernel<<<dim3(g1, R), 256, 0, s>>>(Z, RN, K.hdev, J, u, N, R, +1.0, F.offs);
         }
         bool all_done = true;
         for (int r = 0; r < R; ++r) all_done &= (bool)done[r];
@@ -521,10 +553,77 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     if (use_graph && !warm) {   // later solves with this R, transpose and m replay captured iterations
         std::vector<std::array<long long, 4>> keep;
         for (const auto& k : c->graph_warm)
-            if ((unsigned long long)k[2] == c->buf_gen && !(k[0] == R && k[1] == transpose && k[3] == m))
+            if ((unsigned long long)k[2] == gen_of(c) && !(k[0] == R && k[1] == transpose && k[3] == m))
                 keep.push_back(k);
-        keep.push_back({(long long)R, (long long)transpose, (long long)c->buf_gen, (long long)m});
+        keep.push_back({(long long)R, (long long)transpose, (long long)gen_of(c), (long long)m});
         c->graph_warm.swap(keep);
     }
     return conv ? LSS_OK : lss_fail(c, LSS_ERR_NOCONVERGE, "GMRES reached max_iter before tol");
+}
+
+}  // namespace
+
+int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
+               cudaStream_t s, int transpose) {
+    // transpose = 1: solve A^T x = g (A^T = I + omega^2 M K) preconditioned by P^T;
+    // transpose = 2: the sparsified system H x = g on the n_tot^2 grid (Sec. 4)
+    // preconditioned by the sweep on grid vectors
+    const int mv_in = transpose ? MV_IN_U : MV_IN_MU, mv_out = transpose ? MV_OUT_AT : MV_OUT_A;
+    const bool grid = transpose == 2;
+    const long long N = grid ? (long long)c->n_tot * c->n_tot : c->npts();
+    if (transpose == 1) {
+        const int rc = lss_prepare_sweep_t(c, s);
+        if (rc) return rc;
+    }
+    FgOps F;
+    F.N = N;
+    F.RN = (long long)R * N;
+    F.offs = nullptr;
+    F.apply_A = [c, R, grid, mv_in, mv_out](const double2* x, double2* y, cudaStream_t st_) -> int {
+        return grid ? lss_apply_H(c, x, y, R, st_) : lss_matvec(c, x, y, R, mv_in, mv_out, nullptr, nullptr, st_);
+    };
+    F.precond = [c, R, grid, transpose](const double2* x, double2* y, cudaStream_t st_) -> int {
+        return grid ? lss_sweep_grid(c, x, y, R, st_)
+                    : (transpose ? lss_sweep_t(c, x, y, R, st_) : lss_sweep(c, x, y, R, st_));
+    };
+    // not for the 3D sweep (a cooperative grid-synchronised launch)
+    F.graphs = c->dim == 2;
+    F.key = transpose;
+    return fgmres_core(c, F, g, u, R, o, st, s);
+}
+
+// The ragged batch in lockstep: every instance's right-hand sides advance
+// together as the segments of one set of Krylov vectors (instance q's R x n_q^2
+// entries side by side, as in the batch layout), one driver for all of them;
+// the operator and the preconditioner act on every instance (lss_batch_op).
+int lss_fgmres_batch(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
+                     cudaStream_t s, int transpose) {
+    const int nq = (int)c->inst.size();
+    const int RB = nq * R;
+    std::vector<long long> offs(RB + 1);
+    long long nmax = 0;
+    for (int q = 0; q < nq; ++q) {
+        const long long nn = c->inst_off[q + 1] - c->inst_off[q];
+        nmax = std::max(nmax, nn);
+        for (int r = 0; r < R; ++r) offs[q * R + r] = (long long)R * c->inst_off[q] + (long long)r * nn;
+    }
+    offs[RB] = (long long)R * c->inst_off[nq];
+    int rc = lss_grow(c, &c->seg_buf, &c->seg_cap, offs.size() * sizeof(long long));
+    if (!rc) rc = lss_check_cuda(c, cudaMemcpyAsync(c->seg_buf, offs.data(), offs.size() * sizeof(long long),
+                                                    cudaMemcpyHostToDevice, s), "batch segments");
+    if (!rc) rc = lss_check_cuda(c, cudaStreamSynchronize(s), "batch segments");
+    if (rc) return rc;
+    FgOps F;
+    F.N = nmax;
+    F.RN = offs[RB];
+    F.offs = (const long long*)c->seg_buf;
+    F.apply_A = [c, R, transpose](const double2* x, double2* y, cudaStream_t st_) -> int {
+        return lss_batch_op(c, 0, x, y, R, transpose, st_);
+    };
+    F.precond = [c, R, transpose](const double2* x, double2* y, cudaStream_t st_) -> int {
+        return lss_batch_op(c, 1, x, y, R, transpose, st_);
+    };
+    F.graphs = true;   // the instances' launches join the capture through the fork/join events
+    F.key = transpose;
+    return fgmres_core(c, F, g, u, RB, o, st, s);
 }

@@ -38,7 +38,7 @@ void free_ctx(lss_ctx* c) {
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->gam_aux_r, c->coef64,
                     c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->iface_t, c->d_slabs,
                     c->d_err, c->d_bar, c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf,
-                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf, c->hz_buf};
+                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf, c->hz_buf, c->seg_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->chunk_dev)
@@ -127,6 +127,13 @@ int lss_check_cuda(lss_ctx* c, cudaError_t e, const char* what) {
 }
 
 int lss_check_device_err(lss_ctx* c, cudaStream_t s) {
+    if (!c->d_err) {   // a batch: its instances' status words
+        for (size_t q = 0; q < c->inst.size(); ++q) {
+            const int rc = lss_check_device_err(c->inst[q], s);
+            if (rc) return lss_fail(c, rc, "instance " + std::to_string(q) + ": " + c->inst[q]->err);
+        }
+        return LSS_OK;
+    }
     int h = 0;
     cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (!e) e = cudaStreamSynchronize(s);

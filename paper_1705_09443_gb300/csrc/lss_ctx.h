@@ -196,6 +196,7 @@ struct lss_ctx {
     std::vector<GraphRec> graphs;
     std::vector<std::array<long long, 4>> graph_warm;   // (R, transpose, buf_gen, m) solved once uncaptured
     void* gm_buf = nullptr; size_t gm_cap = 0;          // device GMRES state (Hessenberg, rotations, masks)
+    void* seg_buf = nullptr; size_t seg_cap = 0;        // ragged batch in lockstep: the right-hand sides' segments
     int* host_flags = nullptr;                          // pinned host copies of the "RHS active" flag per iteration
     cudaEvent_t iter_ev[8] = {};                        // completion of the last iterations' flag copies
 
@@ -308,3 +309,8 @@ int lss_extract_grid(lss_ctx* c, const double2* U, double2* u, int R, cudaStream
 int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s);
 int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
                cudaStream_t s, int transpose = 0);
+int lss_fgmres_batch(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
+                     cudaStream_t s, int transpose = 0);
+// batch.cu: the operator (which = 0) or the preconditioner (1) of every
+// instance of a batch, issued from the calling thread on the instances' streams
+int lss_batch_op(lss_ctx* c, int which, const double2* x, double2* y, int R, int transpose, cudaStream_t s);

@@ -300,6 +300,12 @@ class LSSolverBatch:
     def use_graphs(self, enable: bool = True):
         self._check(self.lib.lss_set_graphs(self.ctx, int(enable)))
 
+    def graph_count(self):
+        """(captured, refused) iteration graphs held by the batch and its instances."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.lss_graph_count(self.ctx, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def autotune(self, R: int = 1, stream=None):
         """Tune every instance for R right-hand sides (lss_autotune); returns instance 0's choice."""
         ch = (ctypes.c_int * 7)()
