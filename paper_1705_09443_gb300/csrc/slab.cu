@@ -1023,11 +1023,81 @@ __device__ __forceinline__ void recur_tile(const cx<T>* __restrict__ M, const cx
     }
 }
 
+// Few right-hand sides (R <= RM, RM in 1, 2, 4, 8): a 16-column tile would
+// spend most of its multiply-adds on absent columns (on FP64, where the pipe
+// is the bound, up to 16 times the work), so a tile is TR rows instead, two
+// per warp: lanes stride over k (coalesced map rows, the vector entries shared
+// by the warp's two rows), then a shuffle reduction per row and column.
+template <typename T, int RM>
+__device__ __forceinline__ void recur_rows(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
+                                           cx<T>* out, int n_tot, int R, int row0, int nrows) {
+    using C = cx<T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int p = 2 * warp; p < nrows; p += 2 * nw) {
+        const int r0 = row0 + p;
+        const bool two = p + 1 < nrows;
+        const C* m0 = M + (long long)r0 * n_tot;
+        const C* m1 = two ? m0 + n_tot : m0;
+        C a0[RM], a1[RM];
+#pragma unroll
+        for (int c = 0; c < RM; ++c) a0[c] = a1[c] = czero<C>();
+#pragma unroll 2
+        for (int k = lane; k < n_tot; k += 32) {
+            const C u0 = m0[k], u1 = m1[k];
+#pragma unroll
+            for (int c = 0; c < RM; ++c) {
+                if (RM > 1 && c >= R) break;
+                const C xv = x[(long long)k * R + c];
+                a0[c] = cfma(u0, xv, a0[c]);
+                a1[c] = cfma(u1, xv, a1[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < RM; ++c) {
+            if (RM > 1 && c >= R) break;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a0[c].x += __shfl_xor_sync(0xffffffffu, a0[c].x, o);
+                a0[c].y += __shfl_xor_sync(0xffffffffu, a0[c].y, o);
+                a1[c].x += __shfl_xor_sync(0xffffffffu, a1[c].x, o);
+                a1[c].y += __shfl_xor_sync(0xffffffffu, a1[c].y, o);
+            }
+            if (lane == 0) {
+                const long long e0 = (long long)r0 * R + c;
+                C v = base[e0];
+                v.x -= a0[c].x;
+                v.y -= a0[c].y;
+                out[e0] = v;
+                if (two) {
+                    C w = base[e0 + R];
+                    w.x -= a1[c].x;
+                    w.y -= a1[c].y;
+                    out[e0 + R] = w;
+                }
+            }
+        }
+    }
+}
+
+// One task of a recurrence step: tile (rt, ct) of out = base - M x.  RM = 0:
+// TR x kGtC tiles staged through the ring; RM > 0: TR-row tiles, every column.
+template <typename T, int TR, int RM>
+__device__ __forceinline__ void recur_task(const cx<T>* __restrict__ M, const cx<T>* x, const cx<T>* base,
+                                           cx<T>* out, int n_tot, int R, int rt, int ct, cx<T>* ring) {
+    if constexpr (RM == 0)
+        recur_tile<T, TR>(M, x, base, out, n_tot, R, rt, ct, ring);
+    else
+        recur_rows<T, RM>(M, x, base, out, n_tot, R, rt * TR, min(TR, n_tot - rt * TR));
+}
+
+template <int RM>
+__host__ __device__ constexpr int recur_col_tiles(int R) { return RM ? 1 : (R + kGtC - 1) / kGtC; }
+
 // Recurrences of all slabs with one cooperative grid when the vectors do not
 // fit the cluster kernels (many right-hand sides): lambda and mu, then phi,
 // one step per slab, a grid barrier between steps; the tiles of a step are
 // spread over the CTAs.
-template <typename T, int TR>
+template <typename T, int TR, int RM>
 __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot, int R,
                                                          const cx<T>* __restrict__ iface,
                                                          const cx<T>* __restrict__ a_first,
@@ -1039,7 +1109,7 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
     unsigned nbar = 0;                     // grid barriers passed (the arrival counter starts at zero)
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
-    const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
+    const int nrt = (n_tot + TR - 1) / TR, nct = recur_col_tiles<RM>(R);
     const int ntile = nrt * nct;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < vec;
          e += (long long)gridDim.x * blockDim.x)
@@ -1050,17 +1120,17 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
         for (int task = blockIdx.x; task < nwhich * ntile; task += gridDim.x) {   // uniform per CTA
             const int which = task / ntile, t = task % ntile;
             if (which == 0)   // mu_i = first(a_i) - Gamma_i lambda_{i-1}
-                recur_tile<T, TR>(iface + (1LL * n_slabs + i) * nt2, lp, a_first + (long long)i * vec,
+                recur_task<T, TR, RM>(iface + (1LL * n_slabs + i) * nt2, lp, a_first + (long long)i * vec,
                               phi + (long long)i * vec, n_tot, R, t / nct, t % nct, ring);
             else              // lambda_i = last(a_i) - Lambda_i lambda_{i-1}
-                recur_tile<T, TR>(iface + (long long)i * nt2, lp, a_last + (long long)i * vec,
+                recur_task<T, TR, RM>(iface + (long long)i * nt2, lp, a_last + (long long)i * vec,
                               lam + (long long)i * vec, n_tot, R, t / nct, t % nct, ring);
         }
         grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
     for (int i = n_slabs - 2; i >= 1; --i) {   // phi_i = mu_i - Phi_i phi_{i+1}
         for (int task = blockIdx.x; task < ntile; task += gridDim.x)
-            recur_tile<T, TR>(iface + (2LL * n_slabs + i) * nt2, phi + (long long)(i + 1) * vec,
+            recur_task<T, TR, RM>(iface + (2LL * n_slabs + i) * nt2, phi + (long long)(i + 1) * vec,
                           phi + (long long)i * vec, phi + (long long)i * vec, n_tot, R, task / nct, task % nct, ring);
         grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
@@ -1080,7 +1150,7 @@ __global__ void __launch_bounds__(256) recur_grid_kernel(int n_slabs, int n_tot,
 //   back:    phi_i = mu_i - Phi_i phi_{i+1} (i < c),  lambda_i = nu_i - Lambda_i lambda_{i-1} (i > c)
 // Both fronts advance in the same grid step, so the dependent steps are about
 // half of the one-front recurrences'.
-template <typename T, int TR>
+template <typename T, int TR, int RM>
 __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, int n_tot, int R,
                                                           const cx<T>* __restrict__ iface,
                                                           const cx<T>* __restrict__ a_first,
@@ -1092,7 +1162,7 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
     unsigned nbar = 0;                     // grid barriers passed (the arrival counter starts at zero)
     const long long nt2 = (long long)n_tot * n_tot;
     const long long vec = (long long)n_tot * R;
-    const int nrt = (n_tot + TR - 1) / TR, nct = (R + kGtC - 1) / kGtC;
+    const int nrt = (n_tot + TR - 1) / TR, nct = recur_col_tiles<RM>(R);
     const int ntile = nrt * nct;
     const int ns = n_slabs, c = mid;
     const C* LAM = iface;
@@ -1119,15 +1189,15 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
             const int t = task % ntile;
             if (!onL) which += 2;
             if (which == 0)
-                recur_tile<T, TR>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct, ring);
+                recur_task<T, TR, RM>(LAM + iL * nt2, V(lam, iL - 1), Vc(a_last, iL), V(lam, iL), n_tot, R, t / nct, t % nct, ring);
             else if (which == 1)
-                recur_tile<T, TR>(GAM + iL * nt2, V(lam, iL - 1), Vc(a_first, iL), V(phi, iL), n_tot, R, t / nct,
+                recur_task<T, TR, RM>(GAM + iL * nt2, V(lam, iL - 1), Vc(a_first, iL), V(phi, iL), n_tot, R, t / nct,
                               t % nct, ring);
             else if (which == 2)
-                recur_tile<T, TR>(PHI + iR * nt2, V(phi, iR + 1), Vc(a_first, iR), V(phi, iR), n_tot, R, t / nct,
+                recur_task<T, TR, RM>(PHI + iR * nt2, V(phi, iR + 1), Vc(a_first, iR), V(phi, iR), n_tot, R, t / nct,
                               t % nct, ring);
             else
-                recur_tile<T, TR>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct, ring);
+                recur_task<T, TR, RM>(PSI + iR * nt2, V(phi, iR + 1), Vc(a_last, iR), V(lam, iR), n_tot, R, t / nct, t % nct, ring);
         }
         grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
@@ -1136,18 +1206,18 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
         for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
             const int t = task % ntile;
             if (task < ntile)
-                recur_tile<T, TR>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, ring);
+                recur_task<T, TR, RM>(GAM + c * nt2, V(lam, c - 1), Vc(a_first, c), V(phi, c), n_tot, R, t / nct, t % nct, ring);
             else
-                recur_tile<T, TR>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, ring);
+                recur_task<T, TR, RM>(LAM + c * nt2, V(lam, c - 1), Vc(a_last, c), V(lam, c), n_tot, R, t / nct, t % nct, ring);
         }
         grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
     for (int task = blockIdx.x; task < 2 * ntile; task += gridDim.x) {
         const int t = task % ntile;
         if (task < ntile)
-            recur_tile<T, TR>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, ring);
+            recur_task<T, TR, RM>(PHI + c * nt2, V(phi, c + 1), V(phi, c), V(phi, c), n_tot, R, t / nct, t % nct, ring);
         else
-            recur_tile<T, TR>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, ring);
+            recur_task<T, TR, RM>(PSI + c * nt2, V(phi, c + 1), V(lam, c), V(lam, c), n_tot, R, t / nct, t % nct, ring);
     }
     grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     for (int st = 0; st < S; ++st) {   // both fronts back toward the boundaries
@@ -1158,9 +1228,9 @@ __global__ void __launch_bounds__(256) recur_grid2_kernel(int n_slabs, int mid, 
             const int t = task % ntile;
             const bool left = onL && task < ntile;
             if (left)
-                recur_tile<T, TR>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, ring);
+                recur_task<T, TR, RM>(PHI + iL * nt2, V(phi, iL + 1), V(phi, iL), V(phi, iL), n_tot, R, t / nct, t % nct, ring);
             else
-                recur_tile<T, TR>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, ring);
+                recur_task<T, TR, RM>(LAM + iR * nt2, V(lam, iR - 1), V(lam, iR), V(lam, iR), n_tot, R, t / nct, t % nct, ring);
         }
         grid_barrier_count(bar, (++nbar) * gridDim.x, err);
     }
@@ -1970,21 +2040,33 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
     cudaStreamIsCapturing(s, &cap);
     if (cap != cudaStreamCaptureStatusNone) return LSS_ERR_UNSUPPORTED;
     // tiles of the widest step (lambda and mu with one front, both fronts' two
-    // products with two): 64-row tiles when they cover at least half the SMs
-    // (two 32-row tiles on one SM take longer than one 64-row tile), else 32-row
-    const long long prods = two ? 4 : 2, nct = (R + kGtC - 1) / kGtC;
-    const int TR = 2 * prods * ((c->n_tot + 63) / 64) * nct >= c->num_sms ? 64 : 32;
-    const size_t smem = (size_t)kGtS * (TR == 64 ? gt_stage_ent<64>() : gt_stage_ent<32>()) * sizeof(C);
-    const void* k = two ? (TR == 64 ? (const void*)recur_grid2_kernel<T, 64> : (const void*)recur_grid2_kernel<T, 32>)
-                        : (TR == 64 ? (const void*)recur_grid_kernel<T, 64> : (const void*)recur_grid_kernel<T, 32>);
-    static int grid[2][2] = {{0, 0}, {0, 0}};   // per (fronts, tile height), this process's device
+    // products with two): with up to 8 right-hand sides, 16-row tiles of every
+    // column (recur_rows); else 64 x 16 tiles when they cover at least half the
+    // SMs (two 32-row tiles on one SM take longer than one 64-row tile), else 32 x 16
+    const long long prods = two ? 4 : 2;
+    const int RM = R == 1 ? 1 : R == 2 ? 2 : R <= 4 ? 4 : R <= 8 ? 8 : 0;
+    const long long nct = RM ? 1 : (R + kGtC - 1) / kGtC;
+    const int TR = RM ? 16 : 2 * prods * ((c->n_tot + 63) / 64) * nct >= c->num_sms ? 64 : 32;
+    const size_t smem = RM ? 0 : (size_t)kGtS * (TR == 64 ? gt_stage_ent<64>() : gt_stage_ent<32>()) * sizeof(C);
+    const int var = RM ? 2 + (RM == 1 ? 0 : RM == 2 ? 1 : RM == 4 ? 2 : 3) : TR == 64;
+    using KernPtr = const void*;
+    const KernPtr k1[6] = {(KernPtr)recur_grid_kernel<T, 32, 0>, (KernPtr)recur_grid_kernel<T, 64, 0>,
+                           (KernPtr)recur_grid_kernel<T, 16, 1>, (KernPtr)recur_grid_kernel<T, 16, 2>,
+                           (KernPtr)recur_grid_kernel<T, 16, 4>, (KernPtr)recur_grid_kernel<T, 16, 8>};
+    const KernPtr k2[6] = {(KernPtr)recur_grid2_kernel<T, 32, 0>, (KernPtr)recur_grid2_kernel<T, 64, 0>,
+                           (KernPtr)recur_grid2_kernel<T, 16, 1>, (KernPtr)recur_grid2_kernel<T, 16, 2>,
+                           (KernPtr)recur_grid2_kernel<T, 16, 4>, (KernPtr)recur_grid2_kernel<T, 16, 8>};
+    const void* k = two ? k2[var] : k1[var];
+    static int grid[2][6] = {};   // per (fronts, variant), this process's device
     int grid_now;
     {
         std::lock_guard<std::mutex> lock(lss_config_mutex());
-        int& g = grid[two][TR == 64];
+        int& g = grid[two][var];
         if (!g) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e) return lss_check_cuda(c, e, "recurrence attribute");
+            if (smem) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e) return lss_check_cuda(c, e, "recurrence attribute");
+            }
             int per = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, smem);
             g = std::max(1, per) * c->num_sms;

@@ -114,6 +114,26 @@ def test_grid_recurrences_with_many_right_hand_sides(fronts, R):
         assert rel(y[r], pb.precondition(x[r])) <= 1e-10
 
 
+@pytest.mark.parametrize("fronts", [2, 1])
+def test_grid_recurrences_with_few_right_hand_sides(fronts):
+    """FP64 at n = 320 (n_tot = 346): a 16-CTA cluster's block of map rows
+    exceeds the cluster kernels' budget even for one right-hand side, so the
+    grid recurrences run, with R <= 8 in their row form (16-row tiles of every
+    column, no padded columns).  R = 1, 2, 3, 5 and 8 equal the same columns
+    of the 16-column tile form (R = 16) to 1e-12; R = 1 equals the oracle to
+    1e-10."""
+    n = 320
+    s, m, om = make(n, 40.0, 23 + fronts, fronts=fronts)
+    x = crand((16, n, n), 40 + fronts)
+    y16 = s.apply_P(to_dev(x)).cpu().numpy()
+    for R in (1, 2, 3, 5, 8):
+        y = s.apply_P(to_dev(x[:R])).cpu().numpy()
+        for r in range(R):
+            assert rel(y[r], y16[r]) <= 1e-12, (R, r)
+    pb = O.Problem2D(n, om, m, O.Params(b_pml=12, b_slab=4, fronts=fronts))
+    assert rel(y16[0], pb.precondition(x[0])) <= 1e-10
+
+
 def test_solution_matches_oracle(n64):
     from paper_1705_09443_gb300 import GmresOptions
     s, m, om, pb = n64
