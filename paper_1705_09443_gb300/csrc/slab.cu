@@ -935,21 +935,6 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
 // bytes in flight per SM: the maps come from DRAM at every step).
 constexpr int kGtC = 16, kGtK = 32, kGtS = 4;
 
-template <typename C>
-__device__ __forceinline__ void cp_async_entry(C* dst, const C* src, bool valid) {
-    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "complex float or double");
-    if constexpr (sizeof(C) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                     "r"(valid ? 8 : 0)
-                     : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                     "r"(valid ? 16 : 0)
-                     : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // entries of one ring stage: the map tile (TR rows, kGtK + 2 per row) and
 // the vector tile (kGtK rows, kGtC + 1 per row)
