@@ -709,8 +709,11 @@ __device__ __forceinline__ void cr_body(const CrArgs<C>& A, const SlabDev& sd, i
         const int4 dsc = desc[st];
         if (dsc.x < 0) break;
         const int kind = dsc.x, l = dsc.y, r0 = dsc.z, r1 = dsc.w;
-        if (!mbar_wait(&full[st], (g / A.nst) & 1, A.err)) ok = false;
-        if (!__syncthreads_and(ok)) { ok = false; return; }
+        // every thread waits for the stage itself (no block-wide consensus
+        // barrier here); after an expired wait a thread stops waiting and the
+        // walk runs to its end on stale data, whose results the host discards
+        // (the status word carries the timeout)
+        if (ok && !mbar_wait(&full[st], (g / A.nst) & 1, A.err)) ok = false;
         const C* S = ring + (size_t)st * A.stage_ent;
         const int cnt = r1 - r0;
         const int Kl = lv[l].K;
@@ -912,7 +915,7 @@ __global__ void __launch_bounds__(kSolveThreads) cr_solve_kernel(CrArgs<cx<T>> A
     if (sd.w <= 16) cr_body<C, MODE, 16, NR>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
     else if constexpr (NR == 1) cr_body<C, MODE, 32, 1>(A, sd, i, r, b, tb, ring, full, desc, lv, ok);
     else if (threadIdx.x == 0) atomicOr(A.err, LSS_DERR_CONFIG);   // the host launches NR > 1 for 16-wide slabs only
-    if (!ok && threadIdx.x == 0) {
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) {
         // a wait expired: give the copies already issued a bounded chance to land
         const long long t0 = clock64();
         while (clock64() - t0 < 2000000ll) __nanosleep(1000);
