@@ -574,6 +574,9 @@ int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres*
     if (transpose == 1) {
         const int rc = lss_prepare_sweep_t(c, s);
         if (rc) return rc;
+    } else {   // block LU factors before any iteration is captured
+        const int rc = lss_thomas_prepare(c, R, s);
+        if (rc) return rc;
     }
     FgOps F;
     F.N = N;

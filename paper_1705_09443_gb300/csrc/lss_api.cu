@@ -38,7 +38,8 @@ void free_ctx(lss_ctx* c) {
     void* ptrs[] = {c->m, c->khatT, c->tw, c->gam_phys, c->gam_aux, c->gam_aux_r, c->coef64,
                     c->coef == c->coef64 ? nullptr : c->coef, c->fac, c->cr_work, c->iface, c->iface_t, c->d_slabs,
                     c->d_err, c->d_bar, c->mv_buf, c->f_buf, c->side_buf, c->z_buf, c->kr_buf, c->red_buf,
-                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf, c->hz_buf, c->seg_buf};
+                    c->io_buf, c->dir_buf, c->gr_buf, c->ifx_buf, c->ifp_buf, c->gm_buf, c->hz_buf, c->seg_buf,
+                    c->th_buf, c->tq_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (void* p : c->chunk_dev)

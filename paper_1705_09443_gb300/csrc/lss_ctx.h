@@ -197,6 +197,9 @@ struct lss_ctx {
     std::vector<std::array<long long, 4>> graph_warm;   // (R, transpose, buf_gen, m) solved once uncaptured
     void* gm_buf = nullptr; size_t gm_cap = 0;          // device GMRES state (Hessenberg, rotations, masks)
     void* seg_buf = nullptr; size_t seg_cap = 0;        // ragged batch in lockstep: the right-hand sides' segments
+    void* th_buf = nullptr; size_t th_cap = 0;          // block LU of the 16-wide slabs: T_k^{-1}, V_k, Y_k per block row
+    void* tq_buf = nullptr; size_t tq_cap = 0;          // block LU solves: q_k per CTA
+    bool th_valid = false;                              // th_buf holds the factors of the current medium
     int* host_flags = nullptr;                          // pinned host copies of the "RHS active" flag per iteration
     cudaEvent_t iter_ev[8] = {};                        // completion of the last iterations' flag copies
 
@@ -309,6 +312,9 @@ int lss_extract_grid(lss_ctx* c, const double2* U, double2* u, int R, cudaStream
 int lss_set_medium_impl(lss_ctx* c, const double* m_dev, cudaStream_t s);
 int lss_fgmres(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
                cudaStream_t s, int transpose = 0);
+// slab.cu: the block LU factors of the 16-wide slabs for solves with R >= 16
+// right-hand sides (nothing to do for fewer, or when they are current)
+int lss_thomas_prepare(lss_ctx* c, int R, cudaStream_t s);
 int lss_fgmres_batch(lss_ctx* c, const double2* g, double2* u, int R, const lss_gmres* o, lss_stats* st,
                      cudaStream_t s, int transpose = 0);
 // batch.cu: the operator (which = 0) or the preconditioner (1) of every

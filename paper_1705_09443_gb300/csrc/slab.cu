@@ -34,6 +34,7 @@
 // run for all slabs at once; only the short recurrences on n_tot-vectors are
 // sequential.
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1677,6 +1678,370 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
     return lss_check_cuda(c, cudaGetLastError(), "slab solve launch");
 }
 
+// ---------------------------------------------------------------- block LU slab solves (many right-hand sides)
+// With at least kThMinR right-hand sides the 16-wide slabs are solved by the
+// block LU factorization along x2 (block Thomas) instead of the cyclic
+// reduction: its forward and backward sweeps are one dense (16 x 16)(16 x NRB)
+// product per block row, so each factor entry read serves NRB right-hand
+// sides from registers.  Bottom-up Schur complements (rows k = K-1 .. 0):
+//   T_{K-1} = D_{K-1},  T_k = D_k + B_k Y_{k+1},  Y_k = -T_k^{-1} C_k,
+// stored per block row as T_k^{-1}, V_k = -T_k^{-1} B_k and Y_k.  Solve:
+//   q_{K-1} = T_{K-1}^{-1} f_{K-1},  q_k = T_k^{-1} f_k + V_k q_{k+1}   (bottom-up)
+//   x_0 = q_0,  x_k = q_k + Y_k x_{k-1}                                  (top-down)
+// (rows C_k x_{k-1} + D_k x_k + B_k x_{k+1} = f_k; T_k x_k + C_k x_{k-1} =
+// f_k - B_k T_{k+1}^{-1} (...) by induction from the bottom row).  The
+// factorization is a chain of K dependent 16 x 16 inversions per slab, one
+// warp each (Gauss-Jordan with partial pivoting by warp reductions and
+// shuffles), run once per factorization when a sweep first needs it.
+constexpr int kThMinR = 16;
+constexpr int kThThreads = 128;
+constexpr int kThCoefMax = 16 * 9;
+
+// A 16 x 16 complex matrix held by one warp: lane l owns row l % 16, columns
+// 8 (l / 16) .. 8 (l / 16) + 7.
+template <typename T>
+struct WMat16 {
+    cx<T> v[8];
+};
+
+__device__ __forceinline__ float2 shfl_c(float2 a, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src));
+}
+__device__ __forceinline__ double2 shfl_c(double2 a, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, a.x, src), __shfl_sync(0xffffffffu, a.y, src));
+}
+
+// 1/a scaled by the larger component (no overflow or underflow in |a|^2).
+template <typename C>
+__device__ __forceinline__ C piv_recip(C a) {
+    using T = decltype(a.x);
+    const T s = T(1) / fmax(fabs(a.x), fabs(a.y));
+    const T xs = a.x * s, ys = a.y * s;
+    const T d = s / (xs * xs + ys * ys);
+    return mk(xs * d, -ys * d);
+}
+
+// Warp-synchronous Gauss-Jordan inversion with partial pivoting (candidate of
+// largest modulus by one warp reduction of a single-precision key, ties to the
+// lower row; rows exchanged only when the pivot is off the diagonal).  On
+// return the warp holds (P A)^{-1}; perm names, per row position, the row of A
+// placed there, so that A^{-1} = (P A)^{-1} P.  sing: every candidate zero.
+template <typename T>
+__device__ __forceinline__ void warp_gj16(WMat16<T>& A, int& perm, bool& sing) {
+    using C = cx<T>;
+    const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int ih = i >> 3, iu = i & 7;
+        const C ci = A.v[iu];
+        unsigned key = 0;
+        if (h == ih && r >= i) key = (__float_as_uint((float)cabs2(ci)) & ~31u) | (unsigned)(31 - r);
+        key = __reduce_max_sync(0xffffffffu, key);
+        const int p = 31 - (int)(key & 31u);
+        sing |= (key >> 5) == 0u;
+        if (p != i) {
+            const int src = (r == i ? p : (r == p ? i : r)) + 16 * h;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) A.v[u] = shfl_c(A.v[u], src);
+            const int perm_i = __shfl_sync(0xffffffffu, perm, i), perm_p = __shfl_sync(0xffffffffu, perm, p);
+            if (r == i) perm = perm_p;
+            else if (r == p) perm = perm_i;
+        }
+        const C cn = A.v[iu];
+        const C inv = piv_recip(shfl_c(cn, i + 16 * ih));
+        const C f = shfl_c(cn, r + 16 * ih) * inv;   // A[r][i] / pivot
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const C pr = shfl_c(A.v[u], i + 16 * h);
+            const int c = 8 * h + u;
+            C nv = r == i ? pr * inv : A.v[u] - f * pr;
+            if (c == i) nv = r == i ? inv : mk(-f.x, -f.y);
+            A.v[u] = nv;
+        }
+    }
+}
+
+// Coefficient of row (r, k) toward unknown (a, k + slot - 1) of a w-wide
+// subproblem: zero outside the w x w block and off the layer tridiagonal.
+template <typename C>
+__device__ __forceinline__ C th_cf(const C* row, int w, int r, int a, int slot) {
+    if (r >= w || a < 0 || a >= w || a - r < -1 || a - r > 1) return czero<C>();
+    return row[r * 9 + (a - r + 1) * 3 + slot];
+}
+
+// The bottom-up Schur chain of one 16-wide slab (one warp): T_k^{-1}, V_k, Y_k
+// at th + i * 3 K 256 (three K x 256 arrays).  Layers w..15 are identity rows.
+template <typename T>
+__global__ void __launch_bounds__(32) th_chain_kernel(const SlabDev* __restrict__ slabs, const cx<T>* __restrict__ coef,
+                                                      cx<T>* th, int K, int* err) {
+    using C = cx<T>;
+    constexpr int G = 16, LD = 17, GG = 256;
+    const SlabDev sd = slabs[blockIdx.x];
+    if (sd.ldw != 16) return;
+    __shared__ C Ts[G * LD];
+    __shared__ C Ys[GG];
+    __shared__ __align__(16) C cr[2][kThCoefMax];
+    __shared__ int ipos[G];
+    const int w = sd.w, cs = sd.cstride;
+    const int lane = threadIdx.x & 31, r = lane & 15, h = lane >> 4, cb = 8 * h;
+    const C* cf = coef + sd.coef_off;
+    C* Ti = th + (long long)blockIdx.x * 3 * K * GG;
+    C* V = Ti + (long long)K * GG;
+    C* Y = V + (long long)K * GG;
+    auto fetch = [&](int t) {
+        if (t < K) {
+            const C* src = cf + (long long)(K - 1 - t) * cs;
+            for (int e = lane; e < cs; e += 32) cp_async_entry(&cr[t & 1][e], src + e, true);
+        }
+        cp_async_commit();
+    };
+    fetch(0);
+    bool sing = false;
+    for (int t = 0; t < K; ++t) {
+        const int k = K - 1 - t;
+        cp_async_wait<0>();
+        __syncwarp();   // row k staged; the previous step's reads of Ts, Ys and ipos done
+        fetch(t + 1);
+        const C* ck = cr[t & 1];
+        WMat16<T> M;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {   // T_k = D_k + B_k Y_{k+1}
+            const int c = cb + u;
+            C v = czero<C>();
+            if (r < w) {
+                v = th_cf(ck, w, r, c, 1);
+                if (t > 0 && c < w)
+                    for (int a = max(0, r - 1); a <= min(w - 1, r + 1); ++a)
+                        v = cfma(th_cf(ck, w, r, a, 2), Ys[a * G + c], v);
+            } else if (r == c) {
+                v.x = T(1);
+            }
+            M.v[u] = v;
+        }
+        int perm = r;
+        warp_gj16<T>(M, perm, sing);
+        __syncwarp();   // every lane's reads of Ys done
+#pragma unroll
+        for (int u = 0; u < 8; ++u) Ts[r * LD + cb + u] = M.v[u];
+        if (h == 0) ipos[perm] = r;
+        __syncwarp();
+        const long long o = (long long)k * GG + r * G;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int c = cb + u;
+            Ti[o + c] = Ts[r * LD + ipos[c]];
+            C vb = czero<C>(), yc = czero<C>();
+            if (c < w)
+                for (int b = max(0, c - 1); b <= min(w - 1, c + 1); ++b) {
+                    const C tb = Ts[r * LD + ipos[b]];
+                    if (k + 1 < K) vb = cfma(tb, th_cf(ck, w, b, c, 2), vb);
+                    if (k > 0) yc = cfma(tb, th_cf(ck, w, b, c, 0), yc);
+                }
+            V[o + c] = mk(-vb.x, -vb.y);
+            Y[o + c] = mk(-yc.x, -yc.y);
+            Ys[r * G + c] = mk(-yc.x, -yc.y);
+        }
+    }
+    cp_async_wait<0>();
+    if (sing && lane == 0) atomicOr(err, LSS_DERR_SINGULAR);
+}
+
+// The sweep passes on a run of 16-wide slabs by the block LU: CTA (column
+// group, slab) solves NRB right-hand sides; thread (pg, cg) owns rows
+// 4 pg .. 4 pg + 3 of columns 2 cg, 2 cg + 1 (a 4 x 2 register tile: per k
+// of a product, four map entries and two vector entries serve eight
+// multiply-adds).  The per-row maps arrive by cp.async one step ahead, the
+// right-hand-side row is loaded one step ahead, q_k goes to a global scratch
+// (read back by the same thread in the top-down sweep).
+template <typename T, int MODE, int NRB>
+__global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, const cx<T>* __restrict__ th,
+                                                             cx<T>* qscr) {
+    using C = cx<T>;
+    constexpr int G = 16, LD = 17, GG = 256, PT = 4, CT = 2, NPG = G / PT, NCG = (NRB + CT - 1) / CT;
+    constexpr int FE = (G * NRB + kThThreads - 1) / kThThreads;   // right-hand-side entries staged per thread
+    static_assert(NPG * NCG <= kThThreads, "tile grid fits the CTA");
+    extern __shared__ __align__(16) unsigned char smt[];
+    C* Ms = reinterpret_cast<C*>(smt);   // [2 stages][2 maps][G x LD]
+    C* Fs = Ms + 4 * G * LD;             // [2][G][NRB] right-hand-side rows
+    C* Xs = Fs + 2 * G * NRB;            // [2][G][NRB] q / x rows
+    const int K = A.n_tot, tid = threadIdx.x;
+    const int i = A.slab0 + blockIdx.y, r0 = blockIdx.x * NRB;
+    const SlabDev sd = A.slabs[i];
+    const int w = sd.w, na = sd.na, ll = sd.ll;
+    const int pg = tid % NPG, cg = tid / NPG, p0 = PT * pg, c0 = CT * cg;
+    const bool act = cg < NCG;
+    const C* Ti = th + (long long)i * 3 * K * GG;
+    const C* V = Ti + (long long)K * GG;
+    const C* Y = V + (long long)K * GG;
+    C* q = qscr + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * K * G * NRB;
+    const long long nt2 = (long long)K * K, vec = (long long)K * A.R;
+    const C* cf = A.coef + sd.coef_off;
+    // right-hand side entry (block row k, layer p, column c) of Algorithm 2's pass
+    auto rhs = [&](int k, int p, int c) -> C {
+        C v = czero<C>();
+        const int rq = r0 + c;
+        if (c >= NRB || rq >= A.R || p >= w) return v;
+        if (p >= na && p <= ll) v = A.f[(long long)rq * nt2 + (long long)k * K + sd.s + A.b + (p - na)];
+        if (MODE == CR_E) {
+            const C* ck = cf + (long long)k * sd.cstride + p * 9;
+            if (p == na && i > 0)
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int kk = k + dk;
+                    if (kk >= 0 && kk < K) v = cfnma(ck[dk + 1], A.lam[(long long)(i - 1) * vec + (long long)kk * A.R + rq], v);
+                }
+            if (p == ll && i < A.n_slabs - 1)
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int kk = k + dk;
+                    if (kk >= 0 && kk < K)
+                        v = cfnma(ck[6 + dk + 1], A.phi[(long long)(i + 1) * vec + (long long)kk * A.R + rq], v);
+                }
+        }
+        return v;
+    };
+    auto fetch = [&](int stage, const C* m0, const C* m1) {
+        C* d = Ms + (size_t)stage * 2 * G * LD;
+        for (int e = tid; e < GG; e += kThThreads) {
+            cp_async_entry(d + (e >> 4) * LD + (e & 15), m0 + e, true);
+            if (m1) cp_async_entry(d + G * LD + (e >> 4) * LD + (e & 15), m1 + e, true);
+        }
+        cp_async_commit();
+    };
+    C fr[FE];   // this thread's staged right-hand-side entries of the next row: e = tid + 128 u -> (c = e / G, p = e % G)
+    auto load_f = [&](int k) {
+#pragma unroll
+        for (int u = 0; u < FE; ++u) {
+            const int e = tid + kThThreads * u;
+            fr[u] = (k >= 0 && e < G * NRB) ? rhs(k, e % G, e / G) : czero<C>();
+        }
+    };
+    auto store_f = [&](int stage) {
+#pragma unroll
+        for (int u = 0; u < FE; ++u) {
+            const int e = tid + kThThreads * u;
+            if (e < G * NRB) Fs[stage * G * NRB + (e % G) * NRB + e / G] = fr[u];
+        }
+    };
+    // ---- bottom-up: q_k = T_k^{-1} f_k + V_k q_{k+1}
+    load_f(K - 1);
+    store_f(0);
+    fetch(0, Ti + (long long)(K - 1) * GG, nullptr);
+    load_f(K - 2);
+    for (int s = 0; s < K; ++s) {
+        const int k = K - 1 - s;
+        cp_async_wait<0>();
+        __syncthreads();   // maps and right-hand side of row k staged; q_{k+1} complete
+        if (s + 1 < K) {
+            fetch((s + 1) & 1, Ti + (long long)(k - 1) * GG, V + (long long)(k - 1) * GG);
+            store_f((s + 1) & 1);
+            load_f(k - 2);
+        }
+        if (act) {
+            C acc[PT][CT];
+#pragma unroll
+            for (int a = 0; a < PT; ++a)
+#pragma unroll
+                for (int b = 0; b < CT; ++b) acc[a][b] = czero<C>();
+            const C* M0 = Ms + (size_t)(s & 1) * 2 * G * LD;
+            const C* F = Fs + (s & 1) * G * NRB;
+#pragma unroll 4
+            for (int a = 0; a < G; ++a) {
+                C m[PT], x[CT];
+#pragma unroll
+                for (int u = 0; u < PT; ++u) m[u] = M0[(p0 + u) * LD + a];
+#pragma unroll
+                for (int b = 0; b < CT; ++b) x[b] = c0 + b < NRB ? F[a * NRB + c0 + b] : czero<C>();
+#pragma unroll
+                for (int u = 0; u < PT; ++u)
+#pragma unroll
+                    for (int b = 0; b < CT; ++b) acc[u][b] = cfma(m[u], x[b], acc[u][b]);
+            }
+            if (s > 0) {
+                const C* M1 = M0 + G * LD;
+                const C* X = Xs + ((s + 1) & 1) * G * NRB;
+#pragma unroll 4
+                for (int a = 0; a < G; ++a) {
+                    C m[PT], x[CT];
+#pragma unroll
+                    for (int u = 0; u < PT; ++u) m[u] = M1[(p0 + u) * LD + a];
+#pragma unroll
+                    for (int b = 0; b < CT; ++b) x[b] = c0 + b < NRB ? X[a * NRB + c0 + b] : czero<C>();
+#pragma unroll
+                    for (int u = 0; u < PT; ++u)
+#pragma unroll
+                        for (int b = 0; b < CT; ++b) acc[u][b] = cfma(m[u], x[b], acc[u][b]);
+                }
+            }
+            C* Xo = Xs + (s & 1) * G * NRB;
+#pragma unroll
+            for (int u = 0; u < PT; ++u)
+#pragma unroll
+                for (int b = 0; b < CT; ++b)
+                    if (c0 + b < NRB) {
+                        Xo[(p0 + u) * NRB + c0 + b] = acc[u][b];
+                        q[((long long)k * G + p0 + u) * NRB + c0 + b] = acc[u][b];
+                    }
+        }
+    }
+    // ---- top-down: x_0 = q_0, x_k = q_k + Y_k x_{k-1}
+    cp_async_wait<0>();
+    __syncthreads();   // the bottom-up sweep's last reads of both stages are done
+    fetch(0, Y + GG, nullptr);   // (row 0 needs no map; stage 0 holds Y_1 for s = 1)
+    for (int s = 0; s < K; ++s) {
+        const int k = s;
+        cp_async_wait<0>();
+        __syncthreads();
+        if (s >= 1 && s + 1 < K) fetch(s & 1, Y + (long long)(k + 1) * GG, nullptr);   // Y_{k+1} into the other stage
+        if (act) {
+            C acc[PT][CT];
+#pragma unroll
+            for (int u = 0; u < PT; ++u)
+#pragma unroll
+                for (int b = 0; b < CT; ++b)
+                    acc[u][b] = c0 + b < NRB ? q[((long long)k * G + p0 + u) * NRB + c0 + b] : czero<C>();
+            if (s > 0) {
+                const C* M = Ms + (size_t)((s - 1) & 1) * 2 * G * LD;   // Y_k
+                const C* X = Xs + ((s + 1) & 1) * G * NRB;
+#pragma unroll 4
+                for (int a = 0; a < G; ++a) {
+                    C m[PT], x[CT];
+#pragma unroll
+                    for (int u = 0; u < PT; ++u) m[u] = M[(p0 + u) * LD + a];
+#pragma unroll
+                    for (int b = 0; b < CT; ++b) x[b] = c0 + b < NRB ? X[a * NRB + c0 + b] : czero<C>();
+#pragma unroll
+                    for (int u = 0; u < PT; ++u)
+#pragma unroll
+                        for (int b = 0; b < CT; ++b) acc[u][b] = cfma(m[u], x[b], acc[u][b]);
+                }
+            }
+            C* Xo = Xs + (s & 1) * G * NRB;
+#pragma unroll
+            for (int u = 0; u < PT; ++u) {
+                const int p = p0 + u;
+#pragma unroll
+                for (int b = 0; b < CT; ++b) {
+                    const int c = c0 + b, rq = r0 + c;
+                    if (c >= NRB) continue;
+                    Xo[p * NRB + c] = acc[u][b];
+                    if (rq >= A.R) continue;
+                    if (MODE == CR_A) {
+                        const long long o = ((long long)i * K + k) * A.R + rq;
+                        if (p == na) A.a_first[o] = acc[u][b];
+                        if (p == ll) A.a_last[o] = acc[u][b];
+                    } else if (p >= na && p <= ll) {
+                        const int x1 = sd.s + (p - na), i2 = k - A.b;
+                        if (A.y_grid)
+                            A.y[(long long)rq * nt2 + (long long)k * K + (x1 + A.b)] = to_d(acc[u][b]);
+                        else if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
+                            A.y[(long long)rq * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(acc[u][b]);
+                    }
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+}
+
 // The sweep's slab solves run per run of consecutive slabs with the same
 // block width, concurrently (run 0 on the caller's stream, the others on
 // auxiliary streams): each launch sizes its right-hand sides and ring stages
@@ -1722,11 +2087,69 @@ int prepare_chunk_tables(lss_ctx* c, cudaStream_t s) {
 }
 
 // One sweep pass (MODE CR_A or CR_E) over every slab, run by run.
+// Block LU solves switched off by LSS_SLAB_SOLVE=cr (cyclic reduction for every run).
+bool thomas_enabled() {
+    const char* v = std::getenv("LSS_SLAB_SOLVE");
+    return !(v && v[0] == 'c');
+}
+
+// Columns per CTA of the block LU solves.
+int th_nrb(int R) { return R >= 32 ? 32 : 16; }
+
+template <typename T>
+int thomas_prepare_t(lss_ctx* c, cudaStream_t s) {
+    using C = cx<T>;
+    if (c->th_valid) return LSS_OK;
+    const size_t bytes = sizeof(C) * (size_t)c->n_slabs * 3 * c->n_tot * 256;
+    int rc = lss_grow(c, &c->th_buf, &c->th_cap, bytes);
+    if (rc) return rc;
+    th_chain_kernel<T><<<c->n_slabs, 32, 0, s>>>(c->d_slabs, (const C*)c->coef, (C*)c->th_buf, c->n_tot, c->d_err);
+    rc = lss_check_cuda(c, cudaGetLastError(), "block LU factorization launch");
+    if (!rc) c->th_valid = true;
+    return rc;
+}
+
+// One run of nsl 16-wide slabs (from A.slab0) solved by the block LU; its
+// q scratch at tq_buf + q_off bytes.
+template <typename T, int MODE, int NRB>
+int launch_thomas_nrb(lss_ctx* c, const CrArgs<cx<T>>& A, int nsl, int R, cudaStream_t s, size_t q_off) {
+    using C = cx<T>;
+    const size_t sh = sizeof(C) * (4 * 16 * 17 + 4 * 16 * (size_t)NRB);
+    static size_t cfg = 0;
+    int rc = set_smem(c, th_solve_kernel<T, MODE, NRB>, sh, &cfg);
+    if (rc) return rc;
+    th_solve_kernel<T, MODE, NRB><<<dim3((R + NRB - 1) / NRB, nsl), kThThreads, sh, s>>>(
+        A, (const C*)c->th_buf, (C*)((char*)c->tq_buf + q_off));
+    return lss_check_cuda(c, cudaGetLastError(), "block LU solve launch");
+}
+
 template <typename T, int MODE>
-int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s) {
+int launch_thomas(lss_ctx* c, const CrArgs<cx<T>>& A, int nsl, int R, cudaStream_t s, size_t q_off) {
+    return th_nrb(R) == 32 ? launch_thomas_nrb<T, MODE, 32>(c, A, nsl, R, s, q_off)
+                           : launch_thomas_nrb<T, MODE, 16>(c, A, nsl, R, s, q_off);
+}
+
+// q scratch bytes of one run's block LU solves.
+template <typename T>
+size_t thomas_scratch(const lss_ctx* c, int nsl, int R) {
+    const int nrb = th_nrb(R);
+    return sizeof(cx<T>) * (size_t)((R + nrb - 1) / nrb) * nsl * c->n_tot * 16 * nrb;
+}
+
+template <typename T, int MODE>
+int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s, bool thomas = false) {
     const std::vector<SweepRun> runs = sweep_runs(c);
     int rc = lss_ensure_aux(c, runs.size());
     if (rc) return rc;
+    // 16-wide runs by the block LU when the caller prepared its factors
+    auto th_run = [&](const SweepRun& u) { return thomas && u.ldw == 16; };
+    size_t qtot = 0;
+    std::vector<size_t> qoff(runs.size());
+    for (size_t ri = 0; ri < runs.size(); ++ri) {
+        qoff[ri] = qtot;
+        if (th_run(runs[ri])) qtot += thomas_scratch<T>(c, runs[ri].n, R);
+    }
+    if (qtot && (rc = lss_grow(c, &c->tq_buf, &c->tq_cap, qtot))) return rc;
     // global right-hand-side scratch of every run, grown before any launch so
     // that concurrent runs use disjoint parts of one buffer
     // right-hand sides per CTA: two on 16-wide runs when the autotuner chose so
@@ -1746,7 +2169,9 @@ int sweep_pass(lss_ctx* c, CrArgs<cx<T>> A, int R, cudaStream_t s) {
         if (ri > 0) cudaStreamWaitEvent(su, c->fork_event, 0);
         CrArgs<cx<T>> Ar = A;
         Ar.slab0 = u.s0;
-        if (nr_of(u) == 2)
+        if (th_run(u))
+            rc = launch_thomas<T, MODE>(c, Ar, u.n, R, su, qoff[ri]);
+        else if (nr_of(u) == 2)
             rc = launch_solve<T, MODE, 2>(c, Ar, dim3((R + 1) / 2, u.n), 2LL * c->n_tot * u.ldw, nullptr, 0, su, u.ldw,
                                           zoff[ri]);
         else
@@ -2122,17 +2547,27 @@ int sweep_impl(lss_ctx* c, const double2* r, double2* y, int R, cudaStream_t s, 
     A.y = y;
     A.y_grid = grid_in ? 1 : 0;
     const int nrun = (int)sweep_runs(c).size();
+    // block LU solves for the 16-wide slabs with many right-hand sides; their
+    // factors are computed here when missing, but never inside a stream
+    // capture (a captured sweep without them uses the cyclic reduction)
+    bool thomas = R >= kThMinR && thomas_enabled();
+    if (thomas && !c->th_valid) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &cap);
+        if (cap != cudaStreamCaptureStatusNone) thomas = false;
+        else if ((rc = thomas_prepare_t<T>(c, s))) return rc;
+    }
     if (c->n_slabs > 1) {
         {
             ProfScope ps(c, s, LSS_PROF_SLAB_A, nrun);
-            rc = sweep_pass<T, CR_A>(c, A, R, s);
+            rc = sweep_pass<T, CR_A>(c, A, R, s, thomas);
         }
         if (rc) return rc;
         rc = launch_recur<T>(c, (const C*)c->iface, lam, phi, A.a_first, A.a_last, R, s);
         if (rc) return rc;
     }
     ProfScope ps(c, s, LSS_PROF_SLAB_E, nrun);
-    return sweep_pass<T, CR_E>(c, A, R, s);
+    return sweep_pass<T, CR_E>(c, A, R, s, thomas);
 }
 
 template <typename T>
@@ -2171,12 +2606,18 @@ int lss_ensure_aux(lss_ctx* c, size_t n) {
     return LSS_OK;
 }
 
+int lss_thomas_prepare(lss_ctx* c, int R, cudaStream_t s) {
+    if (c->dim != 2 || R < kThMinR || !thomas_enabled() || c->th_valid) return LSS_OK;
+    return c->prec == LSS_FP64 ? thomas_prepare_t<double>(c, s) : thomas_prepare_t<float>(c, s);
+}
+
 int lss_prepare_solve_tables(lss_ctx* c, cudaStream_t s) {
     return c->prec == LSS_FP64 ? prepare_chunk_tables<double>(c, s) : prepare_chunk_tables<float>(c, s);
 }
 
 int lss_factor_slabs(lss_ctx* c, cudaStream_t s) {
     c->iface_t_valid = false;
+    c->th_valid = false;
     return c->prec == LSS_FP64 ? factor_impl<double>(c, s) : factor_impl<float>(c, s);
 }
 
