@@ -200,6 +200,7 @@ struct lss_ctx {
     void* th_buf = nullptr; size_t th_cap = 0;          // block LU of the 16-wide slabs: T_k^{-1}, V_k, Y_k per block row
     void* tq_buf = nullptr; size_t tq_cap = 0;          // block LU solves: q_k per CTA
     bool th_valid = false;                              // th_buf holds the factors of the current medium
+    bool th_wanted = false;                             // a sweep used them: factorizations compute them
     int* host_flags = nullptr;                          // pinned host copies of the "RHS active" flag per iteration
     cudaEvent_t iter_ev[8] = {};                        // completion of the last iterations' flag copies
 

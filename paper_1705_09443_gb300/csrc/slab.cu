@@ -1853,6 +1853,15 @@ __global__ void __launch_bounds__(32) th_chain_kernel(const SlabDev* __restrict_
 // multiply-adds).  The per-row maps arrive by cp.async one step ahead, the
 // right-hand-side row is loaded one step ahead, q_k goes to a global scratch
 // (read back by the same thread in the top-down sweep).
+// Pass E's outputs on I go through a shared-memory buffer of kThYS block
+// rows, so that each right-hand side's values of one x1 line leave as
+// contiguous runs along x2 (the vector layout's fast index) instead of one
+// scattered entry per block row.
+constexpr int kThYS = 8;
+
+template <int NRB>
+constexpr size_t th_smem_entries() { return 4 * 16 * 17 + 4 * 16 * (size_t)NRB; }
+
 template <typename T, int MODE, int NRB>
 __global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, const cx<T>* __restrict__ th,
                                                              cx<T>* qscr) {
@@ -1864,6 +1873,7 @@ __global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, c
     C* Ms = reinterpret_cast<C*>(smt);   // [2 stages][2 maps][G x LD]
     C* Fs = Ms + 4 * G * LD;             // [2][G][NRB] right-hand-side rows
     C* Xs = Fs + 2 * G * NRB;            // [2][G][NRB] q / x rows
+    C* Yb = Xs + 2 * G * NRB;            // pass E on I: [G][NRB][kThYS]
     const int K = A.n_tot, tid = threadIdx.x;
     const int i = A.slab0 + blockIdx.y, r0 = blockIdx.x * NRB;
     const SlabDev sd = A.slabs[i];
@@ -2029,12 +2039,26 @@ __global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, c
                         if (p == na) A.a_first[o] = acc[u][b];
                         if (p == ll) A.a_last[o] = acc[u][b];
                     } else if (p >= na && p <= ll) {
-                        const int x1 = sd.s + (p - na), i2 = k - A.b;
-                        if (A.y_grid)
+                        const int x1 = sd.s + (p - na);
+                        if (A.y_grid) {
                             A.y[(long long)rq * nt2 + (long long)k * K + (x1 + A.b)] = to_d(acc[u][b]);
-                        else if (x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n)
-                            A.y[(long long)rq * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] = to_d(acc[u][b]);
+                        } else {
+                            Yb[((p - na) * NRB + c) * kThYS + k % kThYS] = acc[u][b];
+                        }
                     }
+                }
+            }
+        }
+        if (MODE == CR_E && !A.y_grid && (k % kThYS == kThYS - 1 || k == K - 1)) {
+            // rows k0 .. k of every line x1 of D_i and right-hand side, x2 fastest
+            __syncthreads();
+            const int k0 = k - k % kThYS, nk = k - k0 + 1, nl = ll - na + 1;
+            for (int e = tid; e < nl * NRB * kThYS; e += kThThreads) {
+                const int kk = e % kThYS, c = (e / kThYS) % NRB, pl = e / (kThYS * NRB);
+                const int rq = r0 + c, x1 = sd.s + pl, i2 = k0 + kk - A.b;
+                if (kk < nk && rq < A.R && x1 >= 1 && x1 <= A.n && i2 >= 1 && i2 <= A.n) {
+                    A.y[(long long)rq * A.n * A.n + (long long)(x1 - 1) * A.n + (i2 - 1)] =
+                        to_d(Yb[(pl * NRB + c) * kThYS + kk]);
                 }
             }
         }
@@ -2093,16 +2117,25 @@ bool thomas_enabled() {
     return !(v && v[0] == 'c');
 }
 
-// Columns per CTA of the block LU solves.
-int th_nrb(int R) { return R >= 32 ? 32 : 16; }
+// Columns per CTA of the block LU solves: 16 (at n = 512 with 64 right-hand
+// sides, 32 per CTA took 15.6 + 29.8 ms for the step's passes A and E, 16
+// took 15.1 + 18.9 ms: twice the CTAs, and pass E's output staging keeps
+// more of them resident).
+int th_nrb(int) { return 16; }
 
+// The block LU factors of every 16-wide slab (one warp per slab).  Called
+// when a sweep with many right-hand sides finds them missing; once a context
+// has used them, each later factorization computes them beside the cyclic
+// reduction and the interface maps (th_wanted), on an auxiliary stream.
 template <typename T>
 int thomas_prepare_t(lss_ctx* c, cudaStream_t s) {
     using C = cx<T>;
+    c->th_wanted = true;
     if (c->th_valid) return LSS_OK;
     const size_t bytes = sizeof(C) * (size_t)c->n_slabs * 3 * c->n_tot * 256;
     int rc = lss_grow(c, &c->th_buf, &c->th_cap, bytes);
     if (rc) return rc;
+    ProfScope ps(c, s, LSS_PROF_FACTOR, 1);
     th_chain_kernel<T><<<c->n_slabs, 32, 0, s>>>(c->d_slabs, (const C*)c->coef, (C*)c->th_buf, c->n_tot, c->d_err);
     rc = lss_check_cuda(c, cudaGetLastError(), "block LU factorization launch");
     if (!rc) c->th_valid = true;
@@ -2114,7 +2147,7 @@ int thomas_prepare_t(lss_ctx* c, cudaStream_t s) {
 template <typename T, int MODE, int NRB>
 int launch_thomas_nrb(lss_ctx* c, const CrArgs<cx<T>>& A, int nsl, int R, cudaStream_t s, size_t q_off) {
     using C = cx<T>;
-    const size_t sh = sizeof(C) * (4 * 16 * 17 + 4 * 16 * (size_t)NRB);
+    const size_t sh = sizeof(C) * th_smem_entries<NRB>() + (MODE == CR_E ? sizeof(C) * 16 * NRB * kThYS : 0);
     static size_t cfg = 0;
     int rc = set_smem(c, th_solve_kernel<T, MODE, NRB>, sh, &cfg);
     if (rc) return rc;
@@ -2211,7 +2244,18 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
     // slabs factor independently: run 0 on s, every other run on an auxiliary
     // stream of its own, forked after the level-0 blocks are built and joined
     // before the interface maps
-    if ((rc = lss_ensure_aux(c, runs.size()))) return rc;
+    if ((rc = lss_ensure_aux(c, runs.size() + 1))) return rc;
+    // the block LU factors (when this context's sweeps use them) on the last
+    // auxiliary stream, joined at the end of the factorization
+    const bool chain = c->th_wanted && thomas_enabled();
+    cudaStream_t sch = c->aux_stream[runs.size() - 1];
+    if (chain) {
+        if ((rc = lss_grow(c, &c->th_buf, &c->th_cap, sizeof(C) * (size_t)ns * 3 * K0 * 256))) return rc;
+        cudaEventRecord(c->fork_event, s);
+        cudaStreamWaitEvent(sch, c->fork_event, 0);
+        th_chain_kernel<T><<<ns, 32, 0, sch>>>(c->d_slabs, (const C*)c->coef, (C*)c->th_buf, K0, c->d_err);
+        if ((rc = lss_check_cuda(c, cudaGetLastError(), "block LU factorization launch"))) return rc;
+    }
     {
         ProfScope ps(c, s, LSS_PROF_FACTOR, 2 + (2 * nlev) * (int)runs.size());
         cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
@@ -2241,8 +2285,13 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
         }
     }
     rc = lss_check_cuda(c, cudaGetLastError(), "factor launch");
-    if (rc || ns == 1) return rc;
-    return lss_iface_maps(c, s);
+    if (!rc && ns > 1) rc = lss_iface_maps(c, s);
+    if (chain) {   // join the block LU chain (also on an error, so that nothing is left in flight)
+        cudaEventRecord(c->aux_event[runs.size() - 1], sch);
+        cudaStreamWaitEvent(s, c->aux_event[runs.size() - 1], 0);
+        if (!rc) c->th_valid = true;
+    }
+    return rc;
 }
 
 // Cluster size for the recurrence kernels: 16 CTAs when the GPU can
