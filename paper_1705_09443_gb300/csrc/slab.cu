@@ -1996,18 +1996,27 @@ __global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, c
     cp_async_wait<0>();
     __syncthreads();   // the bottom-up sweep's last reads of both stages are done
     fetch(0, Y + GG, nullptr);   // (row 0 needs no map; stage 0 holds Y_1 for s = 1)
+    C qn[PT][CT];                // q_k of this thread's tile, loaded one row ahead
+    auto load_q = [&](int k) {
+#pragma unroll
+        for (int u = 0; u < PT; ++u)
+#pragma unroll
+            for (int b = 0; b < CT; ++b)
+                qn[u][b] = (act && k < K && c0 + b < NRB) ? q[((long long)k * G + p0 + u) * NRB + c0 + b] : czero<C>();
+    };
+    load_q(0);
     for (int s = 0; s < K; ++s) {
         const int k = s;
         cp_async_wait<0>();
         __syncthreads();
         if (s >= 1 && s + 1 < K) fetch(s & 1, Y + (long long)(k + 1) * GG, nullptr);   // Y_{k+1} into the other stage
+        C acc[PT][CT];
+#pragma unroll
+        for (int u = 0; u < PT; ++u)
+#pragma unroll
+            for (int b = 0; b < CT; ++b) acc[u][b] = qn[u][b];
+        load_q(k + 1);
         if (act) {
-            C acc[PT][CT];
-#pragma unroll
-            for (int u = 0; u < PT; ++u)
-#pragma unroll
-                for (int b = 0; b < CT; ++b)
-                    acc[u][b] = c0 + b < NRB ? q[((long long)k * G + p0 + u) * NRB + c0 + b] : czero<C>();
             if (s > 0) {
                 const C* M = Ms + (size_t)((s - 1) & 1) * 2 * G * LD;   // Y_k
                 const C* X = Xs + ((s + 1) & 1) * G * NRB;
@@ -2158,8 +2167,7 @@ int launch_thomas_nrb(lss_ctx* c, const CrArgs<cx<T>>& A, int nsl, int R, cudaSt
 
 template <typename T, int MODE>
 int launch_thomas(lss_ctx* c, const CrArgs<cx<T>>& A, int nsl, int R, cudaStream_t s, size_t q_off) {
-    return th_nrb(R) == 32 ? launch_thomas_nrb<T, MODE, 32>(c, A, nsl, R, s, q_off)
-                           : launch_thomas_nrb<T, MODE, 16>(c, A, nsl, R, s, q_off);
+    return launch_thomas_nrb<T, MODE, 16>(c, A, nsl, R, s, q_off);
 }
 
 // q scratch bytes of one run's block LU solves.
