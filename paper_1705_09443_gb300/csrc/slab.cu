@@ -2265,7 +2265,7 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
         if ((rc = lss_check_cuda(c, cudaGetLastError(), "block LU factorization launch"))) return rc;
     }
     {
-        ProfScope ps(c, s, LSS_PROF_FACTOR, 2 + (2 * nlev) * (int)runs.size());
+        ProfScope ps(c, s, LSS_PROF_FACTOR, 2 + (2 * nlev) * (int)runs.size() + (chain ? 1 : 0));
         cr_build0_kernel<T><<<dim3(K0, ns), 128, 0, s>>>(c->d_slabs, (const C*)c->coef, work, fac, K0);
         cudaEventRecord(c->fork_event, s);
         for (size_t ri = 0; ri < runs.size(); ++ri) {
