@@ -32,6 +32,17 @@
  *  - Return value: LSS_OK (0) or a negative LSS_ERR_* code; lss_last_error()
  *    then describes the failure.  A failed call leaves the context usable
  *    unless the code is LSS_ERR_CUDA.
+ *
+ * Environment switches (read at each call; each selects between two exact
+ * implementations of the same operation, for comparison and testing):
+ *  - LSS_SLAB_SOLVE=cr: 2D slab solves always by the block cyclic reduction
+ *    (default: the 16-wide slabs of solves with R >= 16 by the block LU).
+ *  - LSS_BATCH_THREADS=1: a batch context solves each instance on its own
+ *    host thread (default: one lockstep Krylov driver for all instances).
+ *  - LSS_SOLVE_NR=2: two right-hand sides per cyclic-reduction CTA on 16-wide
+ *    slabs from the start (default: the autotuner decides).
+ *  - LSS_TC_UPDATE=0: the 3D mixed factorization's rank updates on CUDA
+ *    cores (default: 3xTF32 tcgen05 tensor cores).
  */
 #ifndef LSS_H
 #define LSS_H
