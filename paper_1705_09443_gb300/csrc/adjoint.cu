@@ -312,13 +312,13 @@ int launch_t(lss_ctx* c, TArgs<cx<T>> A, dim3 grid, cudaStream_t s) {
         if (rc) return rc;
         A.bg = (C*)c->z_buf;
     }
-    static size_t cfg = 0;
     std::unique_lock<std::mutex> lock(lss_config_mutex());
-    if (sh > cfg) {
+    long long& cfg = lss_dev_cache((const void*)cr_solve_t_kernel<T, MODE>, 0);
+    if ((long long)sh > cfg) {
         cudaError_t e = cudaFuncSetAttribute(cr_solve_t_kernel<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "transposed solve attribute");
-        cfg = sh;
+        cfg = (long long)sh;
     }
     lock.unlock();
     cr_solve_t_kernel<T, MODE><<<grid, kTThreads, sh, s>>>(A);

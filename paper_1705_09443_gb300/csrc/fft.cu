@@ -198,10 +198,10 @@ int lss_fft_kernel_table(lss_ctx* c, const double2* kc, cudaStream_t s) {
     return lss_check_cuda(c, cudaGetLastError(), "kernel table fft");
 }
 
-// Opt the FFT kernels into large dynamic shared memory once per process.
+// Opt the FFT kernels into large dynamic shared memory once per device.
 int lss_fft_configure(lss_ctx* c) {
     std::lock_guard<std::mutex> lock(lss_config_mutex());
-    static bool done = false;
+    long long& done = lss_dev_cache((const void*)&lss_fft_configure, 0);
     if (done) return LSS_OK;
     const int smax = kFftSmax;
     cudaError_t e = cudaSuccess;
@@ -215,6 +215,6 @@ int lss_fft_configure(lss_ctx* c) {
     if (!e) e = cudaFuncSetAttribute(mv_rows_inv<MV_OUT_AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     if (!e) e = cudaFuncSetAttribute(mv_rows_inv<MV_OUT_NEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
     if (e) return lss_check_cuda(c, e, "fft smem attribute");
-    done = true;
+    done = 1;
     return LSS_OK;
 }

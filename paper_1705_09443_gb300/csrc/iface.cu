@@ -497,28 +497,29 @@ int iface_impl(lss_ctx* c, cudaStream_t s) {
     A.maps = (C*)c->iface;
     A.psi = c->fronts == 2;
     const size_t sh = sizeof(C) * ((size_t)3 * gmax * gmax + (size_t)8 * gmax);
-    static size_t cfg_f = 0;
     std::unique_lock<std::mutex> lock(lss_config_mutex());
-    if (sh > cfg_f) {
+    long long& cfg_f = lss_dev_cache((const void*)if_fwd_kernel<T>, 0);
+    if ((long long)sh > cfg_f) {
         cudaError_t e = cudaFuncSetAttribute(if_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "interface attribute");
-        cfg_f = sh;
+        cfg_f = (long long)sh;
     }
     const size_t sht = sizeof(C) * ((size_t)2 * gmax * gmax + (size_t)2 * gmax * kBtNP);
     const size_t sh0 = sizeof(T) == 4 ? sizeof(C) * (size_t)kB0N * (gmax + 1) : 0;
-    static size_t cfg_t = 0, cfg_0 = 0;
-    if (sizeof(T) == 4 && sh0 > cfg_0) {
+    long long& cfg_t = lss_dev_cache((const void*)if_bwdt_kernel<T>, 0);
+    long long& cfg_0 = lss_dev_cache((const void*)if_bwd0_kernel<T>, 0);
+    if (sizeof(T) == 4 && (long long)sh0 > cfg_0) {
         cudaError_t e = cudaFuncSetAttribute(if_bwd0_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh0, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "interface attribute");
-        cfg_0 = sh0;
+        cfg_0 = (long long)sh0;
     }
-    if (sht > cfg_t) {
+    if ((long long)sht > cfg_t) {
         cudaError_t e = cudaFuncSetAttribute(if_bwdt_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sht, 48 * 1024));
         if (e) return lss_check_cuda(c, e, "interface attribute");
-        cfg_t = sht;
+        cfg_t = (long long)sht;
     }
     lock.unlock();
     const int L = cr_levels(K);

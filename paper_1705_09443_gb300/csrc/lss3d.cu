@@ -1079,11 +1079,8 @@ int dalloc3(lss_ctx* c, void** p, size_t bytes, const char* what) {
 
 int configure3(lss_ctx* c) {
     std::lock_guard<std::mutex> lock(lss_config_mutex());
-    int dev = 0;
-    cudaGetDevice(&dev);
-    static std::vector<int> done_dev;
-    for (int d : done_dev)
-        if (d == dev) return LSS_OK;
+    long long& done = lss_dev_cache((const void*)&configure3, 0);
+    if (done) return LSS_OK;
     const int smax = 200 * 1024;
     cudaError_t e = cudaSuccess;
     e = cudaFuncSetAttribute(mv3_rows_fwd<MV_IN_MU>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
@@ -1104,7 +1101,7 @@ int configure3(lss_ctx* c) {
     if (!e) e = cudaFuncSetAttribute(sweep3_kernel<double2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
     if (!e) e = cudaFuncSetAttribute(sweep3_kernel<float2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, psm);
     if (e) return lss_check_cuda(c, e, "3D kernel attributes");
-    done_dev.push_back(dev);
+    done = 1;
     return LSS_OK;
 }
 

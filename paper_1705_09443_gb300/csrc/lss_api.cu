@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lss_common.cuh"
@@ -113,6 +115,13 @@ ProfScope::~ProfScope() {
 std::mutex& lss_config_mutex() {
     static std::mutex m;
     return m;
+}
+
+long long& lss_dev_cache(const void* key, int slot) {
+    static std::map<std::tuple<const void*, int, int>, long long> cache;   // nodes never move
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return cache[std::make_tuple(key, slot, dev)];
 }
 
 // ---------------------------------------------------------------- status helpers

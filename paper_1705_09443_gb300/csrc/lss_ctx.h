@@ -238,10 +238,15 @@ struct ProfScope {
     ~ProfScope();
 };
 
-// Guards the process-wide, once-per-kernel launch configuration (shared
-// memory and cluster attributes, cached occupancy) when instances of a batch
-// are driven from several host threads.
+// Guards the once-per-kernel launch configuration (shared memory and cluster
+// attributes, cached occupancy) when instances of a batch are driven from
+// several host threads.
 std::mutex& lss_config_mutex();
+// The launch configuration applied or measured for (key, slot) on the current
+// device (kernel attributes are per device, and so are cluster sizes and
+// occupancy-derived grids); zero until a caller sets it.  Callers hold
+// lss_config_mutex().
+long long& lss_dev_cache(const void* key, int slot);
 
 // batch.cu: ragged instances (contexts made by lss_setup_batch)
 void lss_batch_free(lss_ctx* c);

@@ -1520,14 +1520,17 @@ long long max_row_ent(const lss_ctx* c) {
     return m;
 }
 
+// Opts kern into sh bytes of dynamic shared memory on the current device
+// (once per size increase).
 template <typename F>
-int set_smem(lss_ctx* c, F kern, size_t sh, size_t* configured) {
+int set_smem(lss_ctx* c, F kern, size_t sh) {
     std::lock_guard<std::mutex> lock(lss_config_mutex());
-    if (sh <= *configured) return LSS_OK;
+    long long& configured = lss_dev_cache((const void*)kern, 0);
+    if ((long long)sh <= configured) return LSS_OK;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max<size_t>(sh, 48 * 1024));
     if (e) return lss_check_cuda(c, e, "shared memory attribute");
-    *configured = sh;
+    configured = (long long)sh;
     return LSS_OK;
 }
 
@@ -1656,8 +1659,7 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
     A.tab32 = (const CrChunk*)tabs.t32;
     A.n16 = tabs.n16;
     A.n32 = tabs.n32;
-    static size_t cfg = 0;
-    rc = set_smem(c, kern, P.sh, &cfg);
+    rc = set_smem(c, kern, P.sh);
     if (rc) return rc;
     if (!A.bsm) {
         const size_t need = bb * (size_t)grid.x * grid.y;
@@ -2157,8 +2159,7 @@ template <typename T, int MODE, int NRB>
 int launch_thomas_nrb(lss_ctx* c, const CrArgs<cx<T>>& A, int nsl, int R, cudaStream_t s, size_t q_off) {
     using C = cx<T>;
     const size_t sh = sizeof(C) * th_smem_entries<NRB>() + (MODE == CR_E ? sizeof(C) * 16 * NRB * kThYS : 0);
-    static size_t cfg = 0;
-    int rc = set_smem(c, th_solve_kernel<T, MODE, NRB>, sh, &cfg);
+    int rc = set_smem(c, th_solve_kernel<T, MODE, NRB>, sh);
     if (rc) return rc;
     th_solve_kernel<T, MODE, NRB><<<dim3((R + NRB - 1) / NRB, nsl), kThThreads, sh, s>>>(
         A, (const C*)c->th_buf, (C*)((char*)c->tq_buf + q_off));
@@ -2245,9 +2246,8 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
     }
     auto shgw_of = [](int w) { return sizeof(C) * (size_t)w * (4 * w + 1); };
     const size_t shew = sizeof(C) * (size_t)6 * 32 * 33;
-    static size_t cfg_gw = 0, cfg_ew = 0;
-    int rc = set_smem(c, cr_gjw_kernel<T>, shgw_of(32), &cfg_gw);
-    if (!rc) rc = set_smem(c, cr_evenw_kernel<T>, shew, &cfg_ew);
+    int rc = set_smem(c, cr_gjw_kernel<T>, shgw_of(32));
+    if (!rc) rc = set_smem(c, cr_evenw_kernel<T>, shew);
     if (rc) return rc;
     // slabs factor independently: run 0 on s, every other run on an auxiliary
     // stream of its own, forked after the level-0 blocks are built and joined
@@ -2309,16 +2309,16 @@ int factor_impl(lss_ctx* c, cudaStream_t s) {
 template <typename T, int RW, int CW, int NT>
 int launch_chain_cfg(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, cudaStream_t s) {
     const size_t sh = 2 * (size_t)c->n_tot * R * sizeof(cx<T>);
-    static int cl_size = 0;
-    static size_t configured = 0;
     auto kern = recur_chain_kernel<T, RW, CW, NT>;
     std::unique_lock<std::mutex> lock(lss_config_mutex());
-    if (sh > configured) {
+    long long& configured = lss_dev_cache((const void*)kern, 0);   // shared memory opted into
+    long long& cl_size = lss_dev_cache((const void*)kern, 1);      // cluster size that co-schedules
+    if ((long long)sh > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)std::max<size_t>(sh, 48 * 1024));
         if (!e) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e) return lss_check_cuda(c, e, "recurrence attribute");
-        configured = sh;
+        configured = (long long)sh;
         cl_size = 0;
     }
     cudaLaunchConfig_t cfg{};
@@ -2342,7 +2342,7 @@ int launch_chain_cfg(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, 
         }
         if (!cl_size) return LSS_ERR_UNSUPPORTED;
     }
-    const int cl = cl_size;
+    const int cl = (int)cl_size;
     lock.unlock();
     const int rows_per = (c->n_tot + cl - 1) / cl;
     if ((rows_per * R + NT / 32 - 1) / (NT / 32) > RW || c->n_tot > 32 * CW) return LSS_ERR_UNSUPPORTED;
@@ -2361,14 +2361,14 @@ int launch_chain_tma(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, 
     using C = cx<T>;
     constexpr int NT = sizeof(T) == 8 ? 512 : 1024;   // a warp per (row, rhs) task where possible
     auto kern = recur_tma_kernel<T, NT>;
-    static int cl_size = 0;
-    static bool attr_done = false;
     std::unique_lock<std::mutex> lock(lss_config_mutex());
+    long long& attr_done = lss_dev_cache((const void*)kern, 0);
+    long long& cl_size = lss_dev_cache((const void*)kern, 1);   // cluster size that co-schedules
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (!e) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e) return lss_check_cuda(c, e, "recurrence attribute");
-        attr_done = true;
+        attr_done = 1;
     }
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute attr[1];
@@ -2395,7 +2395,7 @@ int launch_chain_tma(lss_ctx* c, const ChainPair<cx<T>>& P, int nchains, int R, 
         }
         if (!cl_size) return LSS_ERR_UNSUPPORTED;
     }
-    const int cl = cl_size;
+    const int cl = (int)cl_size;
     lock.unlock();
     int nb = c->tune.rec_nb ? std::min(c->tune.rec_nb, 4) : 3;   // full[] holds at most 4 stages
     while (nb >= 2 && smem_for(cl, nb) > (size_t)220 * 1024) --nb;
@@ -2527,11 +2527,10 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
                            (KernPtr)recur_grid2_kernel<T, 16, 1>, (KernPtr)recur_grid2_kernel<T, 16, 2>,
                            (KernPtr)recur_grid2_kernel<T, 16, 4>, (KernPtr)recur_grid2_kernel<T, 16, 8>};
     const void* k = two ? k2[var] : k1[var];
-    static int grid[2][6] = {};   // per (fronts, variant), this process's device
     int grid_now;
     {
         std::lock_guard<std::mutex> lock(lss_config_mutex());
-        int& g = grid[two][var];
+        long long& g = lss_dev_cache(k, 0);   // co-resident CTAs on this device
         if (!g) {
             if (smem) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2539,9 +2538,9 @@ int launch_recur(lss_ctx* c, const cx<T>* ifc, cx<T>* lam, cx<T>* phi, const cx<
             }
             int per = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, smem);
-            g = std::max(1, per) * c->num_sms;
+            g = (long long)std::max(1, per) * c->num_sms;
         }
-        grid_now = g;
+        grid_now = (int)g;
     }
     const long long tiles = prods * ((c->n_tot + TR - 1) / TR) * nct;
     int nb = (int)std::min<long long>(grid_now, std::max<long long>(1, tiles));

@@ -260,13 +260,14 @@ __global__ void __launch_bounds__(128) f3_update_tc(const Slab3* __restrict__ sl
 // slab (FP32 factors).
 int lss3_update_tc(lss_ctx* c, float2* W, const float2* T64, int J0, int NO, cudaStream_t s) {
     Ctx3* d = c->d3;
-    static int configured_dev = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(f3_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-        if (e) return lss_check_cuda(c, e, "tensor-core update attribute");
-        configured_dev = dev;
+    {
+        std::lock_guard<std::mutex> lock(lss_config_mutex());
+        long long& done = lss_dev_cache((const void*)f3_update_tc, 0);
+        if (!done) {
+            cudaError_t e = cudaFuncSetAttribute(f3_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+            if (e) return lss_check_cuda(c, e, "tensor-core update attribute");
+            done = 1;
+        }
     }
     const int tmax = (d->Mmax + 127) / 128;
     const long long slots = (long long)c->n_slabs * tmax * tmax;
