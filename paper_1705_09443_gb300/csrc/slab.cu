@@ -1889,24 +1889,55 @@ __global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, c
     const long long nt2 = (long long)K * K, vec = (long long)K * A.R;
     const C* cf = A.coef + sd.coef_off;
     // right-hand side entry (block row k, layer p, column c) of Algorithm 2's pass
-    auto rhs = [&](int k, int p, int c) -> C {
-        C v = czero<C>();
+    // Right-hand side entry (block row k, layer p, column c) of Algorithm 2's
+    // pass, in two halves so that its loads stay in flight for a whole block
+    // row: rhs_load issues them (the f value and, in pass E on the first or
+    // last layer, the three coupling coefficients and neighbour values of
+    // lambda_{i-1} or phi_{i+1}); rhs_value combines them one row later.  (A
+    // one-layer slab needs both couplings on one entry: rare, combined at once.)
+    struct RhsPre {
+        C f, cc[3], nb[3];
+    };
+    auto rhs_load = [&](int k, int p, int c, RhsPre& o) {
+        o.f = czero<C>();
+#pragma unroll
+        for (int d = 0; d < 3; ++d) o.cc[d] = o.nb[d] = czero<C>();
         const int rq = r0 + c;
-        if (c >= NRB || rq >= A.R || p >= w) return v;
-        if (p >= na && p <= ll) v = A.f[(long long)rq * nt2 + (long long)k * K + sd.s + A.b + (p - na)];
+        if (k < 0 || c >= NRB || rq >= A.R || p >= w) return;
+        if (p >= na && p <= ll) o.f = A.f[(long long)rq * nt2 + (long long)k * K + sd.s + A.b + (p - na)];
+        if (MODE != CR_E) return;
+        const C* ck = cf + (long long)k * sd.cstride + p * 9;
+        const bool left = p == na && i > 0, right = p == ll && i < A.n_slabs - 1;
+        if (left && right) {   // both couplings on one entry: combined here, in the usual order
+            C v = o.f;
+            for (int dk = -1; dk <= 1; ++dk) {
+                const int kk = k + dk;
+                if (kk >= 0 && kk < K) v = cfnma(ck[dk + 1], A.lam[(long long)(i - 1) * vec + (long long)kk * A.R + rq], v);
+            }
+            for (int dk = -1; dk <= 1; ++dk) {
+                const int kk = k + dk;
+                if (kk >= 0 && kk < K) v = cfnma(ck[6 + dk + 1], A.phi[(long long)(i + 1) * vec + (long long)kk * A.R + rq], v);
+            }
+            o.f = v;
+            return;
+        }
+        if (!left && !right) return;
+        const C* nbv = left ? A.lam + (long long)(i - 1) * vec : A.phi + (long long)(i + 1) * vec;
+        const int off = left ? 0 : 6;
+#pragma unroll
+        for (int dk = -1; dk <= 1; ++dk) {
+            const int kk = k + dk;
+            if (kk >= 0 && kk < K) {
+                o.cc[dk + 1] = ck[off + dk + 1];
+                o.nb[dk + 1] = nbv[(long long)kk * A.R + rq];
+            }
+        }
+    };
+    auto rhs_value = [&](const RhsPre& o) -> C {
+        C v = o.f;
         if (MODE == CR_E) {
-            const C* ck = cf + (long long)k * sd.cstride + p * 9;
-            if (p == na && i > 0)
-                for (int dk = -1; dk <= 1; ++dk) {
-                    const int kk = k + dk;
-                    if (kk >= 0 && kk < K) v = cfnma(ck[dk + 1], A.lam[(long long)(i - 1) * vec + (long long)kk * A.R + rq], v);
-                }
-            if (p == ll && i < A.n_slabs - 1)
-                for (int dk = -1; dk <= 1; ++dk) {
-                    const int kk = k + dk;
-                    if (kk >= 0 && kk < K)
-                        v = cfnma(ck[6 + dk + 1], A.phi[(long long)(i + 1) * vec + (long long)kk * A.R + rq], v);
-                }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v = cfnma(o.cc[d], o.nb[d], v);
         }
         return v;
     };
@@ -1918,19 +1949,19 @@ __global__ void __launch_bounds__(kThThreads) th_solve_kernel(CrArgs<cx<T>> A, c
         }
         cp_async_commit();
     };
-    C fr[FE];   // this thread's staged right-hand-side entries of the next row: e = tid + 128 u -> (c = e / G, p = e % G)
+    RhsPre fr[FE];   // this thread's entries of the next row in flight: e = tid + 128 u -> (c = e / G, p = e % G)
     auto load_f = [&](int k) {
 #pragma unroll
         for (int u = 0; u < FE; ++u) {
             const int e = tid + kThThreads * u;
-            fr[u] = (k >= 0 && e < G * NRB) ? rhs(k, e % G, e / G) : czero<C>();
+            rhs_load(e < G * NRB ? k : -1, e % G, e / G, fr[u]);
         }
     };
     auto store_f = [&](int stage) {
 #pragma unroll
         for (int u = 0; u < FE; ++u) {
             const int e = tid + kThThreads * u;
-            if (e < G * NRB) Fs[stage * G * NRB + (e % G) * NRB + e / G] = fr[u];
+            if (e < G * NRB) Fs[stage * G * NRB + (e % G) * NRB + e / G] = rhs_value(fr[u]);
         }
     };
     // ---- bottom-up: q_k = T_k^{-1} f_k + V_k q_{k+1}
