@@ -404,7 +404,10 @@ def run_leg(args, dev, world, flush, wname, prec, steps, warmup, recursive=False
     prof_ms, prof_n = profile_pass(s, step, 1)
     flat = [x for st in stats for x in st]
     out = {"workload": wname, "precision": "mixed" if prec else "fp64", "R": R, "fronts": leg_fronts(w),
-           "slab_solver": "recursive (inner sweep along x2)" if recursive else "block LU of the whole slab",
+           "slab_solver": ("recursive (inner sweep along x2)" if recursive else
+                           "block elimination of the whole slab along x2" if w.dim == 3 else
+                           "block LU on 16-wide slabs, cyclic reduction on the others" if R >= 16 else
+                           "block cyclic reduction"),
            "value": R * steps * world / (tot / 1e3), "unit": "solves/s", "ms_per_step": tot / steps,
            "solve_only": {"value": R * steps * world / (sum(ts_s) / 1e3), "ms_per_solve_call": sum(ts_s) / steps},
            "setup_factor_ms": float(ts_f[0]), "iters": float(np.mean([x["iters"] for x in flat])),
@@ -717,6 +720,9 @@ def main():
         "vs_baseline": None, "dtype": "c64 preconditioner / c128 operator, Arnoldi, Givens, true residual",
         "data": "synthetic",
         "config": {"workload": workload_text(w), "precision": "mixed (FP32 slab factors and sweep)",
+                   "slab_solver": ("block LU (bottom-up Schur complements along x2) on the 16-wide slabs, "
+                                   "block cyclic reduction on the 32-wide ones") if R >= 16 and w.dim == 2 else
+                                  "block cyclic reduction" if w.dim == 2 else "block elimination along x2",
                    "l2": "flushed (256 MB write) before every timed step; vectors exceed L2",
                    "per_omega_tables": "built once at solver creation (kernel FFT, alpha/beta, physical PML stencils)"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": head["e2e"],
