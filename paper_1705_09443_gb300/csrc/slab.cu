@@ -1690,11 +1690,13 @@ int launch_solve(lss_ctx* c, CrArgs<cx<T>> A, dim3 grid, long long per_cta, void
 // stored per block row as T_k^{-1}, V_k = -T_k^{-1} B_k and Y_k.  Solve:
 //   q_{K-1} = T_{K-1}^{-1} f_{K-1},  q_k = T_k^{-1} f_k + V_k q_{k+1}   (bottom-up)
 //   x_0 = q_0,  x_k = q_k + Y_k x_{k-1}                                  (top-down)
-// (rows C_k x_{k-1} + D_k x_k + B_k x_{k+1} = f_k; T_k x_k + C_k x_{k-1} =
-// f_k - B_k T_{k+1}^{-1} (...) by induction from the bottom row).  The
+// (For the rows C_k x_{k-1} + D_k x_k + B_k x_{k+1} = f_k: from the bottom row
+// up, T_k x_k + C_k x_{k-1} = g_k with g_{K-1} = f_{K-1} and
+// g_k = f_k - B_k T_{k+1}^{-1} g_{k+1}; q_k = T_k^{-1} g_k.)  The
 // factorization is a chain of K dependent 16 x 16 inversions per slab, one
 // warp each (Gauss-Jordan with partial pivoting by warp reductions and
-// shuffles), run once per factorization when a sweep first needs it.
+// shuffles): computed when a sweep first needs it, and from then on with
+// every factorization, on its own stream.
 constexpr int kThMinR = 16;
 constexpr int kThThreads = 128;
 constexpr int kThCoefMax = 16 * 9;
